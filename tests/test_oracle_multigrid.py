@@ -1,0 +1,154 @@
+"""Pins for the oracle's Q1 transfer, coarse matrix, AMG, block smoother,
+V-cycle (Algorithm 1) and Krylov solvers."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import amg, dg, solvers, transfer
+
+
+def small_problem(p=2, nc=(3, 2, 3), bc=(0, 0, 1, 0, 0, 1), seed=5, advect=False, react=False):
+    rng = np.random.default_rng(seed)
+    ncell = int(np.prod(nc))
+    K = np.exp(rng.normal(size=(ncell, 3)))
+    bv = None
+    if advect:
+        nv = [n + 1 for n in nc]
+        bv = rng.uniform(-1, 1, size=(int(np.prod(nv)), 3))
+    c = rng.uniform(0, 1, size=ncell) if react else None
+    return dg.Problem(*nc, 1.0, 0.8, 1.2, p, list(bc), K, b_vertex=bv, c_cell=c)
+
+
+def test_prolongation_reproduces_trilinear_functions():
+    """P is injection (Sec. 2.2.2): a trilinear function given by its vertex
+    values is reproduced exactly at every GLL node."""
+    P = small_problem(p=3)
+    Pm = transfer.prolongation(P)
+    q = lambda x, y, z: 1.0 + 2 * x - y + 0.5 * z + 3 * x * y - x * z + y * z - 2 * x * y * z
+    nx, ny, nz = P.nc
+    vals = np.zeros(P.nvert)
+    for vz in range(nz + 1):
+        for vy in range(ny + 1):
+            for vx in range(nx + 1):
+                vals[P.vertex_index(vx, vy, vz)] = q(vx * P.h[0], vy * P.h[1], vz * P.h[2])
+    np.testing.assert_allclose(Pm @ vals, P.interpolate(q), atol=1e-13)
+    np.testing.assert_allclose(Pm @ np.ones(P.nvert), 1.0, atol=1e-14)    # partition of unity
+
+
+@pytest.mark.parametrize("advect,react", [(False, False), (True, True)])
+def test_q1_rediscretisation_equals_galerkin_product(advect, react):
+    """App. A.2: re-discretising in Q1 (Dirichlet terms with gamma from the DG
+    degree p) gives exactly P^T A P."""
+    P = small_problem(p=2, advect=advect, react=react)
+    Pm = transfer.prolongation(P)
+    G = (Pm.T @ P.assemble() @ Pm).toarray()
+    Ah = transfer.q1_matrix(P).toarray()
+    assert np.abs(G - Ah).max() < 1e-13 * np.abs(G).max()
+
+
+def test_aggregation_shapes_and_galerkin():
+    Pa, cd = amg.aggregation((9, 9, 9))
+    assert cd == (5, 5, 5) and Pa.shape == (729, 125)
+    np.testing.assert_array_equal(np.asarray(Pa.sum(axis=1)).ravel(), 1.0)
+    Pa, cd = amg.aggregation((61, 221, 86))
+    assert cd == (31, 111, 43)
+
+
+def test_amg_symmetric_and_convergent():
+    """For symmetric A_hat the V-cycle (equal pre/post Jacobi) is a symmetric
+    operator, and as a stationary iteration it converges."""
+    P = small_problem(p=2, nc=(7, 6, 5), bc=(0,) * 6)
+    Ah = transfer.q1_matrix(P)
+    am = amg.AggregationAMG(Ah, P.nv, coarse_size=20)
+    assert am.nlevels >= 3
+    rng = np.random.default_rng(0)
+    x, y = rng.normal(size=P.nvert), rng.normal(size=P.nvert)
+    assert abs(y @ am.vcycle(x) - x @ am.vcycle(y)) < 1e-12 * abs(y @ am.vcycle(x))
+    b = rng.normal(size=P.nvert)
+    u = np.zeros_like(b)
+    r0 = np.linalg.norm(b)
+    for _ in range(30):
+        u = u + am.vcycle(b - Ah @ u)
+    assert np.linalg.norm(b - Ah @ u) < 1e-3 * r0
+    full = amg.AggregationAMG(Ah, P.nv, coarse_size=10 ** 6)    # one level: exact solve
+    assert np.abs(Ah @ full.vcycle(b) - b).max() < 1e-10 * np.abs(b).max()
+
+
+def test_block_pcg_and_gmres():
+    rng = np.random.default_rng(2)
+    P = small_problem(p=3, nc=(2, 2, 2))
+    D = P.diagonal_block(3)
+    d = rng.normal(size=P.N)
+    exact = np.linalg.solve(D, d)
+    x, it = solvers.block_pcg(D, d, np.diag(D), 1e-14, P.N)
+    assert np.abs(x - exact).max() < 1e-9 * np.abs(exact).max()
+    x, it = solvers.block_pcg(D, d, np.diag(D), 1e-2, P.N)
+    assert np.linalg.norm(d - D @ x) <= 1e-2 * np.linalg.norm(d) and it >= 1
+    Pa = small_problem(p=3, nc=(2, 2, 2), advect=True)
+    Da = Pa.diagonal_block(5)
+    exact = np.linalg.solve(Da, d)
+    x, it = solvers.block_gmres(Da, d, np.diag(Da), 1e-13, 10 * P.N, 12)
+    assert np.abs(x - exact).max() < 1e-8 * np.abs(exact).max()
+    x, it = solvers.block_gmres(Da, d, np.diag(Da), 1e-2, 10 * P.N, 12)
+    assert np.linalg.norm(d - Da @ x) <= 1e-2 * np.linalg.norm(d) * (1 + 1e-12)
+
+
+def test_block_jacobi_single_cell_is_exact():
+    P = small_problem(p=2, nc=(1, 1, 1), bc=(0,) * 6)
+    A = P.assemble()
+    f = np.random.default_rng(1).normal(size=P.ndof)
+    S = solvers.BlockJacobi(A, P.N, inner="lu")
+    u = S(f, np.zeros_like(f), 1, 1.0)
+    np.testing.assert_allclose(A @ u, f, atol=1e-12 * np.abs(f).max())
+
+
+def _c1_like(nx=4, p=2):
+    P = dg.Problem(nx, nx, nx, 1, 1, 1, p, [0] * 6, np.ones(nx ** 3))
+    A = P.assemble()
+    Pm = transfer.prolongation(P)
+    Ah = transfer.q1_matrix(P)
+    return P, A, Pm, Ah
+
+
+def test_vcycle_symmetric_with_exact_blocks():
+    """With exact block solves and n_pre = n_post, the V-cycle of Algorithm 1
+    (zero initial guess) is a symmetric linear operator for symmetric A."""
+    P, A, Pm, Ah = _c1_like()
+    am = amg.AggregationAMG(Ah, P.nv, coarse_size=10 ** 6)
+    V = solvers.HybridVCycle(A, Pm, solvers.BlockJacobi(A, P.N, inner="lu"), am.vcycle)
+    rng = np.random.default_rng(4)
+    x, y = rng.normal(size=P.ndof), rng.normal(size=P.ndof)
+    assert abs(y @ V(x) - x @ V(y)) < 1e-11 * abs(y @ V(x))
+
+
+def test_cg_vcycle_solves_poisson():
+    """CG + hybrid V-cycle (block-Jacobi, inner PCG eps = 1e-2, Q1 + AMG)
+    reaches 1e-8.  Smoke check of the inner iteration counts against Sec. 4.2
+    (mean below 4, maximum 15 for Poisson on the paper's smooth RHS): with a
+    random RHS the mean here is about 4.3, so the bound is mean < 5, max <= 15."""
+    P, A, Pm, Ah = _c1_like(nx=4, p=2)
+    am = amg.AggregationAMG(Ah, P.nv, coarse_size=30)
+    S = solvers.BlockJacobi(A, P.N, inner="pcg", eps=1e-2)
+    V = solvers.HybridVCycle(A, Pm, S, am.vcycle)
+    f = np.random.default_rng(9).normal(size=P.ndof)
+    x, it, hist = solvers.cg(lambda v: A @ v, f, V, rtol=1e-8)
+    assert np.linalg.norm(f - A @ x) <= 1e-8 * np.linalg.norm(f) * 1.0001
+    assert it < 40
+    assert S.last_its.mean() < 5 and S.last_its.max() <= 15
+    xf, itf, _ = solvers.cg(lambda v: A @ v, f, V, rtol=1e-8, flexible=True)
+    assert np.linalg.norm(f - A @ xf) <= 1e-8 * np.linalg.norm(f) * 1.0001
+    exact = spla.spsolve(A.tocsc(), f)
+    assert np.abs(x - exact).max() < 1e-5 * np.abs(exact).max()
+
+
+def test_fgmres_nonsymmetric():
+    P = small_problem(p=2, nc=(3, 3, 2), bc=(0,) * 6, advect=True)
+    A = P.assemble()
+    Pm = transfer.prolongation(P)
+    am = amg.AggregationAMG(transfer.q1_matrix(P), P.nv, coarse_size=10 ** 6)
+    V = solvers.HybridVCycle(A, Pm, solvers.BlockJacobi(A, P.N, inner="lu"), am.vcycle)
+    f = np.random.default_rng(8).normal(size=P.ndof)
+    x, it, hist = solvers.fgmres(lambda v: A @ v, f, V, restart=30, rtol=1e-10)
+    assert np.linalg.norm(f - A @ x) <= 1e-10 * np.linalg.norm(f) * 1.0001
+    exact = spla.spsolve(A.tocsc(), f)
+    assert np.abs(x - exact).max() < 1e-7 * np.abs(exact).max()

@@ -1,0 +1,221 @@
+"""Pins for the oracle's DG operator and right-hand side (Sec. 2.1, eqs.
+bilinear_form_split, rhs, linear_equation).
+
+Each test checks the assembled matrix against something fixed by the
+mathematics rather than by the code: closed-form values of a_h on
+piecewise-constant or piecewise-linear functions, symmetry and definiteness,
+conservation, exact reproduction of discrete (polynomial) solutions, and the
+O(h^(p+1)) convergence rate.  A swapped weight, a dropped term or a wrong
+sign in any part of a_h or l_h fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import dg
+
+ALPHA = 1.25
+
+
+def vertex_field(nc, L, fn):
+    nx, ny, nz = nc
+    out = []
+    for vz in range(nz + 1):
+        for vy in range(ny + 1):
+            for vx in range(nx + 1):
+                out.append(fn(vx * L[0] / nx, vy * L[1] / ny, vz * L[2] / nz))
+    return np.array(out)
+
+
+def boundary_values(P, fn):
+    vals = []
+    for cells, xyz in P.boundary_points():
+        vals.append(fn(xyz[..., 0], xyz[..., 1], xyz[..., 2]).reshape(-1))
+    return np.concatenate(vals)
+
+
+def test_symmetric_positive_definite_without_advection():
+    rng = np.random.default_rng(1805)
+    nc = (3, 2, 2)
+    K = np.exp(rng.normal(size=(12, 3)))
+    c = rng.uniform(0.0, 2.0, size=12)
+    P = dg.Problem(*nc, 1.0, 0.7, 1.3, 2, [0, 1, 0, 0, 1, 0], K, c_cell=c)
+    A = P.assemble().toarray()
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    np.linalg.cholesky(A)          # SPD: raises if not
+
+
+def test_neumann_kernel_and_conservation():
+    """All-Neumann, c = 0: A 1 = 0 when b = 0 (constants have zero energy),
+    and 1^T A = 0 for any b, since a_h(u, 1) has only the reaction term."""
+    rng = np.random.default_rng(7)
+    nc = (2, 2, 3)
+    K = np.exp(rng.normal(size=12))
+    P = dg.Problem(*nc, 1, 1, 1, 3, [1] * 6, K)
+    A = P.assemble()
+    assert np.abs(A @ np.ones(P.ndof)).max() < 1e-12 * abs(A).max()
+    b = vertex_field(nc, (1, 1, 1), lambda x, y, z: np.array([1 + x, y - 0.5 * z, 0.3]))
+    Pb = dg.Problem(*nc, 1, 1, 1, 3, [1] * 6, K, b_vertex=b)
+    Ab = Pb.assemble()
+    assert np.abs(Ab.T @ np.ones(P.ndof)).max() < 1e-12 * abs(Ab).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_interior_penalty_closed_form(p):
+    """u = 1 on cell 0 and 0 on cell 1 (Neumann elsewhere, b = 0): only the
+    penalty term survives, u^T A u = gamma_F |F| with
+    gamma_F = alpha p (p+2) <K0_xx, K1_xx> / h_x."""
+    K = np.array([[2.0, 5.0, 7.0], [0.5, 3.0, 1.0]])
+    P = dg.Problem(2, 1, 1, 1.0, 0.6, 0.3, p, [1] * 6, K)
+    A = P.assemble().toarray()
+    u = np.zeros(P.ndof)
+    u[:P.N] = 1.0
+    hx, hy, hz = 0.5, 0.6, 0.3
+    harm = 2 * 2.0 * 0.5 / 2.5
+    expected = ALPHA * p * (p + 2) * harm / hx * hy * hz
+    assert abs(u @ A @ u - expected) < 1e-12 * expected
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_dirichlet_penalty_closed_form(p):
+    """One cell, all Dirichlet, u = 1, b = 0, c = 0: u^T A u = sum over the six
+    faces of gamma_F |F| = sum_k 2 alpha p (p+2) K_kk |F_k| / h_k."""
+    K = np.array([[2.0, 3.0, 0.5]])
+    h = np.array([0.5, 0.25, 2.0])
+    P = dg.Problem(1, 1, 1, *h, p, [0] * 6, K)
+    A = P.assemble().toarray()
+    u = np.ones(P.N)
+    area = [h[1] * h[2], h[0] * h[2], h[0] * h[1]]
+    expected = sum(2 * ALPHA * p * (p + 2) * K[0, k] * area[k] / h[k] for k in range(3))
+    assert abs(u @ A @ u - expected) < 1e-12 * expected
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_weighted_average_closed_form(p):
+    """u = x on cell 0, 0 on cell 1; v = 1 on cell 1 (Neumann, b = 0).
+    a_h(u, v) = |F| K0 K1/(K0+K1) (1 - 2 alpha p (p+2)): the consistency term
+    carries w^- K0 = K1 K0/(K0+K1), the penalty gamma_F [[u]] [[v]] with
+    [[u]] = h_x, [[v]] = -1.  Swapping w^- and w^+ gives K0^2/(K0+K1)."""
+    K0, K1 = 4.0, 0.25
+    P = dg.Problem(2, 1, 1, 2.0, 1.0, 1.0, p, [1] * 6, np.array([K0, K1]))
+    A = P.assemble().toarray()
+    u = P.interpolate(lambda x, y, z: x)
+    u[P.N:] = 0.0
+    v = np.zeros(P.ndof)
+    v[P.N:] = 1.0
+    expected = K0 * K1 / (K0 + K1) * (1 - 2 * ALPHA * p * (p + 2))
+    assert abs(v @ A @ u - expected) < 1e-12 * abs(expected)
+    assert abs(u @ A @ v - expected) < 1e-12 * abs(expected)      # symmetry term
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_upwind_closed_form(p):
+    """Piecewise constants a, beta on two cells, b = (bx, 0, 0): the
+    advection part of u^T A u is the interior upwind flux |F| bx a (a - beta)
+    (bx > 0, u^- = a) plus the Dirichlet outflow term |F| bx beta^2; the
+    inflow face contributes nothing.  Downwinding would give bx beta (a - beta)."""
+    nc = (2, 1, 1)
+    K = np.ones(2) * 0.1
+    for bx in (1.5, -0.75):
+        b = vertex_field(nc, (2, 1, 1), lambda x, y, z: np.array([bx, 0.0, 0.0]))
+        P0 = dg.Problem(*nc, 2, 1, 1, p, [0] * 6, K)
+        Pb = dg.Problem(*nc, 2, 1, 1, p, [0] * 6, K, b_vertex=b)
+        Aadv = Pb.assemble().toarray() - P0.assemble().toarray()
+        a, beta = 0.8, -1.7
+        u = np.concatenate([np.full(P0.N, a), np.full(P0.N, beta)])
+        if bx > 0:
+            expected = bx * a * (a - beta) + bx * beta ** 2
+        else:   # flow towards -x: u^+ = beta is upwind; outflow through x = 0
+            expected = bx * beta * (a - beta) + (-bx) * a ** 2
+        assert abs(u @ Aadv @ u - expected) < 1e-12 * abs(expected)
+
+
+def _poly_problem(p, bc, K, b=None):
+    nc = (2, 3, 2)
+    L = (1.0, 1.5, 0.8)
+    bv = None if b is None else vertex_field(nc, L, b)
+    return dg.Problem(*nc, *L, p, bc, K, b_vertex=bv)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_discrete_solution_reproduced(p):
+    """u = 1 + x^2 + 2y^2 - 3z^2 + xy is in V_h for p >= 2; with anisotropic
+    constant K, f = -(2K1 + 4K2 - 6K3), Dirichlet g = u and Neumann
+    j = (b u - K grad u).nu, consistency of the method gives A u_I = F
+    exactly (every integrand is integrated exactly by the Gauss rule)."""
+    Kd = np.array([1.5, 0.5, 2.0])
+    bc = [0, 1, 0, 0, 1, 0]
+    P = _poly_problem(p, bc, np.tile(Kd, (12, 1)))
+    ue = lambda x, y, z: 1 + x ** 2 + 2 * y ** 2 - 3 * z ** 2 + x * y
+    grad = lambda x, y, z: (2 * x + y, 4 * y + x, -6 * z)
+    f = lambda x, y, z: -(2 * Kd[0] + 4 * Kd[1] - 6 * Kd[2]) + 0 * x
+    X = P.volume_points()
+    g = boundary_values(P, ue)
+    jv = []
+    for k in range(3):
+        for side in (0, 1):
+            cells, xyz = P.boundary_points()[2 * k + side]
+            gr = grad(xyz[..., 0], xyz[..., 1], xyz[..., 2])
+            nu = 1.0 if side == 1 else -1.0
+            jv.append((-Kd[k] * gr[k] * nu).reshape(-1))
+    F = P.rhs(f(X[..., 0], X[..., 1], X[..., 2]), g_qp=g, j_qp=np.concatenate(jv))
+    A = P.assemble()
+    uI = P.interpolate(ue)
+    assert np.abs(A @ uI - F).max() < 1e-12 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_advection_discrete_solution(p):
+    """u = x(1-x) y(1-y) z(1-z) with the divergence-free linear field
+    b = (2(1/2 - y), x - 1/2, 1/4), kappa = 1e-3, g = 0:
+    f = -kappa lap u + b . grad u, and A u_I = F exactly (Sec. 4.3 uses this u)."""
+    kap = 1e-3
+    nc = (3, 2, 2)
+    L = (1.0, 1.0, 1.0)
+    bf = lambda x, y, z: np.array([2 * (0.5 - y), x - 0.5, 0.25 + 0 * x])
+    P = dg.Problem(*nc, *L, p, [0] * 6, np.full(12, kap), b_vertex=vertex_field(nc, L, bf))
+    u = lambda x, y, z: x * (1 - x) * y * (1 - y) * z * (1 - z)
+
+    def f(x, y, z):
+        lap = -2 * (y * (1 - y) * z * (1 - z) + x * (1 - x) * z * (1 - z) + x * (1 - x) * y * (1 - y))
+        ux = (1 - 2 * x) * y * (1 - y) * z * (1 - z)
+        uy = x * (1 - x) * (1 - 2 * y) * z * (1 - z)
+        uz = x * (1 - x) * y * (1 - y) * (1 - 2 * z)
+        b = bf(x, y, z)
+        return -kap * lap + b[0] * ux + b[1] * uy + b[2] * uz
+
+    X = P.volume_points()
+    F = P.rhs(f(X[..., 0], X[..., 1], X[..., 2]), g_qp=boundary_values(P, lambda x, y, z: 0 * x))
+    A = P.assemble()
+    assert np.abs(A @ P.interpolate(u) - F).max() < 1e-12 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_convergence_order(p):
+    """-lap u = 3 pi^2 prod sin(pi x_k), u = 0 on the boundary: L2 error
+    O(h^(p+1)) over 2^3, 4^3, 8^3 meshes."""
+    import scipy.sparse.linalg as spla
+    u = lambda x, y, z: np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+    errs = []
+    for nx in (2, 4, 8):
+        P = dg.Problem(nx, nx, nx, 1, 1, 1, p, [0] * 6, np.ones(nx ** 3))
+        X = P.volume_points()
+        F = P.rhs(3 * np.pi ** 2 * u(X[..., 0], X[..., 1], X[..., 2]),
+                  g_qp=boundary_values(P, lambda x, y, z: 0 * x))
+        uh = spla.spsolve(P.assemble().tocsc(), F)
+        errs.append(P.l2_error(uh, u))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > p + 1 - 0.25, (errs, rates)
+
+
+def test_sampled_rows_match_assembly():
+    rng = np.random.default_rng(3)
+    nc = (3, 3, 2)
+    K = np.exp(rng.normal(size=(18, 3)))
+    b = vertex_field(nc, (1, 1, 1), lambda x, y, z: np.array([1 - y, x, 0.2]))
+    P = dg.Problem(*nc, 1, 1, 1, 2, [0, 1, 0, 1, 0, 0], K, b_vertex=b, c_cell=rng.uniform(size=18))
+    u = rng.uniform(-1, 1, P.ndof)
+    v = P.assemble() @ u
+    cells = [0, 4, 17, 9]
+    vs = P.apply_rows(u, cells)
+    for r, c in enumerate(cells):
+        np.testing.assert_allclose(vs[r], v[c * P.N:(c + 1) * P.N], rtol=0, atol=1e-13 * np.abs(v).max())
