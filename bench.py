@@ -1,0 +1,382 @@
+"""Benchmark of the matrix-free hybrid multigrid solve on GB300.
+
+One step = one complete solve of the variable-coefficient diffusion workload
+(log-normal K per cell, Q4 on a 32^3 hex mesh, 4,096,000 dofs): outer FP64 CG
+to a 1e-8 relative residual, preconditioned by one hybrid V-cycle (block-Jacobi
+with per-cell inner PCG to eps = 1e-2, Q1 coarse space with aggregation AMG).
+Every step of the hot path runs: operator apply, fused smoother, residual,
+restriction, AMG cycle, prolongation, Krylov vector kernels.
+
+  value      dofs solved per second (GDOF/s), inputs resident in HBM, L2
+             flushed between steps (a 256 MiB write outside the timed events)
+  e2e        the same through the C ABI with host buffers: f copied in from
+             pinned memory and u copied back, inside the timed region
+  roofline   the dominant kernel (the fused smoother, FP64), algorithmic FP64
+             operations per launch / its CUDA-event duration, against the
+             FP64 pipe peak (4 flop/clk/SM x 152 SMs x 2070 MHz)
+  extra      apply GDOF/s (FP64 and FP32), the mixed-precision solve time
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgmg|reference]
+Under torchrun (N > 1) each rank solves its own replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DG apply GDOF/s; solve s to 1e-8 residual (FP64 vs mixed); serve p99 latency"
+WORKLOAD = dict(kind="lognormal", n=32, p=4)
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4          # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz)
+SM_MAX_MHZ = 2070.0
+CPU_SAMPLE = dict(n=6, p=4)        # oracle sample: same workload family, 6^3 cells
+
+
+def fp64_peak_tflops():
+    mhz = SM_MAX_MHZ
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return SM_COUNT * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- workload
+def make_workload():
+    from paper_1805_11930_gb300 import inputs
+    return inputs.lognormal(WORKLOAD["n"], WORKLOAD["p"])
+
+
+def setup_context(w, device):
+    import torch
+    from paper_1805_11930_gb300 import dgmg, inputs
+    ctx = dgmg.Context(device)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
+    vol, face = ctx.quadrature_points()
+    s = ctx.sizes()
+    f = torch.empty(s["ndof"], dtype=torch.float64, device=f"cuda:{device}")
+    ctx.assemble_rhs(inputs.evaluate(w["f"], vol), f, g_qp=inputs.evaluate(w["g"], face),
+                     j_qp=inputs.evaluate(w["j"], face))
+    return ctx, f, s
+
+
+def run_dgmg(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1805_11930_gb300 import dgmg, flops
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    w = make_workload()
+    ctx, f, s = setup_context(w, local_rank)
+    ndof, ncell, n = s["ndof"], s["ncell"], w["p"] + 1
+    stream = torch.cuda.current_stream(local_rank)
+    u = torch.zeros_like(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts = dgmg.default_opts(timing=1)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        u.zero_()
+        ctx.solve(f, u, opts)
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    stats = []
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u.zero_()
+        st = ctx.solve(f, u, opts)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ndof * args.steps * world / (total_ms / 1e3) / 1e9
+
+    # dominant kernel: the fused smoother (CUDA events around each launch)
+    sm_ms = sum(x["ms_smooth"] for x in stats)
+    ap_ms = sum(x["ms_apply"] for x in stats)
+    sweeps = sum(x["sweeps"] for x in stats)
+    zero = sum(x["zero_sweeps"] for x in stats)
+    its = sum(x["inner_its_total"] for x in stats)
+    sm_flops = flops.smoother_total(n, ncell, sweeps, zero, its)
+    ap_flops = flops.apply_full(n) * ncell * sum(x["applies"] for x in stats)
+    peak = fp64_peak_tflops()
+    dominant = "smoother" if sm_ms >= ap_ms else "apply"
+    if dominant == "smoother":
+        achieved = sm_flops / (sm_ms / 1e3) / 1e12
+        per_launch = sm_flops / max(sweeps, 1)
+        launch_ms = sm_ms / max(sweeps, 1)
+    else:
+        nap = sum(x["applies"] for x in stats)
+        achieved = ap_flops / (ap_ms / 1e3) / 1e12
+        per_launch = ap_flops / max(nap, 1)
+        launch_ms = ap_ms / max(nap, 1)
+    roofline = {"bound": "alu", "kernel": "k_smooth_pcg<double>" if dominant == "smoother" else "k_apply<double>",
+                "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "flops_per_launch": per_launch, "launch_ms": round(launch_ms, 4),
+                "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x sm_max_mhz (derived, nominal 1.25 TFLOP/s)",
+                "time_share": {"smoother": round(sm_ms / total_ms, 3) if world == 1 else None,
+                               "apply": round(ap_ms / total_ms, 3) if world == 1 else None}}
+
+    # apply throughput, FP64 and FP32 (separate timed loop, inputs resident)
+    def time_apply(dtype, reps=20):
+        x = torch.rand(ndof, dtype=dtype, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ctx.apply(x, y)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.apply(x, y)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ndof / (statistics.median(ms) / 1e3) / 1e9, statistics.median(ms)
+
+    apply64, apply64_ms = time_apply(torch.float64)
+    apply32, apply32_ms = time_apply(torch.float32)
+
+    # mixed precision solve (FP32 smoother and V-cycle, FP64 flexible CG)
+    mixed = dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
+    for _ in range(2):
+        u.zero_()
+        ctx.solve(f, u, mixed)
+    mixed_ms = []
+    mst = None
+    for _ in range(3):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        u.zero_()
+        mst = ctx.solve(f, u, mixed)
+        b.record(stream)
+        b.synchronize()
+        mixed_ms.append(a.elapsed_time(b))
+
+    # end to end through the C ABI with host buffers
+    f_host = f.cpu().pin_memory()
+    u_host = torch.empty(ndof, dtype=torch.float64).pin_memory()
+    f_dev = torch.empty_like(f)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f_dev.copy_(f_host, non_blocking=True)
+        u.zero_()
+        ctx.solve(f_dev, u, dgmg.default_opts())
+        u_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(ndof * args.steps * world / e2e_s / 1e9, 6), "unit": "GDOF/s",
+           "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
+
+    last = stats[-1]
+    out = {
+        "metric": METRIC, "value": round(value, 6), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"variable-coefficient diffusion, log-normal K per cell (sigma 1, seed 1805), "
+                               f"SIPG Q{w['p']} on {WORKLOAD['n']}^3 hexes, {ndof} dofs, FP64 CG + hybrid V-cycle "
+                               f"(block-Jacobi, inner PCG eps 1e-2, Q1 + AMG), rtol 1e-8",
+                   "ndof": ndof, "p": w["p"], "mesh": list(w["nc"]), "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "gpu_launches": int(sum(x["kernel_launches"] for x in stats)),
+        "roofline": roofline,
+        "clocks": clk,
+        "solve": {"iterations": last["iterations"], "rel_residual": last["rel_residual"],
+                  "inner_mean": round(last["inner_mean"], 3), "inner_max": last["inner_max"],
+                  "solve_s_fp64": round(total_ms / args.steps / 1e3, 5),
+                  "solve_s_mixed": round(statistics.median(mixed_ms) / 1e3, 5),
+                  "mixed_iterations": mst["iterations"], "mixed_rel_residual": mst["rel_residual"]},
+        "apply": {"gdofs_fp64": round(apply64, 4), "ms_fp64": round(apply64_ms, 4),
+                  "gdofs_fp32": round(apply32, 4), "ms_fp32": round(apply32_ms, 4)},
+    }
+    return out
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+def oracle_solve_sample():
+    """The CPU oracle (MX design: assembled block-CSR A, PCG on dense blocks,
+    P^T A P + AMG, CG) on a bounded sample of the same workload family.
+    Returns (dofs per second of the solve phase, description)."""
+    import numpy as np
+    from oracle import amg, dg, solvers, transfer
+    from paper_1805_11930_gb300 import inputs
+    w = inputs.lognormal(CPU_SAMPLE["n"], CPU_SAMPLE["p"])
+    t0 = time.perf_counter()
+    P = dg.Problem(*w["nc"], *w["L"], w["p"], w["bc"], w["K"])
+    A = P.assemble()
+    X = P.volume_points()
+    pts = np.concatenate([xyz.reshape(-1, 3) for _, xyz in P.boundary_points()])
+    F = P.rhs(inputs.evaluate(w["f"], X), g_qp=inputs.evaluate(w["g"], pts))
+    Pm = transfer.prolongation(P)
+    am = amg.AggregationAMG(transfer.q1_matrix(P), P.nv)
+    S = solvers.BlockJacobi(A, P.N, inner="pcg", eps=1e-2)
+    V = solvers.HybridVCycle(A, Pm, S, am.vcycle)
+    t1 = time.perf_counter()
+    x, it, hist = solvers.cg(lambda v: A @ v, F, V, rtol=1e-8)
+    t2 = time.perf_counter()
+    desc = (f"oracle solve of lognormal {CPU_SAMPLE['n']}^3 Q{CPU_SAMPLE['p']} ({P.ndof} dofs), "
+            f"CG {it} its to {hist[-1]:.1e}, setup {t1 - t0:.1f} s excluded, solve {t2 - t1:.1f} s, 1 thread")
+    return P.ndof / (t2 - t1), t2 - t1, desc
+
+
+def cpu_baseline_subprocess():
+    """Run the oracle sample in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker"], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(d["dofs_per_s"] / 1e9, 9), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+            "sample": d["desc"], "seconds": round(d["seconds"], 2)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is one bounded oracle solve."""
+    vals = []
+    desc = ""
+    secs = 0.0
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline_subprocess()
+        if cb["value"] is None:
+            return {"impl": "reference", "unavailable": cb["sample"]}
+        vals.append(cb["value"])
+        desc = cb["sample"]
+        secs += cb["seconds"]
+    v = statistics.median(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": 1,
+            "steps": len(vals), "warmup": 0, "ms_per_step": round(secs / len(vals) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bounded sample: " + desc},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dgmg", choices=["dgmg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-worker", action="store_true")
+    args = ap.parse_args()
+
+    if args.cpu_baseline_worker:
+        dps, secs, desc = oracle_solve_sample()
+        print(json.dumps({"dofs_per_s": dps, "seconds": secs, "desc": desc}))
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_dgmg(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_subprocess()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * dgmg.h -- C ABI of the GB300 matrix-free hybrid multigrid library for
+ * SIPG / upwind Discontinuous Galerkin discretisations on hexahedral grids
+ * (Bastian, Mueller, Muething, Piatkowski, arXiv 1805.11930).
+ *
+ * Problem (Sec. 2, eq. linearproblem):  div(b u - K grad u) + c u = f on the
+ * box [0,Lx]x[0,Ly]x[0,Lz], u = g on Dirichlet planes, (b u - K grad u).nu = j
+ * on Neumann planes.  Discretisation (Sec. 2.1): weighted SIPG with upwind flux,
+ * tensor-product Q_p Gauss-Lobatto nodal basis, Gauss quadrature with p+1 points
+ * per direction, penalty alpha p (p+2) <delta-,delta+> |F| / min|T| with
+ * alpha = 1.25.
+ *
+ * Conventions shared by every call:
+ *  - A uniform nx x ny x nz grid; cell (cx,cy,cz) has index cx + nx (cy + ny cz).
+ *  - A DG vector is cell-major: n^3 values per cell (n = p+1), dof (i1,i2,i3)
+ *    at offset i1 + n i2 + n^2 i3 inside its cell.  Unpadded, contiguous.
+ *  - A vertex (Q1) vector has (nx+1)(ny+1)(nz+1) values, vertex (vx,vy,vz) at
+ *    vx + (nx+1)(vy + (ny+1) vz).
+ *  - Boundary planes are ordered -x,+x,-y,+y,-z,+z; bc[i] = 0 Dirichlet,
+ *    1 Neumann.
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller,
+ *    which must stay valid until the work queued on the context's stream has
+ *    finished.  Pointers marked "host" are read or written before the call
+ *    returns.  The library owns the context, its copies of mesh and
+ *    coefficients, and its workspace.
+ *  - FP64 vectors are double, FP32 vectors float; `prec` selects which.
+ *  - Every call is stream-ordered on the stream given to dgmg_create and
+ *    returns a dgmg_status; on an error nothing is queued unless stated.
+ *    dgmg_last_error() gives the message.  A context must not be used from
+ *    two threads at once; separate contexts are independent.
+ */
+#ifndef DGMG_H
+#define DGMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgmg_ctx dgmg_ctx;
+
+typedef enum {
+  DGMG_OK = 0,
+  DGMG_ERR_ARG = 1,            /* invalid argument; nothing modified            */
+  DGMG_ERR_OOM = 2,            /* device allocation failed                      */
+  DGMG_ERR_CUDA = 3,           /* CUDA runtime error (message has the details)  */
+  DGMG_ERR_STATE = 4,          /* call needs set_mesh / set_coefficients first  */
+  DGMG_ERR_NOT_CONVERGED = 5,  /* solve hit maxit; u holds the last iterate     */
+  DGMG_ERR_BREAKDOWN = 6,      /* Krylov breakdown (p^T A p <= 0, zero norm)    */
+  DGMG_ERR_TIMEOUT = 7         /* reserved: a bounded device wait gave up       */
+} dgmg_status;
+
+typedef enum { DGMG_FP64 = 0, DGMG_FP32 = 1 } dgmg_prec;
+typedef enum { DGMG_KRYLOV_CG = 0, DGMG_KRYLOV_FCG = 1, DGMG_KRYLOV_FGMRES = 2 } dgmg_krylov;
+typedef enum { DGMG_INNER_PCG = 0, DGMG_INNER_GMRES = 1 } dgmg_inner;
+typedef enum { DGMG_COARSE_AMG = 0, DGMG_COARSE_NONE = 1 } dgmg_coarse;
+
+/* Options of the hybrid V-cycle (Algorithm 1) and of the outer Krylov solve. */
+typedef struct {
+  int krylov;          /* dgmg_krylov: CG (Sec. 4.2), flexible CG, FGMRES (Sec. 4.3) */
+  int restart;         /* FGMRES restart length (default 30)                       */
+  double rtol;         /* outer stop: ||r||_2 <= rtol ||r_0||_2 (default 1e-8)     */
+  int maxit;           /* outer iteration cap (default 500)                        */
+  int smoother_prec;   /* dgmg_prec of the V-cycle's DG part (smoother, residual)  */
+  double omega;        /* block-Jacobi damping (Algorithm 2), default 0.8          */
+  int npre, npost;     /* smoothing sweeps (default 1, 1)                          */
+  double eps_inner;    /* block solve: reduce ||d - D_T x||_2 by eps (default 1e-2) */
+  int maxit_inner;     /* block solve iteration cap (default n^3 when <= 0)        */
+  int inner;           /* dgmg_inner: PCG (symmetric) or GMRES (b != 0)            */
+  int inner_restart;   /* inner GMRES restart (default 12)                         */
+  int coarse;          /* dgmg_coarse: Q1 + AMG correction, or none               */
+  int timing;          /* 1: time smoother and operator launches with CUDA events */
+} dgmg_solve_opts;
+
+typedef struct {
+  int iterations;       /* outer iterations                                       */
+  int converged;        /* 1 if the recomputed FP64 residual met rtol             */
+  double rel_residual;  /* ||f - A u||_2 / ||f - A u_0||_2, recomputed in FP64    */
+  double inner_mean;    /* mean inner block-solve iterations over all cells/sweeps */
+  int inner_max;        /* maximum inner iterations seen                          */
+  double ms_total;      /* wall time of the solve (host clock, stream synced)    */
+  long long inner_its_total;  /* sum over cells and sweeps of inner iterations     */
+  long long sweeps;           /* block-Jacobi sweeps (one smoother launch each)    */
+  long long zero_sweeps;      /* of which started from u = 0 (no defect apply)     */
+  long long applies;          /* full-operator applications (one launch each)      */
+  long long kernel_launches;  /* all kernels this library launched in the solve    */
+  double ms_smooth;     /* device time of the smoother launches (opts->timing)    */
+  double ms_apply;      /* device time of the operator launches (opts->timing)    */
+} dgmg_solve_stats;
+
+/* Fill *opts with the defaults listed above. */
+void dgmg_default_opts(dgmg_solve_opts* opts);
+
+/* Create a context on CUDA `device`; `cuda_stream` is a cudaStream_t (NULL =
+ * the legacy default stream).  *out receives the context. */
+dgmg_status dgmg_create(dgmg_ctx** out, int device, void* cuda_stream);
+dgmg_status dgmg_destroy(dgmg_ctx* ctx);
+const char* dgmg_last_error(const dgmg_ctx* ctx);
+
+/* Grid and degree (Sec. 2.1, uniform axis-parallel hexahedra): 1 <= p <= 8,
+ * n* >= 1, L* > 0, bc[6] in {0,1} (host).  Discards coefficients and
+ * workspace of an earlier mesh. */
+dgmg_status dgmg_set_mesh(dgmg_ctx* ctx, int nx, int ny, int nz, double lx, double ly,
+                          double lz, int p, const int bc[6]);
+
+/* Coefficients, piecewise constant per cell except b (Sec. 2, eq.
+ * linearproblem; Sec. 4.2 evaluates K and c at cell centres in the
+ * preconditioner).
+ *   K: host, ncell*kdim values > 0; kdim 1 = scalar, 3 = diagonal (Kxx,Kyy,Kzz).
+ *   b_vertex: host, 3*nvert values (bx,by,bz per vertex) of a continuous
+ *     trilinear advection field, or NULL for b = 0.
+ *   c_cell: host, ncell values, or NULL for c = 0.
+ * Also computes diag(D_T) and the Q1 coarse matrix and AMG hierarchy (setup,
+ * Sec. 2.2.3 and App. A.2).  Synchronises the stream. */
+dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim,
+                                  const double* b_vertex, const double* c_cell);
+
+/* Sizes of the current mesh: DG dofs, vertices, cells, volume quadrature
+ * points (ncell (p+1)^3) and boundary-face quadrature points over all six
+ * planes (2 (ny nz + nx nz + nx ny) (p+1)^2). */
+dgmg_status dgmg_sizes(const dgmg_ctx* ctx, long long* ndof, long long* nvert, long long* ncell,
+                       long long* nvol_qp, long long* nface_qp);
+
+/* Physical coordinates (x,y,z interleaved, host) of the quadrature points at
+ * which dgmg_assemble_rhs expects data.  Volume: cell-major, point
+ * q1 + m q2 + m^2 q3 within a cell.  Faces: planes -x,+x,-y,+y,-z,+z; within a
+ * plane normal to axis k with tangential axes a < b, cells ordered ca + n_a cb,
+ * points qa + m qb within a cell face.  Either pointer may be NULL. */
+dgmg_status dgmg_quadrature_points(const dgmg_ctx* ctx, double* vol_xyz, double* face_xyz);
+
+/* Right-hand side f_i = l_h(psi_i) (Sec. 2.1, eq. rhs) from values at the
+ * quadrature points of dgmg_quadrature_points (all host, FP64):
+ * f_qp (nvol_qp), g_qp and j_qp (nface_qp, read only on Dirichlet resp.
+ * Neumann planes; NULL = 0).  rhs: device FP64, ndof. */
+dgmg_status dgmg_assemble_rhs(dgmg_ctx* ctx, const double* f_qp, const double* g_qp,
+                              const double* j_qp, double* rhs);
+
+/* v = A u, matrix-free and sum-factorised (Sec. 3.1: volume terms by 1D
+ * contractions to the Gauss points and back; interior and boundary face terms
+ * of eq. bilinear_form_split).  u, v: device, ndof values of `prec`; u != v. */
+dgmg_status dgmg_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec);
+
+/* v = D u with D the block diagonal, D_T u_T = A^v_TT u_T + own-side face
+ * terms (Sec. 3.2, eq. block_diag_apply).  u, v: device, ndof; u != v. */
+dgmg_status dgmg_block_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec);
+
+/* diag(D_T) of every cell (Sec. 3.2, the inner preconditioner), device, ndof. */
+dgmg_status dgmg_block_diagonal(dgmg_ctx* ctx, void* diag, dgmg_prec prec);
+
+/* nsweep block-Jacobi sweeps (Algorithm 2): d = f - A u; solve D_T x_T = d_T
+ * per cell matrix-free (inner = PCG with 1/diag(D_T), or right-preconditioned
+ * GMRES(inner_restart)) until ||d_T - D_T x_T||_2 <= eps ||d_T||_2 or maxit
+ * iterations (maxit <= 0 means n^3); u += omega x.  One fused kernel per sweep.
+ * f, u: device, ndof, `prec`; u is updated in place.  inner_its: device int
+ * array of ncell receiving the last sweep's per-cell iteration counts, or
+ * NULL. */
+dgmg_status dgmg_block_smooth(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega,
+                              double eps, int maxit, int inner, int inner_restart,
+                              dgmg_prec prec, int* inner_its);
+
+/* r_hat = R r with R = P^T, the Q1 restriction (Sec. 2.2.2).  r: device DG
+ * vector of `prec`; r_hat: device FP64 vertex vector (overwritten). */
+dgmg_status dgmg_restrict(dgmg_ctx* ctx, const void* r, double* r_hat, dgmg_prec prec);
+
+/* u += P u_hat, Q1 prolongation by injection, (P|_T)_ij = psi_hat_j(zeta_i)
+ * (Sec. 2.2.2).  u_hat: device FP64 vertex vector; u: device DG vector. */
+dgmg_status dgmg_prolong_add(dgmg_ctx* ctx, const double* u_hat, void* u, dgmg_prec prec);
+
+/* The Q1 matrix A_hat by re-discretisation (Sec. 2.2.3, App. A.2) as a 27-point
+ * stencil: stencil[v*27 + (dx+1) + 3(dy+1) + 9(dz+1)] = A_hat(v, v+(dx,dy,dz))
+ * (0 outside the grid).  stencil: host, 27*nvert doubles. */
+dgmg_status dgmg_coarse_matrix(const dgmg_ctx* ctx, double* stencil);
+
+/* u_hat = one aggregation-AMG V-cycle on A_hat from zero (Algorithm 1, AMG step):
+ * 2x2x2 vertex aggregates, piecewise-constant transfer, Galerkin levels, one
+ * pre- and post-sweep of Jacobi (2/3), dense solve below 512 unknowns.
+ * r_hat, u_hat: device FP64 vertex vectors, distinct. */
+dgmg_status dgmg_coarse_cycle(dgmg_ctx* ctx, const double* r_hat, double* u_hat);
+
+/* One hybrid V-cycle (Algorithm 1) for A u = f starting from the u given
+ * (pass zeros for the preconditioner form): presmooth, residual, restrict,
+ * AMG, prolongate-add, postsmooth, with opts (NULL = defaults).  The DG part
+ * runs in opts->smoother_prec, the coarse part in FP64.  f, u: device FP64. */
+dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts);
+
+/* Solve A u = f to ||r||_2 <= rtol ||r_0||_2 with CG, flexible CG or
+ * right-preconditioned flexible GMRES(restart), preconditioned by one V-cycle
+ * (Sec. 4.2, 4.3).  Outer vectors, dot products and the final residual check
+ * are FP64.  f: device FP64; u: device FP64, initial guess in, solution out.
+ * stats: host or NULL.  Synchronises the stream. */
+dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
+                       dgmg_solve_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGMG_H */

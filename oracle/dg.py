@@ -197,11 +197,11 @@ class Problem:
         val, g = self.vol_val, self.vol_grad
         K = self.K[c]
         bq = self.b_at(c, self.vol_xi)
-        A = np.einsum('q,kl,qjl,qik->ij', w, K, g, g)
-        A -= np.einsum('q,qk,qj,qik->ij', w, bq, val, g)
+        A = np.einsum('q,kl,qjl,qik->ij', w, K, g, g, optimize=True)
+        A -= np.einsum('q,qk,qj,qik->ij', w, bq, val, g, optimize=True)
         cc = self.c_of(c)
         if cc != 0.0:
-            A += cc * np.einsum('q,qj,qi->ij', w, val, val)
+            A += cc * np.einsum('q,qj,qi->ij', w, val, val, optimize=True)
         return A
 
     def interior_face_matrix(self, cm, k):
@@ -233,10 +233,10 @@ class Problem:
         bnu = self.b_at(cm, xm) @ nu
         Phi = np.where(bnu[:, None] >= 0.0, bnu[:, None] * VM, bnu[:, None] * VP)
         gamma = self.penalty_interior(dm, dp, k)
-        A = np.einsum('q,qJ,qI->IJ', w, Phi, jump)
-        A -= np.einsum('q,qJ,qI->IJ', w, avg, jump)
-        A -= np.einsum('q,qI,qJ->IJ', w, avg, jump)
-        A += gamma * np.einsum('q,qJ,qI->IJ', w, jump, jump)
+        A = np.einsum('q,qJ,qI->IJ', w, Phi, jump, optimize=True)
+        A -= np.einsum('q,qJ,qI->IJ', w, avg, jump, optimize=True)
+        A -= np.einsum('q,qI,qJ->IJ', w, avg, jump, optimize=True)
+        A += gamma * np.einsum('q,qJ,qI->IJ', w, jump, jump, optimize=True)
         return A, cp
 
     def boundary_face_block(self, c, k, side):
@@ -253,10 +253,10 @@ class Problem:
         bnu = self.b_at(c, xi) @ nu
         Phi = np.where(bnu[:, None] >= 0.0, bnu[:, None] * v, 0.0)
         gamma = self.penalty_boundary(delta, k)
-        A = np.einsum('q,qj,qi->ij', w, Phi, v)
-        A -= np.einsum('q,qj,qi->ij', w, fl, v)
-        A -= np.einsum('q,qi,qj->ij', w, fl, v)
-        A += gamma * np.einsum('q,qj,qi->ij', w, v, v)
+        A = np.einsum('q,qj,qi->ij', w, Phi, v, optimize=True)
+        A -= np.einsum('q,qj,qi->ij', w, fl, v, optimize=True)
+        A -= np.einsum('q,qi,qj->ij', w, fl, v, optimize=True)
+        A += gamma * np.einsum('q,qj,qi->ij', w, v, v, optimize=True)
         return A
 
     def is_boundary(self, c, k, side):
@@ -361,7 +361,7 @@ class Problem:
         F = np.zeros(self.ndof)
         f_qp = np.asarray(f_qp, dtype=np.float64).reshape(self.ncell, -1)
         for c in range(self.ncell):
-            F[c * N:(c + 1) * N] += np.einsum('q,q,qi->i', self.vol_w, f_qp[c], self.vol_val)
+            F[c * N:(c + 1) * N] += np.einsum('q,q,qi->i', self.vol_w, f_qp[c], self.vol_val, optimize=True)
         off = 0
         mm = self.m * self.m
         for k in range(3):
@@ -378,20 +378,20 @@ class Problem:
                     if self.bc[2 * k + side] == 1:
                         if j_qp is not None:
                             jv = np.asarray(j_qp, dtype=np.float64)[sl]
-                            F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, jv, v)
+                            F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, jv, v, optimize=True)
                         continue
                     if g_qp is None:
                         continue
                     gv = np.asarray(g_qp, dtype=np.float64)[sl]
                     Kc = self.K[c]
                     delta = nu @ Kc @ nu
-                    fl = np.einsum('l,qil->qi', Kc @ nu, g)
+                    fl = np.einsum('l,qil->qi', Kc @ nu, g, optimize=True)
                     bnu = self.b_at(c, xi) @ nu
                     phi = np.where(bnu >= 0.0, 0.0, bnu * gv)       # Phi(0, g, b_nu)
                     gamma = self.penalty_boundary(delta, k)
-                    F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, phi, v)
-                    F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, gv, fl)
-                    F[c * N:(c + 1) * N] += gamma * np.einsum('q,q,qi->i', w, gv, v)
+                    F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, phi, v, optimize=True)
+                    F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, gv, fl, optimize=True)
+                    F[c * N:(c + 1) * N] += gamma * np.einsum('q,q,qi->i', w, gv, v, optimize=True)
         return F
 
     def interpolate(self, fn):

@@ -104,11 +104,11 @@ def q1_matrix(prob):
     for c in range(prob.ncell):
         K = prob.K[c]
         bq = prob.b_at(c, pts)
-        blk = np.einsum('q,kl,qjl,qik->ij', wv, K, grad, grad)
-        blk -= np.einsum('q,qk,qj,qik->ij', wv, bq, val, grad)
+        blk = np.einsum('q,kl,qjl,qik->ij', wv, K, grad, grad, optimize=True)
+        blk -= np.einsum('q,qk,qj,qik->ij', wv, bq, val, grad, optimize=True)
         cc = prob.c_of(c)
         if cc != 0.0:
-            blk += cc * np.einsum('q,qj,qi->ij', wv, val, val)
+            blk += cc * np.einsum('q,qj,qi->ij', wv, val, val, optimize=True)
         scatter(c, blk)
     # Dirichlet boundary terms of a^bf with gamma from the DG degree p.
     for k in range(3):
@@ -123,13 +123,13 @@ def q1_matrix(prob):
             for c in prob.boundary_cells(k, side):
                 K = prob.K[c]
                 delta = nu @ K @ nu
-                fl = np.einsum('l,qjl->qj', K @ nu, gr)
+                fl = np.einsum('l,qjl->qj', K @ nu, gr, optimize=True)
                 bnu = prob.b_at(c, xi) @ nu
                 Phi = np.where(bnu[:, None] >= 0.0, bnu[:, None] * v, 0.0)
                 gamma = prob.penalty_boundary(delta, k)
-                blk = np.einsum('q,qj,qi->ij', wf, Phi, v)
-                blk -= np.einsum('q,qj,qi->ij', wf, fl, v)
-                blk -= np.einsum('q,qi,qj->ij', wf, fl, v)
-                blk += gamma * np.einsum('q,qj,qi->ij', wf, v, v)
+                blk = np.einsum('q,qj,qi->ij', wf, Phi, v, optimize=True)
+                blk -= np.einsum('q,qj,qi->ij', wf, fl, v, optimize=True)
+                blk -= np.einsum('q,qi,qj->ij', wf, fl, v, optimize=True)
+                blk += gamma * np.einsum('q,qj,qi->ij', wf, v, v, optimize=True)
                 scatter(c, blk)
     return sp.csr_matrix((vals, (rows, cols)), shape=(prob.nvert, prob.nvert))

@@ -1,0 +1,906 @@
+// The C ABI of include/dgmg.h: context, mesh and coefficient setup, the
+// matrix-free operator and smoother entry points, the hybrid V-cycle
+// (Algorithm 1 of arXiv 1805.11930) and the outer Krylov drivers.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dgmg.h"
+#include "dgmg_internal.h"
+#include "setup_host.h"
+
+namespace dgmg {
+unsigned long long g_launches = 0;
+
+const CellOps* cell_ops_n2();
+const CellOps* cell_ops_n3();
+const CellOps* cell_ops_n4();
+const CellOps* cell_ops_n5();
+const CellOps* cell_ops_n6();
+const CellOps* cell_ops_n7();
+const CellOps* cell_ops_n8();
+const CellOps* cell_ops_n9();
+
+const CellOps* cell_ops(int n) {
+  switch (n) {
+    case 2: return cell_ops_n2();
+    case 3: return cell_ops_n3();
+    case 4: return cell_ops_n4();
+    case 5: return cell_ops_n5();
+    case 6: return cell_ops_n6();
+    case 7: return cell_ops_n7();
+    case 8: return cell_ops_n8();
+    case 9: return cell_ops_n9();
+    default: return nullptr;
+  }
+}
+
+namespace {
+__global__ void k_its_acc(long long n, const int* __restrict__ its, unsigned long long* sum, int* mx) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    atomicAdd(sum, (unsigned long long)its[i]);
+    atomicMax(mx, its[i]);
+  }
+}
+}  // namespace
+}  // namespace dgmg
+
+using namespace dgmg;
+
+struct AmgLevel {
+  int vx, vy, vz;
+  long long n;
+  double* st = nullptr;
+  double* dinv = nullptr;
+  double* b = nullptr;
+  double* x = nullptr;
+  double* xt = nullptr;
+  double* r = nullptr;
+};
+
+struct dgmg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool has_mesh = false, has_coef = false;
+  int nx = 0, ny = 0, nz = 0, p = 0, n = 0;
+  double L[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  long long ncell = 0, ndof = 0, nvert = 0;
+  const CellOps* ops = nullptr;
+  int kdim = 1;
+  std::vector<double> hK, hb, hc, q1;
+  double *dK = nullptr, *dc = nullptr, *db = nullptr;
+  double* diag64 = nullptr;
+  float* diag32 = nullptr;
+  double* w64[3] = {nullptr, nullptr, nullptr};
+  float* w32[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* corners = nullptr;
+  int* its = nullptr;
+  unsigned long long* itsum = nullptr;
+  int* itmax = nullptr;
+  double *rhat = nullptr, *uhat = nullptr;
+  std::vector<AmgLevel> lv;
+  double* coarse_inv = nullptr;
+  int coarse_n = 0;
+  double* kry = nullptr;
+  size_t kry_vecs = 0;
+  double* dot_partial = nullptr;
+  double* dot_out = nullptr;
+  double* dot_host = nullptr;      // pinned
+  const double** dot_ptrs = nullptr;  // device array of vector pointers
+  bool track_its = false;
+  long long sweeps_tracked = 0;
+  // per-launch CUDA-event timing of the smoother and operator kernels
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  std::vector<std::pair<size_t, size_t>> ev_smooth, ev_apply;
+  long long n_apply = 0, n_sweep = 0, n_zero_sweep = 0;
+  std::vector<void*> mesh_allocs;  // freed on a new mesh
+};
+
+namespace {
+
+constexpr int kMaxDots = 72;
+
+dgmg_status fail(dgmg_ctx* c, dgmg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+size_t record_event(dgmg_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ctx->ev.push_back(e);
+  }
+  cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream);
+  return ctx->ev_used++;
+}
+
+#define CK(expr)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, DGMG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+#define CS(expr)                      \
+  do {                                \
+    dgmg_status s_ = (expr);          \
+    if (s_ != DGMG_OK) return s_;     \
+  } while (0)
+
+template <typename T>
+dgmg_status dalloc(dgmg_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DGMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->mesh_allocs.push_back((void*)*p);
+  return DGMG_OK;
+}
+
+void free_mesh(dgmg_ctx* ctx) {
+  for (void* q : ctx->mesh_allocs) cudaFree(q);
+  ctx->mesh_allocs.clear();
+  ctx->dK = ctx->dc = ctx->db = ctx->diag64 = nullptr;
+  ctx->diag32 = nullptr;
+  for (auto& w : ctx->w64) w = nullptr;
+  for (auto& w : ctx->w32) w = nullptr;
+  ctx->corners = nullptr;
+  ctx->its = nullptr;
+  ctx->itsum = nullptr;
+  ctx->itmax = nullptr;
+  ctx->rhat = ctx->uhat = nullptr;
+  ctx->lv.clear();
+  ctx->coarse_inv = nullptr;
+  ctx->kry = nullptr;
+  ctx->kry_vecs = 0;
+  ctx->has_coef = false;
+}
+
+MeshParams params(const dgmg_ctx* ctx) {
+  MeshParams m;
+  m.nx = ctx->nx;
+  m.ny = ctx->ny;
+  m.nz = ctx->nz;
+  m.p = ctx->p;
+  m.ncell = ctx->ncell;
+  for (int d = 0; d < 3; ++d) m.h[d] = ctx->h[d];
+  for (int i = 0; i < 6; ++i) m.bc[i] = ctx->bc[i];
+  m.K = ctx->dK;
+  m.kdim = ctx->kdim;
+  m.c = ctx->dc;
+  m.bvert = ctx->db;
+  m.alpha = 1.25;
+  return m;
+}
+
+HostMesh host_mesh(const dgmg_ctx* ctx) {
+  HostMesh m;
+  m.nx = ctx->nx;
+  m.ny = ctx->ny;
+  m.nz = ctx->nz;
+  m.p = ctx->p;
+  for (int d = 0; d < 3; ++d) m.h[d] = ctx->h[d];
+  for (int i = 0; i < 6; ++i) m.bc[i] = ctx->bc[i];
+  m.K = ctx->hK.data();
+  m.kdim = ctx->kdim;
+  m.b = ctx->hb.empty() ? nullptr : ctx->hb.data();
+  m.c = ctx->hc.empty() ? nullptr : ctx->hc.data();
+  m.alpha = 1.25;
+  return m;
+}
+
+dgmg_status ready(dgmg_ctx* ctx) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (!ctx->has_mesh || !ctx->has_coef) return fail(ctx, DGMG_ERR_STATE, "set_mesh and set_coefficients first");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, cudaGetErrorString(e));
+  return DGMG_OK;
+}
+
+// ------------------------------------------------------------------ dots
+dgmg_status dot(dgmg_ctx* ctx, const double* x, const double* y, double& out) {
+  CK(vec_dot(ctx->ndof, x, y, ctx->dot_partial, ctx->dot_out, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dot_host, ctx->dot_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out = ctx->dot_host[0];
+  return DGMG_OK;
+}
+
+dgmg_status multi_dot(dgmg_ctx* ctx, int k, double* const* xs, const double* y, double* out) {
+  CK(cudaMemcpyAsync(ctx->dot_ptrs, xs, k * sizeof(double*), cudaMemcpyHostToDevice, ctx->stream));
+  CK(vec_multi_dot(ctx->ndof, k, ctx->dot_ptrs, y, ctx->dot_partial, ctx->dot_out, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dot_host, ctx->dot_out, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < k; ++i) out[i] = ctx->dot_host[i];
+  return DGMG_OK;
+}
+
+// ------------------------------------------------------------------ smoother
+// nsweep block-Jacobi sweeps on u (in place) with ping-pong through tmp.
+dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, int nsweep, double omega, double eps,
+                            int maxit, int inner, int restart, bool fp32, bool zero_first, int* its) {
+  if (nsweep <= 0) {
+    if (zero_first) {
+      if (fp32)
+        CK(vec_fill_f(ctx->ndof, 0.f, (float*)u, ctx->stream));
+      else
+        CK(vec_fill(ctx->ndof, 0.0, (double*)u, ctx->stream));
+    }
+    return DGMG_OK;
+  }
+  if (maxit <= 0) maxit = ctx->n * ctx->n * ctx->n;
+  if (inner != DGMG_INNER_PCG) return fail(ctx, DGMG_ERR_ARG, "inner GMRES block solve is not built yet");
+  const MeshParams mp = params(ctx);
+  void* src = u;
+  void* dst = tmp;
+  for (int k = 0; k < nsweep; ++k) {
+    SmoothArgs a;
+    a.f = f;
+    a.uold = (k == 0 && zero_first) ? nullptr : src;
+    a.unew = dst;
+    a.diag = fp32 ? (const void*)ctx->diag32 : (const void*)ctx->diag64;
+    a.omega = omega;
+    a.eps = eps;
+    a.maxit = maxit;
+    a.inner = inner;
+    a.restart = restart;
+    a.its = (its || ctx->track_its) ? ctx->its : nullptr;
+    const size_t e0 = ctx->timing ? record_event(ctx) : 0;
+    CK(ctx->ops->smooth(mp, a, fp32, ctx->stream));
+    if (ctx->timing) ctx->ev_smooth.push_back({e0, record_event(ctx)});
+    ++ctx->n_sweep;
+    if (k == 0 && zero_first) ++ctx->n_zero_sweep;
+    if (ctx->track_its) {
+      k_its_acc<<<152 * 8, 256, 0, ctx->stream>>>(ctx->ncell, ctx->its, ctx->itsum, ctx->itmax);
+      count_launch();
+      CK(cudaGetLastError());
+      ++ctx->sweeps_tracked;
+    }
+    void* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != u) CK(cudaMemcpyAsync(u, src, ctx->ndof * (fp32 ? 4 : 8), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (its && its != ctx->its)
+    CK(cudaMemcpyAsync(its, ctx->its, ctx->ncell * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+  return DGMG_OK;
+}
+
+// ------------------------------------------------------------------ AMG
+dgmg_status amg_cycle(dgmg_ctx* ctx, int l, const double* b, double* xout) {
+  const int last = (int)ctx->lv.size() - 1;
+  if (l == last) {
+    CK(dense_matvec(ctx->coarse_n, ctx->coarse_inv, b, xout, ctx->stream));
+    return DGMG_OK;
+  }
+  AmgLevel& L = ctx->lv[l];
+  AmgLevel& C = ctx->lv[l + 1];
+  const double w = 2.0 / 3.0;
+  CK(stencil_jacobi(L.vx, L.vy, L.vz, L.st, L.dinv, b, nullptr, L.xt, w, true, ctx->stream));
+  CK(stencil_residual(L.vx, L.vy, L.vz, L.st, b, L.xt, L.r, ctx->stream));
+  CK(agg_restrict(L.vx, L.vy, L.vz, L.r, C.b, ctx->stream));
+  CS(amg_cycle(ctx, l + 1, C.b, C.x));
+  CK(agg_prolong_add(L.vx, L.vy, L.vz, C.x, L.xt, ctx->stream));
+  CK(stencil_jacobi(L.vx, L.vy, L.vz, L.st, L.dinv, b, L.xt, xout, w, false, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status restrict_internal(dgmg_ctx* ctx, const void* r, double* rhat, bool fp32) {
+  const MeshParams mp = params(ctx);
+  CK(ctx->ops->restrict_cells(mp, r, ctx->corners, fp32, ctx->stream));
+  CK(restrict_gather(ctx->nx, ctx->ny, ctx->nz, ctx->corners, rhat, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, bool fp32);
+
+// ------------------------------------------------------------------ V-cycle
+// One V-cycle of Algorithm 1 on FP64 f, u (u updated in place; zero: u == 0 on entry).
+dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, bool zero) {
+  const bool fp32 = o.smoother_prec == DGMG_FP32;
+  const MeshParams mp = params(ctx);
+  const long long n = ctx->ndof;
+  void *F, *U, *T1, *T2;
+  if (fp32) {
+    F = ctx->w32[0];
+    U = ctx->w32[1];
+    T1 = ctx->w32[2];
+    T2 = ctx->w32[3];
+    CK(vec_d2f(n, f, (float*)F, ctx->stream));
+    if (!zero) CK(vec_d2f(n, u, (float*)U, ctx->stream));
+  } else {
+    F = (void*)f;
+    U = u;
+    T1 = ctx->w64[0];
+    T2 = ctx->w64[1];
+  }
+  CS(smooth_internal(ctx, F, U, T1, o.npre, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, fp32,
+                     zero, nullptr));
+  const bool u_zero = zero && o.npre <= 0;
+  if (o.coarse == DGMG_COARSE_AMG) {
+    // r = f - A u
+    if (u_zero) {
+      CS(restrict_internal(ctx, F, ctx->rhat, fp32));
+    } else {
+      CS(timed_apply(ctx, U, T2, fp32));
+      if (fp32)
+        CK(vec_sub_f(n, (const float*)F, (const float*)T2, (float*)T2, ctx->stream));
+      else
+        CK(vec_sub(n, (const double*)F, (const double*)T2, (double*)T2, ctx->stream));
+      CS(restrict_internal(ctx, T2, ctx->rhat, fp32));
+    }
+    CS(amg_cycle(ctx, 0, ctx->rhat, ctx->uhat));
+    CK(ctx->ops->prolong_add(mp, ctx->uhat, U, fp32, ctx->stream));
+    CS(smooth_internal(ctx, F, U, T1, o.npost, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, fp32,
+                       false, nullptr));
+  } else {
+    CS(smooth_internal(ctx, F, U, T1, o.npost, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, fp32,
+                       u_zero, nullptr));
+  }
+  if (fp32) CK(vec_f2d(n, (const float*)U, u, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, bool fp32) {
+  const MeshParams mp = params(ctx);
+  const size_t e0 = ctx->timing ? record_event(ctx) : 0;
+  CK(ctx->ops->apply(mp, u, v, fp32, true, ctx->stream));
+  if (ctx->timing) ctx->ev_apply.push_back({e0, record_event(ctx)});
+  ++ctx->n_apply;
+  return DGMG_OK;
+}
+
+dgmg_status ensure_krylov(dgmg_ctx* ctx, size_t nvec) {
+  if (ctx->kry_vecs >= nvec) return DGMG_OK;
+  if (ctx->kry) {
+    for (auto it = ctx->mesh_allocs.begin(); it != ctx->mesh_allocs.end(); ++it)
+      if (*it == (void*)ctx->kry) {
+        ctx->mesh_allocs.erase(it);
+        break;
+      }
+    cudaFree(ctx->kry);
+    ctx->kry = nullptr;
+    ctx->kry_vecs = 0;
+  }
+  CS(dalloc(ctx, &ctx->kry, nvec * (size_t)ctx->ndof));
+  ctx->kry_vecs = nvec;
+  return DGMG_OK;
+}
+
+dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_opts& o) {
+  CK(vec_fill(ctx->ndof, 0.0, z, ctx->stream));
+  return vcycle_internal(ctx, r, z, o, true);
+}
+
+dgmg_status apply64(dgmg_ctx* ctx, const double* u, double* v) { return timed_apply(ctx, u, v, false); }
+
+dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, dgmg_solve_stats& st) {
+  const long long n = ctx->ndof;
+  const bool flex = o.krylov == DGMG_KRYLOV_FCG;
+  CS(ensure_krylov(ctx, flex ? 5 : 4));
+  double* r = ctx->kry;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* ro = flex ? q + n : nullptr;
+  CS(apply64(ctx, u, q));
+  CK(vec_sub(n, f, q, r, ctx->stream));
+  double rr;
+  CS(dot(ctx, r, r, rr));
+  const double r0 = std::sqrt(rr);
+  st.iterations = 0;
+  if (r0 == 0.0) {
+    st.converged = 1;
+    st.rel_residual = 0.0;
+    return DGMG_OK;
+  }
+  CS(precond(ctx, r, z, o));
+  CK(vec_copy(n, z, p, ctx->stream));
+  double rz;
+  CS(dot(ctx, r, z, rz));
+  dgmg_status result = DGMG_ERR_NOT_CONVERGED;
+  for (int it = 1; it <= o.maxit; ++it) {
+    CS(apply64(ctx, p, q));
+    double pq;
+    CS(dot(ctx, p, q, pq));
+    if (!(pq > 0.0)) {
+      result = DGMG_ERR_BREAKDOWN;
+      ctx->err = "CG breakdown: p^T A p <= 0";
+      break;
+    }
+    const double alpha = rz / pq;
+    CK(vec_axpby(n, alpha, p, 1.0, u, ctx->stream));
+    if (flex) CK(vec_copy(n, r, ro, ctx->stream));
+    CK(vec_axpby(n, -alpha, q, 1.0, r, ctx->stream));
+    CS(dot(ctx, r, r, rr));
+    st.iterations = it;
+    if (std::sqrt(rr) <= o.rtol * r0) {
+      result = DGMG_OK;
+      break;
+    }
+    CS(precond(ctx, r, z, o));
+    double rzn;
+    CS(dot(ctx, r, z, rzn));
+    double num = rzn;
+    if (flex) {
+      double zro;
+      CS(dot(ctx, z, ro, zro));
+      num = rzn - zro;
+    }
+    const double beta = num / rz;
+    rz = rzn;
+    CK(vec_axpby(n, 1.0, z, beta, p, ctx->stream));
+  }
+  // true residual in FP64
+  CS(apply64(ctx, u, q));
+  CK(vec_sub(n, f, q, r, ctx->stream));
+  CS(dot(ctx, r, r, rr));
+  st.rel_residual = std::sqrt(rr) / r0;
+  st.converged = st.rel_residual <= o.rtol * (1.0 + 1e-6) ? 1 : 0;
+  if (result == DGMG_ERR_NOT_CONVERGED) ctx->err = "outer Krylov solve reached maxit";
+  return result == DGMG_OK && !st.converged ? DGMG_ERR_NOT_CONVERGED : result;
+}
+
+dgmg_status solve_fgmres(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, dgmg_solve_stats& st) {
+  const long long n = ctx->ndof;
+  const int m = o.restart;
+  if (m < 1 || m + 1 > kMaxDots) return fail(ctx, DGMG_ERR_ARG, "restart must be in [1, 71]");
+  CS(ensure_krylov(ctx, 2 * (size_t)m + 2));
+  double* r = ctx->kry;
+  std::vector<double*> V(m + 1), Z(m);
+  for (int i = 0; i <= m; ++i) V[i] = r + (size_t)(i + 1) * n;
+  for (int i = 0; i < m; ++i) Z[i] = r + (size_t)(m + 2 + i) * n;
+  CS(apply64(ctx, u, V[0]));
+  CK(vec_sub(n, f, V[0], r, ctx->stream));
+  double rr;
+  CS(dot(ctx, r, r, rr));
+  const double r0 = std::sqrt(rr);
+  st.iterations = 0;
+  if (r0 == 0.0) {
+    st.converged = 1;
+    st.rel_residual = 0.0;
+    return DGMG_OK;
+  }
+  double beta = r0;
+  int it = 0;
+  dgmg_status result = DGMG_ERR_NOT_CONVERGED;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), h2(m + 1), y(m);
+  while (it < o.maxit) {
+    CK(vec_axpby(n, 1.0 / beta, r, 0.0, V[0], ctx->stream));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    bool done = false;
+    for (int j = 0; j < m; ++j) {
+      CS(precond(ctx, V[j], Z[j], o));
+      CS(apply64(ctx, Z[j], V[j + 1]));
+      CS(multi_dot(ctx, j + 1, V.data(), V[j + 1], h.data()));
+      for (int i = 0; i <= j; ++i) CK(vec_axpby(n, -h[i], V[i], 1.0, V[j + 1], ctx->stream));
+      CS(multi_dot(ctx, j + 1, V.data(), V[j + 1], h2.data()));
+      for (int i = 0; i <= j; ++i) CK(vec_axpby(n, -h2[i], V[i], 1.0, V[j + 1], ctx->stream));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
+      double ww;
+      CS(dot(ctx, V[j + 1], V[j + 1], ww));
+      const double hn = std::sqrt(ww);
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) CK(vec_axpby(n, 0.0, V[j + 1], 1.0 / hn, V[j + 1], ctx->stream));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+      if (den == 0.0) {
+        result = DGMG_ERR_BREAKDOWN;
+        ctx->err = "FGMRES breakdown";
+        done = true;
+        break;
+      }
+      cs[j] = H[(size_t)j * m + j] / den;
+      sn[j] = H[(size_t)(j + 1) * m + j] / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) <= o.rtol * r0 || it >= o.maxit) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < k; ++i) CK(vec_axpby(n, y[i], Z[i], 1.0, u, ctx->stream));
+    CS(apply64(ctx, u, V[0]));
+    CK(vec_sub(n, f, V[0], r, ctx->stream));
+    CS(dot(ctx, r, r, rr));
+    beta = std::sqrt(rr);
+    st.iterations = it;
+    if (beta <= o.rtol * r0) {
+      result = DGMG_OK;
+      break;
+    }
+    if (done) break;
+  }
+  st.rel_residual = beta / r0;
+  st.converged = st.rel_residual <= o.rtol * (1.0 + 1e-6) ? 1 : 0;
+  if (result == DGMG_ERR_NOT_CONVERGED) ctx->err = "outer Krylov solve reached maxit";
+  return result;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+void dgmg_default_opts(dgmg_solve_opts* o) {
+  if (!o) return;
+  o->krylov = DGMG_KRYLOV_CG;
+  o->restart = 30;
+  o->rtol = 1e-8;
+  o->maxit = 500;
+  o->smoother_prec = DGMG_FP64;
+  o->omega = 0.8;
+  o->npre = 1;
+  o->npost = 1;
+  o->eps_inner = 1e-2;
+  o->maxit_inner = 0;
+  o->inner = DGMG_INNER_PCG;
+  o->inner_restart = 12;
+  o->coarse = DGMG_COARSE_AMG;
+  o->timing = 0;
+}
+
+dgmg_status dgmg_create(dgmg_ctx** out, int device, void* cuda_stream) {
+  if (!out) return DGMG_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return DGMG_ERR_ARG;
+  }
+  dgmg_ctx* ctx = new dgmg_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) {
+    for (int n = kMinN; n <= kMaxN && e == cudaSuccess; ++n) {
+      const std::vector<double> t = build_tables(n);
+      e = cell_ops(n)->upload_tables(t.data(), ctx->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->dot_partial, sizeof(double) * kDotBlocks * kMaxDots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->dot_out, sizeof(double) * kMaxDots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->dot_ptrs, sizeof(double*) * kMaxDots);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->dot_host, sizeof(double) * kMaxDots);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return DGMG_ERR_CUDA;
+  }
+  *out = ctx;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_destroy(dgmg_ctx* ctx) {
+  if (!ctx) return DGMG_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  free_mesh(ctx);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  cudaFree(ctx->dot_partial);
+  cudaFree(ctx->dot_out);
+  cudaFree(ctx->dot_ptrs);
+  cudaFreeHost(ctx->dot_host);
+  delete ctx;
+  return DGMG_OK;
+}
+
+const char* dgmg_last_error(const dgmg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dgmg_status dgmg_set_mesh(dgmg_ctx* ctx, int nx, int ny, int nz, double lx, double ly, double lz, int p,
+                          const int bc[6]) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(ctx, DGMG_ERR_ARG, "nx, ny, nz must be >= 1");
+  if (!(lx > 0) || !(ly > 0) || !(lz > 0)) return fail(ctx, DGMG_ERR_ARG, "lengths must be > 0");
+  if (p < kMinN - 1 || p > kMaxN - 1) return fail(ctx, DGMG_ERR_ARG, "p must be in [1, 8]");
+  if (!bc) return fail(ctx, DGMG_ERR_ARG, "bc is NULL");
+  for (int i = 0; i < 6; ++i)
+    if (bc[i] != 0 && bc[i] != 1) return fail(ctx, DGMG_ERR_ARG, "bc values must be 0 or 1");
+  const long long ncell = (long long)nx * ny * nz;
+  const long long n3 = (long long)(p + 1) * (p + 1) * (p + 1);
+  if (ncell * n3 > (1LL << 40)) return fail(ctx, DGMG_ERR_ARG, "mesh too large");
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_mesh(ctx);
+  ctx->nx = nx;
+  ctx->ny = ny;
+  ctx->nz = nz;
+  ctx->p = p;
+  ctx->n = p + 1;
+  ctx->L[0] = lx;
+  ctx->L[1] = ly;
+  ctx->L[2] = lz;
+  ctx->h[0] = lx / nx;
+  ctx->h[1] = ly / ny;
+  ctx->h[2] = lz / nz;
+  for (int i = 0; i < 6; ++i) ctx->bc[i] = bc[i];
+  ctx->ncell = ncell;
+  ctx->ndof = ncell * n3;
+  ctx->nvert = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  ctx->ops = cell_ops(p + 1);
+  ctx->has_mesh = true;
+  ctx->has_coef = false;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, const double* b_vertex,
+                                  const double* c_cell) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (!ctx->has_mesh) return fail(ctx, DGMG_ERR_STATE, "set_mesh first");
+  if (!K || (kdim != 1 && kdim != 3)) return fail(ctx, DGMG_ERR_ARG, "K must be non-NULL with kdim 1 or 3");
+  const long long nK = ctx->ncell * kdim;
+  for (long long i = 0; i < nK; ++i)
+    if (!(K[i] > 0.0) || !std::isfinite(K[i])) return fail(ctx, DGMG_ERR_ARG, "K must be finite and > 0");
+  if (c_cell)
+    for (long long i = 0; i < ctx->ncell; ++i)
+      if (!std::isfinite(c_cell[i])) return fail(ctx, DGMG_ERR_ARG, "c must be finite");
+  if (b_vertex)
+    for (long long i = 0; i < 3 * ctx->nvert; ++i)
+      if (!std::isfinite(b_vertex[i])) return fail(ctx, DGMG_ERR_ARG, "b must be finite");
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+  free_mesh(ctx);
+  ctx->kdim = kdim;
+  ctx->hK.assign(K, K + nK);
+  ctx->hb.assign(b_vertex ? b_vertex : K, b_vertex ? b_vertex + 3 * ctx->nvert : K);
+  ctx->hc.assign(c_cell ? c_cell : K, c_cell ? c_cell + ctx->ncell : K);
+  const long long n = ctx->ndof;
+  CS(dalloc(ctx, &ctx->dK, nK));
+  CK(cudaMemcpy(ctx->dK, K, nK * sizeof(double), cudaMemcpyHostToDevice));
+  if (b_vertex) {
+    CS(dalloc(ctx, &ctx->db, 3 * ctx->nvert));
+    CK(cudaMemcpy(ctx->db, b_vertex, 3 * ctx->nvert * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (c_cell) {
+    CS(dalloc(ctx, &ctx->dc, ctx->ncell));
+    CK(cudaMemcpy(ctx->dc, c_cell, ctx->ncell * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  CS(dalloc(ctx, &ctx->diag64, n));
+  CS(dalloc(ctx, &ctx->diag32, n));
+  for (auto& w : ctx->w64) CS(dalloc(ctx, &w, n));
+  for (auto& w : ctx->w32) CS(dalloc(ctx, &w, n));
+  CS(dalloc(ctx, &ctx->corners, 8 * ctx->ncell));
+  CS(dalloc(ctx, &ctx->its, ctx->ncell));
+  CS(dalloc(ctx, &ctx->itsum, 1));
+  CS(dalloc(ctx, &ctx->itmax, 1));
+  CS(dalloc(ctx, &ctx->rhat, ctx->nvert));
+  CS(dalloc(ctx, &ctx->uhat, ctx->nvert));
+  const MeshParams mp = params(ctx);
+  CK(ctx->ops->diag(mp, ctx->diag64, ctx->stream));
+  CK(vec_d2f(n, ctx->diag64, ctx->diag32, ctx->stream));
+  // Q1 matrix and AMG hierarchy (host setup, device cycle)
+  const HostMesh hm = host_mesh(ctx);
+  ctx->q1 = q1_stencil(hm);
+  std::vector<double> st = ctx->q1;
+  int vx = ctx->nx + 1, vy = ctx->ny + 1, vz = ctx->nz + 1;
+  while (true) {
+    AmgLevel L;
+    L.vx = vx;
+    L.vy = vy;
+    L.vz = vz;
+    L.n = (long long)vx * vy * vz;
+    const bool coarsest = L.n <= 512;
+    if (!coarsest) {
+      std::vector<double> dinv(L.n);
+      for (long long i = 0; i < L.n; ++i) dinv[i] = 1.0 / st[27 * i + 13];
+      CS(dalloc(ctx, &L.st, 27 * L.n));
+      CS(dalloc(ctx, &L.dinv, L.n));
+      CK(cudaMemcpy(L.st, st.data(), 27 * L.n * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(L.dinv, dinv.data(), L.n * sizeof(double), cudaMemcpyHostToDevice));
+      CS(dalloc(ctx, &L.xt, L.n));
+      CS(dalloc(ctx, &L.r, L.n));
+    }
+    CS(dalloc(ctx, &L.b, L.n));
+    CS(dalloc(ctx, &L.x, L.n));
+    ctx->lv.push_back(L);
+    if (coarsest) {
+      std::vector<double> A = stencil_dense(st, vx, vy, vz);
+      if (!dense_inverse((int)L.n, A)) return fail(ctx, DGMG_ERR_ARG, "coarse matrix is singular");
+      ctx->coarse_n = (int)L.n;
+      CS(dalloc(ctx, &ctx->coarse_inv, A.size()));
+      CK(cudaMemcpy(ctx->coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+      break;
+    }
+    int cx, cy, cz;
+    st = coarsen_stencil(st, vx, vy, vz, cx, cy, cz);
+    vx = cx;
+    vy = cy;
+    vz = cz;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  ctx->has_coef = true;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_sizes(const dgmg_ctx* ctx, long long* ndof, long long* nvert, long long* ncell, long long* nvol_qp,
+                       long long* nface_qp) {
+  if (!ctx || !ctx->has_mesh) return DGMG_ERR_STATE;
+  const long long m2 = (long long)ctx->n * ctx->n;
+  if (ndof) *ndof = ctx->ndof;
+  if (nvert) *nvert = ctx->nvert;
+  if (ncell) *ncell = ctx->ncell;
+  if (nvol_qp) *nvol_qp = ctx->ncell * m2 * ctx->n;
+  if (nface_qp)
+    *nface_qp = 2 * ((long long)ctx->ny * ctx->nz + (long long)ctx->nx * ctx->nz + (long long)ctx->nx * ctx->ny) * m2;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_quadrature_points(const dgmg_ctx* cctx, double* vol_xyz, double* face_xyz) {
+  if (!cctx || !cctx->has_mesh) return DGMG_ERR_STATE;
+  HostMesh hm;
+  hm.nx = cctx->nx;
+  hm.ny = cctx->ny;
+  hm.nz = cctx->nz;
+  hm.p = cctx->p;
+  for (int d = 0; d < 3; ++d) hm.h[d] = cctx->h[d];
+  quadrature_points_host(hm, vol_xyz, face_xyz);
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_assemble_rhs(dgmg_ctx* ctx, const double* f_qp, const double* g_qp, const double* j_qp,
+                              double* rhs) {
+  CS(ready(ctx));
+  if (!rhs) return fail(ctx, DGMG_ERR_ARG, "rhs is NULL");
+  std::vector<double> h((size_t)ctx->ndof, 0.0);
+  assemble_rhs_host(host_mesh(ctx), f_qp, g_qp, j_qp, h.data());
+  CK(cudaMemcpyAsync(rhs, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!u || !v || u == v) return fail(ctx, DGMG_ERR_ARG, "u, v must be distinct non-NULL device pointers");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CK(ctx->ops->apply(params(ctx), u, v, prec == DGMG_FP32, true, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_block_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!u || !v || u == v) return fail(ctx, DGMG_ERR_ARG, "u, v must be distinct non-NULL device pointers");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CK(ctx->ops->apply(params(ctx), u, v, prec == DGMG_FP32, false, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_block_diagonal(dgmg_ctx* ctx, void* diag, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!diag) return fail(ctx, DGMG_ERR_ARG, "diag is NULL");
+  const size_t bytes = ctx->ndof * (prec == DGMG_FP32 ? 4 : 8);
+  CK(cudaMemcpyAsync(diag, prec == DGMG_FP32 ? (const void*)ctx->diag32 : (const void*)ctx->diag64, bytes,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_block_smooth(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega, double eps, int maxit,
+                              int inner, int inner_restart, dgmg_prec prec, int* inner_its) {
+  CS(ready(ctx));
+  if (!f || !u || f == u) return fail(ctx, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
+  if (nsweep < 0 || !(eps >= 0.0) || !std::isfinite(omega)) return fail(ctx, DGMG_ERR_ARG, "bad sweep arguments");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  const bool fp32 = prec == DGMG_FP32;
+  void* tmp = fp32 ? (void*)ctx->w32[3] : (void*)ctx->w64[2];
+  return smooth_internal(ctx, f, u, tmp, nsweep, omega, eps, maxit, inner, inner_restart, fp32, false, inner_its);
+}
+
+dgmg_status dgmg_restrict(dgmg_ctx* ctx, const void* r, double* r_hat, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!r || !r_hat) return fail(ctx, DGMG_ERR_ARG, "NULL pointer");
+  return restrict_internal(ctx, r, r_hat, prec == DGMG_FP32);
+}
+
+dgmg_status dgmg_prolong_add(dgmg_ctx* ctx, const double* u_hat, void* u, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!u || !u_hat) return fail(ctx, DGMG_ERR_ARG, "NULL pointer");
+  CK(ctx->ops->prolong_add(params(ctx), u_hat, u, prec == DGMG_FP32, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_coarse_matrix(const dgmg_ctx* ctx, double* stencil) {
+  if (!ctx || !ctx->has_coef) return DGMG_ERR_STATE;
+  if (!stencil) return DGMG_ERR_ARG;
+  std::memcpy(stencil, ctx->q1.data(), ctx->q1.size() * sizeof(double));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_coarse_cycle(dgmg_ctx* ctx, const double* r_hat, double* u_hat) {
+  CS(ready(ctx));
+  if (!r_hat || !u_hat || r_hat == u_hat) return fail(ctx, DGMG_ERR_ARG, "r_hat, u_hat must be distinct");
+  return amg_cycle(ctx, 0, r_hat, u_hat);
+}
+
+dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts) {
+  CS(ready(ctx));
+  if (!f || !u || f == u) return fail(ctx, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
+  dgmg_solve_opts o;
+  dgmg_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.npre < 0 || o.npost < 0) return fail(ctx, DGMG_ERR_ARG, "npre, npost must be >= 0");
+  return vcycle_internal(ctx, f, u, o, false);
+}
+
+dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
+                       dgmg_solve_stats* stats) {
+  CS(ready(ctx));
+  if (!f || !u || f == u) return fail(ctx, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
+  dgmg_solve_opts o;
+  dgmg_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0.0) || o.maxit < 1) return fail(ctx, DGMG_ERR_ARG, "rtol > 0 and maxit >= 1 required");
+  if (o.krylov < DGMG_KRYLOV_CG || o.krylov > DGMG_KRYLOV_FGMRES) return fail(ctx, DGMG_ERR_ARG, "bad krylov");
+  dgmg_solve_stats st;
+  std::memset(&st, 0, sizeof(st));
+  const auto t0 = std::chrono::steady_clock::now();
+  ctx->track_its = stats != nullptr;
+  ctx->sweeps_tracked = 0;
+  ctx->timing = o.timing != 0;
+  ctx->ev_used = 0;
+  ctx->ev_smooth.clear();
+  ctx->ev_apply.clear();
+  ctx->n_apply = ctx->n_sweep = ctx->n_zero_sweep = 0;
+  const unsigned long long launches0 = g_launches;
+  if (ctx->track_its) {
+    CK(cudaMemsetAsync(ctx->itsum, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->itmax, 0, sizeof(int), ctx->stream));
+  }
+  dgmg_status s = o.krylov == DGMG_KRYLOV_FGMRES ? solve_fgmres(ctx, f, u, o, st) : solve_cg(ctx, f, u, o, st);
+  ctx->track_its = false;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, cudaGetErrorString(e));
+  st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  st.kernel_launches = (long long)(g_launches - launches0);
+  st.sweeps = ctx->n_sweep;
+  st.zero_sweeps = ctx->n_zero_sweep;
+  st.applies = ctx->n_apply;
+  if (ctx->timing) {
+    float ms;
+    for (auto& pr : ctx->ev_smooth)
+      if (cudaEventElapsedTime(&ms, ctx->ev[pr.first], ctx->ev[pr.second]) == cudaSuccess) st.ms_smooth += ms;
+    for (auto& pr : ctx->ev_apply)
+      if (cudaEventElapsedTime(&ms, ctx->ev[pr.first], ctx->ev[pr.second]) == cudaSuccess) st.ms_apply += ms;
+    ctx->timing = false;
+  }
+  if (stats) {
+    unsigned long long sum = 0;
+    int mx = 0;
+    cudaMemcpy(&sum, ctx->itsum, sizeof(sum), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&mx, ctx->itmax, sizeof(mx), cudaMemcpyDeviceToHost);
+    const long long sw = ctx->sweeps_tracked;
+    st.inner_mean = sw > 0 ? (double)sum / ((double)ctx->ncell * sw) : 0.0;
+    st.inner_its_total = (long long)sum;
+    st.inner_max = mx;
+    *stats = st;
+  }
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,1006 @@
+// Per-order kernels of the matrix-free DG operator, the block-diagonal apply,
+// the fused block-Jacobi smoother and the DG <-> Q1 transfer.
+//
+// Built once per n = p+1 with -DDGMG_N=n.  One warp owns CPW = max(1, 32/n^2)
+// whole cells; there is no block-level synchronisation, so every warp runs
+// independently (cells whose inner solves take different iteration counts do
+// not wait for each other beyond their own warp).  A cell's data live in
+// shared memory as n x n x n arrays (x fastest).  A 1D contraction along axis
+// d is done by "lines": the n^2 lines of a cell parallel to d are spread over
+// the lanes, each lane loads its line into registers, multiplies it by an
+// n x n matrix from constant memory and writes it back.  The same line
+// decomposition gives the face node grid of the two faces normal to d.
+//
+// Operator (arXiv 1805.11930, Sec. 2.1, eq. bilinear_form_split):
+//  volume  (K grad u - b u, grad v)_T + (c u, v)_T, evaluated by sum
+//          factorisation (Sec. 3.1, Stages 1-3): u to the Gauss points by three
+//          contractions with B, derivatives there by the Gauss collocation
+//          derivative Dg, pointwise coefficients, Dg^T and B^T back;
+//  faces   cell-centric: each cell adds the test-function side of the six face
+//          integrals it touches.  With diagonal K constant per cell,
+//          w^- K^- = w^+ K^+ = K^-K^+/(K^-+K^+) =: kap, so the consistency and
+//          symmetry terms and the penalty reduce, per face node, to
+//              qv  = gamma [[u]] - kap (dn u_in + dn u_out),   qdv = -kap [[u]],
+//          integrated exactly with the 1D face mass matrix M1 (x) M1; the upwind
+//          term is integrated at the face Gauss points (b varies on the face).
+//  block   D_T: the same with the neighbour's trace set to zero
+//          (Sec. 3.2, eq. block_diag_apply).
+#include <cuda_runtime.h>
+
+#include "dgmg_internal.h"
+
+#ifndef DGMG_N
+#error "compile with -DDGMG_N=<p+1>"
+#endif
+
+namespace dgmg {
+namespace {
+
+constexpr int N = DGMG_N;
+constexpr int N2 = N * N;
+constexpr int N3 = N * N * N;
+constexpr int CPW = (N2 <= 32) ? (32 / N2) : 1;       // cells per warp
+constexpr int LINES = CPW * N2;                        // lines per axis per warp
+constexpr int LPL = (LINES + 31) / 32;                 // lines per lane
+constexpr int VEC = CPW * N3;                          // values per warp vector
+constexpr int WPB = 4;                                 // warps per block
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+template <typename T>
+struct Tab {
+  T B[N][N];
+  T Dg[N][N];
+  T w[N];
+  T dl[2][N];
+  T M1[N][N];
+  T G[N][N];
+  T hat[2][N];
+  T gq[N];
+};
+
+__constant__ Tab<double> c_tab_d;
+__constant__ Tab<float> c_tab_f;
+
+template <typename T>
+__device__ __forceinline__ const Tab<T>& tab();
+template <>
+__device__ __forceinline__ const Tab<double>& tab<double>() { return c_tab_d; }
+template <>
+__device__ __forceinline__ const Tab<float>& tab<float>() { return c_tab_f; }
+
+// Per-cell coefficients staged in shared memory.
+template <typename T>
+struct CellInfo {
+  T kd[3];      // |J| K_d / h_d^2
+  T cJ;         // c |J|
+  T jh[3];      // |J| / h_d
+  T bc[3][8];   // b_d at the 8 corners, corner = ox + 2 oy + 4 oz
+  T pad;
+};
+
+// Geometry of line L along axis D: owning cell slot cw, first element,
+// stride, and the two tangential coordinates (a < b in axis order).
+template <int D>
+__device__ __forceinline__ void line_geom(int L, int& cw, int& base, int& st, int& a, int& b) {
+  cw = L / N2;
+  const int r = L - cw * N2;
+  a = r % N;
+  b = r / N;
+  if (D == 0) {
+    base = cw * N3 + N * a + N2 * b;
+    st = 1;
+  } else if (D == 1) {
+    base = cw * N3 + a + N2 * b;
+    st = N;
+  } else {
+    base = cw * N3 + a + N * b;
+    st = N2;
+  }
+}
+
+__device__ __forceinline__ void cell_xyz(const MeshParams& mp, long long c, int& cx, int& cy, int& cz) {
+  cx = (int)(c % mp.nx);
+  long long t = c / mp.nx;
+  cy = (int)(t % mp.ny);
+  cz = (int)(t / mp.ny);
+}
+
+__device__ __forceinline__ double kcoef(const MeshParams& mp, long long c, int d) {
+  return __ldg(mp.K + c * mp.kdim + (mp.kdim == 3 ? d : 0));
+}
+
+// 0 = interior (nb set), 1 = Dirichlet, 2 = Neumann.
+__device__ __forceinline__ int face_kind(const MeshParams& mp, long long c, int d, int s, long long& nb) {
+  int cx, cy, cz;
+  cell_xyz(mp, c, cx, cy, cz);
+  const int ci = d == 0 ? cx : (d == 1 ? cy : cz);
+  const int nd = d == 0 ? mp.nx : (d == 1 ? mp.ny : mp.nz);
+  const long long stride = d == 0 ? 1LL : (d == 1 ? (long long)mp.nx : (long long)mp.nx * mp.ny);
+  if ((s == 0 && ci == 0) || (s == 1 && ci == nd - 1)) return mp.bc[2 * d + s] == 0 ? 1 : 2;
+  nb = s ? c + stride : c - stride;
+  return 0;
+}
+
+// out = A in (or A^T in) along axis D for all lines of active cells.
+template <int D, bool TR, bool ACC, typename T>
+__device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out,
+                                         const T (&A)[N][N], int lane, const unsigned char* act) {
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+    T x[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = in[base + j * st];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(TR ? A[j][i] : A[i][j], x[j], s);
+      if (ACC)
+        out[base + i * st] += s;
+      else
+        out[base + i * st] = s;
+    }
+  }
+}
+
+// Stage 2 along axis D, fused with the derivative and its transpose:
+// Y(+)= Dg^T [ w|J| (K_D/h_D^2) Dg U - w |J|/h_D b_D U ]  (+ w c|J| U for D = 0).
+template <int D, bool ACC, bool ADV, bool REACT, typename T>
+__device__ __forceinline__ void grad_pass(const T* __restrict__ U, T* __restrict__ Y, int lane,
+                                          const CellInfo<T>* ci, const unsigned char* act) {
+  const Tab<T>& t = tab<T>();
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+    T u[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) u[j] = U[base + j * st];
+    const T wab = t.w[a] * t.w[b];
+    const T kd = ci[cw].kd[D] * wab;
+    T lo = T(0), hi = T(0);
+    if (ADV) {
+      // b_D along the line is linear in xi_D: bilinear interpolation of the
+      // corner values on the faces xi_D = 0 and xi_D = 1.
+      const T xa = t.gq[a], xb = t.gq[b];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        const int ka = D == 0 ? 1 : 0, kb = D == 2 ? 1 : 2;
+        const T wa = o[ka] ? xa : T(1) - xa;
+        const T wb = o[kb] ? xb : T(1) - xb;
+        const T v = ci[cw].bc[D][c] * wa * wb;
+        if (o[D])
+          hi += v;
+        else
+          lo += v;
+      }
+      lo *= ci[cw].jh[D] * wab;
+      hi *= ci[cw].jh[D] * wab;
+    }
+    T q[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T g = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) g = fma(t.Dg[i][j], u[j], g);
+      T v = kd * t.w[i] * g;
+      if (ADV) {
+        const T bq = lo + (hi - lo) * t.gq[i];
+        v = fma(-t.w[i] * bq, u[i], v);
+      }
+      q[i] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) s = fma(t.Dg[i][r], q[i], s);
+      if (REACT && D == 0) s = fma(ci[cw].cJ * wab * t.w[r], u[r], s);
+      if (ACC)
+        Y[base + r * st] += s;
+      else
+        Y[base + r * st] = s;
+    }
+  }
+}
+
+// Y = A^v X for the warp's cells (Sec. 3.1, Stages 1-3).  S0, S1 scratch.
+template <bool ADV, bool REACT, typename T>
+__device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane, const CellInfo<T>* ci,
+                                       const unsigned char* act) {
+  const Tab<T>& t = tab<T>();
+  contract<0, false, false>(X, S0, t.B, lane, act);
+  __syncwarp();
+  contract<1, false, false>(S0, S1, t.B, lane, act);
+  __syncwarp();
+  contract<2, false, false>(S1, S0, t.B, lane, act);   // S0 = u at the Gauss points
+  __syncwarp();
+  grad_pass<0, false, ADV, REACT>(S0, S1, lane, ci, act);
+  __syncwarp();
+  grad_pass<1, true, ADV, REACT>(S0, S1, lane, ci, act);
+  __syncwarp();
+  grad_pass<2, true, ADV, REACT>(S0, S1, lane, ci, act);
+  __syncwarp();
+  contract<2, true, false>(S1, S0, t.B, lane, act);
+  __syncwarp();
+  contract<1, true, false>(S0, S1, t.B, lane, act);
+  __syncwarp();
+  contract<0, true, false>(S1, Y, t.B, lane, act);
+  __syncwarp();
+}
+
+// Diffusion and penalty terms of face (D, S) of every active cell, added to Y.
+// FULL: neighbour trace read from gu (global); otherwise it is zero (D_T).
+template <int D, int S, bool FULL, typename T>
+__device__ __forceinline__ void face_diffusion(const T* X, T* Y, T* F0, T* F1, const T* __restrict__ gu,
+                                               const MeshParams& mp, long long cell0, int lane,
+                                               const unsigned char* act) {
+  const Tab<T>& t = tab<T>();
+  constexpr int lin = S ? N - 1 : 0;
+  constexpr int lout = S ? 0 : N - 1;
+  const T ih = T(1.0 / mp.h[D]);
+  const T sgn = S ? T(1) : T(-1);
+  const T pen = T(mp.alpha * mp.p * (mp.p + 2));
+  const int ta = D == 0 ? 1 : 0, tb = D == 2 ? 1 : 2;
+  const T area = T(mp.h[ta] * mp.h[tb]);
+  // phase 1: qv, qdv at the face nodes
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    T qv = T(0), qdv = T(0);
+    const long long c = cell0 + cw;
+    long long nb = -1;
+    const int kind = act[cw] ? face_kind(mp, c, D, S, nb) : 2;
+    if (kind != 2) {
+      T x[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) x[j] = X[base + j * st];
+      T dn = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], x[j], dn);
+      dn *= sgn * ih;
+      const T kin = T(kcoef(mp, c, D));
+      if (kind == 0) {
+        const T kout = T(kcoef(mp, nb, D));
+        const T kap = kin * kout / (kin + kout);
+        const T gam = T(2) * pen * kap * ih;
+        T tout = T(0), dno = T(0);
+        if (FULL) {
+          const T* xo = gu + nb * N3 + (base - cw * N3);
+          T y[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) y[j] = xo[j * st];
+          tout = y[lout];
+#pragma unroll
+          for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], y[j], dno);
+          dno *= sgn * ih;
+        }
+        const T jmp = x[lin] - tout;
+        qv = gam * jmp - kap * (dn + dno);
+        qdv = -kap * jmp;
+      } else {
+        const T kap = kin;
+        const T gam = pen * kap * ih;
+        qv = gam * x[lin] - kap * dn;
+        qdv = -kap * x[lin];
+      }
+    }
+    F0[L] = qv;
+    F1[L] = qdv;
+  }
+  __syncwarp();
+  // phase 2: M1 along the first tangential axis
+  T r0[LPL], r1[LPL];
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    r0[k] = T(0);
+    r1[k] = T(0);
+    if (L < LINES) {
+      const int cw = L / N2, r = L - cw * N2, a = r % N, b = r / N;
+      const int row = cw * N2 + N * b;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        r0[k] = fma(t.M1[a][j], F0[row + j], r0[k]);
+        r1[k] = fma(t.M1[a][j], F1[row + j], r1[k]);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    if (L < LINES) {
+      F0[L] = r0[k];
+      F1[L] = r1[k];
+    }
+  }
+  __syncwarp();
+  // phase 3: M1 along the second tangential axis, then scatter into Y
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+    const int col = cw * N2 + a;
+    T mv = T(0), mdv = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      mv = fma(t.M1[b][j], F0[col + N * j], mv);
+      mdv = fma(t.M1[b][j], F1[col + N * j], mdv);
+    }
+    mv *= area;
+    mdv *= area * sgn * ih;
+    Y[base + lin * st] += mv;
+#pragma unroll
+    for (int j = 0; j < N; ++j) Y[base + j * st] = fma(t.dl[S][j], mdv, Y[base + j * st]);
+  }
+  __syncwarp();
+}
+
+// Upwind term of face (D, S): int_F Phi(u_in, u_out, b.n) v_in at the face
+// Gauss points (b.n from the bilinear interpolation of the face corners).
+template <int D, int S, bool FULL, typename T>
+__device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, const T* __restrict__ gu,
+                                            const MeshParams& mp, long long cell0, int lane,
+                                            const unsigned char* act, const CellInfo<T>* ci) {
+  const Tab<T>& t = tab<T>();
+  constexpr int lin = S ? N - 1 : 0;
+  constexpr int lout = S ? 0 : N - 1;
+  const int ta = D == 0 ? 1 : 0, tb = D == 2 ? 1 : 2;
+  const T area = T(mp.h[ta] * mp.h[tb]);
+  const T sgn = S ? T(1) : T(-1);
+  // phase 1: traces at the face nodes
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    T tin = T(0), tout = T(0);
+    long long nb = -1;
+    const long long c = cell0 + cw;
+    const int kind = act[cw] ? face_kind(mp, c, D, S, nb) : 2;
+    if (kind != 2) {
+      tin = X[base + lin * st];
+      if (kind == 0 && FULL) tout = gu[nb * N3 + (base - cw * N3) + lout * st];
+    }
+    F0[L] = tin;
+    F1[L] = tout;
+  }
+  __syncwarp();
+  // phase 2: B along the first tangential axis (nodes -> Gauss points)
+  T r0[LPL], r1[LPL];
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    r0[k] = T(0);
+    r1[k] = T(0);
+    if (L < LINES) {
+      const int cw = L / N2, r = L - cw * N2, a = r % N, b = r / N;
+      const int row = cw * N2 + N * b;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        r0[k] = fma(t.B[a][j], F0[row + j], r0[k]);
+        r1[k] = fma(t.B[a][j], F1[row + j], r1[k]);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    if (L < LINES) {
+      F0[L] = r0[k];
+      F1[L] = r1[k];
+    }
+  }
+  __syncwarp();
+  // phase 3: B along the second axis, flux at the Gauss point (qa, qb)
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    r0[k] = T(0);
+    if (L < LINES) {
+      const int cw = L / N2, r = L - cw * N2, qa = r % N, qb = r / N;
+      if (act[cw]) {
+        const int col = cw * N2 + qa;
+        T ti = T(0), to = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          ti = fma(t.B[qb][j], F0[col + N * j], ti);
+          to = fma(t.B[qb][j], F1[col + N * j], to);
+        }
+        const T xa = t.gq[qa], xb = t.gq[qb];
+        T bn = T(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+          if (o[D] != S) continue;
+          const T wa = o[ta] ? xa : T(1) - xa;
+          const T wb = o[tb] ? xb : T(1) - xb;
+          bn = fma(ci[cw].bc[D][c], wa * wb, bn);
+        }
+        bn *= sgn;
+        r0[k] = t.w[qa] * t.w[qb] * area * bn * (bn >= T(0) ? ti : to);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    if (L < LINES) F0[L] = r0[k];
+  }
+  __syncwarp();
+  // phase 4: B^T along the second axis
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    r0[k] = T(0);
+    if (L < LINES) {
+      const int cw = L / N2, r = L - cw * N2, a = r % N, b = r / N;
+      const int col = cw * N2 + a;
+#pragma unroll
+      for (int j = 0; j < N; ++j) r0[k] = fma(t.B[j][b], F0[col + N * j], r0[k]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < LPL; ++k) {
+    const int L = lane + 32 * k;
+    if (L < LINES) F0[L] = r0[k];
+  }
+  __syncwarp();
+  // phase 5: B^T along the first axis, add to the face layer of Y
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+    const int row = cw * N2 + N * b;
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) s = fma(t.B[j][a], F0[row + j], s);
+    Y[base + lin * st] += s;
+  }
+  __syncwarp();
+}
+
+template <bool FULL, bool ADV, typename T>
+__device__ __forceinline__ void all_faces(const T* X, T* Y, T* F0, T* F1, const T* gu, const MeshParams& mp,
+                                          long long cell0, int lane, const unsigned char* act,
+                                          const CellInfo<T>* ci) {
+  face_diffusion<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  face_diffusion<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  face_diffusion<1, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  face_diffusion<1, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  face_diffusion<2, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  face_diffusion<2, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  if (ADV) {
+    face_upwind<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+    face_upwind<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+    face_upwind<1, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+    face_upwind<1, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+    face_upwind<2, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+    face_upwind<2, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  }
+}
+
+// Stage the per-cell coefficients of the warp's cells; act[cw] = cell exists.
+template <typename T>
+__device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell0, int lane, CellInfo<T>* ci,
+                                            unsigned char* act) {
+  if (lane < CPW) {
+    const long long c = cell0 + lane;
+    const bool ok = c < mp.ncell;
+    act[lane] = ok ? 1 : 0;
+    if (ok) {
+      const double J = mp.h[0] * mp.h[1] * mp.h[2];
+      for (int d = 0; d < 3; ++d) {
+        ci[lane].kd[d] = T(J * kcoef(mp, c, d) / (mp.h[d] * mp.h[d]));
+        ci[lane].jh[d] = T(J / mp.h[d]);
+      }
+      ci[lane].cJ = mp.c ? T(J * __ldg(mp.c + c)) : T(0);
+      if (mp.bvert) {
+        int cx, cy, cz;
+        cell_xyz(mp, c, cx, cy, cz);
+        const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
+        for (int k = 0; k < 8; ++k) {
+          const long long v = (cx + (k & 1)) + vx * (cy + ((k >> 1) & 1)) + vxy * (cz + (k >> 2));
+          for (int d = 0; d < 3; ++d) ci[lane].bc[d][k] = T(__ldg(mp.bvert + 3 * v + d));
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Shared-memory carve-up of one warp.
+template <typename T>
+struct WarpMem {
+  static constexpr int nvec_apply = 4;
+  static constexpr int nvec_smooth = 6;
+  static __host__ __device__ constexpr size_t bytes(int nvec) {
+    return (size_t)(nvec * VEC + 5 * LINES) * sizeof(T) + CPW * sizeof(CellInfo<T>) + 16;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T** F0, T** F1, T** red,
+                                      CellInfo<T>** ci, unsigned char** act) {
+  T* p = reinterpret_cast<T*>(raw);
+  for (int k = 0; k < nvec; ++k) vec[k] = p + k * VEC;
+  *F0 = p + nvec * VEC;
+  *F1 = *F0 + LINES;
+  *red = *F1 + LINES;     // 3 * LINES spare (reductions)
+  *ci = reinterpret_cast<CellInfo<T>*>(*red + 3 * LINES);
+  *act = reinterpret_cast<unsigned char*>(*ci + CPW);
+}
+
+template <typename T, bool FULL, bool ADV, bool REACT>
+__global__ void __launch_bounds__(WPB * 32) k_apply(MeshParams mp, const T* __restrict__ u, T* __restrict__ v) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long cell0 = ((long long)blockIdx.x * WPB + warp) * CPW;
+  if (cell0 >= mp.ncell) return;
+  T* vec[4];
+  T *F0, *F1, *red;
+  CellInfo<T>* ci;
+  unsigned char* act;
+  carve(smem + warp * WarpMem<T>::bytes(4), 4, vec, &F0, &F1, &red, &ci, &act);
+  T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
+  stage_cells(mp, cell0, lane, ci, act);
+  const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
+  const T* ug = u + cell0 * N3;
+  for (int e = lane; e < VEC; e += 32) X[e] = e < nval ? ug[e] : T(0);
+  __syncwarp();
+  volume<ADV, REACT>(X, Y, S0, S1, lane, ci, act);
+  all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
+  T* vg = v + cell0 * N3;
+  for (int e = lane; e < nval; e += 32) vg[e] = Y[e];
+}
+
+// Sum over the lanes that own lines of the same cell; every lane of that cell
+// gets the same value (fixed summation order).
+template <typename T>
+__device__ __forceinline__ T cell_sum(T part, int lane, T* red) {
+  if (CPW == 1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULLMASK, part, o);
+    return part;
+  } else {
+    red[lane] = part;
+    __syncwarp();
+    T s = T(0);
+    if (lane < LINES) {
+      const int c0 = (lane / N2) * N2;
+#pragma unroll
+      for (int k = 0; k < N2; ++k) s += red[c0 + k];
+    }
+    __syncwarp();
+    return s;
+  }
+}
+
+// Block-Jacobi sweep with inner PCG (Algorithm 2; inner solve Sec. 2.2.1).
+// Each lane owns the z-lines L = lane + 32k (elements base + N2 iz) for the
+// pointwise vector operations, so all of its elements belong to one cell.
+template <typename T, bool ADV, bool REACT, bool ZERO>
+__global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T* __restrict__ f,
+                                                         const T* __restrict__ uold, T* __restrict__ unew,
+                                                         const T* __restrict__ diag, T omega, T eps,
+                                                         int maxit, int* __restrict__ its) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long cell0 = ((long long)blockIdx.x * WPB + warp) * CPW;
+  if (cell0 >= mp.ncell) return;
+  T* vec[6];
+  T *F0, *F1, *red;
+  CellInfo<T>* ci;
+  unsigned char* act;
+  carve(smem + warp * WarpMem<T>::bytes(6), 6, vec, &F0, &F1, &red, &ci, &act);
+  T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3], *R = vec[4], *DL = vec[5];
+  stage_cells(mp, cell0, lane, ci, act);
+  const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
+  const long long g0 = cell0 * N3;
+  // my cell slot (lanes without a line: -1)
+  const int mycw = lane < LINES ? lane / N2 : -1;
+  const bool mine = mycw >= 0 && act[mycw];
+  // defect d = f - A u_old
+  if (!ZERO) {
+    for (int e = lane; e < VEC; e += 32) P[e] = e < nval ? uold[g0 + e] : T(0);
+    __syncwarp();
+    volume<ADV, REACT>(P, Q, S0, S1, lane, ci, act);
+    all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+  }
+  T prr = T(0), prz = T(0);
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<2>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int e = base + i * N2;
+      const T r = f[g0 + e] - (ZERO ? T(0) : Q[e]);
+      const T z = r / diag[g0 + e];
+      R[e] = r;
+      P[e] = z;
+      DL[e] = T(0);
+      prr = fma(r, r, prr);
+      prz = fma(r, z, prz);
+    }
+  }
+  const T rr0 = cell_sum(prr, lane, red);
+  T rz = cell_sum(prz, lane, red);
+  const T thr = eps * eps * rr0;
+  bool live = mine && rr0 > T(0);
+  int it = 0;
+  while (__any_sync(FULLMASK, live && it < maxit)) {
+    if (lane < LINES) act[mycw] = (live && it < maxit) ? 1 : 0;
+    __syncwarp();
+    const bool run = live && it < maxit;
+    volume<ADV, REACT>(P, Q, S0, S1, lane, ci, act);
+    all_faces<false, ADV>(P, Q, F0, F1, (const T*)nullptr, mp, cell0, lane, act, ci);
+    T ppq = T(0);
+    if (run) {
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, base, st, a, b;
+        line_geom<2>(L, cw, base, st, a, b);
+#pragma unroll
+        for (int i = 0; i < N; ++i) ppq = fma(P[base + i * N2], Q[base + i * N2], ppq);
+      }
+    }
+    const T pq = cell_sum(ppq, lane, red);
+    bool upd = run && pq > T(0);
+    if (run && !upd) live = false;   // breakdown: stop this cell
+    T prr2 = T(0);
+    if (upd) {
+      const T alpha = rz / pq;
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, base, st, a, b;
+        line_geom<2>(L, cw, base, st, a, b);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int e = base + i * N2;
+          DL[e] = fma(alpha, P[e], DL[e]);
+          const T r = fma(-alpha, Q[e], R[e]);
+          R[e] = r;
+          prr2 = fma(r, r, prr2);
+        }
+      }
+      ++it;
+    }
+    const T rr = cell_sum(prr2, lane, red);
+    if (upd && rr <= thr) {
+      live = false;
+      upd = false;
+    }
+    if (upd && it >= maxit) upd = false;
+    T prz2 = T(0);
+    if (upd) {
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, base, st, a, b;
+        line_geom<2>(L, cw, base, st, a, b);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int e = base + i * N2;
+          const T z = R[e] / diag[g0 + e];
+          S0[e] = z;
+          prz2 = fma(R[e], z, prz2);
+        }
+      }
+    }
+    const T rzn = cell_sum(prz2, lane, red);
+    if (upd) {
+      const T beta = rzn / rz;
+      rz = rzn;
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, base, st, a, b;
+        line_geom<2>(L, cw, base, st, a, b);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int e = base + i * N2;
+          P[e] = fma(beta, P[e], S0[e]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // u_new = u_old + omega delta
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<2>(L, cw, base, st, a, b);
+    if (cell0 + cw >= mp.ncell) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const long long g = g0 + base + i * N2;
+      unew[g] = ZERO ? omega * DL[base + i * N2] : fma(omega, DL[base + i * N2], uold[g]);
+    }
+  }
+  if (its && lane < LINES && (lane % N2) == 0 && cell0 + mycw < mp.ncell) its[cell0 + mycw] = it;
+}
+
+// diag(D_T) by direct quadrature per dof (setup; FP64).
+template <bool ADV>
+__global__ void k_diag(MeshParams mp, double* __restrict__ diag) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= mp.ncell * N3) return;
+  const long long c = gid / N3;
+  const int i = (int)(gid - c * N3);
+  const int ii[3] = {i % N, (i / N) % N, i / N2};
+  const Tab<double>& t = c_tab_d;
+  const double J = mp.h[0] * mp.h[1] * mp.h[2];
+  const double K[3] = {kcoef(mp, c, 0), kcoef(mp, c, 1), kcoef(mp, c, 2)};
+  const double cc = mp.c ? mp.c[c] : 0.0;
+  double bc[3][8];
+  if (ADV) {
+    int cx, cy, cz;
+    cell_xyz(mp, c, cx, cy, cz);
+    const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
+    for (int k = 0; k < 8; ++k) {
+      const long long v = (cx + (k & 1)) + vx * (cy + ((k >> 1) & 1)) + vxy * (cz + (k >> 2));
+      for (int d = 0; d < 3; ++d) bc[d][k] = mp.bvert[3 * v + d];
+    }
+  }
+  double acc = 0.0;
+  for (int q3 = 0; q3 < N; ++q3)
+    for (int q2 = 0; q2 < N; ++q2)
+      for (int q1 = 0; q1 < N; ++q1) {
+        const int q[3] = {q1, q2, q3};
+        const double w = t.w[q1] * t.w[q2] * t.w[q3] * J;
+        double val = 1.0, g[3];
+        for (int d = 0; d < 3; ++d) val *= t.B[q[d]][ii[d]];
+        for (int d = 0; d < 3; ++d) {
+          g[d] = t.G[q[d]][ii[d]] / mp.h[d];
+          for (int e = 0; e < 3; ++e)
+            if (e != d) g[d] *= t.B[q[e]][ii[e]];
+        }
+        acc += w * (K[0] * g[0] * g[0] + K[1] * g[1] * g[1] + K[2] * g[2] * g[2] + cc * val * val);
+        if (ADV) {
+          double b[3] = {0, 0, 0};
+          for (int k = 0; k < 8; ++k) {
+            double wk = 1.0;
+            for (int d = 0; d < 3; ++d) wk *= ((k >> d) & 1) ? t.gq[q[d]] : 1.0 - t.gq[q[d]];
+            for (int d = 0; d < 3; ++d) b[d] += wk * bc[d][k];
+          }
+          acc -= w * val * (b[0] * g[0] + b[1] * g[1] + b[2] * g[2]);
+        }
+      }
+  const double pen = mp.alpha * mp.p * (mp.p + 2);
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s) {
+      if (ii[d] != (s ? N - 1 : 0)) continue;
+      long long nb;
+      const int kind = face_kind(mp, c, d, s, nb);
+      if (kind == 2) continue;
+      const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+      const double area = mp.h[ta] * mp.h[tb];
+      const double mass = area * t.M1[ii[ta]][ii[ta]] * t.M1[ii[tb]][ii[tb]];
+      const double sgn = s ? 1.0 : -1.0;
+      const double dterm = sgn / mp.h[d] * t.dl[s][ii[d]] * mass;
+      double kap, gam;
+      if (kind == 0) {
+        const double ko = kcoef(mp, nb, d);
+        kap = K[d] * ko / (K[d] + ko);
+        gam = 2.0 * pen * kap / mp.h[d];
+      } else {
+        kap = K[d];
+        gam = pen * kap / mp.h[d];
+      }
+      acc += gam * mass - 2.0 * kap * dterm;
+      if (ADV) {
+        for (int qb = 0; qb < N; ++qb)
+          for (int qa = 0; qa < N; ++qa) {
+            double bn = 0.0;
+            for (int k = 0; k < 8; ++k) {
+              const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+              if (o[d] != s) continue;
+              const double wa = o[ta] ? t.gq[qa] : 1.0 - t.gq[qa];
+              const double wb = o[tb] ? t.gq[qb] : 1.0 - t.gq[qb];
+              bn += bc[d][k] * wa * wb;
+            }
+            bn *= sgn;
+            if (bn > 0.0) {
+              const double ph = t.B[qa][ii[ta]] * t.B[qb][ii[tb]];
+              acc += t.w[qa] * t.w[qb] * area * bn * ph * ph;
+            }
+          }
+      }
+    }
+  diag[gid] = acc;
+}
+
+// Corner sums r_hat_c(T) = sum_i prod_k phi_{c_k}(zeta_{i_k}) r_T(i), one
+// thread per (cell, corner) (the cell part of R = P^T).
+template <typename T>
+__global__ void k_restrict_cells(long long ncell, const T* __restrict__ r, double* __restrict__ corners) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ncell * 8) return;
+  const long long c = gid >> 3;
+  const int k = (int)(gid & 7);
+  const Tab<double>& t = c_tab_d;
+  const double* hx = t.hat[k & 1];
+  const double* hy = t.hat[(k >> 1) & 1];
+  const double* hz = t.hat[k >> 2];
+  const T* rc = r + c * N3;
+  double s = 0.0;
+  for (int i3 = 0; i3 < N; ++i3) {
+    double sy = 0.0;
+    for (int i2 = 0; i2 < N; ++i2) {
+      double sx = 0.0;
+      for (int i1 = 0; i1 < N; ++i1) sx += hx[i1] * (double)rc[i1 + N * i2 + N2 * i3];
+      sy += hy[i2] * sx;
+    }
+    s += hz[i3] * sy;
+  }
+  corners[gid] = s;
+}
+
+// u_T(i) += sum_c u_hat(vertex(T, c)) prod_k phi_{c_k}(zeta_{i_k}).
+template <typename T>
+__global__ void k_prolong_add(MeshParams mp, const double* __restrict__ uhat, T* __restrict__ u) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= mp.ncell * N3) return;
+  const long long c = gid / N3;
+  const int i = (int)(gid - c * N3);
+  const int i1 = i % N, i2 = (i / N) % N, i3 = i / N2;
+  int cx, cy, cz;
+  cell_xyz(mp, c, cx, cy, cz);
+  const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
+  const Tab<double>& t = c_tab_d;
+  double s = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    const int ox = k & 1, oy = (k >> 1) & 1, oz = k >> 2;
+    const long long v = (cx + ox) + vx * (cy + oy) + vxy * (cz + oz);
+    s += uhat[v] * t.hat[ox][i1] * t.hat[oy][i2] * t.hat[oz][i3];
+  }
+  u[gid] = (T)((double)u[gid] + s);
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t upload_one(const double* h, cudaStream_t s) {
+  Tab<T> tb;
+  const double* p = h;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) tb.B[i][j] = T(p[i * N + j]);
+  p += N2;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) tb.Dg[i][j] = T(p[i * N + j]);
+  p += N2;
+  for (int i = 0; i < N; ++i) tb.w[i] = T(p[i]);
+  p += N;
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int i = 0; i < N; ++i) tb.dl[s2][i] = T(p[s2 * N + i]);
+  p += 2 * N;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) tb.M1[i][j] = T(p[i * N + j]);
+  p += N2;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) tb.G[i][j] = T(p[i * N + j]);
+  p += N2;
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int i = 0; i < N; ++i) tb.hat[s2][i] = T(p[s2 * N + i]);
+  p += 2 * N;
+  for (int i = 0; i < N; ++i) tb.gq[i] = T(p[i]);
+  if (sizeof(T) == 8) return cudaMemcpyToSymbol(c_tab_d, &tb, sizeof(tb));
+  return cudaMemcpyToSymbol(c_tab_f, &tb, sizeof(tb));
+}
+
+cudaError_t upload_tables(const double* h, cudaStream_t s) {
+  cudaError_t e = upload_one<double>(h, s);
+  if (e != cudaSuccess) return e;
+  return upload_one<float>(h, s);
+}
+
+inline unsigned grid_for(long long ncell) {
+  const long long groups = (ncell + CPW - 1) / CPW;
+  return (unsigned)((groups + WPB - 1) / WPB);
+}
+
+template <typename KernelT>
+cudaError_t set_smem(KernelT k, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+template <typename T, bool FULL, bool ADV, bool REACT>
+cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
+  const size_t sm = WPB * WarpMem<T>::bytes(4);
+  auto k = k_apply<T, FULL, ADV, REACT>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid_for(mp.ncell), WPB * 32, sm, s>>>(mp, (const T*)u, (T*)v);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, bool FULL>
+cudaError_t apply_t(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
+  const bool adv = mp.bvert != nullptr, react = mp.c != nullptr;
+  if (adv)
+    return react ? launch_apply<T, FULL, true, true>(mp, u, v, s) : launch_apply<T, FULL, true, false>(mp, u, v, s);
+  return react ? launch_apply<T, FULL, false, true>(mp, u, v, s) : launch_apply<T, FULL, false, false>(mp, u, v, s);
+}
+
+cudaError_t apply(const MeshParams& mp, const void* u, void* v, bool fp32, bool full, cudaStream_t s) {
+  if (mp.ncell == 0) return cudaSuccess;
+  if (fp32) return full ? apply_t<float, true>(mp, u, v, s) : apply_t<float, false>(mp, u, v, s);
+  return full ? apply_t<double, true>(mp, u, v, s) : apply_t<double, false>(mp, u, v, s);
+}
+
+template <typename T, bool ADV, bool REACT, bool ZERO>
+cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  const size_t sm = WPB * WarpMem<T>::bytes(6);
+  auto k = k_smooth_pcg<T, ADV, REACT, ZERO>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid_for(mp.ncell), WPB * 32, sm, s>>>(mp, (const T*)a.f, (const T*)a.uold, (T*)a.unew, (const T*)a.diag,
+                                              T(a.omega), T(a.eps), a.maxit, a.its);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, bool ADV, bool REACT>
+cudaError_t smooth_z(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  return a.uold ? launch_smooth<T, ADV, REACT, false>(mp, a, s) : launch_smooth<T, ADV, REACT, true>(mp, a, s);
+}
+
+template <typename T>
+cudaError_t smooth_t(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  const bool adv = mp.bvert != nullptr, react = mp.c != nullptr;
+  if (adv) return react ? smooth_z<T, true, true>(mp, a, s) : smooth_z<T, true, false>(mp, a, s);
+  return react ? smooth_z<T, false, true>(mp, a, s) : smooth_z<T, false, false>(mp, a, s);
+}
+
+cudaError_t smooth(const MeshParams& mp, const SmoothArgs& a, bool fp32, cudaStream_t s) {
+  if (mp.ncell == 0) return cudaSuccess;
+  return fp32 ? smooth_t<float>(mp, a, s) : smooth_t<double>(mp, a, s);
+}
+
+cudaError_t diag(const MeshParams& mp, double* d, cudaStream_t s) {
+  const long long n = mp.ncell * N3;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  if (mp.bvert)
+    k_diag<true><<<grid, 128, 0, s>>>(mp, d);
+  else
+    k_diag<false><<<grid, 128, 0, s>>>(mp, d);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t restrict_cells(const MeshParams& mp, const void* r, double* corners, bool fp32, cudaStream_t s) {
+  const long long n = mp.ncell * 8;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (fp32)
+    k_restrict_cells<float><<<grid, 256, 0, s>>>(mp.ncell, (const float*)r, corners);
+  else
+    k_restrict_cells<double><<<grid, 256, 0, s>>>(mp.ncell, (const double*)r, corners);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool fp32, cudaStream_t s) {
+  const long long n = mp.ncell * N3;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (fp32)
+    k_prolong_add<float><<<grid, 256, 0, s>>>(mp, uhat, (float*)u);
+  else
+    k_prolong_add<double><<<grid, 256, 0, s>>>(mp, uhat, (double*)u);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DGMG_CAT2(a, b) a##b
+#define DGMG_CAT(a, b) DGMG_CAT2(a, b)
+
+const CellOps* DGMG_CAT(cell_ops_n, DGMG_N)() {
+  static const CellOps ops = {N, &upload_tables, &apply, &smooth, &diag, &restrict_cells, &prolong_add};
+  return &ops;
+}
+
+}  // namespace dgmg

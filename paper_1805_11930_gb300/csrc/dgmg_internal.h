@@ -1,0 +1,103 @@
+// Internal declarations shared by the host library and the per-order kernel
+// translation units.  Not part of the public ABI (include/dgmg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dgmg.h"
+
+namespace dgmg {
+
+// Number of kernels launched by this library (for launch accounting).
+extern unsigned long long g_launches;
+inline void count_launch(unsigned long long k = 1) { g_launches += k; }
+
+constexpr int kMinN = 2;   // p = 1
+constexpr int kMaxN = 9;   // p = 8
+
+// Mesh and coefficients as seen by the kernels (passed by value).
+struct MeshParams {
+  int nx, ny, nz, p;
+  long long ncell;
+  double h[3];
+  int bc[6];              // 0 Dirichlet, 1 Neumann; planes -x,+x,-y,+y,-z,+z
+  const double* K;        // device, ncell * kdim
+  int kdim;               // 1 or 3
+  const double* c;        // device, ncell, or nullptr
+  const double* bvert;    // device, 3 * nvert, or nullptr
+  double alpha;           // penalty parameter (1.25)
+};
+
+// Flat layout of the 1D tables uploaded to constant memory for one n (all in
+// double on the host; the kernels keep a float copy too):
+//   B[n][n]    GLL Lagrange basis at the Gauss points, B[q][j] = l_j(g_q)
+//   Dg[n][n]   collocation derivative on the Gauss points
+//   w[n]       Gauss weights on [0,1]
+//   dl[2][n]   l_j'(0), l_j'(1)
+//   M1[n][n]   1D mass matrix of the GLL basis, sum_q w_q B[q][i] B[q][j]
+//   G[n][n]    G[q][j] = l_j'(g_q)
+//   hat[2][n]  Q1 hat functions at the GLL nodes: 1 - zeta_i, zeta_i
+//   gq[n]      Gauss points on [0,1]
+inline int table_size(int n) { return 4 * n * n + 6 * n; }
+
+struct SmoothArgs {
+  const void* f;
+  const void* uold;       // nullptr: zero initial guess
+  void* unew;
+  const void* diag;       // diag(D_T) in the same precision
+  double omega, eps;
+  int maxit;
+  int inner;              // DGMG_INNER_PCG / DGMG_INNER_GMRES
+  int restart;
+  int* its;               // device int[ncell] or nullptr
+};
+
+// Per-order kernel entry points, one table per n (cell_kernels.cu built with
+// -DDGMG_N=n).
+struct CellOps {
+  int n;
+  cudaError_t (*upload_tables)(const double* host_tables, cudaStream_t s);
+  // full = A (with neighbour terms); !full = block diagonal D.
+  cudaError_t (*apply)(const MeshParams& mp, const void* u, void* v, bool fp32, bool full,
+                       cudaStream_t s);
+  cudaError_t (*smooth)(const MeshParams& mp, const SmoothArgs& a, bool fp32, cudaStream_t s);
+  cudaError_t (*diag)(const MeshParams& mp, double* diag, cudaStream_t s);
+  cudaError_t (*restrict_cells)(const MeshParams& mp, const void* r, double* corners, bool fp32,
+                                cudaStream_t s);
+  cudaError_t (*prolong_add)(const MeshParams& mp, const double* uhat, void* u, bool fp32,
+                             cudaStream_t s);
+};
+
+const CellOps* cell_ops(int n);
+
+// Vector, stencil and conversion kernels (vec_kernels.cu).
+cudaError_t vec_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);  // y = a x + b y
+cudaError_t vec_axpby_f(long long n, float a, const float* x, float b, float* y, cudaStream_t s);
+cudaError_t vec_sub(long long n, const double* a, const double* b, double* out, cudaStream_t s);   // out = a - b
+cudaError_t vec_sub_f(long long n, const float* a, const float* b, float* out, cudaStream_t s);
+cudaError_t vec_copy(long long n, const double* x, double* y, cudaStream_t s);
+cudaError_t vec_fill(long long n, double v, double* y, cudaStream_t s);
+cudaError_t vec_fill_f(long long n, float v, float* y, cudaStream_t s);
+cudaError_t vec_d2f(long long n, const double* x, float* y, cudaStream_t s);
+cudaError_t vec_f2d(long long n, const float* x, double* y, cudaStream_t s);
+// Deterministic dot products: partial sums per block in a fixed order, then
+// one block sums the partials; result written to out (device).
+cudaError_t vec_dot(long long n, const double* x, const double* y, double* partial, double* out,
+                    cudaStream_t s);
+cudaError_t vec_multi_dot(long long n, int k, const double* const* xs, const double* y,
+                          double* partial, double* out, cudaStream_t s);
+constexpr int kDotBlocks = 1024;
+
+// 27-point stencil operators of the AMG levels (row-major, 27 per row).
+cudaError_t stencil_jacobi(int vx, int vy, int vz, const double* st, const double* dinv,
+                           const double* b, const double* x, double* xout, double omega,
+                           bool zero_x, cudaStream_t s);
+cudaError_t stencil_residual(int vx, int vy, int vz, const double* st, const double* b,
+                             const double* x, double* r, cudaStream_t s);
+cudaError_t agg_restrict(int vx, int vy, int vz, const double* r, double* rc, cudaStream_t s);
+cudaError_t agg_prolong_add(int vx, int vy, int vz, const double* xc, double* x, cudaStream_t s);
+cudaError_t dense_matvec(int n, const double* A, const double* x, double* y, cudaStream_t s);
+cudaError_t restrict_gather(int nx, int ny, int nz, const double* corners, double* rhat,
+                            cudaStream_t s);
+
+}  // namespace dgmg

@@ -1,0 +1,477 @@
+// Host-side setup: quadrature tables, Q1 re-discretisation (App. A.2), AMG
+// coarsening and the right-hand side l_h (Sec. 2.1, eq. rhs).
+#include "setup_host.h"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace dgmg {
+
+namespace {
+
+// P_k(x) and P_{k-1}(x) by the three-term recurrence.
+void legendre(int k, double x, double& pk, double& pkm1) {
+  double p0 = 1.0, p1 = x;
+  if (k == 0) {
+    pk = 1.0;
+    pkm1 = 0.0;
+    return;
+  }
+  for (int j = 1; j < k; ++j) {
+    const double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  pk = p1;
+  pkm1 = p0;
+}
+
+const double kPi = 3.14159265358979323846;
+
+}  // namespace
+
+void gauss_legendre01(int m, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(m, 0.0);
+  w.assign(m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    double t = std::cos(kPi * (i + 0.75) / (m + 0.5));
+    double pm = 0, pm1 = 0, dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      legendre(m, t, pm, pm1);
+      dp = m * (t * pm - pm1) / (t * t - 1.0);
+      const double dt = pm / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    legendre(m, t, pm, pm1);
+    dp = m * (t * pm - pm1) / (t * t - 1.0);
+    // descending t -> ascending x
+    x[m - 1 - i] = 0.5 * (t + 1.0);
+    w[m - 1 - i] = 0.5 * 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+void gauss_lobatto01(int n, std::vector<double>& x, std::vector<double>& w) {
+  const int N = n - 1;
+  std::vector<double> t(n);
+  t[0] = -1.0;
+  t[N] = 1.0;
+  for (int i = 1; i < N; ++i) {
+    double s = -std::cos(kPi * i / N);
+    for (int it = 0; it < 100; ++it) {
+      double pn, pn1;
+      legendre(N, s, pn, pn1);
+      const double d1 = N * (pn1 - s * pn) / (1.0 - s * s);                  // P_N'
+      const double d2 = (2.0 * s * d1 - N * (N + 1.0) * pn) / (1.0 - s * s);  // P_N''
+      const double ds = d1 / d2;
+      s -= ds;
+      if (std::fabs(ds) < 1e-16) break;
+    }
+    t[i] = s;
+  }
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double pn, pn1;
+    legendre(N, t[i], pn, pn1);
+    x[i] = 0.5 * (t[i] + 1.0);
+    w[i] = 0.5 * 2.0 / (N * (N + 1.0) * pn * pn);
+  }
+}
+
+void lagrange(const std::vector<double>& z, double x, double* val, double* der) {
+  const int n = (int)z.size();
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) v *= (x - z[k]) / (z[j] - z[k]);
+    if (val) val[j] = v;
+    if (der) {
+      double d = 0.0;
+      for (int l = 0; l < n; ++l) {
+        if (l == j) continue;
+        double term = 1.0 / (z[j] - z[l]);
+        for (int k = 0; k < n; ++k)
+          if (k != j && k != l) term *= (x - z[k]) / (z[j] - z[k]);
+        d += term;
+      }
+      der[j] = d;
+    }
+  }
+}
+
+std::vector<double> build_tables(int n) {
+  std::vector<double> gll, gllw, gq, gw;
+  gauss_lobatto01(n, gll, gllw);
+  gauss_legendre01(n, gq, gw);
+  std::vector<double> T(4 * n * n + 6 * n, 0.0);
+  double* B = T.data();
+  double* Dg = B + n * n;
+  double* W = Dg + n * n;
+  double* dl = W + n;
+  double* M1 = dl + 2 * n;
+  double* G = M1 + n * n;
+  double* hat = G + n * n;
+  double* GQ = hat + 2 * n;
+  for (int q = 0; q < n; ++q) {
+    lagrange(gll, gq[q], B + q * n, G + q * n);
+    lagrange(gq, gq[q], nullptr, Dg + q * n);
+    W[q] = gw[q];
+    GQ[q] = gq[q];
+  }
+  lagrange(gll, 0.0, nullptr, dl);
+  lagrange(gll, 1.0, nullptr, dl + n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += gw[q] * B[q * n + i] * B[q * n + j];
+      M1[i * n + j] = s;
+    }
+  for (int i = 0; i < n; ++i) {
+    hat[i] = 1.0 - gll[i];
+    hat[n + i] = gll[i];
+  }
+  return T;
+}
+
+namespace {
+
+inline double kval(const HostMesh& m, long long c, int d) { return m.K[c * m.kdim + (m.kdim == 3 ? d : 0)]; }
+
+inline double q1phi(int k, const double xi[3]) {
+  double v = 1.0;
+  for (int d = 0; d < 3; ++d) v *= ((k >> d) & 1) ? xi[d] : 1.0 - xi[d];
+  return v;
+}
+
+inline double q1grad(int k, const double xi[3], int d, const double h[3]) {
+  double v = (((k >> d) & 1) ? 1.0 : -1.0) / h[d];
+  for (int e = 0; e < 3; ++e)
+    if (e != d) v *= ((k >> e) & 1) ? xi[e] : 1.0 - xi[e];
+  return v;
+}
+
+inline long long vid(const HostMesh& m, int vx, int vy, int vz) {
+  return vx + (long long)(m.nx + 1) * (vy + (long long)(m.ny + 1) * vz);
+}
+
+void b_at(const HostMesh& m, int cx, int cy, int cz, const double xi[3], double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (!m.b) return;
+  for (int k = 0; k < 8; ++k) {
+    const long long v = vid(m, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
+    const double wk = q1phi(k, xi);
+    for (int d = 0; d < 3; ++d) out[d] += wk * m.b[3 * v + d];
+  }
+}
+
+}  // namespace
+
+std::vector<double> q1_stencil(const HostMesh& m) {
+  const long long nvert = (long long)(m.nx + 1) * (m.ny + 1) * (m.nz + 1);
+  std::vector<double> st(27 * nvert, 0.0);
+  // The DG rule (p+1 Gauss points per direction): with it A_hat equals P^T A P
+  // exactly, also where the upwind term max(b.n, 0) has a kink inside a face.
+  const int nq = m.p + 1;
+  std::vector<double> g2, w2;
+  gauss_legendre01(nq, g2, w2);
+  const double J = m.h[0] * m.h[1] * m.h[2];
+  const double pen = m.alpha * m.p * (m.p + 2);
+  auto scatter = [&](int cx, int cy, int cz, const double Ae[8][8]) {
+    for (int a = 0; a < 8; ++a) {
+      const long long va = vid(m, cx + (a & 1), cy + ((a >> 1) & 1), cz + (a >> 2));
+      for (int b = 0; b < 8; ++b) {
+        const int dx = (b & 1) - (a & 1), dy = ((b >> 1) & 1) - ((a >> 1) & 1), dz = (b >> 2) - (a >> 2);
+        st[27 * va + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += Ae[a][b];
+      }
+    }
+  };
+  for (int cz = 0; cz < m.nz; ++cz)
+    for (int cy = 0; cy < m.ny; ++cy)
+      for (int cx = 0; cx < m.nx; ++cx) {
+        const long long c = cx + (long long)m.nx * (cy + (long long)m.ny * cz);
+        const double K[3] = {kval(m, c, 0), kval(m, c, 1), kval(m, c, 2)};
+        const double cc = m.c ? m.c[c] : 0.0;
+        double Ae[8][8];
+        std::memset(Ae, 0, sizeof(Ae));
+        for (int q3 = 0; q3 < nq; ++q3)
+          for (int q2 = 0; q2 < nq; ++q2)
+            for (int q1 = 0; q1 < nq; ++q1) {
+              const double xi[3] = {g2[q1], g2[q2], g2[q3]};
+              const double w = w2[q1] * w2[q2] * w2[q3] * J;
+              double bq[3];
+              b_at(m, cx, cy, cz, xi, bq);
+              double phi[8], gr[8][3];
+              for (int k = 0; k < 8; ++k) {
+                phi[k] = q1phi(k, xi);
+                for (int d = 0; d < 3; ++d) gr[k][d] = q1grad(k, xi, d, m.h);
+              }
+              for (int a = 0; a < 8; ++a)
+                for (int b = 0; b < 8; ++b) {
+                  double v = cc * phi[b] * phi[a];
+                  for (int d = 0; d < 3; ++d) v += K[d] * gr[b][d] * gr[a][d] - bq[d] * phi[b] * gr[a][d];
+                  Ae[a][b] += w * v;
+                }
+            }
+        // Dirichlet faces of boundary cells (gamma from the DG degree p).
+        const int cc3[3] = {cx, cy, cz};
+        const int nn3[3] = {m.nx, m.ny, m.nz};
+        for (int d = 0; d < 3; ++d)
+          for (int s = 0; s < 2; ++s) {
+            if (cc3[d] != (s ? nn3[d] - 1 : 0) || m.bc[2 * d + s] != 0) continue;
+            const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+            const double area = m.h[ta] * m.h[tb];
+            const double sgn = s ? 1.0 : -1.0;
+            const double gam = pen * K[d] / m.h[d];
+            for (int qb = 0; qb < nq; ++qb)
+              for (int qa = 0; qa < nq; ++qa) {
+                double xi[3];
+                xi[d] = s;
+                xi[ta] = g2[qa];
+                xi[tb] = g2[qb];
+                const double w = w2[qa] * w2[qb] * area;
+                double bq[3];
+                b_at(m, cx, cy, cz, xi, bq);
+                const double bn = sgn * bq[d];
+                double phi[8], dn[8];
+                for (int k = 0; k < 8; ++k) {
+                  phi[k] = q1phi(k, xi);
+                  dn[k] = sgn * q1grad(k, xi, d, m.h);
+                }
+                for (int a = 0; a < 8; ++a)
+                  for (int b = 0; b < 8; ++b) {
+                    const double up = bn >= 0.0 ? bn * phi[b] : 0.0;
+                    Ae[a][b] += w * (up * phi[a] - K[d] * dn[b] * phi[a] - K[d] * dn[a] * phi[b] + gam * phi[b] * phi[a]);
+                  }
+              }
+          }
+        scatter(cx, cy, cz, Ae);
+      }
+  return st;
+}
+
+std::vector<double> coarsen_stencil(const std::vector<double>& st, int vx, int vy, int vz, int& cx, int& cy,
+                                    int& cz) {
+  cx = (vx + 1) / 2;
+  cy = (vy + 1) / 2;
+  cz = (vz + 1) / 2;
+  std::vector<double> sc(27 * (size_t)cx * cy * cz, 0.0);
+  for (int iz = 0; iz < vz; ++iz)
+    for (int iy = 0; iy < vy; ++iy)
+      for (int ix = 0; ix < vx; ++ix) {
+        const long long i = ix + (long long)vx * (iy + (long long)vy * iz);
+        const long long I = ix / 2 + (long long)cx * (iy / 2 + (long long)cy * (iz / 2));
+        for (int k = 0; k < 27; ++k) {
+          const double a = st[27 * i + k];
+          if (a == 0.0) continue;
+          const int jx = ix + k % 3 - 1, jy = iy + (k / 3) % 3 - 1, jz = iz + k / 9 - 1;
+          if (jx < 0 || jy < 0 || jz < 0 || jx >= vx || jy >= vy || jz >= vz) continue;
+          const int ox = jx / 2 - ix / 2, oy = jy / 2 - iy / 2, oz = jz / 2 - iz / 2;
+          sc[27 * I + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] += a;
+        }
+      }
+  return sc;
+}
+
+std::vector<double> stencil_dense(const std::vector<double>& st, int vx, int vy, int vz) {
+  const long long n = (long long)vx * vy * vz;
+  std::vector<double> A(n * n, 0.0);
+  for (int iz = 0; iz < vz; ++iz)
+    for (int iy = 0; iy < vy; ++iy)
+      for (int ix = 0; ix < vx; ++ix) {
+        const long long i = ix + (long long)vx * (iy + (long long)vy * iz);
+        for (int k = 0; k < 27; ++k) {
+          const int jx = ix + k % 3 - 1, jy = iy + (k / 3) % 3 - 1, jz = iz + k / 9 - 1;
+          if (jx < 0 || jy < 0 || jz < 0 || jx >= vx || jy >= vy || jz >= vz) continue;
+          A[i * n + jx + (long long)vx * (jy + (long long)vy * jz)] += st[27 * i + k];
+        }
+      }
+  return A;
+}
+
+bool dense_inverse(int n, std::vector<double>& A) {
+  // Gauss-Jordan elimination with partial pivoting on [A | I].
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = std::fabs(A[(size_t)col * n + col]);
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + col]) > best) {
+        best = std::fabs(A[(size_t)r * n + col]);
+        piv = r;
+      }
+    if (best == 0.0) return false;
+    if (piv != col)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[(size_t)piv * n + j], A[(size_t)col * n + j]);
+        std::swap(I[(size_t)piv * n + j], I[(size_t)col * n + j]);
+      }
+    const double d = 1.0 / A[(size_t)col * n + col];
+    for (int j = 0; j < n; ++j) {
+      A[(size_t)col * n + j] *= d;
+      I[(size_t)col * n + j] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[(size_t)r * n + j] -= f * A[(size_t)col * n + j];
+        I[(size_t)r * n + j] -= f * I[(size_t)col * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp, const double* j_qp, double* rhs) {
+  const int n = m.p + 1, n2 = n * n, n3 = n2 * n;
+  const std::vector<double> T = build_tables(n);
+  const double* B = T.data();
+  const double* W = B + 2 * n * n;
+  const double* dl = W + n;
+  const double J = m.h[0] * m.h[1] * m.h[2];
+  const long long ncell = (long long)m.nx * m.ny * m.nz;
+  std::vector<double> t0(n3), t1(n3);
+  for (long long c = 0; c < ncell; ++c) {
+    double* out = rhs + c * n3;
+    for (int q = 0; q < n3; ++q) t0[q] = (f_qp ? f_qp[c * n3 + q] : 0.0) * W[q % n] * W[(q / n) % n] * W[q / n2] * J;
+    // B^T along x, y, z (quadrature point -> dof index)
+    for (int z = 0; z < n; ++z)
+      for (int y = 0; y < n; ++y)
+        for (int i = 0; i < n; ++i) {
+          double s = 0.0;
+          for (int q = 0; q < n; ++q) s += B[q * n + i] * t0[q + n * y + n2 * z];
+          t1[i + n * y + n2 * z] = s;
+        }
+    for (int z = 0; z < n; ++z)
+      for (int i = 0; i < n; ++i)
+        for (int x = 0; x < n; ++x) {
+          double s = 0.0;
+          for (int q = 0; q < n; ++q) s += B[q * n + i] * t1[x + n * q + n2 * z];
+          t0[x + n * i + n2 * z] = s;
+        }
+    for (int i = 0; i < n; ++i)
+      for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+          double s = 0.0;
+          for (int q = 0; q < n; ++q) s += B[q * n + i] * t0[x + n * y + n2 * q];
+          out[x + n * y + n2 * i] = s;
+        }
+  }
+  // boundary faces
+  const double pen = m.alpha * m.p * (m.p + 2);
+  const int nn3[3] = {m.nx, m.ny, m.nz};
+  long long off = 0;
+  std::vector<double> val(n2), der(n2), tv(n2), td(n2);
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s) {
+      const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+      const double area = m.h[ta] * m.h[tb];
+      const double sgn = s ? 1.0 : -1.0;
+      const bool dir = m.bc[2 * d + s] == 0;
+      for (int cb = 0; cb < nn3[tb]; ++cb)
+        for (int ca = 0; ca < nn3[ta]; ++ca) {
+          int idx[3];
+          idx[d] = s ? nn3[d] - 1 : 0;
+          idx[ta] = ca;
+          idx[tb] = cb;
+          const long long c = idx[0] + (long long)m.nx * (idx[1] + (long long)m.ny * idx[2]);
+          const double* gv = g_qp ? g_qp + off : nullptr;
+          const double* jv = j_qp ? j_qp + off : nullptr;
+          off += n2;
+          if (dir && !gv) continue;
+          if (!dir && !jv) continue;
+          const double Kd = kval(m, c, d);
+          const double gam = pen * Kd / m.h[d];
+          for (int qb = 0; qb < n; ++qb)
+            for (int qa = 0; qa < n; ++qa) {
+              const int f = qa + n * qb;
+              const double w = W[qa] * W[qb] * area;
+              if (!dir) {
+                val[f] = -w * jv[f];
+                der[f] = 0.0;
+                continue;
+              }
+              double xi[3];
+              xi[d] = s;
+              xi[ta] = T[4 * n * n + 5 * n + qa];   // gq
+              xi[tb] = T[4 * n * n + 5 * n + qb];
+              double bq[3];
+              b_at(m, idx[0], idx[1], idx[2], xi, bq);
+              const double bn = sgn * bq[d];
+              val[f] = w * (gam * gv[f] - (bn < 0.0 ? bn * gv[f] : 0.0));
+              der[f] = -w * Kd * gv[f] * sgn / m.h[d];
+            }
+          // B^T along a then b
+          for (int qb = 0; qb < n; ++qb)
+            for (int ia = 0; ia < n; ++ia) {
+              double sv = 0.0, sd = 0.0;
+              for (int qa = 0; qa < n; ++qa) {
+                sv += B[qa * n + ia] * val[qa + n * qb];
+                sd += B[qa * n + ia] * der[qa + n * qb];
+              }
+              tv[ia + n * qb] = sv;
+              td[ia + n * qb] = sd;
+            }
+          for (int ib = 0; ib < n; ++ib)
+            for (int ia = 0; ia < n; ++ia) {
+              double sv = 0.0, sd = 0.0;
+              for (int qb = 0; qb < n; ++qb) {
+                sv += B[qb * n + ib] * tv[ia + n * qb];
+                sd += B[qb * n + ib] * td[ia + n * qb];
+              }
+              // dof with tangential indices (ia, ib), normal index k
+              int ii[3];
+              ii[ta] = ia;
+              ii[tb] = ib;
+              ii[d] = s ? n - 1 : 0;
+              rhs[c * n3 + ii[0] + n * ii[1] + n2 * ii[2]] += sv;
+              for (int k = 0; k < n; ++k) {
+                ii[d] = k;
+                rhs[c * n3 + ii[0] + n * ii[1] + n2 * ii[2]] += dl[s * n + k] * sd;
+              }
+            }
+        }
+    }
+}
+
+void quadrature_points_host(const HostMesh& m, double* vol, double* face) {
+  const int n = m.p + 1, n2 = n * n, n3 = n2 * n;
+  std::vector<double> gq, gw;
+  gauss_legendre01(n, gq, gw);
+  const long long ncell = (long long)m.nx * m.ny * m.nz;
+  if (vol) {
+    for (long long c = 0; c < ncell; ++c) {
+      const int cx = (int)(c % m.nx), cy = (int)((c / m.nx) % m.ny), cz = (int)(c / ((long long)m.nx * m.ny));
+      for (int q = 0; q < n3; ++q) {
+        double* o = vol + 3 * (c * n3 + q);
+        o[0] = (cx + gq[q % n]) * m.h[0];
+        o[1] = (cy + gq[(q / n) % n]) * m.h[1];
+        o[2] = (cz + gq[q / n2]) * m.h[2];
+      }
+    }
+  }
+  if (face) {
+    const int nn3[3] = {m.nx, m.ny, m.nz};
+    long long off = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int s = 0; s < 2; ++s) {
+        const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+        for (int cb = 0; cb < nn3[tb]; ++cb)
+          for (int ca = 0; ca < nn3[ta]; ++ca)
+            for (int qb = 0; qb < n; ++qb)
+              for (int qa = 0; qa < n; ++qa) {
+                double* o = face + 3 * off++;
+                o[d] = s ? nn3[d] * m.h[d] : 0.0;
+                o[ta] = (ca + gq[qa]) * m.h[ta];
+                o[tb] = (cb + gq[qb]) * m.h[tb];
+              }
+      }
+  }
+}
+
+}  // namespace dgmg

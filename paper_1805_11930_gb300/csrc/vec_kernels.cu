@@ -1,0 +1,300 @@
+// Vector kernels of the outer Krylov solvers (FP64 dots with a fixed
+// reduction order, axpby, precision conversion) and the sparse kernels of the
+// aggregation-AMG cycle on the Q1 coarse space: 27-point stencil residual and
+// damped Jacobi, 2x2x2 aggregate restriction / prolongation, the dense
+// coarsest-level solve, and the vertex gather of the DG -> Q1 restriction.
+#include <cuda_runtime.h>
+
+#include "dgmg_internal.h"
+
+namespace dgmg {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid1(long long n, int per = kThreads) {
+  long long g = (n + per - 1) / per;
+  if (g > 152LL * 64) g = 152LL * 64;     // grid-stride beyond 64 blocks per SM
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+template <typename T>
+__global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+__global__ void k_sub(long long n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a[i] - b[i];
+}
+
+template <typename T>
+__global__ void k_fill(long long n, T v, T* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
+template <typename A, typename B>
+__global__ void k_convert(long long n, const A* __restrict__ x, B* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (B)x[i];
+}
+
+// Block-level sum in a fixed tree order.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// Stage 1 of a dot: kDotBlocks blocks, block b sums indices b*chunk + ...
+// in a fixed order independent of timing.  k vectors xs[0..k) against y.
+__global__ void k_dot_partial(long long n, int k, const double* const* __restrict__ xs, const double* __restrict__ x1,
+                              const double* __restrict__ y, double* __restrict__ partial) {
+  __shared__ double sh[kThreads];
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  for (int j = 0; j < k; ++j) {
+    const double* x = xs ? xs[j] : x1;
+    double s = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(x[i], y[i], s);
+    const double tot = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[(long long)j * gridDim.x + blockIdx.x] = tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_dot_final(int nblocks, int k, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  for (int j = 0; j < k; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partial[(long long)j * nblocks + i];
+    const double tot = block_sum(s, sh);
+    if (threadIdx.x == 0) out[j] = tot;
+    __syncthreads();
+  }
+}
+
+// 27-point stencil helpers: row v of a (vx, vy, vz) vertex grid.
+__device__ __forceinline__ double stencil_row(int vx, int vy, int vz, const double* __restrict__ st,
+                                              const double* __restrict__ x, long long v) {
+  const int ix = (int)(v % vx);
+  const long long t = v / vx;
+  const int iy = (int)(t % vy), iz = (int)(t / vy);
+  const double* a = st + 27 * v;
+  double s = 0.0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = iz + dz;
+    if (z < 0 || z >= vz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = iy + dy;
+      if (y < 0 || y >= vy) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = ix + dx;
+        if (xx < 0 || xx >= vx) continue;
+        s = fma(a[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)], x[xx + (long long)vx * (y + (long long)vy * z)], s);
+      }
+    }
+  }
+  return s;
+}
+
+__global__ void k_stencil_jacobi(int vx, int vy, int vz, const double* __restrict__ st, const double* __restrict__ dinv,
+                                 const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ xo,
+                                 double omega, bool zero_x) {
+  const long long n = (long long)vx * vy * vz;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    if (zero_x)
+      xo[v] = omega * dinv[v] * b[v];
+    else
+      xo[v] = x[v] + omega * dinv[v] * (b[v] - stencil_row(vx, vy, vz, st, x, v));
+  }
+}
+
+__global__ void k_stencil_residual(int vx, int vy, int vz, const double* __restrict__ st, const double* __restrict__ b,
+                                   const double* __restrict__ x, double* __restrict__ r) {
+  const long long n = (long long)vx * vy * vz;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    r[v] = b[v] - stencil_row(vx, vy, vz, st, x, v);
+}
+
+// rc[I] = sum of r over the (up to) 8 fine vertices of aggregate I, fixed order.
+__global__ void k_agg_restrict(int vx, int vy, int vz, const double* __restrict__ r, double* __restrict__ rc) {
+  const int cx = (vx + 1) / 2, cy = (vy + 1) / 2, cz = (vz + 1) / 2;
+  const long long n = (long long)cx * cy * cz;
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < n; I += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(I % cx);
+    const long long t = I / cx;
+    const int iy = (int)(t % cy), iz = (int)(t / cy);
+    double s = 0.0;
+    for (int oz = 0; oz < 2; ++oz) {
+      const int z = 2 * iz + oz;
+      if (z >= vz) continue;
+      for (int oy = 0; oy < 2; ++oy) {
+        const int y = 2 * iy + oy;
+        if (y >= vy) continue;
+        for (int ox = 0; ox < 2; ++ox) {
+          const int x = 2 * ix + ox;
+          if (x >= vx) continue;
+          s += r[x + (long long)vx * (y + (long long)vy * z)];
+        }
+      }
+    }
+    rc[I] = s;
+  }
+}
+
+__global__ void k_agg_prolong_add(int vx, int vy, int vz, const double* __restrict__ xc, double* __restrict__ x) {
+  const int cx = (vx + 1) / 2, cy = (vy + 1) / 2;
+  const long long n = (long long)vx * vy * vz;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(v % vx);
+    const long long t = v / vx;
+    const int iy = (int)(t % vy), iz = (int)(t / vy);
+    x[v] += xc[(ix / 2) + (long long)cx * ((iy / 2) + (long long)cy * (iz / 2))];
+  }
+}
+
+// y = A x, A dense n x n row-major; one warp per row.
+__global__ void k_dense_matvec(int n, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s = fma(A[(long long)warp * n + j], x[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[warp] = s;
+}
+
+// r_hat(v) = sum over the cells around vertex v (fixed order) of their corner
+// sums for the corner at v.
+__global__ void k_restrict_gather(int nx, int ny, int nz, const double* __restrict__ corners, double* __restrict__ rhat) {
+  const int vx = nx + 1, vy = ny + 1;
+  const long long n = (long long)vx * vy * (nz + 1);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(v % vx);
+    const long long t = v / vx;
+    const int iy = (int)(t % vy), iz = (int)(t / vy);
+    double s = 0.0;
+    for (int az = 0; az < 2; ++az) {
+      const int cz = iz - 1 + az;
+      if (cz < 0 || cz >= nz) continue;
+      for (int ay = 0; ay < 2; ++ay) {
+        const int cy = iy - 1 + ay;
+        if (cy < 0 || cy >= ny) continue;
+        for (int ax = 0; ax < 2; ++ax) {
+          const int cx = ix - 1 + ax;
+          if (cx < 0 || cx >= nx) continue;
+          const long long c = cx + (long long)nx * (cy + (long long)ny * cz);
+          const int corner = (1 - ax) + 2 * (1 - ay) + 4 * (1 - az);
+          s += corners[8 * c + corner];
+        }
+      }
+    }
+    rhat[v] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t vec_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
+  k_axpby<double><<<grid1(n), kThreads, 0, s>>>(n, a, x, b, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_axpby_f(long long n, float a, const float* x, float b, float* y, cudaStream_t s) {
+  k_axpby<float><<<grid1(n), kThreads, 0, s>>>(n, a, x, b, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_sub(long long n, const double* a, const double* b, double* out, cudaStream_t s) {
+  k_sub<double><<<grid1(n), kThreads, 0, s>>>(n, a, b, out);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_sub_f(long long n, const float* a, const float* b, float* out, cudaStream_t s) {
+  k_sub<float><<<grid1(n), kThreads, 0, s>>>(n, a, b, out);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_copy(long long n, const double* x, double* y, cudaStream_t s) {
+  return cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+cudaError_t vec_fill(long long n, double v, double* y, cudaStream_t s) {
+  k_fill<double><<<grid1(n), kThreads, 0, s>>>(n, v, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_fill_f(long long n, float v, float* y, cudaStream_t s) {
+  k_fill<float><<<grid1(n), kThreads, 0, s>>>(n, v, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_d2f(long long n, const double* x, float* y, cudaStream_t s) {
+  k_convert<double, float><<<grid1(n), kThreads, 0, s>>>(n, x, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_f2d(long long n, const float* x, double* y, cudaStream_t s) {
+  k_convert<float, double><<<grid1(n), kThreads, 0, s>>>(n, x, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_dot(long long n, const double* x, const double* y, double* partial, double* out, cudaStream_t s) {
+  k_dot_partial<<<kDotBlocks, kThreads, 0, s>>>(n, 1, nullptr, x, y, partial);
+  k_dot_final<<<1, kThreads, 0, s>>>(kDotBlocks, 1, partial, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+cudaError_t vec_multi_dot(long long n, int k, const double* const* xs, const double* y, double* partial, double* out,
+                          cudaStream_t s) {
+  k_dot_partial<<<kDotBlocks, kThreads, 0, s>>>(n, k, xs, nullptr, y, partial);
+  k_dot_final<<<1, kThreads, 0, s>>>(kDotBlocks, k, partial, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+cudaError_t stencil_jacobi(int vx, int vy, int vz, const double* st, const double* dinv, const double* b,
+                           const double* x, double* xout, double omega, bool zero_x, cudaStream_t s) {
+  k_stencil_jacobi<<<grid1((long long)vx * vy * vz), kThreads, 0, s>>>(vx, vy, vz, st, dinv, b, x, xout, omega, zero_x);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t stencil_residual(int vx, int vy, int vz, const double* st, const double* b, const double* x, double* r,
+                             cudaStream_t s) {
+  k_stencil_residual<<<grid1((long long)vx * vy * vz), kThreads, 0, s>>>(vx, vy, vz, st, b, x, r);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t agg_restrict(int vx, int vy, int vz, const double* r, double* rc, cudaStream_t s) {
+  const long long nc = (long long)((vx + 1) / 2) * ((vy + 1) / 2) * ((vz + 1) / 2);
+  k_agg_restrict<<<grid1(nc), kThreads, 0, s>>>(vx, vy, vz, r, rc);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t agg_prolong_add(int vx, int vy, int vz, const double* xc, double* x, cudaStream_t s) {
+  k_agg_prolong_add<<<grid1((long long)vx * vy * vz), kThreads, 0, s>>>(vx, vy, vz, xc, x);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t dense_matvec(int n, const double* A, const double* x, double* y, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)(((long long)n * 32 + threads - 1) / threads);
+  k_dense_matvec<<<blocks, threads, 0, s>>>(n, A, x, y);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t restrict_gather(int nx, int ny, int nz, const double* corners, double* rhat, cudaStream_t s) {
+  k_restrict_gather<<<grid1((long long)(nx + 1) * (ny + 1) * (nz + 1)), kThreads, 0, s>>>(nx, ny, nz, corners, rhat);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace dgmg

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of the C ABI in include/dgmg.h.
+
+Every function here only marshals arguments (torch tensors -> device
+pointers, numpy arrays -> host pointers) and checks the returned status; all
+computation happens in libdgmg.so.  There is no fallback: if the library
+cannot be loaded, or a call fails, a DgmgError is raised.
+
+The function names are those of the C ABI (dgmg_create, dgmg_apply, ...);
+`Context` bundles them for convenience.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DGMG_OK = 0
+STATUS = {0: "DGMG_OK", 1: "DGMG_ERR_ARG", 2: "DGMG_ERR_OOM", 3: "DGMG_ERR_CUDA", 4: "DGMG_ERR_STATE",
+          5: "DGMG_ERR_NOT_CONVERGED", 6: "DGMG_ERR_BREAKDOWN", 7: "DGMG_ERR_TIMEOUT"}
+FP64, FP32 = 0, 1
+KRYLOV_CG, KRYLOV_FCG, KRYLOV_FGMRES = 0, 1, 2
+INNER_PCG, INNER_GMRES = 0, 1
+COARSE_AMG, COARSE_NONE = 0, 1
+
+
+class DgmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("krylov", ctypes.c_int), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("smoother_prec", ctypes.c_int), ("omega", ctypes.c_double),
+                ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("eps_inner", ctypes.c_double),
+                ("maxit_inner", ctypes.c_int), ("inner", ctypes.c_int), ("inner_restart", ctypes.c_int),
+                ("coarse", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("inner_mean", ctypes.c_double), ("inner_max", ctypes.c_int), ("ms_total", ctypes.c_double),
+                ("inner_its_total", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
+                ("zero_sweeps", ctypes.c_longlong),
+                ("applies", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("ms_smooth", ctypes.c_double), ("ms_apply", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_LL = ctypes.c_longlong
+_SIG = {
+    "dgmg_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
+    "dgmg_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "dgmg_destroy": (_I, [_P]),
+    "dgmg_last_error": (ctypes.c_char_p, [_P]),
+    "dgmg_set_mesh": (_I, [_P, _I, _I, _I, _D, _D, _D, _I, _P]),
+    "dgmg_set_coefficients": (_I, [_P, _P, _I, _P, _P]),
+    "dgmg_sizes": (_I, [_P] + [ctypes.POINTER(_LL)] * 5),
+    "dgmg_quadrature_points": (_I, [_P, _P, _P]),
+    "dgmg_assemble_rhs": (_I, [_P, _P, _P, _P, _P]),
+    "dgmg_apply": (_I, [_P, _P, _P, _I]),
+    "dgmg_block_apply": (_I, [_P, _P, _P, _I]),
+    "dgmg_block_diagonal": (_I, [_P, _P, _I]),
+    "dgmg_block_smooth": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, _I, _I, _P]),
+    "dgmg_restrict": (_I, [_P, _P, _P, _I]),
+    "dgmg_prolong_add": (_I, [_P, _P, _P, _I]),
+    "dgmg_coarse_matrix": (_I, [_P, _P]),
+    "dgmg_coarse_cycle": (_I, [_P, _P, _P]),
+    "dgmg_vcycle": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts)]),
+    "dgmg_solve": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libdgmg.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or (build_if_missing and not _build.up_to_date()):
+        if not build_if_missing:
+            raise DgmgError(3, f"{path} not built; run paper_1805_11930_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIG.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int), None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise DgmgError(1, "expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise DgmgError(1, "expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _host(a, dtype=np.float64):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data
+
+
+def _prec(t):
+    import torch
+    if t.dtype == torch.float64:
+        return FP64
+    if t.dtype == torch.float32:
+        return FP32
+    raise DgmgError(1, f"unsupported dtype {t.dtype}")
+
+
+def default_opts(**kw):
+    o = SolveOpts()
+    load().dgmg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """A dgmg_ctx bound to one device and stream (default: torch's current
+    stream on that device)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self.stream = stream
+        self.device = device
+        h = _P()
+        st = self.lib.dgmg_create(ctypes.byref(h), device, stream)
+        if st != DGMG_OK:
+            raise DgmgError(st, "dgmg_create failed")
+        self.h = h
+        self.mesh = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != DGMG_OK:
+            raise DgmgError(st, self.lib.dgmg_last_error(self.h).decode())
+        return st
+
+    # ------------------------------------------------------------ setup
+    def set_mesh(self, nx, ny, nz, lx, ly, lz, p, bc):
+        bca = (ctypes.c_int * 6)(*[int(b) for b in bc])
+        self._check(self.lib.dgmg_set_mesh(self.h, nx, ny, nz, lx, ly, lz, p, bca))
+        self.mesh = (nx, ny, nz, lx, ly, lz, p, list(bc))
+
+    def set_coefficients(self, K, b_vertex=None, c_cell=None):
+        K = np.asarray(K, dtype=np.float64)
+        kdim = 1 if K.ndim == 1 else K.shape[1]
+        Ka, Kp = _host(K)
+        ba, bp = _host(b_vertex)
+        ca, cp = _host(c_cell)
+        self._check(self.lib.dgmg_set_coefficients(self.h, Kp, kdim, bp, cp))
+
+    def sizes(self):
+        v = [_LL() for _ in range(5)]
+        self._check(self.lib.dgmg_sizes(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("ndof", "nvert", "ncell", "nvol_qp", "nface_qp"), [x.value for x in v]))
+
+    def quadrature_points(self):
+        s = self.sizes()
+        vol = np.zeros((s["nvol_qp"], 3))
+        face = np.zeros((s["nface_qp"], 3))
+        self._check(self.lib.dgmg_quadrature_points(self.h, vol.ctypes.data, face.ctypes.data))
+        return vol, face
+
+    def assemble_rhs(self, f_qp, rhs, g_qp=None, j_qp=None):
+        fa, fp = _host(f_qp)
+        ga, gp = _host(g_qp)
+        ja, jp = _host(j_qp)
+        self._check(self.lib.dgmg_assemble_rhs(self.h, fp, gp, jp, _ptr(rhs)))
+
+    # ------------------------------------------------------------ operators
+    def apply(self, u, v):
+        self._check(self.lib.dgmg_apply(self.h, _ptr(u), _ptr(v), _prec(u)))
+
+    def block_apply(self, u, v):
+        self._check(self.lib.dgmg_block_apply(self.h, _ptr(u), _ptr(v), _prec(u)))
+
+    def block_diagonal(self, diag):
+        self._check(self.lib.dgmg_block_diagonal(self.h, _ptr(diag), _prec(diag)))
+
+    def block_smooth(self, f, u, nsweep=1, omega=1.0, eps=1e-2, maxit=0, inner=INNER_PCG, inner_restart=12,
+                     inner_its=None):
+        self._check(self.lib.dgmg_block_smooth(self.h, _ptr(f), _ptr(u), nsweep, omega, eps, maxit, inner,
+                                               inner_restart, _prec(u), _ptr(inner_its)))
+
+    def restrict(self, r, r_hat):
+        self._check(self.lib.dgmg_restrict(self.h, _ptr(r), _ptr(r_hat), _prec(r)))
+
+    def prolong_add(self, u_hat, u):
+        self._check(self.lib.dgmg_prolong_add(self.h, _ptr(u_hat), _ptr(u), _prec(u)))
+
+    def coarse_matrix(self):
+        s = self.sizes()
+        st = np.zeros(27 * s["nvert"])
+        self._check(self.lib.dgmg_coarse_matrix(self.h, st.ctypes.data))
+        return st.reshape(s["nvert"], 27)
+
+    def coarse_cycle(self, r_hat, u_hat):
+        self._check(self.lib.dgmg_coarse_cycle(self.h, _ptr(r_hat), _ptr(u_hat)))
+
+    def vcycle(self, f, u, opts=None):
+        o = opts if opts is not None else default_opts()
+        self._check(self.lib.dgmg_vcycle(self.h, _ptr(f), _ptr(u), ctypes.byref(o)))
+
+    def solve(self, f, u, opts=None, check=True):
+        o = opts if opts is not None else default_opts()
+        stats = SolveStats()
+        st = self.lib.dgmg_solve(self.h, _ptr(f), _ptr(u), ctypes.byref(o), ctypes.byref(stats))
+        if check:
+            self._check(st)
+        return stats.as_dict() | {"status": STATUS.get(st, st)}
+
+
+def exported_symbols(header_path=None):
+    """Names of the functions declared in include/dgmg.h."""
+    import re
+    header_path = header_path or os.path.join(_build.INCLUDE, "dgmg.h")
+    text = open(header_path).read()
+    return sorted(set(re.findall(r"\b(dgmg_[a-z_]+)\s*\(", text)))

@@ -1,0 +1,303 @@
+"""GPU parity: every step of the hot path through the C ABI against the CPU
+oracle, element by element, on seeded inputs.
+
+Tolerances: FP64 operators 1e-12 relative (norm-wise), FP32 operators 1e-5
+relative; quantities that pass through an iterative inner solve get a bound
+derived from the solve tolerance (stated at each test).  Mesh sizes span
+several thread blocks and leave ragged tails (one warp owns
+max(1, 32/(p+1)^2) cells, a block 4 warps)."""
+import numpy as np
+import pytest
+
+from oracle import amg, dg, solvers, transfer
+from paper_1805_11930_gb300 import inputs
+
+from gpu_helpers import custom, gpu_context, gpu_rhs, oracle_problem, oracle_rhs, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # (nc, p, bc, advect, react, kdim)
+    "p1_dir": ((5, 3, 3), 1, [0] * 6, False, False, 1),
+    "p2_mixed": ((5, 3, 3), 2, [0, 1, 0, 0, 1, 0], False, True, 3),
+    "p3_adv": ((4, 3, 3), 3, [0, 0, 1, 0, 0, 1], True, False, 3),
+    "p4_full": ((3, 3, 3), 4, [0, 1, 0, 1, 0, 0], True, True, 3),
+    "p5_dir": ((3, 2, 2), 5, [0] * 6, False, False, 1),
+    "p6_adv": ((2, 2, 2), 6, [1, 0, 0, 0, 0, 0], True, True, 3),
+    "p8_dir": ((2, 1, 1), 8, [0] * 6, False, True, 3),
+}
+
+
+def make_case(name, seed=11):
+    nc, p, bc, adv, react, kdim = CASES[name]
+    rng = np.random.default_rng(seed)
+    ncell = int(np.prod(nc))
+    L = (1.0, 0.75, 1.25)
+    K = np.exp(rng.normal(size=(ncell, kdim) if kdim == 3 else ncell))
+    b = None
+    if adv:
+        b = inputs.vertex_field(nc, L, lambda x, y, z: np.stack([1 - 2 * y, x - 0.3, 0.25 + 0.5 * z], -1))
+    c = rng.uniform(0.1, 2.0, size=ncell) if react else None
+    return custom(nc, L, p, bc, K, b=b, c=c, g=lambda x, y, z: x + y * z, j=lambda x, y, z: np.cos(x))
+
+
+_cache = {}
+
+
+def oracle_matrix(name):
+    if name not in _cache:
+        w = make_case(name)
+        P = oracle_problem(w)
+        _cache[name] = (w, P, P.assemble())
+    return _cache[name]
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda").contiguous()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_fp64_and_fp32(name):
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    u = inputs.random_dg_vector(P.ndof, seed=3)
+    ref = A @ u
+    v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(u), v)
+    assert rel_err(v.cpu().numpy(), ref) < 1e-12
+    u32 = dev(u, torch.float32)
+    v32 = torch.empty(P.ndof, dtype=torch.float32, device="cuda")
+    ctx.apply(u32, v32)
+    assert rel_err(v32.cpu().numpy(), A @ u32.cpu().double().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_block_apply_and_diagonal(name):
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    N = P.N
+    Ab = A.tobsr(blocksize=(N, N))
+    D = np.zeros((P.ncell, N, N))
+    for c in range(P.ncell):
+        for k in range(Ab.indptr[c], Ab.indptr[c + 1]):
+            if Ab.indices[k] == c:
+                D[c] = Ab.data[k]
+    u = inputs.random_dg_vector(P.ndof, seed=4)
+    ref = np.einsum('cij,cj->ci', D, u.reshape(P.ncell, N)).reshape(-1)
+    v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.block_apply(dev(u), v)
+    assert rel_err(v.cpu().numpy(), ref) < 1e-12
+    dg_ = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.block_diagonal(dg_)
+    refd = np.einsum('cii->ci', D).reshape(-1)
+    assert rel_err(dg_.cpu().numpy(), refd) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p5_dir"])
+def test_restrict_prolong_and_coarse_matrix(name):
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    Pm = transfer.prolongation(P)
+    r = inputs.random_dg_vector(P.ndof, seed=5)
+    rh = torch.empty(P.nvert, dtype=torch.float64, device="cuda")
+    ctx.restrict(dev(r), rh)
+    assert rel_err(rh.cpu().numpy(), Pm.T @ r) < 1e-13
+    uh = inputs.random_dg_vector(P.nvert, seed=6)
+    u = inputs.random_dg_vector(P.ndof, seed=7)
+    ud = dev(u)
+    ctx.prolong_add(dev(uh), ud)
+    assert rel_err(ud.cpu().numpy(), u + Pm @ uh) < 1e-13
+    # A_hat (27-point stencil) against the oracle's P^T A P
+    G = (Pm.T @ A @ Pm).toarray()
+    st = ctx.coarse_matrix()
+    Ah = np.zeros_like(G)
+    Vx, Vy, Vz = P.nv
+    for v in range(P.nvert):
+        ix, iy, iz = v % Vx, (v // Vx) % Vy, v // (Vx * Vy)
+        for k in range(27):
+            jx, jy, jz = ix + k % 3 - 1, iy + (k // 3) % 3 - 1, iz + k // 9 - 1
+            if 0 <= jx < Vx and 0 <= jy < Vy and 0 <= jz < Vz:
+                Ah[v, jx + Vx * (jy + Vy * jz)] = st[v, k]
+            else:
+                assert st[v, k] == 0.0
+    assert np.abs(Ah - G).max() < 1e-12 * np.abs(G).max()
+
+
+@pytest.mark.parametrize("nc", [(7, 6, 5), (9, 8, 8)])
+def test_coarse_amg_cycle(nc):
+    """Device AMG V-cycle equals the oracle's AMG (same aggregation,
+    Galerkin levels, Jacobi 2/3, dense coarsest solve)."""
+    rng = np.random.default_rng(8)
+    w = custom(nc, (1, 1, 1), 2, [0] * 6, np.exp(rng.normal(size=int(np.prod(nc)))))
+    P = oracle_problem(w)
+    Ah = transfer.q1_matrix(P)
+    am = amg.AggregationAMG(Ah, P.nv, coarse_size=512)
+    ctx = gpu_context(w)
+    r = rng.normal(size=P.nvert)
+    out = torch.empty(P.nvert, dtype=torch.float64, device="cuda")
+    ctx.coarse_cycle(dev(r), out)
+    assert rel_err(out.cpu().numpy(), am.vcycle(r)) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p4_full", "p5_dir"])
+def test_block_smooth_exact_blocks(name):
+    """eps = 1e-13: each block solve is exact to ~kappa(D_T) 1e-13, so two
+    sweeps match the oracle's dense-LU block-Jacobi to 1e-9."""
+    w, P, A = oracle_matrix(name)
+    if w["b"] is not None:
+        pytest.skip("PCG needs symmetric blocks")
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=9)
+    u0 = inputs.random_dg_vector(P.ndof, seed=10)
+    S = solvers.BlockJacobi(A, P.N, inner="lu")
+    ref = S(f, u0, 2, 0.8)
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=2, omega=0.8, eps=1e-13, maxit=10 * P.N)
+    assert rel_err(u.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["p2_mixed", "p5_dir"])
+def test_block_smooth_inexact_matches_oracle_pcg(name):
+    """eps = 1e-2: same PCG on the same block from the same start; cells whose
+    iteration count equals the oracle's match to 1e-10, and every cell meets
+    its stopping test."""
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=12)
+    u0 = inputs.random_dg_vector(P.ndof, seed=13)
+    S = solvers.BlockJacobi(A, P.N, inner="pcg", eps=1e-2)
+    ref = S(f, u0, 1, 1.0)
+    its = torch.zeros(P.ncell, dtype=torch.int32, device="cuda")
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=1, omega=1.0, eps=1e-2, inner_its=its)
+    got = u.cpu().numpy()
+    its = its.cpu().numpy()
+    same = its == S.last_its
+    assert same.mean() > 0.9
+    N = P.N
+    d = f - A @ u0
+    for c in range(P.ncell):
+        sl = slice(c * N, (c + 1) * N)
+        delta = got[sl] - u0[sl]
+        D = S.D[c]
+        assert np.linalg.norm(d[sl] - D @ delta) <= 1e-2 * np.linalg.norm(d[sl]) * (1 + 1e-9)
+        if same[c]:
+            assert rel_err(got[sl] - u0[sl], ref[sl] - u0[sl]) < 1e-10
+
+
+def test_vcycle_matches_oracle():
+    """One V-cycle (Algorithm 1) with near-exact block solves against the
+    oracle's V-cycle with dense-LU blocks and the same AMG."""
+    w = make_case("p2_mixed")
+    P = oracle_problem(w)
+    A = P.assemble()
+    Pm = transfer.prolongation(P)
+    am = amg.AggregationAMG(transfer.q1_matrix(P), P.nv, coarse_size=512)
+    V = solvers.HybridVCycle(A, Pm, solvers.BlockJacobi(A, P.N, inner="lu"), am.vcycle, omega=0.8)
+    f = inputs.random_dg_vector(P.ndof, seed=14)
+    ref = V(f)
+    from paper_1805_11930_gb300 import dgmg
+    ctx = gpu_context(w)
+    u = torch.zeros(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.vcycle(dev(f), u, dgmg.default_opts(omega=0.8, eps_inner=1e-13, maxit_inner=10 * P.N))
+    assert rel_err(u.cpu().numpy(), ref) < 1e-9
+
+
+def test_rhs_assembly():
+    w = make_case("p3_adv")
+    P = oracle_problem(w)
+    ref = oracle_rhs(P, w)
+    ctx = gpu_context(w)
+    rhs = gpu_rhs(ctx, w, torch)
+    assert rel_err(rhs.cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("krylov", ["cg", "fcg"])
+def test_solve_poisson_c1(krylov):
+    """Poisson 8^3, Q2 (13,824 dofs): CG + V-cycle to 1e-8 (true FP64
+    residual); the solution matches the oracle's direct solve to the
+    accuracy the residual allows, and the discretisation error is O(h^3)-small."""
+    import scipy.sparse.linalg as spla
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.poisson_sine(8, 2)
+    P = oracle_problem(w)
+    A = P.assemble()
+    F = oracle_rhs(P, w)
+    x = spla.spsolve(A.tocsc(), F)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    assert rel_err(f.cpu().numpy(), F) < 1e-13
+    u = torch.zeros_like(f)
+    kry = dgmg.KRYLOV_CG if krylov == "cg" else dgmg.KRYLOV_FCG
+    st = ctx.solve(f, u, dgmg.default_opts(krylov=kry))
+    assert st["converged"] == 1 and st["rel_residual"] <= 1e-8
+    assert st["iterations"] < 40
+    assert st["inner_mean"] < 5 and st["inner_max"] <= 27
+    uh = u.cpu().numpy()
+    assert rel_err(uh, x) < 1e-6
+    assert P.l2_error(uh, w["exact"]) < 2e-3
+
+
+def test_solve_mixed_precision_same_residual():
+    """FP32 smoother and V-cycle, FP64 outer flexible CG: same 1e-8 FP64
+    residual; solution within 1e-6 of the FP64 GPU solution."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.lognormal(8, 3)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    u64 = torch.zeros_like(f)
+    s64 = ctx.solve(f, u64, dgmg.default_opts())
+    u32 = torch.zeros_like(f)
+    s32 = ctx.solve(f, u32, dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG))
+    assert s64["converged"] and s32["converged"]
+    assert s32["rel_residual"] <= 1e-8
+    assert rel_err(u32.cpu().numpy(), u64.cpu().numpy()) < 1e-6
+
+
+def test_solve_fgmres_matches_cg():
+    """Right-preconditioned flexible GMRES(30) reaches the same 1e-8 residual
+    and the same solution as CG on a symmetric problem."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.lognormal(6, 2)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    u = torch.zeros_like(f)
+    st = ctx.solve(f, u, dgmg.default_opts(krylov=dgmg.KRYLOV_FGMRES, restart=30))
+    assert st["converged"] and st["rel_residual"] <= 1e-8
+    u2 = torch.zeros_like(f)
+    ctx.solve(f, u2, dgmg.default_opts())
+    assert rel_err(u.cpu().numpy(), u2.cpu().numpy()) < 1e-6
+
+
+def test_full_size_sampled_apply_lognormal_32():
+    """32^3, Q4 (4.1M dofs), the launch configuration the benchmark times:
+    sampled cells (corners, edges, faces, interior) against the oracle's block
+    rows."""
+    w = inputs.lognormal(32, 4)
+    P = oracle_problem(w)
+    ctx = gpu_context(w)
+    u = inputs.random_dg_vector(P.ndof, seed=15)
+    v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(u), v)
+    n = 32
+    picks = [P.cell_index(0, 0, 0), P.cell_index(n - 1, n - 1, n - 1), P.cell_index(0, n - 1, 5),
+             P.cell_index(17, 0, n - 1), P.cell_index(16, 16, 16), P.cell_index(3, 29, 11)]
+    picks += list(np.random.default_rng(16).integers(0, P.ncell, size=6))
+    ref = P.apply_rows(u, picks)
+    got = v.cpu().numpy().reshape(P.ncell, P.N)[picks]
+    assert rel_err(got, ref) < 1e-12
+
+
+def test_errors_are_reported():
+    from paper_1805_11930_gb300 import dgmg
+    w = make_case("p2_mixed")
+    ctx = dgmg.Context(0)
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_mesh(2, 2, 2, 1, 1, 1, 9, [0] * 6)          # p out of range
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    with pytest.raises(dgmg.DgmgError):
+        ctx.apply(torch.zeros(10, dtype=torch.float64, device="cuda"),
+                  torch.zeros(10, dtype=torch.float64, device="cuda"))   # no coefficients yet
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_coefficients(-np.ones(np.prod(w["nc"])))                  # K <= 0
