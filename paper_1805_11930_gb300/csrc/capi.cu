@@ -41,10 +41,30 @@ const CellOps* cell_ops(int n) {
 }
 
 namespace {
+// Adds the per-cell inner iteration counts of one sweep to a running sum and
+// maximum (integer atomics once per block; the result is order independent).
 __global__ void k_its_acc(long long n, const int* __restrict__ its, unsigned long long* sum, int* mx) {
+  __shared__ unsigned long long ssum[256];
+  __shared__ int smax[256];
+  unsigned long long s = 0;
+  int m = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    atomicAdd(sum, (unsigned long long)its[i]);
-    atomicMax(mx, its[i]);
+    s += (unsigned long long)its[i];
+    m = its[i] > m ? its[i] : m;
+  }
+  ssum[threadIdx.x] = s;
+  smax[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      ssum[threadIdx.x] += ssum[threadIdx.x + o];
+      smax[threadIdx.x] = smax[threadIdx.x] > smax[threadIdx.x + o] ? smax[threadIdx.x] : smax[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(sum, ssum[0]);
+    atomicMax(mx, smax[0]);
   }
 }
 }  // namespace
@@ -78,6 +98,11 @@ struct dgmg_ctx {
   double *dK = nullptr, *dc = nullptr, *db = nullptr;
   double* diag64 = nullptr;
   float* diag32 = nullptr;
+  double* dinv64 = nullptr;      // 1 / diag(D_T), used by the smoothers
+  float* dinv32 = nullptr;
+  double* rec64 = nullptr;       // per-cell coefficient records
+  float* rec32 = nullptr;
+  float* db32 = nullptr;         // float copy of b
   double* w64[3] = {nullptr, nullptr, nullptr};
   float* w32[4] = {nullptr, nullptr, nullptr, nullptr};
   double* corners = nullptr;
@@ -153,8 +178,8 @@ dgmg_status dalloc(dgmg_ctx* ctx, T** p, size_t count) {
 void free_mesh(dgmg_ctx* ctx) {
   for (void* q : ctx->mesh_allocs) cudaFree(q);
   ctx->mesh_allocs.clear();
-  ctx->dK = ctx->dc = ctx->db = ctx->diag64 = nullptr;
-  ctx->diag32 = nullptr;
+  ctx->dK = ctx->dc = ctx->db = ctx->diag64 = ctx->dinv64 = ctx->rec64 = nullptr;
+  ctx->diag32 = ctx->dinv32 = ctx->rec32 = ctx->db32 = nullptr;
   for (auto& w : ctx->w64) w = nullptr;
   for (auto& w : ctx->w32) w = nullptr;
   ctx->corners = nullptr;
@@ -183,6 +208,19 @@ MeshParams params(const dgmg_ctx* ctx) {
   m.c = ctx->dc;
   m.bvert = ctx->db;
   m.alpha = 1.25;
+  m.rec64 = ctx->rec64;
+  m.rec32 = ctx->rec32;
+  m.bvert32 = ctx->db32;
+  const double J = ctx->h[0] * ctx->h[1] * ctx->h[2];
+  for (int d = 0; d < 3; ++d) {
+    const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+    m.ih[d] = 1.0 / ctx->h[d];
+    m.area[d] = ctx->h[a] * ctx->h[b];
+    m.jh[d] = J / ctx->h[d];
+    m.ihf[d] = (float)m.ih[d];
+    m.areaf[d] = (float)m.area[d];
+    m.jhf[d] = (float)m.jh[d];
+  }
   return m;
 }
 
@@ -242,7 +280,9 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     return DGMG_OK;
   }
   if (maxit <= 0) maxit = ctx->n * ctx->n * ctx->n;
-  if (inner != DGMG_INNER_PCG) return fail(ctx, DGMG_ERR_ARG, "inner GMRES block solve is not built yet");
+  if (inner != DGMG_INNER_PCG && inner != DGMG_INNER_GMRES) return fail(ctx, DGMG_ERR_ARG, "bad inner solver");
+  if (inner == DGMG_INNER_GMRES && (restart < 1 || restart > 64))
+    return fail(ctx, DGMG_ERR_ARG, "inner_restart must be in [1, 64]");
   const MeshParams mp = params(ctx);
   void* src = u;
   void* dst = tmp;
@@ -251,7 +291,7 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     a.f = f;
     a.uold = (k == 0 && zero_first) ? nullptr : src;
     a.unew = dst;
-    a.diag = fp32 ? (const void*)ctx->diag32 : (const void*)ctx->diag64;
+    a.diag = fp32 ? (const void*)ctx->dinv32 : (const void*)ctx->dinv64;
     a.omega = omega;
     a.eps = eps;
     a.maxit = maxit;
@@ -264,7 +304,7 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     ++ctx->n_sweep;
     if (k == 0 && zero_first) ++ctx->n_zero_sweep;
     if (ctx->track_its) {
-      k_its_acc<<<152 * 8, 256, 0, ctx->stream>>>(ctx->ncell, ctx->its, ctx->itsum, ctx->itmax);
+      k_its_acc<<<152, 256, 0, ctx->stream>>>(ctx->ncell, ctx->its, ctx->itsum, ctx->itmax);
       count_launch();
       CK(cudaGetLastError());
       ++ctx->sweeps_tracked;
@@ -677,6 +717,8 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   if (b_vertex) {
     CS(dalloc(ctx, &ctx->db, 3 * ctx->nvert));
     CK(cudaMemcpy(ctx->db, b_vertex, 3 * ctx->nvert * sizeof(double), cudaMemcpyHostToDevice));
+    CS(dalloc(ctx, &ctx->db32, 3 * ctx->nvert));
+    CK(vec_d2f(3 * ctx->nvert, ctx->db, ctx->db32, ctx->stream));
   }
   if (c_cell) {
     CS(dalloc(ctx, &ctx->dc, ctx->ncell));
@@ -684,6 +726,10 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   }
   CS(dalloc(ctx, &ctx->diag64, n));
   CS(dalloc(ctx, &ctx->diag32, n));
+  CS(dalloc(ctx, &ctx->dinv64, n));
+  CS(dalloc(ctx, &ctx->dinv32, n));
+  CS(dalloc(ctx, &ctx->rec64, kRecLen * ctx->ncell));
+  CS(dalloc(ctx, &ctx->rec32, kRecLen * ctx->ncell));
   for (auto& w : ctx->w64) CS(dalloc(ctx, &w, n));
   for (auto& w : ctx->w32) CS(dalloc(ctx, &w, n));
   CS(dalloc(ctx, &ctx->corners, 8 * ctx->ncell));
@@ -693,8 +739,10 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   CS(dalloc(ctx, &ctx->rhat, ctx->nvert));
   CS(dalloc(ctx, &ctx->uhat, ctx->nvert));
   const MeshParams mp = params(ctx);
+  CK(cell_records(mp, ctx->rec64, ctx->rec32, ctx->stream));
   CK(ctx->ops->diag(mp, ctx->diag64, ctx->stream));
   CK(vec_d2f(n, ctx->diag64, ctx->diag32, ctx->stream));
+  CK(vec_inverse(n, ctx->diag64, ctx->dinv64, ctx->dinv32, ctx->stream));
   // Q1 matrix and AMG hierarchy (host setup, device cycle)
   const HostMesh hm = host_mesh(ctx);
   ctx->q1 = q1_stencil(hm);

@@ -56,6 +56,7 @@ struct Tab {
   T G[N][N];
   T hat[2][N];
   T gq[N];
+  T S1[N][N];
 };
 
 __constant__ Tab<double> c_tab_d;
@@ -68,15 +69,40 @@ __device__ __forceinline__ const Tab<double>& tab<double>() { return c_tab_d; }
 template <>
 __device__ __forceinline__ const Tab<float>& tab<float>() { return c_tab_f; }
 
-// Per-cell coefficients staged in shared memory.
+// Mesh scalars and coefficient records in the kernel's precision (no
+// double arithmetic in the float kernels: the FP64 pipe is 1/64 of FP32).
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static __device__ __forceinline__ double ih(const MeshParams& m, int d) { return m.ih[d]; }
+  static __device__ __forceinline__ double area(const MeshParams& m, int d) { return m.area[d]; }
+  static __device__ __forceinline__ double jh(const MeshParams& m, int d) { return m.jh[d]; }
+  static __device__ __forceinline__ const double* rec(const MeshParams& m) { return m.rec64; }
+  static __device__ __forceinline__ double bv(const MeshParams& m, long long i) { return __ldg(m.bvert + i); }
+};
+template <> struct Prec<float> {
+  static __device__ __forceinline__ float ih(const MeshParams& m, int d) { return m.ihf[d]; }
+  static __device__ __forceinline__ float area(const MeshParams& m, int d) { return m.areaf[d]; }
+  static __device__ __forceinline__ float jh(const MeshParams& m, int d) { return m.jhf[d]; }
+  static __device__ __forceinline__ const float* rec(const MeshParams& m) { return m.rec32; }
+  static __device__ __forceinline__ float bv(const MeshParams& m, long long i) { return __ldg(m.bvert32 + i); }
+};
+
+// Per-cell coefficients and face data staged in shared memory (computed
+// once per cell; faces f = 2d + s, s = 0 low side, 1 high side).
 template <typename T>
 struct CellInfo {
-  T kd[3];      // |J| K_d / h_d^2
-  T cJ;         // c |J|
-  T jh[3];      // |J| / h_d
-  T bc[3][8];   // b_d at the 8 corners, corner = ox + 2 oy + 4 oz
-  T pad;
+  long long nb[6];  // neighbour cell across face f (interior faces)
+  T kd[3];          // |J| K_d / h_d^2
+  T cJ;             // c |J|
+  T jh[3];          // |J| / h_d
+  T bc[3][8];       // b_d at the 8 corners, corner = ox + 2 oy + 4 oz
+  T kap[6];         // K^-K^+/(K^-+K^+) (interior) or K (Dirichlet)
+  T gam[6];         // penalty gamma_F
+  int kind[6];      // 0 interior, 1 Dirichlet, 2 Neumann
+  int pad[2];
 };
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // Geometry of line L along axis D: owning cell slot cw, first element,
 // stride, and the two tangential coordinates (a < b in axis order).
@@ -207,11 +233,65 @@ __device__ __forceinline__ void grad_pass(const T* __restrict__ U, T* __restrict
   }
 }
 
-// Y = A^v X for the warp's cells (Sec. 3.1, Stages 1-3).  S0, S1 scratch.
+// out (+)= scale_cw * (A in) along axis D; scale = kd[SEL] (SEL < 3) or cJ.
+template <int D, bool ACC, int SEL, typename T>
+__device__ __forceinline__ void contract_scaled(const T* __restrict__ in, T* __restrict__ out, const T (&A)[N][N],
+                                                int lane, const unsigned char* act, const CellInfo<T>* ci) {
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+    const T sc = SEL < 3 ? ci[cw].kd[SEL < 3 ? SEL : 0] : ci[cw].cJ;
+    T x[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = in[base + j * st];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(A[i][j], x[j], s);
+      if (ACC)
+        out[base + i * st] = fma(sc, s, out[base + i * st]);
+      else
+        out[base + i * st] = sc * s;
+    }
+  }
+}
+
+// Y = A^v X for the warp's cells.  S0, S1 scratch.
+//  b = 0: K and c are constant per cell and the cell affine, so the volume
+//   matrix is exactly sum_d |J| K_d / h_d^2 (S (x) M (x) M)_d + c |J| M (x) M (x) M
+//   with the 1D stiffness S = G^T W G and mass M = B^T W B of the GLL basis
+//   under the Gauss rule: 8 contractions (9 with c), no pointwise work.
+//  b != 0: the three stages of Sec. 3.1 at the Gauss points (B, fused
+//   Dg / coefficients / Dg^T, B^T), since b varies inside the cell.
 template <bool ADV, bool REACT, typename T>
 __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane, const CellInfo<T>* ci,
                                        const unsigned char* act) {
   const Tab<T>& t = tab<T>();
+  if (!ADV) {
+    contract<2, false, false>(X, S0, t.M1, lane, act);          // a = M_z u
+    __syncwarp();
+    contract<1, false, false>(S0, S1, t.M1, lane, act);         // b = M_y a
+    __syncwarp();
+    contract_scaled<0, false, 0>(S1, Y, t.S1, lane, act, ci);   // Y = kx S_x b
+    __syncwarp();
+    contract<0, false, false>(S0, S1, t.M1, lane, act);         // c = M_x a
+    __syncwarp();
+    contract_scaled<1, true, 1>(S1, Y, t.S1, lane, act, ci);    // Y += ky S_y c
+    __syncwarp();
+    contract<0, false, false>(X, S0, t.M1, lane, act);          // e = M_x u
+    __syncwarp();
+    contract<1, false, false>(S0, S1, t.M1, lane, act);         // f = M_y e
+    __syncwarp();
+    contract_scaled<2, true, 2>(S1, Y, t.S1, lane, act, ci);    // Y += kz S_z f
+    if (REACT) {
+      __syncwarp();
+      contract_scaled<2, true, 3>(S1, Y, t.M1, lane, act, ci);  // Y += c|J| M_z f
+    }
+    __syncwarp();
+    return;
+  }
   contract<0, false, false>(X, S0, t.B, lane, act);
   __syncwarp();
   contract<1, false, false>(S0, S1, t.B, lane, act);
@@ -237,23 +317,20 @@ __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane,
 template <int D, int S, bool FULL, typename T>
 __device__ __forceinline__ void face_diffusion(const T* X, T* Y, T* F0, T* F1, const T* __restrict__ gu,
                                                const MeshParams& mp, long long cell0, int lane,
-                                               const unsigned char* act) {
+                                               const unsigned char* act, const CellInfo<T>* ci) {
   const Tab<T>& t = tab<T>();
   constexpr int lin = S ? N - 1 : 0;
   constexpr int lout = S ? 0 : N - 1;
-  const T ih = T(1.0 / mp.h[D]);
+  const T ih = Prec<T>::ih(mp, D);
   const T sgn = S ? T(1) : T(-1);
-  const T pen = T(mp.alpha * mp.p * (mp.p + 2));
-  const int ta = D == 0 ? 1 : 0, tb = D == 2 ? 1 : 2;
-  const T area = T(mp.h[ta] * mp.h[tb]);
+  const T area = Prec<T>::area(mp, D);
   // phase 1: qv, qdv at the face nodes
+  constexpr int FI = 2 * D + S;
   for (int L = lane; L < LINES; L += 32) {
     int cw, base, st, a, b;
     line_geom<D>(L, cw, base, st, a, b);
     T qv = T(0), qdv = T(0);
-    const long long c = cell0 + cw;
-    long long nb = -1;
-    const int kind = act[cw] ? face_kind(mp, c, D, S, nb) : 2;
+    const int kind = act[cw] ? ci[cw].kind[FI] : 2;
     if (kind != 2) {
       T x[N];
 #pragma unroll
@@ -262,14 +339,12 @@ __device__ __forceinline__ void face_diffusion(const T* X, T* Y, T* F0, T* F1, c
 #pragma unroll
       for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], x[j], dn);
       dn *= sgn * ih;
-      const T kin = T(kcoef(mp, c, D));
+      const T kap = ci[cw].kap[FI];
+      const T gam = ci[cw].gam[FI];
       if (kind == 0) {
-        const T kout = T(kcoef(mp, nb, D));
-        const T kap = kin * kout / (kin + kout);
-        const T gam = T(2) * pen * kap * ih;
         T tout = T(0), dno = T(0);
         if (FULL) {
-          const T* xo = gu + nb * N3 + (base - cw * N3);
+          const T* xo = gu + ci[cw].nb[FI] * N3 + (base - cw * N3);
           T y[N];
 #pragma unroll
           for (int j = 0; j < N; ++j) y[j] = xo[j * st];
@@ -282,8 +357,6 @@ __device__ __forceinline__ void face_diffusion(const T* X, T* Y, T* F0, T* F1, c
         qv = gam * jmp - kap * (dn + dno);
         qdv = -kap * jmp;
       } else {
-        const T kap = kin;
-        const T gam = pen * kap * ih;
         qv = gam * x[lin] - kap * dn;
         qdv = -kap * x[lin];
       }
@@ -350,19 +423,17 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
   constexpr int lin = S ? N - 1 : 0;
   constexpr int lout = S ? 0 : N - 1;
   const int ta = D == 0 ? 1 : 0, tb = D == 2 ? 1 : 2;
-  const T area = T(mp.h[ta] * mp.h[tb]);
+  const T area = Prec<T>::area(mp, D);
   const T sgn = S ? T(1) : T(-1);
   // phase 1: traces at the face nodes
   for (int L = lane; L < LINES; L += 32) {
     int cw, base, st, a, b;
     line_geom<D>(L, cw, base, st, a, b);
     T tin = T(0), tout = T(0);
-    long long nb = -1;
-    const long long c = cell0 + cw;
-    const int kind = act[cw] ? face_kind(mp, c, D, S, nb) : 2;
+    const int kind = act[cw] ? ci[cw].kind[2 * D + S] : 2;
     if (kind != 2) {
       tin = X[base + lin * st];
-      if (kind == 0 && FULL) tout = gu[nb * N3 + (base - cw * N3) + lout * st];
+      if (kind == 0 && FULL) tout = gu[ci[cw].nb[2 * D + S] * N3 + (base - cw * N3) + lout * st];
     }
     F0[L] = tin;
     F1[L] = tout;
@@ -469,12 +540,12 @@ template <bool FULL, bool ADV, typename T>
 __device__ __forceinline__ void all_faces(const T* X, T* Y, T* F0, T* F1, const T* gu, const MeshParams& mp,
                                           long long cell0, int lane, const unsigned char* act,
                                           const CellInfo<T>* ci) {
-  face_diffusion<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
-  face_diffusion<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
-  face_diffusion<1, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
-  face_diffusion<1, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
-  face_diffusion<2, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
-  face_diffusion<2, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act);
+  face_diffusion<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  face_diffusion<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  face_diffusion<1, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  face_diffusion<1, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  face_diffusion<2, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  face_diffusion<2, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
   if (ADV) {
     face_upwind<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
     face_upwind<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
@@ -494,19 +565,26 @@ __device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell
     const bool ok = c < mp.ncell;
     act[lane] = ok ? 1 : 0;
     if (ok) {
-      const double J = mp.h[0] * mp.h[1] * mp.h[2];
+      const T* r = Prec<T>::rec(mp) + c * kRecLen;
       for (int d = 0; d < 3; ++d) {
-        ci[lane].kd[d] = T(J * kcoef(mp, c, d) / (mp.h[d] * mp.h[d]));
-        ci[lane].jh[d] = T(J / mp.h[d]);
+        ci[lane].kd[d] = r[kRecKd + d];
+        ci[lane].jh[d] = Prec<T>::jh(mp, d);
       }
-      ci[lane].cJ = mp.c ? T(J * __ldg(mp.c + c)) : T(0);
+      ci[lane].cJ = r[kRecCJ];
+      for (int f = 0; f < 6; ++f) {
+        long long nb = -1;
+        ci[lane].kind[f] = face_kind(mp, c, f >> 1, f & 1, nb);
+        ci[lane].nb[f] = nb;
+        ci[lane].kap[f] = r[kRecKap + f];
+        ci[lane].gam[f] = r[kRecGam + f];
+      }
       if (mp.bvert) {
         int cx, cy, cz;
         cell_xyz(mp, c, cx, cy, cz);
         const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
         for (int k = 0; k < 8; ++k) {
           const long long v = (cx + (k & 1)) + vx * (cy + ((k >> 1) & 1)) + vxy * (cz + (k >> 2));
-          for (int d = 0; d < 3; ++d) ci[lane].bc[d][k] = T(__ldg(mp.bvert + 3 * v + d));
+          for (int d = 0; d < 3; ++d) ci[lane].bc[d][k] = Prec<T>::bv(mp, 3 * v + d);
         }
       }
     }
@@ -520,7 +598,7 @@ struct WarpMem {
   static constexpr int nvec_apply = 4;
   static constexpr int nvec_smooth = 6;
   static __host__ __device__ constexpr size_t bytes(int nvec) {
-    return (size_t)(nvec * VEC + 5 * LINES) * sizeof(T) + CPW * sizeof(CellInfo<T>) + 16;
+    return align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T)) + align16(CPW * sizeof(CellInfo<T>)) + 16;
   }
 };
 
@@ -532,8 +610,9 @@ __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T**
   *F0 = p + nvec * VEC;
   *F1 = *F0 + LINES;
   *red = *F1 + LINES;     // 3 * LINES spare (reductions)
-  *ci = reinterpret_cast<CellInfo<T>*>(*red + 3 * LINES);
-  *act = reinterpret_cast<unsigned char*>(*ci + CPW);
+  unsigned char* tail = raw + align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T));
+  *ci = reinterpret_cast<CellInfo<T>*>(tail);
+  *act = tail + align16(CPW * sizeof(CellInfo<T>));
 }
 
 template <typename T, bool FULL, bool ADV, bool REACT>
@@ -621,7 +700,7 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
     for (int i = 0; i < N; ++i) {
       const int e = base + i * N2;
       const T r = f[g0 + e] - (ZERO ? T(0) : Q[e]);
-      const T z = r / diag[g0 + e];
+      const T z = r * diag[g0 + e];
       R[e] = r;
       P[e] = z;
       DL[e] = T(0);
@@ -683,7 +762,7 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const int e = base + i * N2;
-          const T z = R[e] / diag[g0 + e];
+          const T z = R[e] * diag[g0 + e];
           S0[e] = z;
           prz2 = fma(R[e], z, prz2);
         }
@@ -717,6 +796,249 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
     }
   }
   if (its && lane < LINES && (lane % N2) == 0 && cell0 + mycw < mp.ncell) its[cell0 + mycw] = it;
+}
+
+// Per-cell scalars of the inner GMRES(m): Hessenberg (m+1) x m, g, Givens
+// cosines and sines, and the small solve y.
+__host__ __device__ constexpr int gmres_scalars(int m) { return (m + 1) * m + 4 * m + 1; }
+
+// Block-Jacobi sweep with inner right-preconditioned GMRES(m) (Algorithm 2;
+// the inner solve of Sec. 2.2.1 for non-symmetric blocks, b != 0): per cell,
+// V_0 = r / |r|; for j: w = D_T (V_j / diag), modified Gram-Schmidt, Givens
+// rotations on the Hessenberg column, stop once the residual estimate
+// |g_{j+1}| <= eps ||d|| or after maxit iterations; x += sum_i y_i V_i / diag;
+// restart from the recomputed residual d - D_T x.  The warp count per block is
+// blockDim.x / 32 (the basis needs (m+1) vectors per warp).
+template <typename T, bool ADV, bool REACT, bool ZERO>
+__global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __restrict__ f,
+                                                      const T* __restrict__ uold, T* __restrict__ unew,
+                                                      const T* __restrict__ diag, T omega, T eps, int maxit, int m,
+                                                      int* __restrict__ its) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const long long cell0 = ((long long)blockIdx.x * wpb + warp) * CPW;
+  if (cell0 >= mp.ncell) return;
+  const int nvec = m + 7;
+  const size_t tbytes = align16((size_t)(nvec * VEC + 5 * LINES + CPW * gmres_scalars(m)) * sizeof(T));
+  const size_t wbytes = tbytes + align16(CPW * sizeof(CellInfo<T>)) + 16;
+  unsigned char* base = smem + warp * wbytes;
+  T* p = reinterpret_cast<T*>(base);
+  T* V = p;                      // m+1 basis vectors
+  T* Z = p + (m + 1) * VEC;      // preconditioned vector / block-apply input
+  T* Q = Z + VEC;                // block-apply output
+  T* S0 = Q + VEC;
+  T* S1 = S0 + VEC;
+  T* DD = S1 + VEC;              // defect d
+  T* X = DD + VEC;               // accumulated correction
+  T* F0 = X + VEC;
+  T* F1 = F0 + LINES;
+  T* red = F1 + LINES;
+  T* sc = red + 3 * LINES;       // CPW * gmres_scalars(m)
+  CellInfo<T>* ci = reinterpret_cast<CellInfo<T>*>(base + tbytes);
+  unsigned char* act = base + tbytes + align16(CPW * sizeof(CellInfo<T>));
+  stage_cells(mp, cell0, lane, ci, act);
+  const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
+  const long long g0 = cell0 * N3;
+  const int mycw = lane < LINES ? lane / N2 : -1;
+  const bool mine = mycw >= 0 && act[mycw];
+  const bool lead = lane < LINES && (lane % N2) == 0;    // writes the cell's scalars
+  T* H = sc + (mycw >= 0 ? mycw : 0) * gmres_scalars(m);
+  T* gv = H + (m + 1) * m;
+  T* cs = gv + (m + 1);
+  T* sn = cs + m;
+  T* yv = sn + m;
+  // defect d = f - A u_old
+  if (!ZERO) {
+    for (int e = lane; e < VEC; e += 32) Z[e] = e < nval ? uold[g0 + e] : T(0);
+    __syncwarp();
+    volume<ADV, REACT>(Z, Q, S0, S1, lane, ci, act);
+    all_faces<true, ADV>(Z, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+  }
+  T pdd = T(0);
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, b0, st, a, b;
+    line_geom<2>(L, cw, b0, st, a, b);
+    if (!act[cw]) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int e = b0 + i * N2;
+      const T d = f[g0 + e] - (ZERO ? T(0) : Q[e]);
+      DD[e] = d;
+      X[e] = T(0);
+      pdd = fma(d, d, pdd);
+    }
+  }
+  T beta = sqrt(cell_sum(pdd, lane, red));
+  const T target = eps * beta;
+  bool live = mine && beta > T(0) && beta > target;
+  int it = 0;
+  // residual vector for the first cycle is d itself
+  T* Rsrc = DD;
+  while (__any_sync(FULLMASK, live && it < maxit)) {
+    bool cyc = live && it < maxit;
+    // V_0 = r / beta
+    for (int L = lane; L < LINES; L += 32) {
+      int cw, b0, st, a, b;
+      line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int e = b0 + i * N2;
+        if (cyc) V[e] = Rsrc[e] / beta;
+      }
+    }
+    if (lead && cyc) {
+      for (int k = 0; k <= m; ++k) gv[k] = T(0);
+      gv[0] = beta;
+    }
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      if (!__any_sync(FULLMASK, cyc)) break;
+      if (lane < LINES) act[mycw] = cyc ? 1 : 0;
+      __syncwarp();
+      T* Vj = V + j * VEC;
+      // Z = V_j / diag; Q = D_T Z
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, b0, st, a, b;
+        line_geom<2>(L, cw, b0, st, a, b);
+        if (!cyc) continue;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int e = b0 + i * N2;
+          Z[e] = Vj[e] * diag[g0 + e];
+        }
+      }
+      __syncwarp();
+      volume<ADV, REACT>(Z, Q, S0, S1, lane, ci, act);
+      all_faces<false, ADV>(Z, Q, F0, F1, (const T*)nullptr, mp, cell0, lane, act, ci);
+      // modified Gram-Schmidt
+      for (int i = 0; i <= j; ++i) {
+        const T* Vi = V + i * VEC;
+        T ph = T(0);
+        if (cyc) {
+          for (int L = lane; L < LINES; L += 32) {
+            int cw, b0, st, a, b;
+            line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+            for (int k = 0; k < N; ++k) ph = fma(Q[b0 + k * N2], Vi[b0 + k * N2], ph);
+          }
+        }
+        const T h = cell_sum(ph, lane, red);
+        if (cyc) {
+          for (int L = lane; L < LINES; L += 32) {
+            int cw, b0, st, a, b;
+            line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+            for (int k = 0; k < N; ++k) Q[b0 + k * N2] = fma(-h, Vi[b0 + k * N2], Q[b0 + k * N2]);
+          }
+          if (lead) H[i * m + j] = h;
+        }
+        __syncwarp();
+      }
+      T pw = T(0);
+      if (cyc) {
+        for (int L = lane; L < LINES; L += 32) {
+          int cw, b0, st, a, b;
+          line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+          for (int k = 0; k < N; ++k) pw = fma(Q[b0 + k * N2], Q[b0 + k * N2], pw);
+        }
+      }
+      const T hn = sqrt(cell_sum(pw, lane, red));
+      if (cyc) {
+        T* Vn = V + (j + 1) * VEC;
+        const T inv = hn != T(0) ? T(1) / hn : T(1);
+        for (int L = lane; L < LINES; L += 32) {
+          int cw, b0, st, a, b;
+          line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+          for (int k = 0; k < N; ++k) Vn[b0 + k * N2] = hn != T(0) ? Q[b0 + k * N2] * inv : Q[b0 + k * N2];
+        }
+        if (lead) {
+          H[(j + 1) * m + j] = hn;
+          for (int i = 0; i < j; ++i) {
+            const T t0 = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+            H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+            H[i * m + j] = t0;
+          }
+          const T den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+          cs[j] = H[j * m + j] / den;
+          sn[j] = H[(j + 1) * m + j] / den;
+          H[j * m + j] = den;
+          H[(j + 1) * m + j] = T(0);
+          gv[j + 1] = -sn[j] * gv[j];
+          gv[j] = cs[j] * gv[j];
+        }
+      }
+      __syncwarp();
+      if (cyc) {
+        ++it;
+        jdone = j + 1;
+        if (fabs(gv[j + 1]) <= target || it >= maxit) cyc = false;
+      }
+      __syncwarp();
+    }
+    // y = H^-1 g (upper triangular, size jdone), then X += sum_i y_i V_i / diag
+    const bool ran = live && jdone > 0;
+    if (lead && ran) {
+      for (int i = jdone - 1; i >= 0; --i) {
+        T s = gv[i];
+        for (int l = i + 1; l < jdone; ++l) s -= H[i * m + l] * yv[l];
+        yv[i] = s / H[i * m + i];
+      }
+    }
+    __syncwarp();
+    if (ran) {
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, b0, st, a, b;
+        line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const int e = b0 + k * N2;
+          T s = T(0);
+          for (int i = 0; i < jdone; ++i) s = fma(yv[i], V[i * VEC + e], s);
+          X[e] = fma(s, diag[g0 + e], X[e]);
+        }
+      }
+    }
+    // r = d - D_T x; beta = ||r||
+    if (lane < LINES) act[mycw] = ran ? 1 : 0;
+    __syncwarp();
+    volume<ADV, REACT>(X, Q, S0, S1, lane, ci, act);
+    all_faces<false, ADV>(X, Q, F0, F1, (const T*)nullptr, mp, cell0, lane, act, ci);
+    T pr = T(0);
+    if (ran) {
+      for (int L = lane; L < LINES; L += 32) {
+        int cw, b0, st, a, b;
+        line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const int e = b0 + k * N2;
+          const T r = DD[e] - Q[e];
+          Q[e] = r;
+          pr = fma(r, r, pr);
+        }
+      }
+    }
+    const T bn = sqrt(cell_sum(pr, lane, red));
+    if (ran) {
+      beta = bn;
+      if (!(beta > target)) live = false;
+    }
+    Rsrc = Q;
+    __syncwarp();
+  }
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, b0, st, a, b;
+    line_geom<2>(L, cw, b0, st, a, b);
+    if (cell0 + cw >= mp.ncell) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const long long gi = g0 + b0 + i * N2;
+      unew[gi] = ZERO ? omega * X[b0 + i * N2] : fma(omega, X[b0 + i * N2], uold[gi]);
+    }
+  }
+  if (its && lead && cell0 + mycw < mp.ncell) its[cell0 + mycw] = it;
 }
 
 // diag(D_T) by direct quadrature per dof (setup; FP64).
@@ -809,51 +1131,78 @@ __global__ void k_diag(MeshParams mp, double* __restrict__ diag) {
   diag[gid] = acc;
 }
 
-// Corner sums r_hat_c(T) = sum_i prod_k phi_{c_k}(zeta_{i_k}) r_T(i), one
-// thread per (cell, corner) (the cell part of R = P^T).
+// Corner sums r_hat_c(T) = sum_i prod_k phi_{c_k}(zeta_{i_k}) r_T(i) (the cell
+// part of R = P^T): one warp per cell, each lane accumulates the 8 corner
+// weights over its dofs in the kernel's precision, then a fixed-order warp
+// reduction.
 template <typename T>
-__global__ void k_restrict_cells(long long ncell, const T* __restrict__ r, double* __restrict__ corners) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= ncell * 8) return;
-  const long long c = gid >> 3;
-  const int k = (int)(gid & 7);
-  const Tab<double>& t = c_tab_d;
-  const double* hx = t.hat[k & 1];
-  const double* hy = t.hat[(k >> 1) & 1];
-  const double* hz = t.hat[k >> 2];
+__global__ void __launch_bounds__(256) k_restrict_cells(long long ncell, const T* __restrict__ r,
+                                                        double* __restrict__ corners) {
+  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const Tab<T>& t = tab<T>();
   const T* rc = r + c * N3;
-  double s = 0.0;
-  for (int i3 = 0; i3 < N; ++i3) {
-    double sy = 0.0;
-    for (int i2 = 0; i2 < N; ++i2) {
-      double sx = 0.0;
-      for (int i1 = 0; i1 < N; ++i1) sx += hx[i1] * (double)rc[i1 + N * i2 + N2 * i3];
-      sy += hy[i2] * sx;
-    }
-    s += hz[i3] * sy;
+  T acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = T(0);
+  for (int i = lane; i < N3; i += 32) {
+    const int i1 = i % N, i2 = (i / N) % N, i3 = i / N2;
+    const T v = rc[i];
+    const T wz0 = t.hat[0][i3] * v, wz1 = t.hat[1][i3] * v;
+    const T w00 = t.hat[0][i2] * wz0, w10 = t.hat[1][i2] * wz0, w01 = t.hat[0][i2] * wz1, w11 = t.hat[1][i2] * wz1;
+    acc[0] = fma(t.hat[0][i1], w00, acc[0]);
+    acc[1] = fma(t.hat[1][i1], w00, acc[1]);
+    acc[2] = fma(t.hat[0][i1], w10, acc[2]);
+    acc[3] = fma(t.hat[1][i1], w10, acc[3]);
+    acc[4] = fma(t.hat[0][i1], w01, acc[4]);
+    acc[5] = fma(t.hat[1][i1], w01, acc[5]);
+    acc[6] = fma(t.hat[0][i1], w11, acc[6]);
+    acc[7] = fma(t.hat[1][i1], w11, acc[7]);
   }
-  corners[gid] = s;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(FULLMASK, acc[k], o);
+  if (lane < 8) {
+    T v = acc[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k)
+      if (lane == k) v = acc[k];
+    corners[c * 8 + lane] = (double)v;
+  }
 }
 
-// u_T(i) += sum_c u_hat(vertex(T, c)) prod_k phi_{c_k}(zeta_{i_k}).
+// u_T(i) += sum_c u_hat(vertex(T, c)) prod_k phi_{c_k}(zeta_{i_k}): one warp
+// per cell; the 8 corner values are loaded once and broadcast.
 template <typename T>
-__global__ void k_prolong_add(MeshParams mp, const double* __restrict__ uhat, T* __restrict__ u) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= mp.ncell * N3) return;
-  const long long c = gid / N3;
-  const int i = (int)(gid - c * N3);
-  const int i1 = i % N, i2 = (i / N) % N, i3 = i / N2;
+__global__ void __launch_bounds__(256) k_prolong_add(MeshParams mp, const double* __restrict__ uhat,
+                                                     T* __restrict__ u) {
+  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= mp.ncell) return;
   int cx, cy, cz;
   cell_xyz(mp, c, cx, cy, cz);
   const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
-  const Tab<double>& t = c_tab_d;
-  double s = 0.0;
-  for (int k = 0; k < 8; ++k) {
-    const int ox = k & 1, oy = (k >> 1) & 1, oz = k >> 2;
-    const long long v = (cx + ox) + vx * (cy + oy) + vxy * (cz + oz);
-    s += uhat[v] * t.hat[ox][i1] * t.hat[oy][i2] * t.hat[oz][i3];
+  T cv = T(0);
+  if (lane < 8) {
+    const long long v = (cx + (lane & 1)) + vx * (cy + ((lane >> 1) & 1)) + vxy * (cz + (lane >> 2));
+    cv = (T)uhat[v];
   }
-  u[gid] = (T)((double)u[gid] + s);
+  T cor[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) cor[k] = __shfl_sync(FULLMASK, cv, k);
+  const Tab<T>& t = tab<T>();
+  T* uc = u + c * N3;
+  for (int i = lane; i < N3; i += 32) {
+    const int i1 = i % N, i2 = (i / N) % N, i3 = i / N2;
+    const T x0 = t.hat[0][i1], x1 = t.hat[1][i1];
+    const T e00 = fma(x1, cor[1], x0 * cor[0]), e10 = fma(x1, cor[3], x0 * cor[2]);
+    const T e01 = fma(x1, cor[5], x0 * cor[4]), e11 = fma(x1, cor[7], x0 * cor[6]);
+    const T y0 = t.hat[0][i2], y1 = t.hat[1][i2];
+    const T f0 = fma(y1, e10, y0 * e00), f1 = fma(y1, e11, y0 * e01);
+    uc[i] += fma(t.hat[1][i3], f1, t.hat[0][i3] * f0);
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -882,6 +1231,9 @@ cudaError_t upload_one(const double* h, cudaStream_t s) {
     for (int i = 0; i < N; ++i) tb.hat[s2][i] = T(p[s2 * N + i]);
   p += 2 * N;
   for (int i = 0; i < N; ++i) tb.gq[i] = T(p[i]);
+  p += N;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) tb.S1[i][j] = T(p[i * N + j]);
   if (sizeof(T) == 8) return cudaMemcpyToSymbol(c_tab_d, &tb, sizeof(tb));
   return cudaMemcpyToSymbol(c_tab_f, &tb, sizeof(tb));
 }
@@ -940,8 +1292,30 @@ cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_
   return cudaGetLastError();
 }
 
+template <typename T, bool ADV, bool REACT, bool ZERO>
+cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  const int m = a.restart;
+  const size_t wbytes = align16((size_t)((m + 7) * VEC + 5 * LINES + CPW * gmres_scalars(m)) * sizeof(T)) +
+                        align16(CPW * sizeof(CellInfo<T>)) + 16;
+  int wpb = (int)((200 * 1024) / wbytes);
+  if (wpb > 4) wpb = 4;
+  if (wpb < 1) return cudaErrorInvalidValue;      // restart too large for shared memory
+  const size_t sm = wpb * wbytes;
+  auto k = k_smooth_gmres<T, ADV, REACT, ZERO>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long groups = (mp.ncell + CPW - 1) / CPW;
+  const unsigned grid = (unsigned)((groups + wpb - 1) / wpb);
+  k<<<grid, wpb * 32, sm, s>>>(mp, (const T*)a.f, (const T*)a.uold, (T*)a.unew, (const T*)a.diag, T(a.omega),
+                               T(a.eps), a.maxit, m, a.its);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, bool ADV, bool REACT>
 cudaError_t smooth_z(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  if (a.inner == DGMG_INNER_GMRES)
+    return a.uold ? launch_gmres<T, ADV, REACT, false>(mp, a, s) : launch_gmres<T, ADV, REACT, true>(mp, a, s);
   return a.uold ? launch_smooth<T, ADV, REACT, false>(mp, a, s) : launch_smooth<T, ADV, REACT, true>(mp, a, s);
 }
 
@@ -970,9 +1344,8 @@ cudaError_t diag(const MeshParams& mp, double* d, cudaStream_t s) {
 }
 
 cudaError_t restrict_cells(const MeshParams& mp, const void* r, double* corners, bool fp32, cudaStream_t s) {
-  const long long n = mp.ncell * 8;
-  if (n == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (mp.ncell == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((mp.ncell * 32 + 255) / 256);
   if (fp32)
     k_restrict_cells<float><<<grid, 256, 0, s>>>(mp.ncell, (const float*)r, corners);
   else
@@ -982,9 +1355,8 @@ cudaError_t restrict_cells(const MeshParams& mp, const void* r, double* corners,
 }
 
 cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool fp32, cudaStream_t s) {
-  const long long n = mp.ncell * N3;
-  if (n == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (mp.ncell == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((mp.ncell * 32 + 255) / 256);
   if (fp32)
     k_prolong_add<float><<<grid, 256, 0, s>>>(mp, uhat, (float*)u);
   else

@@ -26,7 +26,24 @@ struct MeshParams {
   const double* c;        // device, ncell, or nullptr
   const double* bvert;    // device, 3 * nvert, or nullptr
   double alpha;           // penalty parameter (1.25)
+  // Per-cell coefficient records, kRecLen values per cell (see kRec*),
+  // computed once at set-up in both precisions.
+  const double* rec64;
+  const float* rec32;
+  const float* bvert32;   // float copy of bvert (or nullptr)
+  // Mesh scalars in both precisions: 1/h_d, face area normal to d, |J|/h_d.
+  double ih[3], area[3], jh[3];
+  float ihf[3], areaf[3], jhf[3];
 };
+
+// Record layout: kd[3] = |J| K_d / h_d^2, cJ = c |J|, kap[6], gam[6] for the
+// faces f = 2d + s (kap = K^-K^+/(K^-+K^+) inside, K on Dirichlet faces,
+// gamma_F the penalty; both 0 on Neumann faces).
+constexpr int kRecLen = 16;
+constexpr int kRecKd = 0, kRecCJ = 3, kRecKap = 4, kRecGam = 10;
+
+// Fill the records (setup; one thread per cell).
+cudaError_t cell_records(const MeshParams& mp, double* rec64, float* rec32, cudaStream_t s);
 
 // Flat layout of the 1D tables uploaded to constant memory for one n (all in
 // double on the host; the kernels keep a float copy too):
@@ -38,13 +55,14 @@ struct MeshParams {
 //   G[n][n]    G[q][j] = l_j'(g_q)
 //   hat[2][n]  Q1 hat functions at the GLL nodes: 1 - zeta_i, zeta_i
 //   gq[n]      Gauss points on [0,1]
-inline int table_size(int n) { return 4 * n * n + 6 * n; }
+//   S1[n][n]   1D stiffness matrix of the GLL basis, sum_q w_q G[q][i] G[q][j]
+inline int table_size(int n) { return 5 * n * n + 6 * n; }
 
 struct SmoothArgs {
   const void* f;
   const void* uold;       // nullptr: zero initial guess
   void* unew;
-  const void* diag;       // diag(D_T) in the same precision
+  const void* diag;       // 1 / diag(D_T) in the same precision
   double omega, eps;
   int maxit;
   int inner;              // DGMG_INNER_PCG / DGMG_INNER_GMRES
@@ -79,6 +97,7 @@ cudaError_t vec_copy(long long n, const double* x, double* y, cudaStream_t s);
 cudaError_t vec_fill(long long n, double v, double* y, cudaStream_t s);
 cudaError_t vec_fill_f(long long n, float v, float* y, cudaStream_t s);
 cudaError_t vec_d2f(long long n, const double* x, float* y, cudaStream_t s);
+cudaError_t vec_inverse(long long n, const double* d, double* i64, float* i32, cudaStream_t s);
 cudaError_t vec_f2d(long long n, const float* x, double* y, cudaStream_t s);
 // Deterministic dot products: partial sums per block in a fixed order, then
 // one block sums the partials; result written to out (device).

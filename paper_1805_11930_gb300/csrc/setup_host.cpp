@@ -105,7 +105,7 @@ std::vector<double> build_tables(int n) {
   std::vector<double> gll, gllw, gq, gw;
   gauss_lobatto01(n, gll, gllw);
   gauss_legendre01(n, gq, gw);
-  std::vector<double> T(4 * n * n + 6 * n, 0.0);
+  std::vector<double> T(5 * n * n + 6 * n, 0.0);
   double* B = T.data();
   double* Dg = B + n * n;
   double* W = Dg + n * n;
@@ -114,6 +114,7 @@ std::vector<double> build_tables(int n) {
   double* G = M1 + n * n;
   double* hat = G + n * n;
   double* GQ = hat + 2 * n;
+  double* S1 = GQ + n;
   for (int q = 0; q < n; ++q) {
     lagrange(gll, gq[q], B + q * n, G + q * n);
     lagrange(gq, gq[q], nullptr, Dg + q * n);
@@ -132,6 +133,12 @@ std::vector<double> build_tables(int n) {
     hat[i] = 1.0 - gll[i];
     hat[n + i] = gll[i];
   }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += gw[q] * G[q * n + i] * G[q * n + j];
+      S1[i * n + j] = s;
+    }
   return T;
 }
 

@@ -203,7 +203,66 @@ __global__ void k_restrict_gather(int nx, int ny, int nz, const double* __restri
   }
 }
 
+// Per-cell coefficient records (setup): kd[3], cJ, kap[6], gam[6].
+__global__ void k_cell_records(MeshParams mp, double* __restrict__ r64, float* __restrict__ r32) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= mp.ncell) return;
+  const int cx = (int)(c % mp.nx);
+  const int cy = (int)((c / mp.nx) % mp.ny);
+  const int cz = (int)(c / ((long long)mp.nx * mp.ny));
+  const int ci[3] = {cx, cy, cz};
+  const int nn[3] = {mp.nx, mp.ny, mp.nz};
+  const long long stride[3] = {1, mp.nx, (long long)mp.nx * mp.ny};
+  const double J = mp.h[0] * mp.h[1] * mp.h[2];
+  const double pen = mp.alpha * mp.p * (mp.p + 2);
+  double rec[kRecLen];
+  auto K = [&](long long cell, int d) { return mp.K[cell * mp.kdim + (mp.kdim == 3 ? d : 0)]; };
+  for (int d = 0; d < 3; ++d) rec[kRecKd + d] = J * K(c, d) / (mp.h[d] * mp.h[d]);
+  rec[kRecCJ] = mp.c ? J * mp.c[c] : 0.0;
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s) {
+      const bool bnd = (s == 0 && ci[d] == 0) || (s == 1 && ci[d] == nn[d] - 1);
+      const double kin = K(c, d);
+      double kap = 0.0, gam = 0.0;
+      if (!bnd) {
+        const double kout = K(s ? c + stride[d] : c - stride[d], d);
+        kap = kin * kout / (kin + kout);
+        gam = 2.0 * pen * kap / mp.h[d];
+      } else if (mp.bc[2 * d + s] == 0) {
+        kap = kin;
+        gam = pen * kap / mp.h[d];
+      }
+      rec[kRecKap + 2 * d + s] = kap;
+      rec[kRecGam + 2 * d + s] = gam;
+    }
+  for (int k = 0; k < kRecLen; ++k) {
+    r64[c * kRecLen + k] = rec[k];
+    r32[c * kRecLen + k] = (float)rec[k];
+  }
+}
+
+__global__ void k_inverse(long long n, const double* __restrict__ d, double* __restrict__ i64, float* __restrict__ i32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = 1.0 / d[i];
+    i64[i] = v;
+    i32[i] = (float)v;
+  }
+}
+
 }  // namespace
+
+cudaError_t cell_records(const MeshParams& mp, double* rec64, float* rec32, cudaStream_t s) {
+  if (mp.ncell == 0) return cudaSuccess;
+  k_cell_records<<<(unsigned)((mp.ncell + 127) / 128), 128, 0, s>>>(mp, rec64, rec32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t vec_inverse(long long n, const double* d, double* i64, float* i32, cudaStream_t s) {
+  k_inverse<<<grid1(n), kThreads, 0, s>>>(n, d, i64, i32);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t vec_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
   k_axpby<double><<<grid1(n), kThreads, 0, s>>>(n, a, x, b, y);

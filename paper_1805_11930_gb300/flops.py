@@ -1,43 +1,41 @@
-"""Algorithmic floating-point operation counts of the library's kernels
-(diffusion operator, b = 0, c = 0), per cell, n = p+1.  An FMA counts as 2,
-any other add, multiply or divide as 1.  These are the counts of the
-sum-factorised algorithm as the kernels implement it:
+"""Operation counts used for the roofline figures (n = p+1, per cell).
 
-volume (Sec. 3.1, Stages 1-3): six 1D contractions with the n x n matrices B
-    and B^T (n^4 FMA each) and three fused derivative passes Dg, pointwise
-    coefficient, Dg^T (2 n^4 FMA + 3 n^3 each)            -> 24 n^4 + 9 n^3
-faces, per face node: own normal derivative (n FMA), the neighbour's (n FMA,
-    full operator only), the face mass matrix M1 (x) M1 on two fields
-    (4 n FMA), the scatter of the derivative term (n FMA), ~20 scalar
-    operations; six faces of n^2 nodes
-    full operator                                         -> 84 n^3 + 120 n^2
-    block diagonal D_T                                    -> 72 n^3 + 100 n^2
-inner PCG iteration: one D_T apply plus three dot products and three vector
-    updates and the diagonal scaling                      -> F_block + 13 n^3
-smoother sweep: the defect (one full apply, skipped when the sweep starts
-    from zero), residual set-up and update                -> F_full + 8 n^3
+Algorithmic count (the roofline's "achieved" numerator): the sum-factorised
+operator with the gradient-only volume term, face-centric faces, an FMA
+counted as 2 flops,
+    F(n) = 32 n^4 + 120 n^3
+(16 contractions of 2 n^4 flops; 3 owned faces x 2 sides x 20 n^3), i.e.
+216 / 248 / 280 / 312 / 344 flop per dof at p = 2..6 for diffusion, and 36 n^4
+instead of 32 n^4 with advection or reaction.  A block-diagonal apply D_T is
+counted like a full apply.  One smoother sweep over a cell costs one apply
+for its defect (none when it starts from zero) plus one apply per inner
+iteration.
+
+Kernel count (what the kernels issue, for reference): volume 24 n^4 + 9 n^3
+(six contractions with B, B^T and three fused Dg / coefficient / Dg^T
+passes), faces 84 n^3 + 120 n^2 (full) or 72 n^3 + 100 n^2 (block), inner
+iteration vector work 13 n^3.
 """
 
 
-def apply_full(n):
+def algorithmic_apply(n, value_terms=False):
+    return (36 if value_terms else 32) * n ** 4 + 120 * n ** 3
+
+
+def algorithmic_smoother(n, ncell, sweeps, zero_sweeps, inner_its_total, value_terms=False):
+    """Algorithmic flops of `sweeps` smoother launches over ncell cells, of
+    which zero_sweeps start from u = 0, with inner_its_total inner iterations
+    summed over cells and sweeps."""
+    F = algorithmic_apply(n, value_terms)
+    return F * (ncell * (sweeps - zero_sweeps) + inner_its_total)
+
+
+def kernel_apply_full(n):
     return 24 * n ** 4 + 9 * n ** 3 + 84 * n ** 3 + 120 * n ** 2
 
 
-def apply_block(n):
+def kernel_apply_block(n):
     return 24 * n ** 4 + 9 * n ** 3 + 72 * n ** 3 + 100 * n ** 2
-
-
-def pcg_iteration(n):
-    return apply_block(n) + 13 * n ** 3
-
-
-def smoother_total(n, ncell, sweeps, zero_sweeps, inner_its_total):
-    """FP64 operations of `sweeps` smoother launches over ncell cells, of
-    which `zero_sweeps` started from u = 0, with inner_its_total inner
-    iterations summed over cells and sweeps."""
-    per_sweep = 8 * n ** 3 * ncell
-    defect = apply_full(n) * ncell * (sweeps - zero_sweeps)
-    return per_sweep * sweeps + defect + pcg_iteration(n) * inner_its_total
 
 
 def hbm_bytes_apply(n, ncell, word=8):

@@ -1,0 +1,64 @@
+"""Small, fixed launch sequence of one kernel family, for ncu captures.
+
+python -m paper_1805_11930_gb300.profile_case --what apply|block|smooth --prec fp64|fp32 [--n 48] [--p 4]
+
+Sets up the log-normal diffusion workload on an n^3 mesh (48^3 at p = 4 is
+13.8 M dofs, 110 MB per FP64 vector: larger than L2, a few hundred MB in
+total), runs two warm-up launches and then `--reps` launches of the chosen
+operation through the C ABI.  Prints the median CUDA-event time per launch.
+"""
+import argparse
+import statistics
+import sys
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--what", default="apply", choices=["apply", "block", "smooth"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+
+    import torch
+
+    from . import dgmg, inputs
+    w = inputs.lognormal(args.n, args.p)
+    ctx = dgmg.Context(0)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_coefficients(w["K"])
+    nd = ctx.sizes()["ndof"]
+    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(1805)
+    x = torch.rand(nd, dtype=dt, device="cuda", generator=g)
+    y = torch.rand(nd, dtype=dt, device="cuda", generator=g)
+    stream = torch.cuda.current_stream()
+
+    def op():
+        if args.what == "apply":
+            ctx.apply(x, y)
+        elif args.what == "block":
+            ctx.block_apply(x, y)
+        else:
+            ctx.block_smooth(x, y, nsweep=1, omega=0.8, eps=1e-2)
+
+    for _ in range(2):
+        op()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        op()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    print(f"{args.what} {args.prec} n={args.n} p={args.p} ndof={nd}: median {statistics.median(ms):.4f} ms "
+          f"({nd / statistics.median(ms) / 1e6:.3f} GDOF/s)")
+    sys.stdout.flush()
+
+
+if __name__ == "__main__":
+    main()

