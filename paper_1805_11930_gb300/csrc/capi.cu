@@ -15,7 +15,7 @@
 #include "setup_host.h"
 
 namespace dgmg {
-unsigned long long g_launches = 0;
+thread_local unsigned long long t_launches = 0;
 
 const CellOps* cell_ops_n2();
 const CellOps* cell_ops_n3();
@@ -166,17 +166,19 @@ template <typename T>
 dgmg_status dalloc(dgmg_ctx* ctx, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  // Stream-ordered allocation: no device-wide synchronisation, so contexts
+  // on other streams (concurrent solves) keep running.
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(ctx, DGMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return fail(ctx, DGMG_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   }
   ctx->mesh_allocs.push_back((void*)*p);
   return DGMG_OK;
 }
 
 void free_mesh(dgmg_ctx* ctx) {
-  for (void* q : ctx->mesh_allocs) cudaFree(q);
+  for (void* q : ctx->mesh_allocs) cudaFreeAsync(q, ctx->stream);
   ctx->mesh_allocs.clear();
   ctx->dK = ctx->dc = ctx->db = ctx->diag64 = ctx->dinv64 = ctx->rec64 = nullptr;
   ctx->diag32 = ctx->dinv32 = ctx->rec32 = ctx->db32 = nullptr;
@@ -411,7 +413,7 @@ dgmg_status ensure_krylov(dgmg_ctx* ctx, size_t nvec) {
         ctx->mesh_allocs.erase(it);
         break;
       }
-    cudaFree(ctx->kry);
+    cudaFreeAsync(ctx->kry, ctx->stream);
     ctx->kry = nullptr;
     ctx->kry_vecs = 0;
   }
@@ -643,6 +645,8 @@ dgmg_status dgmg_destroy(dgmg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   free_mesh(ctx);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   cudaFree(ctx->dot_partial);
   cudaFree(ctx->dot_out);
@@ -713,16 +717,16 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   ctx->hc.assign(c_cell ? c_cell : K, c_cell ? c_cell + ctx->ncell : K);
   const long long n = ctx->ndof;
   CS(dalloc(ctx, &ctx->dK, nK));
-  CK(cudaMemcpy(ctx->dK, K, nK * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(ctx->dK, K, nK * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   if (b_vertex) {
     CS(dalloc(ctx, &ctx->db, 3 * ctx->nvert));
-    CK(cudaMemcpy(ctx->db, b_vertex, 3 * ctx->nvert * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(ctx->db, b_vertex, 3 * ctx->nvert * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CS(dalloc(ctx, &ctx->db32, 3 * ctx->nvert));
     CK(vec_d2f(3 * ctx->nvert, ctx->db, ctx->db32, ctx->stream));
   }
   if (c_cell) {
     CS(dalloc(ctx, &ctx->dc, ctx->ncell));
-    CK(cudaMemcpy(ctx->dc, c_cell, ctx->ncell * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(ctx->dc, c_cell, ctx->ncell * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   }
   CS(dalloc(ctx, &ctx->diag64, n));
   CS(dalloc(ctx, &ctx->diag32, n));
@@ -760,8 +764,8 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
       for (long long i = 0; i < L.n; ++i) dinv[i] = 1.0 / st[27 * i + 13];
       CS(dalloc(ctx, &L.st, 27 * L.n));
       CS(dalloc(ctx, &L.dinv, L.n));
-      CK(cudaMemcpy(L.st, st.data(), 27 * L.n * sizeof(double), cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(L.dinv, dinv.data(), L.n * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpyAsync(L.st, st.data(), 27 * L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(L.dinv, dinv.data(), L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
       CS(dalloc(ctx, &L.xt, L.n));
       CS(dalloc(ctx, &L.r, L.n));
     }
@@ -773,7 +777,8 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
       if (!dense_inverse((int)L.n, A)) return fail(ctx, DGMG_ERR_ARG, "coarse matrix is singular");
       ctx->coarse_n = (int)L.n;
       CS(dalloc(ctx, &ctx->coarse_inv, A.size()));
-      CK(cudaMemcpy(ctx->coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpyAsync(ctx->coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         ctx->stream));
       break;
     }
     int cx, cy, cz;
@@ -915,7 +920,7 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   ctx->ev_smooth.clear();
   ctx->ev_apply.clear();
   ctx->n_apply = ctx->n_sweep = ctx->n_zero_sweep = 0;
-  const unsigned long long launches0 = g_launches;
+  const unsigned long long launches0 = t_launches;
   if (ctx->track_its) {
     CK(cudaMemsetAsync(ctx->itsum, 0, sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->itmax, 0, sizeof(int), ctx->stream));
@@ -925,7 +930,7 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, cudaGetErrorString(e));
   st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  st.kernel_launches = (long long)(g_launches - launches0);
+  st.kernel_launches = (long long)(t_launches - launches0);
   st.sweeps = ctx->n_sweep;
   st.zero_sweeps = ctx->n_zero_sweep;
   st.applies = ctx->n_apply;
@@ -940,8 +945,9 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   if (stats) {
     unsigned long long sum = 0;
     int mx = 0;
-    cudaMemcpy(&sum, ctx->itsum, sizeof(sum), cudaMemcpyDeviceToHost);
-    cudaMemcpy(&mx, ctx->itmax, sizeof(mx), cudaMemcpyDeviceToHost);
+    cudaMemcpyAsync(&sum, ctx->itsum, sizeof(sum), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(&mx, ctx->itmax, sizeof(mx), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     const long long sw = ctx->sweeps_tracked;
     st.inner_mean = sw > 0 ? (double)sum / ((double)ctx->ncell * sw) : 0.0;
     st.inner_its_total = (long long)sum;

@@ -312,73 +312,74 @@ __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane,
   __syncwarp();
 }
 
-// Diffusion and penalty terms of face (D, S) of every active cell, added to Y.
-// FULL: neighbour trace read from gu (global); otherwise it is zero (D_T).
-template <int D, int S, bool FULL, typename T>
-__device__ __forceinline__ void face_diffusion(const T* X, T* Y, T* F0, T* F1, const T* __restrict__ gu,
-                                               const MeshParams& mp, long long cell0, int lane,
-                                               const unsigned char* act, const CellInfo<T>* ci) {
+// Diffusion and penalty terms of both faces normal to axis D (s = 0, 1) of
+// every active cell, added to Y.  The lines along D give both faces' node
+// grids, so each own line is loaded once for the two faces.  F points to
+// 4 * LINES scratch values (qv, qdv of face 0, then of face 1).
+template <int D, bool FULL, typename T>
+__device__ __forceinline__ void faces_diffusion_dir(const T* X, T* Y, T* F, const T* __restrict__ gu,
+                                                    const MeshParams& mp, int lane, const unsigned char* act,
+                                                    const CellInfo<T>* ci) {
   const Tab<T>& t = tab<T>();
-  constexpr int lin = S ? N - 1 : 0;
-  constexpr int lout = S ? 0 : N - 1;
   const T ih = Prec<T>::ih(mp, D);
-  const T sgn = S ? T(1) : T(-1);
   const T area = Prec<T>::area(mp, D);
-  // phase 1: qv, qdv at the face nodes
-  constexpr int FI = 2 * D + S;
+  // phase 1: qv, qdv of both faces at the face nodes
   for (int L = lane; L < LINES; L += 32) {
     int cw, base, st, a, b;
     line_geom<D>(L, cw, base, st, a, b);
-    T qv = T(0), qdv = T(0);
-    const int kind = act[cw] ? ci[cw].kind[FI] : 2;
-    if (kind != 2) {
+    T q[4] = {T(0), T(0), T(0), T(0)};
+    if (act[cw]) {
       T x[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) x[j] = X[base + j * st];
-      T dn = T(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], x[j], dn);
-      dn *= sgn * ih;
-      const T kap = ci[cw].kap[FI];
-      const T gam = ci[cw].gam[FI];
-      if (kind == 0) {
+      for (int S = 0; S < 2; ++S) {
+        const int f = 2 * D + S;
+        const int kind = ci[cw].kind[f];
+        if (kind == 2) continue;
+        const T sgn = S ? T(1) : T(-1);
+        const T xin = x[S ? N - 1 : 0];
+        T dn = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], x[j], dn);
+        dn *= sgn * ih;
+        const T kap = ci[cw].kap[f];
+        const T gam = ci[cw].gam[f];
         T tout = T(0), dno = T(0);
-        if (FULL) {
-          const T* xo = gu + ci[cw].nb[FI] * N3 + (base - cw * N3);
+        if (FULL && kind == 0) {
+          const T* xo = gu + ci[cw].nb[f] * N3 + (base - cw * N3);
           T y[N];
 #pragma unroll
           for (int j = 0; j < N; ++j) y[j] = xo[j * st];
-          tout = y[lout];
+          tout = y[S ? 0 : N - 1];
 #pragma unroll
           for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], y[j], dno);
           dno *= sgn * ih;
         }
-        const T jmp = x[lin] - tout;
-        qv = gam * jmp - kap * (dn + dno);
-        qdv = -kap * jmp;
-      } else {
-        qv = gam * x[lin] - kap * dn;
-        qdv = -kap * x[lin];
+        const T jmp = xin - tout;
+        q[2 * S] = gam * jmp - kap * (dn + dno);
+        q[2 * S + 1] = -kap * jmp;
       }
     }
-    F0[L] = qv;
-    F1[L] = qdv;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k * LINES + L] = q[k];
   }
   __syncwarp();
-  // phase 2: M1 along the first tangential axis
-  T r0[LPL], r1[LPL];
+  // phase 2: M1 along the first tangential axis, four fields
+  T r[4][LPL];
 #pragma unroll
   for (int k = 0; k < LPL; ++k) {
     const int L = lane + 32 * k;
-    r0[k] = T(0);
-    r1[k] = T(0);
+#pragma unroll
+    for (int fld = 0; fld < 4; ++fld) r[fld][k] = T(0);
     if (L < LINES) {
-      const int cw = L / N2, r = L - cw * N2, a = r % N, b = r / N;
+      const int cw = L / N2, rr = L - cw * N2, a = rr % N, b = rr / N;
       const int row = cw * N2 + N * b;
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        r0[k] = fma(t.M1[a][j], F0[row + j], r0[k]);
-        r1[k] = fma(t.M1[a][j], F1[row + j], r1[k]);
+        const T m = t.M1[a][j];
+#pragma unroll
+        for (int fld = 0; fld < 4; ++fld) r[fld][k] = fma(m, F[fld * LINES + row + j], r[fld][k]);
       }
     }
   }
@@ -386,29 +387,31 @@ __device__ __forceinline__ void face_diffusion(const T* X, T* Y, T* F0, T* F1, c
 #pragma unroll
   for (int k = 0; k < LPL; ++k) {
     const int L = lane + 32 * k;
-    if (L < LINES) {
-      F0[L] = r0[k];
-      F1[L] = r1[k];
-    }
+    if (L < LINES)
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld) F[fld * LINES + L] = r[fld][k];
   }
   __syncwarp();
-  // phase 3: M1 along the second tangential axis, then scatter into Y
+  // phase 3: M1 along the second tangential axis, then scatter both faces
   for (int L = lane; L < LINES; L += 32) {
     int cw, base, st, a, b;
     line_geom<D>(L, cw, base, st, a, b);
     if (!act[cw]) continue;
     const int col = cw * N2 + a;
-    T mv = T(0), mdv = T(0);
+    T m[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      mv = fma(t.M1[b][j], F0[col + N * j], mv);
-      mdv = fma(t.M1[b][j], F1[col + N * j], mdv);
-    }
-    mv *= area;
-    mdv *= area * sgn * ih;
-    Y[base + lin * st] += mv;
+      const T mm = t.M1[b][j];
 #pragma unroll
-    for (int j = 0; j < N; ++j) Y[base + j * st] = fma(t.dl[S][j], mdv, Y[base + j * st]);
+      for (int fld = 0; fld < 4; ++fld) m[fld] = fma(mm, F[fld * LINES + col + N * j], m[fld]);
+    }
+    const T d0 = -area * ih * m[1];   // sgn = -1 on face 0
+    const T d1 = area * ih * m[3];
+    Y[base] = fma(area, m[0], Y[base]);
+    Y[base + (N - 1) * st] = fma(area, m[2], Y[base + (N - 1) * st]);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      Y[base + j * st] = fma(t.dl[0][j], d0, fma(t.dl[1][j], d1, Y[base + j * st]));
   }
   __syncwarp();
 }
@@ -536,16 +539,15 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
   __syncwarp();
 }
 
+// F0 must be followed by 4 * LINES values of scratch (F0, F1 and the
+// reduction area are contiguous in every kernel's shared-memory carve).
 template <bool FULL, bool ADV, typename T>
 __device__ __forceinline__ void all_faces(const T* X, T* Y, T* F0, T* F1, const T* gu, const MeshParams& mp,
                                           long long cell0, int lane, const unsigned char* act,
                                           const CellInfo<T>* ci) {
-  face_diffusion<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
-  face_diffusion<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
-  face_diffusion<1, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
-  face_diffusion<1, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
-  face_diffusion<2, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
-  face_diffusion<2, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
+  faces_diffusion_dir<0, FULL>(X, Y, F0, gu, mp, lane, act, ci);
+  faces_diffusion_dir<1, FULL>(X, Y, F0, gu, mp, lane, act, ci);
+  faces_diffusion_dir<2, FULL>(X, Y, F0, gu, mp, lane, act, ci);
   if (ADV) {
     face_upwind<0, 0, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
     face_upwind<0, 1, FULL>(X, Y, F0, F1, gu, mp, cell0, lane, act, ci);
@@ -595,8 +597,6 @@ __device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell
 // Shared-memory carve-up of one warp.
 template <typename T>
 struct WarpMem {
-  static constexpr int nvec_apply = 4;
-  static constexpr int nvec_smooth = 6;
   static __host__ __device__ constexpr size_t bytes(int nvec) {
     return align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T)) + align16(CPW * sizeof(CellInfo<T>)) + 16;
   }
@@ -710,7 +710,9 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
   }
   const T rr0 = cell_sum(prr, lane, red);
   T rz = cell_sum(prz, lane, red);
-  const T thr = eps * eps * rr0;
+  // Stop at ||r|| <= eps ||d||, compared as norms: eps^2 ||d||^2 can underflow
+  // in FP32 for cells whose defect is tiny.
+  const T thr = eps * sqrt(rr0);
   bool live = mine && rr0 > T(0);
   int it = 0;
   while (__any_sync(FULLMASK, live && it < maxit)) {
@@ -749,7 +751,7 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
       ++it;
     }
     const T rr = cell_sum(prr2, lane, red);
-    if (upd && rr <= thr) {
+    if (upd && sqrt(rr) <= thr) {
       live = false;
       upd = false;
     }

@@ -8,9 +8,11 @@
 
 namespace dgmg {
 
-// Number of kernels launched by this library (for launch accounting).
-extern unsigned long long g_launches;
-inline void count_launch(unsigned long long k = 1) { g_launches += k; }
+// Number of kernels launched by this library from the calling host thread
+// (a solve's launch count is the difference over the call; each thread of a
+// serving loop drives its own context).
+extern thread_local unsigned long long t_launches;
+inline void count_launch(unsigned long long k = 1) { t_launches += k; }
 
 constexpr int kMinN = 2;   // p = 1
 constexpr int kMaxN = 9;   // p = 8

@@ -31,9 +31,7 @@ const double kPi = 3.14159265358979323846;
 
 }  // namespace
 
-void gauss_legendre01(int m, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(m, 0.0);
-  w.assign(m, 0.0);
+void gauss_legendre01(int m, double* x, double* w) {
   for (int i = 0; i < m; ++i) {
     double t = std::cos(kPi * (i + 0.75) / (m + 0.5));
     double pm = 0, pm1 = 0, dp = 0;
@@ -52,9 +50,15 @@ void gauss_legendre01(int m, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
-void gauss_lobatto01(int n, std::vector<double>& x, std::vector<double>& w) {
+void gauss_legendre01(int m, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(m, 0.0);
+  w.assign(m, 0.0);
+  gauss_legendre01(m, x.data(), w.data());
+}
+
+void gauss_lobatto01(int n, double* x, double* w) {
   const int N = n - 1;
-  std::vector<double> t(n);
+  double t[kMaxTableN];
   t[0] = -1.0;
   t[N] = 1.0;
   for (int i = 1; i < N; ++i) {
@@ -70,8 +74,6 @@ void gauss_lobatto01(int n, std::vector<double>& x, std::vector<double>& w) {
     }
     t[i] = s;
   }
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
   for (int i = 0; i < n; ++i) {
     double pn, pn1;
     legendre(N, t[i], pn, pn1);
@@ -80,8 +82,17 @@ void gauss_lobatto01(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+void gauss_lobatto01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  gauss_lobatto01(n, x.data(), w.data());
+}
+
 void lagrange(const std::vector<double>& z, double x, double* val, double* der) {
-  const int n = (int)z.size();
+  lagrange(z.data(), (int)z.size(), x, val, der);
+}
+
+void lagrange(const double* z, int n, double x, double* val, double* der) {
   for (int j = 0; j < n; ++j) {
     double v = 1.0;
     for (int k = 0; k < n; ++k)
@@ -102,11 +113,17 @@ void lagrange(const std::vector<double>& z, double x, double* val, double* der) 
 }
 
 std::vector<double> build_tables(int n) {
-  std::vector<double> gll, gllw, gq, gw;
+  std::vector<double> T(5 * n * n + 6 * n, 0.0);
+  build_tables_into(n, T.data());
+  return T;
+}
+
+void build_tables_into(int n, double* T) {
+  double gll[kMaxTableN], gllw[kMaxTableN], gq[kMaxTableN], gw[kMaxTableN];
   gauss_lobatto01(n, gll, gllw);
   gauss_legendre01(n, gq, gw);
-  std::vector<double> T(5 * n * n + 6 * n, 0.0);
-  double* B = T.data();
+  for (int i = 0; i < 5 * n * n + 6 * n; ++i) T[i] = 0.0;
+  double* B = T;
   double* Dg = B + n * n;
   double* W = Dg + n * n;
   double* dl = W + n;
@@ -116,13 +133,13 @@ std::vector<double> build_tables(int n) {
   double* GQ = hat + 2 * n;
   double* S1 = GQ + n;
   for (int q = 0; q < n; ++q) {
-    lagrange(gll, gq[q], B + q * n, G + q * n);
-    lagrange(gq, gq[q], nullptr, Dg + q * n);
+    lagrange(gll, n, gq[q], B + q * n, G + q * n);
+    lagrange(gq, n, gq[q], nullptr, Dg + q * n);
     W[q] = gw[q];
     GQ[q] = gq[q];
   }
-  lagrange(gll, 0.0, nullptr, dl);
-  lagrange(gll, 1.0, nullptr, dl + n);
+  lagrange(gll, n, 0.0, nullptr, dl);
+  lagrange(gll, n, 1.0, nullptr, dl + n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       double s = 0.0;
@@ -139,7 +156,6 @@ std::vector<double> build_tables(int n) {
       for (int q = 0; q < n; ++q) s += gw[q] * G[q * n + i] * G[q * n + j];
       S1[i * n + j] = s;
     }
-  return T;
 }
 
 namespace {
@@ -194,6 +210,25 @@ std::vector<double> q1_stencil(const HostMesh& m) {
       }
     }
   };
+  // Without advection the element matrix is sum_d K_d R_d + c R_m with the
+  // reference matrices R_d = int grad_d phi_b grad_d phi_a, R_m = int phi_b phi_a
+  // over the cell (integrated once with the same rule, exact for Q1).
+  double Rd[3][8][8], Rm[8][8];
+  std::memset(Rd, 0, sizeof(Rd));
+  std::memset(Rm, 0, sizeof(Rm));
+  if (!m.b) {
+    for (int q3 = 0; q3 < nq; ++q3)
+      for (int q2 = 0; q2 < nq; ++q2)
+        for (int q1 = 0; q1 < nq; ++q1) {
+          const double xi[3] = {g2[q1], g2[q2], g2[q3]};
+          const double w = w2[q1] * w2[q2] * w2[q3] * J;
+          for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b) {
+              Rm[a][b] += w * q1phi(b, xi) * q1phi(a, xi);
+              for (int d = 0; d < 3; ++d) Rd[d][a][b] += w * q1grad(b, xi, d, m.h) * q1grad(a, xi, d, m.h);
+            }
+        }
+  }
   for (int cz = 0; cz < m.nz; ++cz)
     for (int cy = 0; cy < m.ny; ++cy)
       for (int cx = 0; cx < m.nx; ++cx) {
@@ -202,7 +237,12 @@ std::vector<double> q1_stencil(const HostMesh& m) {
         const double cc = m.c ? m.c[c] : 0.0;
         double Ae[8][8];
         std::memset(Ae, 0, sizeof(Ae));
-        for (int q3 = 0; q3 < nq; ++q3)
+        if (!m.b) {
+          for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b)
+              Ae[a][b] = K[0] * Rd[0][a][b] + K[1] * Rd[1][a][b] + K[2] * Rd[2][a][b] + cc * Rm[a][b];
+        }
+        for (int q3 = 0; q3 < (m.b ? nq : 0); ++q3)
           for (int q2 = 0; q2 < nq; ++q2)
             for (int q1 = 0; q1 < nq; ++q1) {
               const double xi[3] = {g2[q1], g2[q2], g2[q3]};

@@ -6,15 +6,22 @@
 
 namespace dgmg {
 
+constexpr int kMaxTableN = 9;   // largest n = p + 1 of the tables
+
 // Gauss-Legendre (m points) and Gauss-Lobatto-Legendre (n >= 2 points) rules on
 // [0, 1] by Newton iteration on the Legendre polynomials.
 void gauss_legendre01(int m, std::vector<double>& x, std::vector<double>& w);
 void gauss_lobatto01(int n, std::vector<double>& x, std::vector<double>& w);
+void gauss_legendre01(int m, double* x, double* w);
+void gauss_lobatto01(int n, double* x, double* w);
 // l_j(x) and l_j'(x) of the Lagrange basis on `nodes`.
 void lagrange(const std::vector<double>& nodes, double x, double* val, double* der);
+void lagrange(const double* nodes, int n, double x, double* val, double* der);
 
-// All per-order tables in the flat layout of dgmg_internal.h.
+// All per-order tables in the flat layout of dgmg_internal.h; the _into form
+// writes table_size(n) doubles to T and uses no heap memory.
 std::vector<double> build_tables(int n);
+void build_tables_into(int n, double* T);
 
 struct HostMesh {
   int nx, ny, nz, p;

@@ -1,0 +1,236 @@
+"""Continuous-batching solve server for a stream of DG diffusion problems.
+
+Requests (mesh N^3, order p, log-normal K with its own sigma and seed,
+Gaussian source, homogeneous Dirichlet) arrive over time.  The server keeps
+`slots` workers; each worker is a host thread with its own CUDA stream and its
+own library context (re-used across requests).  A request is admitted, in
+arrival order, as soon as a worker is idle and its HBM footprint
+(footprint.library_bytes) fits into what the running requests leave of the
+budget; its set-up and solve then run on that worker's stream, overlapping on
+the device with the other workers' solves.  The library's kernels reduce in a
+fixed order, so a request's result does not depend on what runs beside it.
+
+    python -m paper_1805_11930_gb300.serve [--requests 512] [--slots 4] [--rates 0.5,0.8,1.0,1.2]
+
+measures the single-stream capacity (requests served back to back on one
+worker), then for each rate multiplier replays a seeded Poisson arrival trace
+at that multiple of the capacity and prints solves/s and p50 / p99 latency
+(arrival to completion) as one JSON line per rate.
+"""
+import argparse
+import collections
+import json
+import queue
+import statistics
+import threading
+import time
+
+import numpy as np
+
+from . import footprint
+
+SEED = 1805
+
+
+class Request:
+    def __init__(self, rid, arrival, n, p, sigma, seed):
+        self.rid, self.arrival, self.n, self.p, self.sigma, self.seed = rid, arrival, n, p, sigma, seed
+        self.t_admit = self.t_start = self.t_done = None
+        self.stats = None
+        self.solution = None
+        self.error = None
+        self.footprint = footprint.library_bytes((n, n, n), p, krylov="fcg")
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.arrival
+
+
+def make_trace(n_requests, rate, seed=SEED, n_range=(8, 48), p_range=(2, 6), sigma_range=(0.0, 2.0)):
+    """Seeded Poisson arrivals (rate requests/s; rate None = all at t = 0)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_requests) if rate else np.zeros(n_requests)
+    arrivals = np.cumsum(gaps) - (gaps[0] if rate else 0.0)
+    ns = rng.integers(n_range[0], n_range[1] + 1, n_requests)
+    ps = rng.integers(p_range[0], p_range[1] + 1, n_requests)
+    sig = rng.uniform(*sigma_range, n_requests)
+    seeds = rng.integers(0, 2 ** 31, n_requests)
+    return [Request(i, float(arrivals[i]), int(ns[i]), int(ps[i]), float(sig[i]), int(seeds[i]))
+            for i in range(n_requests)]
+
+
+def request_inputs(req):
+    """Coefficients and source of a request: K_T = exp(sigma N(0,1)) per cell;
+    f the Gaussian of the diffusion experiments (centre (0.75, 0.5, 0.3),
+    width 0.1) taken at each cell centre for all of the cell's quadrature
+    points."""
+    n, p = req.n, req.p
+    rng = np.random.default_rng(req.seed)
+    K = np.exp(req.sigma * rng.normal(size=n ** 3))
+    c = (np.arange(n) + 0.5) / n
+    cz, cy, cx = np.meshgrid(c, c, c, indexing="ij")
+    fc = np.exp(-((cx - 0.75) ** 2 + (cy - 0.5) ** 2 + (cz - 0.3) ** 2) / (2 * 0.1 ** 2)).reshape(-1)
+    return K, np.repeat(fc, (p + 1) ** 3)
+
+
+class DeviceRunner:
+    """Runs one request on one worker: its own stream and context."""
+
+    def __init__(self, device=0, keep_solutions=False, **opts):
+        self.device = device
+        self.keep = keep_solutions
+        self.opts = dict(opts)
+        self._local = threading.local()
+
+    def _worker_state(self):
+        st = getattr(self._local, "state", None)
+        if st is None:
+            import torch
+            from . import dgmg
+            torch.cuda.set_device(self.device)
+            stream = torch.cuda.Stream(self.device)
+            ctx = dgmg.Context(self.device, stream=stream)
+            st = self._local.state = (stream, ctx)
+        return st
+
+    def __call__(self, req):
+        import torch
+        from . import dgmg
+        stream, ctx = self._worker_state()
+        K, f_qp = request_inputs(req)
+        with torch.cuda.stream(stream):
+            ctx.set_mesh(req.n, req.n, req.n, 1.0, 1.0, 1.0, req.p, [0] * 6)
+            ctx.set_coefficients(K)
+            nd = ctx.sizes()["ndof"]
+            f = torch.empty(nd, dtype=torch.float64, device=f"cuda:{self.device}")
+            ctx.assemble_rhs(f_qp, f)
+            u = torch.zeros_like(f)
+            kw = dict(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
+            kw.update(self.opts)
+            stats = ctx.solve(f, u, dgmg.default_opts(**kw), check=False)
+            sol = u.cpu().numpy() if self.keep else None
+        stream.synchronize()
+        return stats, sol
+
+
+class SolveServer:
+    """Continuous batching over `slots` persistent workers with an HBM budget
+    (bytes).  The runner is called on the worker's own thread, so per-worker
+    state (stream, context) lives as long as the server."""
+
+    def __init__(self, runner, slots=4, hbm_budget=None):
+        self.runner = runner
+        self.slots = slots
+        self.budget = hbm_budget
+        self._lock = threading.Condition()
+        self._jobs = queue.Queue()
+        self._used = 0
+        self._idle = slots
+        self.max_concurrent = 0
+        self.max_used = 0
+        self._clock0 = None
+        self._workers = [threading.Thread(target=self._loop, daemon=True) for _ in range(slots)]
+        for t in self._workers:
+            t.start()
+
+    def _loop(self):
+        while True:
+            req = self._jobs.get()
+            if req is None:
+                return
+            req.t_start = time.perf_counter() - self._clock0
+            try:
+                req.stats, req.solution = self.runner(req)
+            except Exception as e:   # reported per request, the server keeps going
+                req.error = repr(e)
+            req.t_done = time.perf_counter() - self._clock0
+            with self._lock:
+                self._used -= req.footprint
+                self._idle += 1
+                self._lock.notify_all()
+
+    def run(self, trace):
+        """Serve the trace; returns when every request has completed."""
+        pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
+        self._clock0 = time.perf_counter()
+        with self._lock:
+            while pending:
+                head = pending[0]
+                now = time.perf_counter() - self._clock0
+                if head.arrival > now:
+                    self._lock.wait(timeout=head.arrival - now)
+                    continue
+                fits = self.budget is None or self._used + head.footprint <= self.budget or self._used == 0
+                if self._idle == 0 or not fits:
+                    self._lock.wait(timeout=0.05)
+                    continue
+                pending.popleft()
+                head.t_admit = now
+                self._idle -= 1
+                self._used += head.footprint
+                self.max_concurrent = max(self.max_concurrent, self.slots - self._idle)
+                self.max_used = max(self.max_used, self._used)
+                self._jobs.put(head)
+            while self._idle < self.slots:
+                self._lock.wait(timeout=0.05)
+        return trace
+
+    def close(self):
+        for _ in self._workers:
+            self._jobs.put(None)
+        for t in self._workers:
+            t.join()
+
+
+def summarize(reqs):
+    done = [r for r in reqs if r.t_done is not None and r.error is None]
+    lat = sorted(r.latency for r in done)
+    span = max(r.t_done for r in done) - min(r.arrival for r in reqs)
+    conv = sum(1 for r in done if r.stats and r.stats["converged"])
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(np.ceil(q * len(lat))) - 1)]
+
+    return {"requests": len(reqs), "completed": len(done), "converged": conv,
+            "errors": sum(1 for r in reqs if r.error), "solves_per_s": round(len(done) / span, 4),
+            "p50_latency_s": round(pct(0.50), 4), "p99_latency_s": round(pct(0.99), 4),
+            "mean_service_s": round(statistics.mean(r.t_done - r.t_start for r in done), 4),
+            "makespan_s": round(span, 3)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--rates", default="0.5,0.8,1.0,1.2")
+    ap.add_argument("--capacity-requests", type=int, default=16)
+    ap.add_argument("--nmax", type=int, default=48)
+    ap.add_argument("--budget-gb", type=float, default=200.0)
+    args = ap.parse_args()
+    runner = DeviceRunner()
+    budget = args.budget_gb * 1e9
+    rng_kw = dict(n_range=(8, args.nmax))
+    # single-stream capacity: one worker, requests back to back (after warm-up)
+    one = SolveServer(runner, slots=1, hbm_budget=budget)
+    one.run(make_trace(2, None, seed=SEED + 7, **rng_kw))
+    cap_trace = make_trace(args.capacity_requests, None, seed=SEED + 1, **rng_kw)
+    one.run(cap_trace)
+    one.close()
+    cap = summarize(cap_trace)
+    capacity = 1.0 / cap["mean_service_s"]
+    print(json.dumps({"single_stream": cap, "capacity_req_per_s": round(capacity, 4)}), flush=True)
+    for mult in [float(x) for x in args.rates.split(",")]:
+        trace = make_trace(args.requests, mult * capacity, seed=SEED, **rng_kw)
+        srv = SolveServer(runner, slots=args.slots, hbm_budget=budget)
+        srv.run(make_trace(args.slots, None, seed=SEED + 9, n_range=(8, 12)))    # warm the workers
+        srv.max_concurrent = srv.max_used = 0
+        srv.run(trace)
+        srv.close()
+        out = summarize(trace)
+        out.update({"rate_multiplier": mult, "rate_req_per_s": round(mult * capacity, 4), "slots": args.slots,
+                    "max_concurrent": srv.max_concurrent, "max_hbm_gb": round(srv.max_used / 1e9, 3)})
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,100 @@
+"""Time-to-solution report for the synthetic workloads.
+
+python -m paper_1805_11930_gb300.solve_report [--workloads poisson,lognormal,convection,reservoir] [--repeat 3]
+
+For each workload: set-up time (coefficients, diag(D_T), Q1 matrix, AMG),
+then the solve to a 1e-8 relative residual from u = 0, in FP64 and with the
+mixed-precision V-cycle (FP32 smoother, inner solves and residual; FP64 outer
+Krylov, dots, coarse solve and final residual check).  Reports the median
+solve time over --repeat runs (CUDA events, inputs resident), outer
+iterations, mean / max inner iterations, the recomputed FP64 residual, the
+difference between the mixed and FP64 solutions and, where the workload has
+an exact solution, the max nodal error.  One JSON line per workload.
+"""
+import argparse
+import json
+import statistics
+import time
+
+
+def run(name, repeat):
+    import numpy as np
+    import torch
+
+    from . import dgmg, inputs
+    if name == "poisson":
+        w, kry, inner = inputs.poisson_sine(8, 2), dgmg.KRYLOV_CG, dgmg.INNER_PCG
+    elif name == "lognormal":
+        w, kry, inner = inputs.lognormal(32, 4), dgmg.KRYLOV_CG, dgmg.INNER_PCG
+    elif name == "convection":
+        w, kry, inner = inputs.convection(64, 3), dgmg.KRYLOV_FGMRES, dgmg.INNER_GMRES
+    elif name == "reservoir":
+        w, kry, inner = inputs.reservoir(), dgmg.KRYLOV_CG, dgmg.INNER_PCG
+    else:
+        raise ValueError(name)
+    t0 = time.perf_counter()
+    ctx = dgmg.Context(0)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
+    vol, face = ctx.quadrature_points()
+    s = ctx.sizes()
+    f = torch.empty(s["ndof"], dtype=torch.float64, device="cuda")
+    ctx.assemble_rhs(inputs.evaluate(w["f"], vol), f, g_qp=inputs.evaluate(w["g"], face),
+                     j_qp=inputs.evaluate(w["j"], face))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = {"workload": w["name"], "ndof": s["ndof"], "setup_s": round(setup_s, 3)}
+    flex = dgmg.KRYLOV_FCG if kry == dgmg.KRYLOV_CG else kry
+    sols = {}
+    for tag, opts in (("fp64", dgmg.default_opts(krylov=kry, inner=inner, maxit=1000)),
+                      ("mixed", dgmg.default_opts(krylov=flex, inner=inner, smoother_prec=dgmg.FP32,
+                                                  maxit=1000))):
+        u = torch.zeros_like(f)
+        ms, st = [], None
+        for _ in range(repeat):
+            u.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            st = ctx.solve(f, u, opts, check=False)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        sols[tag] = u.clone()
+        out[tag] = {"solve_s": round(statistics.median(ms) / 1e3, 4), "status": st["status"],
+                    "iterations": st["iterations"], "rel_residual": st["rel_residual"],
+                    "inner_mean": round(st["inner_mean"], 2), "inner_max": st["inner_max"],
+                    "us_per_dof": round(statistics.median(ms) * 1e3 / s["ndof"], 5)}
+    d = (sols["mixed"] - sols["fp64"]).norm() / sols["fp64"].norm()
+    out["mixed_vs_fp64_rel_diff"] = float(d)
+    if w["exact"] is not None:
+        # exact solution at the GLL nodes (end points and roots of P_p')
+        gll = np.polynomial.legendre.Legendre.basis(w["p"]).deriv().roots()
+        z = np.sort(np.concatenate(([-1.0], np.real(gll), [1.0])))
+        z = 0.5 * (z + 1.0)
+        nx, ny, nz = w["nc"]
+        h = np.array(w["L"]) / np.array(w["nc"])
+        n = w["p"] + 1
+        i3, i2, i1 = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        cz, cy, cx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        X = (cx.reshape(-1, 1) + z[i1.reshape(1, -1)]) * h[0]
+        Y = (cy.reshape(-1, 1) + z[i2.reshape(1, -1)]) * h[1]
+        Z = (cz.reshape(-1, 1) + z[i3.reshape(1, -1)]) * h[2]
+        ue = w["exact"](X, Y, Z).reshape(-1)
+        for tag in ("fp64", "mixed"):
+            out[tag]["max_nodal_error"] = float(np.abs(sols[tag].cpu().numpy() - ue).max())
+    ctx.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workloads", default="poisson,lognormal,convection,reservoir")
+    ap.add_argument("--repeat", type=int, default=3)
+    args = ap.parse_args()
+    for name in args.workloads.split(","):
+        print(json.dumps(run(name, args.repeat)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,56 @@
+"""Host logic of the serving loop on CPU, with a fake runner: arrival order,
+slot limit, HBM budget (a request waits until enough running ones finish),
+per-request latency accounting."""
+import threading
+import time
+
+from paper_1805_11930_gb300 import serve
+
+
+class FakeRunner:
+    def __init__(self, service=0.05):
+        self.service = service
+        self.lock = threading.Lock()
+        self.running = 0
+        self.peak = 0
+        self.order = []
+
+    def __call__(self, req):
+        with self.lock:
+            self.running += 1
+            self.peak = max(self.peak, self.running)
+            self.order.append(req.rid)
+        time.sleep(self.service)
+        with self.lock:
+            self.running -= 1
+        return {"converged": 1, "rel_residual": 1e-9}, None
+
+
+def test_slots_fifo_and_latency():
+    trace = serve.make_trace(12, None, n_range=(8, 10), p_range=(2, 2))
+    r = FakeRunner()
+    srv = serve.SolveServer(r, slots=3)
+    srv.run(trace)
+    srv.close()
+    assert r.peak == 3 and srv.max_concurrent == 3
+    assert r.order[:3] == sorted(r.order[:3]) and set(r.order) == set(range(12))
+    s = serve.summarize(trace)
+    assert s["completed"] == 12 and s["converged"] == 12
+    assert s["p50_latency_s"] >= 0.05 and s["p99_latency_s"] >= s["p50_latency_s"]
+
+
+def test_budget_limits_concurrency():
+    trace = serve.make_trace(6, None, n_range=(8, 8), p_range=(3, 3))
+    fp = trace[0].footprint
+    r = FakeRunner()
+    srv = serve.SolveServer(r, slots=6, hbm_budget=2 * fp)      # room for two at a time
+    srv.run(trace)
+    srv.close()
+    assert r.peak == 2 and srv.max_used <= 2 * fp
+
+
+def test_poisson_arrivals_are_seeded():
+    a = [x.arrival for x in serve.make_trace(50, 10.0)]
+    b = [x.arrival for x in serve.make_trace(50, 10.0)]
+    assert a == b and a[0] == 0.0 and all(y >= x for x, y in zip(a, a[1:]))
+    assert 2.5 < a[-1] < 8.0      # 49 gaps of mean 0.1 s
