@@ -192,6 +192,31 @@ dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_so
 dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
                        dgmg_solve_stats* stats);
 
+/* Largest grid (nx*ny*nz cells) dgmg_restrict_noalloc accepts. */
+#define DGMG_NOALLOC_MAX_CELLS 131072
+
+/* r_hat = R r, the same restriction as dgmg_restrict, for callers that cannot
+ * allocate device memory (code running under CUDA-graph capture, hosts that
+ * own all device memory through their own pool, loops that must not block on
+ * an allocator).  The paper has no counterpart: this is a deployment variant.
+ *
+ * No context is needed and nothing is allocated: the per-cell corner sums live
+ * in a fixed file-scope device array of 8 * DGMG_NOALLOC_MAX_CELLS doubles
+ * (8 MiB), which every GPU that loads this library holds until the process
+ * exits.  Grids with more than DGMG_NOALLOC_MAX_CELLS cells return
+ * DGMG_ERR_ARG, as do p outside [1, 8], non-positive sizes and NULL pointers.
+ *   r: device DG vector of `prec` (ncell (p+1)^3 values, layout above);
+ *   r_hat: device FP64 vertex vector ((nx+1)(ny+1)(nz+1) values), overwritten;
+ *   cuda_stream: cudaStream_t of the current device (NULL = default stream).
+ * The first call on a device sets it up (with that device current it copies
+ * the 1D tables into constant memory and looks up the scratch array's device
+ * address), synchronously; make that first call before any stream capture.
+ * All calls on a device share the one scratch array: calls whose work may
+ * overlap on the GPU (different streams without ordering) race and give wrong
+ * results.  Returns DGMG_ERR_CUDA if a CUDA call fails. */
+dgmg_status dgmg_restrict_noalloc(int nx, int ny, int nz, int p, const void* r, double* r_hat, dgmg_prec prec,
+                                  void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

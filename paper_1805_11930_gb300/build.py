@@ -35,7 +35,7 @@ def _jobs():
     for n in ORDERS:
         obj = os.path.join(BUILD, f"cell_kernels_n{n}.o")
         jobs.append((obj, [nv] + common + [f"-DDGMG_N={n}", "-c", os.path.join(CSRC, "cell_kernels.cu"), "-o", obj]))
-    for name in ("vec_kernels", "capi"):
+    for name in ("vec_kernels", "capi", "noalloc"):
         obj = os.path.join(BUILD, name + ".o")
         jobs.append((obj, [nv] + common + ["-c", os.path.join(CSRC, name + ".cu"), "-o", obj]))
     gxx = shutil.which("g++") or "g++"

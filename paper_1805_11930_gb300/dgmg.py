@@ -75,7 +75,10 @@ _SIG = {
     "dgmg_coarse_cycle": (_I, [_P, _P, _P]),
     "dgmg_vcycle": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts)]),
     "dgmg_solve": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)]),
+    "dgmg_restrict_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P]),
 }
+
+NOALLOC_MAX_CELLS = 131072
 
 
 def library_path():
@@ -249,6 +252,22 @@ class Context:
         if check:
             self._check(st)
         return stats.as_dict() | {"status": STATUS.get(st, st)}
+
+
+def restrict_noalloc(nx, ny, nz, p, r, r_hat, stream=None):
+    """dgmg_restrict_noalloc: R r into r_hat without a context or any device
+    allocation (the scratch is a fixed array inside the library).  `stream`:
+    a torch.cuda.Stream, a raw cudaStream_t or None (torch's current stream)."""
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    st = lib.dgmg_restrict_noalloc(nx, ny, nz, p, _ptr(r), _ptr(r_hat), _prec(r), stream)
+    if st != DGMG_OK:
+        raise DgmgError(st, "dgmg_restrict_noalloc failed (sizes beyond "
+                            f"{NOALLOC_MAX_CELLS} cells, bad arguments or a CUDA error)")
 
 
 def exported_symbols(header_path=None):
