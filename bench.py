@@ -208,11 +208,11 @@ def run_dgmg(args, rank, world, local_rank):
                                "apply": round(ap_ms / total_ms, 3) if world == 1 else None}}
 
     # apply throughput, FP64 and FP32 (separate timed loop, inputs resident)
-    def time_apply(dtype, reps=20):
+    def time_apply(dtype, reps=20, df64=False):
         x = torch.rand(ndof, dtype=dtype, device=dev)
         y = torch.empty_like(x)
         for _ in range(3):
-            ctx.apply(x, y)
+            ctx.apply(x, y, df64=df64)
         torch.cuda.synchronize()
         ms = []
         for _ in range(reps):
@@ -220,7 +220,7 @@ def run_dgmg(args, rank, world, local_rank):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ctx.apply(x, y)
+            ctx.apply(x, y, df64=df64)
             b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))
@@ -228,24 +228,32 @@ def run_dgmg(args, rank, world, local_rank):
 
     apply64, apply64_ms = time_apply(torch.float64)
     apply32, apply32_ms = time_apply(torch.float32)
+    applydf, applydf_ms = time_apply(torch.float64, df64=True)
 
-    # mixed precision solve (FP32 smoother and V-cycle, FP64 flexible CG)
-    mixed = dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
-    for _ in range(2):
-        u.zero_()
-        ctx.solve(f, u, mixed)
-    mixed_ms = []
-    mst = None
-    for _ in range(3):
-        flush.fill_(1.0)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        u.zero_()
-        mst = ctx.solve(f, u, mixed)
-        b.record(stream)
-        b.synchronize()
-        mixed_ms.append(a.elapsed_time(b))
+    def time_solve(opts, reps=3):
+        for _ in range(2):
+            u.zero_()
+            ctx.solve(f, u, opts)
+        ms, st = [], None
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            u.zero_()
+            st = ctx.solve(f, u, opts)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms), st
+
+    # mixed precision (FP32 smoother and V-cycle, FP64 flexible CG) and the
+    # double-float variants (FP64 vectors, FP32-pair arithmetic)
+    mixed_ms, mst = time_solve(dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG))
+    mdf_ms, mdfst = time_solve(dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG,
+                                                 apply_prec=dgmg.DF64))
+    df_ms, dfst = time_solve(dgmg.default_opts(smoother_prec=dgmg.DF64, krylov=dgmg.KRYLOV_FCG,
+                                               apply_prec=dgmg.DF64))
 
     # end to end through the C ABI with host buffers
     f_host = f.cpu().pin_memory()
@@ -282,10 +290,14 @@ def run_dgmg(args, rank, world, local_rank):
         "solve": {"iterations": last["iterations"], "rel_residual": last["rel_residual"],
                   "inner_mean": round(last["inner_mean"], 3), "inner_max": last["inner_max"],
                   "solve_s_fp64": round(total_ms / args.steps / 1e3, 5),
-                  "solve_s_mixed": round(statistics.median(mixed_ms) / 1e3, 5),
-                  "mixed_iterations": mst["iterations"], "mixed_rel_residual": mst["rel_residual"]},
+                  "solve_s_mixed": round(mixed_ms / 1e3, 5),
+                  "mixed_iterations": mst["iterations"], "mixed_rel_residual": mst["rel_residual"],
+                  "solve_s_mixed_df64_outer": round(mdf_ms / 1e3, 5), "mixed_df64_rel_residual": mdfst["rel_residual"],
+                  "solve_s_df64": round(df_ms / 1e3, 5), "df64_iterations": dfst["iterations"],
+                  "df64_rel_residual": dfst["rel_residual"]},
         "apply": {"gdofs_fp64": round(apply64, 4), "ms_fp64": round(apply64_ms, 4),
-                  "gdofs_fp32": round(apply32, 4), "ms_fp32": round(apply32_ms, 4)},
+                  "gdofs_fp32": round(apply32, 4), "ms_fp32": round(apply32_ms, 4),
+                  "gdofs_df64": round(applydf, 4), "ms_df64": round(applydf_ms, 4)},
     }
     return out
 

@@ -51,10 +51,16 @@ typedef enum {
   DGMG_ERR_TIMEOUT = 7         /* reserved: a bounded device wait gave up       */
 } dgmg_status;
 
-typedef enum { DGMG_FP64 = 0, DGMG_FP32 = 1 } dgmg_prec;
+/* DGMG_DF64: FP64 vectors in memory, arithmetic in double-float (pairs of
+ * FP32 numbers, about 48 significant bits): FP64-level accuracy on the FP32
+ * pipe, which GB300 issues 62x faster than FP64.  Built for diffusion (b = 0)
+ * with p <= 6, and in the smoothers with the inner PCG; other combinations
+ * return DGMG_ERR_ARG. */
+typedef enum { DGMG_FP64 = 0, DGMG_FP32 = 1, DGMG_DF64 = 2 } dgmg_prec;
 typedef enum { DGMG_KRYLOV_CG = 0, DGMG_KRYLOV_FCG = 1, DGMG_KRYLOV_FGMRES = 2 } dgmg_krylov;
 typedef enum { DGMG_INNER_PCG = 0, DGMG_INNER_GMRES = 1 } dgmg_inner;
 typedef enum { DGMG_COARSE_AMG = 0, DGMG_COARSE_NONE = 1 } dgmg_coarse;
+typedef enum { DGMG_SMOOTHER_JACOBI = 0, DGMG_SMOOTHER_SSOR = 1 } dgmg_smoother;
 
 /* Options of the hybrid V-cycle (Algorithm 1) and of the outer Krylov solve. */
 typedef struct {
@@ -63,6 +69,7 @@ typedef struct {
   double rtol;         /* outer stop: ||r||_2 <= rtol ||r_0||_2 (default 1e-8)     */
   int maxit;           /* outer iteration cap (default 500)                        */
   int smoother_prec;   /* dgmg_prec of the V-cycle's DG part (smoother, residual)  */
+                       /* FP64, FP32 or DF64 (FP64 vectors, double-float math)   */
   double omega;        /* block-Jacobi damping (Algorithm 2), default 0.8          */
   int npre, npost;     /* smoothing sweeps (default 1, 1)                          */
   double eps_inner;    /* block solve: reduce ||d - D_T x||_2 by eps (default 1e-2) */
@@ -71,6 +78,13 @@ typedef struct {
   int inner_restart;   /* inner GMRES restart (default 12)                         */
   int coarse;          /* dgmg_coarse: Q1 + AMG correction, or none               */
   int timing;          /* 1: time smoother and operator launches with CUDA events */
+  int coarse_cycles;   /* AMG V-cycles per coarse correction, iterated on the     */
+                       /* coarse residual (default 1)                             */
+  int smoother;        /* dgmg_smoother: block-Jacobi (Algorithm 2, default) or   */
+                       /* multicolour block-SSOR (one forward + one backward pass */
+                       /* over the 8 parity colours per sweep)                    */
+  int apply_prec;      /* dgmg_prec of the outer operator applications: FP64      */
+                       /* (default) or DF64; the final residual check is FP64    */
 } dgmg_solve_opts;
 
 typedef struct {
@@ -158,6 +172,20 @@ dgmg_status dgmg_block_diagonal(dgmg_ctx* ctx, void* diag, dgmg_prec prec);
 dgmg_status dgmg_block_smooth(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega,
                               double eps, int maxit, int inner, int inner_restart,
                               dgmg_prec prec, int* inner_its);
+
+/* nsweep multicolour block-SOR passes (symmetric = 0) or block-SSOR sweeps
+ * (symmetric = 1: a forward then a backward pass), the data-parallel form of
+ * the successive block over-relaxation of Algorithm 3 and of block-SSOR
+ * (Sec. 2.2.1): cells are ordered by colour kx + 2 ky + 4 kz, (kx,ky,kz) the
+ * parities of the cell indices; cells of one colour share no face, so each
+ * colour is updated in place in one launch from the current values of the
+ * other colours: d_T = f_T - sum_T' A_TT' u_T', D_T x_T = d_T solved as in
+ * dgmg_block_smooth, u_T += omega x_T.  The result differs from a
+ * lexicographic sweep (another ordering).  Arguments as dgmg_block_smooth;
+ * u is updated in place. */
+dgmg_status dgmg_block_sor(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega, double eps,
+                           int maxit, int inner, int inner_restart, int symmetric, dgmg_prec prec,
+                           int* inner_its);
 
 /* r_hat = R r with R = P^T, the Q1 restriction (Sec. 2.2.2).  r: device DG
  * vector of `prec`; r_hat: device FP64 vertex vector (overwritten). */

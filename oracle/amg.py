@@ -12,7 +12,10 @@ compared with it exactly:
   (vx, vy, vz) belongs to aggregate (vx//2, vy//2, vz//2);
 * the tentative prolongation is piecewise constant (not smoothed);
 * coarse matrices are Galerkin products A_{l+1} = P_l^T A_l P_l;
-* one pre- and one post-smoothing sweep of damped Jacobi, omega = 2/3;
+* one pre- and one post-smoothing sweep of damped Jacobi with the weight
+  4 / (3 G), G = max_i sum_j |a_ij| / |a_ii| the Gershgorin bound of the
+  spectrum of D^-1 A on that level (2/3 for the isotropic Q1 Laplacian,
+  smaller where anisotropy or high contrast would make 2/3 unstable);
 * coarsening stops once a level has at most 512 unknowns, which is solved
   exactly (dense LU);
 * one V-cycle from a zero initial guess per use.
@@ -37,8 +40,7 @@ def aggregation(dims):
 
 
 class AggregationAMG:
-    def __init__(self, A, dims, coarse_size=512, omega=2.0 / 3.0, max_levels=32):
-        self.omega = omega
+    def __init__(self, A, dims, coarse_size=512, max_levels=32):
         self.A = [sp.csr_matrix(A)]
         self.P = []
         self.dims = [tuple(dims)]
@@ -48,6 +50,10 @@ class AggregationAMG:
             self.A.append(sp.csr_matrix(P.T @ self.A[-1] @ P))
             self.dims.append(cd)
         self.dinv = [1.0 / Al.diagonal() for Al in self.A]
+        self.omega = []
+        for Al, dl in zip(self.A, self.dinv):
+            G = np.max(np.asarray(abs(Al).sum(axis=1)).ravel() * np.abs(dl))
+            self.omega.append(4.0 / (3.0 * G))
         self.coarse_lu = sla.lu_factor(self.A[-1].toarray())
 
     @property
@@ -58,7 +64,7 @@ class AggregationAMG:
         """One V-cycle for A_level x = b from x = 0."""
         if level == len(self.A) - 1:
             return sla.lu_solve(self.coarse_lu, b)
-        A, dinv, w = self.A[level], self.dinv[level], self.omega
+        A, dinv, w = self.A[level], self.dinv[level], self.omega[level]
         x = np.zeros_like(b)
         x = x + w * dinv * (b - A @ x)                    # pre-smoothing
         r = b - A @ x

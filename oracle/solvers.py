@@ -147,6 +147,39 @@ class BlockJacobi:
         return u
 
 
+class MulticolourBlockSOR(BlockJacobi):
+    """Block-SOR / block-SSOR (Algorithm 3 and Sec. 2.2.1) with the cells taken
+    colour by colour: colour(T) = (cx mod 2) + 2 (cy mod 2) + 4 (cz mod 2).
+    Cells of one colour share no face, so within a colour the order does not
+    matter; each cell's defect uses the current values of all other cells.
+    A forward pass visits colours 0..7, the backward pass 7..0; symmetric
+    sweeps do both.  Update: u_T <- u_T + omega D_T^-1 d_T (the correction
+    form of Algorithm 2, read into Algorithm 3 whose printed update is
+    inconsistent with it)."""
+
+    def __init__(self, A, N, nc, symmetric=True, **kw):
+        super().__init__(A, N, **kw)
+        nx, ny, nz = nc
+        c = np.arange(nx * ny * nz)
+        cx, cy, cz = c % nx, (c // nx) % ny, c // (nx * ny)
+        self.colour = (cx % 2) + 2 * (cy % 2) + 4 * (cz % 2)
+        self.symmetric = symmetric
+
+    def __call__(self, f, u, nsweep, omega):
+        N = self.N
+        u = u.copy()
+        its = np.zeros(self.ncell, dtype=np.int64)
+        order = list(range(8)) + (list(range(7, -1, -1)) if self.symmetric else [])
+        for _ in range(nsweep):
+            for k in order:
+                d = f - self.A @ u
+                for c in np.nonzero(self.colour == k)[0]:
+                    du, its[c] = self.solve_block(c, d[c * N:(c + 1) * N])
+                    u[c * N:(c + 1) * N] += omega * du
+        self.last_its = its
+        return u
+
+
 # ----------------------------------------------------------------- V-cycle
 class HybridVCycle:
     """One V-cycle of Algorithm 1: presmooth, residual, restrict, coarse

@@ -1,0 +1,68 @@
+"""Operator-apply throughput over the polynomial degree.
+
+python -m paper_1805_11930_gb300.apply_sweep [--degrees 2,3,4,5,6]
+
+Meshes sized to 30-300 MB per FP64 vector: 64^3 cells for p <= 3, 40^3 for
+p = 4..6 (log-normal K, Dirichlet).  For each p and precision: median
+CUDA-event time of dgmg_apply over 20 launches (an L2-sized buffer is
+written between launches), GDOF/s, the algorithmic rate (32 n^4 + 120 n^3
+flop per cell) as a fraction of the FP64 pipe peak (4 flop/clk/SM x 152 SMs
+x 2070 MHz; for df64, FP64 vectors in double-float arithmetic, as well) or of
+the measured FP32 FMA rate (75.6 TFLOP/s), and the HBM
+rate of the compulsory traffic (read u, write v) as a fraction of the
+measured copy bandwidth.  One JSON line per (p, precision).
+"""
+import argparse
+import json
+import statistics
+
+FP64_PEAK = 152 * 4 * 2070e6
+FP32_PEAK = 75.6e12
+HBM_GBS = 6686.8
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--degrees", default="2,3,4,5,6")
+    ap.add_argument("--reps", type=int, default=20)
+    args = ap.parse_args()
+    import torch
+
+    from . import dgmg, flops, inputs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for p in [int(x) for x in args.degrees.split(",")]:
+        n = 64 if p <= 3 else 40
+        w = inputs.lognormal(n, p)
+        ctx = dgmg.Context(0)
+        ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+        ctx.set_coefficients(w["K"])
+        s = ctx.sizes()
+        for dt, name, peak in ((torch.float64, "fp64", FP64_PEAK), (torch.float32, "fp32", FP32_PEAK),
+                               (torch.float64, "df64", FP64_PEAK)):
+            x = torch.rand(s["ndof"], dtype=dt, device="cuda")
+            y = torch.empty_like(x)
+            df = name == "df64"
+            for _ in range(3):
+                ctx.apply(x, y, df64=df)
+            ms = []
+            for _ in range(args.reps):
+                flush.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.apply(x, y, df64=df)
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = statistics.median(ms) / 1e3
+            fl = flops.algorithmic_apply(p + 1) * s["ncell"] / t
+            by = flops.hbm_bytes_apply(p + 1, s["ncell"], 4 if name == "fp32" else 8) / t
+            print(json.dumps({"p": p, "mesh": n, "ndof": s["ndof"], "prec": name, "ms": round(t * 1e3, 4),
+                              "gdofs": round(s["ndof"] / t / 1e9, 3), "tflops": round(fl / 1e12, 3),
+                              "alu_frac": round(fl / peak, 3), "hbm_gbs": round(by / 1e9, 1),
+                              "hbm_frac": round(by / 1e9 / HBM_GBS, 4)}), flush=True)
+        ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -3,6 +3,7 @@
 // (Algorithm 1 of arXiv 1805.11930) and the outer Krylov drivers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -75,6 +76,7 @@ using namespace dgmg;
 struct AmgLevel {
   int vx, vy, vz;
   long long n;
+  double omega = 2.0 / 3.0;  // damped-Jacobi weight 4 / (3 G), G the Gershgorin bound of D^-1 A
   double* st = nullptr;
   double* dinv = nullptr;
   double* b = nullptr;
@@ -250,6 +252,16 @@ dgmg_status ready(dgmg_ctx* ctx) {
   return DGMG_OK;
 }
 
+// Double-float kernels exist for diffusion (b = 0) with p <= 6 and, in the
+// smoothers, the inner PCG.
+dgmg_status check_df64(dgmg_ctx* ctx, int prec, int inner) {
+  if (prec != DGMG_DF64) return DGMG_OK;
+  if (ctx->p > 6) return fail(ctx, DGMG_ERR_ARG, "DF64 kernels are built for p <= 6");
+  if (ctx->db) return fail(ctx, DGMG_ERR_ARG, "DF64 kernels are built for b = 0");
+  if (inner == DGMG_INNER_GMRES) return fail(ctx, DGMG_ERR_ARG, "DF64 smoothers use the inner PCG");
+  return DGMG_OK;
+}
+
 // ------------------------------------------------------------------ dots
 dgmg_status dot(dgmg_ctx* ctx, const double* x, const double* y, double& out) {
   CK(vec_dot(ctx->ndof, x, y, ctx->dot_partial, ctx->dot_out, ctx->stream));
@@ -271,7 +283,8 @@ dgmg_status multi_dot(dgmg_ctx* ctx, int k, double* const* xs, const double* y, 
 // ------------------------------------------------------------------ smoother
 // nsweep block-Jacobi sweeps on u (in place) with ping-pong through tmp.
 dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, int nsweep, double omega, double eps,
-                            int maxit, int inner, int restart, bool fp32, bool zero_first, int* its) {
+                            int maxit, int inner, int restart, int prec, bool zero_first, int* its) {
+  const bool fp32 = prec == DGMG_FP32;
   if (nsweep <= 0) {
     if (zero_first) {
       if (fp32)
@@ -301,7 +314,7 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     a.restart = restart;
     a.its = (its || ctx->track_its) ? ctx->its : nullptr;
     const size_t e0 = ctx->timing ? record_event(ctx) : 0;
-    CK(ctx->ops->smooth(mp, a, fp32, ctx->stream));
+    CK(ctx->ops->smooth(mp, a, prec, ctx->stream));
     if (ctx->timing) ctx->ev_smooth.push_back({e0, record_event(ctx)});
     ++ctx->n_sweep;
     if (k == 0 && zero_first) ++ctx->n_zero_sweep;
@@ -321,6 +334,69 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
   return DGMG_OK;
 }
 
+// nsweep multicolour block-SOR passes on u in place (NEXT to Algorithm 3):
+// colours 0..7 (cells whose index parities (cx, cy, cz) give kx + 2ky + 4kz),
+// each colour in one launch that reads the current values of the other
+// colours; symmetric = forward colours then backward colours (block-SSOR).
+dgmg_status sor_internal(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega, double eps, int maxit,
+                         int inner, int restart, int prec, bool zero_first, bool symmetric, int* its) {
+  const bool fp32 = prec == DGMG_FP32;
+  if (zero_first) {
+    if (fp32)
+      CK(vec_fill_f(ctx->ndof, 0.f, (float*)u, ctx->stream));
+    else
+      CK(vec_fill(ctx->ndof, 0.0, (double*)u, ctx->stream));
+  }
+  if (nsweep <= 0) return DGMG_OK;
+  if (maxit <= 0) maxit = ctx->n * ctx->n * ctx->n;
+  if (inner != DGMG_INNER_PCG && inner != DGMG_INNER_GMRES) return fail(ctx, DGMG_ERR_ARG, "bad inner solver");
+  if (inner == DGMG_INNER_GMRES && (restart < 1 || restart > 64))
+    return fail(ctx, DGMG_ERR_ARG, "inner_restart must be in [1, 64]");
+  const MeshParams mp = params(ctx);
+  const int passes = symmetric ? 2 : 1;
+  for (int k = 0; k < nsweep; ++k)
+    for (int pass = 0; pass < passes; ++pass) {
+      for (int c = 0; c < 8; ++c) {
+        SmoothArgs a;
+        a.f = f;
+        a.uold = u;
+        a.unew = u;
+        a.diag = fp32 ? (const void*)ctx->dinv32 : (const void*)ctx->dinv64;
+        a.omega = omega;
+        a.eps = eps;
+        a.maxit = maxit;
+        a.inner = inner;
+        a.restart = restart;
+        a.its = (its || ctx->track_its) ? ctx->its : nullptr;
+        a.color = pass == 0 ? c : 7 - c;
+        const size_t e0 = ctx->timing ? record_event(ctx) : 0;
+        CK(ctx->ops->smooth(mp, a, prec, ctx->stream));
+        if (ctx->timing) ctx->ev_smooth.push_back({e0, record_event(ctx)});
+      }
+      ++ctx->n_sweep;
+      if (ctx->track_its) {
+        k_its_acc<<<152, 256, 0, ctx->stream>>>(ctx->ncell, ctx->its, ctx->itsum, ctx->itmax);
+        count_launch();
+        CK(cudaGetLastError());
+        ++ctx->sweeps_tracked;
+      }
+    }
+  if (its && its != ctx->its)
+    CK(cudaMemcpyAsync(its, ctx->its, ctx->ncell * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+  return DGMG_OK;
+}
+
+// The smoother of the V-cycle: block-Jacobi (ping-pong) or multicolour
+// block-SSOR (in place).
+dgmg_status vcycle_smooth(dgmg_ctx* ctx, const dgmg_solve_opts& o, const void* F, void* U, void* T1, int nsweep,
+                          int prec, bool zero) {
+  if (o.smoother == DGMG_SMOOTHER_SSOR)
+    return sor_internal(ctx, F, U, nsweep, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, prec,
+                        zero, true, nullptr);
+  return smooth_internal(ctx, F, U, T1, nsweep, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart,
+                         prec, zero, nullptr);
+}
+
 // ------------------------------------------------------------------ AMG
 dgmg_status amg_cycle(dgmg_ctx* ctx, int l, const double* b, double* xout) {
   const int last = (int)ctx->lv.size() - 1;
@@ -330,13 +406,27 @@ dgmg_status amg_cycle(dgmg_ctx* ctx, int l, const double* b, double* xout) {
   }
   AmgLevel& L = ctx->lv[l];
   AmgLevel& C = ctx->lv[l + 1];
-  const double w = 2.0 / 3.0;
+  const double w = L.omega;
   CK(stencil_jacobi(L.vx, L.vy, L.vz, L.st, L.dinv, b, nullptr, L.xt, w, true, ctx->stream));
   CK(stencil_residual(L.vx, L.vy, L.vz, L.st, b, L.xt, L.r, ctx->stream));
   CK(agg_restrict(L.vx, L.vy, L.vz, L.r, C.b, ctx->stream));
   CS(amg_cycle(ctx, l + 1, C.b, C.x));
   CK(agg_prolong_add(L.vx, L.vy, L.vz, C.x, L.xt, ctx->stream));
   CK(stencil_jacobi(L.vx, L.vy, L.vz, L.st, L.dinv, b, L.xt, xout, w, false, ctx->stream));
+  return DGMG_OK;
+}
+
+// u_hat ~ A_hat^-1 r_hat by `cycles` AMG V-cycles: the first from zero, each
+// further one on the current coarse residual (stationary iteration).
+dgmg_status coarse_correction(dgmg_ctx* ctx, int cycles) {
+  CS(amg_cycle(ctx, 0, ctx->rhat, ctx->uhat));
+  AmgLevel& L = ctx->lv[0];
+  for (int k = 1; k < cycles && ctx->lv.size() > 1; ++k) {
+    // r = r_hat - A_hat u_hat into L.b, correction into L.x, then u_hat += L.x
+    CK(stencil_residual(L.vx, L.vy, L.vz, L.st, ctx->rhat, ctx->uhat, L.b, ctx->stream));
+    CS(amg_cycle(ctx, 0, L.b, L.x));
+    CK(vec_axpby(L.n, 1.0, L.x, 1.0, ctx->uhat, ctx->stream));
+  }
   return DGMG_OK;
 }
 
@@ -347,12 +437,13 @@ dgmg_status restrict_internal(dgmg_ctx* ctx, const void* r, double* rhat, bool f
   return DGMG_OK;
 }
 
-dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, bool fp32);
+dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec);
 
 // ------------------------------------------------------------------ V-cycle
 // One V-cycle of Algorithm 1 on FP64 f, u (u updated in place; zero: u == 0 on entry).
 dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, bool zero) {
-  const bool fp32 = o.smoother_prec == DGMG_FP32;
+  const int prec = o.smoother_prec;
+  const bool fp32 = prec == DGMG_FP32;
   const MeshParams mp = params(ctx);
   const long long n = ctx->ndof;
   void *F, *U, *T1, *T2;
@@ -369,37 +460,34 @@ dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgm
     T1 = ctx->w64[0];
     T2 = ctx->w64[1];
   }
-  CS(smooth_internal(ctx, F, U, T1, o.npre, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, fp32,
-                     zero, nullptr));
+  CS(vcycle_smooth(ctx, o, F, U, T1, o.npre, prec, zero));
   const bool u_zero = zero && o.npre <= 0;
   if (o.coarse == DGMG_COARSE_AMG) {
     // r = f - A u
     if (u_zero) {
       CS(restrict_internal(ctx, F, ctx->rhat, fp32));
     } else {
-      CS(timed_apply(ctx, U, T2, fp32));
+      CS(timed_apply(ctx, U, T2, prec));
       if (fp32)
         CK(vec_sub_f(n, (const float*)F, (const float*)T2, (float*)T2, ctx->stream));
       else
         CK(vec_sub(n, (const double*)F, (const double*)T2, (double*)T2, ctx->stream));
       CS(restrict_internal(ctx, T2, ctx->rhat, fp32));
     }
-    CS(amg_cycle(ctx, 0, ctx->rhat, ctx->uhat));
+    CS(coarse_correction(ctx, o.coarse_cycles));
     CK(ctx->ops->prolong_add(mp, ctx->uhat, U, fp32, ctx->stream));
-    CS(smooth_internal(ctx, F, U, T1, o.npost, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, fp32,
-                       false, nullptr));
+    CS(vcycle_smooth(ctx, o, F, U, T1, o.npost, prec, false));
   } else {
-    CS(smooth_internal(ctx, F, U, T1, o.npost, o.omega, o.eps_inner, o.maxit_inner, o.inner, o.inner_restart, fp32,
-                       u_zero, nullptr));
+    CS(vcycle_smooth(ctx, o, F, U, T1, o.npost, prec, u_zero));
   }
   if (fp32) CK(vec_f2d(n, (const float*)U, u, ctx->stream));
   return DGMG_OK;
 }
 
-dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, bool fp32) {
+dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec) {
   const MeshParams mp = params(ctx);
   const size_t e0 = ctx->timing ? record_event(ctx) : 0;
-  CK(ctx->ops->apply(mp, u, v, fp32, true, ctx->stream));
+  CK(ctx->ops->apply(mp, u, v, prec, true, ctx->stream));
   if (ctx->timing) ctx->ev_apply.push_back({e0, record_event(ctx)});
   ++ctx->n_apply;
   return DGMG_OK;
@@ -427,7 +515,10 @@ dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_
   return vcycle_internal(ctx, r, z, o, true);
 }
 
-dgmg_status apply64(dgmg_ctx* ctx, const double* u, double* v) { return timed_apply(ctx, u, v, false); }
+// Outer Krylov operator: FP64 vectors, FP64 or double-float arithmetic.
+dgmg_status apply64(dgmg_ctx* ctx, const double* u, double* v, int prec = DGMG_FP64) {
+  return timed_apply(ctx, u, v, prec == DGMG_DF64 ? DGMG_DF64 : DGMG_FP64);
+}
 
 dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, dgmg_solve_stats& st) {
   const long long n = ctx->ndof;
@@ -455,7 +546,7 @@ dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve
   CS(dot(ctx, r, z, rz));
   dgmg_status result = DGMG_ERR_NOT_CONVERGED;
   for (int it = 1; it <= o.maxit; ++it) {
-    CS(apply64(ctx, p, q));
+    CS(apply64(ctx, p, q, o.apply_prec));
     double pq;
     CS(dot(ctx, p, q, pq));
     if (!(pq > 0.0)) {
@@ -529,7 +620,7 @@ dgmg_status solve_fgmres(dgmg_ctx* ctx, const double* f, double* u, const dgmg_s
     bool done = false;
     for (int j = 0; j < m; ++j) {
       CS(precond(ctx, V[j], Z[j], o));
-      CS(apply64(ctx, Z[j], V[j + 1]));
+      CS(apply64(ctx, Z[j], V[j + 1], o.apply_prec));
       CS(multi_dot(ctx, j + 1, V.data(), V[j + 1], h.data()));
       for (int i = 0; i <= j; ++i) CK(vec_axpby(n, -h[i], V[i], 1.0, V[j + 1], ctx->stream));
       CS(multi_dot(ctx, j + 1, V.data(), V[j + 1], h2.data()));
@@ -606,6 +697,9 @@ void dgmg_default_opts(dgmg_solve_opts* o) {
   o->inner_restart = 12;
   o->coarse = DGMG_COARSE_AMG;
   o->timing = 0;
+  o->coarse_cycles = 1;
+  o->smoother = DGMG_SMOOTHER_JACOBI;
+  o->apply_prec = DGMG_FP64;
 }
 
 dgmg_status dgmg_create(dgmg_ctx** out, int device, void* cuda_stream) {
@@ -761,7 +855,14 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
     const bool coarsest = L.n <= 512;
     if (!coarsest) {
       std::vector<double> dinv(L.n);
-      for (long long i = 0; i < L.n; ++i) dinv[i] = 1.0 / st[27 * i + 13];
+      double gmax = 0.0;
+      for (long long i = 0; i < L.n; ++i) {
+        dinv[i] = 1.0 / st[27 * i + 13];
+        double row = 0.0;
+        for (int k = 0; k < 27; ++k) row += std::fabs(st[27 * i + k]);
+        gmax = std::max(gmax, row * std::fabs(dinv[i]));
+      }
+      L.omega = 4.0 / (3.0 * gmax);
       CS(dalloc(ctx, &L.st, 27 * L.n));
       CS(dalloc(ctx, &L.dinv, L.n));
       CK(cudaMemcpyAsync(L.st, st.data(), 27 * L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
@@ -832,16 +933,18 @@ dgmg_status dgmg_assemble_rhs(dgmg_ctx* ctx, const double* f_qp, const double* g
 dgmg_status dgmg_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec) {
   CS(ready(ctx));
   if (!u || !v || u == v) return fail(ctx, DGMG_ERR_ARG, "u, v must be distinct non-NULL device pointers");
-  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
-  CK(ctx->ops->apply(params(ctx), u, v, prec == DGMG_FP32, true, ctx->stream));
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CS(check_df64(ctx, prec, DGMG_INNER_PCG));
+  CK(ctx->ops->apply(params(ctx), u, v, prec, true, ctx->stream));
   return DGMG_OK;
 }
 
 dgmg_status dgmg_block_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec) {
   CS(ready(ctx));
   if (!u || !v || u == v) return fail(ctx, DGMG_ERR_ARG, "u, v must be distinct non-NULL device pointers");
-  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
-  CK(ctx->ops->apply(params(ctx), u, v, prec == DGMG_FP32, false, ctx->stream));
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CS(check_df64(ctx, prec, DGMG_INNER_PCG));
+  CK(ctx->ops->apply(params(ctx), u, v, prec, false, ctx->stream));
   return DGMG_OK;
 }
 
@@ -859,10 +962,21 @@ dgmg_status dgmg_block_smooth(dgmg_ctx* ctx, const void* f, void* u, int nsweep,
   CS(ready(ctx));
   if (!f || !u || f == u) return fail(ctx, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
   if (nsweep < 0 || !(eps >= 0.0) || !std::isfinite(omega)) return fail(ctx, DGMG_ERR_ARG, "bad sweep arguments");
-  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
-  const bool fp32 = prec == DGMG_FP32;
-  void* tmp = fp32 ? (void*)ctx->w32[3] : (void*)ctx->w64[2];
-  return smooth_internal(ctx, f, u, tmp, nsweep, omega, eps, maxit, inner, inner_restart, fp32, false, inner_its);
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CS(check_df64(ctx, prec, inner));
+  void* tmp = prec == DGMG_FP32 ? (void*)ctx->w32[3] : (void*)ctx->w64[2];
+  return smooth_internal(ctx, f, u, tmp, nsweep, omega, eps, maxit, inner, inner_restart, prec, false, inner_its);
+}
+
+dgmg_status dgmg_block_sor(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega, double eps, int maxit,
+                           int inner, int inner_restart, int symmetric, dgmg_prec prec, int* inner_its) {
+  CS(ready(ctx));
+  if (!f || !u || f == u) return fail(ctx, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
+  if (nsweep < 0 || !(eps >= 0.0) || !std::isfinite(omega)) return fail(ctx, DGMG_ERR_ARG, "bad sweep arguments");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CS(check_df64(ctx, prec, inner));
+  return sor_internal(ctx, f, u, nsweep, omega, eps, maxit, inner, inner_restart, prec, false, symmetric != 0,
+                      inner_its);
 }
 
 dgmg_status dgmg_restrict(dgmg_ctx* ctx, const void* r, double* r_hat, dgmg_prec prec) {
@@ -910,6 +1024,9 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   if (opts) o = *opts;
   if (!(o.rtol > 0.0) || o.maxit < 1) return fail(ctx, DGMG_ERR_ARG, "rtol > 0 and maxit >= 1 required");
   if (o.krylov < DGMG_KRYLOV_CG || o.krylov > DGMG_KRYLOV_FGMRES) return fail(ctx, DGMG_ERR_ARG, "bad krylov");
+  if (o.smoother_prec < DGMG_FP64 || o.smoother_prec > DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad smoother_prec");
+  CS(check_df64(ctx, o.smoother_prec, o.inner));
+  CS(check_df64(ctx, o.apply_prec, DGMG_INNER_PCG));
   dgmg_solve_stats st;
   std::memset(&st, 0, sizeof(st));
   const auto t0 = std::chrono::steady_clock::now();

@@ -27,6 +27,9 @@
 //          (Sec. 3.2, eq. block_diag_apply).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "dfloat.cuh"
 #include "dgmg_internal.h"
 
 #ifndef DGMG_N
@@ -61,6 +64,7 @@ struct Tab {
 
 __constant__ Tab<double> c_tab_d;
 __constant__ Tab<float> c_tab_f;
+__constant__ Tab<df> c_tab_df;
 
 template <typename T>
 __device__ __forceinline__ const Tab<T>& tab();
@@ -68,6 +72,8 @@ template <>
 __device__ __forceinline__ const Tab<double>& tab<double>() { return c_tab_d; }
 template <>
 __device__ __forceinline__ const Tab<float>& tab<float>() { return c_tab_f; }
+template <>
+__device__ __forceinline__ const Tab<df>& tab<df>() { return c_tab_df; }
 
 // Mesh scalars and coefficient records in the kernel's precision (no
 // double arithmetic in the float kernels: the FP64 pipe is 1/64 of FP32).
@@ -76,16 +82,33 @@ template <> struct Prec<double> {
   static __device__ __forceinline__ double ih(const MeshParams& m, int d) { return m.ih[d]; }
   static __device__ __forceinline__ double area(const MeshParams& m, int d) { return m.area[d]; }
   static __device__ __forceinline__ double jh(const MeshParams& m, int d) { return m.jh[d]; }
-  static __device__ __forceinline__ const double* rec(const MeshParams& m) { return m.rec64; }
+  static __device__ __forceinline__ double rec(const MeshParams& m, long long i) { return m.rec64[i]; }
   static __device__ __forceinline__ double bv(const MeshParams& m, long long i) { return __ldg(m.bvert + i); }
 };
 template <> struct Prec<float> {
   static __device__ __forceinline__ float ih(const MeshParams& m, int d) { return m.ihf[d]; }
   static __device__ __forceinline__ float area(const MeshParams& m, int d) { return m.areaf[d]; }
   static __device__ __forceinline__ float jh(const MeshParams& m, int d) { return m.jhf[d]; }
-  static __device__ __forceinline__ const float* rec(const MeshParams& m) { return m.rec32; }
+  static __device__ __forceinline__ float rec(const MeshParams& m, long long i) { return m.rec32[i]; }
   static __device__ __forceinline__ float bv(const MeshParams& m, long long i) { return __ldg(m.bvert32 + i); }
 };
+// double-float: the FP64 values split once per use (few per cell)
+template <> struct Prec<df> {
+  static __device__ __forceinline__ df ih(const MeshParams& m, int d) { return df(m.ih[d]); }
+  static __device__ __forceinline__ df area(const MeshParams& m, int d) { return df(m.area[d]); }
+  static __device__ __forceinline__ df jh(const MeshParams& m, int d) { return df(m.jh[d]); }
+  static __device__ __forceinline__ df rec(const MeshParams& m, long long i) { return df(m.rec64[i]); }
+  static __device__ __forceinline__ df bv(const MeshParams& m, long long i) { return df(__ldg(m.bvert + i)); }
+};
+
+// Values in global memory (G) and in the kernel's arithmetic (T): the same
+// type, except double-float arithmetic on FP64 vectors.
+template <typename T> struct Store { using type = T; };
+template <> struct Store<df> { using type = double; };
+
+__device__ __forceinline__ float shfl_x(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df shfl_x(df v, int o) { return shfl_xor(v, o); }
 
 // Per-cell coefficients and face data staged in shared memory (computed
 // once per cell; faces f = 2d + s, s = 0 low side, 1 high side).
@@ -265,9 +288,9 @@ __device__ __forceinline__ void contract_scaled(const T* __restrict__ in, T* __r
 //   under the Gauss rule: 8 contractions (9 with c), no pointwise work.
 //  b != 0: the three stages of Sec. 3.1 at the Gauss points (B, fused
 //   Dg / coefficients / Dg^T, B^T), since b varies inside the cell.
-template <bool ADV, bool REACT, typename T>
+template <bool ADV, typename T>
 __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane, const CellInfo<T>* ci,
-                                       const unsigned char* act) {
+                                       const unsigned char* act, bool react) {
   const Tab<T>& t = tab<T>();
   if (!ADV) {
     contract<2, false, false>(X, S0, t.M1, lane, act);          // a = M_z u
@@ -285,7 +308,7 @@ __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane,
     contract<1, false, false>(S0, S1, t.M1, lane, act);         // f = M_y e
     __syncwarp();
     contract_scaled<2, true, 2>(S1, Y, t.S1, lane, act, ci);    // Y += kz S_z f
-    if (REACT) {
+    if (react) {
       __syncwarp();
       contract_scaled<2, true, 3>(S1, Y, t.M1, lane, act, ci);  // Y += c|J| M_z f
     }
@@ -298,11 +321,11 @@ __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane,
   __syncwarp();
   contract<2, false, false>(S1, S0, t.B, lane, act);   // S0 = u at the Gauss points
   __syncwarp();
-  grad_pass<0, false, ADV, REACT>(S0, S1, lane, ci, act);
+  grad_pass<0, false, ADV, true>(S0, S1, lane, ci, act);   // c|J| = 0 without reaction
   __syncwarp();
-  grad_pass<1, true, ADV, REACT>(S0, S1, lane, ci, act);
+  grad_pass<1, true, ADV, false>(S0, S1, lane, ci, act);
   __syncwarp();
-  grad_pass<2, true, ADV, REACT>(S0, S1, lane, ci, act);
+  grad_pass<2, true, ADV, false>(S0, S1, lane, ci, act);
   __syncwarp();
   contract<2, true, false>(S1, S0, t.B, lane, act);
   __syncwarp();
@@ -316,8 +339,8 @@ __device__ __forceinline__ void volume(const T* X, T* Y, T* S0, T* S1, int lane,
 // every active cell, added to Y.  The lines along D give both faces' node
 // grids, so each own line is loaded once for the two faces.  F points to
 // 4 * LINES scratch values (qv, qdv of face 0, then of face 1).
-template <int D, bool FULL, typename T>
-__device__ __forceinline__ void faces_diffusion_dir(const T* X, T* Y, T* F, const T* __restrict__ gu,
+template <int D, bool FULL, typename T, typename G>
+__device__ __forceinline__ void faces_diffusion_dir(const T* X, T* Y, T* F, const G* __restrict__ gu,
                                                     const MeshParams& mp, int lane, const unsigned char* act,
                                                     const CellInfo<T>* ci) {
   const Tab<T>& t = tab<T>();
@@ -347,10 +370,10 @@ __device__ __forceinline__ void faces_diffusion_dir(const T* X, T* Y, T* F, cons
         const T gam = ci[cw].gam[f];
         T tout = T(0), dno = T(0);
         if (FULL && kind == 0) {
-          const T* xo = gu + ci[cw].nb[f] * N3 + (base - cw * N3);
+          const G* xo = gu + ci[cw].nb[f] * N3 + (base - cw * N3);
           T y[N];
 #pragma unroll
-          for (int j = 0; j < N; ++j) y[j] = xo[j * st];
+          for (int j = 0; j < N; ++j) y[j] = T(xo[j * st]);
           tout = y[S ? 0 : N - 1];
 #pragma unroll
           for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], y[j], dno);
@@ -418,8 +441,8 @@ __device__ __forceinline__ void faces_diffusion_dir(const T* X, T* Y, T* F, cons
 
 // Upwind term of face (D, S): int_F Phi(u_in, u_out, b.n) v_in at the face
 // Gauss points (b.n from the bilinear interpolation of the face corners).
-template <int D, int S, bool FULL, typename T>
-__device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, const T* __restrict__ gu,
+template <int D, int S, bool FULL, typename T, typename G>
+__device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, const G* __restrict__ gu,
                                             const MeshParams& mp, long long cell0, int lane,
                                             const unsigned char* act, const CellInfo<T>* ci) {
   const Tab<T>& t = tab<T>();
@@ -436,7 +459,7 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
     const int kind = act[cw] ? ci[cw].kind[2 * D + S] : 2;
     if (kind != 2) {
       tin = X[base + lin * st];
-      if (kind == 0 && FULL) tout = gu[ci[cw].nb[2 * D + S] * N3 + (base - cw * N3) + lout * st];
+      if (kind == 0 && FULL) tout = T(gu[ci[cw].nb[2 * D + S] * N3 + (base - cw * N3) + lout * st]);
     }
     F0[L] = tin;
     F1[L] = tout;
@@ -541,8 +564,8 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
 
 // F0 must be followed by 4 * LINES values of scratch (F0, F1 and the
 // reduction area are contiguous in every kernel's shared-memory carve).
-template <bool FULL, bool ADV, typename T>
-__device__ __forceinline__ void all_faces(const T* X, T* Y, T* F0, T* F1, const T* gu, const MeshParams& mp,
+template <bool FULL, bool ADV, typename T, typename G>
+__device__ __forceinline__ void all_faces(const T* X, T* Y, T* F0, T* F1, const G* gu, const MeshParams& mp,
                                           long long cell0, int lane, const unsigned char* act,
                                           const CellInfo<T>* ci) {
   faces_diffusion_dir<0, FULL>(X, Y, F0, gu, mp, lane, act, ci);
@@ -559,26 +582,51 @@ __device__ __forceinline__ void all_faces(const T* X, T* Y, T* F0, T* F1, const 
 }
 
 // Stage the per-cell coefficients of the warp's cells; act[cw] = cell exists.
+// Global cell of each slot of a warp: the CPW consecutive cells from cell0, or
+// (color >= 0) the cells of one parity class (cx, cy, cz) = (kx, ky, kz) mod 2,
+// color = kx + 2 ky + 4 kz, enumerated x fastest.  -1 = no cell.
+__device__ __forceinline__ long long colored_cell(const MeshParams& mp, int color, long long j) {
+  const int kx = color & 1, ky = (color >> 1) & 1, kz = color >> 2;
+  const long long mx = (mp.nx - kx + 1) / 2, my = (mp.ny - ky + 1) / 2;
+  const long long jx = j % mx, t = j / mx, jy = t % my, jz = t / my;
+  return (2 * jx + kx) + (long long)mp.nx * ((2 * jy + ky) + (long long)mp.ny * (2 * jz + kz));
+}
+
+__device__ __forceinline__ long long color_count(const MeshParams& mp, int color) {
+  if (color < 0) return mp.ncell;
+  const int kx = color & 1, ky = (color >> 1) & 1, kz = color >> 2;
+  return (long long)((mp.nx - kx + 1) / 2) * ((mp.ny - ky + 1) / 2) * ((mp.nz - kz + 1) / 2);
+}
+
+__device__ __forceinline__ void slot_cells(const MeshParams& mp, int color, long long s0, int lane, long long* cid) {
+  if (lane < CPW) {
+    const long long j = s0 + lane;
+    const long long total = color_count(mp, color);
+    cid[lane] = j < total ? (color < 0 ? j : colored_cell(mp, color, j)) : -1;
+  }
+  __syncwarp();
+}
+
 template <typename T>
 __device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell0, int lane, CellInfo<T>* ci,
-                                            unsigned char* act) {
+                                            unsigned char* act, const long long* cid = nullptr) {
   if (lane < CPW) {
-    const long long c = cell0 + lane;
-    const bool ok = c < mp.ncell;
+    const long long c = cid ? cid[lane] : cell0 + lane;
+    const bool ok = c >= 0 && c < mp.ncell;
     act[lane] = ok ? 1 : 0;
     if (ok) {
-      const T* r = Prec<T>::rec(mp) + c * kRecLen;
+      const long long r = c * kRecLen;
       for (int d = 0; d < 3; ++d) {
-        ci[lane].kd[d] = r[kRecKd + d];
+        ci[lane].kd[d] = Prec<T>::rec(mp, r + kRecKd + d);
         ci[lane].jh[d] = Prec<T>::jh(mp, d);
       }
-      ci[lane].cJ = r[kRecCJ];
+      ci[lane].cJ = Prec<T>::rec(mp, r + kRecCJ);
       for (int f = 0; f < 6; ++f) {
         long long nb = -1;
         ci[lane].kind[f] = face_kind(mp, c, f >> 1, f & 1, nb);
         ci[lane].nb[f] = nb;
-        ci[lane].kap[f] = r[kRecKap + f];
-        ci[lane].gam[f] = r[kRecGam + f];
+        ci[lane].kap[f] = Prec<T>::rec(mp, r + kRecKap + f);
+        ci[lane].gam[f] = Prec<T>::rec(mp, r + kRecGam + f);
       }
       if (mp.bvert) {
         int cx, cy, cz;
@@ -598,13 +646,14 @@ __device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell
 template <typename T>
 struct WarpMem {
   static __host__ __device__ constexpr size_t bytes(int nvec) {
-    return align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T)) + align16(CPW * sizeof(CellInfo<T>)) + 16;
+    return align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T)) + align16(CPW * sizeof(CellInfo<T>)) + 16 +
+           align16(CPW * sizeof(long long));
   }
 };
 
 template <typename T>
 __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T** F0, T** F1, T** red,
-                                      CellInfo<T>** ci, unsigned char** act) {
+                                      CellInfo<T>** ci, unsigned char** act, long long** cid = nullptr) {
   T* p = reinterpret_cast<T*>(raw);
   for (int k = 0; k < nvec; ++k) vec[k] = p + k * VEC;
   *F0 = p + nvec * VEC;
@@ -613,10 +662,12 @@ __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T**
   unsigned char* tail = raw + align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T));
   *ci = reinterpret_cast<CellInfo<T>*>(tail);
   *act = tail + align16(CPW * sizeof(CellInfo<T>));
+  if (cid) *cid = reinterpret_cast<long long*>(*act + 16);
 }
 
-template <typename T, bool FULL, bool ADV, bool REACT>
-__global__ void __launch_bounds__(WPB * 32) k_apply(MeshParams mp, const T* __restrict__ u, T* __restrict__ v) {
+template <typename T, bool FULL, bool ADV, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(WPB * 32) k_apply(MeshParams mp, const G* __restrict__ u, G* __restrict__ v) {
+  const bool react = mp.c != nullptr;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long cell0 = ((long long)blockIdx.x * WPB + warp) * CPW;
@@ -629,13 +680,13 @@ __global__ void __launch_bounds__(WPB * 32) k_apply(MeshParams mp, const T* __re
   T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
   stage_cells(mp, cell0, lane, ci, act);
   const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
-  const T* ug = u + cell0 * N3;
-  for (int e = lane; e < VEC; e += 32) X[e] = e < nval ? ug[e] : T(0);
+  const G* ug = u + cell0 * N3;
+  for (int e = lane; e < VEC; e += 32) X[e] = e < nval ? T(ug[e]) : T(0);
   __syncwarp();
-  volume<ADV, REACT>(X, Y, S0, S1, lane, ci, act);
+  volume<ADV>(X, Y, S0, S1, lane, ci, act, react);
   all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
-  T* vg = v + cell0 * N3;
-  for (int e = lane; e < nval; e += 32) vg[e] = Y[e];
+  G* vg = v + cell0 * N3;
+  for (int e = lane; e < nval; e += 32) vg[e] = static_cast<G>(Y[e]);
 }
 
 // Sum over the lanes that own lines of the same cell; every lane of that cell
@@ -644,7 +695,7 @@ template <typename T>
 __device__ __forceinline__ T cell_sum(T part, int lane, T* red) {
   if (CPW == 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULLMASK, part, o);
+    for (int o = 16; o > 0; o >>= 1) part += shfl_x(part, o);
     return part;
   } else {
     red[lane] = part;
@@ -663,32 +714,38 @@ __device__ __forceinline__ T cell_sum(T part, int lane, T* red) {
 // Block-Jacobi sweep with inner PCG (Algorithm 2; inner solve Sec. 2.2.1).
 // Each lane owns the z-lines L = lane + 32k (elements base + N2 iz) for the
 // pointwise vector operations, so all of its elements belong to one cell.
-template <typename T, bool ADV, bool REACT, bool ZERO>
-__global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T* __restrict__ f,
-                                                         const T* __restrict__ uold, T* __restrict__ unew,
-                                                         const T* __restrict__ diag, T omega, T eps,
-                                                         int maxit, int* __restrict__ its) {
+template <typename T, bool ADV, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const G* __restrict__ f,
+                                                         const G* uold, G* unew, const G* __restrict__ diag,
+                                                         T omega, T eps, int maxit, int* __restrict__ its,
+                                                         int color) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long cell0 = ((long long)blockIdx.x * WPB + warp) * CPW;
-  if (cell0 >= mp.ncell) return;
+  const long long s0 = ((long long)blockIdx.x * WPB + warp) * CPW;
+  if (s0 >= color_count(mp, color)) return;
   T* vec[6];
   T *F0, *F1, *red;
   CellInfo<T>* ci;
   unsigned char* act;
-  carve(smem + warp * WarpMem<T>::bytes(6), 6, vec, &F0, &F1, &red, &ci, &act);
+  long long* cid;
+  carve(smem + warp * WarpMem<T>::bytes(6), 6, vec, &F0, &F1, &red, &ci, &act, &cid);
   T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3], *R = vec[4], *DL = vec[5];
-  stage_cells(mp, cell0, lane, ci, act);
-  const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
-  const long long g0 = cell0 * N3;
+  const bool react = mp.c != nullptr;
+  const bool zero = uold == nullptr;   // first sweep from u = 0: no defect apply
+  slot_cells(mp, color, s0, lane, cid);
+  stage_cells(mp, 0, lane, ci, act, cid);
+  const long long cell0 = cid[0];
   // my cell slot (lanes without a line: -1)
   const int mycw = lane < LINES ? lane / N2 : -1;
   const bool mine = mycw >= 0 && act[mycw];
   // defect d = f - A u_old
-  if (!ZERO) {
-    for (int e = lane; e < VEC; e += 32) P[e] = e < nval ? uold[g0 + e] : T(0);
+  if (!zero) {
+    for (int e = lane; e < VEC; e += 32) {
+      const int cw = e / N3;
+      P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
+    }
     __syncwarp();
-    volume<ADV, REACT>(P, Q, S0, S1, lane, ci, act);
+    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
     all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
   }
   T prr = T(0), prz = T(0);
@@ -696,11 +753,12 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
     int cw, base, st, a, b;
     line_geom<2>(L, cw, base, st, a, b);
     if (!act[cw]) continue;
+    const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int e = base + i * N2;
-      const T r = f[g0 + e] - (ZERO ? T(0) : Q[e]);
-      const T z = r * diag[g0 + e];
+      const T r = T(f[gb + e]) - (zero ? T(0) : Q[e]);
+      const T z = r * T(diag[gb + e]);
       R[e] = r;
       P[e] = z;
       DL[e] = T(0);
@@ -710,17 +768,32 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
   }
   const T rr0 = cell_sum(prr, lane, red);
   T rz = cell_sum(prz, lane, red);
-  // Stop at ||r|| <= eps ||d||, compared as norms: eps^2 ||d||^2 can underflow
-  // in FP32 for cells whose defect is tiny.
-  const T thr = eps * sqrt(rr0);
+  // The inner solve works on d / ||d|| (and scales the correction back):
+  // FP32 products of a tiny defect would otherwise lose precision in the
+  // subnormal range.  The stopping test ||r|| <= eps ||d|| becomes ||r|| <= eps.
+  const T dnorm = sqrt(rr0);
+  const T isc = rr0 > T(0) ? T(1) / dnorm : T(0);
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<2>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int e = base + i * N2;
+      R[e] = R[e] * isc;
+      P[e] = P[e] * isc;
+    }
+  }
+  rz = rz * isc * isc;
+  const T thr = eps;
   bool live = mine && rr0 > T(0);
   int it = 0;
   while (__any_sync(FULLMASK, live && it < maxit)) {
     if (lane < LINES) act[mycw] = (live && it < maxit) ? 1 : 0;
     __syncwarp();
     const bool run = live && it < maxit;
-    volume<ADV, REACT>(P, Q, S0, S1, lane, ci, act);
-    all_faces<false, ADV>(P, Q, F0, F1, (const T*)nullptr, mp, cell0, lane, act, ci);
+    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+    all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
     T ppq = T(0);
     if (run) {
       for (int L = lane; L < LINES; L += 32) {
@@ -761,10 +834,11 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
       for (int L = lane; L < LINES; L += 32) {
         int cw, base, st, a, b;
         line_geom<2>(L, cw, base, st, a, b);
+        const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const int e = base + i * N2;
-          const T z = R[e] * diag[g0 + e];
+          const T z = R[e] * T(diag[gb + e]);
           S0[e] = z;
           prz2 = fma(R[e], z, prz2);
         }
@@ -786,18 +860,21 @@ __global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const T*
     }
     __syncwarp();
   }
-  // u_new = u_old + omega delta
+  // u_new = u_old + omega delta (in place is allowed: a launch touches only its
+  // own cells' values, and reads neighbours only of other colours)
   for (int L = lane; L < LINES; L += 32) {
     int cw, base, st, a, b;
     line_geom<2>(L, cw, base, st, a, b);
-    if (cell0 + cw >= mp.ncell) continue;
+    if (cid[cw] < 0) continue;
+    const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const long long g = g0 + base + i * N2;
-      unew[g] = ZERO ? omega * DL[base + i * N2] : fma(omega, DL[base + i * N2], uold[g]);
+      const long long g = gb + base + i * N2;
+      const T dl = DL[base + i * N2] * dnorm;
+      unew[g] = static_cast<G>(zero ? omega * dl : fma(omega, dl, T(uold[g])));
     }
   }
-  if (its && lane < LINES && (lane % N2) == 0 && cell0 + mycw < mp.ncell) its[cell0 + mycw] = it;
+  if (its && lane < LINES && (lane % N2) == 0 && cid[mycw] >= 0) its[cid[mycw]] = it;
 }
 
 // Per-cell scalars of the inner GMRES(m): Hessenberg (m+1) x m, g, Givens
@@ -811,19 +888,18 @@ __host__ __device__ constexpr int gmres_scalars(int m) { return (m + 1) * m + 4 
 // |g_{j+1}| <= eps ||d|| or after maxit iterations; x += sum_i y_i V_i / diag;
 // restart from the recomputed residual d - D_T x.  The warp count per block is
 // blockDim.x / 32 (the basis needs (m+1) vectors per warp).
-template <typename T, bool ADV, bool REACT, bool ZERO>
-__global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __restrict__ f,
-                                                      const T* __restrict__ uold, T* __restrict__ unew,
-                                                      const T* __restrict__ diag, T omega, T eps, int maxit, int m,
-                                                      int* __restrict__ its) {
+template <typename T, bool ADV, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __restrict__ f, const G* uold,
+                                                      G* unew, const G* __restrict__ diag, T omega, T eps,
+                                                      int maxit, int m, int* __restrict__ its, int color) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  const long long cell0 = ((long long)blockIdx.x * wpb + warp) * CPW;
-  if (cell0 >= mp.ncell) return;
+  const long long s0 = ((long long)blockIdx.x * wpb + warp) * CPW;
+  if (s0 >= color_count(mp, color)) return;
   const int nvec = m + 7;
   const size_t tbytes = align16((size_t)(nvec * VEC + 5 * LINES + CPW * gmres_scalars(m)) * sizeof(T));
-  const size_t wbytes = tbytes + align16(CPW * sizeof(CellInfo<T>)) + 16;
+  const size_t wbytes = tbytes + align16(CPW * sizeof(CellInfo<T>)) + 16 + align16(CPW * sizeof(long long));
   unsigned char* base = smem + warp * wbytes;
   T* p = reinterpret_cast<T*>(base);
   T* V = p;                      // m+1 basis vectors
@@ -831,6 +907,8 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
   T* Q = Z + VEC;                // block-apply output
   T* S0 = Q + VEC;
   T* S1 = S0 + VEC;
+  const bool react = mp.c != nullptr;
+  const bool zero = uold == nullptr;
   T* DD = S1 + VEC;              // defect d
   T* X = DD + VEC;               // accumulated correction
   T* F0 = X + VEC;
@@ -839,9 +917,10 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
   T* sc = red + 3 * LINES;       // CPW * gmres_scalars(m)
   CellInfo<T>* ci = reinterpret_cast<CellInfo<T>*>(base + tbytes);
   unsigned char* act = base + tbytes + align16(CPW * sizeof(CellInfo<T>));
-  stage_cells(mp, cell0, lane, ci, act);
-  const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
-  const long long g0 = cell0 * N3;
+  long long* cid = reinterpret_cast<long long*>(act + 16);
+  slot_cells(mp, color, s0, lane, cid);
+  stage_cells(mp, 0, lane, ci, act, cid);
+  const long long cell0 = cid[0];
   const int mycw = lane < LINES ? lane / N2 : -1;
   const bool mine = mycw >= 0 && act[mycw];
   const bool lead = lane < LINES && (lane % N2) == 0;    // writes the cell's scalars
@@ -851,10 +930,13 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
   T* sn = cs + m;
   T* yv = sn + m;
   // defect d = f - A u_old
-  if (!ZERO) {
-    for (int e = lane; e < VEC; e += 32) Z[e] = e < nval ? uold[g0 + e] : T(0);
+  if (!zero) {
+    for (int e = lane; e < VEC; e += 32) {
+      const int cw = e / N3;
+      Z[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
+    }
     __syncwarp();
-    volume<ADV, REACT>(Z, Q, S0, S1, lane, ci, act);
+    volume<ADV>(Z, Q, S0, S1, lane, ci, act, react);
     all_faces<true, ADV>(Z, Q, F0, F1, uold, mp, cell0, lane, act, ci);
   }
   T pdd = T(0);
@@ -862,31 +944,44 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
     int cw, b0, st, a, b;
     line_geom<2>(L, cw, b0, st, a, b);
     if (!act[cw]) continue;
+    const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int e = b0 + i * N2;
-      const T d = f[g0 + e] - (ZERO ? T(0) : Q[e]);
+      const T d = T(f[gb + e]) - (zero ? T(0) : Q[e]);
       DD[e] = d;
       X[e] = T(0);
       pdd = fma(d, d, pdd);
     }
   }
-  T beta = sqrt(cell_sum(pdd, lane, red));
-  const T target = eps * beta;
-  bool live = mine && beta > T(0) && beta > target;
+  // Work on d / ||d|| (subnormal FP32 products otherwise); the correction is
+  // scaled back at the end, and the target eps ||d|| becomes eps.
+  const T dnorm = sqrt(cell_sum(pdd, lane, red));
+  const T isc = dnorm > T(0) ? T(1) / dnorm : T(0);
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, b0, st, a, b;
+    line_geom<2>(L, cw, b0, st, a, b);
+    if (!act[cw]) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i) DD[b0 + i * N2] = DD[b0 + i * N2] * isc;
+  }
+  T beta = dnorm > T(0) ? T(1) : T(0);
+  const T target = eps;
+  bool live = mine && dnorm > T(0) && beta > target;
   int it = 0;
   // residual vector for the first cycle is d itself
   T* Rsrc = DD;
   while (__any_sync(FULLMASK, live && it < maxit)) {
     bool cyc = live && it < maxit;
     // V_0 = r / beta
+    const T ibeta = cyc ? T(1) / beta : T(0);
     for (int L = lane; L < LINES; L += 32) {
       int cw, b0, st, a, b;
       line_geom<2>(L, cw, b0, st, a, b);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int e = b0 + i * N2;
-        if (cyc) V[e] = Rsrc[e] / beta;
+        if (cyc) V[e] = Rsrc[e] * ibeta;
       }
     }
     if (lead && cyc) {
@@ -904,15 +999,16 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
         int cw, b0, st, a, b;
         line_geom<2>(L, cw, b0, st, a, b);
         if (!cyc) continue;
+        const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const int e = b0 + i * N2;
-          Z[e] = Vj[e] * diag[g0 + e];
+          Z[e] = Vj[e] * T(diag[gb + e]);
         }
       }
       __syncwarp();
-      volume<ADV, REACT>(Z, Q, S0, S1, lane, ci, act);
-      all_faces<false, ADV>(Z, Q, F0, F1, (const T*)nullptr, mp, cell0, lane, act, ci);
+      volume<ADV>(Z, Q, S0, S1, lane, ci, act, react);
+      all_faces<false, ADV>(Z, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
       // modified Gram-Schmidt
       for (int i = 0; i <= j; ++i) {
         const T* Vi = V + i * VEC;
@@ -985,7 +1081,7 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
     if (lead && ran) {
       for (int i = jdone - 1; i >= 0; --i) {
         T s = gv[i];
-        for (int l = i + 1; l < jdone; ++l) s -= H[i * m + l] * yv[l];
+        for (int l = i + 1; l < jdone; ++l) s = s - H[i * m + l] * yv[l];
         yv[i] = s / H[i * m + i];
       }
     }
@@ -994,20 +1090,21 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
       for (int L = lane; L < LINES; L += 32) {
         int cw, b0, st, a, b;
         line_geom<2>(L, cw, b0, st, a, b);
+        const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           const int e = b0 + k * N2;
           T s = T(0);
           for (int i = 0; i < jdone; ++i) s = fma(yv[i], V[i * VEC + e], s);
-          X[e] = fma(s, diag[g0 + e], X[e]);
+          X[e] = fma(s, T(diag[gb + e]), X[e]);
         }
       }
     }
     // r = d - D_T x; beta = ||r||
     if (lane < LINES) act[mycw] = ran ? 1 : 0;
     __syncwarp();
-    volume<ADV, REACT>(X, Q, S0, S1, lane, ci, act);
-    all_faces<false, ADV>(X, Q, F0, F1, (const T*)nullptr, mp, cell0, lane, act, ci);
+    volume<ADV>(X, Q, S0, S1, lane, ci, act, react);
+    all_faces<false, ADV>(X, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
     T pr = T(0);
     if (ran) {
       for (int L = lane; L < LINES; L += 32) {
@@ -1033,14 +1130,16 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const T* __
   for (int L = lane; L < LINES; L += 32) {
     int cw, b0, st, a, b;
     line_geom<2>(L, cw, b0, st, a, b);
-    if (cell0 + cw >= mp.ncell) continue;
+    if (cid[cw] < 0) continue;
+    const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const long long gi = g0 + b0 + i * N2;
-      unew[gi] = ZERO ? omega * X[b0 + i * N2] : fma(omega, X[b0 + i * N2], uold[gi]);
+      const long long gi = gb + b0 + i * N2;
+      const T x = X[b0 + i * N2] * dnorm;
+      unew[gi] = static_cast<G>(zero ? omega * x : fma(omega, x, T(uold[gi])));
     }
   }
-  if (its && lead && cell0 + mycw < mp.ncell) its[cell0 + mycw] = it;
+  if (its && lead && cid[mycw] >= 0) its[cid[mycw]] = it;
 }
 
 // diag(D_T) by direct quadrature per dof (setup; FP64).
@@ -1236,14 +1335,22 @@ cudaError_t upload_one(const double* h, cudaStream_t s) {
   p += N;
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j) tb.S1[i][j] = T(p[i * N + j]);
-  if (sizeof(T) == 8) return cudaMemcpyToSymbol(c_tab_d, &tb, sizeof(tb));
+  if (std::is_same<T, double>::value) return cudaMemcpyToSymbol(c_tab_d, &tb, sizeof(tb));
+  if (std::is_same<T, df>::value) return cudaMemcpyToSymbol(c_tab_df, &tb, sizeof(tb));
   return cudaMemcpyToSymbol(c_tab_f, &tb, sizeof(tb));
 }
 
 cudaError_t upload_tables(const double* h, cudaStream_t s) {
   cudaError_t e = upload_one<double>(h, s);
   if (e != cudaSuccess) return e;
-  return upload_one<float>(h, s);
+  e = upload_one<float>(h, s);
+  if (e != cudaSuccess) return e;
+  return upload_one<df>(h, s);
+}
+
+inline long long host_color_count(const MeshParams& mp, int color) {
+  const int kx = color & 1, ky = (color >> 1) & 1, kz = color >> 2;
+  return (long long)((mp.nx - kx + 1) / 2) * ((mp.ny - ky + 1) / 2) * ((mp.nz - kz + 1) / 2);
 }
 
 inline unsigned grid_for(long long ncell) {
@@ -1257,80 +1364,94 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
   return cudaSuccess;
 }
 
-template <typename T, bool FULL, bool ADV, bool REACT>
+template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
+  using G = typename Store<T>::type;
   const size_t sm = WPB * WarpMem<T>::bytes(4);
-  auto k = k_apply<T, FULL, ADV, REACT>;
+  auto k = k_apply<T, FULL, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
-  k<<<grid_for(mp.ncell), WPB * 32, sm, s>>>(mp, (const T*)u, (T*)v);
+  k<<<grid_for(mp.ncell), WPB * 32, sm, s>>>(mp, (const G*)u, (G*)v);
   count_launch();
   return cudaGetLastError();
 }
 
 template <typename T, bool FULL>
 cudaError_t apply_t(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
-  const bool adv = mp.bvert != nullptr, react = mp.c != nullptr;
-  if (adv)
-    return react ? launch_apply<T, FULL, true, true>(mp, u, v, s) : launch_apply<T, FULL, true, false>(mp, u, v, s);
-  return react ? launch_apply<T, FULL, false, true>(mp, u, v, s) : launch_apply<T, FULL, false, false>(mp, u, v, s);
+  return mp.bvert ? launch_apply<T, FULL, true>(mp, u, v, s) : launch_apply<T, FULL, false>(mp, u, v, s);
 }
 
-cudaError_t apply(const MeshParams& mp, const void* u, void* v, bool fp32, bool full, cudaStream_t s) {
+cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool full, cudaStream_t s) {
   if (mp.ncell == 0) return cudaSuccess;
-  if (fp32) return full ? apply_t<float, true>(mp, u, v, s) : apply_t<float, false>(mp, u, v, s);
+  if (prec == DGMG_FP32) return full ? apply_t<float, true>(mp, u, v, s) : apply_t<float, false>(mp, u, v, s);
+  if (prec == DGMG_DF64) {
+    // double-float kernels: diffusion operators (b = 0), p <= 6
+#if DGMG_N <= 7
+    if (mp.bvert) return cudaErrorNotSupported;
+    return full ? launch_apply<df, true, false>(mp, u, v, s) : launch_apply<df, false, false>(mp, u, v, s);
+#else
+    return cudaErrorNotSupported;
+#endif
+  }
   return full ? apply_t<double, true>(mp, u, v, s) : apply_t<double, false>(mp, u, v, s);
 }
 
-template <typename T, bool ADV, bool REACT, bool ZERO>
+template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  using G = typename Store<T>::type;
   const size_t sm = WPB * WarpMem<T>::bytes(6);
-  auto k = k_smooth_pcg<T, ADV, REACT, ZERO>;
+  auto k = k_smooth_pcg<T, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
-  k<<<grid_for(mp.ncell), WPB * 32, sm, s>>>(mp, (const T*)a.f, (const T*)a.uold, (T*)a.unew, (const T*)a.diag,
-                                              T(a.omega), T(a.eps), a.maxit, a.its);
+  const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
+  k<<<grid_for(cells), WPB * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const G*)a.diag,
+                                          T(a.omega), T(a.eps), a.maxit, a.its, a.color);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename T, bool ADV, bool REACT, bool ZERO>
+template <typename T, bool ADV>
 cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  using G = typename Store<T>::type;
   const int m = a.restart;
   const size_t wbytes = align16((size_t)((m + 7) * VEC + 5 * LINES + CPW * gmres_scalars(m)) * sizeof(T)) +
-                        align16(CPW * sizeof(CellInfo<T>)) + 16;
+                        align16(CPW * sizeof(CellInfo<T>)) + 16 + align16(CPW * sizeof(long long));
   int wpb = (int)((200 * 1024) / wbytes);
   if (wpb > 4) wpb = 4;
   if (wpb < 1) return cudaErrorInvalidValue;      // restart too large for shared memory
   const size_t sm = wpb * wbytes;
-  auto k = k_smooth_gmres<T, ADV, REACT, ZERO>;
+  auto k = k_smooth_gmres<T, ADV>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const long long groups = (mp.ncell + CPW - 1) / CPW;
+  const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
+  const long long groups = (cells + CPW - 1) / CPW;
   const unsigned grid = (unsigned)((groups + wpb - 1) / wpb);
-  k<<<grid, wpb * 32, sm, s>>>(mp, (const T*)a.f, (const T*)a.uold, (T*)a.unew, (const T*)a.diag, T(a.omega),
-                               T(a.eps), a.maxit, m, a.its);
+  k<<<grid, wpb * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const G*)a.diag, T(a.omega),
+                               T(a.eps), a.maxit, m, a.its, a.color);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename T, bool ADV, bool REACT>
-cudaError_t smooth_z(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
-  if (a.inner == DGMG_INNER_GMRES)
-    return a.uold ? launch_gmres<T, ADV, REACT, false>(mp, a, s) : launch_gmres<T, ADV, REACT, true>(mp, a, s);
-  return a.uold ? launch_smooth<T, ADV, REACT, false>(mp, a, s) : launch_smooth<T, ADV, REACT, true>(mp, a, s);
-}
-
 template <typename T>
 cudaError_t smooth_t(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
-  const bool adv = mp.bvert != nullptr, react = mp.c != nullptr;
-  if (adv) return react ? smooth_z<T, true, true>(mp, a, s) : smooth_z<T, true, false>(mp, a, s);
-  return react ? smooth_z<T, false, true>(mp, a, s) : smooth_z<T, false, false>(mp, a, s);
+  const bool adv = mp.bvert != nullptr;
+  if (a.inner == DGMG_INNER_GMRES) return adv ? launch_gmres<T, true>(mp, a, s) : launch_gmres<T, false>(mp, a, s);
+  return adv ? launch_smooth<T, true>(mp, a, s) : launch_smooth<T, false>(mp, a, s);
 }
 
-cudaError_t smooth(const MeshParams& mp, const SmoothArgs& a, bool fp32, cudaStream_t s) {
+cudaError_t smooth(const MeshParams& mp, const SmoothArgs& a, int prec, cudaStream_t s) {
   if (mp.ncell == 0) return cudaSuccess;
-  return fp32 ? smooth_t<float>(mp, a, s) : smooth_t<double>(mp, a, s);
+  if (prec == DGMG_FP32) return smooth_t<float>(mp, a, s);
+  if (prec == DGMG_DF64) {
+    // double-float smoother: block-Jacobi / SOR with inner PCG, b = 0, p <= 6
+#if DGMG_N <= 7
+    if (mp.bvert || a.inner == DGMG_INNER_GMRES) return cudaErrorNotSupported;
+    return launch_smooth<df, false>(mp, a, s);
+#else
+    return cudaErrorNotSupported;
+#endif
+  }
+  return smooth_t<double>(mp, a, s);
 }
 
 cudaError_t diag(const MeshParams& mp, double* d, cudaStream_t s) {

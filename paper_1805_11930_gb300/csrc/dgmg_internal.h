@@ -70,6 +70,7 @@ struct SmoothArgs {
   int inner;              // DGMG_INNER_PCG / DGMG_INNER_GMRES
   int restart;
   int* its;               // device int[ncell] or nullptr
+  int color = -1;         // -1: all cells (Jacobi); 0..7: one parity class, in place allowed
 };
 
 // Per-order kernel entry points, one table per n (cell_kernels.cu built with
@@ -78,9 +79,10 @@ struct CellOps {
   int n;
   cudaError_t (*upload_tables)(const double* host_tables, cudaStream_t s);
   // full = A (with neighbour terms); !full = block diagonal D.
-  cudaError_t (*apply)(const MeshParams& mp, const void* u, void* v, bool fp32, bool full,
+  // prec: DGMG_FP64, DGMG_FP32 or DGMG_DF64 (FP64 vectors, double-float arithmetic)
+  cudaError_t (*apply)(const MeshParams& mp, const void* u, void* v, int prec, bool full,
                        cudaStream_t s);
-  cudaError_t (*smooth)(const MeshParams& mp, const SmoothArgs& a, bool fp32, cudaStream_t s);
+  cudaError_t (*smooth)(const MeshParams& mp, const SmoothArgs& a, int prec, cudaStream_t s);
   cudaError_t (*diag)(const MeshParams& mp, double* diag, cudaStream_t s);
   cudaError_t (*restrict_cells)(const MeshParams& mp, const void* r, double* corners, bool fp32,
                                 cudaStream_t s);

@@ -18,10 +18,11 @@ from . import build as _build
 DGMG_OK = 0
 STATUS = {0: "DGMG_OK", 1: "DGMG_ERR_ARG", 2: "DGMG_ERR_OOM", 3: "DGMG_ERR_CUDA", 4: "DGMG_ERR_STATE",
           5: "DGMG_ERR_NOT_CONVERGED", 6: "DGMG_ERR_BREAKDOWN", 7: "DGMG_ERR_TIMEOUT"}
-FP64, FP32 = 0, 1
+FP64, FP32, DF64 = 0, 1, 2
 KRYLOV_CG, KRYLOV_FCG, KRYLOV_FGMRES = 0, 1, 2
 INNER_PCG, INNER_GMRES = 0, 1
 COARSE_AMG, COARSE_NONE = 0, 1
+SMOOTHER_JACOBI, SMOOTHER_SSOR = 0, 1
 
 
 class DgmgError(RuntimeError):
@@ -35,7 +36,8 @@ class SolveOpts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("smoother_prec", ctypes.c_int), ("omega", ctypes.c_double),
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("eps_inner", ctypes.c_double),
                 ("maxit_inner", ctypes.c_int), ("inner", ctypes.c_int), ("inner_restart", ctypes.c_int),
-                ("coarse", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("coarse", ctypes.c_int), ("timing", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("apply_prec", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -69,6 +71,7 @@ _SIG = {
     "dgmg_block_apply": (_I, [_P, _P, _P, _I]),
     "dgmg_block_diagonal": (_I, [_P, _P, _I]),
     "dgmg_block_smooth": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, _I, _I, _P]),
+    "dgmg_block_sor": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, _I, _I, _I, _P]),
     "dgmg_restrict": (_I, [_P, _P, _P, _I]),
     "dgmg_prolong_add": (_I, [_P, _P, _P, _I]),
     "dgmg_coarse_matrix": (_I, [_P, _P]),
@@ -124,10 +127,10 @@ def _host(a, dtype=np.float64):
     return arr, arr.ctypes.data
 
 
-def _prec(t):
+def _prec(t, df64=False):
     import torch
     if t.dtype == torch.float64:
-        return FP64
+        return DF64 if df64 else FP64
     if t.dtype == torch.float32:
         return FP32
     raise DgmgError(1, f"unsupported dtype {t.dtype}")
@@ -212,19 +215,26 @@ class Context:
         self._check(self.lib.dgmg_assemble_rhs(self.h, fp, gp, jp, _ptr(rhs)))
 
     # ------------------------------------------------------------ operators
-    def apply(self, u, v):
-        self._check(self.lib.dgmg_apply(self.h, _ptr(u), _ptr(v), _prec(u)))
+    def apply(self, u, v, df64=False):
+        """v = A u; df64=True: FP64 vectors, double-float arithmetic."""
+        self._check(self.lib.dgmg_apply(self.h, _ptr(u), _ptr(v), _prec(u, df64)))
 
-    def block_apply(self, u, v):
-        self._check(self.lib.dgmg_block_apply(self.h, _ptr(u), _ptr(v), _prec(u)))
+    def block_apply(self, u, v, df64=False):
+        self._check(self.lib.dgmg_block_apply(self.h, _ptr(u), _ptr(v), _prec(u, df64)))
 
     def block_diagonal(self, diag):
         self._check(self.lib.dgmg_block_diagonal(self.h, _ptr(diag), _prec(diag)))
 
     def block_smooth(self, f, u, nsweep=1, omega=1.0, eps=1e-2, maxit=0, inner=INNER_PCG, inner_restart=12,
-                     inner_its=None):
+                     inner_its=None, df64=False):
         self._check(self.lib.dgmg_block_smooth(self.h, _ptr(f), _ptr(u), nsweep, omega, eps, maxit, inner,
-                                               inner_restart, _prec(u), _ptr(inner_its)))
+                                               inner_restart, _prec(u, df64), _ptr(inner_its)))
+
+    def block_sor(self, f, u, nsweep=1, omega=1.0, eps=1e-2, maxit=0, inner=INNER_PCG, inner_restart=12,
+                  symmetric=True, inner_its=None, df64=False):
+        self._check(self.lib.dgmg_block_sor(self.h, _ptr(f), _ptr(u), nsweep, omega, eps, maxit, inner,
+                                            inner_restart, 1 if symmetric else 0, _prec(u, df64),
+                                            _ptr(inner_its)))
 
     def restrict(self, r, r_hat):
         self._check(self.lib.dgmg_restrict(self.h, _ptr(r), _ptr(r_hat), _prec(r)))

@@ -152,3 +152,30 @@ def test_fgmres_nonsymmetric():
     assert np.linalg.norm(f - A @ x) <= 1e-10 * np.linalg.norm(f) * 1.0001
     exact = spla.spsolve(A.tocsc(), f)
     assert np.abs(x - exact).max() < 1e-7 * np.abs(exact).max()
+
+
+def test_multicolour_sor_properties():
+    """Colour classes have no face neighbours (so a colour can be updated in
+    parallel); with one cell per colour (2x2x2 mesh) a forward pass with exact
+    blocks is block Gauss-Seidel in colour order, which converges for SPD A;
+    the symmetric sweep makes the smoother operator symmetric."""
+    P = small_problem(p=2, nc=(2, 2, 2), bc=(0,) * 6)
+    A = P.assemble()
+    S = solvers.MulticolourBlockSOR(A, P.N, P.nc, symmetric=True, inner="lu")
+    for c in range(P.ncell):
+        for k in range(3):
+            cx = list(P.cell_coords(c))
+            if cx[k] + 1 < P.nc[k]:
+                cx[k] += 1
+                assert S.colour[c] != S.colour[P.cell_index(*cx)]
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=P.ndof)
+    u = np.zeros_like(f)
+    r0 = np.linalg.norm(f)
+    for _ in range(20):
+        u = S(f, u, 1, 1.0)
+    assert np.linalg.norm(f - A @ u) < 1e-3 * r0
+    x, y = rng.normal(size=P.ndof), rng.normal(size=P.ndof)
+    Sx = S(x, np.zeros_like(x), 1, 1.0)
+    Sy = S(y, np.zeros_like(y), 1, 1.0)
+    assert abs(y @ Sx - x @ Sy) < 1e-10 * abs(y @ Sx)
