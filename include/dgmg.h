@@ -85,6 +85,8 @@ typedef struct {
                        /* over the 8 parity colours per sweep)                    */
   int apply_prec;      /* dgmg_prec of the outer operator applications: FP64      */
                        /* (default) or DF64; the final residual check is FP64    */
+  int graph;           /* 1: capture the preconditioner into a CUDA graph and     */
+                       /* replay it (needs a non-default stream; off when timing) */
 } dgmg_solve_opts;
 
 typedef struct {
@@ -219,6 +221,32 @@ dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_so
  * stats: host or NULL.  Synchronises the stream. */
 dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
                        dgmg_solve_stats* stats);
+
+/* Launch shape of the warp-per-cell operator and smoother kernels.  Each warp
+ * owns whole cells and no two warps share data, so the warps per block (1, 2,
+ * 4 or 8) change only speed, never a result bit.  The best value depends on
+ * order, precision and how many blocks fit per SM, which is why the library
+ * times it instead of fixing it (the paper tunes its kernels to one CPU by
+ * hand; Sec. 3.3).
+ *
+ * dgmg_set_launch_shape sets the warps per block used by dgmg_apply /
+ * dgmg_block_apply (wpb_apply) and by the inner-PCG smoother kernels of
+ * dgmg_block_smooth, dgmg_block_sor, dgmg_vcycle and dgmg_solve (wpb_smooth)
+ * for arithmetic `prec`; 0 restores the default of 4.  A value whose shared
+ * memory does not fit is halved at launch.  Other values: DGMG_ERR_ARG.
+ * The setting belongs to the current mesh: dgmg_set_mesh resets it. */
+dgmg_status dgmg_set_launch_shape(dgmg_ctx* ctx, dgmg_prec prec, int wpb_apply, int wpb_smooth);
+
+/* Times every warps-per-block candidate (1, 2, 4, 8) of the operator kernel
+ * and of one inner-PCG block-Jacobi sweep (eps 1e-2, from u = 0 with f = 1)
+ * on the current mesh and coefficients in arithmetic `prec`, `reps` timed
+ * launches each after one warm-up (reps <= 0 means 3), with CUDA events on the
+ * context's stream, and keeps the fastest of each through
+ * dgmg_set_launch_shape.  wpb_apply, wpb_smooth: host ints receiving the
+ * choices, or NULL.  Allocates three DG vectors for the duration of the call
+ * and synchronises the stream.  DGMG_ERR_ARG for DF64 where dgmg_apply
+ * rejects it, DGMG_ERR_STATE before dgmg_set_coefficients. */
+dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_apply, int* wpb_smooth);
 
 /* Largest grid (nx*ny*nz cells) dgmg_restrict_noalloc accepts. */
 #define DGMG_NOALLOC_MAX_CELLS 131072

@@ -129,7 +129,19 @@ struct dgmg_ctx {
   size_t ev_used = 0;
   std::vector<std::pair<size_t, size_t>> ev_smooth, ev_apply;
   long long n_apply = 0, n_sweep = 0, n_zero_sweep = 0;
+  // Captured preconditioner graphs, keyed by (input, output, options).
+  struct PrecGraph {
+    const double* in;
+    double* out;
+    dgmg_solve_opts opts;
+    cudaGraphExec_t exec;
+    long long d_sweep, d_zero, d_apply, d_tracked;
+    unsigned long long d_launches;
+  };
+  std::vector<PrecGraph> graphs;
   std::vector<void*> mesh_allocs;  // freed on a new mesh
+  // warps per block of the operator / smoother kernels per precision (0 = 4)
+  int wpb_apply[3] = {0, 0, 0}, wpb_smooth[3] = {0, 0, 0};
 };
 
 namespace {
@@ -179,7 +191,13 @@ dgmg_status dalloc(dgmg_ctx* ctx, T** p, size_t count) {
   return DGMG_OK;
 }
 
+void drop_graphs(dgmg_ctx* ctx) {
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+}
+
 void free_mesh(dgmg_ctx* ctx) {
+  drop_graphs(ctx);
   for (void* q : ctx->mesh_allocs) cudaFreeAsync(q, ctx->stream);
   ctx->mesh_allocs.clear();
   ctx->dK = ctx->dc = ctx->db = ctx->diag64 = ctx->dinv64 = ctx->rec64 = nullptr;
@@ -215,6 +233,10 @@ MeshParams params(const dgmg_ctx* ctx) {
   m.rec64 = ctx->rec64;
   m.rec32 = ctx->rec32;
   m.bvert32 = ctx->db32;
+  for (int i = 0; i < 3; ++i) {
+    m.wpb_apply[i] = ctx->wpb_apply[i];
+    m.wpb_smooth[i] = ctx->wpb_smooth[i];
+  }
   const double J = ctx->h[0] * ctx->h[1] * ctx->h[2];
   for (int d = 0; d < 3; ++d) {
     const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
@@ -510,9 +532,64 @@ dgmg_status ensure_krylov(dgmg_ctx* ctx, size_t nvec) {
   return DGMG_OK;
 }
 
-dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_opts& o) {
+dgmg_status precond_eager(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_opts& o) {
   CK(vec_fill(ctx->ndof, 0.0, z, ctx->stream));
   return vcycle_internal(ctx, r, z, o, true);
+}
+
+// z = M r.  With opts.graph the V-cycle (no host synchronisation inside) is
+// captured into a CUDA graph on its second use with the same (r, z, opts) and
+// replayed afterwards, removing the per-kernel launch cost; the launch and
+// sweep counters of the captured work are added on each replay.
+dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_opts& o) {
+  if (!o.graph || ctx->timing || !ctx->stream) return precond_eager(ctx, r, z, o);
+  for (auto& g : ctx->graphs) {
+    if (g.in == r && g.out == z && std::memcmp(&g.opts, &o, sizeof(o)) == 0) {
+      if (!g.exec) {   // second use: capture
+        const long long s0 = ctx->n_sweep, z0 = ctx->n_zero_sweep, a0 = ctx->n_apply, t0 = ctx->sweeps_tracked;
+        const unsigned long long l0 = t_launches;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        dgmg_status st = precond_eager(ctx, r, z, o);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (st != DGMG_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return st;
+        }
+        if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        g.d_sweep = ctx->n_sweep - s0;
+        g.d_zero = ctx->n_zero_sweep - z0;
+        g.d_apply = ctx->n_apply - a0;
+        g.d_tracked = ctx->sweeps_tracked - t0;
+        g.d_launches = t_launches - l0;
+        ctx->n_sweep = s0;
+        ctx->n_zero_sweep = z0;
+        ctx->n_apply = a0;
+        ctx->sweeps_tracked = t0;
+        t_launches = l0;
+      }
+      CK(cudaGraphLaunch(g.exec, ctx->stream));
+      ctx->n_sweep += g.d_sweep;
+      ctx->n_zero_sweep += g.d_zero;
+      ctx->n_apply += g.d_apply;
+      ctx->sweeps_tracked += g.d_tracked;
+      t_launches += g.d_launches;
+      return DGMG_OK;
+    }
+  }
+  // first use: run eagerly (sets kernel attributes) and remember the key
+  if (ctx->graphs.size() < 64) {
+    dgmg_ctx::PrecGraph g = {};
+    g.in = r;
+    g.out = z;
+    g.opts = o;
+    g.exec = nullptr;
+    ctx->graphs.push_back(g);
+  }
+  return precond_eager(ctx, r, z, o);
 }
 
 // Outer Krylov operator: FP64 vectors, FP64 or double-float arithmetic.
@@ -700,6 +777,7 @@ void dgmg_default_opts(dgmg_solve_opts* o) {
   o->coarse_cycles = 1;
   o->smoother = DGMG_SMOOTHER_JACOBI;
   o->apply_prec = DGMG_FP64;
+  o->graph = 0;
 }
 
 dgmg_status dgmg_create(dgmg_ctx** out, int device, void* cuda_stream) {
@@ -742,6 +820,7 @@ dgmg_status dgmg_destroy(dgmg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  drop_graphs(ctx);
   cudaFree(ctx->dot_partial);
   cudaFree(ctx->dot_out);
   cudaFree(ctx->dot_ptrs);
@@ -783,6 +862,7 @@ dgmg_status dgmg_set_mesh(dgmg_ctx* ctx, int nx, int ny, int nz, double lx, doub
   ctx->ndof = ncell * n3;
   ctx->nvert = (long long)(nx + 1) * (ny + 1) * (nz + 1);
   ctx->ops = cell_ops(p + 1);
+  for (int i = 0; i < 3; ++i) ctx->wpb_apply[i] = ctx->wpb_smooth[i] = 0;
   ctx->has_mesh = true;
   ctx->has_coef = false;
   return DGMG_OK;
@@ -1072,6 +1152,96 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
     *stats = st;
   }
   return s;
+}
+
+dgmg_status dgmg_set_launch_shape(dgmg_ctx* ctx, dgmg_prec prec, int wpb_apply, int wpb_smooth) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (!ctx->has_mesh) return fail(ctx, DGMG_ERR_STATE, "set_mesh first");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  auto ok = [](int w) { return w == 0 || w == 1 || w == 2 || w == 4 || w == 8; };
+  if (!ok(wpb_apply) || !ok(wpb_smooth)) return fail(ctx, DGMG_ERR_ARG, "warps per block must be 0, 1, 2, 4 or 8");
+  drop_graphs(ctx);   // captured graphs hold the old launch shapes
+  ctx->wpb_apply[prec] = wpb_apply;
+  ctx->wpb_smooth[prec] = wpb_smooth;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_apply, int* wpb_smooth) {
+  if (!ctx) return DGMG_ERR_ARG;
+  CS(ready(ctx));
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CS(check_df64(ctx, prec, DGMG_INNER_PCG));
+  if (reps <= 0) reps = 3;
+  cudaSetDevice(ctx->device);
+  const size_t es = prec == DGMG_FP32 ? 4 : 8;
+  void* buf = nullptr;
+  CK(cudaMallocAsync(&buf, 3 * ctx->ndof * es, ctx->stream));
+  char* f = (char*)buf;
+  char* u = f + ctx->ndof * es;
+  char* t = u + ctx->ndof * es;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  dgmg_status st = DGMG_OK;
+  const int cand[4] = {1, 2, 4, 8};
+  int best[2] = {0, 0};
+  const int saved_a = ctx->wpb_apply[prec], saved_s = ctx->wpb_smooth[prec];
+  const bool saved_track = ctx->track_its, saved_timing = ctx->timing;
+  ctx->track_its = false;
+  ctx->timing = false;
+  auto run = [&]() -> dgmg_status {
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return fail(ctx, DGMG_ERR_CUDA, "event create");
+    if (prec == DGMG_FP32)
+      CK(vec_fill_f(ctx->ndof, 1.f, (float*)f, ctx->stream));
+    else
+      CK(vec_fill(ctx->ndof, 1.0, (double*)f, ctx->stream));
+    for (int kind = 0; kind < 2; ++kind) {
+      float best_ms = 0.f;
+      for (int w : cand) {
+        if (kind == 0)
+          ctx->wpb_apply[prec] = w;
+        else
+          ctx->wpb_smooth[prec] = w;
+        const MeshParams mp = params(ctx);
+        float total = 0.f;
+        for (int r = 0; r <= reps; ++r) {
+          CK(cudaEventRecord(e0, ctx->stream));
+          if (kind == 0) {
+            CK(ctx->ops->apply(mp, f, u, prec, true, ctx->stream));
+          } else {
+            CS(smooth_internal(ctx, f, u, t, 1, 1.0, 1e-2, 0, DGMG_INNER_PCG, 0, prec, true, nullptr));
+          }
+          CK(cudaEventRecord(e1, ctx->stream));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (r > 0) total += ms;   // r = 0 is the warm-up
+        }
+        if (best[kind] == 0 || total < best_ms) {
+          best[kind] = w;
+          best_ms = total;
+        }
+      }
+    }
+    return DGMG_OK;
+  };
+  st = run();
+  ctx->track_its = saved_track;
+  ctx->timing = saved_timing;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(buf, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  if (st != DGMG_OK) {
+    ctx->wpb_apply[prec] = saved_a;
+    ctx->wpb_smooth[prec] = saved_s;
+    return st;
+  }
+  drop_graphs(ctx);
+  ctx->wpb_apply[prec] = best[0];
+  ctx->wpb_smooth[prec] = best[1];
+  if (wpb_apply) *wpb_apply = best[0];
+  if (wpb_smooth) *wpb_smooth = best[1];
+  return DGMG_OK;
 }
 
 }  // extern "C"

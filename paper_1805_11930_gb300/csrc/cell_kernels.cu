@@ -183,9 +183,17 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
     for (int j = 0; j < N; ++j) x[j] = in[base + j * st];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      T s = T(0);
+      T s;
+      if constexpr (std::is_same<T, df>::value) {
+        df_acc acc;
 #pragma unroll
-      for (int j = 0; j < N; ++j) s = fma(TR ? A[j][i] : A[i][j], x[j], s);
+        for (int j = 0; j < N; ++j) acc.add_prod(TR ? A[j][i] : A[i][j], x[j]);
+        s = acc.value();
+      } else {
+        s = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(TR ? A[j][i] : A[i][j], x[j], s);
+      }
       if (ACC)
         out[base + i * st] += s;
       else
@@ -270,9 +278,17 @@ __device__ __forceinline__ void contract_scaled(const T* __restrict__ in, T* __r
     for (int j = 0; j < N; ++j) x[j] = in[base + j * st];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      T s = T(0);
+      T s;
+      if constexpr (std::is_same<T, df>::value) {
+        df_acc acc;
 #pragma unroll
-      for (int j = 0; j < N; ++j) s = fma(A[i][j], x[j], s);
+        for (int j = 0; j < N; ++j) acc.add_prod(A[i][j], x[j]);
+        s = acc.value();
+      } else {
+        s = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(A[i][j], x[j], s);
+      }
       if (ACC)
         out[base + i * st] = fma(sc, s, out[base + i * st]);
       else
@@ -666,11 +682,11 @@ __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T**
 }
 
 template <typename T, bool FULL, bool ADV, typename G = typename Store<T>::type>
-__global__ void __launch_bounds__(WPB * 32) k_apply(MeshParams mp, const G* __restrict__ u, G* __restrict__ v) {
+__global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restrict__ u, G* __restrict__ v) {
   const bool react = mp.c != nullptr;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long cell0 = ((long long)blockIdx.x * WPB + warp) * CPW;
+  const long long cell0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
   if (cell0 >= mp.ncell) return;
   T* vec[4];
   T *F0, *F1, *red;
@@ -715,13 +731,13 @@ __device__ __forceinline__ T cell_sum(T part, int lane, T* red) {
 // Each lane owns the z-lines L = lane + 32k (elements base + N2 iz) for the
 // pointwise vector operations, so all of its elements belong to one cell.
 template <typename T, bool ADV, typename G = typename Store<T>::type>
-__global__ void __launch_bounds__(WPB * 32) k_smooth_pcg(MeshParams mp, const G* __restrict__ f,
+__global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __restrict__ f,
                                                          const G* uold, G* unew, const G* __restrict__ diag,
                                                          T omega, T eps, int maxit, int* __restrict__ its,
                                                          int color) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long s0 = ((long long)blockIdx.x * WPB + warp) * CPW;
+  const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
   if (s0 >= color_count(mp, color)) return;
   T* vec[6];
   T *F0, *F1, *red;
@@ -1353,10 +1369,22 @@ inline long long host_color_count(const MeshParams& mp, int color) {
   return (long long)((mp.nx - kx + 1) / 2) * ((mp.ny - ky + 1) / 2) * ((mp.nz - kz + 1) / 2);
 }
 
-inline unsigned grid_for(long long ncell) {
+inline unsigned grid_for(long long ncell, int wpb) {
   const long long groups = (ncell + CPW - 1) / CPW;
-  return (unsigned)((groups + WPB - 1) / WPB);
+  return (unsigned)((groups + wpb - 1) / wpb);
 }
+
+// Warps per block of a launch: the tuned value if it fits in shared memory,
+// else the largest power of two <= 4 that does.
+inline int pick_wpb(int tuned, size_t per_warp) {
+  int w = (tuned >= 1 && tuned <= 8) ? tuned : WPB;
+  while (w > 1 && (size_t)w * per_warp > 200 * 1024) w >>= 1;
+  return w;
+}
+
+template <typename T> constexpr int prec_index() { return DGMG_FP64; }
+template <> constexpr int prec_index<float>() { return DGMG_FP32; }
+template <> constexpr int prec_index<df>() { return DGMG_DF64; }
 
 template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
@@ -1367,11 +1395,12 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  const size_t sm = WPB * WarpMem<T>::bytes(4);
+  const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4));
+  const size_t sm = wpb * WarpMem<T>::bytes(4);
   auto k = k_apply<T, FULL, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
-  k<<<grid_for(mp.ncell), WPB * 32, sm, s>>>(mp, (const G*)u, (G*)v);
+  k<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, (const G*)u, (G*)v);
   count_launch();
   return cudaGetLastError();
 }
@@ -1399,12 +1428,13 @@ cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool f
 template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  const size_t sm = WPB * WarpMem<T>::bytes(6);
+  const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6));
+  const size_t sm = wpb * WarpMem<T>::bytes(6);
   auto k = k_smooth_pcg<T, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
   const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
-  k<<<grid_for(cells), WPB * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const G*)a.diag,
+  k<<<grid_for(cells, wpb), wpb * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const G*)a.diag,
                                           T(a.omega), T(a.eps), a.maxit, a.its, a.color);
   count_launch();
   return cudaGetLastError();

@@ -36,6 +36,9 @@ struct MeshParams {
   // Mesh scalars in both precisions: 1/h_d, face area normal to d, |J|/h_d.
   double ih[3], area[3], jh[3];
   float ihf[3], areaf[3], jhf[3];
+  // Warps per block of the operator and smoother (inner PCG) kernels per
+  // precision (index DGMG_FP64 / FP32 / DF64; 0 = the default of 4).
+  int wpb_apply[3], wpb_smooth[3];
 };
 
 // Record layout: kd[3] = |J| K_d / h_d^2, cJ = c |J|, kap[6], gam[6] for the

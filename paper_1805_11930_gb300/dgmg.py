@@ -37,7 +37,7 @@ class SolveOpts(ctypes.Structure):
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("eps_inner", ctypes.c_double),
                 ("maxit_inner", ctypes.c_int), ("inner", ctypes.c_int), ("inner_restart", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("timing", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("apply_prec", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("apply_prec", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -79,6 +79,8 @@ _SIG = {
     "dgmg_vcycle": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts)]),
     "dgmg_solve": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)]),
     "dgmg_restrict_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P]),
+    "dgmg_set_launch_shape": (_I, [_P, _I, _I, _I]),
+    "dgmg_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
 NOALLOC_MAX_CELLS = 131072
@@ -254,6 +256,19 @@ class Context:
     def vcycle(self, f, u, opts=None):
         o = opts if opts is not None else default_opts()
         self._check(self.lib.dgmg_vcycle(self.h, _ptr(f), _ptr(u), ctypes.byref(o)))
+
+    # ------------------------------------------------------------ launch shapes
+    def set_launch_shape(self, prec, wpb_apply=0, wpb_smooth=0):
+        """Warps per block of the operator / smoother kernels for FP64, FP32 or
+        DF64 arithmetic (0 = default)."""
+        self._check(self.lib.dgmg_set_launch_shape(self.h, prec, wpb_apply, wpb_smooth))
+
+    def autotune(self, prec=FP64, reps=3):
+        """Time the launch-shape candidates on the current mesh and keep the
+        fastest; returns (wpb_apply, wpb_smooth)."""
+        a, s = _I(0), _I(0)
+        self._check(self.lib.dgmg_autotune(self.h, prec, reps, ctypes.byref(a), ctypes.byref(s)))
+        return a.value, s.value
 
     def solve(self, f, u, opts=None, check=True):
         o = opts if opts is not None else default_opts()

@@ -479,3 +479,75 @@ def test_solve_df64_poisson_c1():
     st = ctx.solve(f, u, dgmg.default_opts(smoother_prec=dgmg.DF64, apply_prec=dgmg.DF64, krylov=dgmg.KRYLOV_FCG))
     assert st["converged"] and st["rel_residual"] <= 1e-8
     assert rel_err(u.cpu().numpy(), u64.cpu().numpy()) < 1e-7
+
+
+def test_graph_captured_preconditioner_same_result():
+    """Capturing the V-cycle into a CUDA graph and replaying it gives the same
+    iterates, bit for bit, as launching its kernels one by one."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.lognormal(6, 3)
+    stream = torch.cuda.Stream()
+    ctx = dgmg.Context(0, stream=stream)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_coefficients(w["K"])
+    with torch.cuda.stream(stream):
+        f = gpu_rhs(ctx, w, torch)
+        out = []
+        for graph in (0, 1):
+            u = torch.zeros_like(f)
+            st = ctx.solve(f, u, dgmg.default_opts(graph=graph, smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG))
+            out.append((u.cpu().numpy(), st))
+    stream.synchronize()
+    (u0, s0), (u1, s1) = out
+    assert s1["converged"] and s0["iterations"] == s1["iterations"]
+    assert np.array_equal(u0, u1)
+    assert s0["kernel_launches"] == s1["kernel_launches"] and s0["sweeps"] == s1["sweeps"]
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32", "DF64"])
+def test_launch_shape_does_not_change_results(prec_name):
+    """Every warp owns whole cells, so the warps per block of the operator and
+    smoother kernels change no bit of their outputs (ragged last block
+    included: 5^3 cells do not fill any of the shapes evenly)."""
+    from paper_1805_11930_gb300 import dgmg
+    prec = getattr(dgmg, prec_name)
+    w = inputs.lognormal(5, 3)
+    ctx = gpu_context(w)
+    dt = torch.float32 if prec == dgmg.FP32 else torch.float64
+    df64 = prec == dgmg.DF64
+    s = ctx.sizes()
+    x = torch.tensor(inputs.random_dg_vector(s["ndof"], seed=11), device="cuda").to(dt)
+    f = torch.tensor(inputs.random_dg_vector(s["ndof"], seed=12), device="cuda").to(dt)
+    outs = []
+    for wpb in (0, 1, 2, 8):
+        ctx.set_launch_shape(prec, wpb, wpb)
+        v = torch.empty_like(x)
+        ctx.apply(x, v, df64=df64)
+        u = x.clone()
+        ctx.block_smooth(f, u, nsweep=2, omega=0.8, eps=1e-2, df64=df64)
+        outs.append((v.cpu().numpy(), u.cpu().numpy()))
+    for v, u in outs[1:]:
+        assert np.array_equal(v, outs[0][0]) and np.array_equal(u, outs[0][1])
+
+
+def test_autotune_choices_and_bitwise_solve():
+    """dgmg_autotune picks a shape for each kernel from {1, 2, 4, 8}, rejects
+    bad arguments, and a solve after tuning equals the untuned solve bit for
+    bit."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.lognormal(8, 4)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    opts = dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
+    u0 = torch.zeros_like(f)
+    s0 = ctx.solve(f, u0, opts)
+    for prec in (dgmg.FP64, dgmg.FP32, dgmg.DF64):
+        a, s = ctx.autotune(prec, reps=2)
+        assert a in (1, 2, 4, 8) and s in (1, 2, 4, 8)
+    u1 = torch.zeros_like(f)
+    s1 = ctx.solve(f, u1, opts)
+    assert s0["iterations"] == s1["iterations"] and np.array_equal(u0.cpu().numpy(), u1.cpu().numpy())
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_launch_shape(dgmg.FP64, 3, 0)
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_launch_shape(7, 4, 4)
