@@ -9,6 +9,10 @@ inverses.
   update.  Exact block solves use a dense LU with partial pivoting per block;
   inexact ones reduce the block residual two-norm by a factor eps with a
   Krylov method preconditioned by diag(D_T) (Sec. 2.2.1 and Sec. 3.2).
+* Inner preconditioners: the diagonal of D_T (diffusion) or, for strongly
+  convection-dominated blocks, the tridiagonal part of D_T in the cell's
+  lexicographic dof order (x fastest) solved by the Thomas algorithm
+  (Sec. 3.2 and Sec. 4.3, where the diagonal one fails to converge).
 * Hybrid V-cycle (Algorithm 1).
 * CG, flexible CG (Polak-Ribiere beta) and right-preconditioned flexible
   GMRES(restart) (Saad 1993) for the outer solve.
@@ -23,6 +27,40 @@ import scipy.linalg as sla
 
 
 # ----------------------------------------------------------------- inner solves
+def tridiagonal_part(D):
+    """(sub, diag, sup) of a square matrix: sub[i] = D[i, i-1] (sub[0] = 0),
+    sup[i] = D[i, i+1] (sup[-1] = 0)."""
+    n = D.shape[0]
+    sub = np.zeros(n)
+    sup = np.zeros(n)
+    sub[1:] = np.diagonal(D, -1)
+    sup[:-1] = np.diagonal(D, 1)
+    return sub, np.diagonal(D).copy(), sup
+
+
+def thomas_solve(sub, diag, sup, r):
+    """Solve the tridiagonal system (sub, diag, sup) x = r by the Thomas
+    algorithm (Gaussian elimination without pivoting): forward sweep
+    c'_0 = c_0 / b_0, c'_i = c_i / (b_i - a_i c'_{i-1}),
+    d'_i = (r_i - a_i d'_{i-1}) / (b_i - a_i c'_{i-1}); back substitution
+    x_{n-1} = d'_{n-1}, x_i = d'_i - c'_i x_{i+1}."""
+    n = len(r)
+    cp = np.zeros(n)
+    dp = np.zeros(n)
+    prev_c = 0.0
+    prev_d = 0.0
+    for i in range(n):
+        den = diag[i] - sub[i] * prev_c
+        cp[i] = sup[i] / den
+        dp[i] = (r[i] - sub[i] * prev_d) / den
+        prev_c, prev_d = cp[i], dp[i]
+    x = np.zeros(n)
+    x[n - 1] = dp[n - 1]
+    for i in range(n - 2, -1, -1):
+        x[i] = dp[i] - cp[i] * x[i + 1]
+    return x
+
+
 def block_pcg(D, d, dg, eps, maxit):
     """PCG on the dense block D with preconditioner 1/dg, from delta = 0.
     Returns (delta, iterations)."""
@@ -54,9 +92,11 @@ def block_pcg(D, d, dg, eps, maxit):
     return x, it
 
 
-def block_gmres(D, d, dg, eps, maxit, restart):
-    """Right-preconditioned (1/dg) restarted GMRES on the dense block D with
-    modified Gram-Schmidt and Givens rotations, from delta = 0.
+def block_gmres(D, d, dg, eps, maxit, restart, minv=None):
+    """Right-preconditioned restarted GMRES on the dense block D with modified
+    Gram-Schmidt and Givens rotations, from delta = 0.  The preconditioner is
+    1/dg, or the map minv(v) = M^-1 v when given; with minv each cycle ends
+    with x += M^-1 (V y) (Saad's right-preconditioned update).
     Returns (delta, iterations)."""
     x = np.zeros_like(d)
     target = eps * np.linalg.norm(d)
@@ -72,7 +112,7 @@ def block_gmres(D, d, dg, eps, maxit, restart):
         g[0] = beta
         j_done = 0
         for j in range(restart):
-            w = D @ (V[j] / dg)
+            w = D @ (V[j] / dg if minv is None else minv(V[j]))
             for i in range(j + 1):
                 H[i, j] = w @ V[i]
                 w = w - H[i, j] * V[i]
@@ -94,8 +134,11 @@ def block_gmres(D, d, dg, eps, maxit, restart):
             if abs(g[j + 1]) <= target or it >= maxit:
                 break
         y = sla.solve_triangular(H[:j_done, :j_done], g[:j_done])
-        for i in range(j_done):
-            x += y[i] * V[i] / dg
+        if minv is None:
+            for i in range(j_done):
+                x += y[i] * V[i] / dg
+        else:
+            x += minv(sum(y[i] * V[i] for i in range(j_done)))
         r = d - D @ x
         beta = np.linalg.norm(r)
     return x, it
@@ -106,8 +149,9 @@ class BlockJacobi:
     """Block-Jacobi smoother S(f, u; nsweep, omega) of Algorithm 2 on the
     assembled BSR matrix A."""
 
-    def __init__(self, A, N, inner="lu", eps=1e-2, maxit=None, restart=12):
+    def __init__(self, A, N, inner="lu", eps=1e-2, maxit=None, restart=12, precond="diag"):
         self.A = A.tocsr()
+        self.precond = precond
         self.N = N
         self.ncell = A.shape[0] // N
         self.inner = inner
@@ -131,7 +175,11 @@ class BlockJacobi:
         dg = np.diag(self.D[c])
         if self.inner == "pcg":
             return block_pcg(self.D[c], d, dg, self.eps, self.maxit)
-        return block_gmres(self.D[c], d, dg, self.eps, self.maxit, self.restart)
+        minv = None
+        if self.precond == "tridiag":
+            tri = tridiagonal_part(self.D[c])
+            minv = lambda v: thomas_solve(*tri, v)   # noqa: E731
+        return block_gmres(self.D[c], d, dg, self.eps, self.maxit, self.restart, minv=minv)
 
     def __call__(self, f, u, nsweep, omega):
         N = self.N
