@@ -7,6 +7,11 @@ library).
   evaluating the coarse basis at the nodal points: (P|_T)_{ij} =
   psi_hat_j(zeta_i) (Sec. 2.2.2, "Intergrid operators").
 * Restriction R = P^T (same section).
+* The piecewise-constant subspace P0 (Sec. 2.2.2; the coarse space of the
+  paper's SPE10 runs, Sec. 4.4): P|_T = 1 (the nodal basis is a partition
+  of unity), R = P^T sums a cell's values, and A_hat = P^T A P, the Galerkin
+  product (App. A.1 defines A_hat this way and shows that it equals a
+  re-scaled finite-volume matrix).
 * Q1 matrix A_hat by re-discretisation (Sec. 2.2.3 and App. A.2): the
   conforming Q1 finite element matrix of the PDE plus the Dirichlet boundary
   terms of a_h, with the penalty gamma_F computed from the DG degree p.  Jump
@@ -62,6 +67,20 @@ def prolongation(prob):
 def restriction(prob):
     """R = P^T."""
     return prolongation(prob).T.tocsr()
+
+
+def p0_prolongation(prob):
+    """Sparse P (ndof x ncell) of the P0 subspace: every dof of cell T takes
+    the cell's coarse value."""
+    rows = np.arange(prob.ndof)
+    return sp.csr_matrix((np.ones(prob.ndof), (rows, rows // prob.N)), shape=(prob.ndof, prob.ncell))
+
+
+def p0_matrix(A, prob):
+    """A_hat = P^T A P for the P0 subspace (App. A.1), CSR (ncell x ncell),
+    from the assembled DG matrix A."""
+    P0 = p0_prolongation(prob)
+    return sp.csr_matrix(P0.T @ A @ P0)
 
 
 def _q1_basis(xi):

@@ -224,3 +224,78 @@ def test_tridiagonal_preconditioner_convection_dominated_block():
     tri = solvers.tridiagonal_part(D)
     x, it = solvers.block_gmres(D, d, np.diag(D), 1e-2, 200, 12, minv=lambda v: solvers.thomas_solve(*tri, v))
     assert it <= 20 and np.linalg.norm(d - D @ x) <= 1e-2 * np.linalg.norm(d) * (1 + 1e-12)
+
+
+def _modified_fv(nc, L, p, bc, K, c=None, bconst=None, alpha=1.25):
+    """The cell-centred finite-volume matrix of App. A.1 (central differences
+    with the harmonic mean of K on interior faces, one-sided differences over
+    the centre-to-face distance h/2 on Dirichlet faces, upwind convection with
+    b at the face centre, c |T| on the diagonal), with its diffusion terms
+    scaled as the P0 Galerkin product scales them: interior faces by
+    alpha p (p + 2), Dirichlet faces by alpha p (p + 2) / 2 (relative to the
+    true distance h/2; the appendix prints |F| / (2 |T|) for that inverse
+    distance, i.e. 1/(2h) instead of 2/h, and hence the factor 2 alpha p (p+2))."""
+    nx, ny, nz = nc
+    h = np.array(L) / np.array(nc)
+    vol = np.prod(h)
+    n = nx * ny * nz
+    M = np.zeros((n, n))
+    s = alpha * p * (p + 2)
+    idx = lambda x, y, z: x + nx * (y + ny * z)   # noqa: E731
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = idx(x, y, z)
+                if c is not None:
+                    M[i, i] += c[i] * vol
+                for k in range(3):
+                    area = vol / h[k]
+                    for side, step in ((0, -1), (1, 1)):
+                        q = [x, y, z]
+                        q[k] += step
+                        inside = 0 <= q[k] < nc[k]
+                        bn = 0.0 if bconst is None else bconst[k] * step   # b . outward normal
+                        if inside:
+                            j = idx(*q)
+                            Kh = 2 * K[i, k] * K[j, k] / (K[i, k] + K[j, k])
+                            M[i, i] += s * Kh / h[k] * area
+                            M[i, j] -= s * Kh / h[k] * area
+                            M[i, i] += max(bn, 0.0) * area
+                            M[i, j] += min(bn, 0.0) * area
+                        elif bc[2 * k + side] == 0:
+                            M[i, i] += 0.5 * s * K[i, k] / (h[k] / 2) * area
+                            M[i, i] += max(bn, 0.0) * area
+    return M
+
+
+@pytest.mark.parametrize("advect", [False, True])
+def test_p0_galerkin_matrix_is_modified_fv(advect):
+    """App. A.1: on an equidistant axis-parallel grid with K, b and c constant
+    per cell, P^T A P for the P0 subspace is the finite-volume matrix with the
+    diffusion terms re-scaled (interior faces by alpha p (p+d-1))."""
+    from paper_1805_11930_gb300 import inputs
+    rng = np.random.default_rng(11)
+    nc, L, p, bc = (3, 4, 2), (1.0, 0.8, 1.2), 3, [0, 1, 0, 0, 1, 0]
+    ncell = int(np.prod(nc))
+    K = np.exp(rng.normal(size=(ncell, 3)))
+    c = rng.uniform(0.1, 1.0, size=ncell)
+    bconst = np.array([0.7, -0.4, 0.2]) if advect else None
+    bv = None
+    if advect:
+        bv = inputs.vertex_field(nc, L, lambda x, y, z: np.stack([0 * x + bconst[0], 0 * x + bconst[1],
+                                                                  0 * x + bconst[2]], -1))
+    P = dg.Problem(*nc, *L, p, bc, K, b_vertex=bv, c_cell=c)
+    Ah = transfer.p0_matrix(P.assemble(), P).toarray()
+    M = _modified_fv(nc, L, p, bc, K, c=c, bconst=bconst)
+    assert np.abs(Ah - M).max() < 1e-12 * np.abs(M).max()
+
+
+def test_p0_transfer_and_neumann_nullspace():
+    """P0: P injects cell constants (R P = N I, N dofs per cell) and, with
+    pure Neumann conditions, b = 0 and c = 0, the constants span the kernel
+    of P^T A P (zero row sums)."""
+    P = small_problem(p=2, nc=(3, 2, 2), bc=(1,) * 6)
+    P0 = transfer.p0_prolongation(P)
+    assert np.abs((P0.T @ P0).toarray() - P.N * np.eye(P.ncell)).max() == 0.0
+    Ah = transfer.p0_matrix(P.assemble(), P)
+    assert np.abs(Ah @ np.ones(P.ncell)).max() < 1e-12 * abs(Ah).max()
