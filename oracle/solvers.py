@@ -254,28 +254,52 @@ class HybridVCycle:
 
 
 # ----------------------------------------------------------------- outer Krylov
-def cg(apply_A, b, precond, rtol=1e-8, maxit=1000, x0=None, flexible=False):
+def cg(apply_A, b, precond, rtol=1e-8, maxit=1000, x0=None, flexible=False, stop="residual", delay=4):
     """Preconditioned CG; with flexible=True the Polak-Ribiere beta
-    z_{k+1}.(r_{k+1} - r_k) / z_k.r_k.  Returns (x, iterations, history)."""
+    z_{k+1}.(r_{k+1} - r_k) / z_k.r_k.  Returns (x, iterations, history).
+
+    stop="residual": ||r_k||_2 <= rtol ||r_0||_2; history holds the relative
+    residuals.  stop="energy": the energy-norm error estimate of Strakos and
+    Tichy (BIT 45, 2005, Sec. 3.1; used in the paper's Sec. 4.4 with an
+    error bandwidth of 4): in PCG, ||e_k||_A^2 - ||e_{k+d}||_A^2 equals
+    sum_{j=k}^{k+d-1} alpha_j (r_j, z_j), so after iteration k+d that sum
+    estimates ||e_k||_A^2 from below, and sum_{j<k+d} estimates ||x - x_0||_A^2.
+    The loop stops at the first k with sqrt(nu_k / total) <= rtol and returns
+    x_{k+d}, the iteration count k (the d run-ahead iterations not counted)
+    and the estimates as history."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply_A(x)
     r0 = np.linalg.norm(r)
     hist = [1.0]
     if r0 == 0.0:
         return x, 0, hist
+    energy = stop == "energy"
+    terms = []
+    if energy:
+        hist = []
     z = precond(r)
     p = z.copy()
     rz = r @ z
     for it in range(1, maxit + 1):
         q = apply_A(p)
         alpha = rz / (p @ q)
+        terms.append(alpha * rz)
         x = x + alpha * p
         r_old = r
         r = r - alpha * q
         rel = np.linalg.norm(r) / r0
-        hist.append(rel)
-        if rel <= rtol:
-            return x, it, hist
+        if energy:
+            if it >= delay:
+                k = it - delay
+                nu = sum(terms[k:it])
+                est = np.sqrt(nu / sum(terms[:it]))
+                hist.append(est)
+                if est <= rtol:
+                    return x, k, hist
+        else:
+            hist.append(rel)
+            if rel <= rtol:
+                return x, it, hist
         z = precond(r)
         rz_new = z @ (r - r_old) if flexible else r @ z
         beta = rz_new / rz

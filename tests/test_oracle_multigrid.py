@@ -299,3 +299,44 @@ def test_p0_transfer_and_neumann_nullspace():
     assert np.abs((P0.T @ P0).toarray() - P.N * np.eye(P.ncell)).max() == 0.0
     Ah = transfer.p0_matrix(P.assemble(), P)
     assert np.abs(Ah @ np.ones(P.ncell)).max() < 1e-12 * abs(Ah).max()
+
+
+def test_energy_norm_estimate_identity():
+    """Strakos-Tichy: in PCG, ||e_k||_A^2 - ||e_{k+d}||_A^2 equals
+    sum_{j=k}^{k+d-1} alpha_j (r_j, z_j); checked against the dense solution
+    (brute force) for every k, together with the lower-bound property of the
+    delay-4 estimate, and the stopping rule on the returned iterate."""
+    P = small_problem(p=2, nc=(3, 3, 2), bc=(0,) * 6)
+    A = P.assemble().tocsr()
+    b = np.random.default_rng(3).normal(size=P.ndof)
+    xs = np.linalg.solve(A.toarray(), b)
+    dinv = 1.0 / A.diagonal()
+    xs_list, terms = [], []
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rz = r @ z
+    for _ in range(120):
+        xs_list.append(x.copy())
+        q = A @ p
+        alpha = rz / (p @ q)
+        terms.append(alpha * rz)
+        x = x + alpha * p
+        r = r - alpha * q
+        z = dinv * r
+        rzn = r @ z
+        p = z + rzn / rz * p
+        rz = rzn
+    xs_list.append(x.copy())
+    eA = [(xs - xk) @ (A @ (xs - xk)) for xk in xs_list]
+    d = 4
+    for k in range(0, 26):
+        nu = sum(terms[k:k + d])
+        assert abs((eA[k] - eA[k + d]) - nu) <= 1e-8 * eA[k]
+        assert nu <= eA[k] * (1 + 1e-10)
+    xe, k, hist = solvers.cg(lambda v: A @ v, b, lambda v: dinv * v, rtol=1e-6, stop="energy", delay=4)
+    assert hist[-1] <= 1e-6 < hist[-2] and k + d < len(xs_list)
+    assert np.sqrt(eA[k] / (xs @ (A @ xs))) == pytest.approx(hist[-1], rel=0.5)
+    assert np.abs(xe - xs_list[k + d]).max() <= 1e-12 * np.abs(xs).max()
+    assert np.sqrt((xs - xe) @ (A @ (xs - xe)) / (xs @ (A @ xs))) <= 1e-6
