@@ -148,6 +148,10 @@ def run_dgmg(args, rank, world, local_rank):
     u = torch.zeros_like(f)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = dgmg.default_opts(timing=1)
+    # launch shapes (warps per block) of the operator and smoother kernels,
+    # timed on this mesh for each arithmetic before anything is measured
+    shapes = {name: ctx.autotune(prec) for name, prec in (("fp64", dgmg.FP64), ("fp32", dgmg.FP32),
+                                                          ("df64", dgmg.DF64))}
 
     def barrier():
         if world > 1:
@@ -254,6 +258,14 @@ def run_dgmg(args, rank, world, local_rank):
                                                  apply_prec=dgmg.DF64))
     df_ms, dfst = time_solve(dgmg.default_opts(smoother_prec=dgmg.DF64, krylov=dgmg.KRYLOV_FCG,
                                                apply_prec=dgmg.DF64))
+    # exact block solves by stored inverses (partially matrix-free smoother)
+    t_inv = time.perf_counter()
+    ctx.block_inverse(dgmg.FP64)
+    ctx.block_inverse(dgmg.FP32)
+    inv_setup_s = time.perf_counter() - t_inv
+    pmf_ms, pmfst = time_solve(dgmg.default_opts(inner=dgmg.INNER_DIRECT))
+    pmf32_ms, pmf32st = time_solve(dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.FP32,
+                                                     krylov=dgmg.KRYLOV_FCG))
 
     # end to end through the C ABI with host buffers
     f_host = f.cpu().pin_memory()
@@ -270,19 +282,20 @@ def run_dgmg(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     barrier()
     e2e_s = max_over_ranks(e2e_s, world, dev)
-    e2e = {"value": round(job_throughput(ndof, args.steps, world, e2e_s * 1e3), 6), "unit": "GDOF/s",
+    e2e = {"value": round(job_throughput(ndof, args.steps, world, e2e_s * 1e3), 9), "unit": "GDOF/s",
            "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
 
     last = stats[-1]
     out = {
-        "metric": METRIC, "value": round(value, 6), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": round(value, 9), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"variable-coefficient diffusion, log-normal K per cell (sigma 1, seed 1805), "
                                f"SIPG Q{w['p']} on {WORKLOAD['n']}^3 hexes, {ndof} dofs, FP64 CG + hybrid V-cycle "
                                f"(block-Jacobi, inner PCG eps 1e-2, Q1 + AMG), rtol 1e-8",
                    "ndof": ndof, "p": w["p"], "mesh": list(w["nc"]), "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "warps_per_block": {k: {"apply": a, "smoother": b} for k, (a, b) in shapes.items()}},
         "e2e": e2e,
         "gpu_launches": int(sum(x["kernel_launches"] for x in stats)),
         "roofline": roofline,
@@ -294,7 +307,12 @@ def run_dgmg(args, rank, world, local_rank):
                   "mixed_iterations": mst["iterations"], "mixed_rel_residual": mst["rel_residual"],
                   "solve_s_mixed_df64_outer": round(mdf_ms / 1e3, 5), "mixed_df64_rel_residual": mdfst["rel_residual"],
                   "solve_s_df64": round(df_ms / 1e3, 5), "df64_iterations": dfst["iterations"],
-                  "df64_rel_residual": dfst["rel_residual"]},
+                  "df64_rel_residual": dfst["rel_residual"],
+                  "block_inverse_setup_s": round(inv_setup_s, 4),
+                  "solve_s_fp64_direct": round(pmf_ms / 1e3, 5), "fp64_direct_iterations": pmfst["iterations"],
+                  "fp64_direct_rel_residual": pmfst["rel_residual"],
+                  "solve_s_mixed_direct": round(pmf32_ms / 1e3, 5), "mixed_direct_iterations": pmf32st["iterations"],
+                  "mixed_direct_rel_residual": pmf32st["rel_residual"]},
         "apply": {"gdofs_fp64": round(apply64, 4), "ms_fp64": round(apply64_ms, 4),
                   "gdofs_fp32": round(apply32, 4), "ms_fp32": round(apply32_ms, 4),
                   "gdofs_df64": round(applydf, 4), "ms_df64": round(applydf_ms, 4)},

@@ -58,9 +58,34 @@ typedef enum {
  * return DGMG_ERR_ARG. */
 typedef enum { DGMG_FP64 = 0, DGMG_FP32 = 1, DGMG_DF64 = 2 } dgmg_prec;
 typedef enum { DGMG_KRYLOV_CG = 0, DGMG_KRYLOV_FCG = 1, DGMG_KRYLOV_FGMRES = 2 } dgmg_krylov;
-typedef enum { DGMG_INNER_PCG = 0, DGMG_INNER_GMRES = 1 } dgmg_inner;
-typedef enum { DGMG_COARSE_AMG = 0, DGMG_COARSE_NONE = 1 } dgmg_coarse;
+/* Block solves of the smoother: inner PCG or GMRES on the matrix-free block,
+ * preconditioned by diag(D_T) (Sec. 2.2.1, 3.2); GMRES_TRIDIAG: GMRES
+ * preconditioned by the tridiagonal part of D_T in the cell's lexicographic
+ * dof order (x fastest), solved by the Thomas algorithm, for strongly
+ * convection-dominated blocks (Sec. 3.2, 4.3; its factors, 3 n^3 values per
+ * cell and precision, are built on first use); or DIRECT: multiplication by
+ * the explicit inverse of D_T stored on the device (the partially matrix-free
+ * variant, Sec. 4.1; see dgmg_block_inverse), p <= 4. */
+typedef enum {
+  DGMG_INNER_PCG = 0,
+  DGMG_INNER_GMRES = 1,
+  DGMG_INNER_DIRECT = 2,
+  DGMG_INNER_GMRES_TRIDIAG = 3
+} dgmg_inner;
+/* Coarse correction of the V-cycle: the conforming Q1 subspace with AMG
+ * (Sec. 2.2.2-2.2.3, the default), none, or the piecewise-constant P0
+ * subspace with AMG on its 7-point matrix (App. A.1; the paper's choice for
+ * its SPE10 runs, Sec. 4.4; built on first use). */
+typedef enum { DGMG_COARSE_AMG = 0, DGMG_COARSE_NONE = 1, DGMG_COARSE_P0 = 2 } dgmg_coarse;
 typedef enum { DGMG_SMOOTHER_JACOBI = 0, DGMG_SMOOTHER_SSOR = 1 } dgmg_smoother;
+/* Outer stopping rule.  RESIDUAL: ||r_k||_2 <= rtol ||r_0||_2.  ENERGY: the
+ * estimate of Strakos and Tichy (BIT 45, 2005, Sec. 3.1) used in Sec. 4.4:
+ * in PCG, ||e_k||_A^2 - ||e_{k+d}||_A^2 = sum_{j=k}^{k+d-1} alpha_j (r_j, z_j),
+ * so after iteration k+d that sum estimates ||e_k||_A^2 (from below) and
+ * sum_{j<k+d} alpha_j (r_j, z_j) estimates ||x - x_0||_A^2; the solve stops at
+ * the first k whose relative estimate is <= rtol and returns x_{k+d}, with
+ * iterations = k (the d run-ahead iterations are in iterations_run). */
+typedef enum { DGMG_STOP_RESIDUAL = 0, DGMG_STOP_ENERGY = 1 } dgmg_stop;
 
 /* Options of the hybrid V-cycle (Algorithm 1) and of the outer Krylov solve. */
 typedef struct {
@@ -74,9 +99,10 @@ typedef struct {
   int npre, npost;     /* smoothing sweeps (default 1, 1)                          */
   double eps_inner;    /* block solve: reduce ||d - D_T x||_2 by eps (default 1e-2) */
   int maxit_inner;     /* block solve iteration cap (default n^3 when <= 0)        */
-  int inner;           /* dgmg_inner: PCG (symmetric) or GMRES (b != 0)            */
+  int inner;           /* dgmg_inner: PCG (symmetric), GMRES (b != 0),             */
+                       /* GMRES_TRIDIAG (convection-dominated) or DIRECT          */
   int inner_restart;   /* inner GMRES restart (default 12)                         */
-  int coarse;          /* dgmg_coarse: Q1 + AMG correction, or none               */
+  int coarse;          /* dgmg_coarse: Q1 + AMG correction, none, or P0 + AMG     */
   int timing;          /* 1: time smoother and operator launches with CUDA events */
   int coarse_cycles;   /* AMG V-cycles per coarse correction, iterated on the     */
                        /* coarse residual (default 1)                             */
@@ -87,11 +113,15 @@ typedef struct {
                        /* (default) or DF64; the final residual check is FP64    */
   int graph;           /* 1: capture the preconditioner into a CUDA graph and     */
                        /* replay it (needs a non-default stream; off when timing) */
+  int stop;            /* dgmg_stop: relative residual (default) or the energy-   */
+                       /* norm error estimate (CG and flexible CG only)           */
+  int delay;           /* error bandwidth d of the energy-norm estimate (def. 4)  */
 } dgmg_solve_opts;
 
 typedef struct {
   int iterations;       /* outer iterations                                       */
-  int converged;        /* 1 if the recomputed FP64 residual met rtol             */
+  int converged;        /* 1 if the recomputed FP64 residual (stop = RESIDUAL) or   */
+                        /* the energy-norm estimate (stop = ENERGY) met rtol      */
   double rel_residual;  /* ||f - A u||_2 / ||f - A u_0||_2, recomputed in FP64    */
   double inner_mean;    /* mean inner block-solve iterations over all cells/sweeps */
   int inner_max;        /* maximum inner iterations seen                          */
@@ -103,6 +133,8 @@ typedef struct {
   long long kernel_launches;  /* all kernels this library launched in the solve    */
   double ms_smooth;     /* device time of the smoother launches (opts->timing)    */
   double ms_apply;      /* device time of the operator launches (opts->timing)    */
+  double energy_estimate; /* last relative energy-norm estimate (stop = ENERGY)   */
+  int iterations_run;   /* outer iterations performed (iterations + d for ENERGY)  */
 } dgmg_solve_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -208,6 +240,29 @@ dgmg_status dgmg_coarse_matrix(const dgmg_ctx* ctx, double* stencil);
  * r_hat, u_hat: device FP64 vertex vectors, distinct. */
 dgmg_status dgmg_coarse_cycle(dgmg_ctx* ctx, const double* r_hat, double* u_hat);
 
+/* The piecewise-constant subspace P0 (Sec. 2.2.2, App. A.1): P|_T = 1, so
+ * r_hat_T = sum of the cell's n^3 values of r (R = P^T) and u_T += u_hat_T.
+ *   r, u: device DG vectors of `prec` (FP64 or FP32);
+ *   r_hat, u_hat: device FP64 cell vectors (ncell values, cells x fastest).
+ * The sums run one warp per cell in a fixed order. */
+dgmg_status dgmg_restrict_p0(dgmg_ctx* ctx, const void* r, double* r_hat, dgmg_prec prec);
+dgmg_status dgmg_prolong_add_p0(dgmg_ctx* ctx, const double* u_hat, void* u, dgmg_prec prec);
+
+/* A_hat = P^T A P of the P0 subspace by re-discretisation (App. A.1): per
+ * cell c |T|, on interior faces the penalty alpha p (p+2) <K_d^-, K_d^+> / h_d
+ * times |F| (diagonal +, face neighbour -) and the upwind flux split by the
+ * sign of b.n (outflow on the diagonal, inflow to the neighbour), on
+ * Dirichlet faces alpha p (p+2) K_d / h_d |F| and the outflow; face
+ * integrals of the upwind parts with the DG rule.  stencil: host, 27 * ncell
+ * doubles in the layout of dgmg_coarse_matrix on the cell grid (7 non-zero
+ * entries per row).  Builds the P0 hierarchy if needed. */
+dgmg_status dgmg_coarse_matrix_p0(dgmg_ctx* ctx, double* stencil);
+
+/* u_hat = one aggregation-AMG V-cycle on the P0 A_hat from zero, as
+ * dgmg_coarse_cycle does on Q1.  r_hat, u_hat: device FP64 cell vectors,
+ * distinct. */
+dgmg_status dgmg_coarse_cycle_p0(dgmg_ctx* ctx, const double* r_hat, double* u_hat);
+
 /* One hybrid V-cycle (Algorithm 1) for A u = f starting from the u given
  * (pass zeros for the preconditioner form): presmooth, residual, restrict,
  * AMG, prolongate-add, postsmooth, with opts (NULL = defaults).  The DG part
@@ -221,6 +276,29 @@ dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_so
  * stats: host or NULL.  Synchronises the stream. */
 dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
                        dgmg_solve_stats* stats);
+
+/* Explicit inverse of every diagonal block D_T (the (T,T) part of A: volume
+ * terms and the own-side face terms), for the partially matrix-free smoother
+ * (PMF, Sec. 4.1: the paper stores a factorisation of D_T and solves with it;
+ * this library stores D_T^-1 itself, so that a block solve is one dense
+ * matrix-vector product streamed from HBM instead of two triangular solves).
+ *
+ * Built on the device: column j of D_T is the block operator applied to the
+ * unit vector e_j (n^3 block applications per cell), then each block is
+ * inverted by Gauss-Jordan elimination with partial pivoting in FP64, one
+ * thread block per cell with the block in shared memory.  The inverse is kept
+ * in the context in FP64 and, when prec is FP32, also rounded to FP32; the
+ * smoothers with inner = DGMG_INNER_DIRECT use the copy of their precision
+ * (building it on first use when this call was not made).  Storage:
+ * ncell n^6 values per precision (p = 2: 5.8 KB per cell in FP64, p = 4:
+ * 125 KB).  dgmg_set_coefficients and dgmg_set_mesh drop it.
+ *   prec: FP64 or FP32 (DF64: DGMG_ERR_ARG);
+ *   out: device buffer of ncell n^6 values of prec receiving a copy, or NULL;
+ *        block T at out + T n^6, column-major: (D_T^-1)_{ij} at i + j n^3.
+ * p > 4: DGMG_ERR_ARG (the block no longer fits in shared memory); a singular
+ * block: DGMG_ERR_ARG with nothing stored; allocation failure: DGMG_ERR_OOM.
+ * Synchronises the stream. */
+dgmg_status dgmg_block_inverse(dgmg_ctx* ctx, dgmg_prec prec, void* out);
 
 /* Launch shape of the warp-per-cell operator and smoother kernels.  Each warp
  * owns whole cells and no two warps share data, so the warps per block (1, 2,

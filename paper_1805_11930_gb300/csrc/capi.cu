@@ -85,6 +85,18 @@ struct AmgLevel {
   double* r = nullptr;
 };
 
+// One aggregation-AMG hierarchy on a structured grid: the Q1 vertices, or the
+// cells for the P0 subspace.  Level 0 holds A_hat as a 27-point stencil.
+struct Hier {
+  std::vector<AmgLevel> lv;
+  double* coarse_inv = nullptr;   // dense inverse of the coarsest level
+  int coarse_n = 0;
+  double* rhat = nullptr;         // restricted residual / coarse correction
+  double* uhat = nullptr;
+  std::vector<double> st;         // host copy of the level-0 stencil
+  bool built = false;
+};
+
 struct dgmg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -111,10 +123,8 @@ struct dgmg_ctx {
   int* its = nullptr;
   unsigned long long* itsum = nullptr;
   int* itmax = nullptr;
-  double *rhat = nullptr, *uhat = nullptr;
-  std::vector<AmgLevel> lv;
-  double* coarse_inv = nullptr;
-  int coarse_n = 0;
+  Hier q1h;   // Q1 coarse space (built with the coefficients)
+  Hier p0h;   // P0 coarse space (built on first use)
   double* kry = nullptr;
   size_t kry_vecs = 0;
   double* dot_partial = nullptr;
@@ -142,6 +152,12 @@ struct dgmg_ctx {
   std::vector<void*> mesh_allocs;  // freed on a new mesh
   // warps per block of the operator / smoother kernels per precision (0 = 4)
   int wpb_apply[3] = {0, 0, 0}, wpb_smooth[3] = {0, 0, 0};
+  // stored inverses of the diagonal blocks (DGMG_INNER_DIRECT), built on demand
+  double* binv64 = nullptr;
+  float* binv32 = nullptr;
+  // Thomas factors of the tridiagonal part of D_T (DGMG_INNER_GMRES_TRIDIAG)
+  double* tri64 = nullptr;
+  float* tri32 = nullptr;
 };
 
 namespace {
@@ -208,12 +224,25 @@ void free_mesh(dgmg_ctx* ctx) {
   ctx->its = nullptr;
   ctx->itsum = nullptr;
   ctx->itmax = nullptr;
-  ctx->rhat = ctx->uhat = nullptr;
-  ctx->lv.clear();
-  ctx->coarse_inv = nullptr;
+  ctx->q1h = Hier();
+  ctx->p0h = Hier();
   ctx->kry = nullptr;
   ctx->kry_vecs = 0;
+  ctx->binv64 = nullptr;
+  ctx->binv32 = nullptr;
+  ctx->tri64 = nullptr;
+  ctx->tri32 = nullptr;
   ctx->has_coef = false;
+}
+
+// Frees one allocation made by dalloc before the mesh changes.
+void dfree(dgmg_ctx* ctx, void* q) {
+  for (auto it = ctx->mesh_allocs.begin(); it != ctx->mesh_allocs.end(); ++it)
+    if (*it == q) {
+      ctx->mesh_allocs.erase(it);
+      cudaFreeAsync(q, ctx->stream);
+      return;
+    }
 }
 
 MeshParams params(const dgmg_ctx* ctx) {
@@ -280,7 +309,7 @@ dgmg_status check_df64(dgmg_ctx* ctx, int prec, int inner) {
   if (prec != DGMG_DF64) return DGMG_OK;
   if (ctx->p > 6) return fail(ctx, DGMG_ERR_ARG, "DF64 kernels are built for p <= 6");
   if (ctx->db) return fail(ctx, DGMG_ERR_ARG, "DF64 kernels are built for b = 0");
-  if (inner == DGMG_INNER_GMRES) return fail(ctx, DGMG_ERR_ARG, "DF64 smoothers use the inner PCG");
+  if (inner != DGMG_INNER_PCG) return fail(ctx, DGMG_ERR_ARG, "DF64 smoothers use the inner PCG");
   return DGMG_OK;
 }
 
@@ -302,6 +331,120 @@ dgmg_status multi_dot(dgmg_ctx* ctx, int k, double* const* xs, const double* y, 
   return DGMG_OK;
 }
 
+// ------------------------------------------------------------------ stored block inverses
+// D_T^-1 of every cell in FP64 (and rounded to FP32 when prec is FP32): block
+// matrices by unit-vector block applications, Gauss-Jordan per block.
+dgmg_status ensure_binv(dgmg_ctx* ctx, int prec) {
+  if (prec != DGMG_FP64 && prec != DGMG_FP32)
+    return fail(ctx, DGMG_ERR_ARG, "stored block inverses are FP64 or FP32");
+  if (ctx->p > 4) return fail(ctx, DGMG_ERR_ARG, "stored block inverses are built for p <= 4");
+  if (prec == DGMG_FP64 ? ctx->binv64 != nullptr : ctx->binv32 != nullptr) return DGMG_OK;
+  if (ctx->stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(ctx, DGMG_ERR_STATE, "build the block inverses (dgmg_block_inverse) before stream capture");
+  }
+  const int nb = ctx->n * ctx->n * ctx->n;
+  const size_t count = (size_t)ctx->ncell * nb * nb;
+  if (!ctx->binv64) {
+    double* m = nullptr;
+    int* sing = nullptr;
+    CS(dalloc(ctx, &m, count));
+    dgmg_status st = dalloc(ctx, &sing, 1);
+    if (st != DGMG_OK) {
+      dfree(ctx, m);
+      return st;
+    }
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = ctx->ops->block_matrix(params(ctx), m, ctx->stream);
+    if (e == cudaSuccess) e = block_invert(m, nb, ctx->ncell, sing, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, sing);
+    if (e != cudaSuccess || h) {
+      dfree(ctx, m);
+      if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
+      return fail(ctx, DGMG_ERR_ARG, "a diagonal block is singular");
+    }
+    ctx->binv64 = m;
+  }
+  if (prec == DGMG_FP32) {
+    float* m32 = nullptr;
+    CS(dalloc(ctx, &m32, count));
+    CK(vec_d2f((long long)count, ctx->binv64, m32, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->binv32 = m32;
+  }
+  return DGMG_OK;
+}
+
+// Thomas factors of the tridiagonal part of every D_T, FP64 (rounded to FP32
+// when prec is FP32), for the GMRES_TRIDIAG inner solver.
+dgmg_status ensure_tri(dgmg_ctx* ctx, int prec) {
+  if (prec != DGMG_FP64 && prec != DGMG_FP32)
+    return fail(ctx, DGMG_ERR_ARG, "the tridiagonal inner preconditioner is FP64 or FP32");
+  if (prec == DGMG_FP64 ? ctx->tri64 != nullptr : ctx->tri32 != nullptr) return DGMG_OK;
+  if (ctx->stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(ctx, DGMG_ERR_STATE, "run one uncaptured solve or sweep before stream capture");
+  }
+  const size_t count = (size_t)ctx->ncell * 3 * ctx->n * ctx->n * ctx->n;
+  if (!ctx->tri64) {
+    double* m = nullptr;
+    int* sing = nullptr;
+    CS(dalloc(ctx, &m, count));
+    dgmg_status st = dalloc(ctx, &sing, 1);
+    if (st != DGMG_OK) {
+      dfree(ctx, m);
+      return st;
+    }
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = ctx->ops->block_tridiag(params(ctx), m, sing, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, sing);
+    if (e != cudaSuccess || h) {
+      dfree(ctx, m);
+      if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("tridiagonal factors: ") + cudaGetErrorString(e));
+      return fail(ctx, DGMG_ERR_ARG, "the tridiagonal part of a diagonal block has a zero pivot");
+    }
+    ctx->tri64 = m;
+  }
+  if (prec == DGMG_FP32) {
+    float* m32 = nullptr;
+    CS(dalloc(ctx, &m32, count));
+    CK(vec_d2f((long long)count, ctx->tri64, m32, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tri32 = m32;
+  }
+  return DGMG_OK;
+}
+
+// Per-sweep arguments that depend on the inner solver: the stored inverses
+// (DIRECT) or the Thomas factors (GMRES_TRIDIAG), built on first use.
+dgmg_status inner_data(dgmg_ctx* ctx, int inner, int prec, const void** binv, const void** tri) {
+  *binv = *tri = nullptr;
+  const bool fp32 = prec == DGMG_FP32;
+  if (inner == DGMG_INNER_DIRECT) {
+    CS(ensure_binv(ctx, prec));
+    *binv = fp32 ? (const void*)ctx->binv32 : (const void*)ctx->binv64;
+  } else if (inner == DGMG_INNER_GMRES_TRIDIAG) {
+    CS(ensure_tri(ctx, prec));
+    *tri = fp32 ? (const void*)ctx->tri32 : (const void*)ctx->tri64;
+  }
+  return DGMG_OK;
+}
+
+dgmg_status prepare_inner(dgmg_ctx* ctx, int inner, int prec) {
+  const void *b, *t;
+  return inner_data(ctx, inner, prec, &b, &t);
+}
+
 // ------------------------------------------------------------------ smoother
 // nsweep block-Jacobi sweeps on u (in place) with ping-pong through tmp.
 dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, int nsweep, double omega, double eps,
@@ -317,9 +460,11 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     return DGMG_OK;
   }
   if (maxit <= 0) maxit = ctx->n * ctx->n * ctx->n;
-  if (inner != DGMG_INNER_PCG && inner != DGMG_INNER_GMRES) return fail(ctx, DGMG_ERR_ARG, "bad inner solver");
-  if (inner == DGMG_INNER_GMRES && (restart < 1 || restart > 64))
+  if (inner < DGMG_INNER_PCG || inner > DGMG_INNER_GMRES_TRIDIAG) return fail(ctx, DGMG_ERR_ARG, "bad inner solver");
+  if ((inner == DGMG_INNER_GMRES || inner == DGMG_INNER_GMRES_TRIDIAG) && (restart < 1 || restart > 64))
     return fail(ctx, DGMG_ERR_ARG, "inner_restart must be in [1, 64]");
+  const void *binv = nullptr, *tri = nullptr;
+  CS(inner_data(ctx, inner, prec, &binv, &tri));
   const MeshParams mp = params(ctx);
   void* src = u;
   void* dst = tmp;
@@ -334,6 +479,8 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     a.maxit = maxit;
     a.inner = inner;
     a.restart = restart;
+    a.binv = binv;
+    a.tri = tri;
     a.its = (its || ctx->track_its) ? ctx->its : nullptr;
     const size_t e0 = ctx->timing ? record_event(ctx) : 0;
     CK(ctx->ops->smooth(mp, a, prec, ctx->stream));
@@ -371,9 +518,11 @@ dgmg_status sor_internal(dgmg_ctx* ctx, const void* f, void* u, int nsweep, doub
   }
   if (nsweep <= 0) return DGMG_OK;
   if (maxit <= 0) maxit = ctx->n * ctx->n * ctx->n;
-  if (inner != DGMG_INNER_PCG && inner != DGMG_INNER_GMRES) return fail(ctx, DGMG_ERR_ARG, "bad inner solver");
-  if (inner == DGMG_INNER_GMRES && (restart < 1 || restart > 64))
+  if (inner < DGMG_INNER_PCG || inner > DGMG_INNER_GMRES_TRIDIAG) return fail(ctx, DGMG_ERR_ARG, "bad inner solver");
+  if ((inner == DGMG_INNER_GMRES || inner == DGMG_INNER_GMRES_TRIDIAG) && (restart < 1 || restart > 64))
     return fail(ctx, DGMG_ERR_ARG, "inner_restart must be in [1, 64]");
+  const void *binv = nullptr, *tri = nullptr;
+  CS(inner_data(ctx, inner, prec, &binv, &tri));
   const MeshParams mp = params(ctx);
   const int passes = symmetric ? 2 : 1;
   for (int k = 0; k < nsweep; ++k)
@@ -389,6 +538,8 @@ dgmg_status sor_internal(dgmg_ctx* ctx, const void* f, void* u, int nsweep, doub
         a.maxit = maxit;
         a.inner = inner;
         a.restart = restart;
+        a.binv = binv;
+        a.tri = tri;
         a.its = (its || ctx->track_its) ? ctx->its : nullptr;
         a.color = pass == 0 ? c : 7 - c;
         const size_t e0 = ctx->timing ? record_event(ctx) : 0;
@@ -420,36 +571,103 @@ dgmg_status vcycle_smooth(dgmg_ctx* ctx, const dgmg_solve_opts& o, const void* F
 }
 
 // ------------------------------------------------------------------ AMG
-dgmg_status amg_cycle(dgmg_ctx* ctx, int l, const double* b, double* xout) {
-  const int last = (int)ctx->lv.size() - 1;
+dgmg_status amg_cycle(dgmg_ctx* ctx, Hier& H, int l, const double* b, double* xout) {
+  const int last = (int)H.lv.size() - 1;
   if (l == last) {
-    CK(dense_matvec(ctx->coarse_n, ctx->coarse_inv, b, xout, ctx->stream));
+    CK(dense_matvec(H.coarse_n, H.coarse_inv, b, xout, ctx->stream));
     return DGMG_OK;
   }
-  AmgLevel& L = ctx->lv[l];
-  AmgLevel& C = ctx->lv[l + 1];
+  AmgLevel& L = H.lv[l];
+  AmgLevel& C = H.lv[l + 1];
   const double w = L.omega;
   CK(stencil_jacobi(L.vx, L.vy, L.vz, L.st, L.dinv, b, nullptr, L.xt, w, true, ctx->stream));
   CK(stencil_residual(L.vx, L.vy, L.vz, L.st, b, L.xt, L.r, ctx->stream));
   CK(agg_restrict(L.vx, L.vy, L.vz, L.r, C.b, ctx->stream));
-  CS(amg_cycle(ctx, l + 1, C.b, C.x));
+  CS(amg_cycle(ctx, H, l + 1, C.b, C.x));
   CK(agg_prolong_add(L.vx, L.vy, L.vz, C.x, L.xt, ctx->stream));
   CK(stencil_jacobi(L.vx, L.vy, L.vz, L.st, L.dinv, b, L.xt, xout, w, false, ctx->stream));
   return DGMG_OK;
 }
 
-// u_hat ~ A_hat^-1 r_hat by `cycles` AMG V-cycles: the first from zero, each
+// H.uhat ~ A_hat^-1 H.rhat by `cycles` AMG V-cycles: the first from zero, each
 // further one on the current coarse residual (stationary iteration).
-dgmg_status coarse_correction(dgmg_ctx* ctx, int cycles) {
-  CS(amg_cycle(ctx, 0, ctx->rhat, ctx->uhat));
-  AmgLevel& L = ctx->lv[0];
-  for (int k = 1; k < cycles && ctx->lv.size() > 1; ++k) {
+dgmg_status coarse_correction(dgmg_ctx* ctx, Hier& H, int cycles) {
+  CS(amg_cycle(ctx, H, 0, H.rhat, H.uhat));
+  AmgLevel& L = H.lv[0];
+  for (int k = 1; k < cycles && H.lv.size() > 1; ++k) {
     // r = r_hat - A_hat u_hat into L.b, correction into L.x, then u_hat += L.x
-    CK(stencil_residual(L.vx, L.vy, L.vz, L.st, ctx->rhat, ctx->uhat, L.b, ctx->stream));
-    CS(amg_cycle(ctx, 0, L.b, L.x));
-    CK(vec_axpby(L.n, 1.0, L.x, 1.0, ctx->uhat, ctx->stream));
+    CK(stencil_residual(L.vx, L.vy, L.vz, L.st, H.rhat, H.uhat, L.b, ctx->stream));
+    CS(amg_cycle(ctx, H, 0, L.b, L.x));
+    CK(vec_axpby(L.n, 1.0, L.x, 1.0, H.uhat, ctx->stream));
   }
   return DGMG_OK;
+}
+
+// Aggregation-AMG hierarchy from a level-0 stencil on a vx x vy x vz grid:
+// Gershgorin-weighted Jacobi per level, 2x2x2 Galerkin coarsening down to at
+// most 512 unknowns, dense inverse there (host set-up, device storage).
+dgmg_status build_hier(dgmg_ctx* ctx, Hier& H, std::vector<double> st, int vx, int vy, int vz) {
+  H = Hier();
+  H.st = st;
+  const long long n0 = (long long)vx * vy * vz;
+  CS(dalloc(ctx, &H.rhat, n0));
+  CS(dalloc(ctx, &H.uhat, n0));
+  while (true) {
+    AmgLevel L;
+    L.vx = vx;
+    L.vy = vy;
+    L.vz = vz;
+    L.n = (long long)vx * vy * vz;
+    const bool coarsest = L.n <= 512;
+    if (!coarsest) {
+      std::vector<double> dinv(L.n);
+      double gmax = 0.0;
+      for (long long i = 0; i < L.n; ++i) {
+        dinv[i] = 1.0 / st[27 * i + 13];
+        double row = 0.0;
+        for (int k = 0; k < 27; ++k) row += std::fabs(st[27 * i + k]);
+        gmax = std::max(gmax, row * std::fabs(dinv[i]));
+      }
+      L.omega = 4.0 / (3.0 * gmax);
+      CS(dalloc(ctx, &L.st, 27 * L.n));
+      CS(dalloc(ctx, &L.dinv, L.n));
+      CK(cudaMemcpyAsync(L.st, st.data(), 27 * L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(L.dinv, dinv.data(), L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      CS(dalloc(ctx, &L.xt, L.n));
+      CS(dalloc(ctx, &L.r, L.n));
+    }
+    CS(dalloc(ctx, &L.b, L.n));
+    CS(dalloc(ctx, &L.x, L.n));
+    H.lv.push_back(L);
+    if (coarsest) {
+      std::vector<double> A = stencil_dense(st, vx, vy, vz);
+      if (!dense_inverse((int)L.n, A)) return fail(ctx, DGMG_ERR_ARG, "coarse matrix is singular");
+      H.coarse_n = (int)L.n;
+      CS(dalloc(ctx, &H.coarse_inv, A.size()));
+      CK(cudaMemcpyAsync(H.coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      break;
+    }
+    int cx, cy, cz;
+    st = coarsen_stencil(st, vx, vy, vz, cx, cy, cz);
+    vx = cx;
+    vy = cy;
+    vz = cz;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));   // the host stencils above must outlive their copies
+  H.built = true;
+  return DGMG_OK;
+}
+
+// The P0 hierarchy, built on first use (not under stream capture).
+dgmg_status ensure_p0(dgmg_ctx* ctx) {
+  if (ctx->p0h.built) return DGMG_OK;
+  if (ctx->stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(ctx, DGMG_ERR_STATE, "run one uncaptured solve with the P0 coarse space before stream capture");
+  }
+  return build_hier(ctx, ctx->p0h, p0_stencil(host_mesh(ctx)), ctx->nx, ctx->ny, ctx->nz);
 }
 
 dgmg_status restrict_internal(dgmg_ctx* ctx, const void* r, double* rhat, bool fp32) {
@@ -484,20 +702,28 @@ dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgm
   }
   CS(vcycle_smooth(ctx, o, F, U, T1, o.npre, prec, zero));
   const bool u_zero = zero && o.npre <= 0;
-  if (o.coarse == DGMG_COARSE_AMG) {
-    // r = f - A u
-    if (u_zero) {
-      CS(restrict_internal(ctx, F, ctx->rhat, fp32));
-    } else {
+  if (o.coarse == DGMG_COARSE_AMG || o.coarse == DGMG_COARSE_P0) {
+    const bool p0 = o.coarse == DGMG_COARSE_P0;
+    Hier& H = p0 ? ctx->p0h : ctx->q1h;
+    // r = f - A u, restricted to the coarse space
+    const void* R = F;
+    if (!u_zero) {
       CS(timed_apply(ctx, U, T2, prec));
       if (fp32)
         CK(vec_sub_f(n, (const float*)F, (const float*)T2, (float*)T2, ctx->stream));
       else
         CK(vec_sub(n, (const double*)F, (const double*)T2, (double*)T2, ctx->stream));
-      CS(restrict_internal(ctx, T2, ctx->rhat, fp32));
+      R = T2;
     }
-    CS(coarse_correction(ctx, o.coarse_cycles));
-    CK(ctx->ops->prolong_add(mp, ctx->uhat, U, fp32, ctx->stream));
+    if (p0)
+      CK(cell_sums(ctx->ncell, ctx->n * ctx->n * ctx->n, R, H.rhat, fp32, ctx->stream));
+    else
+      CS(restrict_internal(ctx, R, H.rhat, fp32));
+    CS(coarse_correction(ctx, H, o.coarse_cycles));
+    if (p0)
+      CK(cell_add(ctx->ncell, ctx->n * ctx->n * ctx->n, H.uhat, U, fp32, ctx->stream));
+    else
+      CK(ctx->ops->prolong_add(mp, H.uhat, U, fp32, ctx->stream));
     CS(vcycle_smooth(ctx, o, F, U, T1, o.npost, prec, false));
   } else {
     CS(vcycle_smooth(ctx, o, F, U, T1, o.npost, prec, u_zero));
@@ -622,6 +848,9 @@ dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve
   double rz;
   CS(dot(ctx, r, z, rz));
   dgmg_status result = DGMG_ERR_NOT_CONVERGED;
+  const bool energy = o.stop == DGMG_STOP_ENERGY;
+  std::vector<double> terms;   // alpha_j (r_j, z_j), the energy-norm estimate's terms
+  bool est_met = false;
   for (int it = 1; it <= o.maxit; ++it) {
     CS(apply64(ctx, p, q, o.apply_prec));
     double pq;
@@ -632,12 +861,28 @@ dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve
       break;
     }
     const double alpha = rz / pq;
+    terms.push_back(alpha * rz);
     CK(vec_axpby(n, alpha, p, 1.0, u, ctx->stream));
     if (flex) CK(vec_copy(n, r, ro, ctx->stream));
     CK(vec_axpby(n, -alpha, q, 1.0, r, ctx->stream));
     CS(dot(ctx, r, r, rr));
     st.iterations = it;
-    if (std::sqrt(rr) <= o.rtol * r0) {
+    st.iterations_run = it;
+    if (energy) {
+      if (it >= o.delay) {
+        const int k = it - o.delay;
+        double nu = 0.0, tot = 0.0;
+        for (int j = k; j < it; ++j) nu += terms[j];
+        for (int j = 0; j < it; ++j) tot += terms[j];
+        st.energy_estimate = std::sqrt(nu / tot);
+        st.iterations = k;
+        if (st.energy_estimate <= o.rtol) {
+          est_met = true;
+          result = DGMG_OK;
+          break;
+        }
+      }
+    } else if (std::sqrt(rr) <= o.rtol * r0) {
       result = DGMG_OK;
       break;
     }
@@ -659,7 +904,7 @@ dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve
   CK(vec_sub(n, f, q, r, ctx->stream));
   CS(dot(ctx, r, r, rr));
   st.rel_residual = std::sqrt(rr) / r0;
-  st.converged = st.rel_residual <= o.rtol * (1.0 + 1e-6) ? 1 : 0;
+  st.converged = (energy ? est_met : st.rel_residual <= o.rtol * (1.0 + 1e-6)) ? 1 : 0;
   if (result == DGMG_ERR_NOT_CONVERGED) ctx->err = "outer Krylov solve reached maxit";
   return result == DGMG_OK && !st.converged ? DGMG_ERR_NOT_CONVERGED : result;
 }
@@ -778,6 +1023,8 @@ void dgmg_default_opts(dgmg_solve_opts* o) {
   o->smoother = DGMG_SMOOTHER_JACOBI;
   o->apply_prec = DGMG_FP64;
   o->graph = 0;
+  o->stop = DGMG_STOP_RESIDUAL;
+  o->delay = 4;
 }
 
 dgmg_status dgmg_create(dgmg_ctx** out, int device, void* cuda_stream) {
@@ -914,60 +1161,13 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   CS(dalloc(ctx, &ctx->its, ctx->ncell));
   CS(dalloc(ctx, &ctx->itsum, 1));
   CS(dalloc(ctx, &ctx->itmax, 1));
-  CS(dalloc(ctx, &ctx->rhat, ctx->nvert));
-  CS(dalloc(ctx, &ctx->uhat, ctx->nvert));
   const MeshParams mp = params(ctx);
   CK(cell_records(mp, ctx->rec64, ctx->rec32, ctx->stream));
   CK(ctx->ops->diag(mp, ctx->diag64, ctx->stream));
   CK(vec_d2f(n, ctx->diag64, ctx->diag32, ctx->stream));
   CK(vec_inverse(n, ctx->diag64, ctx->dinv64, ctx->dinv32, ctx->stream));
   // Q1 matrix and AMG hierarchy (host setup, device cycle)
-  const HostMesh hm = host_mesh(ctx);
-  ctx->q1 = q1_stencil(hm);
-  std::vector<double> st = ctx->q1;
-  int vx = ctx->nx + 1, vy = ctx->ny + 1, vz = ctx->nz + 1;
-  while (true) {
-    AmgLevel L;
-    L.vx = vx;
-    L.vy = vy;
-    L.vz = vz;
-    L.n = (long long)vx * vy * vz;
-    const bool coarsest = L.n <= 512;
-    if (!coarsest) {
-      std::vector<double> dinv(L.n);
-      double gmax = 0.0;
-      for (long long i = 0; i < L.n; ++i) {
-        dinv[i] = 1.0 / st[27 * i + 13];
-        double row = 0.0;
-        for (int k = 0; k < 27; ++k) row += std::fabs(st[27 * i + k]);
-        gmax = std::max(gmax, row * std::fabs(dinv[i]));
-      }
-      L.omega = 4.0 / (3.0 * gmax);
-      CS(dalloc(ctx, &L.st, 27 * L.n));
-      CS(dalloc(ctx, &L.dinv, L.n));
-      CK(cudaMemcpyAsync(L.st, st.data(), 27 * L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaMemcpyAsync(L.dinv, dinv.data(), L.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-      CS(dalloc(ctx, &L.xt, L.n));
-      CS(dalloc(ctx, &L.r, L.n));
-    }
-    CS(dalloc(ctx, &L.b, L.n));
-    CS(dalloc(ctx, &L.x, L.n));
-    ctx->lv.push_back(L);
-    if (coarsest) {
-      std::vector<double> A = stencil_dense(st, vx, vy, vz);
-      if (!dense_inverse((int)L.n, A)) return fail(ctx, DGMG_ERR_ARG, "coarse matrix is singular");
-      ctx->coarse_n = (int)L.n;
-      CS(dalloc(ctx, &ctx->coarse_inv, A.size()));
-      CK(cudaMemcpyAsync(ctx->coarse_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice,
-                         ctx->stream));
-      break;
-    }
-    int cx, cy, cz;
-    st = coarsen_stencil(st, vx, vy, vz, cx, cy, cz);
-    vx = cx;
-    vy = cy;
-    vz = cz;
-  }
+  CS(build_hier(ctx, ctx->q1h, q1_stencil(host_mesh(ctx)), ctx->nx + 1, ctx->ny + 1, ctx->nz + 1));
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaGetLastError());
   ctx->has_coef = true;
@@ -1075,14 +1275,45 @@ dgmg_status dgmg_prolong_add(dgmg_ctx* ctx, const double* u_hat, void* u, dgmg_p
 dgmg_status dgmg_coarse_matrix(const dgmg_ctx* ctx, double* stencil) {
   if (!ctx || !ctx->has_coef) return DGMG_ERR_STATE;
   if (!stencil) return DGMG_ERR_ARG;
-  std::memcpy(stencil, ctx->q1.data(), ctx->q1.size() * sizeof(double));
+  std::memcpy(stencil, ctx->q1h.st.data(), ctx->q1h.st.size() * sizeof(double));
   return DGMG_OK;
 }
 
 dgmg_status dgmg_coarse_cycle(dgmg_ctx* ctx, const double* r_hat, double* u_hat) {
   CS(ready(ctx));
   if (!r_hat || !u_hat || r_hat == u_hat) return fail(ctx, DGMG_ERR_ARG, "r_hat, u_hat must be distinct");
-  return amg_cycle(ctx, 0, r_hat, u_hat);
+  return amg_cycle(ctx, ctx->q1h, 0, r_hat, u_hat);
+}
+
+dgmg_status dgmg_restrict_p0(dgmg_ctx* ctx, const void* r, double* r_hat, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!r || !r_hat) return fail(ctx, DGMG_ERR_ARG, "NULL pointer");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CK(cell_sums(ctx->ncell, ctx->n * ctx->n * ctx->n, r, r_hat, prec == DGMG_FP32, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_prolong_add_p0(dgmg_ctx* ctx, const double* u_hat, void* u, dgmg_prec prec) {
+  CS(ready(ctx));
+  if (!u || !u_hat) return fail(ctx, DGMG_ERR_ARG, "NULL pointer");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  CK(cell_add(ctx->ncell, ctx->n * ctx->n * ctx->n, u_hat, u, prec == DGMG_FP32, ctx->stream));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_coarse_matrix_p0(dgmg_ctx* ctx, double* stencil) {
+  CS(ready(ctx));
+  if (!stencil) return fail(ctx, DGMG_ERR_ARG, "NULL pointer");
+  CS(ensure_p0(ctx));
+  std::memcpy(stencil, ctx->p0h.st.data(), ctx->p0h.st.size() * sizeof(double));
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_coarse_cycle_p0(dgmg_ctx* ctx, const double* r_hat, double* u_hat) {
+  CS(ready(ctx));
+  if (!r_hat || !u_hat || r_hat == u_hat) return fail(ctx, DGMG_ERR_ARG, "r_hat, u_hat must be distinct");
+  CS(ensure_p0(ctx));
+  return amg_cycle(ctx, ctx->p0h, 0, r_hat, u_hat);
 }
 
 dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts) {
@@ -1092,6 +1323,9 @@ dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_so
   dgmg_default_opts(&o);
   if (opts) o = *opts;
   if (o.npre < 0 || o.npost < 0) return fail(ctx, DGMG_ERR_ARG, "npre, npost must be >= 0");
+  if (o.coarse < DGMG_COARSE_AMG || o.coarse > DGMG_COARSE_P0) return fail(ctx, DGMG_ERR_ARG, "bad coarse");
+  CS(prepare_inner(ctx, o.inner, o.smoother_prec));
+  if (o.coarse == DGMG_COARSE_P0) CS(ensure_p0(ctx));
   return vcycle_internal(ctx, f, u, o, false);
 }
 
@@ -1107,6 +1341,12 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   if (o.smoother_prec < DGMG_FP64 || o.smoother_prec > DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad smoother_prec");
   CS(check_df64(ctx, o.smoother_prec, o.inner));
   CS(check_df64(ctx, o.apply_prec, DGMG_INNER_PCG));
+  if (o.coarse < DGMG_COARSE_AMG || o.coarse > DGMG_COARSE_P0) return fail(ctx, DGMG_ERR_ARG, "bad coarse");
+  if (o.stop != DGMG_STOP_RESIDUAL && o.stop != DGMG_STOP_ENERGY) return fail(ctx, DGMG_ERR_ARG, "bad stop");
+  if (o.stop == DGMG_STOP_ENERGY && (o.krylov == DGMG_KRYLOV_FGMRES || o.delay < 1))
+    return fail(ctx, DGMG_ERR_ARG, "the energy-norm estimate needs CG or flexible CG and delay >= 1");
+  CS(prepare_inner(ctx, o.inner, o.smoother_prec));
+  if (o.coarse == DGMG_COARSE_P0) CS(ensure_p0(ctx));
   dgmg_solve_stats st;
   std::memset(&st, 0, sizeof(st));
   const auto t0 = std::chrono::steady_clock::now();
@@ -1123,6 +1363,7 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
     CK(cudaMemsetAsync(ctx->itmax, 0, sizeof(int), ctx->stream));
   }
   dgmg_status s = o.krylov == DGMG_KRYLOV_FGMRES ? solve_fgmres(ctx, f, u, o, st) : solve_cg(ctx, f, u, o, st);
+  if (st.iterations_run == 0) st.iterations_run = st.iterations;
   ctx->track_its = false;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, cudaGetErrorString(e));
@@ -1152,6 +1393,19 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
     *stats = st;
   }
   return s;
+}
+
+dgmg_status dgmg_block_inverse(dgmg_ctx* ctx, dgmg_prec prec, void* out) {
+  CS(ready(ctx));
+  CS(ensure_binv(ctx, prec));
+  if (out) {
+    const size_t nb = (size_t)ctx->n * ctx->n * ctx->n;
+    const size_t bytes = (size_t)ctx->ncell * nb * nb * (prec == DGMG_FP32 ? 4 : 8);
+    const void* src = prec == DGMG_FP32 ? (const void*)ctx->binv32 : (const void*)ctx->binv64;
+    CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DGMG_OK;
 }
 
 dgmg_status dgmg_set_launch_shape(dgmg_ctx* ctx, dgmg_prec prec, int wpb_apply, int wpb_smooth) {

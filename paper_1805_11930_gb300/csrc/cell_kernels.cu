@@ -893,6 +893,180 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   if (its && lane < LINES && (lane % N2) == 0 && cid[mycw] >= 0) its[cid[mycw]] = it;
 }
 
+// D_T of each cell column by column: column j is the block operator (volume
+// terms and own-side face terms) applied to the unit vector e_j.  FP64;
+// output column-major, n^3 x n^3 per cell.  Set-up of the stored inverses.
+template <bool ADV>
+__global__ void __launch_bounds__(256) k_block_matrix(MeshParams mp, double* __restrict__ out) {
+  using T = double;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+  if (s0 >= mp.ncell) return;
+  T* vec[4];
+  T *F0, *F1, *red;
+  CellInfo<T>* ci;
+  unsigned char* act;
+  long long* cid;
+  carve(smem + warp * WarpMem<T>::bytes(4), 4, vec, &F0, &F1, &red, &ci, &act, &cid);
+  T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3];
+  const bool react = mp.c != nullptr;
+  slot_cells(mp, -1, s0, lane, cid);
+  stage_cells(mp, 0, lane, ci, act, cid);
+  const long long cell0 = cid[0];
+  for (int j = 0; j < N3; ++j) {
+    for (int e = lane; e < VEC; e += 32) P[e] = (e % N3 == j) ? T(1) : T(0);
+    __syncwarp();
+    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+    all_faces<false, ADV>(P, Q, F0, F1, (const double*)nullptr, mp, cell0, lane, act, ci);
+    __syncwarp();
+    for (int e = lane; e < VEC; e += 32) {
+      const int cw = e / N3;
+      if (act[cw]) out[cid[cw] * (long long)(N3 * N3) + (long long)j * N3 + (e - cw * N3)] = Q[e];
+    }
+    __syncwarp();
+  }
+}
+
+// Block-Jacobi (color < 0) or one colour of block-SOR with exact block solves
+// by the stored inverses (the partially matrix-free smoother): per cell
+// d = f - A u_old (skipped from u = 0), delta = D_T^-1 d as a dense
+// matrix-vector product whose columns are read coalesced from HBM,
+// u_new = u_old + omega delta.
+template <typename T, bool ADV, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __restrict__ f, const G* uold, G* unew,
+                                                    const T* __restrict__ binv, T omega, int* __restrict__ its,
+                                                    int color) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+  if (s0 >= color_count(mp, color)) return;
+  T* vec[4];
+  T *F0, *F1, *red;
+  CellInfo<T>* ci;
+  unsigned char* act;
+  long long* cid;
+  carve(smem + warp * WarpMem<T>::bytes(4), 4, vec, &F0, &F1, &red, &ci, &act, &cid);
+  T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3];
+  const bool react = mp.c != nullptr;
+  const bool zero = uold == nullptr;
+  slot_cells(mp, color, s0, lane, cid);
+  stage_cells(mp, 0, lane, ci, act, cid);
+  const long long cell0 = cid[0];
+  if (!zero) {
+    for (int e = lane; e < VEC; e += 32) {
+      const int cw = e / N3;
+      P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
+    }
+    __syncwarp();
+    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+    all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+    __syncwarp();
+  }
+  // the defect goes to P (no longer needed)
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    P[e] = act[cw] ? T(f[cid[cw] * N3 + (e - cw * N3)]) - (zero ? T(0) : Q[e]) : T(0);
+  }
+  __syncwarp();
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    if (!act[cw]) continue;
+    const int i = e - cw * N3;
+    const T* col = binv + cid[cw] * (long long)(N3 * N3) + i;
+    const T* d = P + cw * N3;
+    T acc = T(0);
+#pragma unroll 8
+    for (int j = 0; j < N3; ++j) acc = fma(__ldg(col + (long long)j * N3), d[j], acc);
+    const long long g = cid[cw] * N3 + i;
+    unew[g] = static_cast<G>(zero ? omega * acc : fma(omega, acc, T(uold[g])));
+  }
+  if (its && lane < CPW && cid[lane] >= 0) its[cid[lane]] = 0;
+}
+
+// Tridiagonal part of D_T in the cell's lexicographic dof order (x fastest)
+// and its Thomas factors, per cell [a | c' | 1/den] (3 n^3 values):
+// a_i = D[i][i-1] (a_0 = 0), den_i = D[i][i] - a_i c'_{i-1},
+// c'_i = D[i][i+1] / den_i (c'_{n^3-1} = 0).  Columns of D_T come from block
+// applications to unit vectors, as for the stored inverses.  FP64 set-up;
+// a zero or non-finite den sets *singular.  (The inner preconditioner the
+// paper uses for strongly convection-dominated blocks, Sec. 3.2 and 4.3.)
+template <bool ADV>
+__global__ void __launch_bounds__(256) k_block_tridiag(MeshParams mp, double* __restrict__ out,
+                                                       int* __restrict__ singular) {
+  using T = double;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+  if (s0 >= mp.ncell) return;
+  T* vec[7];
+  T *F0, *F1, *red;
+  CellInfo<T>* ci;
+  unsigned char* act;
+  long long* cid;
+  carve(smem + warp * WarpMem<T>::bytes(7), 7, vec, &F0, &F1, &red, &ci, &act, &cid);
+  T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3], *TA = vec[4], *TB = vec[5], *TC = vec[6];
+  const bool react = mp.c != nullptr;
+  slot_cells(mp, -1, s0, lane, cid);
+  stage_cells(mp, 0, lane, ci, act, cid);
+  const long long cell0 = cid[0];
+  for (int j = 0; j < N3; ++j) {
+    for (int e = lane; e < VEC; e += 32) P[e] = (e % N3 == j) ? T(1) : T(0);
+    __syncwarp();
+    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+    all_faces<false, ADV>(P, Q, F0, F1, (const double*)nullptr, mp, cell0, lane, act, ci);
+    __syncwarp();
+    for (int e = lane; e < VEC; e += 32) {
+      const int i = e % N3;
+      if (i == j) TB[e] = Q[e];
+      else if (i == j + 1) TA[e] = Q[e];
+      else if (i + 1 == j) TC[e] = Q[e];
+    }
+    __syncwarp();
+  }
+  if (lane < CPW && act[lane]) {
+    double* o = out + cid[lane] * (3LL * N3);
+    const int b = lane * N3;
+    T pc = T(0);
+    bool bad = false;
+    for (int i = 0; i < N3; ++i) {
+      const T a = i > 0 ? TA[b + i] : T(0);
+      const T c = i + 1 < N3 ? TC[b + i] : T(0);
+      const T den = TB[b + i] - a * pc;
+      if (den == T(0) || !isfinite(den)) bad = true;
+      const T id = T(1) / den;
+      pc = c * id;
+      o[i] = a;
+      o[N3 + i] = pc;
+      o[2 * N3 + i] = id;
+    }
+    if (bad) *singular = 1;
+  }
+}
+
+// dst = M^-1 src for the cells with act set, M the tridiagonal part of D_T
+// given by its Thomas factors: forward d'_i = (r_i - a_i d'_{i-1}) / den_i,
+// back x_i = d'_i - c'_i x_{i+1}.  One lane per cell (the recurrence is
+// sequential); called by the whole warp.
+template <typename T>
+__device__ __forceinline__ void thomas_apply(const T* __restrict__ tri, const long long* cid,
+                                             const unsigned char* act, const T* src, T* dst, int lane) {
+  if (lane < CPW && act[lane]) {
+    const T* fa = tri + cid[lane] * (3LL * N3);
+    const T* fc = fa + N3;
+    const T* fi = fc + N3;
+    const T* r = src + lane * N3;
+    T* x = dst + lane * N3;
+    T prev = T(0);
+    for (int i = 0; i < N3; ++i) {
+      prev = (r[i] - fa[i] * prev) * fi[i];
+      x[i] = prev;
+    }
+    for (int i = N3 - 2; i >= 0; --i) x[i] = fma(-fc[i], x[i + 1], x[i]);
+  }
+  __syncwarp();
+}
+
 // Per-cell scalars of the inner GMRES(m): Hessenberg (m+1) x m, g, Givens
 // cosines and sines, and the small solve y.
 __host__ __device__ constexpr int gmres_scalars(int m) { return (m + 1) * m + 4 * m + 1; }
@@ -907,7 +1081,8 @@ __host__ __device__ constexpr int gmres_scalars(int m) { return (m + 1) * m + 4 
 template <typename T, bool ADV, typename G = typename Store<T>::type>
 __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __restrict__ f, const G* uold,
                                                       G* unew, const G* __restrict__ diag, T omega, T eps,
-                                                      int maxit, int m, int* __restrict__ its, int color) {
+                                                      int maxit, int m, int* __restrict__ its, int color,
+                                                      const T* __restrict__ tri) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -1010,16 +1185,20 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
       if (lane < LINES) act[mycw] = cyc ? 1 : 0;
       __syncwarp();
       T* Vj = V + j * VEC;
-      // Z = V_j / diag; Q = D_T Z
-      for (int L = lane; L < LINES; L += 32) {
-        int cw, b0, st, a, b;
-        line_geom<2>(L, cw, b0, st, a, b);
-        if (!cyc) continue;
-        const long long gb = cid[cw] * N3 - cw * N3;
+      // Z = M^-1 V_j (M = diag(D_T), or its tridiagonal part); Q = D_T Z
+      if (tri) {
+        thomas_apply(tri, cid, act, Vj, Z, lane);
+      } else {
+        for (int L = lane; L < LINES; L += 32) {
+          int cw, b0, st, a, b;
+          line_geom<2>(L, cw, b0, st, a, b);
+          if (!cyc) continue;
+          const long long gb = cid[cw] * N3 - cw * N3;
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const int e = b0 + i * N2;
-          Z[e] = Vj[e] * T(diag[gb + e]);
+          for (int i = 0; i < N; ++i) {
+            const int e = b0 + i * N2;
+            Z[e] = Vj[e] * T(diag[gb + e]);
+          }
         }
       }
       __syncwarp();
@@ -1102,7 +1281,33 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
       }
     }
     __syncwarp();
-    if (ran) {
+    if (tri) {
+      // X += M^-1 (V y)
+      if (lane < LINES) act[mycw] = ran ? 1 : 0;
+      if (ran) {
+        for (int L = lane; L < LINES; L += 32) {
+          int cw, b0, st, a, b;
+          line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const int e = b0 + k * N2;
+            T s = T(0);
+            for (int i = 0; i < jdone; ++i) s = fma(yv[i], V[i * VEC + e], s);
+            Z[e] = s;
+          }
+        }
+      }
+      __syncwarp();
+      thomas_apply(tri, cid, act, Z, S0, lane);
+      if (ran) {
+        for (int L = lane; L < LINES; L += 32) {
+          int cw, b0, st, a, b;
+          line_geom<2>(L, cw, b0, st, a, b);
+#pragma unroll
+          for (int k = 0; k < N; ++k) X[b0 + k * N2] += S0[b0 + k * N2];
+        }
+      }
+    } else if (ran) {
       for (int L = lane; L < LINES; L += 32) {
         int cw, b0, st, a, b;
         line_geom<2>(L, cw, b0, st, a, b);
@@ -1441,6 +1646,57 @@ cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_
 }
 
 template <typename T, bool ADV>
+cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  using G = typename Store<T>::type;
+  if (!a.binv) return cudaErrorInvalidValue;
+  const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4));
+  const size_t sm = wpb * WarpMem<T>::bytes(4);
+  auto k = k_smooth_inv<T, ADV>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
+  k<<<grid_for(cells, wpb), wpb * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const T*)a.binv,
+                                          T(a.omega), a.its, a.color);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <bool ADV>
+cudaError_t launch_block_matrix(const MeshParams& mp, double* out, cudaStream_t s) {
+  const int wpb = pick_wpb(0, WarpMem<double>::bytes(4));
+  const size_t sm = wpb * WarpMem<double>::bytes(4);
+  auto k = k_block_matrix<ADV>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <bool ADV>
+cudaError_t launch_block_tridiag(const MeshParams& mp, double* out, int* singular, cudaStream_t s) {
+  const int wpb = pick_wpb(0, WarpMem<double>::bytes(7));
+  const size_t sm = wpb * WarpMem<double>::bytes(7);
+  auto k = k_block_tridiag<ADV>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, out, singular);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t block_tridiag(const MeshParams& mp, double* out, int* singular, cudaStream_t s) {
+  if (mp.ncell == 0) return cudaSuccess;
+  return mp.bvert ? launch_block_tridiag<true>(mp, out, singular, s)
+                  : launch_block_tridiag<false>(mp, out, singular, s);
+}
+
+cudaError_t block_matrix(const MeshParams& mp, double* out, cudaStream_t s) {
+  if (mp.ncell == 0) return cudaSuccess;
+  return mp.bvert ? launch_block_matrix<true>(mp, out, s) : launch_block_matrix<false>(mp, out, s);
+}
+
+template <typename T, bool ADV>
 cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
   const int m = a.restart;
@@ -1457,7 +1713,7 @@ cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t
   const long long groups = (cells + CPW - 1) / CPW;
   const unsigned grid = (unsigned)((groups + wpb - 1) / wpb);
   k<<<grid, wpb * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const G*)a.diag, T(a.omega),
-                               T(a.eps), a.maxit, m, a.its, a.color);
+                               T(a.eps), a.maxit, m, a.its, a.color, (const T*)a.tri);
   count_launch();
   return cudaGetLastError();
 }
@@ -1465,7 +1721,11 @@ cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t
 template <typename T>
 cudaError_t smooth_t(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   const bool adv = mp.bvert != nullptr;
-  if (a.inner == DGMG_INNER_GMRES) return adv ? launch_gmres<T, true>(mp, a, s) : launch_gmres<T, false>(mp, a, s);
+  if (a.inner == DGMG_INNER_GMRES || a.inner == DGMG_INNER_GMRES_TRIDIAG) {
+    if ((a.inner == DGMG_INNER_GMRES_TRIDIAG) != (a.tri != nullptr)) return cudaErrorInvalidValue;
+    return adv ? launch_gmres<T, true>(mp, a, s) : launch_gmres<T, false>(mp, a, s);
+  }
+  if (a.inner == DGMG_INNER_DIRECT) return adv ? launch_inv<T, true>(mp, a, s) : launch_inv<T, false>(mp, a, s);
   return adv ? launch_smooth<T, true>(mp, a, s) : launch_smooth<T, false>(mp, a, s);
 }
 
@@ -1475,7 +1735,7 @@ cudaError_t smooth(const MeshParams& mp, const SmoothArgs& a, int prec, cudaStre
   if (prec == DGMG_DF64) {
     // double-float smoother: block-Jacobi / SOR with inner PCG, b = 0, p <= 6
 #if DGMG_N <= 7
-    if (mp.bvert || a.inner == DGMG_INNER_GMRES) return cudaErrorNotSupported;
+    if (mp.bvert || a.inner != DGMG_INNER_PCG) return cudaErrorNotSupported;
     return launch_smooth<df, false>(mp, a, s);
 #else
     return cudaErrorNotSupported;
@@ -1524,7 +1784,8 @@ cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool 
 #define DGMG_CAT(a, b) DGMG_CAT2(a, b)
 
 const CellOps* DGMG_CAT(cell_ops_n, DGMG_N)() {
-  static const CellOps ops = {N, &upload_tables, &apply, &smooth, &diag, &restrict_cells, &prolong_add};
+  static const CellOps ops = {N, &upload_tables, &apply, &smooth, &diag, &restrict_cells, &prolong_add,
+                              &block_matrix, &block_tridiag};
   return &ops;
 }
 

@@ -70,8 +70,10 @@ struct SmoothArgs {
   const void* diag;       // 1 / diag(D_T) in the same precision
   double omega, eps;
   int maxit;
-  int inner;              // DGMG_INNER_PCG / DGMG_INNER_GMRES
+  int inner;              // DGMG_INNER_PCG / GMRES / DIRECT
   int restart;
+  const void* binv = nullptr;  // DIRECT: ncell column-major n^3 x n^3 inverses, same precision
+  const void* tri = nullptr;   // GMRES_TRIDIAG: per cell Thomas factors [a | c' | 1/den], same precision
   int* its;               // device int[ncell] or nullptr
   int color = -1;         // -1: all cells (Jacobi); 0..7: one parity class, in place allowed
 };
@@ -91,6 +93,10 @@ struct CellOps {
                                 cudaStream_t s);
   cudaError_t (*prolong_add)(const MeshParams& mp, const double* uhat, void* u, bool fp32,
                              cudaStream_t s);
+  // D_T of every cell, FP64, column-major n^3 x n^3 per cell (column j = D_T e_j)
+  cudaError_t (*block_matrix)(const MeshParams& mp, double* out, cudaStream_t s);
+  // Thomas factors of the tridiagonal part of every D_T, FP64, 3 n^3 per cell
+  cudaError_t (*block_tridiag)(const MeshParams& mp, double* out, int* singular, cudaStream_t s);
 };
 
 const CellOps* cell_ops(int n);
@@ -105,6 +111,13 @@ cudaError_t vec_fill(long long n, double v, double* y, cudaStream_t s);
 cudaError_t vec_fill_f(long long n, float v, float* y, cudaStream_t s);
 cudaError_t vec_d2f(long long n, const double* x, float* y, cudaStream_t s);
 cudaError_t vec_inverse(long long n, const double* d, double* i64, float* i32, cudaStream_t s);
+// In-place inverse of ncell dense nb x nb FP64 blocks (column-major, one after
+// another) by Gauss-Jordan elimination with partial pivoting; nb <= 125.
+// singular: device int, set to 1 when a block has a zero pivot (else untouched).
+cudaError_t block_invert(double* a, int nb, long long ncell, int* singular, cudaStream_t s);
+// P0 transfer: out[c] = sum_i r[c n3 + i]; u[c n3 + i] += uhat[c].
+cudaError_t cell_sums(long long ncell, int n3, const void* r, double* out, bool fp32, cudaStream_t s);
+cudaError_t cell_add(long long ncell, int n3, const double* uhat, void* u, bool fp32, cudaStream_t s);
 cudaError_t vec_f2d(long long n, const float* x, double* y, cudaStream_t s);
 // Deterministic dot products: partial sums per block in a fixed order, then
 // one block sums the partials; result written to out (device).

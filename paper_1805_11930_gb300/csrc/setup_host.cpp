@@ -298,6 +298,77 @@ std::vector<double> q1_stencil(const HostMesh& m) {
   return st;
 }
 
+// A_hat of the piecewise-constant subspace (App. A.1) on the cell grid.  For
+// P0 functions the gradient terms vanish; what remains of a_h is, per row T:
+// c |T| on the diagonal; on each interior face the penalty gamma_F |F| with
+// gamma_F = alpha p (p+2) <K_d^-, K_d^+> / h_d (diagonal +, neighbour -) and
+// the upwind flux split by the sign of b.n_out (n_out the outward normal of
+// T): int max(b.n_out, 0) on the diagonal, int min(b.n_out, 0) for the
+// neighbour; on Dirichlet faces gamma_F |F| with K_d^- alone and the outflow
+// part int max(b.n_out, 0).  Face integrals of the upwind parts use the DG
+// rule (p+1 Gauss points per direction), so that A_hat equals P^T A P also
+// where b.n changes sign inside a face.
+std::vector<double> p0_stencil(const HostMesh& m) {
+  const long long ncell = (long long)m.nx * m.ny * m.nz;
+  std::vector<double> st(27 * ncell, 0.0);
+  const int nq = m.p + 1;
+  std::vector<double> g, w;
+  gauss_legendre01(nq, g, w);
+  const double J = m.h[0] * m.h[1] * m.h[2];
+  const double pen = m.alpha * m.p * (m.p + 2);
+  const int nc[3] = {m.nx, m.ny, m.nz};
+  for (int cz = 0; cz < m.nz; ++cz)
+    for (int cy = 0; cy < m.ny; ++cy)
+      for (int cx = 0; cx < m.nx; ++cx) {
+        const long long c = cx + (long long)m.nx * (cy + (long long)m.ny * cz);
+        double* row = &st[27 * c];
+        if (m.c) row[13] += m.c[c] * J;
+        const int cc[3] = {cx, cy, cz};
+        for (int d = 0; d < 3; ++d) {
+          const double area = J / m.h[d];
+          const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+          for (int side = 0; side < 2; ++side) {
+            const int step = side ? 1 : -1;
+            const bool inside = cc[d] + step >= 0 && cc[d] + step < nc[d];
+            if (!inside && m.bc[2 * d + side] != 0) continue;   // Neumann: nothing
+            // upwind parts: int max(b.n_out, 0) and int min(b.n_out, 0) over the face
+            double fout = 0.0, fin = 0.0;
+            if (m.b) {
+              for (int q2 = 0; q2 < nq; ++q2)
+                for (int q1 = 0; q1 < nq; ++q1) {
+                  double xi[3];
+                  xi[d] = side ? 1.0 : 0.0;
+                  xi[a] = g[q1];
+                  xi[b] = g[q2];
+                  double bv[3];
+                  b_at(m, cx, cy, cz, xi, bv);
+                  const double bn = step * bv[d];
+                  const double wq = w[q1] * w[q2] * area;
+                  if (bn >= 0.0)
+                    fout += wq * bn;
+                  else
+                    fin += wq * bn;
+                }
+            }
+            const double Km = kval(m, c, d);
+            int off[3] = {0, 0, 0};
+            off[d] = step;
+            const int nb = (off[0] + 1) + 3 * (off[1] + 1) + 9 * (off[2] + 1);
+            if (inside) {
+              const long long cn = c + (d == 0 ? step : d == 1 ? step * (long long)m.nx : step * (long long)m.nx * m.ny);
+              const double Kp = kval(m, cn, d);
+              const double gam = pen * (2.0 * Km * Kp / (Km + Kp)) / m.h[d];
+              row[13] += gam * area + fout;
+              row[nb] += -gam * area + fin;
+            } else {
+              row[13] += pen * Km / m.h[d] * area + fout;
+            }
+          }
+        }
+      }
+  return st;
+}
+
 std::vector<double> coarsen_stencil(const std::vector<double>& st, int vx, int vy, int vz, int& cx, int& cy,
                                     int& cz) {
   cx = (vx + 1) / 2;

@@ -37,6 +37,10 @@ struct HostMesh {
 // A_hat (App. A.2) as a 27-point stencil on the (nx+1)(ny+1)(nz+1) vertices.
 std::vector<double> q1_stencil(const HostMesh& m);
 
+// A_hat = P^T A P of the piecewise-constant subspace (App. A.1) as a 27-point
+// stencil on the nx*ny*nz cell grid (7 non-zero entries per row).
+std::vector<double> p0_stencil(const HostMesh& m);
+
 // Galerkin coarsening of a 27-point stencil with 2x2x2 piecewise-constant
 // aggregates; returns the coarse stencil and its grid dims.
 std::vector<double> coarsen_stencil(const std::vector<double>& st, int vx, int vy, int vz, int& cx, int& cy, int& cz);

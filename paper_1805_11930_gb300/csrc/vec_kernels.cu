@@ -249,6 +249,135 @@ __global__ void k_inverse(long long n, const double* __restrict__ d, double* __r
   }
 }
 
+// Gauss-Jordan inversion in place with partial pivoting, one thread block per
+// dense block, the block held in shared memory (column-major M[i + j nb]).
+// Step k: pick the row p >= k with the largest |M[p][k]| (ties: smallest p),
+// swap rows k and p, scale row k by 1 / M[k][k] with M[k][k] <- 1 first, and
+// for every other row i subtract M[i][k] times row k, with M[i][k] <- 0 first;
+// column k then holds the k-th column of the inverse of the eliminated matrix.
+// The row interchanges are undone at the end as column interchanges in reverse
+// order.
+constexpr int kInvMaxN = 128;
+
+
+__global__ void __launch_bounds__(256) k_block_invert(double* __restrict__ a, int nb, long long ncell,
+                                                       int* __restrict__ singular) {
+  extern __shared__ __align__(16) double sm_inv[];
+  __shared__ int perm[kInvMaxN];
+  __shared__ double wv[8];
+  __shared__ int wi[8];
+  __shared__ int piv_row;
+  const long long c = blockIdx.x;
+  if (c >= ncell) return;
+  double* M = sm_inv;
+  double* colk = M + nb * nb;
+  double* rowk = colk + nb;
+  double* g = a + c * (long long)nb * nb;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < nb * nb; t += nt) M[t] = g[t];
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    double best = -1.0;
+    int bi = nb;
+    for (int i = k + tid; i < nb; i += nt) {
+      const double v = fabs(M[i + k * nb]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = wv[0];
+      int r = wi[0];
+      for (int w = 1; w < nt / 32; ++w)
+        if (wv[w] > b || (wv[w] == b && wi[w] < r)) {
+          b = wv[w];
+          r = wi[w];
+        }
+      if (r >= nb) r = k;   // no finite candidate: the pivot test below rejects the block
+      piv_row = r;
+      perm[k] = r;
+    }
+    __syncthreads();
+    const int p = piv_row;
+    if (p != k)
+      for (int j = tid; j < nb; j += nt) {
+        const double t = M[k + j * nb];
+        M[k + j * nb] = M[p + j * nb];
+        M[p + j * nb] = t;
+      }
+    __syncthreads();
+    const double piv = M[k + k * nb];
+    if (piv == 0.0 || !isfinite(piv)) {   // the same shared value for every thread
+      if (tid == 0) *singular = 1;
+      return;
+    }
+    const double pinv = 1.0 / piv;
+    for (int i = tid; i < nb; i += nt) colk[i] = M[i + k * nb];
+    __syncthreads();
+    for (int j = tid; j < nb; j += nt) {
+      const double v = (j == k ? 1.0 : M[k + j * nb]) * pinv;
+      M[k + j * nb] = v;
+      rowk[j] = v;
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * nb; t += nt) {
+      const int i = t % nb, j = t / nb;
+      if (i == k) continue;
+      M[t] = fma(-colk[i], rowk[j], j == k ? 0.0 : M[t]);
+    }
+    __syncthreads();
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = tid; i < nb; i += nt) {
+        const double t = M[i + k * nb];
+        M[i + k * nb] = M[i + p * nb];
+        M[i + p * nb] = t;
+      }
+    __syncthreads();
+  }
+  for (int t = tid; t < nb * nb; t += nt) g[t] = M[t];
+}
+
+// P0 restriction: out[c] = sum of cell c's n3 values, one warp per cell, lanes
+// stride the cell, then a fixed shuffle tree (deterministic order).
+template <typename T>
+__global__ void k_cell_sums(long long ncell, int n3, const T* __restrict__ r, double* __restrict__ out) {
+  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const T* rc = r + c * n3;
+  double s = 0.0;
+  for (int i = lane; i < n3; i += 32) s += (double)rc[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
+}
+
+// P0 prolongation: u[c n3 + i] += uhat[c].
+template <typename T>
+__global__ void k_cell_add(long long ncell, int n3, const double* __restrict__ uhat, T* __restrict__ u) {
+  const long long n = ncell * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    u[i] = (T)((double)u[i] + uhat[i / n3]);
+}
+
 }  // namespace
 
 cudaError_t cell_records(const MeshParams& mp, double* rec64, float* rec32, cudaStream_t s) {
@@ -260,6 +389,42 @@ cudaError_t cell_records(const MeshParams& mp, double* rec64, float* rec32, cuda
 
 cudaError_t vec_inverse(long long n, const double* d, double* i64, float* i32, cudaStream_t s) {
   k_inverse<<<grid1(n), kThreads, 0, s>>>(n, d, i64, i32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t cell_sums(long long ncell, int n3, const void* r, double* out, bool fp32, cudaStream_t s) {
+  if (ncell == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((ncell * 32 + 255) / 256);
+  if (fp32)
+    k_cell_sums<float><<<grid, 256, 0, s>>>(ncell, n3, (const float*)r, out);
+  else
+    k_cell_sums<double><<<grid, 256, 0, s>>>(ncell, n3, (const double*)r, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t cell_add(long long ncell, int n3, const double* uhat, void* u, bool fp32, cudaStream_t s) {
+  if (ncell == 0) return cudaSuccess;
+  const long long n = ncell * n3;
+  if (fp32)
+    k_cell_add<float><<<grid1(n), kThreads, 0, s>>>(ncell, n3, uhat, (float*)u);
+  else
+    k_cell_add<double><<<grid1(n), kThreads, 0, s>>>(ncell, n3, uhat, (double*)u);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t block_invert(double* a, int nb, long long ncell, int* singular, cudaStream_t s) {
+  if (ncell == 0) return cudaSuccess;
+  if (nb < 1 || nb > kInvMaxN) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)nb * nb + 2 * nb) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_block_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (ncell > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_block_invert<<<(unsigned)ncell, nb >= 64 ? 256 : 128, smem, s>>>(a, nb, ncell, singular);
   count_launch();
   return cudaGetLastError();
 }

@@ -20,8 +20,9 @@ STATUS = {0: "DGMG_OK", 1: "DGMG_ERR_ARG", 2: "DGMG_ERR_OOM", 3: "DGMG_ERR_CUDA"
           5: "DGMG_ERR_NOT_CONVERGED", 6: "DGMG_ERR_BREAKDOWN", 7: "DGMG_ERR_TIMEOUT"}
 FP64, FP32, DF64 = 0, 1, 2
 KRYLOV_CG, KRYLOV_FCG, KRYLOV_FGMRES = 0, 1, 2
-INNER_PCG, INNER_GMRES = 0, 1
-COARSE_AMG, COARSE_NONE = 0, 1
+INNER_PCG, INNER_GMRES, INNER_DIRECT, INNER_GMRES_TRIDIAG = 0, 1, 2, 3
+COARSE_AMG, COARSE_NONE, COARSE_P0 = 0, 1, 2
+STOP_RESIDUAL, STOP_ENERGY = 0, 1
 SMOOTHER_JACOBI, SMOOTHER_SSOR = 0, 1
 
 
@@ -37,7 +38,8 @@ class SolveOpts(ctypes.Structure):
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("eps_inner", ctypes.c_double),
                 ("maxit_inner", ctypes.c_int), ("inner", ctypes.c_int), ("inner_restart", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("timing", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("apply_prec", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("apply_prec", ctypes.c_int), ("graph", ctypes.c_int),
+                ("stop", ctypes.c_int), ("delay", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -46,7 +48,8 @@ class SolveStats(ctypes.Structure):
                 ("inner_its_total", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
                 ("zero_sweeps", ctypes.c_longlong),
                 ("applies", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
-                ("ms_smooth", ctypes.c_double), ("ms_apply", ctypes.c_double)]
+                ("ms_smooth", ctypes.c_double), ("ms_apply", ctypes.c_double),
+                ("energy_estimate", ctypes.c_double), ("iterations_run", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +83,11 @@ _SIG = {
     "dgmg_solve": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)]),
     "dgmg_restrict_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P]),
     "dgmg_set_launch_shape": (_I, [_P, _I, _I, _I]),
+    "dgmg_block_inverse": (_I, [_P, _I, _P]),
+    "dgmg_restrict_p0": (_I, [_P, _P, _P, _I]),
+    "dgmg_prolong_add_p0": (_I, [_P, _P, _P, _I]),
+    "dgmg_coarse_matrix_p0": (_I, [_P, _P]),
+    "dgmg_coarse_cycle_p0": (_I, [_P, _P, _P]),
     "dgmg_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
@@ -238,6 +246,12 @@ class Context:
                                             inner_restart, 1 if symmetric else 0, _prec(u, df64),
                                             _ptr(inner_its)))
 
+    def block_inverse(self, prec=FP64, out=None):
+        """Build the stored D_T^-1 of every cell (inner = INNER_DIRECT) in FP64
+        or FP32; `out` (device tensor of ncell n^6 values) receives a copy,
+        column-major per block."""
+        self._check(self.lib.dgmg_block_inverse(self.h, prec, _ptr(out)))
+
     def restrict(self, r, r_hat):
         self._check(self.lib.dgmg_restrict(self.h, _ptr(r), _ptr(r_hat), _prec(r)))
 
@@ -252,6 +266,22 @@ class Context:
 
     def coarse_cycle(self, r_hat, u_hat):
         self._check(self.lib.dgmg_coarse_cycle(self.h, _ptr(r_hat), _ptr(u_hat)))
+
+    # ------------------------------------------------------------ P0 subspace
+    def restrict_p0(self, r, r_hat):
+        self._check(self.lib.dgmg_restrict_p0(self.h, _ptr(r), _ptr(r_hat), _prec(r)))
+
+    def prolong_add_p0(self, u_hat, u):
+        self._check(self.lib.dgmg_prolong_add_p0(self.h, _ptr(u_hat), _ptr(u), _prec(u)))
+
+    def coarse_matrix_p0(self):
+        s = self.sizes()
+        st = np.zeros(27 * s["ncell"])
+        self._check(self.lib.dgmg_coarse_matrix_p0(self.h, st.ctypes.data))
+        return st.reshape(s["ncell"], 27)
+
+    def coarse_cycle_p0(self, r_hat, u_hat):
+        self._check(self.lib.dgmg_coarse_cycle_p0(self.h, _ptr(r_hat), _ptr(u_hat)))
 
     def vcycle(self, f, u, opts=None):
         o = opts if opts is not None else default_opts()
@@ -300,4 +330,4 @@ def exported_symbols(header_path=None):
     import re
     header_path = header_path or os.path.join(_build.INCLUDE, "dgmg.h")
     text = open(header_path).read()
-    return sorted(set(re.findall(r"\b(dgmg_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(dgmg_[a-z0-9_]+)\s*\(", text)))

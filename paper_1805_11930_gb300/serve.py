@@ -13,9 +13,11 @@ fixed order, so a request's result does not depend on what runs beside it.
     python -m paper_1805_11930_gb300.serve [--requests 512] [--slots 4] [--rates 0.5,0.8,1.0,1.2]
 
 measures the single-stream capacity (requests served back to back on one
-worker), then for each rate multiplier replays a seeded Poisson arrival trace
-at that multiple of the capacity and prints solves/s and p50 / p99 latency
-(arrival to completion) as one JSON line per rate.
+worker, mixed precision) and, on the same requests, the plain FP64 solve
+(FP64 smoother and CG) as the reference point, then for each rate
+multiplier replays a seeded Poisson arrival trace at that multiple of the
+capacity and prints solves/s and p50 / p99 latency (arrival to completion) as
+one JSON line per rate.
 """
 import argparse
 import collections
@@ -218,7 +220,13 @@ def main():
     one.close()
     cap = summarize(cap_trace)
     capacity = 1.0 / cap["mean_service_s"]
-    print(json.dumps({"single_stream": cap, "capacity_req_per_s": round(capacity, 4)}), flush=True)
+    # the plain FP64 solve of the same requests, back to back
+    fp64 = SolveServer(DeviceRunner(smoother_prec=0, krylov=0), slots=1, hbm_budget=budget)
+    fp64_trace = make_trace(args.capacity_requests, None, seed=SEED + 1, **rng_kw)
+    fp64.run(fp64_trace)
+    fp64.close()
+    print(json.dumps({"single_stream": cap, "capacity_req_per_s": round(capacity, 4),
+                      "fp64_single_stream": summarize(fp64_trace)}), flush=True)
     for mult in [float(x) for x in args.rates.split(",")]:
         trace = make_trace(args.requests, mult * capacity, seed=SEED, **rng_kw)
         srv = SolveServer(runner, slots=args.slots, hbm_budget=budget)

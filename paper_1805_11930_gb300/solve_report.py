@@ -7,7 +7,9 @@ then the solve to a 1e-8 relative residual from u = 0: in FP64; with the
 mixed-precision V-cycle (FP32 smoother, inner solves and residual; FP64 outer
 Krylov, dots, coarse solve and final residual check); and with the V-cycle and
 the outer operator in double-float arithmetic on FP64 vectors (the final
-residual check stays FP64).  Reports the median
+residual check stays FP64); for p <= 4, also with exact block solves by the
+stored block inverses (inner = DIRECT, FP64 and mixed; the inverse set-up time
+is reported separately).  Reports the median
 solve time over --repeat runs (CUDA events, inputs resident), outer
 iterations, mean / max inner iterations, the recomputed FP64 residual, the
 difference between the mixed and FP64 solutions and, where the workload has
@@ -59,6 +61,14 @@ def run(name, repeat):
     if w["b"] is None:       # the double-float kernels cover diffusion
         variants.append(("df64", dgmg.default_opts(krylov=flex, inner=inner, smoother_prec=dgmg.DF64,
                                                    apply_prec=dgmg.DF64, maxit=1000, **extra)))
+    if w["p"] <= 4:          # stored block inverses (partially matrix-free smoother)
+        t1 = time.perf_counter()
+        ctx.block_inverse(dgmg.FP64)
+        ctx.block_inverse(dgmg.FP32)
+        out["block_inverse_setup_s"] = round(time.perf_counter() - t1, 3)
+        variants.append(("fp64_direct", dgmg.default_opts(krylov=kry, inner=dgmg.INNER_DIRECT, maxit=1000, **extra)))
+        variants.append(("mixed_direct", dgmg.default_opts(krylov=flex, inner=dgmg.INNER_DIRECT,
+                                                           smoother_prec=dgmg.FP32, maxit=1000, **extra)))
     for tag, opts in variants:
         u = torch.zeros_like(f)
         ms, st = [], None
@@ -76,7 +86,7 @@ def run(name, repeat):
                     "iterations": st["iterations"], "rel_residual": st["rel_residual"],
                     "inner_mean": round(st["inner_mean"], 2), "inner_max": st["inner_max"],
                     "us_per_dof": round(statistics.median(ms) * 1e3 / s["ndof"], 5)}
-    for tag in [t for t in ("mixed", "df64") if t in sols]:
+    for tag in [t for t in sols if t != "fp64"]:
         d = (sols[tag] - sols["fp64"]).norm() / sols["fp64"].norm()
         out[f"{tag}_vs_fp64_rel_diff"] = float(d)
     if w["exact"] is not None:

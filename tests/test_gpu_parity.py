@@ -551,3 +551,267 @@ def test_autotune_choices_and_bitwise_solve():
         ctx.set_launch_shape(dgmg.FP64, 3, 0)
     with pytest.raises(dgmg.DgmgError):
         ctx.set_launch_shape(7, 4, 4)
+
+
+# ------------------------------------------------------------- stored inverses
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full"])
+def test_block_inverse_matches_oracle_blocks(name):
+    """dgmg_block_inverse: every stored block times the oracle's assembled
+    diagonal block D_T is the identity to 1e-12 (FP64), and the FP32 copy is
+    the FP64 one rounded (1e-6 relative per block)."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    nb = P.N
+    out = torch.empty(P.ncell * nb * nb, dtype=torch.float64, device="cuda")
+    ctx.block_inverse(dgmg.FP64, out)
+    inv = out.cpu().numpy().reshape(P.ncell, nb, nb).transpose(0, 2, 1)    # column-major per block
+    D = solvers.BlockJacobi(A, nb, inner="lu").D
+    eye = np.eye(nb)
+    for c in range(P.ncell):
+        assert np.abs(inv[c] @ D[c] - eye).max() < 1e-12 * max(1.0, np.linalg.cond(D[c]) * 1e-3)
+    out32 = torch.empty(P.ncell * nb * nb, dtype=torch.float32, device="cuda")
+    ctx.block_inverse(dgmg.FP32, out32)
+    inv32 = out32.cpu().numpy().astype(np.float64).reshape(P.ncell, nb, nb).transpose(0, 2, 1)
+    for c in range(P.ncell):
+        assert rel_err(inv32[c], inv[c]) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full"])
+def test_block_smooth_direct_matches_exact_block_jacobi(name):
+    """inner = DIRECT (stored inverses): two block-Jacobi sweeps equal the
+    oracle's dense-LU block-Jacobi to 1e-12 in FP64 and 1e-5 in FP32, every
+    cell reporting 0 inner iterations."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=31)
+    u0 = inputs.random_dg_vector(P.ndof, seed=32)
+    ref = solvers.BlockJacobi(A, P.N, inner="lu")(f, u0, 2, 0.8)
+    its = torch.full((P.ncell,), 7, dtype=torch.int32, device="cuda")
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=2, omega=0.8, inner=dgmg.INNER_DIRECT, inner_its=its)
+    assert rel_err(u.cpu().numpy(), ref) < 1e-12
+    assert int(its.abs().max()) == 0
+    u32 = dev(u0).float()
+    ctx.block_smooth(dev(f).float(), u32, nsweep=2, omega=0.8, inner=dgmg.INNER_DIRECT)
+    assert rel_err(u32.double().cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["p2_mixed", "p3_adv"])
+def test_block_ssor_direct_matches_oracle(name):
+    """Multicolour block-SSOR with exact block solves by the stored inverses
+    against the oracle's colour-ordered SSOR with dense-LU blocks."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=33)
+    u0 = inputs.random_dg_vector(P.ndof, seed=34)
+    ref = solvers.MulticolourBlockSOR(A, P.N, P.nc, symmetric=True, inner="lu")(f, u0, 1, 1.1)
+    u = dev(u0)
+    ctx.block_sor(dev(f), u, nsweep=1, omega=1.1, inner=dgmg.INNER_DIRECT, symmetric=True)
+    assert rel_err(u.cpu().numpy(), ref) < 1e-12
+
+
+def test_solve_direct_blocks_c1_and_rejections():
+    """CG with a V-cycle whose smoother uses the stored inverses reaches 1e-8
+    on the Poisson workload in no more iterations than inner PCG; DF64 and
+    p > 4 reject DIRECT."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.poisson_sine(8, 2)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    u0 = torch.zeros_like(f)
+    s_pcg = ctx.solve(f, u0, dgmg.default_opts())
+    u1 = torch.zeros_like(f)
+    s_dir = ctx.solve(f, u1, dgmg.default_opts(inner=dgmg.INNER_DIRECT))
+    assert s_dir["converged"] and s_dir["rel_residual"] <= 1e-8
+    assert s_dir["iterations"] <= s_pcg["iterations"]
+    assert rel_err(u1.cpu().numpy(), u0.cpu().numpy()) < 1e-6
+    u2 = torch.zeros_like(f)
+    s32 = ctx.solve(f, u2, dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.FP32,
+                                             krylov=dgmg.KRYLOV_FCG))
+    assert s32["converged"] and s32["rel_residual"] <= 1e-8
+    with pytest.raises(dgmg.DgmgError):
+        ctx.solve(f, torch.zeros_like(f), dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.DF64))
+    w5 = inputs.lognormal(2, 5)
+    ctx5 = gpu_context(w5)
+    with pytest.raises(dgmg.DgmgError):
+        ctx5.block_inverse(dgmg.FP64)
+
+
+# ------------------------------------------------------------- tridiagonal inner preconditioner
+@pytest.mark.parametrize("name", ["p3_adv", "p4_full"])
+def test_block_smooth_gmres_tridiag_exact_blocks(name):
+    """GMRES(12) preconditioned by the tridiagonal part of D_T (Thomas), eps =
+    1e-13: two sweeps equal the oracle's dense-LU block-Jacobi to 1e-9."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=41)
+    u0 = inputs.random_dg_vector(P.ndof, seed=42)
+    ref = solvers.BlockJacobi(A, P.N, inner="lu")(f, u0, 2, 0.8)
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=2, omega=0.8, eps=1e-13, maxit=20 * P.N, inner=dgmg.INNER_GMRES_TRIDIAG,
+                     inner_restart=12)
+    assert rel_err(u.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["p2_mixed", "p3_adv"])
+def test_block_smooth_gmres_tridiag_matches_oracle(name):
+    """eps = 1e-2: the oracle's GMRES(12) with the Thomas preconditioner; cells
+    with equal iteration counts agree to 1e-10, every cell meets its stopping
+    test, in FP64 and (stopping test to 1e-4) in FP32."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    f = inputs.random_dg_vector(P.ndof, seed=43)
+    u0 = inputs.random_dg_vector(P.ndof, seed=44)
+    S = solvers.BlockJacobi(A, P.N, inner="gmres", eps=1e-2, restart=12, maxit=10 * P.N, precond="tridiag")
+    ref = S(f, u0, 1, 1.0)
+    N = P.N
+    d = f - A @ u0
+    for dt, tol in ((torch.float64, 1e-2 * (1 + 1e-9)), (torch.float32, 1.0001e-2 + 1e-4)):
+        its = torch.zeros(P.ncell, dtype=torch.int32, device="cuda")
+        u = dev(u0).to(dt)
+        ctx.block_smooth(dev(f).to(dt), u, nsweep=1, omega=1.0, eps=1e-2, maxit=10 * N,
+                         inner=dgmg.INNER_GMRES_TRIDIAG, inner_restart=12, inner_its=its)
+        got = u.double().cpu().numpy()
+        its = its.cpu().numpy()
+        same = its == S.last_its
+        assert same.mean() > 0.9
+        for c in range(P.ncell):
+            sl = slice(c * N, (c + 1) * N)
+            delta = got[sl] - u0[sl]
+            assert np.linalg.norm(d[sl] - S.D[c] @ delta) <= tol * np.linalg.norm(d[sl])
+            if dt == torch.float64 and same[c]:
+                assert rel_err(delta, ref[sl] - u0[sl]) < 1e-10
+
+
+def test_tridiag_preconditioner_convection_dominated_gpu():
+    """Grid Peclet number 2000, b = (1, 0, 0), p = 3: with diag(D_T) the inner
+    GMRES runs into its 200-iteration cap in most cells; with the Thomas
+    preconditioner every cell stops within 30 iterations."""
+    from paper_1805_11930_gb300 import dgmg
+    nc, L = (4, 4, 4), (1.0, 1.0, 1.0)
+    b = inputs.vertex_field(nc, L, lambda x, y, z: np.stack([np.ones_like(x), 0 * x, 0 * x], -1))
+    w = custom(nc, L, 3, [0] * 6, np.full(64, 0.25 / 2000), b=b)
+    ctx = gpu_context(w)
+    nd = ctx.sizes()["ndof"]
+    f = dev(inputs.random_dg_vector(nd, seed=45))
+    res = {}
+    for inner in (dgmg.INNER_GMRES, dgmg.INNER_GMRES_TRIDIAG):
+        its = torch.zeros(64, dtype=torch.int32, device="cuda")
+        u = torch.zeros(nd, dtype=torch.float64, device="cuda")
+        ctx.block_smooth(f, u, nsweep=1, omega=1.0, eps=1e-2, maxit=200, inner=inner, inner_restart=12,
+                         inner_its=its)
+        res[inner] = its.cpu().numpy()
+    assert (res[dgmg.INNER_GMRES] == 200).mean() > 0.5
+    assert res[dgmg.INNER_GMRES_TRIDIAG].max() <= 30
+
+
+# ------------------------------------------------------------- P0 coarse space
+def _stencil_dense(st, dims):
+    Vx, Vy, Vz = dims
+    n = Vx * Vy * Vz
+    out = np.zeros((n, n))
+    for v in range(n):
+        ix, iy, iz = v % Vx, (v // Vx) % Vy, v // (Vx * Vy)
+        for k in range(27):
+            jx, jy, jz = ix + k % 3 - 1, iy + (k // 3) % 3 - 1, iz + k // 9 - 1
+            if 0 <= jx < Vx and 0 <= jy < Vy and 0 <= jz < Vz:
+                out[v, jx + Vx * (jy + Vy * jz)] = st[v, k]
+            else:
+                assert st[v, k] == 0.0
+    return out
+
+
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p6_adv"])
+def test_p0_transfer_and_coarse_matrix(name):
+    """P0 restriction (cell sums) and prolongation against P^T r and u + P u_hat
+    (FP64 1e-14, FP32 1e-6), and the re-discretised P0 A_hat against the
+    oracle's Galerkin product P^T A P to 1e-12."""
+    w, P, A = oracle_matrix(name)
+    ctx = gpu_context(w)
+    P0 = transfer.p0_prolongation(P)
+    r = inputs.random_dg_vector(P.ndof, seed=51)
+    rh = torch.empty(P.ncell, dtype=torch.float64, device="cuda")
+    ctx.restrict_p0(dev(r), rh)
+    assert rel_err(rh.cpu().numpy(), P0.T @ r) < 1e-14
+    ctx.restrict_p0(dev(r).float(), rh)
+    assert rel_err(rh.cpu().numpy(), P0.T @ r) < 1e-6
+    uh = inputs.random_dg_vector(P.ncell, seed=52)
+    u = inputs.random_dg_vector(P.ndof, seed=53)
+    ud = dev(u)
+    ctx.prolong_add_p0(dev(uh), ud)
+    assert rel_err(ud.cpu().numpy(), u + P0 @ uh) < 1e-14
+    G = transfer.p0_matrix(A, P).toarray()
+    Ah = _stencil_dense(ctx.coarse_matrix_p0(), P.nc)
+    assert np.abs(Ah - G).max() < 1e-12 * np.abs(G).max()
+
+
+@pytest.mark.parametrize("nc", [(6, 5, 4), (12, 10, 9)])
+def test_p0_amg_cycle(nc):
+    """Device AMG V-cycle on the P0 matrix equals the oracle's AMG on
+    P^T A P with the cell grid as its structured grid."""
+    rng = np.random.default_rng(9)
+    w = custom(nc, (1, 1, 1), 2, [0] * 6, np.exp(rng.normal(size=int(np.prod(nc)))))
+    P = oracle_problem(w)
+    am = amg.AggregationAMG(transfer.p0_matrix(P.assemble(), P), P.nc, coarse_size=512)
+    ctx = gpu_context(w)
+    r = rng.normal(size=P.ncell)
+    out = torch.empty(P.ncell, dtype=torch.float64, device="cuda")
+    ctx.coarse_cycle_p0(dev(r), out)
+    assert rel_err(out.cpu().numpy(), am.vcycle(r)) < 1e-11
+
+
+def test_vcycle_p0_matches_oracle_and_solve():
+    """One V-cycle with the P0 coarse space (near-exact blocks) against the
+    oracle's Algorithm 1 with P0, dense-LU blocks and the same AMG; then CG
+    with that V-cycle reaches 1e-8 on the Poisson workload, FP64 and mixed."""
+    from paper_1805_11930_gb300 import dgmg
+    w = make_case("p2_mixed")
+    P = oracle_problem(w)
+    A = P.assemble()
+    P0 = transfer.p0_prolongation(P)
+    am = amg.AggregationAMG(transfer.p0_matrix(A, P), P.nc, coarse_size=512)
+    V = solvers.HybridVCycle(A, P0, solvers.BlockJacobi(A, P.N, inner="lu"), am.vcycle, omega=0.8)
+    f = inputs.random_dg_vector(P.ndof, seed=54)
+    ref = V(f)
+    ctx = gpu_context(w)
+    u = torch.zeros(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.vcycle(dev(f), u, dgmg.default_opts(omega=0.8, eps_inner=1e-13, maxit_inner=10 * P.N,
+                                            coarse=dgmg.COARSE_P0))
+    assert rel_err(u.cpu().numpy(), ref) < 1e-9
+    w1 = inputs.poisson_sine(8, 2)
+    c1 = gpu_context(w1)
+    f1 = gpu_rhs(c1, w1, torch)
+    for prec, kry in ((dgmg.FP64, dgmg.KRYLOV_CG), (dgmg.FP32, dgmg.KRYLOV_FCG)):
+        u1 = torch.zeros_like(f1)
+        st = c1.solve(f1, u1, dgmg.default_opts(coarse=dgmg.COARSE_P0, smoother_prec=prec, krylov=kry))
+        assert st["converged"] and st["rel_residual"] <= 1e-8
+
+
+def test_solve_energy_norm_stopping():
+    """stop = ENERGY (Strakos-Tichy estimate, error bandwidth 4, Sec. 4.4):
+    the solve stops once the estimate is <= rtol, reports k and k + 4
+    iterations, and the returned iterate's true relative energy error against
+    the oracle's direct solution is below rtol; FGMRES rejects the rule."""
+    import scipy.sparse.linalg as spla
+    from paper_1805_11930_gb300 import dgmg
+    rng = np.random.default_rng(61)
+    w = custom((4, 4, 3), (1.0, 1.0, 0.75), 2, [0] * 6, np.exp(2.0 * rng.normal(size=48)))
+    P = oracle_problem(w)
+    A = P.assemble().tocsc()
+    F = oracle_rhs(P, w)
+    xs = spla.spsolve(A, F)
+    ctx = gpu_context(w)
+    f = dev(F)
+    u = torch.zeros_like(f)
+    st = ctx.solve(f, u, dgmg.default_opts(stop=dgmg.STOP_ENERGY, rtol=1e-6))
+    assert st["converged"] and st["energy_estimate"] <= 1e-6
+    assert st["iterations_run"] == st["iterations"] + 4
+    e = u.cpu().numpy() - xs
+    assert np.sqrt(e @ (A @ e) / (xs @ (A @ xs))) <= 1e-6
+    with pytest.raises(dgmg.DgmgError):
+        ctx.solve(f, torch.zeros_like(f), dgmg.default_opts(stop=dgmg.STOP_ENERGY, krylov=dgmg.KRYLOV_FGMRES))
