@@ -166,6 +166,7 @@ def run_dgmg(args, rank, world, local_rank):
     clocks.start()
     stats = []
     step_ms = []
+    torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select the timed region
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -177,6 +178,7 @@ def run_dgmg(args, rank, world, local_rank):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         stats.append(st)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), world, dev)

@@ -83,6 +83,30 @@ def convection(n=64, p=3, kappa=1e-3):
                 f=f, g=_zero, j=None, exact=u)
 
 
+def convection_pe(n=32, p=3, pe=2000.0, bvec=(1.0, 0.5, 0.3)):
+    """Strongly convection-dominated flow of Sec. 4.3: constant b, kappa set by
+    the grid Peclet number Pe = max_i |b_i| h / kappa, manufactured solution
+    u = prod x_k (1 - x_k), homogeneous Dirichlet."""
+    h = 1.0 / n
+    kappa = max(abs(v) for v in bvec) * h / pe
+    bx, by, bz = bvec
+
+    def u(x, y, z):
+        return x * (1 - x) * y * (1 - y) * z * (1 - z)
+
+    def f(x, y, z):
+        lap = -2 * (y * (1 - y) * z * (1 - z) + x * (1 - x) * z * (1 - z) + x * (1 - x) * y * (1 - y))
+        ux = (1 - 2 * x) * y * (1 - y) * z * (1 - z)
+        uy = x * (1 - x) * (1 - 2 * y) * z * (1 - z)
+        uz = x * (1 - x) * y * (1 - y) * (1 - 2 * z)
+        return -kappa * lap + bx * ux + by * uy + bz * uz
+
+    nc = (n, n, n)
+    bfield = vertex_field(nc, (1.0, 1.0, 1.0), lambda x, y, z: np.stack([0 * x + bx, 0 * x + by, 0 * x + bz], -1))
+    return dict(name=f"convection_pe{int(pe)}_{n}^3_p{p}", nc=nc, L=(1.0, 1.0, 1.0), p=p, bc=[0] * 6,
+                K=np.full(n ** 3, kappa), b=bfield, c=None, f=f, g=_zero, j=None, exact=u)
+
+
 def reservoir_permeability(nc=(60, 220, 85), seed=SEED):
     """Diagonal K (ncell, 3) of the channelised layered field."""
     nx, ny, nz = nc

@@ -1,11 +1,15 @@
 """Small, fixed launch sequence of one kernel family, for ncu captures.
 
 python -m paper_1805_11930_gb300.profile_case --what apply|block|smooth --prec fp64|fp32 [--n 48] [--p 4]
+    [--inner pcg|direct] [--wpb-apply W] [--wpb-smooth W]
 
 Sets up the log-normal diffusion workload on an n^3 mesh (48^3 at p = 4 is
 13.8 M dofs, 110 MB per FP64 vector: larger than L2, a few hundred MB in
 total), runs two warm-up launches and then `--reps` launches of the chosen
 operation through the C ABI.  Prints the median CUDA-event time per launch.
+--inner direct times the smoother with the stored block inverses (built
+before the warm-up); --wpb-* set the launch shapes (warps per block) so that
+a capture can use the shapes the benchmark's autotuning picked.
 """
 import argparse
 import statistics
@@ -19,6 +23,9 @@ def main():
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--inner", default="pcg", choices=["pcg", "direct"])
+    ap.add_argument("--wpb-apply", type=int, default=0)
+    ap.add_argument("--wpb-smooth", type=int, default=0)
     args = ap.parse_args()
 
     import torch
@@ -29,6 +36,11 @@ def main():
     ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
     ctx.set_coefficients(w["K"])
     nd = ctx.sizes()["ndof"]
+    prec = dgmg.FP64 if args.prec == "fp64" else dgmg.FP32
+    ctx.set_launch_shape(prec, args.wpb_apply, args.wpb_smooth)
+    inner = dgmg.INNER_DIRECT if args.inner == "direct" else dgmg.INNER_PCG
+    if inner == dgmg.INNER_DIRECT:
+        ctx.block_inverse(prec)
     dt = torch.float64 if args.prec == "fp64" else torch.float32
     g = torch.Generator(device="cuda").manual_seed(1805)
     x = torch.rand(nd, dtype=dt, device="cuda", generator=g)
@@ -41,7 +53,7 @@ def main():
         elif args.what == "block":
             ctx.block_apply(x, y)
         else:
-            ctx.block_smooth(x, y, nsweep=1, omega=0.8, eps=1e-2)
+            ctx.block_smooth(x, y, nsweep=1, omega=0.8, eps=1e-2, inner=inner)
 
     for _ in range(2):
         op()
@@ -55,7 +67,7 @@ def main():
         b.record(stream)
         b.synchronize()
         ms.append(a.elapsed_time(b))
-    print(f"{args.what} {args.prec} n={args.n} p={args.p} ndof={nd}: median {statistics.median(ms):.4f} ms "
+    print(f"{args.what} {args.prec} {args.inner} n={args.n} p={args.p} ndof={nd}: median {statistics.median(ms):.4f} ms "
           f"({nd / statistics.median(ms) / 1e6:.3f} GDOF/s)")
     sys.stdout.flush()
 

@@ -7,8 +7,11 @@ own library context (re-used across requests).  A request is admitted, in
 arrival order, as soon as a worker is idle and its HBM footprint
 (footprint.library_bytes) fits into what the running requests leave of the
 budget; its set-up and solve then run on that worker's stream, overlapping on
-the device with the other workers' solves.  The library's kernels reduce in a
-fixed order, so a request's result does not depend on what runs beside it.
+the device with the other workers' solves.  Each worker's V-cycle is
+captured into a CUDA graph on its second use and replayed (opts.graph), which
+removes most of the per-kernel launch cost of small requests.  The library's
+kernels reduce in a fixed order, so a request's result does not depend on
+what runs beside it.
 
     python -m paper_1805_11930_gb300.serve [--requests 512] [--slots 4] [--rates 0.5,0.8,1.0,1.2]
 
@@ -107,7 +110,7 @@ class DeviceRunner:
             f = torch.empty(nd, dtype=torch.float64, device=f"cuda:{self.device}")
             ctx.assemble_rhs(f_qp, f)
             u = torch.zeros_like(f)
-            kw = dict(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
+            kw = dict(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG, graph=1)
             kw.update(self.opts)
             stats = ctx.solve(f, u, dgmg.default_opts(**kw), check=False)
             sol = u.cpu().numpy() if self.keep else None
@@ -221,7 +224,7 @@ def main():
     cap = summarize(cap_trace)
     capacity = 1.0 / cap["mean_service_s"]
     # the plain FP64 solve of the same requests, back to back
-    fp64 = SolveServer(DeviceRunner(smoother_prec=0, krylov=0), slots=1, hbm_budget=budget)
+    fp64 = SolveServer(DeviceRunner(smoother_prec=0, krylov=0, graph=0), slots=1, hbm_budget=budget)
     fp64_trace = make_trace(args.capacity_requests, None, seed=SEED + 1, **rng_kw)
     fp64.run(fp64_trace)
     fp64.close()

@@ -1,6 +1,6 @@
 """Time-to-solution report for the synthetic workloads.
 
-python -m paper_1805_11930_gb300.solve_report [--workloads poisson,lognormal,convection,reservoir] [--repeat 3]
+python -m paper_1805_11930_gb300.solve_report [--workloads poisson,lognormal,convection,reservoir,convection_pe2000] [--repeat 3]
 
 For each workload: set-up time (coefficients, diag(D_T), Q1 matrix, AMG),
 then the solve to a 1e-8 relative residual from u = 0: in FP64; with the
@@ -9,7 +9,11 @@ Krylov, dots, coarse solve and final residual check); and with the V-cycle and
 the outer operator in double-float arithmetic on FP64 vectors (the final
 residual check stays FP64); for p <= 4, also with exact block solves by the
 stored block inverses (inner = DIRECT, FP64 and mixed; the inverse set-up time
-is reported separately).  Reports the median
+is reported separately); the reservoir workload also with the P0 coarse
+space (the paper's choice for SPE10); the grid-Peclet-2000 convection
+workload (Sec. 4.3) with the paper's set-up: FGMRES preconditioned by two
+multicolour block-SSOR sweeps and no coarse correction, inner GMRES with the
+tridiagonal (Thomas) preconditioner.  Reports the median
 solve time over --repeat runs (CUDA events, inputs resident), outer
 iterations, mean / max inner iterations, the recomputed FP64 residual, the
 difference between the mixed and FP64 solutions and, where the workload has
@@ -39,6 +43,9 @@ def run(name, repeat):
         # high-contrast anisotropic K: three AMG cycles per coarse correction
         w, kry, inner = inputs.reservoir(), dgmg.KRYLOV_CG, dgmg.INNER_PCG
         extra = dict(coarse_cycles=3)
+    elif name == "convection_pe2000":
+        w, kry, inner = inputs.convection_pe(32, 3), dgmg.KRYLOV_FGMRES, dgmg.INNER_GMRES_TRIDIAG
+        extra = dict(smoother=dgmg.SMOOTHER_SSOR, coarse=dgmg.COARSE_NONE)
     else:
         raise ValueError(name)
     t0 = time.perf_counter()
@@ -61,6 +68,11 @@ def run(name, repeat):
     if w["b"] is None:       # the double-float kernels cover diffusion
         variants.append(("df64", dgmg.default_opts(krylov=flex, inner=inner, smoother_prec=dgmg.DF64,
                                                    apply_prec=dgmg.DF64, maxit=1000, **extra)))
+    if name == "reservoir":  # the piecewise-constant coarse space of the paper's SPE10 runs
+        variants.append(("fp64_p0", dgmg.default_opts(krylov=kry, inner=inner, maxit=1000, coarse=dgmg.COARSE_P0,
+                                                      coarse_cycles=3)))
+        variants.append(("mixed_p0", dgmg.default_opts(krylov=flex, inner=inner, smoother_prec=dgmg.FP32,
+                                                       maxit=1000, coarse=dgmg.COARSE_P0, coarse_cycles=3)))
     if w["p"] <= 4:          # stored block inverses (partially matrix-free smoother)
         t1 = time.perf_counter()
         ctx.block_inverse(dgmg.FP64)
@@ -111,7 +123,7 @@ def run(name, repeat):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workloads", default="poisson,lognormal,convection,reservoir")
+    ap.add_argument("--workloads", default="poisson,lognormal,convection,reservoir,convection_pe2000")
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     for name in args.workloads.split(","):

@@ -54,3 +54,28 @@ def test_poisson_arrivals_are_seeded():
     b = [x.arrival for x in serve.make_trace(50, 10.0)]
     assert a == b and a[0] == 0.0 and all(y >= x for x, y in zip(a, a[1:]))
     assert 2.5 < a[-1] < 8.0      # 49 gaps of mean 0.1 s
+
+
+class FailingRunner(FakeRunner):
+    """Raises for some requests, as a runner does when the library returns an
+    error status (a failed allocation, a rejected argument)."""
+
+    def __init__(self, bad, **kw):
+        super().__init__(**kw)
+        self.bad = set(bad)
+
+    def __call__(self, req):
+        if req.rid in self.bad:
+            raise RuntimeError(f"request {req.rid}: DGMG_ERR_OOM")
+        return super().__call__(req)
+
+
+def test_failed_requests_are_reported_and_release_their_slot():
+    trace = serve.make_trace(10, None, n_range=(8, 9), p_range=(2, 3))
+    srv = serve.SolveServer(FailingRunner({2, 7}, service=0.01), slots=2, hbm_budget=2 * trace[0].footprint)
+    srv.run(trace)
+    srv.close()
+    s = serve.summarize(trace)
+    assert s["errors"] == 2 and s["completed"] == 8
+    assert [r.rid for r in trace if r.error] == [2, 7] and all("DGMG_ERR_OOM" in trace[i].error for i in (2, 7))
+    assert srv._used == 0 and srv._idle == 2      # the failed requests gave back slot and memory
