@@ -28,7 +28,12 @@ Readings of the paper used below:
   cell i+1 and nu_F = +e_k; on boundary faces nu is the outward normal;
 * all integrals use the tensor Gauss rule with m = p+1 points per direction;
 * K is given per cell (scalar, diagonal or full symmetric 3x3), c per cell,
-  and b as a continuous trilinear (Q1) vertex field.
+  and b as a continuous trilinear (Q1) vertex field; or K and c are
+  functions of the position (K_fn, c_fn), evaluated at every quadrature
+  point, as in the paper's inhomogeneous test K(x) = sum_k P_k(x_k) n_k n_k^T,
+  c(x) = gamma |x|^2 (Sec. 4.2).  A function K is continuous, so both traces
+  on a face take the same value K(x); delta, the weights and the penalty are
+  then evaluated point by point.
 """
 import itertools
 
@@ -57,7 +62,7 @@ class Problem:
     """
 
     def __init__(self, nx, ny, nz, lx, ly, lz, p, bc, K, b_vertex=None,
-                 c_cell=None, alpha=1.25):
+                 c_cell=None, alpha=1.25, K_fn=None, c_fn=None):
         if p < 1:
             raise ValueError("p >= 1 required")
         self.nc = (int(nx), int(ny), int(nz))
@@ -86,6 +91,7 @@ class Problem:
         self.K = Kf
         self.b = None if b_vertex is None else np.asarray(b_vertex, dtype=np.float64).reshape(self.nvert, 3)
         self.c = None if c_cell is None else np.asarray(c_cell, dtype=np.float64).reshape(self.ncell)
+        self.K_fn, self.c_fn = K_fn, c_fn       # pointwise coefficients (replace K, c when given)
         self.gll, self.gll_w = quad.gauss_lobatto(self.n)
         self.gq, self.gw = quad.gauss_legendre(self.m)
         self._volume_tables()
@@ -172,6 +178,14 @@ class Problem:
             out += wgt[:, None] * self.b[self.vertex_index(cx + ox, cy + oy, cz + oz)][None, :]
         return out
 
+    def K_points(self, c, xi):
+        """K at reference points xi (P, 3) of cell c: (P, 3, 3), from K_fn at
+        the physical points, or the cell's constant K."""
+        xi = np.atleast_2d(xi)
+        if self.K_fn is None:
+            return np.broadcast_to(self.K[c], (xi.shape[0], 3, 3))
+        return np.asarray(self.K_fn(self.cell_origin(c)[None, :] + xi * self.h[None, :]), dtype=np.float64)
+
     def c_of(self, c):
         return 0.0 if self.c is None else float(self.c[c])
 
@@ -195,13 +209,21 @@ class Problem:
         (K grad u - b u, grad v)_T + (c u, v)_T by Gauss quadrature."""
         w = self.vol_w
         val, g = self.vol_val, self.vol_grad
-        K = self.K[c]
         bq = self.b_at(c, self.vol_xi)
-        A = np.einsum('q,kl,qjl,qik->ij', w, K, g, g, optimize=True)
+        if self.K_fn is None:
+            K = self.K[c]
+            A = np.einsum('q,kl,qjl,qik->ij', w, K, g, g, optimize=True)
+        else:
+            Kq = self.K_points(c, self.vol_xi)
+            A = np.einsum('q,qkl,qjl,qik->ij', w, Kq, g, g, optimize=True)
         A -= np.einsum('q,qk,qj,qik->ij', w, bq, val, g, optimize=True)
-        cc = self.c_of(c)
-        if cc != 0.0:
-            A += cc * np.einsum('q,qj,qi->ij', w, val, val, optimize=True)
+        if self.c_fn is not None:
+            X = self.cell_origin(c)[None, :] + self.vol_xi * self.h[None, :]
+            A += np.einsum('q,q,qj,qi->ij', w, self.c_fn(X), val, val, optimize=True)
+        else:
+            cc = self.c_of(c)
+            if cc != 0.0:
+                A += cc * np.einsum('q,qj,qi->ij', w, val, val, optimize=True)
         return A
 
     def interior_face_matrix(self, cm, k):
@@ -220,23 +242,37 @@ class Problem:
         gp = gp / self.h[None, None, :]
         nu = np.zeros(3)
         nu[k] = 1.0
-        Km, Kp = self.K[cm], self.K[cp]
-        dm, dp = nu @ Km @ nu, nu @ Kp @ nu
-        wm, wp = dp / (dm + dp), dm / (dm + dp)
         F = len(w)
         VM = np.concatenate([vm, np.zeros((F, N))], axis=1)
         VP = np.concatenate([np.zeros((F, N)), vp], axis=1)
-        FM = np.concatenate([np.einsum('l,qjl->qj', Km @ nu, gm), np.zeros((F, N))], axis=1)
-        FP = np.concatenate([np.zeros((F, N)), np.einsum('l,qjl->qj', Kp @ nu, gp)], axis=1)
         jump = VM - VP
-        avg = wm * FM + wp * FP
         bnu = self.b_at(cm, xm) @ nu
         Phi = np.where(bnu[:, None] >= 0.0, bnu[:, None] * VM, bnu[:, None] * VP)
+        if self.K_fn is None:
+            Km, Kp = self.K[cm], self.K[cp]
+            dm, dp = nu @ Km @ nu, nu @ Kp @ nu
+            wm, wp = dp / (dm + dp), dm / (dm + dp)
+            FM = np.concatenate([np.einsum('l,qjl->qj', Km @ nu, gm), np.zeros((F, N))], axis=1)
+            FP = np.concatenate([np.zeros((F, N)), np.einsum('l,qjl->qj', Kp @ nu, gp)], axis=1)
+            avg = wm * FM + wp * FP
+            gamma = self.penalty_interior(dm, dp, k)
+            A = np.einsum('q,qJ,qI->IJ', w, Phi, jump, optimize=True)
+            A -= np.einsum('q,qJ,qI->IJ', w, avg, jump, optimize=True)
+            A -= np.einsum('q,qI,qJ->IJ', w, avg, jump, optimize=True)
+            A += gamma * np.einsum('q,qJ,qI->IJ', w, jump, jump, optimize=True)
+            return A, cp
+        # pointwise K (the same value from both sides): weights, delta and gamma per point
+        Km, Kp = self.K_points(cm, xm), self.K_points(cp, xp)
+        dm, dp = Km @ nu @ nu, Kp @ nu @ nu
+        wm, wp = dp / (dm + dp), dm / (dm + dp)
+        FM = np.concatenate([np.einsum('ql,qjl->qj', Km @ nu, gm), np.zeros((F, N))], axis=1)
+        FP = np.concatenate([np.zeros((F, N)), np.einsum('ql,qjl->qj', Kp @ nu, gp)], axis=1)
+        avg = wm[:, None] * FM + wp[:, None] * FP
         gamma = self.penalty_interior(dm, dp, k)
         A = np.einsum('q,qJ,qI->IJ', w, Phi, jump, optimize=True)
         A -= np.einsum('q,qJ,qI->IJ', w, avg, jump, optimize=True)
         A -= np.einsum('q,qI,qJ->IJ', w, avg, jump, optimize=True)
-        A += gamma * np.einsum('q,qJ,qI->IJ', w, jump, jump, optimize=True)
+        A += np.einsum('q,q,qJ,qI->IJ', w, gamma, jump, jump, optimize=True)
         return A, cp
 
     def boundary_face_block(self, c, k, side):
@@ -247,16 +283,25 @@ class Problem:
         g = g / self.h[None, None, :]
         nu = np.zeros(3)
         nu[k] = 1.0 if side == 1 else -1.0
-        Kc = self.K[c]
-        delta = nu @ Kc @ nu
-        fl = np.einsum('l,qjl->qj', Kc @ nu, g)          # nu . K grad psi_j
         bnu = self.b_at(c, xi) @ nu
         Phi = np.where(bnu[:, None] >= 0.0, bnu[:, None] * v, 0.0)
-        gamma = self.penalty_boundary(delta, k)
+        if self.K_fn is None:
+            Kc = self.K[c]
+            delta = nu @ Kc @ nu
+            fl = np.einsum('l,qjl->qj', Kc @ nu, g)          # nu . K grad psi_j
+            gamma = self.penalty_boundary(delta, k)
+            A = np.einsum('q,qj,qi->ij', w, Phi, v, optimize=True)
+            A -= np.einsum('q,qj,qi->ij', w, fl, v, optimize=True)
+            A -= np.einsum('q,qi,qj->ij', w, fl, v, optimize=True)
+            A += gamma * np.einsum('q,qj,qi->ij', w, v, v, optimize=True)
+            return A
+        Kq = self.K_points(c, xi)
+        gamma = self.penalty_boundary(Kq @ nu @ nu, k)
+        fl = np.einsum('ql,qjl->qj', Kq @ nu, g)
         A = np.einsum('q,qj,qi->ij', w, Phi, v, optimize=True)
         A -= np.einsum('q,qj,qi->ij', w, fl, v, optimize=True)
         A -= np.einsum('q,qi,qj->ij', w, fl, v, optimize=True)
-        A += gamma * np.einsum('q,qj,qi->ij', w, v, v, optimize=True)
+        A += np.einsum('q,q,qj,qi->ij', w, gamma, v, v, optimize=True)
         return A
 
     def is_boundary(self, c, k, side):
@@ -383,15 +428,22 @@ class Problem:
                     if g_qp is None:
                         continue
                     gv = np.asarray(g_qp, dtype=np.float64)[sl]
-                    Kc = self.K[c]
-                    delta = nu @ Kc @ nu
-                    fl = np.einsum('l,qil->qi', Kc @ nu, g, optimize=True)
                     bnu = self.b_at(c, xi) @ nu
                     phi = np.where(bnu >= 0.0, 0.0, bnu * gv)       # Phi(0, g, b_nu)
-                    gamma = self.penalty_boundary(delta, k)
                     F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, phi, v, optimize=True)
-                    F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, gv, fl, optimize=True)
-                    F[c * N:(c + 1) * N] += gamma * np.einsum('q,q,qi->i', w, gv, v, optimize=True)
+                    if self.K_fn is None:
+                        Kc = self.K[c]
+                        delta = nu @ Kc @ nu
+                        fl = np.einsum('l,qil->qi', Kc @ nu, g, optimize=True)
+                        gamma = self.penalty_boundary(delta, k)
+                        F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, gv, fl, optimize=True)
+                        F[c * N:(c + 1) * N] += gamma * np.einsum('q,q,qi->i', w, gv, v, optimize=True)
+                    else:
+                        Kq = self.K_points(c, xi)
+                        fl = np.einsum('ql,qil->qi', Kq @ nu, g, optimize=True)
+                        gamma = self.penalty_boundary(Kq @ nu @ nu, k)
+                        F[c * N:(c + 1) * N] -= np.einsum('q,q,qi->i', w, gv, fl, optimize=True)
+                        F[c * N:(c + 1) * N] += np.einsum('q,q,q,qi->i', w, gamma, gv, v, optimize=True)
         return F
 
     def interpolate(self, fn):

@@ -107,6 +107,63 @@ def convection_pe(n=32, p=3, pe=2000.0, bvec=(1.0, 0.5, 0.3)):
                 K=np.full(n ** 3, kappa), b=bfield, c=None, f=f, g=_zero, j=None, exact=u)
 
 
+# Spatially varying diffusion of the paper's inhomogeneous test (Sec. 4.2):
+# K(x) = sum_k P_k(x_k) n_k n_k^T with an orthonormal basis n_k and
+# P_k(z) = p0_k + p2_k z^2 > 0; c(x) = gamma |x|^2 with gamma = 1e-8.
+VARK_BASIS = None   # filled below: rows n_1, n_2, n_3
+VARK_P0 = (1.0, 2.0, 0.5)
+VARK_P2 = (3.0, 1.0, 4.0)
+VARK_GAMMA = 1e-8
+
+
+def _rotation(a, b, c):
+    ca, sa, cb, sb, cc, sc = np.cos(a), np.sin(a), np.cos(b), np.sin(b), np.cos(c), np.sin(c)
+    rz = np.array([[ca, -sa, 0], [sa, ca, 0], [0, 0, 1.0]])
+    ry = np.array([[cb, 0, sb], [0, 1.0, 0], [-sb, 0, cb]])
+    rx = np.array([[1.0, 0, 0], [0, cc, -sc], [0, sc, cc]])
+    return rz @ ry @ rx
+
+
+VARK_BASIS = _rotation(np.pi / 6, np.pi / 8, np.pi / 5).T     # rows are n_k
+
+
+def vark_tensor(x, basis=None, p0=VARK_P0, p2=VARK_P2):
+    """K(x) at points x (..., 3): (..., 3, 3)."""
+    nb = VARK_BASIS if basis is None else np.asarray(basis)
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros(x.shape[:-1] + (3, 3))
+    for k in range(3):
+        pk = p0[k] + p2[k] * x[..., k] ** 2
+        out += pk[..., None, None] * np.outer(nb[k], nb[k])
+    return out
+
+
+def vark_reaction(x, gamma=VARK_GAMMA):
+    x = np.asarray(x, dtype=np.float64)
+    return gamma * np.sum(x * x, axis=-1)
+
+
+def variable_k(n=16, p=3):
+    """The inhomogeneous test of Sec. 4.2 on the unit cube: K(x), c(x) as
+    above, Neumann on x = 1 with j a Gaussian at (1, 0.5, 0.5), Dirichlet
+    elsewhere with g a Gaussian at (0, 0.5, 0.5) (widths 0.1), f the Gaussian
+    at (0.75, 0.5, 0.3).  K_cell / c_cell: the coefficients at the cell
+    centres (the diagonal of the tensor), which the preconditioner uses."""
+    nc = (n, n, n)
+    h = 1.0 / n
+    ce = (np.arange(n) + 0.5) * h
+    cz, cy, cx = np.meshgrid(ce, ce, ce, indexing="ij")
+    centres = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], -1)
+    Kc = vark_tensor(centres)
+    gauss = lambda x0: (lambda x, y, z: np.exp(-((x - x0[0]) ** 2 + (y - x0[1]) ** 2 + (z - x0[2]) ** 2)  # noqa: E731
+                                               / (2 * 0.1 ** 2)))
+    return dict(name=f"variable_k_{n}^3_p{p}", nc=nc, L=(1.0, 1.0, 1.0), p=p, bc=[0, 1, 0, 0, 0, 0],
+                K=np.stack([Kc[:, 0, 0], Kc[:, 1, 1], Kc[:, 2, 2]], -1), b=None, c=vark_reaction(centres),
+                f=gauss((0.75, 0.5, 0.3)), g=gauss((0.0, 0.5, 0.5)), j=gauss((1.0, 0.5, 0.5)), exact=None,
+                K_fn=vark_tensor, c_fn=vark_reaction,
+                vark=dict(basis=VARK_BASIS, p0=VARK_P0, p2=VARK_P2, gamma=VARK_GAMMA))
+
+
 def reservoir_permeability(nc=(60, 220, 85), seed=SEED):
     """Diagonal K (ncell, 3) of the channelised layered field."""
     nx, ny, nz = nc
