@@ -39,6 +39,10 @@ SM_COUNT = 152
 FP64_FLOP_PER_CLK_SM = 4          # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz)
 SM_MAX_MHZ = 2070.0
 CPU_SAMPLE = dict(n=6, p=4)        # oracle sample: same workload family, 6^3 cells
+# DRAM bytes (read + write) of one k_smooth_pcg<double> launch on this mesh, from
+# the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt
+# (a sweep with defect, 2 warps per block); set to None when that kernel changes.
+SMOOTHER_TRAFFIC_BYTES = 103.30112e6 + 13.126912e6
 
 
 def fp64_peak_tflops():
@@ -205,7 +209,11 @@ def run_dgmg(args, rank, world, local_rank):
         launch_ms = ap_ms / max(nap, 1)
     roofline = {"bound": "alu", "kernel": "k_smooth_pcg<double>" if dominant == "smoother" else "k_apply<double>",
                 "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": SMOOTHER_TRAFFIC_BYTES if dominant == "smoother" else None,
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one sweep with defect on this "
+                                "mesh (profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt); algorithmic bytes "
+                                "4 x 8 B x ndof = 131 MB, part of it served from L2",
                 "flops_per_launch": per_launch, "launch_ms": round(launch_ms, 4),
                 "flops_note": "algorithmic: (32 n^4 + 120 n^3) per cell per apply, one apply per defect and per "
                               "inner iteration",

@@ -277,6 +277,28 @@ dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_so
 dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
                        dgmg_solve_stats* stats);
 
+/* Spatially varying coefficients of the paper's inhomogeneous test (Sec. 4.2):
+ * K(x) = sum_k (p0_k + p2_k x_k^2) n_k n_k^T with an orthonormal basis n_k
+ * and c(x) = gamma (x_1^2 + x_2^2 + x_3^2), b = 0.  The outer operator (the
+ * Krylov solver's applications, its final residual, dgmg_apply in FP64)
+ * evaluates K and c at every quadrature point: the volume term with the full
+ * tensor at the Gauss points, the face terms with K(x) at the face Gauss
+ * points (K is continuous, so both traces see the same K: weights 1/2,
+ * delta = nu^T K nu, gamma_F = alpha p (p+2) delta / h_d point by point) and
+ * the full K grad v . n including its tangential derivatives.  Everything in
+ * the preconditioner uses the coefficients at the cell centres, as the paper
+ * does: this call sets them (the diagonal of K(x_T), c(x_T)) through
+ * dgmg_set_coefficients, so the block smoother, its diagonals, stored blocks,
+ * the coarse spaces and AMG are those of the cell-centre problem.
+ * dgmg_assemble_rhs afterwards uses K(x) in the Dirichlet terms.
+ *   basis: host, 9 values, rows n_1, n_2, n_3 (orthonormal to 1e-12);
+ *   p0, p2: host, 3 values each, p0 > 0, p2 >= 0; gamma >= 0.
+ * The outer operator is FP64 only: dgmg_apply in FP32 or DF64 and solves with
+ * apply_prec = DF64 return DGMG_ERR_ARG.  dgmg_set_coefficients and
+ * dgmg_set_mesh turn the variable operator off again.  Synchronises. */
+dgmg_status dgmg_set_variable_coefficients(dgmg_ctx* ctx, const double* basis, const double* p0, const double* p2,
+                                           double gamma);
+
 /* Explicit inverse of every diagonal block D_T (the (T,T) part of A: volume
  * terms and the own-side face terms), for the partially matrix-free smoother
  * (PMF, Sec. 4.1: the paper stores a factorisation of D_T and solves with it;
@@ -286,15 +308,19 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
  * Built on the device: column j of D_T is the block operator applied to the
  * unit vector e_j (n^3 block applications per cell), then each block is
  * inverted by Gauss-Jordan elimination with partial pivoting in FP64, one
- * thread block per cell with the block in shared memory.  The inverse is kept
- * in the context in FP64 and, when prec is FP32, also rounded to FP32; the
- * smoothers with inner = DGMG_INNER_DIRECT use the copy of their precision
- * (building it on first use when this call was not made).  Storage:
- * ncell n^6 values per precision (p = 2: 5.8 KB per cell in FP64, p = 4:
- * 125 KB).  dgmg_set_coefficients and dgmg_set_mesh drop it.
+ * thread block per cell with the block in shared memory.  For FP64 smoothers
+ * the inverse is kept as double-float pairs (hi, lo: about 48 significant
+ * bits) and the block solve runs in double-float arithmetic (GB300's FP64
+ * pipe would bound a FP64 product); for FP32 smoothers it is rounded to FP32.
+ * The smoothers with inner = DGMG_INNER_DIRECT use the copy of their
+ * precision (built on first use when this call was not made).  Storage per
+ * precision: ncell n^3 ld values of 8 (FP64) or 4 (FP32) bytes, ld = n^3
+ * rounded up to a multiple of 8 (p = 2: 6.9 KB per cell for FP64, p = 4:
+ * 128 KB).  dgmg_set_coefficients and dgmg_set_mesh drop it.
  *   prec: FP64 or FP32 (DF64: DGMG_ERR_ARG);
  *   out: device buffer of ncell n^6 values of prec receiving a copy, or NULL;
- *        block T at out + T n^6, column-major: (D_T^-1)_{ij} at i + j n^3.
+ *        block T at out + T n^6, column-major: (D_T^-1)_{ij} at i + j n^3
+ *        (FP64: hi + lo of the stored pairs).
  * p > 4: DGMG_ERR_ARG (the block no longer fits in shared memory); a singular
  * block: DGMG_ERR_ARG with nothing stored; allocation failure: DGMG_ERR_OOM.
  * Synchronises the stream. */

@@ -153,8 +153,13 @@ struct dgmg_ctx {
   // warps per block of the operator / smoother kernels per precision (0 = 4)
   int wpb_apply[3] = {0, 0, 0}, wpb_smooth[3] = {0, 0, 0};
   // stored inverses of the diagonal blocks (DGMG_INNER_DIRECT), built on demand
-  double* binv64 = nullptr;
-  float* binv32 = nullptr;
+  float2* binv_df = nullptr;    // for FP64 smoothers: double-float pairs
+  float* binv32 = nullptr;      // for FP32 smoothers
+  int binv_ld = 0;              // column stride (n^3 rounded up to a multiple of 8)
+  // K(x), c(x) of the outer operator (dgmg_set_variable_coefficients)
+  bool var_on = false;
+  std::vector<double> hvar;     // 16 values: basis rows, p0, p2, gamma
+  double* dvar = nullptr;
   // Thomas factors of the tridiagonal part of D_T (DGMG_INNER_GMRES_TRIDIAG)
   double* tri64 = nullptr;
   float* tri32 = nullptr;
@@ -228,8 +233,11 @@ void free_mesh(dgmg_ctx* ctx) {
   ctx->p0h = Hier();
   ctx->kry = nullptr;
   ctx->kry_vecs = 0;
-  ctx->binv64 = nullptr;
+  ctx->binv_df = nullptr;
   ctx->binv32 = nullptr;
+  ctx->binv_ld = 0;
+  ctx->var_on = false;
+  ctx->dvar = nullptr;
   ctx->tri64 = nullptr;
   ctx->tri32 = nullptr;
   ctx->has_coef = false;
@@ -262,6 +270,7 @@ MeshParams params(const dgmg_ctx* ctx) {
   m.rec64 = ctx->rec64;
   m.rec32 = ctx->rec32;
   m.bvert32 = ctx->db32;
+  m.var = ctx->var_on ? ctx->dvar : nullptr;
   for (int i = 0; i < 3; ++i) {
     m.wpb_apply[i] = ctx->wpb_apply[i];
     m.wpb_smooth[i] = ctx->wpb_smooth[i];
@@ -292,6 +301,7 @@ HostMesh host_mesh(const dgmg_ctx* ctx) {
   m.b = ctx->hb.empty() ? nullptr : ctx->hb.data();
   m.c = ctx->hc.empty() ? nullptr : ctx->hc.data();
   m.alpha = 1.25;
+  m.var = ctx->var_on ? ctx->hvar.data() : nullptr;
   return m;
 }
 
@@ -332,13 +342,15 @@ dgmg_status multi_dot(dgmg_ctx* ctx, int k, double* const* xs, const double* y, 
 }
 
 // ------------------------------------------------------------------ stored block inverses
-// D_T^-1 of every cell in FP64 (and rounded to FP32 when prec is FP32): block
-// matrices by unit-vector block applications, Gauss-Jordan per block.
+// D_T^-1 of every cell: block matrices by unit-vector block applies and
+// Gauss-Jordan per block in FP64 (a temporary), then kept as double-float
+// pairs for FP64 smoothers or rounded to FP32 for FP32 smoothers, column
+// stride ld = n^3 rounded up to a multiple of 8.
 dgmg_status ensure_binv(dgmg_ctx* ctx, int prec) {
   if (prec != DGMG_FP64 && prec != DGMG_FP32)
     return fail(ctx, DGMG_ERR_ARG, "stored block inverses are FP64 or FP32");
   if (ctx->p > 4) return fail(ctx, DGMG_ERR_ARG, "stored block inverses are built for p <= 4");
-  if (prec == DGMG_FP64 ? ctx->binv64 != nullptr : ctx->binv32 != nullptr) return DGMG_OK;
+  if (prec == DGMG_FP64 ? ctx->binv_df != nullptr : ctx->binv32 != nullptr) return DGMG_OK;
   if (ctx->stream) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(ctx->stream, &cs));
@@ -346,37 +358,50 @@ dgmg_status ensure_binv(dgmg_ctx* ctx, int prec) {
       return fail(ctx, DGMG_ERR_STATE, "build the block inverses (dgmg_block_inverse) before stream capture");
   }
   const int nb = ctx->n * ctx->n * ctx->n;
-  const size_t count = (size_t)ctx->ncell * nb * nb;
-  if (!ctx->binv64) {
-    double* m = nullptr;
-    int* sing = nullptr;
-    CS(dalloc(ctx, &m, count));
-    dgmg_status st = dalloc(ctx, &sing, 1);
-    if (st != DGMG_OK) {
-      dfree(ctx, m);
-      return st;
-    }
-    int h = 0;
-    cudaError_t e = cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = ctx->ops->block_matrix(params(ctx), m, ctx->stream);
-    if (e == cudaSuccess) e = block_invert(m, nb, ctx->ncell, sing, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    dfree(ctx, sing);
-    if (e != cudaSuccess || h) {
-      dfree(ctx, m);
-      if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
-      return fail(ctx, DGMG_ERR_ARG, "a diagonal block is singular");
-    }
-    ctx->binv64 = m;
+  const int ld = (nb + 7) / 8 * 8;
+  const size_t count = (size_t)ctx->ncell * nb * ld;
+  double* m = nullptr;
+  int* sing = nullptr;
+  CS(dalloc(ctx, &m, count));
+  dgmg_status st = dalloc(ctx, &sing, 1);
+  if (st != DGMG_OK) {
+    dfree(ctx, m);
+    return st;
   }
-  if (prec == DGMG_FP32) {
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, count * sizeof(double), ctx->stream);
+  if (e == cudaSuccess) e = ctx->ops->block_matrix(params(ctx), m, ld, ctx->stream);
+  if (e == cudaSuccess) e = block_invert(m, nb, ld, ctx->ncell, sing, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  dfree(ctx, sing);
+  if (e != cudaSuccess || h) {
+    dfree(ctx, m);
+    if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
+    return fail(ctx, DGMG_ERR_ARG, "a diagonal block is singular");
+  }
+  if (prec == DGMG_FP64) {
+    float2* pairs = nullptr;
+    st = dalloc(ctx, &pairs, count);
+    if (st == DGMG_OK) {
+      e = vec_split_df((long long)count, m, pairs, nullptr, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e == cudaSuccess) ctx->binv_df = pairs;
+    }
+  } else {
     float* m32 = nullptr;
-    CS(dalloc(ctx, &m32, count));
-    CK(vec_d2f((long long)count, ctx->binv64, m32, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctx->binv32 = m32;
+    st = dalloc(ctx, &m32, count);
+    if (st == DGMG_OK) {
+      e = vec_d2f((long long)count, m, m32, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e == cudaSuccess) ctx->binv32 = m32;
+    }
   }
+  dfree(ctx, m);
+  if (st != DGMG_OK) return st;
+  if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
+  ctx->binv_ld = ld;
   return DGMG_OK;
 }
 
@@ -432,7 +457,7 @@ dgmg_status inner_data(dgmg_ctx* ctx, int inner, int prec, const void** binv, co
   const bool fp32 = prec == DGMG_FP32;
   if (inner == DGMG_INNER_DIRECT) {
     CS(ensure_binv(ctx, prec));
-    *binv = fp32 ? (const void*)ctx->binv32 : (const void*)ctx->binv64;
+    *binv = fp32 ? (const void*)ctx->binv32 : (const void*)ctx->binv_df;
   } else if (inner == DGMG_INNER_GMRES_TRIDIAG) {
     CS(ensure_tri(ctx, prec));
     *tri = fp32 ? (const void*)ctx->tri32 : (const void*)ctx->tri64;
@@ -480,6 +505,7 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
     a.inner = inner;
     a.restart = restart;
     a.binv = binv;
+    a.binv_ld = ctx->binv_ld;
     a.tri = tri;
     a.its = (its || ctx->track_its) ? ctx->its : nullptr;
     const size_t e0 = ctx->timing ? record_event(ctx) : 0;
@@ -539,6 +565,7 @@ dgmg_status sor_internal(dgmg_ctx* ctx, const void* f, void* u, int nsweep, doub
         a.inner = inner;
         a.restart = restart;
         a.binv = binv;
+        a.binv_ld = ctx->binv_ld;
         a.tri = tri;
         a.its = (its || ctx->track_its) ? ctx->its : nullptr;
         a.color = pass == 0 ? c : 7 - c;
@@ -677,7 +704,7 @@ dgmg_status restrict_internal(dgmg_ctx* ctx, const void* r, double* rhat, bool f
   return DGMG_OK;
 }
 
-dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec);
+dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec, bool outer = false);
 
 // ------------------------------------------------------------------ V-cycle
 // One V-cycle of Algorithm 1 on FP64 f, u (u updated in place; zero: u == 0 on entry).
@@ -732,10 +759,13 @@ dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgm
   return DGMG_OK;
 }
 
-dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec) {
+dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec, bool outer) {
   const MeshParams mp = params(ctx);
   const size_t e0 = ctx->timing ? record_event(ctx) : 0;
-  CK(ctx->ops->apply(mp, u, v, prec, true, ctx->stream));
+  if (outer && ctx->var_on)   // the operator with K(x), c(x); the preconditioner keeps cell values
+    CK(ctx->ops->apply_var(mp, (const double*)u, (double*)v, ctx->stream));
+  else
+    CK(ctx->ops->apply(mp, u, v, prec, true, ctx->stream));
   if (ctx->timing) ctx->ev_apply.push_back({e0, record_event(ctx)});
   ++ctx->n_apply;
   return DGMG_OK;
@@ -820,7 +850,7 @@ dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_
 
 // Outer Krylov operator: FP64 vectors, FP64 or double-float arithmetic.
 dgmg_status apply64(dgmg_ctx* ctx, const double* u, double* v, int prec = DGMG_FP64) {
-  return timed_apply(ctx, u, v, prec == DGMG_DF64 ? DGMG_DF64 : DGMG_FP64);
+  return timed_apply(ctx, u, v, prec == DGMG_DF64 ? DGMG_DF64 : DGMG_FP64, true);
 }
 
 dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, dgmg_solve_stats& st) {
@@ -1215,6 +1245,11 @@ dgmg_status dgmg_apply(dgmg_ctx* ctx, const void* u, void* v, dgmg_prec prec) {
   if (!u || !v || u == v) return fail(ctx, DGMG_ERR_ARG, "u, v must be distinct non-NULL device pointers");
   if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
   CS(check_df64(ctx, prec, DGMG_INNER_PCG));
+  if (ctx->var_on) {
+    if (prec != DGMG_FP64) return fail(ctx, DGMG_ERR_ARG, "the operator with K(x), c(x) is FP64");
+    CK(ctx->ops->apply_var(params(ctx), (const double*)u, (double*)v, ctx->stream));
+    return DGMG_OK;
+  }
   CK(ctx->ops->apply(params(ctx), u, v, prec, true, ctx->stream));
   return DGMG_OK;
 }
@@ -1341,6 +1376,7 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   if (o.smoother_prec < DGMG_FP64 || o.smoother_prec > DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad smoother_prec");
   CS(check_df64(ctx, o.smoother_prec, o.inner));
   CS(check_df64(ctx, o.apply_prec, DGMG_INNER_PCG));
+  if (ctx->var_on && o.apply_prec == DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "the operator with K(x), c(x) is FP64");
   if (o.coarse < DGMG_COARSE_AMG || o.coarse > DGMG_COARSE_P0) return fail(ctx, DGMG_ERR_ARG, "bad coarse");
   if (o.stop != DGMG_STOP_RESIDUAL && o.stop != DGMG_STOP_ENERGY) return fail(ctx, DGMG_ERR_ARG, "bad stop");
   if (o.stop == DGMG_STOP_ENERGY && (o.krylov == DGMG_KRYLOV_FGMRES || o.delay < 1))
@@ -1395,14 +1431,58 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   return s;
 }
 
+dgmg_status dgmg_set_variable_coefficients(dgmg_ctx* ctx, const double* basis, const double* p0, const double* p2,
+                                           double gamma) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (!ctx->has_mesh) return fail(ctx, DGMG_ERR_STATE, "set_mesh first");
+  if (!basis || !p0 || !p2) return fail(ctx, DGMG_ERR_ARG, "NULL pointer");
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < 3; ++k) d += basis[3 * i + k] * basis[3 * j + k];
+      if (!(std::fabs(d - (i == j ? 1.0 : 0.0)) <= 1e-12)) return fail(ctx, DGMG_ERR_ARG, "basis rows must be orthonormal");
+    }
+  for (int k = 0; k < 3; ++k)
+    if (!(p0[k] > 0.0) || !(p2[k] >= 0.0) || !std::isfinite(p0[k]) || !std::isfinite(p2[k]))
+      return fail(ctx, DGMG_ERR_ARG, "p0 > 0 and p2 >= 0 required");
+  if (!(gamma >= 0.0) || !std::isfinite(gamma)) return fail(ctx, DGMG_ERR_ARG, "gamma >= 0 required");
+  std::vector<double> vp(16);
+  for (int i = 0; i < 9; ++i) vp[i] = basis[i];
+  for (int k = 0; k < 3; ++k) {
+    vp[9 + k] = p0[k];
+    vp[12 + k] = p2[k];
+  }
+  vp[15] = gamma;
+  // the preconditioner's coefficients: K and c at the cell centres (the
+  // diagonal of the tensor), as the paper evaluates them (Sec. 4.2)
+  std::vector<double> Kc(3 * ctx->ncell), cc(ctx->ncell);
+  for (long long c = 0; c < ctx->ncell; ++c) {
+    const long long cx = c % ctx->nx, cy = (c / ctx->nx) % ctx->ny, cz = c / ((long long)ctx->nx * ctx->ny);
+    const double x[3] = {(cx + 0.5) * ctx->h[0], (cy + 0.5) * ctx->h[1], (cz + 0.5) * ctx->h[2]};
+    double K[6];
+    var_tensor(vp.data(), x, K);
+    for (int d = 0; d < 3; ++d) Kc[3 * c + d] = K[d];
+    cc[c] = gamma * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  }
+  CS(dgmg_set_coefficients(ctx, Kc.data(), 3, nullptr, gamma > 0.0 ? cc.data() : nullptr));
+  CS(dalloc(ctx, &ctx->dvar, 16));
+  CK(cudaMemcpyAsync(ctx->dvar, vp.data(), 16 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->hvar = vp;
+  ctx->var_on = true;
+  return DGMG_OK;
+}
+
 dgmg_status dgmg_block_inverse(dgmg_ctx* ctx, dgmg_prec prec, void* out) {
   CS(ready(ctx));
   CS(ensure_binv(ctx, prec));
   if (out) {
-    const size_t nb = (size_t)ctx->n * ctx->n * ctx->n;
-    const size_t bytes = (size_t)ctx->ncell * nb * nb * (prec == DGMG_FP32 ? 4 : 8);
-    const void* src = prec == DGMG_FP32 ? (const void*)ctx->binv32 : (const void*)ctx->binv64;
-    CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    const int nb = ctx->n * ctx->n * ctx->n;
+    if (prec == DGMG_FP32)
+      CK(cudaMemcpy2DAsync(out, nb * sizeof(float), ctx->binv32, ctx->binv_ld * sizeof(float), nb * sizeof(float),
+                           (size_t)ctx->ncell * nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      CK(blocks_df_to_dense(ctx->ncell, nb, ctx->binv_ld, ctx->binv_df, (double*)out, ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return DGMG_OK;

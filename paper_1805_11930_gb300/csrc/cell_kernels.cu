@@ -895,9 +895,10 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
 
 // D_T of each cell column by column: column j is the block operator (volume
 // terms and own-side face terms) applied to the unit vector e_j.  FP64;
-// output column-major, n^3 x n^3 per cell.  Set-up of the stored inverses.
+// output column-major with column stride ld >= n^3 (block stride n^3 ld).
+// Set-up of the stored inverses.
 template <bool ADV>
-__global__ void __launch_bounds__(256) k_block_matrix(MeshParams mp, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_block_matrix(MeshParams mp, double* __restrict__ out, int ld) {
   using T = double;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -922,7 +923,7 @@ __global__ void __launch_bounds__(256) k_block_matrix(MeshParams mp, double* __r
     __syncwarp();
     for (int e = lane; e < VEC; e += 32) {
       const int cw = e / N3;
-      if (act[cw]) out[cid[cw] * (long long)(N3 * N3) + (long long)j * N3 + (e - cw * N3)] = Q[e];
+      if (act[cw]) out[cid[cw] * (long long)(N3 * ld) + (long long)j * ld + (e - cw * N3)] = Q[e];
     }
     __syncwarp();
   }
@@ -931,12 +932,21 @@ __global__ void __launch_bounds__(256) k_block_matrix(MeshParams mp, double* __r
 // Block-Jacobi (color < 0) or one colour of block-SOR with exact block solves
 // by the stored inverses (the partially matrix-free smoother): per cell
 // d = f - A u_old (skipped from u = 0), delta = D_T^-1 d as a dense
-// matrix-vector product whose columns are read coalesced from HBM,
-// u_new = u_old + omega delta.
-template <typename T, bool ADV, typename G = typename Store<T>::type>
+// matrix-vector product whose columns (stride ld, a multiple of 8 values, so
+// that a warp's reads of one column start on 32-byte sectors) are read
+// coalesced from HBM, u_new = u_old + omega delta.  FP64 smoothers keep the
+// inverse as double-float pairs (hi, lo) and form the product in double-float
+// arithmetic: a FP64 product would make this kernel FP64-pipe bound
+// (2 flop per 8-byte entry is above GB300's FP64 ridge of 0.18 flop/B);
+// pairs keep ~48 significant bits at FP32 issue rates.  FP32 smoothers keep
+// FP32 entries and FP32 arithmetic.
+template <typename T> struct InvEntry { using type = T; };
+template <> struct InvEntry<double> { using type = float2; };
+
+template <typename T, bool ADV, typename G = typename Store<T>::type, typename M = typename InvEntry<T>::type>
 __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __restrict__ f, const G* uold, G* unew,
-                                                    const T* __restrict__ binv, T omega, int* __restrict__ its,
-                                                    int color) {
+                                                    const M* __restrict__ binv, int ld, T omega,
+                                                    int* __restrict__ its, int color) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
@@ -963,21 +973,36 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
     all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
     __syncwarp();
   }
-  // the defect goes to P (no longer needed)
+  // the defect goes to P (no longer needed); FP64: also as double-float pairs in S0
+  df* D2 = reinterpret_cast<df*>(S0);
   for (int e = lane; e < VEC; e += 32) {
     const int cw = e / N3;
-    P[e] = act[cw] ? T(f[cid[cw] * N3 + (e - cw * N3)]) - (zero ? T(0) : Q[e]) : T(0);
+    const T dv = act[cw] ? T(f[cid[cw] * N3 + (e - cw * N3)]) - (zero ? T(0) : Q[e]) : T(0);
+    P[e] = dv;
+    if constexpr (std::is_same<T, double>::value) D2[e] = df(dv);
   }
   __syncwarp();
   for (int e = lane; e < VEC; e += 32) {
     const int cw = e / N3;
     if (!act[cw]) continue;
     const int i = e - cw * N3;
-    const T* col = binv + cid[cw] * (long long)(N3 * N3) + i;
-    const T* d = P + cw * N3;
-    T acc = T(0);
+    const M* col = binv + cid[cw] * (long long)N3 * ld + i;
+    T acc;
+    if constexpr (std::is_same<T, double>::value) {
+      const df* d = D2 + cw * N3;
+      df_acc a;
 #pragma unroll 8
-    for (int j = 0; j < N3; ++j) acc = fma(__ldg(col + (long long)j * N3), d[j], acc);
+      for (int j = 0; j < N3; ++j) {
+        const float2 m = __ldg(col + (long long)j * ld);
+        a.add_prod(df(m.x, m.y), d[j]);
+      }
+      acc = double(a.value());
+    } else {
+      const T* d = P + cw * N3;
+      acc = T(0);
+#pragma unroll 8
+      for (int j = 0; j < N3; ++j) acc = fma(__ldg(col + (long long)j * ld), d[j], acc);
+    }
     const long long g = cid[cw] * N3 + i;
     unew[g] = static_cast<G>(zero ? omega * acc : fma(omega, acc, T(uold[g])));
   }
@@ -1065,6 +1090,269 @@ __device__ __forceinline__ void thomas_apply(const T* __restrict__ tri, const lo
     for (int i = N3 - 2; i >= 0; --i) x[i] = fma(-fc[i], x[i + 1], x[i]);
   }
   __syncwarp();
+}
+
+// ----------------------------------------------------------------- variable coefficients
+// K(x) = sum_k (p0_k + p2_k x_k^2) n_k n_k^T and c(x) = gamma |x|^2 at a
+// physical point (the paper's inhomogeneous test, Sec. 4.2); vp holds the
+// rows n_k (9 values), p0 (3), p2 (3), gamma.  K as (xx, yy, zz, xy, xz, yz).
+__device__ __forceinline__ void var_coef(const double* __restrict__ vp, const double x[3], double K[6], double& c) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) K[i] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double pk = fma(vp[12 + k] * x[k], x[k], vp[9 + k]);
+    const double a = vp[3 * k], b = vp[3 * k + 1], e = vp[3 * k + 2];
+    K[0] = fma(pk * a, a, K[0]);
+    K[1] = fma(pk * b, b, K[1]);
+    K[2] = fma(pk * e, e, K[2]);
+    K[3] = fma(pk * a, b, K[3]);
+    K[4] = fma(pk * a, e, K[4]);
+    K[5] = fma(pk * b, e, K[5]);
+  }
+  c = vp[15] * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+}
+
+__device__ __forceinline__ double kent(const double K[6], int i, int j) {
+  if (i == j) return K[i];
+  const int s = i + j;   // (0,1) -> 3, (0,2) -> 4, (1,2) -> 5
+  return K[s == 1 ? 3 : (s == 2 ? 4 : 5)];
+}
+
+// Index of dof (normal index id, tangential ia, ib) for faces normal to axis D.
+template <int D>
+__device__ __forceinline__ int fidx(int id, int ia, int ib) {
+  if (D == 0) return id + N * ia + N2 * ib;
+  if (D == 1) return ia + N * id + N2 * ib;
+  return ia + N * ib + N2 * id;
+}
+
+// Own-row terms of the faces normal to axis D on side s (SIPG with K(x) at the
+// face Gauss points; a continuous K gives both traces the same value, so the
+// weights are 1/2 and <delta^-, delta^+> = delta = nu^T K nu):
+//   -int {K grad u}.n v - int w (K grad v . n) [[u]] + int gamma [[u]] v,
+// with n the outward normal of the cell, [[u]] = u_T - u_nb (u_nb = 0 and
+// w = 1 on Dirichlet faces, nothing on Neumann faces).  Traces and normal
+// derivatives come from the nodal values (GLL end points), tangential
+// derivatives from the Gauss-point derivative table G.  FS: scratch of at
+// least 18 CPW n^2 values.  Accumulates into Y.
+template <int D>
+__device__ void faces_var(const MeshParams& mp, const double* __restrict__ u, const double* X, double* Y,
+                          double* FS, int s, int lane, const CellInfo<double>* ci, const unsigned char* act,
+                          const long long* cid) {
+  const Tab<double>& t = c_tab_d;
+  constexpr int A = D == 0 ? 1 : 0, Bx = D == 2 ? 1 : 2;
+  const int f = 2 * D + s;
+  const int end = s ? N - 1 : 0, endn = s ? 0 : N - 1;
+  const double ihd = mp.ih[D], iha = mp.ih[A], ihb = mp.ih[Bx];
+  auto arr = [&](int k, int cw) { return FS + (k * CPW + cw) * N2; };
+  // 1: traces and normal derivatives, own (0, 1) and neighbour (2, 3)
+  for (int it = lane; it < CPW * N2; it += 32) {
+    const int cw = it / N2, r = it - cw * N2, ia = r % N, ib = r / N;
+    if (!act[cw] || ci[cw].kind[f] == 2) continue;
+    const double* xc = X + cw * N3;
+    double nd = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) nd = fma(t.dl[s][k], xc[fidx<D>(k, ia, ib)], nd);
+    arr(0, cw)[r] = xc[fidx<D>(end, ia, ib)];
+    arr(1, cw)[r] = nd * ihd;
+    double tn = 0.0, ndn = 0.0;
+    if (ci[cw].kind[f] == 0) {
+      const double* un = u + ci[cw].nb[f] * N3;
+      tn = __ldg(un + fidx<D>(endn, ia, ib));
+#pragma unroll
+      for (int k = 0; k < N; ++k) ndn = fma(t.dl[1 - s][k], __ldg(un + fidx<D>(k, ia, ib)), ndn);
+    }
+    arr(2, cw)[r] = tn;
+    arr(3, cw)[r] = ndn * ihd;
+  }
+  __syncwarp();
+  // 2a: along a: B trace, G trace, B normal derivative (own 4..6, neighbour 7..9); index qa + N ib
+  for (int it = lane; it < CPW * N2; it += 32) {
+    const int cw = it / N2, r = it - cw * N2, qa = r % N, ib = r / N;
+    if (!act[cw] || ci[cw].kind[f] == 2) continue;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int ia = 0; ia < N; ++ia) {
+      const double bq = t.B[qa][ia], gq = t.G[qa][ia];
+      const int k = ia + N * ib;
+      v[0] = fma(bq, arr(0, cw)[k], v[0]);
+      v[1] = fma(gq, arr(0, cw)[k], v[1]);
+      v[2] = fma(bq, arr(1, cw)[k], v[2]);
+      v[3] = fma(bq, arr(2, cw)[k], v[3]);
+      v[4] = fma(gq, arr(2, cw)[k], v[4]);
+      v[5] = fma(bq, arr(3, cw)[k], v[5]);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) arr(4 + j, cw)[r] = v[j];
+  }
+  __syncwarp();
+  // 2b: at the face Gauss points (qa, qb): the flux terms, weighted (10..13)
+  for (int it = lane; it < CPW * N2; it += 32) {
+    const int cw = it / N2, r = it - cw * N2, qa = r % N, qb = r / N;
+    if (!act[cw] || ci[cw].kind[f] == 2) continue;
+    double uT = 0, aT = 0, bT = 0, dT = 0, uN = 0, aN = 0, bN = 0, dN = 0;
+#pragma unroll
+    for (int ib = 0; ib < N; ++ib) {
+      const double bq = t.B[qb][ib], gq = t.G[qb][ib];
+      const int k = qa + N * ib;
+      uT = fma(bq, arr(4, cw)[k], uT);
+      aT = fma(bq, arr(5, cw)[k], aT);
+      bT = fma(gq, arr(4, cw)[k], bT);
+      dT = fma(bq, arr(6, cw)[k], dT);
+      uN = fma(bq, arr(7, cw)[k], uN);
+      aN = fma(bq, arr(8, cw)[k], aN);
+      bN = fma(gq, arr(7, cw)[k], bN);
+      dN = fma(bq, arr(9, cw)[k], dN);
+    }
+    int cx, cy, cz;
+    cell_xyz(mp, cid[cw], cx, cy, cz);
+    const int cc[3] = {cx, cy, cz};
+    double x[3];
+    x[D] = (cc[D] + s) * mp.h[D];
+    x[A] = (cc[A] + t.gq[qa]) * mp.h[A];
+    x[Bx] = (cc[Bx] + t.gq[qb]) * mp.h[Bx];
+    double K[6], cdum;
+    var_coef(mp.var, x, K, cdum);
+    const double sg = s ? 1.0 : -1.0;
+    const double knd = sg * kent(K, D, D), kna = sg * kent(K, A, D), knb = sg * kent(K, Bx, D);
+    const double fT = knd * dT + kna * aT * iha + knb * bT * ihb;
+    const double fN = knd * dN + kna * aN * iha + knb * bN * ihb;
+    const double gam = mp.alpha * mp.p * (mp.p + 2) * kent(K, D, D) * ihd;
+    const double wf = t.w[qa] * t.w[qb] * mp.area[D];
+    double av, bv;
+    if (ci[cw].kind[f] == 0) {
+      av = -0.5 * (fT + fN) + gam * (uT - uN);
+      bv = -0.5 * (uT - uN);
+    } else {
+      av = -fT + gam * uT;
+      bv = -uT;
+    }
+    arr(10, cw)[r] = wf * av;
+    arr(11, cw)[r] = wf * bv * kna;
+    arr(12, cw)[r] = wf * bv * knb;
+    arr(13, cw)[r] = wf * bv * knd;
+  }
+  __syncwarp();
+  // 3a: transposed along b (14..17); index qa + N ib
+  for (int it = lane; it < CPW * N2; it += 32) {
+    const int cw = it / N2, r = it - cw * N2, qa = r % N, ib = r / N;
+    if (!act[cw] || ci[cw].kind[f] == 2) continue;
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+#pragma unroll
+    for (int qb = 0; qb < N; ++qb) {
+      const double bq = t.B[qb][ib], gq = t.G[qb][ib];
+      const int k = qa + N * qb;
+      v0 = fma(bq, arr(10, cw)[k], v0);
+      v1 = fma(bq, arr(11, cw)[k], v1);
+      v2 = fma(gq, arr(12, cw)[k], v2);
+      v3 = fma(bq, arr(13, cw)[k], v3);
+    }
+    arr(14, cw)[r] = v0;
+    arr(15, cw)[r] = v1;
+    arr(16, cw)[r] = v2;
+    arr(17, cw)[r] = v3;
+  }
+  __syncwarp();
+  // 3b: transposed along a, into the face layer (values, tangential
+  // derivatives) and along all layers (normal derivative)
+  for (int it = lane; it < CPW * N2; it += 32) {
+    const int cw = it / N2, r = it - cw * N2, ia = r % N, ib = r / N;
+    if (!act[cw] || ci[cw].kind[f] == 2) continue;
+    double lv = 0, nv = 0;
+#pragma unroll
+    for (int qa = 0; qa < N; ++qa) {
+      const double bq = t.B[qa][ia], gq = t.G[qa][ia];
+      const int k = qa + N * ib;
+      lv = fma(bq, arr(14, cw)[k], lv);
+      lv = fma(gq * iha, arr(15, cw)[k], lv);
+      lv = fma(bq * ihb, arr(16, cw)[k], lv);
+      nv = fma(bq, arr(17, cw)[k], nv);
+    }
+    nv *= ihd;
+    double* yc = Y + cw * N3;
+    yc[fidx<D>(end, ia, ib)] += lv;
+#pragma unroll
+    for (int k = 0; k < N; ++k) yc[fidx<D>(k, ia, ib)] = fma(t.dl[s][k], nv, yc[fidx<D>(k, ia, ib)]);
+  }
+  __syncwarp();
+}
+
+// v = A u for K(x), c(x) varying inside the cells (b = 0), FP64: volume
+// terms at the Gauss points (u, grad u by B and the Gauss derivative Dg;
+// pointwise flux |J| w K(x) grad u and |J| w c(x) u; transposed derivatives
+// and B^T), then the six faces as in faces_var.
+__global__ void __launch_bounds__(256) k_apply_var(MeshParams mp, const double* __restrict__ u, double* __restrict__ v) {
+  using T = double;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+  if (s0 >= mp.ncell) return;
+  T* vec[11];
+  T *F0, *F1, *red;
+  CellInfo<T>* ci;
+  unsigned char* act;
+  long long* cid;
+  carve(smem + warp * WarpMem<T>::bytes(11), 11, vec, &F0, &F1, &red, &ci, &act, &cid);
+  T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3], *G0 = vec[4], *G1 = vec[5], *G2 = vec[6];
+  const Tab<double>& t = c_tab_d;
+  slot_cells(mp, -1, s0, lane, cid);
+  stage_cells(mp, 0, lane, ci, act, cid);
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    X[e] = act[cw] ? u[cid[cw] * N3 + (e - cw * N3)] : 0.0;
+  }
+  __syncwarp();
+  contract<0, false, false>(X, S0, t.B, lane, act);
+  __syncwarp();
+  contract<1, false, false>(S0, S1, t.B, lane, act);
+  __syncwarp();
+  contract<2, false, false>(S1, S0, t.B, lane, act);   // S0 = u at the Gauss points
+  __syncwarp();
+  contract<0, false, false>(S0, G0, t.Dg, lane, act);
+  contract<1, false, false>(S0, G1, t.Dg, lane, act);
+  contract<2, false, false>(S0, G2, t.Dg, lane, act);
+  __syncwarp();
+  const double J = mp.h[0] * mp.h[1] * mp.h[2];
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    if (!act[cw]) continue;
+    const int q = e - cw * N3, qx = q % N, qy = (q / N) % N, qz = q / N2;
+    int cx, cy, cz;
+    cell_xyz(mp, cid[cw], cx, cy, cz);
+    const double x[3] = {(cx + t.gq[qx]) * mp.h[0], (cy + t.gq[qy]) * mp.h[1], (cz + t.gq[qz]) * mp.h[2]};
+    double K[6], c;
+    var_coef(mp.var, x, K, c);
+    const double wq = J * t.w[qx] * t.w[qy] * t.w[qz];
+    const double g0 = G0[e] * mp.ih[0], g1 = G1[e] * mp.ih[1], g2 = G2[e] * mp.ih[2];
+    G0[e] = wq * (K[0] * g0 + K[3] * g1 + K[4] * g2) * mp.ih[0];
+    G1[e] = wq * (K[3] * g0 + K[1] * g1 + K[5] * g2) * mp.ih[1];
+    G2[e] = wq * (K[4] * g0 + K[5] * g1 + K[2] * g2) * mp.ih[2];
+    S0[e] = wq * c * S0[e];
+  }
+  __syncwarp();
+  contract<0, true, true>(G0, S0, t.Dg, lane, act);
+  __syncwarp();
+  contract<1, true, true>(G1, S0, t.Dg, lane, act);
+  __syncwarp();
+  contract<2, true, true>(G2, S0, t.Dg, lane, act);
+  __syncwarp();
+  contract<2, true, false>(S0, S1, t.B, lane, act);
+  __syncwarp();
+  contract<1, true, false>(S1, S0, t.B, lane, act);
+  __syncwarp();
+  contract<0, true, false>(S0, Y, t.B, lane, act);
+  __syncwarp();
+  // faces (scratch: the 9 vectors after Y, contiguous)
+  for (int sd = 0; sd < 2; ++sd) {
+    faces_var<0>(mp, u, X, Y, S0, sd, lane, ci, act, cid);
+    faces_var<1>(mp, u, X, Y, S0, sd, lane, ci, act, cid);
+    faces_var<2>(mp, u, X, Y, S0, sd, lane, ci, act, cid);
+  }
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    if (act[cw]) v[cid[cw] * N3 + (e - cw * N3)] = Y[e];
+  }
 }
 
 // Per-cell scalars of the inner GMRES(m): Hessenberg (m+1) x m, g, Givens
@@ -1655,20 +1943,21 @@ cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
   const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
-  k<<<grid_for(cells, wpb), wpb * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const T*)a.binv,
-                                          T(a.omega), a.its, a.color);
+  using M = typename InvEntry<T>::type;
+  k<<<grid_for(cells, wpb), wpb * 32, sm, s>>>(mp, (const G*)a.f, (const G*)a.uold, (G*)a.unew, (const M*)a.binv,
+                                          a.binv_ld, T(a.omega), a.its, a.color);
   count_launch();
   return cudaGetLastError();
 }
 
 template <bool ADV>
-cudaError_t launch_block_matrix(const MeshParams& mp, double* out, cudaStream_t s) {
+cudaError_t launch_block_matrix(const MeshParams& mp, double* out, int ld, cudaStream_t s) {
   const int wpb = pick_wpb(0, WarpMem<double>::bytes(4));
   const size_t sm = wpb * WarpMem<double>::bytes(4);
   auto k = k_block_matrix<ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
-  k<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, out);
+  k<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, out, ld);
   count_launch();
   return cudaGetLastError();
 }
@@ -1685,15 +1974,28 @@ cudaError_t launch_block_tridiag(const MeshParams& mp, double* out, int* singula
   return cudaGetLastError();
 }
 
+cudaError_t apply_var(const MeshParams& mp, const double* u, double* v, cudaStream_t s) {
+  if (mp.ncell == 0) return cudaSuccess;
+  if (!mp.var || mp.bvert) return cudaErrorInvalidValue;
+  const int wpb = pick_wpb(mp.wpb_apply[DGMG_FP64], WarpMem<double>::bytes(11));
+  const size_t sm = wpb * WarpMem<double>::bytes(11);
+  cudaError_t e = set_smem(k_apply_var, sm);
+  if (e != cudaSuccess) return e;
+  k_apply_var<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, u, v);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t block_tridiag(const MeshParams& mp, double* out, int* singular, cudaStream_t s) {
   if (mp.ncell == 0) return cudaSuccess;
   return mp.bvert ? launch_block_tridiag<true>(mp, out, singular, s)
                   : launch_block_tridiag<false>(mp, out, singular, s);
 }
 
-cudaError_t block_matrix(const MeshParams& mp, double* out, cudaStream_t s) {
+cudaError_t block_matrix(const MeshParams& mp, double* out, int ld, cudaStream_t s) {
   if (mp.ncell == 0) return cudaSuccess;
-  return mp.bvert ? launch_block_matrix<true>(mp, out, s) : launch_block_matrix<false>(mp, out, s);
+  if (ld < N3) return cudaErrorInvalidValue;
+  return mp.bvert ? launch_block_matrix<true>(mp, out, ld, s) : launch_block_matrix<false>(mp, out, ld, s);
 }
 
 template <typename T, bool ADV>
@@ -1785,7 +2087,7 @@ cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool 
 
 const CellOps* DGMG_CAT(cell_ops_n, DGMG_N)() {
   static const CellOps ops = {N, &upload_tables, &apply, &smooth, &diag, &restrict_cells, &prolong_add,
-                              &block_matrix, &block_tridiag};
+                              &block_matrix, &block_tridiag, &apply_var};
   return &ops;
 }
 

@@ -36,6 +36,9 @@ struct MeshParams {
   // Mesh scalars in both precisions: 1/h_d, face area normal to d, |J|/h_d.
   double ih[3], area[3], jh[3];
   float ihf[3], areaf[3], jhf[3];
+  // Spatially varying K(x), c(x) for the outer operator (device, 16 values:
+  // basis rows n_k, p0, p2, gamma), or nullptr.
+  const double* var;
   // Warps per block of the operator and smoother (inner PCG) kernels per
   // precision (index DGMG_FP64 / FP32 / DF64; 0 = the default of 4).
   int wpb_apply[3], wpb_smooth[3];
@@ -72,7 +75,9 @@ struct SmoothArgs {
   int maxit;
   int inner;              // DGMG_INNER_PCG / GMRES / DIRECT
   int restart;
-  const void* binv = nullptr;  // DIRECT: ncell column-major n^3 x n^3 inverses, same precision
+  const void* binv = nullptr;  // DIRECT: ncell column-major n^3 x n^3 inverses (FP64 smoother:
+                               // float2 double-float pairs; FP32: float), column stride binv_ld
+  int binv_ld = 0;
   const void* tri = nullptr;   // GMRES_TRIDIAG: per cell Thomas factors [a | c' | 1/den], same precision
   int* its;               // device int[ncell] or nullptr
   int color = -1;         // -1: all cells (Jacobi); 0..7: one parity class, in place allowed
@@ -93,10 +98,13 @@ struct CellOps {
                                 cudaStream_t s);
   cudaError_t (*prolong_add)(const MeshParams& mp, const double* uhat, void* u, bool fp32,
                              cudaStream_t s);
-  // D_T of every cell, FP64, column-major n^3 x n^3 per cell (column j = D_T e_j)
-  cudaError_t (*block_matrix)(const MeshParams& mp, double* out, cudaStream_t s);
+  // D_T of every cell, FP64, column-major n^3 x n^3 per cell (column j = D_T e_j),
+  // column stride ld >= n^3, block stride n^3 ld
+  cudaError_t (*block_matrix)(const MeshParams& mp, double* out, int ld, cudaStream_t s);
   // Thomas factors of the tridiagonal part of every D_T, FP64, 3 n^3 per cell
   cudaError_t (*block_tridiag)(const MeshParams& mp, double* out, int* singular, cudaStream_t s);
+  // v = A u with K(x), c(x) varying inside the cells (mp.var), FP64, b = 0
+  cudaError_t (*apply_var)(const MeshParams& mp, const double* u, double* v, cudaStream_t s);
 };
 
 const CellOps* cell_ops(int n);
@@ -111,10 +119,16 @@ cudaError_t vec_fill(long long n, double v, double* y, cudaStream_t s);
 cudaError_t vec_fill_f(long long n, float v, float* y, cudaStream_t s);
 cudaError_t vec_d2f(long long n, const double* x, float* y, cudaStream_t s);
 cudaError_t vec_inverse(long long n, const double* d, double* i64, float* i32, cudaStream_t s);
-// In-place inverse of ncell dense nb x nb FP64 blocks (column-major, one after
-// another) by Gauss-Jordan elimination with partial pivoting; nb <= 125.
-// singular: device int, set to 1 when a block has a zero pivot (else untouched).
-cudaError_t block_invert(double* a, int nb, long long ncell, int* singular, cudaStream_t s);
+// In-place inverse of ncell dense nb x nb FP64 blocks (column-major, column
+// stride ld >= nb, block stride nb ld) by Gauss-Jordan elimination with partial
+// pivoting; nb <= 125.  singular: device int, set to 1 when a block has a zero
+// pivot (else untouched).
+cudaError_t block_invert(double* a, int nb, int ld, long long ncell, int* singular, cudaStream_t s);
+// Split FP64 values into double-float pairs (hi = fl(v), lo = fl(v - hi)) and,
+// if f32 is not null, also write hi alone; and the reverse (hi + lo into a
+// dense array, dropping the padding of a column stride ld > nb).
+cudaError_t vec_split_df(long long n, const double* x, float2* pairs, float* f32, cudaStream_t s);
+cudaError_t blocks_df_to_dense(long long ncell, int nb, int ld, const float2* pairs, double* out, cudaStream_t s);
 // P0 transfer: out[c] = sum_i r[c n3 + i]; u[c n3 + i] += uhat[c].
 cudaError_t cell_sums(long long ncell, int n3, const void* r, double* out, bool fp32, cudaStream_t s);
 cudaError_t cell_add(long long ncell, int n3, const double* uhat, void* u, bool fp32, cudaStream_t s);

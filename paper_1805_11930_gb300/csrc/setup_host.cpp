@@ -445,6 +445,28 @@ bool dense_inverse(int n, std::vector<double>& A) {
   return true;
 }
 
+void var_tensor(const double* vp, const double x[3], double K[6]) {
+  for (int i = 0; i < 6; ++i) K[i] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double pk = vp[9 + k] + vp[12 + k] * x[k] * x[k];
+    const double a = vp[3 * k], b = vp[3 * k + 1], e = vp[3 * k + 2];
+    K[0] += pk * a * a;
+    K[1] += pk * b * b;
+    K[2] += pk * e * e;
+    K[3] += pk * a * b;
+    K[4] += pk * a * e;
+    K[5] += pk * b * e;
+  }
+}
+
+namespace {
+inline double kent_host(const double K[6], int i, int j) {
+  if (i == j) return K[i];
+  const int s = i + j;
+  return K[s == 1 ? 3 : (s == 2 ? 4 : 5)];
+}
+}  // namespace
+
 void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp, const double* j_qp, double* rhs) {
   const int n = m.p + 1, n2 = n * n, n3 = n2 * n;
   const std::vector<double> T = build_tables(n);
@@ -485,6 +507,8 @@ void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp
   const int nn3[3] = {m.nx, m.ny, m.nz};
   long long off = 0;
   std::vector<double> val(n2), der(n2), tv(n2), td(n2);
+  std::vector<double> dera(n2), derb(n2), ta_(n2), tb_(n2);   // tangential parts (K(x) only)
+  const double* G = B + 3 * n * n + 3 * n;   // layout: B, Dg, W, dl[2], M1, G, ...
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) {
       const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
@@ -509,6 +533,7 @@ void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp
             for (int qa = 0; qa < n; ++qa) {
               const int f = qa + n * qb;
               const double w = W[qa] * W[qb] * area;
+              dera[f] = derb[f] = 0.0;
               if (!dir) {
                 val[f] = -w * jv[f];
                 der[f] = 0.0;
@@ -521,9 +546,46 @@ void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp
               double bq[3];
               b_at(m, idx[0], idx[1], idx[2], xi, bq);
               const double bn = sgn * bq[d];
+              if (m.var) {
+                // K(x) at the face point: gamma from nu^T K nu, and the test
+                // function's full K grad v . n (normal and tangential parts)
+                double x[3], K[6];
+                for (int e = 0; e < 3; ++e) x[e] = (idx[e] + xi[e]) * m.h[e];
+                var_tensor(m.var, x, K);
+                const double gx = pen * K[d] / m.h[d];
+                val[f] = w * (gx * gv[f] - (bn < 0.0 ? bn * gv[f] : 0.0));
+                der[f] = -w * gv[f] * sgn * kent_host(K, d, d) / m.h[d];
+                dera[f] = -w * gv[f] * sgn * kent_host(K, ta, d) / m.h[ta];
+                derb[f] = -w * gv[f] * sgn * kent_host(K, tb, d) / m.h[tb];
+                continue;
+              }
               val[f] = w * (gam * gv[f] - (bn < 0.0 ? bn * gv[f] : 0.0));
               der[f] = -w * Kd * gv[f] * sgn / m.h[d];
             }
+          if (m.var && dir) {
+            // tangential parts: (G_a^T (x) B_b^T) dera + (B_a^T (x) G_b^T) derb into the face layer
+            for (int qb = 0; qb < n; ++qb)
+              for (int ia = 0; ia < n; ++ia) {
+                double sa = 0.0, sb = 0.0;
+                for (int qa = 0; qa < n; ++qa) {
+                  sa += G[qa * n + ia] * dera[qa + n * qb];
+                  sb += B[qa * n + ia] * derb[qa + n * qb];
+                }
+                ta_[ia + n * qb] = sa;
+                tb_[ia + n * qb] = sb;
+              }
+            for (int ib = 0; ib < n; ++ib)
+              for (int ia = 0; ia < n; ++ia) {
+                double sv = 0.0;
+                for (int qb = 0; qb < n; ++qb)
+                  sv += B[qb * n + ib] * ta_[ia + n * qb] + G[qb * n + ib] * tb_[ia + n * qb];
+                int ii[3];
+                ii[ta] = ia;
+                ii[tb] = ib;
+                ii[d] = s ? n - 1 : 0;
+                rhs[c * n3 + ii[0] + n * ii[1] + n2 * ii[2]] += sv;
+              }
+          }
           // B^T along a then b
           for (int qb = 0; qb < n; ++qb)
             for (int ia = 0; ia < n; ++ia) {

@@ -32,7 +32,13 @@ struct HostMesh {
   const double* b;      // host 3 * nvert or nullptr
   const double* c;      // host ncell or nullptr
   double alpha;
+  // K(x), c(x) varying inside the cells (basis rows n_k, p0, p2, gamma; 16
+  // values) or nullptr; the right-hand side then uses K(x) on Dirichlet faces.
+  const double* var = nullptr;
 };
+
+// K(x) = sum_k (p0_k + p2_k x_k^2) n_k n_k^T at a point: (xx, yy, zz, xy, xz, yz).
+void var_tensor(const double* var, const double x[3], double K[6]);
 
 // A_hat (App. A.2) as a 27-point stencil on the (nx+1)(ny+1)(nz+1) vertices.
 std::vector<double> q1_stencil(const HostMesh& m);

@@ -260,7 +260,7 @@ __global__ void k_inverse(long long n, const double* __restrict__ d, double* __r
 constexpr int kInvMaxN = 128;
 
 
-__global__ void __launch_bounds__(256) k_block_invert(double* __restrict__ a, int nb, long long ncell,
+__global__ void __launch_bounds__(256) k_block_invert(double* __restrict__ a, int nb, int ld, long long ncell,
                                                        int* __restrict__ singular) {
   extern __shared__ __align__(16) double sm_inv[];
   __shared__ int perm[kInvMaxN];
@@ -272,9 +272,9 @@ __global__ void __launch_bounds__(256) k_block_invert(double* __restrict__ a, in
   double* M = sm_inv;
   double* colk = M + nb * nb;
   double* rowk = colk + nb;
-  double* g = a + c * (long long)nb * nb;
+  double* g = a + c * (long long)nb * ld;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int t = tid; t < nb * nb; t += nt) M[t] = g[t];
+  for (int t = tid; t < nb * nb; t += nt) M[t] = g[(t % nb) + (long long)(t / nb) * ld];
   __syncthreads();
   for (int k = 0; k < nb; ++k) {
     double best = -1.0;
@@ -352,7 +352,28 @@ __global__ void __launch_bounds__(256) k_block_invert(double* __restrict__ a, in
       }
     __syncthreads();
   }
-  for (int t = tid; t < nb * nb; t += nt) g[t] = M[t];
+  for (int t = tid; t < nb * nb; t += nt) g[(t % nb) + (long long)(t / nb) * ld] = M[t];
+}
+
+__global__ void k_split_df(long long n, const double* __restrict__ x, float2* __restrict__ pairs,
+                           float* __restrict__ f32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = (float)v;
+    pairs[i] = make_float2(h, (float)(v - (double)h));
+    if (f32) f32[i] = h;
+  }
+}
+
+__global__ void k_df_to_dense(long long ncell, int nb, int ld, const float2* __restrict__ pairs,
+                              double* __restrict__ out) {
+  const long long n = ncell * nb * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long col = t / nb;              // cell * nb + j
+    const int i = (int)(t - col * nb);
+    const float2 p = pairs[col * ld + i];
+    out[t] = (double)p.x + (double)p.y;
+  }
 }
 
 // P0 restriction: out[c] = sum of cell c's n3 values, one warp per cell, lanes
@@ -415,7 +436,22 @@ cudaError_t cell_add(long long ncell, int n3, const double* uhat, void* u, bool 
   return cudaGetLastError();
 }
 
-cudaError_t block_invert(double* a, int nb, long long ncell, int* singular, cudaStream_t s) {
+cudaError_t vec_split_df(long long n, const double* x, float2* pairs, float* f32, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_split_df<<<grid1(n), kThreads, 0, s>>>(n, x, pairs, f32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t blocks_df_to_dense(long long ncell, int nb, int ld, const float2* pairs, double* out, cudaStream_t s) {
+  const long long n = ncell * nb * nb;
+  if (n == 0) return cudaSuccess;
+  k_df_to_dense<<<grid1(n), kThreads, 0, s>>>(ncell, nb, ld, pairs, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t block_invert(double* a, int nb, int ld, long long ncell, int* singular, cudaStream_t s) {
   if (ncell == 0) return cudaSuccess;
   if (nb < 1 || nb > kInvMaxN) return cudaErrorInvalidValue;
   const size_t smem = ((size_t)nb * nb + 2 * nb) * sizeof(double);
@@ -424,7 +460,8 @@ cudaError_t block_invert(double* a, int nb, long long ncell, int* singular, cuda
     if (e != cudaSuccess) return e;
   }
   if (ncell > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_block_invert<<<(unsigned)ncell, nb >= 64 ? 256 : 128, smem, s>>>(a, nb, ncell, singular);
+  if (ld < nb) return cudaErrorInvalidValue;
+  k_block_invert<<<(unsigned)ncell, nb >= 64 ? 256 : 128, smem, s>>>(a, nb, ld, ncell, singular);
   count_launch();
   return cudaGetLastError();
 }

@@ -84,6 +84,7 @@ _SIG = {
     "dgmg_restrict_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P]),
     "dgmg_set_launch_shape": (_I, [_P, _I, _I, _I]),
     "dgmg_block_inverse": (_I, [_P, _I, _P]),
+    "dgmg_set_variable_coefficients": (_I, [_P, _P, _P, _P, _D]),
     "dgmg_restrict_p0": (_I, [_P, _P, _P, _I]),
     "dgmg_prolong_add_p0": (_I, [_P, _P, _P, _I]),
     "dgmg_coarse_matrix_p0": (_I, [_P, _P]),
@@ -205,6 +206,15 @@ class Context:
         ba, bp = _host(b_vertex)
         ca, cp = _host(c_cell)
         self._check(self.lib.dgmg_set_coefficients(self.h, Kp, kdim, bp, cp))
+
+    def set_variable_coefficients(self, basis, p0, p2, gamma):
+        """K(x) = sum_k (p0_k + p2_k x_k^2) n_k n_k^T (rows of `basis` are n_k),
+        c(x) = gamma |x|^2 for the outer operator; cell-centre values for the
+        preconditioner."""
+        b, bp = _host(np.asarray(basis, dtype=np.float64).reshape(9))
+        a0, p0p = _host(p0)
+        a2, p2p = _host(p2)
+        self._check(self.lib.dgmg_set_variable_coefficients(self.h, bp, p0p, p2p, float(gamma)))
 
     def sizes(self):
         v = [_LL() for _ in range(5)]

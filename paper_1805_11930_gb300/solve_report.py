@@ -1,6 +1,6 @@
 """Time-to-solution report for the synthetic workloads.
 
-python -m paper_1805_11930_gb300.solve_report [--workloads poisson,lognormal,convection,reservoir,convection_pe2000] [--repeat 3]
+python -m paper_1805_11930_gb300.solve_report [--workloads poisson,lognormal,convection,reservoir,convection_pe2000,variable_k] [--repeat 3]
 
 For each workload: set-up time (coefficients, diag(D_T), Q1 matrix, AMG),
 then the solve to a 1e-8 relative residual from u = 0: in FP64; with the
@@ -13,7 +13,9 @@ is reported separately); the reservoir workload also with the P0 coarse
 space (the paper's choice for SPE10); the grid-Peclet-2000 convection
 workload (Sec. 4.3) with the paper's set-up: FGMRES preconditioned by two
 multicolour block-SSOR sweeps and no coarse correction, inner GMRES with the
-tridiagonal (Thomas) preconditioner.  Reports the median
+tridiagonal (Thomas) preconditioner; the inhomogeneous test of Sec. 4.2 with
+K(x), c(x) at the quadrature points in the outer operator and cell-centre
+values in the V-cycle.  Reports the median
 solve time over --repeat runs (CUDA events, inputs resident), outer
 iterations, mean / max inner iterations, the recomputed FP64 residual, the
 difference between the mixed and FP64 solutions and, where the workload has
@@ -43,6 +45,9 @@ def run(name, repeat):
         # high-contrast anisotropic K: three AMG cycles per coarse correction
         w, kry, inner = inputs.reservoir(), dgmg.KRYLOV_CG, dgmg.INNER_PCG
         extra = dict(coarse_cycles=3)
+    elif name == "variable_k":
+        # K(x), c(x) at the quadrature points in the outer operator, cell-centre values in the V-cycle
+        w, kry, inner = inputs.variable_k(32, 3), dgmg.KRYLOV_CG, dgmg.INNER_PCG
     elif name == "convection_pe2000":
         w, kry, inner = inputs.convection_pe(32, 3), dgmg.KRYLOV_FGMRES, dgmg.INNER_GMRES_TRIDIAG
         extra = dict(smoother=dgmg.SMOOTHER_SSOR, coarse=dgmg.COARSE_NONE)
@@ -51,7 +56,11 @@ def run(name, repeat):
     t0 = time.perf_counter()
     ctx = dgmg.Context(0)
     ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
-    ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
+    if "vark" in w:
+        vk = w["vark"]
+        ctx.set_variable_coefficients(vk["basis"], vk["p0"], vk["p2"], vk["gamma"])
+    else:
+        ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
     vol, face = ctx.quadrature_points()
     s = ctx.sizes()
     f = torch.empty(s["ndof"], dtype=torch.float64, device="cuda")
@@ -65,7 +74,7 @@ def run(name, repeat):
     variants = [("fp64", dgmg.default_opts(krylov=kry, inner=inner, maxit=1000, **extra)),
                 ("mixed", dgmg.default_opts(krylov=flex, inner=inner, smoother_prec=dgmg.FP32, maxit=1000,
                                             **extra))]
-    if w["b"] is None:       # the double-float kernels cover diffusion
+    if w["b"] is None and "vark" not in w:   # the double-float kernels cover diffusion
         variants.append(("df64", dgmg.default_opts(krylov=flex, inner=inner, smoother_prec=dgmg.DF64,
                                                    apply_prec=dgmg.DF64, maxit=1000, **extra)))
     if name == "reservoir":  # the piecewise-constant coarse space of the paper's SPE10 runs
@@ -123,7 +132,7 @@ def run(name, repeat):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workloads", default="poisson,lognormal,convection,reservoir,convection_pe2000")
+    ap.add_argument("--workloads", default="poisson,lognormal,convection,reservoir,convection_pe2000,variable_k")
     ap.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     for name in args.workloads.split(","):

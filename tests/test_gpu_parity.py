@@ -557,8 +557,10 @@ def test_autotune_choices_and_bitwise_solve():
 @pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full"])
 def test_block_inverse_matches_oracle_blocks(name):
     """dgmg_block_inverse: every stored block times the oracle's assembled
-    diagonal block D_T is the identity to 1e-12 (FP64), and the FP32 copy is
-    the FP64 one rounded (1e-6 relative per block)."""
+    diagonal block D_T is the identity up to the rounding of the stored
+    double-float pairs (64 units of 2^-48 times max |D_T^-1| |D_T|, about
+    1e-13 here), and the FP32 copy is the same inverse rounded (1e-6
+    relative per block)."""
     from paper_1805_11930_gb300 import dgmg
     w, P, A = oracle_matrix(name)
     ctx = gpu_context(w)
@@ -569,7 +571,8 @@ def test_block_inverse_matches_oracle_blocks(name):
     D = solvers.BlockJacobi(A, nb, inner="lu").D
     eye = np.eye(nb)
     for c in range(P.ncell):
-        assert np.abs(inv[c] @ D[c] - eye).max() < 1e-12 * max(1.0, np.linalg.cond(D[c]) * 1e-3)
+        bound = 64 * 2.0 ** -48 * (np.abs(inv[c]) @ np.abs(D[c])).max()
+        assert np.abs(inv[c] @ D[c] - eye).max() < bound
     out32 = torch.empty(P.ncell * nb * nb, dtype=torch.float32, device="cuda")
     ctx.block_inverse(dgmg.FP32, out32)
     inv32 = out32.cpu().numpy().astype(np.float64).reshape(P.ncell, nb, nb).transpose(0, 2, 1)
@@ -815,3 +818,136 @@ def test_solve_energy_norm_stopping():
     assert np.sqrt(e @ (A @ e) / (xs @ (A @ xs))) <= 1e-6
     with pytest.raises(dgmg.DgmgError):
         ctx.solve(f, torch.zeros_like(f), dgmg.default_opts(stop=dgmg.STOP_ENERGY, krylov=dgmg.KRYLOV_FGMRES))
+
+
+# ------------------------------------------------------------- full sizes, sampled cells
+def _picks(P, seed, extra=8):
+    nx, ny, nz = P.nc
+    picks = [P.cell_index(0, 0, 0), P.cell_index(nx - 1, ny - 1, nz - 1), P.cell_index(0, ny - 1, nz // 2),
+             P.cell_index(nx // 2, 0, nz - 1), P.cell_index(nx // 2, ny // 2, nz // 2), P.cell_index(nx - 1, 1, 0)]
+    return picks + [int(c) for c in np.random.default_rng(seed).integers(0, P.ncell, size=extra)]
+
+
+@pytest.mark.parametrize("which", ["convection_64_q3", "reservoir_q2"])
+def test_full_size_sampled_apply(which):
+    """The full convection (64^3 Q3, 16.8 M dofs, advection) and reservoir
+    (60x220x85 Q2, 30.3 M dofs, anisotropic K, mixed boundary) operators on
+    sampled cells (corners, edges, faces, interior, random) against the
+    oracle's block rows: FP64 1e-12, FP32 1e-5."""
+    w = inputs.convection(64, 3) if which.startswith("convection") else inputs.reservoir()
+    P = oracle_problem(w)
+    ctx = gpu_context(w)
+    u = inputs.random_dg_vector(P.ndof, seed=71)
+    picks = _picks(P, 72)
+    ref = P.apply_rows(u, picks)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        x = dev(u).to(dt)
+        v = torch.empty_like(x)
+        ctx.apply(x, v)
+        got = v.double().cpu().numpy().reshape(P.ncell, P.N)[picks]
+        assert rel_err(got, ref) < tol, dt
+        del x, v
+
+
+def test_full_size_sampled_smoothers_lognormal_32():
+    """The benchmark's mesh (32^3 Q4) and autotuned launch shapes: one sweep
+    with stored inverses equals, on sampled cells, u_T + omega D_T^-1 d_T from
+    the oracle's block row and dense solve (1e-12); one inner-PCG sweep
+    (eps = 1e-2) equals the oracle's block PCG from the same defect on every
+    sampled cell with the same iteration count (1e-10) and meets the stopping
+    test on all of them."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.lognormal(32, 4)
+    P = oracle_problem(w)
+    ctx = gpu_context(w)
+    ctx.autotune(dgmg.FP64)
+    N = P.N
+    f = inputs.random_dg_vector(P.ndof, seed=73)
+    u0 = inputs.random_dg_vector(P.ndof, seed=74)
+    picks = _picks(P, 75)
+    d = f.reshape(P.ncell, N)[picks] - P.apply_rows(u0, picks)
+    D = [P.diagonal_block(c) for c in picks]
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=1, omega=0.8, inner=dgmg.INNER_DIRECT)
+    got = u.cpu().numpy().reshape(P.ncell, N)[picks]
+    ref = u0.reshape(P.ncell, N)[picks] + 0.8 * np.stack([np.linalg.solve(Dc, dc) for Dc, dc in zip(D, d)])
+    assert rel_err(got, ref) < 1e-12
+    its = torch.zeros(P.ncell, dtype=torch.int32, device="cuda")
+    u = dev(u0)
+    ctx.block_smooth(dev(f), u, nsweep=1, omega=1.0, eps=1e-2, inner_its=its)
+    got = u.cpu().numpy().reshape(P.ncell, N)[picks] - u0.reshape(P.ncell, N)[picks]
+    its = its.cpu().numpy()[picks]
+    same = 0
+    for r, (Dc, dc) in enumerate(zip(D, d)):
+        assert np.linalg.norm(dc - Dc @ got[r]) <= 1e-2 * np.linalg.norm(dc) * (1 + 1e-9)
+        x, it = solvers.block_pcg(Dc, dc, np.diag(Dc), 1e-2, N)
+        if it == its[r]:
+            same += 1
+            assert rel_err(got[r], x) < 1e-10
+    assert same >= len(picks) - 2
+
+
+# ------------------------------------------------------------- K(x), c(x) varying inside cells
+def _vark_problem(nc, L, p, bc, gamma):
+    return dg.Problem(*nc, *L, p, bc, np.ones(int(np.prod(nc))), K_fn=inputs.vark_tensor,
+                      c_fn=lambda x: inputs.vark_reaction(x, gamma))
+
+
+def _vark_context(nc, L, p, bc, gamma):
+    from paper_1805_11930_gb300 import dgmg
+    ctx = dgmg.Context(0)
+    ctx.set_mesh(*nc, *L, p, bc)
+    ctx.set_variable_coefficients(inputs.VARK_BASIS, inputs.VARK_P0, inputs.VARK_P2, gamma)
+    return ctx
+
+
+@pytest.mark.parametrize("case", [((3, 2, 2), 2, [0, 1, 0, 0, 1, 0]), ((2, 3, 2), 3, [0] * 6),
+                                  ((2, 2, 2), 4, [1, 0, 0, 1, 0, 0]), ((3, 2, 1), 6, [0, 0, 1, 0, 0, 0])])
+def test_variable_operator_and_rhs_match_oracle(case):
+    """The operator with K(x), c(x) evaluated at every quadrature point (the
+    paper's rotated quadratic K, a visible reaction gamma = 0.5) against the
+    oracle's assembled matrix (1e-12), and the right-hand side with K(x) in
+    the Dirichlet terms (1e-13)."""
+    nc, p, bc = case
+    L = (1.0, 0.8, 1.2)
+    P = _vark_problem(nc, L, p, bc, 0.5)
+    A = P.assemble()
+    ctx = _vark_context(nc, L, p, bc, 0.5)
+    u = inputs.random_dg_vector(P.ndof, seed=81)
+    v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(u), v)
+    assert rel_err(v.cpu().numpy(), A @ u) < 1e-12
+    g = lambda x, y, z: np.exp(-((x - 0.2) ** 2 + (y - 0.5) ** 2) / 0.1) + z   # noqa: E731
+    j = lambda x, y, z: np.cos(x + 2 * y) * z                                   # noqa: E731
+    f = lambda x, y, z: np.sin(3 * x) * y + z * z                              # noqa: E731
+    w = custom(nc, L, p, bc, np.ones(int(np.prod(nc))), f=f, g=g, j=j)
+    ref = oracle_rhs(P, w)
+    rhs = gpu_rhs(ctx, w, torch)
+    assert rel_err(rhs.cpu().numpy(), ref) < 1e-13
+
+
+def test_variable_solve_paper_setup():
+    """The inhomogeneous test of Sec. 4.2 (8^3, Q3, Neumann on x = 1, Gaussian
+    data, gamma = 1e-8): CG with the cell-centre V-cycle reaches 1e-8 in the
+    exact operator's residual, in FP64 and mixed precision and with the
+    energy-norm rule, and matches the oracle's direct solve to 1e-6."""
+    import scipy.sparse.linalg as spla
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.variable_k(8, 3)
+    P = dg.Problem(*w["nc"], *w["L"], w["p"], w["bc"], w["K"], K_fn=w["K_fn"], c_fn=w["c_fn"])
+    xs = spla.spsolve(P.assemble().tocsc(), oracle_rhs(P, w))
+    ctx = dgmg.Context(0)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    vk = w["vark"]
+    ctx.set_variable_coefficients(vk["basis"], vk["p0"], vk["p2"], vk["gamma"])
+    f = gpu_rhs(ctx, w, torch)
+    for opts in (dgmg.default_opts(), dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)):
+        u = torch.zeros_like(f)
+        st = ctx.solve(f, u, opts)
+        assert st["converged"] and st["rel_residual"] <= 1e-8
+        assert rel_err(u.cpu().numpy(), xs) < 1e-6
+    u = torch.zeros_like(f)
+    st = ctx.solve(f, u, dgmg.default_opts(stop=dgmg.STOP_ENERGY, rtol=1e-6))
+    assert st["converged"]
+    with pytest.raises(dgmg.DgmgError):
+        ctx.apply(f.float(), torch.empty_like(f).float())
