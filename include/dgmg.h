@@ -54,8 +54,9 @@ typedef enum {
 /* DGMG_DF64: FP64 vectors in memory, arithmetic in double-float (pairs of
  * FP32 numbers, about 48 significant bits): FP64-level accuracy on the FP32
  * pipe, which GB300 issues 62x faster than FP64.  Built for diffusion (b = 0)
- * with p <= 6, and in the smoothers with the inner PCG; other combinations
- * return DGMG_ERR_ARG. */
+ * with p <= 6, and in the smoothers with the inner PCG or the stored inverses
+ * (DIRECT, which then shares the FP64 smoothers' double-float pairs); other
+ * combinations return DGMG_ERR_ARG. */
 typedef enum { DGMG_FP64 = 0, DGMG_FP32 = 1, DGMG_DF64 = 2 } dgmg_prec;
 typedef enum { DGMG_KRYLOV_CG = 0, DGMG_KRYLOV_FCG = 1, DGMG_KRYLOV_FGMRES = 2 } dgmg_krylov;
 /* Block solves of the smoother: inner PCG or GMRES on the matrix-free block,

@@ -314,12 +314,13 @@ dgmg_status ready(dgmg_ctx* ctx) {
 }
 
 // Double-float kernels exist for diffusion (b = 0) with p <= 6 and, in the
-// smoothers, the inner PCG.
+// smoothers, the inner PCG or the stored inverses.
 dgmg_status check_df64(dgmg_ctx* ctx, int prec, int inner) {
   if (prec != DGMG_DF64) return DGMG_OK;
   if (ctx->p > 6) return fail(ctx, DGMG_ERR_ARG, "DF64 kernels are built for p <= 6");
   if (ctx->db) return fail(ctx, DGMG_ERR_ARG, "DF64 kernels are built for b = 0");
-  if (inner != DGMG_INNER_PCG) return fail(ctx, DGMG_ERR_ARG, "DF64 smoothers use the inner PCG");
+  if (inner != DGMG_INNER_PCG && inner != DGMG_INNER_DIRECT)
+    return fail(ctx, DGMG_ERR_ARG, "DF64 smoothers use the inner PCG or stored inverses");
   return DGMG_OK;
 }
 
@@ -456,7 +457,7 @@ dgmg_status inner_data(dgmg_ctx* ctx, int inner, int prec, const void** binv, co
   *binv = *tri = nullptr;
   const bool fp32 = prec == DGMG_FP32;
   if (inner == DGMG_INNER_DIRECT) {
-    CS(ensure_binv(ctx, prec));
+    CS(ensure_binv(ctx, prec == DGMG_DF64 ? DGMG_FP64 : prec));   // DF64 shares the FP64 pairs
     *binv = fp32 ? (const void*)ctx->binv32 : (const void*)ctx->binv_df;
   } else if (inner == DGMG_INNER_GMRES_TRIDIAG) {
     CS(ensure_tri(ctx, prec));

@@ -942,6 +942,7 @@ __global__ void __launch_bounds__(256) k_block_matrix(MeshParams mp, double* __r
 // FP32 entries and FP32 arithmetic.
 template <typename T> struct InvEntry { using type = T; };
 template <> struct InvEntry<double> { using type = float2; };
+template <> struct InvEntry<df> { using type = float2; };
 
 template <typename T, bool ADV, typename G = typename Store<T>::type, typename M = typename InvEntry<T>::type>
 __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __restrict__ f, const G* uold, G* unew,
@@ -980,6 +981,7 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
     const T dv = act[cw] ? T(f[cid[cw] * N3 + (e - cw * N3)]) - (zero ? T(0) : Q[e]) : T(0);
     P[e] = dv;
     if constexpr (std::is_same<T, double>::value) D2[e] = df(dv);
+    if constexpr (std::is_same<T, df>::value) D2[e] = dv;
   }
   __syncwarp();
   for (int e = lane; e < VEC; e += 32) {
@@ -988,7 +990,7 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
     const int i = e - cw * N3;
     const M* col = binv + cid[cw] * (long long)N3 * ld + i;
     T acc;
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (!std::is_same<T, float>::value) {   // FP64 and double-float smoothers
       const df* d = D2 + cw * N3;
       df_acc a;
 #pragma unroll 8
@@ -996,7 +998,10 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
         const float2 m = __ldg(col + (long long)j * ld);
         a.add_prod(df(m.x, m.y), d[j]);
       }
-      acc = double(a.value());
+      if constexpr (std::is_same<T, double>::value)
+        acc = double(a.value());
+      else
+        acc = a.value();
     } else {
       const T* d = P + cw * N3;
       acc = T(0);
@@ -2035,9 +2040,12 @@ cudaError_t smooth(const MeshParams& mp, const SmoothArgs& a, int prec, cudaStre
   if (mp.ncell == 0) return cudaSuccess;
   if (prec == DGMG_FP32) return smooth_t<float>(mp, a, s);
   if (prec == DGMG_DF64) {
-    // double-float smoother: block-Jacobi / SOR with inner PCG, b = 0, p <= 6
+    // double-float smoother: block-Jacobi / SOR with inner PCG or stored
+    // inverses, b = 0, p <= 6
 #if DGMG_N <= 7
-    if (mp.bvert || a.inner != DGMG_INNER_PCG) return cudaErrorNotSupported;
+    if (mp.bvert) return cudaErrorNotSupported;
+    if (a.inner == DGMG_INNER_DIRECT) return launch_inv<df, false>(mp, a, s);
+    if (a.inner != DGMG_INNER_PCG) return cudaErrorNotSupported;
     return launch_smooth<df, false>(mp, a, s);
 #else
     return cudaErrorNotSupported;

@@ -90,6 +90,10 @@ def run(name, repeat):
         variants.append(("fp64_direct", dgmg.default_opts(krylov=kry, inner=dgmg.INNER_DIRECT, maxit=1000, **extra)))
         variants.append(("mixed_direct", dgmg.default_opts(krylov=flex, inner=dgmg.INNER_DIRECT,
                                                            smoother_prec=dgmg.FP32, maxit=1000, **extra)))
+        if w["b"] is None and "vark" not in w:
+            variants.append(("df64_direct", dgmg.default_opts(krylov=flex, inner=dgmg.INNER_DIRECT,
+                                                              smoother_prec=dgmg.DF64, apply_prec=dgmg.DF64,
+                                                              maxit=1000, **extra)))
     for tag, opts in variants:
         u = torch.zeros_like(f)
         ms, st = [], None

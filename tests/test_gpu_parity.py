@@ -583,8 +583,8 @@ def test_block_inverse_matches_oracle_blocks(name):
 @pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full"])
 def test_block_smooth_direct_matches_exact_block_jacobi(name):
     """inner = DIRECT (stored inverses): two block-Jacobi sweeps equal the
-    oracle's dense-LU block-Jacobi to 1e-12 in FP64 and 1e-5 in FP32, every
-    cell reporting 0 inner iterations."""
+    oracle's dense-LU block-Jacobi to 1e-12 in FP64 and double-float (b = 0)
+    and 1e-5 in FP32, every cell reporting 0 inner iterations."""
     from paper_1805_11930_gb300 import dgmg
     w, P, A = oracle_matrix(name)
     ctx = gpu_context(w)
@@ -599,6 +599,10 @@ def test_block_smooth_direct_matches_exact_block_jacobi(name):
     u32 = dev(u0).float()
     ctx.block_smooth(dev(f).float(), u32, nsweep=2, omega=0.8, inner=dgmg.INNER_DIRECT)
     assert rel_err(u32.double().cpu().numpy(), ref) < 1e-5
+    if w["b"] is None:      # double-float defect and product (diffusion only)
+        udf = dev(u0)
+        ctx.block_smooth(dev(f), udf, nsweep=2, omega=0.8, inner=dgmg.INNER_DIRECT, df64=True)
+        assert rel_err(udf.cpu().numpy(), ref) < 1e-12
 
 
 @pytest.mark.parametrize("name", ["p2_mixed", "p3_adv"])
@@ -618,8 +622,9 @@ def test_block_ssor_direct_matches_oracle(name):
 
 def test_solve_direct_blocks_c1_and_rejections():
     """CG with a V-cycle whose smoother uses the stored inverses reaches 1e-8
-    on the Poisson workload in no more iterations than inner PCG; DF64 and
-    p > 4 reject DIRECT."""
+    on the Poisson workload in no more iterations than inner PCG, also in
+    FP32 and double-float; DF64 rejects inner GMRES and p > 4 rejects the
+    stored inverses."""
     from paper_1805_11930_gb300 import dgmg
     w = inputs.poisson_sine(8, 2)
     ctx = gpu_context(w)
@@ -635,8 +640,12 @@ def test_solve_direct_blocks_c1_and_rejections():
     s32 = ctx.solve(f, u2, dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.FP32,
                                              krylov=dgmg.KRYLOV_FCG))
     assert s32["converged"] and s32["rel_residual"] <= 1e-8
+    udf = torch.zeros_like(f)
+    sdf = ctx.solve(f, udf, dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.DF64,
+                                              krylov=dgmg.KRYLOV_FCG))
+    assert sdf["converged"] and sdf["rel_residual"] <= 1e-8
     with pytest.raises(dgmg.DgmgError):
-        ctx.solve(f, torch.zeros_like(f), dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.DF64))
+        ctx.solve(f, torch.zeros_like(f), dgmg.default_opts(inner=dgmg.INNER_GMRES, smoother_prec=dgmg.DF64))
     w5 = inputs.lognormal(2, 5)
     ctx5 = gpu_context(w5)
     with pytest.raises(dgmg.DgmgError):
