@@ -41,8 +41,8 @@ SM_MAX_MHZ = 2070.0
 CPU_SAMPLE = dict(n=6, p=4)        # oracle sample: same workload family, 6^3 cells
 # DRAM bytes (read + write) of one k_smooth_pcg<double> launch on this mesh, from
 # the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt
-# (a sweep with defect, 2 warps per block); set to None when that kernel changes.
-SMOOTHER_TRAFFIC_BYTES = 103.30112e6 + 13.126912e6
+# (a sweep with defect); None while that capture predates the kernel.
+SMOOTHER_TRAFFIC_BYTES = None
 
 
 def fp64_peak_tflops():
@@ -195,6 +195,7 @@ def run_dgmg(args, rank, world, local_rank):
     zero = sum(x["zero_sweeps"] for x in stats)
     its = sum(x["inner_its_total"] for x in stats)
     sm_flops = flops.algorithmic_smoother(n, ncell, sweeps, zero, its)
+    sm_kflops = flops.kernel_smoother(n, ncell, sweeps, zero, its)
     ap_flops = flops.algorithmic_apply(n) * ncell * sum(x["applies"] for x in stats)
     peak = fp64_peak_tflops()
     dominant = "smoother" if sm_ms >= ap_ms else "apply"
@@ -215,6 +216,11 @@ def run_dgmg(args, rank, world, local_rank):
                                 "mesh (profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt); algorithmic bytes "
                                 "4 x 8 B x ndof = 131 MB, part of it served from L2",
                 "flops_per_launch": per_launch, "launch_ms": round(launch_ms, 4),
+                "frac_kernel_count": (round(sm_kflops / (sm_ms / 1e3) / 1e12 / peak, 4)
+                                      if dominant == "smoother" else None),
+                "kernel_count_note": "flops the kernel issues (Kronecker block apply 16 n^4 per inner iteration, "
+                                     "full apply 16 n^4 + 84 n^3 + 120 n^2 per defect, 13 n^3 vector work) over "
+                                     "the same time and peak",
                 "flops_note": "algorithmic: (32 n^4 + 120 n^3) per cell per apply, one apply per defect and per "
                               "inner iteration",
                 "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x sm_max_mhz (derived, nominal 1.25 TFLOP/s)",

@@ -297,6 +297,99 @@ __device__ __forceinline__ void contract_scaled(const T* __restrict__ in, T* __r
   }
 }
 
+// out (+)= A_cw in along axis D with a per-cell n x n matrix: A_cw at
+// Am + (3 cw + D) n^2, row-major (A[i][j] multiplies in_j into out_i).
+template <int D, bool ACC, typename T>
+__device__ __forceinline__ void contract_cell(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ Am,
+                                              int lane, const unsigned char* act) {
+  for (int L = lane; L < LINES; L += 32) {
+    int cw, base, st, a, b;
+    line_geom<D>(L, cw, base, st, a, b);
+    if (!act[cw]) continue;
+    const T* A = Am + (3 * cw + D) * N2;
+    T x[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = in[base + j * st];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T s;
+      if constexpr (std::is_same<T, df>::value) {
+        df_acc acc;
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc.add_prod(A[i * N + j], x[j]);
+        s = acc.value();
+      } else {
+        s = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(A[i * N + j], x[j], s);
+      }
+      if (ACC)
+        out[base + i * st] += s;
+      else
+        out[base + i * st] = s;
+    }
+  }
+}
+
+// The 1D matrices of the block D_T for b = 0: with K diagonal and constant on
+// the affine cell, the volume term and the own-side parts of the face terms
+// (consistency, symmetry, penalty, integrated exactly with the face mass
+// M (x) M) are Kronecker products, so D_T = A_x (x) M (x) M + M (x) A_y (x) M
+// + M (x) M (x) A_z with
+//   A_d = |J| K_d / h_d^2 S + sum over the non-Neumann faces s of d of
+//         |F| [ -kap sg / h_d (e_e dl_s^T + dl_s e_e^T) + gamma e_e e_e^T ],
+// e = end node of side s, sg = +-1 its outward sign, kap = w K (K on
+// Dirichlet faces), plus c |J| M in A_z.  Written to Am (3 n^2 per cell).
+template <typename T>
+__device__ __forceinline__ void block_matrices(const MeshParams& mp, T* Am, const CellInfo<T>* ci,
+                                               const unsigned char* act, int lane) {
+  const Tab<T>& t = tab<T>();
+  for (int k = lane; k < CPW * 3 * N2; k += 32) {
+    const int cw = k / (3 * N2), r = k - cw * 3 * N2, d = r / N2, i = (r % N2) / N, j = r % N;
+    if (!act[cw]) continue;
+    T a = ci[cw].kd[d] * t.S1[i][j];
+    if (d == 2) a = fma(ci[cw].cJ, t.M1[i][j], a);
+    const T ih = Prec<T>::ih(mp, d);
+    for (int s = 0; s < 2; ++s) {
+      const int f = 2 * d + s;
+      if (ci[cw].kind[f] == 2) continue;
+      const int e = s ? N - 1 : 0;
+      const T ks = (s ? -ci[cw].kap[f] : ci[cw].kap[f]) * ih;   // -kap sg / h_d
+      T fv = T(0);
+      if (i == e) fv = fma(ks, t.dl[s][j], fv);
+      if (j == e) fv = fma(ks, t.dl[s][i], fv);
+      if (i == e && j == e) fv = fv + ci[cw].gam[f];
+      a = fma(ci[cw].jh[d], fv, a);
+    }
+    Am[k] = a;
+  }
+  __syncwarp();
+}
+
+// Q = D_T P for b = 0 by the Kronecker form above: 8 contractions, no face
+// passes (the face terms are inside A_d).
+template <typename T>
+__device__ __forceinline__ void block_kron(const T* X, T* Y, T* S0, T* S1, const T* Am, int lane,
+                                           const unsigned char* act) {
+  const Tab<T>& t = tab<T>();
+  contract<2, false, false>(X, S0, t.M1, lane, act);   // a = M_z u
+  __syncwarp();
+  contract<1, false, false>(S0, S1, t.M1, lane, act);  // b = M_y a
+  __syncwarp();
+  contract_cell<0, false>(S1, Y, Am, lane, act);       // Y = A_x b
+  __syncwarp();
+  contract<0, false, false>(S0, S1, t.M1, lane, act);  // c = M_x a
+  __syncwarp();
+  contract_cell<1, true>(S1, Y, Am, lane, act);        // Y += A_y c
+  __syncwarp();
+  contract<0, false, false>(X, S0, t.M1, lane, act);   // e = M_x u
+  __syncwarp();
+  contract<1, false, false>(S0, S1, t.M1, lane, act);  // f = M_y e
+  __syncwarp();
+  contract_cell<2, true>(S1, Y, Am, lane, act);        // Y += A_z f
+  __syncwarp();
+}
+
 // Y = A^v X for the warp's cells.  S0, S1 scratch.
 //  b = 0: K and c are constant per cell and the cell affine, so the volume
 //   matrix is exactly sum_d |J| K_d / h_d^2 (S (x) M (x) M)_d + c |J| M (x) M (x) M
@@ -739,18 +832,20 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
   if (s0 >= color_count(mp, color)) return;
-  T* vec[6];
   T *F0, *F1, *red;
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  carve(smem + warp * WarpMem<T>::bytes(6), 6, vec, &F0, &F1, &red, &ci, &act, &cid);
+  constexpr int NV = ADV ? 6 : 8;   // b = 0: vec[6..7] hold the per-cell 1D matrices of D_T
+  T* vec[8];
+  carve(smem + warp * WarpMem<T>::bytes(NV), NV, vec, &F0, &F1, &red, &ci, &act, &cid);
   T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3], *R = vec[4], *DL = vec[5];
   const bool react = mp.c != nullptr;
   const bool zero = uold == nullptr;   // first sweep from u = 0: no defect apply
   slot_cells(mp, color, s0, lane, cid);
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
+  if constexpr (!ADV) block_matrices(mp, vec[6], ci, act, lane);
   // my cell slot (lanes without a line: -1)
   const int mycw = lane < LINES ? lane / N2 : -1;
   const bool mine = mycw >= 0 && act[mycw];
@@ -808,8 +903,12 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
     if (lane < LINES) act[mycw] = (live && it < maxit) ? 1 : 0;
     __syncwarp();
     const bool run = live && it < maxit;
-    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
-    all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+    if constexpr (ADV) {
+      volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+      all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+    } else {
+      block_kron(P, Q, S0, S1, vec[6], lane, act);
+    }
     T ppq = T(0);
     if (run) {
       for (int L = lane; L < LINES; L += 32) {
@@ -1926,8 +2025,9 @@ cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool f
 template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6));
-  const size_t sm = wpb * WarpMem<T>::bytes(6);
+  constexpr int NV = ADV ? 6 : 8;
+  const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(NV));
+  const size_t sm = wpb * WarpMem<T>::bytes(NV);
   auto k = k_smooth_pcg<T, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;

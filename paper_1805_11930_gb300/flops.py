@@ -11,10 +11,14 @@ counted like a full apply.  One smoother sweep over a cell costs one apply
 for its defect (none when it starts from zero) plus one apply per inner
 iteration.
 
-Kernel count (what the kernels issue, for reference): volume 24 n^4 + 9 n^3
-(six contractions with B, B^T and three fused Dg / coefficient / Dg^T
-passes), faces 84 n^3 + 120 n^2 (full) or 72 n^3 + 100 n^2 (block), inner
-iteration vector work 13 n^3.
+Kernel count (what the kernels issue, b = 0, for reference): the volume term
+is the exact Kronecker form sum_d c_d (S (x) M (x) M)_d, 8 contractions of
+2 n^4 = 16 n^4; the faces of a full apply 84 n^3 + 120 n^2 (cell-centric);
+the inner block apply of the smoother is D_T = sum_d A_d (x) M (x) M with
+per-cell 1D matrices A_d that contain the own-side face terms, again
+16 n^4 with no face pass; inner-iteration vector work 13 n^3.  With
+advection the volume term runs at the Gauss points (24 n^4 + 9 n^3) and the
+block apply adds the own-side faces (72 n^3 + 100 n^2).
 """
 
 
@@ -30,12 +34,23 @@ def algorithmic_smoother(n, ncell, sweeps, zero_sweeps, inner_its_total, value_t
     return F * (ncell * (sweeps - zero_sweeps) + inner_its_total)
 
 
-def kernel_apply_full(n):
-    return 24 * n ** 4 + 9 * n ** 3 + 84 * n ** 3 + 120 * n ** 2
+def kernel_apply_full(n, advection=False):
+    vol = 24 * n ** 4 + 9 * n ** 3 if advection else 16 * n ** 4
+    return vol + 84 * n ** 3 + 120 * n ** 2
 
 
-def kernel_apply_block(n):
-    return 24 * n ** 4 + 9 * n ** 3 + 72 * n ** 3 + 100 * n ** 2
+def kernel_apply_block(n, advection=False):
+    if advection:
+        return 24 * n ** 4 + 9 * n ** 3 + 72 * n ** 3 + 100 * n ** 2
+    return 16 * n ** 4
+
+
+def kernel_smoother(n, ncell, sweeps, zero_sweeps, inner_its_total):
+    """Flops the b = 0 inner-PCG smoother kernels issue over `sweeps` launches:
+    a full apply per defect, a Kronecker block apply plus the vector work per
+    inner iteration."""
+    return (kernel_apply_full(n) * ncell * (sweeps - zero_sweeps)
+            + (kernel_apply_block(n) + 13 * n ** 3) * inner_its_total)
 
 
 def hbm_bytes_apply(n, ncell, word=8):
