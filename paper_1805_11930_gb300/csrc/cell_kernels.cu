@@ -366,6 +366,70 @@ __device__ __forceinline__ void block_matrices(const MeshParams& mp, T* Am, cons
   __syncwarp();
 }
 
+// Element-per-lane variant of the contractions for FP64 and double-float:
+// lane work items are the outputs (cell, line, i) instead of whole lines, so
+// that all 32 lanes stay busy when n^2 lines per cell do not fill the warp
+// (n = 5: 25 lines -> 78 % of the lanes, 125 outputs -> 98 %).  Each output
+// reads its line (n shared-memory loads) and a row of A from shared memory;
+// that costs more load instructions than the line form, which the FP64 pipe
+// can afford (it is the bound) but the FP32 kernels cannot (they are bound by
+// shared-memory instructions), so FP32 keeps the line form.
+constexpr int kLinePasses = (LINES + 31) / 32;
+constexpr int kElemPasses = (VEC + 31) / 32;
+// use the element form where it fills the lanes markedly better
+constexpr bool kElemForm = kElemPasses * LINES * 20 < kLinePasses * VEC * 19;
+
+template <int D, bool ACC, typename T>
+__device__ __forceinline__ void contract_e(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ Am,
+                                           int cstride, int lane, const unsigned char* act) {
+  constexpr int st = D == 0 ? 1 : (D == 1 ? N : N2);
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    if (!act[cw]) continue;
+    const int r = e - cw * N3;
+    const int i = D == 0 ? r % N : (D == 1 ? (r / N) % N : r / N2);
+    const int base = e - i * st;
+    const T* A = Am + cw * cstride + i * N;
+    T s;
+    if constexpr (std::is_same<T, df>::value) {
+      df_acc acc;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.add_prod(A[j], in[base + j * st]);
+      s = acc.value();
+    } else {
+      s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(A[j], in[base + j * st], s);
+    }
+    if (ACC)
+      out[e] += s;
+    else
+      out[e] = s;
+  }
+}
+
+// block_kron with element work items; M1s: the 1D mass matrix in shared memory.
+template <typename T>
+__device__ __forceinline__ void block_kron_e(const T* X, T* Y, T* S0, T* S1, const T* Am, const T* M1s, int lane,
+                                             const unsigned char* act) {
+  contract_e<2, false>(X, S0, M1s, 0, lane, act);               // a = M_z u
+  __syncwarp();
+  contract_e<1, false>(S0, S1, M1s, 0, lane, act);              // b = M_y a
+  __syncwarp();
+  contract_e<0, false>(S1, Y, Am, 3 * N2, lane, act);           // Y = A_x b
+  __syncwarp();
+  contract_e<0, false>(S0, S1, M1s, 0, lane, act);              // c = M_x a
+  __syncwarp();
+  contract_e<1, true>(S1, Y, Am + N2, 3 * N2, lane, act);       // Y += A_y c
+  __syncwarp();
+  contract_e<0, false>(X, S0, M1s, 0, lane, act);               // e = M_x u
+  __syncwarp();
+  contract_e<1, false>(S0, S1, M1s, 0, lane, act);              // f = M_y e
+  __syncwarp();
+  contract_e<2, true>(S1, Y, Am + 2 * N2, 3 * N2, lane, act);   // Y += A_z f
+  __syncwarp();
+}
+
 // Q = D_T P for b = 0 by the Kronecker form above: 8 contractions, no face
 // passes (the face terms are inside A_d).
 template <typename T>
@@ -845,7 +909,12 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   slot_cells(mp, color, s0, lane, cid);
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
-  if constexpr (!ADV) block_matrices(mp, vec[6], ci, act, lane);
+  T* M1s = vec[6] + 3 * CPW * N2;   // the mass matrix next to the per-cell matrices
+  if constexpr (!ADV) {
+    block_matrices(mp, vec[6], ci, act, lane);
+    for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
+    __syncwarp();
+  }
   // my cell slot (lanes without a line: -1)
   const int mycw = lane < LINES ? lane / N2 : -1;
   const bool mine = mycw >= 0 && act[mycw];
@@ -906,6 +975,8 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
     if constexpr (ADV) {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+    } else if constexpr (kElemForm && !std::is_same<T, float>::value) {
+      block_kron_e(P, Q, S0, S1, vec[6], M1s, lane, act);
     } else {
       block_kron(P, Q, S0, S1, vec[6], lane, act);
     }
@@ -1920,8 +1991,9 @@ __global__ void __launch_bounds__(256) k_prolong_add(MeshParams mp, const double
 }
 
 // ---------------------------------------------------------------- launchers
+// Synchronous copies: the staging struct lives on the host stack.
 template <typename T>
-cudaError_t upload_one(const double* h, cudaStream_t s) {
+cudaError_t upload_one(const double* h) {
   Tab<T> tb;
   const double* p = h;
   for (int i = 0; i < N; ++i)
@@ -1953,12 +2025,12 @@ cudaError_t upload_one(const double* h, cudaStream_t s) {
   return cudaMemcpyToSymbol(c_tab_f, &tb, sizeof(tb));
 }
 
-cudaError_t upload_tables(const double* h, cudaStream_t s) {
-  cudaError_t e = upload_one<double>(h, s);
+cudaError_t upload_tables(const double* h, cudaStream_t) {
+  cudaError_t e = upload_one<double>(h);
   if (e != cudaSuccess) return e;
-  e = upload_one<float>(h, s);
+  e = upload_one<float>(h);
   if (e != cudaSuccess) return e;
-  return upload_one<df>(h, s);
+  return upload_one<df>(h);
 }
 
 inline long long host_color_count(const MeshParams& mp, int color) {

@@ -960,3 +960,57 @@ def test_variable_solve_paper_setup():
     assert st["converged"]
     with pytest.raises(dgmg.DgmgError):
         ctx.apply(f.float(), torch.empty_like(f).float())
+
+
+# ------------------------------------------------------------- degenerate sizes and inputs
+@pytest.mark.parametrize("nc,p,bc,react", [((1, 1, 1), 1, [0] * 6, False), ((1, 1, 1), 8, [1] * 6, True),
+                                           ((1, 1, 7), 2, [0, 1, 1, 0, 0, 1], False), ((5, 1, 1), 3, [1, 0] * 3, True),
+                                           ((2, 7, 1), 5, [0] * 6, False)])
+def test_degenerate_meshes(nc, p, bc, react):
+    """One cell, slabs one cell thick, p = 1 and p = 8 (the smallest and
+    largest orders), pure Neumann with a reaction term: operator (FP64 1e-12),
+    exact block smoother against dense-LU block-Jacobi, and the Q1 transfer,
+    all on ragged warp tails."""
+    rng = np.random.default_rng(91)
+    ncell = int(np.prod(nc))
+    w = custom(nc, (0.7, 1.3, 0.9), p, bc, np.exp(rng.normal(size=(ncell, 3))),
+               c=rng.uniform(0.5, 2.0, ncell) if react else None)
+    P = oracle_problem(w)
+    A = P.assemble()
+    ctx = gpu_context(w)
+    u = inputs.random_dg_vector(P.ndof, seed=92)
+    v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(u), v)
+    assert rel_err(v.cpu().numpy(), A @ u) < 1e-12
+    f = inputs.random_dg_vector(P.ndof, seed=93)
+    ref = solvers.BlockJacobi(A, P.N, inner="lu")(f, u, 1, 0.8)
+    x = dev(u)
+    ctx.block_smooth(dev(f), x, nsweep=1, omega=0.8, eps=1e-14, maxit=20 * P.N)
+    assert rel_err(x.cpu().numpy(), ref) < 1e-9
+    Pm = transfer.prolongation(P)
+    rh = torch.empty(P.nvert, dtype=torch.float64, device="cuda")
+    ctx.restrict(dev(u), rh)
+    assert rel_err(rh.cpu().numpy(), Pm.T @ u) < 1e-13
+
+
+def test_zero_inputs():
+    """Zero in, zero out, exactly: the operator, a smoother sweep from u = 0
+    with f = 0 (no 0/0 in the per-cell normalisation), the V-cycle, and a
+    solve with f = 0 (converged at once, u stays 0)."""
+    from paper_1805_11930_gb300 import dgmg
+    w = make_case("p2_mixed")
+    ctx = gpu_context(w)
+    nd = ctx.sizes()["ndof"]
+    z = torch.zeros(nd, dtype=torch.float64, device="cuda")
+    v = torch.full_like(z, 7.0)
+    ctx.apply(z, v)
+    assert torch.count_nonzero(v) == 0
+    for inner in (dgmg.INNER_PCG, dgmg.INNER_GMRES, dgmg.INNER_DIRECT):
+        u = torch.zeros_like(z)
+        ctx.block_smooth(z, u, nsweep=2, omega=0.8, inner=inner)
+        assert torch.count_nonzero(u) == 0 and bool(torch.isfinite(u).all())
+    u = torch.zeros_like(z)
+    ctx.vcycle(z, u)
+    assert torch.count_nonzero(u) == 0
+    st = ctx.solve(z, u)
+    assert st["converged"] and st["iterations"] == 0 and torch.count_nonzero(u) == 0
