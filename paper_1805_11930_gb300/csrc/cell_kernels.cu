@@ -915,9 +915,24 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
     for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
     __syncwarp();
   }
-  // my cell slot (lanes without a line: -1)
-  const int mycw = lane < LINES ? lane / N2 : -1;
+  // The lane's cell slot and its elements for the per-cell vector work: with
+  // one cell per warp every lane takes elements lane, lane + 32, ... (all 32
+  // lanes busy); with several cells each lane owns one z-line of its cell
+  // (cell_sum groups lanes by cell).
+  const int mycw = CPW == 1 ? 0 : (lane < LINES ? lane / N2 : -1);
   const bool mine = mycw >= 0 && act[mycw];
+  const bool lead = CPW == 1 ? lane == 0 : (lane < LINES && lane % N2 == 0);
+  auto my_elems = [&](auto&& fn) {
+    if constexpr (CPW == 1) {
+      for (int e = lane; e < N3; e += 32) fn(e);
+    } else if (lane < LINES) {
+      int cw, base, st, a, b;
+      line_geom<2>(lane, cw, base, st, a, b);
+#pragma unroll
+      for (int i = 0; i < N; ++i) fn(base + i * N2);
+    }
+  };
+  const long long gb = mycw >= 0 ? cid[mycw] * N3 - mycw * N3 : 0;   // global index = gb + e
   // defect d = f - A u_old
   if (!zero) {
     for (int e = lane; e < VEC; e += 32) {
@@ -929,14 +944,8 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
     all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
   }
   T prr = T(0), prz = T(0);
-  for (int L = lane; L < LINES; L += 32) {
-    int cw, base, st, a, b;
-    line_geom<2>(L, cw, base, st, a, b);
-    if (!act[cw]) continue;
-    const long long gb = cid[cw] * N3 - cw * N3;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int e = base + i * N2;
+  if (mine)
+    my_elems([&](int e) {
       const T r = T(f[gb + e]) - (zero ? T(0) : Q[e]);
       const T z = r * T(diag[gb + e]);
       R[e] = r;
@@ -944,32 +953,26 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       DL[e] = T(0);
       prr = fma(r, r, prr);
       prz = fma(r, z, prz);
-    }
-  }
+    });
   const T rr0 = cell_sum(prr, lane, red);
   T rz = cell_sum(prz, lane, red);
   // The inner solve works on d / ||d|| (and scales the correction back):
   // FP32 products of a tiny defect would otherwise lose precision in the
-  // subnormal range.  The stopping test ||r|| <= eps ||d|| becomes ||r|| <= eps.
+  // subnormal range.  The stopping test ||r|| <= eps ||d|| becomes
+  // (r, r) <= eps^2, safe in every precision since (r_0, r_0) = 1.
   const T dnorm = sqrt(rr0);
   const T isc = rr0 > T(0) ? T(1) / dnorm : T(0);
-  for (int L = lane; L < LINES; L += 32) {
-    int cw, base, st, a, b;
-    line_geom<2>(L, cw, base, st, a, b);
-    if (!act[cw]) continue;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int e = base + i * N2;
+  if (mine)
+    my_elems([&](int e) {
       R[e] = R[e] * isc;
       P[e] = P[e] * isc;
-    }
-  }
+    });
   rz = rz * isc * isc;
-  const T thr = eps;
+  const T thr2 = eps * eps;
   bool live = mine && rr0 > T(0);
   int it = 0;
   while (__any_sync(FULLMASK, live && it < maxit)) {
-    if (lane < LINES) act[mycw] = (live && it < maxit) ? 1 : 0;
+    if (mycw >= 0) act[mycw] = (live && it < maxit) ? 1 : 0;
     __syncwarp();
     const bool run = live && it < maxit;
     if constexpr (ADV) {
@@ -981,86 +984,51 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       block_kron(P, Q, S0, S1, vec[6], lane, act);
     }
     T ppq = T(0);
-    if (run) {
-      for (int L = lane; L < LINES; L += 32) {
-        int cw, base, st, a, b;
-        line_geom<2>(L, cw, base, st, a, b);
-#pragma unroll
-        for (int i = 0; i < N; ++i) ppq = fma(P[base + i * N2], Q[base + i * N2], ppq);
-      }
-    }
+    if (run) my_elems([&](int e) { ppq = fma(P[e], Q[e], ppq); });
     const T pq = cell_sum(ppq, lane, red);
     bool upd = run && pq > T(0);
     if (run && !upd) live = false;   // breakdown: stop this cell
     T prr2 = T(0);
     if (upd) {
       const T alpha = rz / pq;
-      for (int L = lane; L < LINES; L += 32) {
-        int cw, base, st, a, b;
-        line_geom<2>(L, cw, base, st, a, b);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const int e = base + i * N2;
-          DL[e] = fma(alpha, P[e], DL[e]);
-          const T r = fma(-alpha, Q[e], R[e]);
-          R[e] = r;
-          prr2 = fma(r, r, prr2);
-        }
-      }
+      my_elems([&](int e) {
+        DL[e] = fma(alpha, P[e], DL[e]);
+        const T r = fma(-alpha, Q[e], R[e]);
+        R[e] = r;
+        prr2 = fma(r, r, prr2);
+      });
       ++it;
     }
     const T rr = cell_sum(prr2, lane, red);
-    if (upd && sqrt(rr) <= thr) {
+    if (upd && rr <= thr2) {
       live = false;
       upd = false;
     }
     if (upd && it >= maxit) upd = false;
     T prz2 = T(0);
-    if (upd) {
-      for (int L = lane; L < LINES; L += 32) {
-        int cw, base, st, a, b;
-        line_geom<2>(L, cw, base, st, a, b);
-        const long long gb = cid[cw] * N3 - cw * N3;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const int e = base + i * N2;
-          const T z = R[e] * T(diag[gb + e]);
-          S0[e] = z;
-          prz2 = fma(R[e], z, prz2);
-        }
-      }
-    }
+    if (upd)
+      my_elems([&](int e) {
+        const T z = R[e] * T(diag[gb + e]);
+        S0[e] = z;
+        prz2 = fma(R[e], z, prz2);
+      });
     const T rzn = cell_sum(prz2, lane, red);
     if (upd) {
       const T beta = rzn / rz;
       rz = rzn;
-      for (int L = lane; L < LINES; L += 32) {
-        int cw, base, st, a, b;
-        line_geom<2>(L, cw, base, st, a, b);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const int e = base + i * N2;
-          P[e] = fma(beta, P[e], S0[e]);
-        }
-      }
+      my_elems([&](int e) { P[e] = fma(beta, P[e], S0[e]); });
     }
     __syncwarp();
   }
   // u_new = u_old + omega delta (in place is allowed: a launch touches only its
   // own cells' values, and reads neighbours only of other colours)
-  for (int L = lane; L < LINES; L += 32) {
-    int cw, base, st, a, b;
-    line_geom<2>(L, cw, base, st, a, b);
-    if (cid[cw] < 0) continue;
-    const long long gb = cid[cw] * N3 - cw * N3;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const long long g = gb + base + i * N2;
-      const T dl = DL[base + i * N2] * dnorm;
+  if (mycw >= 0 && cid[mycw] >= 0)
+    my_elems([&](int e) {
+      const long long g = gb + e;
+      const T dl = DL[e] * dnorm;
       unew[g] = static_cast<G>(zero ? omega * dl : fma(omega, dl, T(uold[g])));
-    }
-  }
-  if (its && lane < LINES && (lane % N2) == 0 && cid[mycw] >= 0) its[cid[mycw]] = it;
+    });
+  if (its && lead && mycw >= 0 && cid[mycw] >= 0) its[cid[mycw]] = it;
 }
 
 // D_T of each cell column by column: column j is the block operator (volume
