@@ -301,6 +301,22 @@ def test_errors_are_reported():
                   torch.zeros(10, dtype=torch.float64, device="cuda"))   # no coefficients yet
     with pytest.raises(dgmg.DgmgError):
         ctx.set_coefficients(-np.ones(np.prod(w["nc"])))                  # K <= 0
+    ctx.set_mesh(1, 1, 1, 1, 1, 1, 2, [0] * 6)
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_coefficients(np.full(1, np.nan))                        # K not finite
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_mesh(16384, 16384, 16384, 1, 1, 1, 8, [0] * 6)          # 2^42 cells x 729 dofs: too large
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_mesh(0, 4, 4, 1, 1, 1, 2, [0] * 6)                     # empty mesh
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_mesh(2, 2, 2, 1, -1, 1, 2, [0] * 6)                    # negative length
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_coefficients(w["K"])
+    x = torch.zeros(ctx.sizes()["ndof"], dtype=torch.float64, device="cuda")
+    with pytest.raises(dgmg.DgmgError):
+        ctx.apply(x, x)                                                 # aliasing u and v
+    with pytest.raises(dgmg.DgmgError):
+        ctx.solve(x, torch.zeros_like(x), dgmg.default_opts(rtol=0.0))  # rtol must be > 0
 
 
 @pytest.mark.parametrize("name", ["p3_adv", "p4_full", "p6_adv"])
