@@ -818,21 +818,24 @@ __device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell
 // Shared-memory carve-up of one warp.
 template <typename T>
 struct WarpMem {
-  static __host__ __device__ constexpr size_t bytes(int nvec) {
-    return align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T)) + align16(CPW * sizeof(CellInfo<T>)) + 16 +
-           align16(CPW * sizeof(long long));
+  // nvec vectors of VEC values, face / reduction scratch, `extra` more values
+  static __host__ __device__ constexpr size_t bytes(int nvec, int extra = 0) {
+    return align16((size_t)(nvec * VEC + 5 * LINES + extra) * sizeof(T)) + align16(CPW * sizeof(CellInfo<T>)) +
+           16 + align16(CPW * sizeof(long long));
   }
 };
 
 template <typename T>
 __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T** F0, T** F1, T** red,
-                                      CellInfo<T>** ci, unsigned char** act, long long** cid = nullptr) {
+                                      CellInfo<T>** ci, unsigned char** act, long long** cid = nullptr,
+                                      int extra = 0, T** xtra = nullptr) {
   T* p = reinterpret_cast<T*>(raw);
   for (int k = 0; k < nvec; ++k) vec[k] = p + k * VEC;
   *F0 = p + nvec * VEC;
   *F1 = *F0 + LINES;
   *red = *F1 + LINES;     // 3 * LINES spare (reductions)
-  unsigned char* tail = raw + align16((size_t)(nvec * VEC + 5 * LINES) * sizeof(T));
+  if (xtra) *xtra = *red + 3 * LINES;
+  unsigned char* tail = raw + align16((size_t)(nvec * VEC + 5 * LINES + extra) * sizeof(T));
   *ci = reinterpret_cast<CellInfo<T>*>(tail);
   *act = tail + align16(CPW * sizeof(CellInfo<T>));
   if (cid) *cid = reinterpret_cast<long long*>(*act + 16);
@@ -900,18 +903,20 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  constexpr int NV = ADV ? 6 : 8;   // b = 0: vec[6..7] hold the per-cell 1D matrices of D_T
-  T* vec[8];
-  carve(smem + warp * WarpMem<T>::bytes(NV), NV, vec, &F0, &F1, &red, &ci, &act, &cid);
+  // b = 0: an extra region holds the per-cell 1D matrices of D_T and the mass matrix
+  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2;
+  T* vec[6];
+  T* Am = nullptr;
+  carve(smem + warp * WarpMem<T>::bytes(6, XT), 6, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Am);
   T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3], *R = vec[4], *DL = vec[5];
   const bool react = mp.c != nullptr;
   const bool zero = uold == nullptr;   // first sweep from u = 0: no defect apply
   slot_cells(mp, color, s0, lane, cid);
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
-  T* M1s = vec[6] + 3 * CPW * N2;   // the mass matrix next to the per-cell matrices
+  T* M1s = Am + 3 * CPW * N2;   // the mass matrix next to the per-cell matrices
   if constexpr (!ADV) {
-    block_matrices(mp, vec[6], ci, act, lane);
+    block_matrices(mp, Am, ci, act, lane);
     for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
     __syncwarp();
   }
@@ -979,9 +984,9 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
     } else if constexpr (kElemForm && !std::is_same<T, float>::value) {
-      block_kron_e(P, Q, S0, S1, vec[6], M1s, lane, act);
+      block_kron_e(P, Q, S0, S1, Am, M1s, lane, act);
     } else {
-      block_kron(P, Q, S0, S1, vec[6], lane, act);
+      block_kron(P, Q, S0, S1, Am, lane, act);
     }
     T ppq = T(0);
     if (run) my_elems([&](int e) { ppq = fma(P[e], Q[e], ppq); });
@@ -2065,9 +2070,9 @@ cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool f
 template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int NV = ADV ? 6 : 8;
-  const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(NV));
-  const size_t sm = wpb * WarpMem<T>::bytes(NV);
+  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2;
+  const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6, XT));
+  const size_t sm = wpb * WarpMem<T>::bytes(6, XT);
   auto k = k_smooth_pcg<T, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
