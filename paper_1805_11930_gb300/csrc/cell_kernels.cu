@@ -340,7 +340,8 @@ __device__ __forceinline__ void contract_cell(const T* __restrict__ in, T* __res
 //         |F| [ -kap sg / h_d (e_e dl_s^T + dl_s e_e^T) + gamma e_e e_e^T ],
 // e = end node of side s, sg = +-1 its outward sign, kap = w K (K on
 // Dirichlet faces), plus c |J| M in A_z.  Written to Am (3 n^2 per cell).
-template <typename T>
+// FACES = false: the volume term alone (A_d = |J| K_d / h_d^2 S, c |J| M in A_z).
+template <bool FACES = true, typename T>
 __device__ __forceinline__ void block_matrices(const MeshParams& mp, T* Am, const CellInfo<T>* ci,
                                                const unsigned char* act, int lane) {
   const Tab<T>& t = tab<T>();
@@ -350,7 +351,7 @@ __device__ __forceinline__ void block_matrices(const MeshParams& mp, T* Am, cons
     T a = ci[cw].kd[d] * t.S1[i][j];
     if (d == 2) a = fma(ci[cw].cJ, t.M1[i][j], a);
     const T ih = Prec<T>::ih(mp, d);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < 2 && FACES; ++s) {
       const int f = 2 * d + s;
       if (ci[cw].kind[f] == 2) continue;
       const int e = s ? N - 1 : 0;
@@ -378,6 +379,11 @@ constexpr int kLinePasses = (LINES + 31) / 32;
 constexpr int kElemPasses = (VEC + 31) / 32;
 // use the element form where it fills the lanes markedly better
 constexpr bool kElemForm = kElemPasses * LINES * 20 < kLinePasses * VEC * 19;
+
+// The b = 0 volume term in element form as well (FP64 and double-float): the
+// same Kronecker sequence with the volume-only 1D matrices.
+template <typename T, bool ADV>
+__host__ __device__ constexpr bool volume_elem() { return !ADV && kElemForm && !std::is_same<T, float>::value; }
 
 template <int D, bool ACC, typename T>
 __device__ __forceinline__ void contract_e(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ Am,
@@ -852,14 +858,25 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
   T *F0, *F1, *red;
   CellInfo<T>* ci;
   unsigned char* act;
-  carve(smem + warp * WarpMem<T>::bytes(4), 4, vec, &F0, &F1, &red, &ci, &act);
+  constexpr bool VE = volume_elem<T, ADV>();
+  constexpr int XT = VE ? 3 * CPW * N2 + N2 : 0;   // volume 1D matrices and the mass matrix
+  T* Vm = nullptr;
+  carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Vm);
   T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
   stage_cells(mp, cell0, lane, ci, act);
   const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
   const G* ug = u + cell0 * N3;
   for (int e = lane; e < VEC; e += 32) X[e] = e < nval ? T(ug[e]) : T(0);
-  __syncwarp();
-  volume<ADV>(X, Y, S0, S1, lane, ci, act, react);
+  if constexpr (VE) {
+    T* M1s = Vm + 3 * CPW * N2;
+    block_matrices<false>(mp, Vm, ci, act, lane);
+    for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
+    __syncwarp();
+    block_kron_e(X, Y, S0, S1, Vm, M1s, lane, act);
+  } else {
+    __syncwarp();
+    volume<ADV>(X, Y, S0, S1, lane, ci, act, react);
+  }
   all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
   G* vg = v + cell0 * N3;
   for (int e = lane; e < nval; e += 32) vg[e] = static_cast<G>(Y[e]);
@@ -903,8 +920,10 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  // b = 0: an extra region holds the per-cell 1D matrices of D_T and the mass matrix
-  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2;
+  // b = 0: an extra region holds the per-cell 1D matrices of D_T, the mass
+  // matrix and (element form) the volume-only 1D matrices of the defect
+  constexpr bool VE = volume_elem<T, ADV>();
+  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2 + (VE ? 3 * CPW * N2 : 0);
   T* vec[6];
   T* Am = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(6, XT), 6, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Am);
@@ -915,8 +934,10 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
   T* M1s = Am + 3 * CPW * N2;   // the mass matrix next to the per-cell matrices
+  T* Vm = M1s + N2;
   if constexpr (!ADV) {
     block_matrices(mp, Am, ci, act, lane);
+    if constexpr (VE) block_matrices<false>(mp, Vm, ci, act, lane);
     for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
     __syncwarp();
   }
@@ -945,7 +966,10 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
     __syncwarp();
-    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+    if constexpr (VE)
+      block_kron_e(P, Q, S0, S1, Vm, M1s, lane, act);
+    else
+      volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
     all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
   }
   T prr = T(0), prz = T(0);
@@ -2037,8 +2061,9 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4));
-  const size_t sm = wpb * WarpMem<T>::bytes(4);
+  constexpr int XT = volume_elem<T, ADV>() ? 3 * CPW * N2 + N2 : 0;
+  const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
+  const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_apply<T, FULL, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
@@ -2070,7 +2095,7 @@ cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool f
 template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2;
+  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2 + (volume_elem<T, ADV>() ? 3 * CPW * N2 : 0);
   const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(6, XT);
   auto k = k_smooth_pcg<T, ADV>;
