@@ -741,6 +741,105 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
   __syncwarp();
 }
 
+// The diffusion and penalty terms of all six faces with element work items
+// (one cell per warp, FP64 and double-float, orders where the line layout
+// leaves lanes idle): the same quantities as faces_diffusion_dir, computed
+// for the three directions at once so that the items fill the warp —
+//   1. per (direction, face point, side): the face values qv = gamma [[u]]
+//      - kap (d_n u + d_n u_nb), qdv = -kap [[u]] (6 n^2 items);
+//   2. M along the first tangential axis of every field (12 n^2 items);
+//   3. M along the second tangential axis (12 n^2 items);
+//   4. per element: the face-layer values and the normal-derivative test
+//      functions of the three directions added to Y (n^3 items, no element
+//      touched by two lanes).
+// FS: 24 n^2 scratch values; M1s: the mass matrix in shared memory.
+template <typename T, typename G>
+__device__ void faces_diffusion_e(const T* X, T* Y, T* FS, const T* M1s, const G* __restrict__ gu,
+                                  const MeshParams& mp, int lane, const unsigned char* act,
+                                  const CellInfo<T>* ci) {
+  static_assert(CPW == 1 || sizeof(T) == 0, "element-form faces need one cell per warp");
+  if (!act[0]) return;
+  const Tab<T>& t = tab<T>();
+  T* Fq = FS;              // [3][4][N2]
+  T* Fr = FS + 12 * N2;    // [3][4][N2]
+  // 1. face values
+  for (int it = lane; it < 6 * N2; it += 32) {
+    const int d = it / (2 * N2), r = it - d * 2 * N2, S = r / N2, L = r - S * N2;
+    const int a = L % N, b = L / N;
+    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+    const int base = d == 0 ? N * a + N2 * b : (d == 1 ? a + N2 * b : a + N * b);
+    const int f = 2 * d + S;
+    const int kind = ci[0].kind[f];
+    T qv = T(0), qdv = T(0);
+    if (kind != 2) {
+      const T ih = Prec<T>::ih(mp, d);
+      const T sgn = S ? T(1) : T(-1);
+      T dn = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], X[base + j * st], dn);
+      dn *= sgn * ih;
+      const T xin = X[base + (S ? N - 1 : 0) * st];
+      T tout = T(0), dno = T(0);
+      if (kind == 0) {
+        const G* xo = gu + ci[0].nb[f] * N3 + base;
+        tout = T(xo[(S ? 0 : N - 1) * st]);
+#pragma unroll
+        for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], T(xo[j * st]), dno);
+        dno *= sgn * ih;
+      }
+      const T kap = ci[0].kap[f];
+      const T jmp = xin - tout;
+      qv = ci[0].gam[f] * jmp - kap * (dn + dno);
+      qdv = -kap * jmp;
+    }
+    Fq[(d * 4 + 2 * S) * N2 + L] = qv;
+    Fq[(d * 4 + 2 * S + 1) * N2 + L] = qdv;
+  }
+  __syncwarp();
+  // 2. M along the first tangential axis: Fr[L = a + N b] = sum_j M[a][j] Fq[j + N b]
+  for (int it = lane; it < 12 * N2; it += 32) {
+    const int df = it / N2, L = it - df * N2, a = L % N, b = L / N;
+    const T* src = Fq + df * N2 + N * b;
+    const T* m = M1s + a * N;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(m[j], src[j], acc);
+    Fr[it] = acc;
+  }
+  __syncwarp();
+  // 3. M along the second tangential axis: Fq[L] = sum_j M[b][j] Fr[a + N j]
+  for (int it = lane; it < 12 * N2; it += 32) {
+    const int df = it / N2, L = it - df * N2, a = L % N, b = L / N;
+    const T* src = Fr + df * N2 + a;
+    const T* m = M1s + b * N;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(m[j], src[j * N], acc);
+    Fq[it] = acc;
+  }
+  __syncwarp();
+  // 4. scatter: element (i0, i1, i2); for direction d its face point and its
+  // index along d
+  for (int e = lane; e < N3; e += 32) {
+    const int i0 = e % N, i1 = (e / N) % N, i2 = e / N2;
+    T y = Y[e];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int j = d == 0 ? i0 : (d == 1 ? i1 : i2);
+      const int L = d == 0 ? i1 + N * i2 : (d == 1 ? i0 + N * i2 : i0 + N * i1);
+      const T area = Prec<T>::area(mp, d), ih = Prec<T>::ih(mp, d);
+      const T* q = Fq + d * 4 * N2 + L;
+      const T d0 = -area * ih * q[N2];       // sgn = -1 on face 0
+      const T d1 = area * ih * q[3 * N2];
+      y = fma(t.dl[0][j], d0, fma(t.dl[1][j], d1, y));
+      if (j == 0) y = fma(area, q[0], y);
+      if (j == N - 1) y = fma(area, q[2 * N2], y);
+    }
+    Y[e] = y;
+  }
+  __syncwarp();
+}
+
 // F0 must be followed by 4 * LINES values of scratch (F0, F1 and the
 // reduction area are contiguous in every kernel's shared-memory carve).
 template <bool FULL, bool ADV, typename T, typename G>
@@ -859,7 +958,8 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
   CellInfo<T>* ci;
   unsigned char* act;
   constexpr bool VE = volume_elem<T, ADV>();
-  constexpr int XT = VE ? 3 * CPW * N2 + N2 : 0;   // volume 1D matrices and the mass matrix
+  // volume 1D matrices, the mass matrix and (full operator) the face scratch
+  constexpr int XT = VE ? 3 * CPW * N2 + N2 + (FULL ? 24 * N2 : 0) : 0;
   T* Vm = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Vm);
   T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
@@ -873,11 +973,15 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
     for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
     __syncwarp();
     block_kron_e(X, Y, S0, S1, Vm, M1s, lane, act);
+    if constexpr (FULL)
+      faces_diffusion_e(X, Y, M1s + N2, M1s, u, mp, lane, act, ci);
+    else
+      all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
   } else {
     __syncwarp();
     volume<ADV>(X, Y, S0, S1, lane, ci, act, react);
+    all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
   }
-  all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
   G* vg = v + cell0 * N3;
   for (int e = lane; e < nval; e += 32) vg[e] = static_cast<G>(Y[e]);
 }
@@ -966,11 +1070,16 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
     __syncwarp();
-    if constexpr (VE)
+    if constexpr (VE) {
       block_kron_e(P, Q, S0, S1, Vm, M1s, lane, act);
-    else
+      // face scratch: S0, S1, R, DL and the face / reduction area are free
+      // here and contiguous (4 VEC + 5 LINES >= 24 n^2 for these orders)
+      static_assert(!VE || 4 * VEC + 5 * LINES >= 24 * N2, "face scratch");
+      faces_diffusion_e(P, Q, S0, M1s, uold, mp, lane, act, ci);
+    } else {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
-    all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+      all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+    }
   }
   T prr = T(0), prz = T(0);
   if (mine)
@@ -2061,7 +2170,7 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = volume_elem<T, ADV>() ? 3 * CPW * N2 + N2 : 0;
+  constexpr int XT = volume_elem<T, ADV>() ? 3 * CPW * N2 + N2 + (FULL ? 24 * N2 : 0) : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_apply<T, FULL, ADV>;
