@@ -742,8 +742,8 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
 }
 
 // The diffusion and penalty terms of all six faces with element work items
-// (one cell per warp, FP64 and double-float, orders where the line layout
-// leaves lanes idle): the same quantities as faces_diffusion_dir, computed
+// (one cell per warp, FP64, orders where the line layout leaves lanes idle):
+// the same quantities as faces_diffusion_dir, computed
 // for the three directions at once so that the items fill the warp —
 //   1. per (direction, face point, side): the face values qv = gamma [[u]]
 //      - kap (d_n u + d_n u_nb), qdv = -kap [[u]] (6 n^2 items);
@@ -959,7 +959,8 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
   unsigned char* act;
   constexpr bool VE = volume_elem<T, ADV>();
   // volume 1D matrices, the mass matrix and (full operator) the face scratch
-  constexpr int XT = VE ? 3 * CPW * N2 + N2 + (FULL ? 24 * N2 : 0) : 0;
+  constexpr bool FE = VE && FULL && std::is_same<T, double>::value;   // element-form faces
+  constexpr int XT = VE ? 3 * CPW * N2 + N2 + (FE ? 24 * N2 : 0) : 0;
   T* Vm = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Vm);
   T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
@@ -973,7 +974,7 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
     for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
     __syncwarp();
     block_kron_e(X, Y, S0, S1, Vm, M1s, lane, act);
-    if constexpr (FULL)
+    if constexpr (FE)
       faces_diffusion_e(X, Y, M1s + N2, M1s, u, mp, lane, act, ci);
     else
       all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
@@ -1075,7 +1076,10 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       // face scratch: S0, S1, R, DL and the face / reduction area are free
       // here and contiguous (4 VEC + 5 LINES >= 24 n^2 for these orders)
       static_assert(!VE || 4 * VEC + 5 * LINES >= 24 * N2, "face scratch");
-      faces_diffusion_e(P, Q, S0, M1s, uold, mp, lane, act, ci);
+      if constexpr (std::is_same<T, double>::value)
+        faces_diffusion_e(P, Q, S0, M1s, uold, mp, lane, act, ci);
+      else   // double-float: the line form is faster (measured)
+        all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
     } else {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
@@ -2170,7 +2174,9 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = volume_elem<T, ADV>() ? 3 * CPW * N2 + N2 + (FULL ? 24 * N2 : 0) : 0;
+  constexpr int XT = volume_elem<T, ADV>()
+                        ? 3 * CPW * N2 + N2 + (FULL && std::is_same<T, double>::value ? 24 * N2 : 0)
+                        : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_apply<T, FULL, ADV>;
