@@ -44,7 +44,7 @@ CPU_SAMPLE = dict(n=6, p=4)        # oracle sample: same workload family, 6^3 ce
 # (a sweep with defect, 2 warps per block; the block shape does not change the
 # DRAM traffic of this L2-resident working set); None while that capture
 # predates the kernel.
-SMOOTHER_TRAFFIC_BYTES = 103.349504e6 + 13.884416e6
+SMOOTHER_TRAFFIC_BYTES = None
 
 
 def fp64_peak_tflops():
