@@ -40,6 +40,7 @@ SEED = 1805
 class Request:
     def __init__(self, rid, arrival, n, p, sigma, seed):
         self.rid, self.arrival, self.n, self.p, self.sigma, self.seed = rid, arrival, n, p, sigma, seed
+        self.ndof = n ** 3 * (p + 1) ** 3
         self.t_admit = self.t_start = self.t_done = None
         self.stats = None
         self.solution = None
@@ -121,12 +122,19 @@ class DeviceRunner:
 class SolveServer:
     """Continuous batching over `slots` persistent workers with an HBM budget
     (bytes).  The runner is called on the worker's own thread, so per-worker
-    state (stream, context) lives as long as the server."""
+    state (stream, context) lives as long as the server.
 
-    def __init__(self, runner, slots=4, hbm_budget=None):
+    exclusive_dofs: requests with at least this many dofs run alone (they are
+    admitted once nothing else runs, and nothing is admitted beside them): a
+    solve that large fills the GPU by itself, and sharing the SMs and L2 with
+    others only slows everyone down; smaller requests share the slots."""
+
+    def __init__(self, runner, slots=4, hbm_budget=None, exclusive_dofs=None):
         self.runner = runner
         self.slots = slots
         self.budget = hbm_budget
+        self.exclusive_dofs = exclusive_dofs
+        self._exclusive_running = False
         self._lock = threading.Condition()
         self._jobs = queue.Queue()
         self._used = 0
@@ -152,7 +160,12 @@ class SolveServer:
             with self._lock:
                 self._used -= req.footprint
                 self._idle += 1
+                if self._is_exclusive(req):
+                    self._exclusive_running = False
                 self._lock.notify_all()
+
+    def _is_exclusive(self, req):
+        return self.exclusive_dofs is not None and req.ndof >= self.exclusive_dofs
 
     def run(self, trace):
         """Serve the trace; returns when every request has completed."""
@@ -166,13 +179,16 @@ class SolveServer:
                     self._lock.wait(timeout=head.arrival - now)
                     continue
                 fits = self.budget is None or self._used + head.footprint <= self.budget or self._used == 0
-                if self._idle == 0 or not fits:
+                alone_ok = not self._is_exclusive(head) or self._idle == self.slots
+                if self._idle == 0 or not fits or self._exclusive_running or not alone_ok:
                     self._lock.wait(timeout=0.05)
                     continue
                 pending.popleft()
                 head.t_admit = now
                 self._idle -= 1
                 self._used += head.footprint
+                if self._is_exclusive(head):
+                    self._exclusive_running = True
                 self.max_concurrent = max(self.max_concurrent, self.slots - self._idle)
                 self.max_used = max(self.max_used, self._used)
                 self._jobs.put(head)
@@ -211,6 +227,8 @@ def main():
     ap.add_argument("--capacity-requests", type=int, default=16)
     ap.add_argument("--nmax", type=int, default=48)
     ap.add_argument("--budget-gb", type=float, default=200.0)
+    ap.add_argument("--exclusive-mdofs", type=float, default=0.0,
+                    help="requests with at least this many million dofs run alone (0: off)")
     args = ap.parse_args()
     runner = DeviceRunner()
     budget = args.budget_gb * 1e9
@@ -232,13 +250,15 @@ def main():
                       "fp64_single_stream": summarize(fp64_trace)}), flush=True)
     for mult in [float(x) for x in args.rates.split(",")]:
         trace = make_trace(args.requests, mult * capacity, seed=SEED, **rng_kw)
-        srv = SolveServer(runner, slots=args.slots, hbm_budget=budget)
+        excl = args.exclusive_mdofs * 1e6 if args.exclusive_mdofs > 0 else None
+        srv = SolveServer(runner, slots=args.slots, hbm_budget=budget, exclusive_dofs=excl)
         srv.run(make_trace(args.slots, None, seed=SEED + 9, n_range=(8, 12)))    # warm the workers
         srv.max_concurrent = srv.max_used = 0
         srv.run(trace)
         srv.close()
         out = summarize(trace)
         out.update({"rate_multiplier": mult, "rate_req_per_s": round(mult * capacity, 4), "slots": args.slots,
+                    "exclusive_mdofs": args.exclusive_mdofs,
                     "max_concurrent": srv.max_concurrent, "max_hbm_gb": round(srv.max_used / 1e9, 3)})
         print(json.dumps(out), flush=True)
 

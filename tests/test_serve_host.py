@@ -79,3 +79,40 @@ def test_failed_requests_are_reported_and_release_their_slot():
     assert s["errors"] == 2 and s["completed"] == 8
     assert [r.rid for r in trace if r.error] == [2, 7] and all("DGMG_ERR_OOM" in trace[i].error for i in (2, 7))
     assert srv._used == 0 and srv._idle == 2      # the failed requests gave back slot and memory
+
+
+class TrackingRunner(FakeRunner):
+    """Records, for every request, how many requests were running with it."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.seen = {}
+
+    def __call__(self, req):
+        with self.lock:
+            self.running += 1
+            self.peak = max(self.peak, self.running)
+            self.order.append(req.rid)
+            self.seen[req.rid] = max(self.seen.get(req.rid, 0), self.running)
+        time.sleep(self.service)
+        with self.lock:
+            self.seen[req.rid] = max(self.seen[req.rid], self.running)
+            self.running -= 1
+        return {"converged": 1, "rel_residual": 1e-9}, None
+
+
+def test_exclusive_requests_run_alone_in_fifo_order():
+    """exclusive_dofs: a request that large runs with nothing beside it, the
+    smaller ones share the slots, and the arrival order is kept."""
+    trace = serve.make_trace(24, None, n_range=(8, 40), p_range=(2, 6), seed=5)
+    limit = sorted(r.ndof for r in trace)[16]          # about a third of the requests are large
+    r = TrackingRunner(service=0.01)
+    srv = serve.SolveServer(r, slots=4, exclusive_dofs=limit)
+    srv.run(trace)
+    srv.close()
+    large = [q for q in trace if q.ndof >= limit]
+    assert large and all(r.seen[q.rid] == 1 for q in large)
+    assert r.peak > 1                                   # the small ones did share
+    adm = [q.t_admit for q in sorted(trace, key=lambda q: q.rid)]
+    assert adm == sorted(adm)                           # FIFO admission
+    assert serve.summarize(trace)["completed"] == 24
