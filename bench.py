@@ -226,8 +226,10 @@ def run_dgmg(args, rank, world, local_rank):
                 "flops_note": "algorithmic: (32 n^4 + 120 n^3) per cell per apply, one apply per defect and per "
                               "inner iteration",
                 "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x sm_max_mhz (derived, nominal 1.25 TFLOP/s)",
-                "time_share": {"smoother": round(sm_ms / total_ms, 3) if world == 1 else None,
-                               "apply": round(ap_ms / total_ms, 3) if world == 1 else None}}
+                "time_share": {k: (round(sum(x[key] for x in stats) / total_ms, 3) if world == 1 else None)
+                               for k, key in (("smoother", "ms_smooth"), ("apply", "ms_apply"),
+                                              ("transfer", "ms_transfer"), ("coarse", "ms_coarse"),
+                                              ("krylov", "ms_krylov"))}}
 
     # apply throughput, FP64 and FP32 (separate timed loop, inputs resident)
     def time_apply(dtype, reps=20, df64=False):
@@ -319,7 +321,8 @@ def run_dgmg(args, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
         "solve": {"iterations": last["iterations"], "rel_residual": last["rel_residual"],
-                  "inner_mean": round(last["inner_mean"], 3), "inner_max": last["inner_max"],
+                  "inner_mean": round(last["inner_mean"], 3), "inner_std": round(last["inner_std"], 3),
+                  "inner_max": last["inner_max"],
                   "solve_s_fp64": round(total_ms / args.steps / 1e3, 5),
                   "solve_s_mixed": round(mixed_ms / 1e3, 5),
                   "mixed_iterations": mst["iterations"], "mixed_rel_residual": mst["rel_residual"],

@@ -104,7 +104,7 @@ typedef struct {
                        /* GMRES_TRIDIAG (convection-dominated) or DIRECT          */
   int inner_restart;   /* inner GMRES restart (default 12)                         */
   int coarse;          /* dgmg_coarse: Q1 + AMG correction, none, or P0 + AMG     */
-  int timing;          /* 1: time smoother and operator launches with CUDA events */
+  int timing;          /* 1: time the solve's components with CUDA events (stats) */
   int coarse_cycles;   /* AMG V-cycles per coarse correction, iterated on the     */
                        /* coarse residual (default 1)                             */
   int smoother;        /* dgmg_smoother: block-Jacobi (Algorithm 2, default) or   */
@@ -136,6 +136,16 @@ typedef struct {
   double ms_apply;      /* device time of the operator launches (opts->timing)    */
   double energy_estimate; /* last relative energy-norm estimate (stop = ENERGY)   */
   int iterations_run;   /* outer iterations performed (iterations + d for ENERGY)  */
+  /* Device time by component with opts->timing (CUDA events on the context's */
+  /* stream; the V-cycle then runs eagerly, not from a graph):               */
+  double ms_transfer;   /* restrictions to and prolongations from the coarse space */
+  double ms_coarse;     /* coarse corrections (AMG cycles, or the direct solve)  */
+  double ms_krylov;     /* the rest of the solve: outer Krylov vector updates,    */
+                        /* dot products, precision conversions, counters        */
+  double ms_device;     /* the whole solve, first to last kernel                  */
+  double inner_std;     /* standard deviation of the inner iteration counts over  */
+                        /* all cells and sweeps (with inner_mean, inner_max: the  */
+                        /* statistics reported with the inner solves, Sec. 4.2)  */
 } dgmg_solve_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -152,6 +162,15 @@ const char* dgmg_last_error(const dgmg_ctx* ctx);
  * workspace of an earlier mesh. */
 dgmg_status dgmg_set_mesh(dgmg_ctx* ctx, int nx, int ny, int nz, double lx, double ly,
                           double lz, int p, const int bc[6]);
+
+/* Penalty parameter alpha of gamma_F = alpha p (p+2) <delta-,delta+> / h on
+ * interior faces and alpha p (p+2) delta / h on Dirichlet faces (Sec. 2.1;
+ * default 1.25, the paper's value).  The context keeps it across meshes; it
+ * enters the operator, diag(D_T), the coarse matrices and the right-hand side
+ * built by the next dgmg_set_coefficients / dgmg_set_variable_coefficients.
+ * alpha finite and > 0, else DGMG_ERR_ARG; DGMG_ERR_STATE once the current
+ * mesh has coefficients (set the penalty before them). */
+dgmg_status dgmg_set_penalty(dgmg_ctx* ctx, double alpha);
 
 /* Coefficients, piecewise constant per cell except b (Sec. 2, eq.
  * linearproblem; Sec. 4.2 evaluates K and c at cell centres in the
@@ -274,7 +293,10 @@ dgmg_status dgmg_vcycle(dgmg_ctx* ctx, const double* f, double* u, const dgmg_so
  * right-preconditioned flexible GMRES(restart), preconditioned by one V-cycle
  * (Sec. 4.2, 4.3).  Outer vectors, dot products and the final residual check
  * are FP64.  f: device FP64; u: device FP64, initial guess in, solution out.
- * stats: host or NULL.  Synchronises the stream. */
+ * stats: host or NULL.  Synchronises the stream.  A non-finite initial
+ * residual (NaN or Inf in f or u) returns DGMG_ERR_ARG before the first
+ * iteration, u unchanged; NOT_CONVERGED and BREAKDOWN leave the last iterate
+ * in u.  The context stays usable after any of these. */
 dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts,
                        dgmg_solve_stats* stats);
 

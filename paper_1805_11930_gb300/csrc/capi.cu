@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dgmg.h"
 #include "dgmg_internal.h"
 #include "setup_host.h"
@@ -44,27 +46,33 @@ const CellOps* cell_ops(int n) {
 namespace {
 // Adds the per-cell inner iteration counts of one sweep to a running sum and
 // maximum (integer atomics once per block; the result is order independent).
+// sum[0] += sum of its, sum[1] += sum of its^2, *mx = max(*mx, its).
 __global__ void k_its_acc(long long n, const int* __restrict__ its, unsigned long long* sum, int* mx) {
-  __shared__ unsigned long long ssum[256];
+  __shared__ unsigned long long ssum[256], ssq[256];
   __shared__ int smax[256];
-  unsigned long long s = 0;
+  unsigned long long s = 0, q = 0;
   int m = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    s += (unsigned long long)its[i];
+    const unsigned long long v = (unsigned long long)its[i];
+    s += v;
+    q += v * v;
     m = its[i] > m ? its[i] : m;
   }
   ssum[threadIdx.x] = s;
+  ssq[threadIdx.x] = q;
   smax[threadIdx.x] = m;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
       ssum[threadIdx.x] += ssum[threadIdx.x + o];
+      ssq[threadIdx.x] += ssq[threadIdx.x + o];
       smax[threadIdx.x] = smax[threadIdx.x] > smax[threadIdx.x + o] ? smax[threadIdx.x] : smax[threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     atomicAdd(sum, ssum[0]);
+    atomicAdd(sum + 1, ssq[0]);
     atomicMax(mx, smax[0]);
   }
 }
@@ -104,6 +112,7 @@ struct dgmg_ctx {
   bool has_mesh = false, has_coef = false;
   int nx = 0, ny = 0, nz = 0, p = 0, n = 0;
   double L[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  double alpha = 1.25;           // interior penalty parameter
   int bc[6] = {0, 0, 0, 0, 0, 0};
   long long ncell = 0, ndof = 0, nvert = 0;
   const CellOps* ops = nullptr;
@@ -121,7 +130,7 @@ struct dgmg_ctx {
   float* w32[4] = {nullptr, nullptr, nullptr, nullptr};
   double* corners = nullptr;
   int* its = nullptr;
-  unsigned long long* itsum = nullptr;
+  unsigned long long* itsum = nullptr;   // [sum of inner iterations, sum of their squares]
   int* itmax = nullptr;
   Hier q1h;   // Q1 coarse space (built with the coefficients)
   Hier p0h;   // P0 coarse space (built on first use)
@@ -137,9 +146,9 @@ struct dgmg_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
-  std::vector<std::pair<size_t, size_t>> ev_smooth, ev_apply;
+  std::vector<std::pair<size_t, size_t>> ev_smooth, ev_apply, ev_transfer, ev_coarse;
   long long n_apply = 0, n_sweep = 0, n_zero_sweep = 0;
-  // Captured preconditioner graphs, keyed by (input, output, options).
+  // Captured preconditioner graphs, keyed by (input, output, V-cycle options).
   struct PrecGraph {
     const double* in;
     double* out;
@@ -166,6 +175,16 @@ struct dgmg_ctx {
 };
 
 namespace {
+
+// NVTX range around a host-side phase (solve, V-cycle, smoother, operator,
+// coarse correction, set-up), so that a profiler can select or attribute
+// the kernels of each; costs a function call when no tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 constexpr int kMaxDots = 72;
 
@@ -266,7 +285,7 @@ MeshParams params(const dgmg_ctx* ctx) {
   m.kdim = ctx->kdim;
   m.c = ctx->dc;
   m.bvert = ctx->db;
-  m.alpha = 1.25;
+  m.alpha = ctx->alpha;
   m.rec64 = ctx->rec64;
   m.rec32 = ctx->rec32;
   m.bvert32 = ctx->db32;
@@ -300,7 +319,7 @@ HostMesh host_mesh(const dgmg_ctx* ctx) {
   m.kdim = ctx->kdim;
   m.b = ctx->hb.empty() ? nullptr : ctx->hb.data();
   m.c = ctx->hc.empty() ? nullptr : ctx->hc.data();
-  m.alpha = 1.25;
+  m.alpha = ctx->alpha;
   m.var = ctx->var_on ? ctx->hvar.data() : nullptr;
   return m;
 }
@@ -348,6 +367,7 @@ dgmg_status multi_dot(dgmg_ctx* ctx, int k, double* const* xs, const double* y, 
 // pairs for FP64 smoothers or rounded to FP32 for FP32 smoothers, column
 // stride ld = n^3 rounded up to a multiple of 8.
 dgmg_status ensure_binv(dgmg_ctx* ctx, int prec) {
+  Range range("dgmg block inverse set-up");
   if (prec != DGMG_FP64 && prec != DGMG_FP32)
     return fail(ctx, DGMG_ERR_ARG, "stored block inverses are FP64 or FP32");
   if (ctx->p > 4) return fail(ctx, DGMG_ERR_ARG, "stored block inverses are built for p <= 4");
@@ -475,6 +495,7 @@ dgmg_status prepare_inner(dgmg_ctx* ctx, int inner, int prec) {
 // nsweep block-Jacobi sweeps on u (in place) with ping-pong through tmp.
 dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, int nsweep, double omega, double eps,
                             int maxit, int inner, int restart, int prec, bool zero_first, int* its) {
+  Range range("dgmg smoother");
   const bool fp32 = prec == DGMG_FP32;
   if (nsweep <= 0) {
     if (zero_first) {
@@ -536,6 +557,7 @@ dgmg_status smooth_internal(dgmg_ctx* ctx, const void* f, void* u, void* tmp, in
 // colours; symmetric = forward colours then backward colours (block-SSOR).
 dgmg_status sor_internal(dgmg_ctx* ctx, const void* f, void* u, int nsweep, double omega, double eps, int maxit,
                          int inner, int restart, int prec, bool zero_first, bool symmetric, int* its) {
+  Range range("dgmg smoother (SSOR)");
   const bool fp32 = prec == DGMG_FP32;
   if (zero_first) {
     if (fp32)
@@ -620,6 +642,7 @@ dgmg_status amg_cycle(dgmg_ctx* ctx, Hier& H, int l, const double* b, double* xo
 // H.uhat ~ A_hat^-1 H.rhat by `cycles` AMG V-cycles: the first from zero, each
 // further one on the current coarse residual (stationary iteration).
 dgmg_status coarse_correction(dgmg_ctx* ctx, Hier& H, int cycles) {
+  Range range("dgmg coarse AMG");
   CS(amg_cycle(ctx, H, 0, H.rhat, H.uhat));
   AmgLevel& L = H.lv[0];
   for (int k = 1; k < cycles && H.lv.size() > 1; ++k) {
@@ -710,6 +733,7 @@ dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec, bool ou
 // ------------------------------------------------------------------ V-cycle
 // One V-cycle of Algorithm 1 on FP64 f, u (u updated in place; zero: u == 0 on entry).
 dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o, bool zero) {
+  Range range("dgmg V-cycle");
   const int prec = o.smoother_prec;
   const bool fp32 = prec == DGMG_FP32;
   const MeshParams mp = params(ctx);
@@ -743,15 +767,21 @@ dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgm
         CK(vec_sub(n, (const double*)F, (const double*)T2, (double*)T2, ctx->stream));
       R = T2;
     }
+    size_t e0 = ctx->timing ? record_event(ctx) : 0;
     if (p0)
       CK(cell_sums(ctx->ncell, ctx->n * ctx->n * ctx->n, R, H.rhat, fp32, ctx->stream));
     else
       CS(restrict_internal(ctx, R, H.rhat, fp32));
+    if (ctx->timing) ctx->ev_transfer.push_back({e0, record_event(ctx)});
+    e0 = ctx->timing ? record_event(ctx) : 0;
     CS(coarse_correction(ctx, H, o.coarse_cycles));
+    if (ctx->timing) ctx->ev_coarse.push_back({e0, record_event(ctx)});
+    e0 = ctx->timing ? record_event(ctx) : 0;
     if (p0)
       CK(cell_add(ctx->ncell, ctx->n * ctx->n * ctx->n, H.uhat, U, fp32, ctx->stream));
     else
       CK(ctx->ops->prolong_add(mp, H.uhat, U, fp32, ctx->stream));
+    if (ctx->timing) ctx->ev_transfer.push_back({e0, record_event(ctx)});
     CS(vcycle_smooth(ctx, o, F, U, T1, o.npost, prec, false));
   } else {
     CS(vcycle_smooth(ctx, o, F, U, T1, o.npost, prec, u_zero));
@@ -761,6 +791,7 @@ dgmg_status vcycle_internal(dgmg_ctx* ctx, const double* f, double* u, const dgm
 }
 
 dgmg_status timed_apply(dgmg_ctx* ctx, const void* u, void* v, int prec, bool outer) {
+  Range range("dgmg operator");
   const MeshParams mp = params(ctx);
   const size_t e0 = ctx->timing ? record_event(ctx) : 0;
   if (outer && ctx->var_on)   // the operator with K(x), c(x); the preconditioner keeps cell values
@@ -794,14 +825,37 @@ dgmg_status precond_eager(dgmg_ctx* ctx, const double* r, double* z, const dgmg_
   return vcycle_internal(ctx, r, z, o, true);
 }
 
+// The options the V-cycle reads.  The outer solver's fields (tolerance,
+// iteration cap, Krylov method, stopping rule, operator precision, timing,
+// graph) do not change the captured work and stay zero, so solves that
+// differ only in those share a graph.
+dgmg_solve_opts precond_key(const dgmg_solve_opts& o) {
+  dgmg_solve_opts k;
+  std::memset(&k, 0, sizeof(k));
+  k.smoother_prec = o.smoother_prec;
+  k.omega = o.omega;
+  k.npre = o.npre;
+  k.npost = o.npost;
+  k.eps_inner = o.eps_inner;
+  k.maxit_inner = o.maxit_inner;
+  k.inner = o.inner;
+  k.inner_restart = o.inner_restart;
+  k.coarse = o.coarse;
+  k.coarse_cycles = o.coarse_cycles;
+  k.smoother = o.smoother;
+  return k;
+}
+
 // z = M r.  With opts.graph the V-cycle (no host synchronisation inside) is
-// captured into a CUDA graph on its second use with the same (r, z, opts) and
-// replayed afterwards, removing the per-kernel launch cost; the launch and
-// sweep counters of the captured work are added on each replay.
+// captured into a CUDA graph on its second use with the same (r, z) and
+// V-cycle options and replayed afterwards, removing the per-kernel launch
+// cost; the launch and sweep counters of the captured work are added on each
+// replay.
 dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_opts& o) {
   if (!o.graph || ctx->timing || !ctx->stream) return precond_eager(ctx, r, z, o);
+  const dgmg_solve_opts key = precond_key(o);
   for (auto& g : ctx->graphs) {
-    if (g.in == r && g.out == z && std::memcmp(&g.opts, &o, sizeof(o)) == 0) {
+    if (g.in == r && g.out == z && std::memcmp(&g.opts, &key, sizeof(key)) == 0) {
       if (!g.exec) {   // second use: capture
         const long long s0 = ctx->n_sweep, z0 = ctx->n_zero_sweep, a0 = ctx->n_apply, t0 = ctx->sweeps_tracked;
         const unsigned long long l0 = t_launches;
@@ -842,7 +896,7 @@ dgmg_status precond(dgmg_ctx* ctx, const double* r, double* z, const dgmg_solve_
     dgmg_ctx::PrecGraph g = {};
     g.in = r;
     g.out = z;
-    g.opts = o;
+    g.opts = key;
     g.exec = nullptr;
     ctx->graphs.push_back(g);
   }
@@ -869,6 +923,7 @@ dgmg_status solve_cg(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve
   CS(dot(ctx, r, r, rr));
   const double r0 = std::sqrt(rr);
   st.iterations = 0;
+  if (!std::isfinite(r0)) return fail(ctx, DGMG_ERR_ARG, "initial residual is not finite (NaN or Inf in f or u)");
   if (r0 == 0.0) {
     st.converged = 1;
     st.rel_residual = 0.0;
@@ -955,6 +1010,7 @@ dgmg_status solve_fgmres(dgmg_ctx* ctx, const double* f, double* u, const dgmg_s
   CS(dot(ctx, r, r, rr));
   const double r0 = std::sqrt(rr);
   st.iterations = 0;
+  if (!std::isfinite(r0)) return fail(ctx, DGMG_ERR_ARG, "initial residual is not finite (NaN or Inf in f or u)");
   if (r0 == 0.0) {
     st.converged = 1;
     st.rel_residual = 0.0;
@@ -1146,6 +1202,14 @@ dgmg_status dgmg_set_mesh(dgmg_ctx* ctx, int nx, int ny, int nz, double lx, doub
   return DGMG_OK;
 }
 
+dgmg_status dgmg_set_penalty(dgmg_ctx* ctx, double alpha) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(ctx, DGMG_ERR_ARG, "alpha must be finite and > 0");
+  if (ctx->has_coef) return fail(ctx, DGMG_ERR_STATE, "set the penalty before the coefficients");
+  ctx->alpha = alpha;
+  return DGMG_OK;
+}
+
 dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, const double* b_vertex,
                                   const double* c_cell) {
   if (!ctx) return DGMG_ERR_ARG;
@@ -1160,6 +1224,7 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   if (b_vertex)
     for (long long i = 0; i < 3 * ctx->nvert; ++i)
       if (!std::isfinite(b_vertex[i])) return fail(ctx, DGMG_ERR_ARG, "b must be finite");
+  Range range("dgmg set-up");
   CK(cudaSetDevice(ctx->device));
   if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
   free_mesh(ctx);
@@ -1190,7 +1255,7 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim, cons
   for (auto& w : ctx->w32) CS(dalloc(ctx, &w, n));
   CS(dalloc(ctx, &ctx->corners, 8 * ctx->ncell));
   CS(dalloc(ctx, &ctx->its, ctx->ncell));
-  CS(dalloc(ctx, &ctx->itsum, 1));
+  CS(dalloc(ctx, &ctx->itsum, 2));
   CS(dalloc(ctx, &ctx->itmax, 1));
   const MeshParams mp = params(ctx);
   CK(cell_records(mp, ctx->rec64, ctx->rec32, ctx->stream));
@@ -1384,6 +1449,7 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
     return fail(ctx, DGMG_ERR_ARG, "the energy-norm estimate needs CG or flexible CG and delay >= 1");
   CS(prepare_inner(ctx, o.inner, o.smoother_prec));
   if (o.coarse == DGMG_COARSE_P0) CS(ensure_p0(ctx));
+  Range range("dgmg solve");
   dgmg_solve_stats st;
   std::memset(&st, 0, sizeof(st));
   const auto t0 = std::chrono::steady_clock::now();
@@ -1393,14 +1459,18 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   ctx->ev_used = 0;
   ctx->ev_smooth.clear();
   ctx->ev_apply.clear();
+  ctx->ev_transfer.clear();
+  ctx->ev_coarse.clear();
   ctx->n_apply = ctx->n_sweep = ctx->n_zero_sweep = 0;
   const unsigned long long launches0 = t_launches;
+  const size_t ev_begin = ctx->timing ? record_event(ctx) : 0;
   if (ctx->track_its) {
-    CK(cudaMemsetAsync(ctx->itsum, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->itsum, 0, 2 * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->itmax, 0, sizeof(int), ctx->stream));
   }
   dgmg_status s = o.krylov == DGMG_KRYLOV_FGMRES ? solve_fgmres(ctx, f, u, o, st) : solve_cg(ctx, f, u, o, st);
   if (st.iterations_run == 0) st.iterations_run = st.iterations;
+  const size_t ev_end = ctx->timing ? record_event(ctx) : 0;
   ctx->track_its = false;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return fail(ctx, DGMG_ERR_CUDA, cudaGetErrorString(e));
@@ -1410,22 +1480,32 @@ dgmg_status dgmg_solve(dgmg_ctx* ctx, const double* f, double* u, const dgmg_sol
   st.zero_sweeps = ctx->n_zero_sweep;
   st.applies = ctx->n_apply;
   if (ctx->timing) {
-    float ms;
-    for (auto& pr : ctx->ev_smooth)
-      if (cudaEventElapsedTime(&ms, ctx->ev[pr.first], ctx->ev[pr.second]) == cudaSuccess) st.ms_smooth += ms;
-    for (auto& pr : ctx->ev_apply)
-      if (cudaEventElapsedTime(&ms, ctx->ev[pr.first], ctx->ev[pr.second]) == cudaSuccess) st.ms_apply += ms;
+    auto total = [ctx](const std::vector<std::pair<size_t, size_t>>& pairs) {
+      double t = 0.0;
+      float ms;
+      for (auto& pr : pairs)
+        if (cudaEventElapsedTime(&ms, ctx->ev[pr.first], ctx->ev[pr.second]) == cudaSuccess) t += ms;
+      return t;
+    };
+    st.ms_smooth = total(ctx->ev_smooth);
+    st.ms_apply = total(ctx->ev_apply);
+    st.ms_transfer = total(ctx->ev_transfer);
+    st.ms_coarse = total(ctx->ev_coarse);
+    st.ms_device = total({{ev_begin, ev_end}});
+    st.ms_krylov = std::max(0.0, st.ms_device - st.ms_smooth - st.ms_apply - st.ms_transfer - st.ms_coarse);
     ctx->timing = false;
   }
   if (stats) {
-    unsigned long long sum = 0;
+    unsigned long long sum[2] = {0, 0};
     int mx = 0;
-    cudaMemcpyAsync(&sum, ctx->itsum, sizeof(sum), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(sum, ctx->itsum, sizeof(sum), cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(&mx, ctx->itmax, sizeof(mx), cudaMemcpyDeviceToHost, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     const long long sw = ctx->sweeps_tracked;
-    st.inner_mean = sw > 0 ? (double)sum / ((double)ctx->ncell * sw) : 0.0;
-    st.inner_its_total = (long long)sum;
+    const double cnt = (double)ctx->ncell * (double)sw;
+    st.inner_mean = sw > 0 ? (double)sum[0] / cnt : 0.0;
+    st.inner_std = sw > 0 ? std::sqrt(std::max(0.0, (double)sum[1] / cnt - st.inner_mean * st.inner_mean)) : 0.0;
+    st.inner_its_total = (long long)sum[0];
     st.inner_max = mx;
     *stats = st;
   }

@@ -49,7 +49,9 @@ class SolveStats(ctypes.Structure):
                 ("zero_sweeps", ctypes.c_longlong),
                 ("applies", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
                 ("ms_smooth", ctypes.c_double), ("ms_apply", ctypes.c_double),
-                ("energy_estimate", ctypes.c_double), ("iterations_run", ctypes.c_int)]
+                ("energy_estimate", ctypes.c_double), ("iterations_run", ctypes.c_int),
+                ("ms_transfer", ctypes.c_double), ("ms_coarse", ctypes.c_double), ("ms_krylov", ctypes.c_double),
+                ("ms_device", ctypes.c_double), ("inner_std", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,6 +68,7 @@ _SIG = {
     "dgmg_destroy": (_I, [_P]),
     "dgmg_last_error": (ctypes.c_char_p, [_P]),
     "dgmg_set_mesh": (_I, [_P, _I, _I, _I, _D, _D, _D, _I, _P]),
+    "dgmg_set_penalty": (_I, [_P, _D]),
     "dgmg_set_coefficients": (_I, [_P, _P, _I, _P, _P]),
     "dgmg_sizes": (_I, [_P] + [ctypes.POINTER(_LL)] * 5),
     "dgmg_quadrature_points": (_I, [_P, _P, _P]),
@@ -198,6 +201,9 @@ class Context:
         bca = (ctypes.c_int * 6)(*[int(b) for b in bc])
         self._check(self.lib.dgmg_set_mesh(self.h, nx, ny, nz, lx, ly, lz, p, bca))
         self.mesh = (nx, ny, nz, lx, ly, lz, p, list(bc))
+
+    def set_penalty(self, alpha):
+        self._check(self.lib.dgmg_set_penalty(self.h, float(alpha)))
 
     def set_coefficients(self, K, b_vertex=None, c_cell=None):
         K = np.asarray(K, dtype=np.float64)

@@ -21,6 +21,16 @@ worker, mixed precision) and, on the same requests, the plain FP64 solve
 multiplier replays a seeded Poisson arrival trace at that multiple of the
 capacity and prints solves/s and p50 / p99 latency (arrival to completion) as
 one JSON line per rate.
+
+A request can be cancelled (`SolveServer.cancel`): if it has not been
+admitted it never runs; if it runs, the runner stops at its next checkpoint.
+A running request can be evicted (`SolveServer.evict`): the runner stops at
+its next checkpoint, hands back its iterate u and residual norm, and the
+request goes back to the head of the queue; when it is admitted again the
+solve restarts from that u (the outer Krylov space is rebuilt, the stopping
+test stays relative to the first residual).  A request whose runner fails
+with DGMG_ERR_OOM while others ran beside it is re-queued once and then
+runs alone.
 """
 import argparse
 import collections
@@ -37,6 +47,26 @@ from . import footprint
 SEED = 1805
 
 
+class Checkpoint:
+    """What a stopped solve hands back: its iterate u (host FP64), the FP64
+    residual norm ||f - A u||_2 and the outer iterations done so far."""
+
+    def __init__(self, u, res_abs, iterations):
+        self.u, self.res_abs, self.iterations = u, res_abs, iterations
+
+
+class Evicted(Exception):
+    """Raised by a runner that stopped a request on request of the server."""
+
+    def __init__(self, checkpoint):
+        super().__init__("evicted")
+        self.checkpoint = checkpoint
+
+
+class Cancelled(Exception):
+    """Raised by a runner that stopped a cancelled request."""
+
+
 class Request:
     def __init__(self, rid, arrival, n, p, sigma, seed):
         self.rid, self.arrival, self.n, self.p, self.sigma, self.seed = rid, arrival, n, p, sigma, seed
@@ -46,6 +76,13 @@ class Request:
         self.solution = None
         self.error = None
         self.footprint = footprint.library_bytes((n, n, n), p, krylov="fcg")
+        self.checkpoint = None          # set when the request was evicted
+        self.evictions = 0
+        self.retries = 0                # re-admissions after a failed allocation
+        self.alone = False              # admit only when nothing else runs
+        self.cancel_requested = False
+        self.evict_requested = False
+        self.cancelled = False
 
     @property
     def latency(self):
@@ -80,11 +117,20 @@ def request_inputs(req):
 
 
 class DeviceRunner:
-    """Runs one request on one worker: its own stream and context."""
+    """Runs one request on one worker: its own stream and context.
 
-    def __init__(self, device=0, keep_solutions=False, **opts):
+    chunk: outer iterations per library call; between calls the runner
+    checks the request's cancel and evict flags (None: one call, no
+    checkpoints).  Each call restarts the Krylov method from the current u
+    with its tolerance rescaled so that the stop stays ||r||_2 <= rtol ||f||_2
+    (u = 0 at the start)."""
+
+    def __init__(self, device=0, keep_solutions=False, chunk=None, rtol=1e-8, maxit=500, **opts):
         self.device = device
         self.keep = keep_solutions
+        self.chunk = chunk
+        self.rtol = rtol
+        self.maxit = maxit
         self.opts = dict(opts)
         self._local = threading.local()
 
@@ -110,13 +156,52 @@ class DeviceRunner:
             nd = ctx.sizes()["ndof"]
             f = torch.empty(nd, dtype=torch.float64, device=f"cuda:{self.device}")
             ctx.assemble_rhs(f_qp, f)
-            u = torch.zeros_like(f)
             kw = dict(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG, graph=1)
             kw.update(self.opts)
-            stats = ctx.solve(f, u, dgmg.default_opts(**kw), check=False)
+            if self.chunk is None and req.checkpoint is None:
+                u = torch.zeros_like(f)
+                stats = ctx.solve(f, u, dgmg.default_opts(rtol=self.rtol, maxit=self.maxit, **kw), check=False)
+            else:
+                u, stats = self._chunked(ctx, f, req, kw)
             sol = u.cpu().numpy() if self.keep else None
         stream.synchronize()
         return stats, sol
+
+    def on_chunk(self, req, iterations, rel_residual):
+        """Called on the worker's thread after each library call of a chunked
+        solve (progress reporting; a subclass may set the request's flags)."""
+
+    def _chunked(self, ctx, f, req, kw):
+        import torch
+        from . import dgmg
+        fnorm = float(torch.linalg.vector_norm(f))
+        target = self.rtol * fnorm
+        cp = req.checkpoint
+        if cp is None:
+            u, res, its = torch.zeros_like(f), fnorm, 0
+        else:
+            u, res, its = torch.as_tensor(cp.u, device=f.device).clone(), cp.res_abs, cp.iterations
+        stats = None
+        while True:
+            if res <= target or fnorm == 0.0:
+                break
+            if req.cancel_requested:
+                raise Cancelled()
+            if req.evict_requested:
+                raise Evicted(Checkpoint(u.cpu().numpy(), res, its))
+            step = min(self.chunk or self.maxit, self.maxit - its)
+            if step <= 0:
+                break
+            stats = ctx.solve(f, u, dgmg.default_opts(rtol=target / res, maxit=step, **kw), check=False)
+            its += stats["iterations"]
+            res *= stats["rel_residual"]
+            if stats["status"] not in ("DGMG_OK", "DGMG_ERR_NOT_CONVERGED"):
+                raise RuntimeError(f"request {req.rid}: {stats['status']}")
+            self.on_chunk(req, its, res / fnorm)
+        out = dict(stats or {"status": "DGMG_OK", "inner_mean": 0.0, "inner_max": 0})
+        out.update(iterations=its, rel_residual=res / fnorm if fnorm > 0 else 0.0,
+                   converged=int(res <= target * (1 + 1e-12)))
+        return u, out
 
 
 class SolveServer:
@@ -137,6 +222,8 @@ class SolveServer:
         self._exclusive_running = False
         self._lock = threading.Condition()
         self._jobs = queue.Queue()
+        self._pending = collections.deque()
+        self._requests = {}
         self._used = 0
         self._idle = slots
         self.max_concurrent = 0
@@ -151,30 +238,80 @@ class SolveServer:
             req = self._jobs.get()
             if req is None:
                 return
-            req.t_start = time.perf_counter() - self._clock0
+            if req.t_start is None:
+                req.t_start = time.perf_counter() - self._clock0
+            requeue = False
             try:
                 req.stats, req.solution = self.runner(req)
+            except Evicted as e:     # back to the head of the queue with its iterate
+                req.checkpoint = e.checkpoint
+                req.evictions += 1
+                requeue = True
+            except Cancelled:
+                req.cancelled = True
             except Exception as e:   # reported per request, the server keeps going
-                req.error = repr(e)
-            req.t_done = time.perf_counter() - self._clock0
+                if "DGMG_ERR_OOM" in str(e) and not req.alone and req.retries == 0:
+                    req.retries += 1  # others held memory: try once more, alone
+                    req.alone = True
+                    requeue = True
+                else:
+                    req.error = repr(e)
             with self._lock:
+                req.evict_requested = False
+                if not requeue:
+                    req.t_done = time.perf_counter() - self._clock0
                 self._used -= req.footprint
                 self._idle += 1
                 if self._is_exclusive(req):
                     self._exclusive_running = False
+                if requeue:
+                    self._pending.appendleft(req)
                 self._lock.notify_all()
 
     def _is_exclusive(self, req):
-        return self.exclusive_dofs is not None and req.ndof >= self.exclusive_dofs
+        return req.alone or (self.exclusive_dofs is not None and req.ndof >= self.exclusive_dofs)
+
+    def cancel(self, rid):
+        """Cancel request rid: dropped if it waits, stopped at its runner's
+        next checkpoint if it runs.  Returns False for an unknown or finished
+        request."""
+        with self._lock:
+            req = self._requests.get(rid)
+            if req is None or req.t_done is not None:
+                return False
+            req.cancel_requested = True
+            self._lock.notify_all()
+            return True
+
+    def evict(self, rid):
+        """Ask the runner of request rid to stop at its next checkpoint and
+        re-queue it at the head of the queue with its iterate.  Returns False
+        unless the request is running."""
+        with self._lock:
+            req = self._requests.get(rid)
+            if req is None or req.t_done is not None or req.t_admit is None or req in self._pending:
+                return False
+            req.evict_requested = True
+            return True
 
     def run(self, trace):
-        """Serve the trace; returns when every request has completed."""
-        pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
+        """Serve the trace; returns when every request has completed, failed
+        or been cancelled."""
         self._clock0 = time.perf_counter()
         with self._lock:
-            while pending:
+            self._pending = pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
+            self._requests = {r.rid: r for r in trace}
+            while pending or self._idle < self.slots:
+                if not pending:
+                    self._lock.wait(timeout=0.05)
+                    continue
                 head = pending[0]
                 now = time.perf_counter() - self._clock0
+                if head.cancel_requested:        # never admitted (again)
+                    pending.popleft()
+                    head.cancelled = True
+                    head.t_done = now
+                    continue
                 if head.arrival > now:
                     self._lock.wait(timeout=head.arrival - now)
                     continue
@@ -184,7 +321,8 @@ class SolveServer:
                     self._lock.wait(timeout=0.05)
                     continue
                 pending.popleft()
-                head.t_admit = now
+                if head.t_admit is None:
+                    head.t_admit = now
                 self._idle -= 1
                 self._used += head.footprint
                 if self._is_exclusive(head):
@@ -192,8 +330,6 @@ class SolveServer:
                 self.max_concurrent = max(self.max_concurrent, self.slots - self._idle)
                 self.max_used = max(self.max_used, self._used)
                 self._jobs.put(head)
-            while self._idle < self.slots:
-                self._lock.wait(timeout=0.05)
         return trace
 
     def close(self):
@@ -204,7 +340,7 @@ class SolveServer:
 
 
 def summarize(reqs):
-    done = [r for r in reqs if r.t_done is not None and r.error is None]
+    done = [r for r in reqs if r.t_done is not None and r.error is None and not r.cancelled]
     lat = sorted(r.latency for r in done)
     span = max(r.t_done for r in done) - min(r.arrival for r in reqs)
     conv = sum(1 for r in done if r.stats and r.stats["converged"])
@@ -213,7 +349,9 @@ def summarize(reqs):
         return lat[min(len(lat) - 1, int(np.ceil(q * len(lat))) - 1)]
 
     return {"requests": len(reqs), "completed": len(done), "converged": conv,
-            "errors": sum(1 for r in reqs if r.error), "solves_per_s": round(len(done) / span, 4),
+            "errors": sum(1 for r in reqs if r.error), "cancelled": sum(1 for r in reqs if r.cancelled),
+            "evictions": sum(r.evictions for r in reqs), "retries": sum(r.retries for r in reqs),
+            "solves_per_s": round(len(done) / span, 4),
             "p50_latency_s": round(pct(0.50), 4), "p99_latency_s": round(pct(0.99), 4),
             "mean_service_s": round(statistics.mean(r.t_done - r.t_start for r in done), 4),
             "makespan_s": round(span, 3)}

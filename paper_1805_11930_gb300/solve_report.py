@@ -109,7 +109,8 @@ def run(name, repeat):
         sols[tag] = u.clone()
         out[tag] = {"solve_s": round(statistics.median(ms) / 1e3, 4), "status": st["status"],
                     "iterations": st["iterations"], "rel_residual": st["rel_residual"],
-                    "inner_mean": round(st["inner_mean"], 2), "inner_max": st["inner_max"],
+                    "inner_mean": round(st["inner_mean"], 2), "inner_std": round(st["inner_std"], 2),
+                    "inner_max": st["inner_max"],
                     "us_per_dof": round(statistics.median(ms) * 1e3 / s["ndof"], 5)}
     for tag in [t for t in sols if t != "fp64"]:
         d = (sols[tag] - sols["fp64"]).norm() / sols["fp64"].norm()

@@ -1030,3 +1030,95 @@ def test_zero_inputs():
     assert torch.count_nonzero(u) == 0
     st = ctx.solve(z, u)
     assert st["converged"] and st["iterations"] == 0 and torch.count_nonzero(u) == 0
+
+
+def test_nan_rhs_is_reported_not_hung():
+    """A NaN in the right-hand side ends the solve with an error status
+    (Krylov breakdown: p^T A p is not > 0) instead of iterating to maxit, and
+    the context stays usable for the next, finite solve."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.poisson_sine(6, 2)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    bad = f.clone()
+    bad[17] = float("nan")
+    for kry in (dgmg.KRYLOV_CG, dgmg.KRYLOV_FCG, dgmg.KRYLOV_FGMRES):
+        u0 = torch.zeros_like(f)
+        st = ctx.solve(bad, u0, dgmg.default_opts(krylov=kry), check=False)
+        assert st["status"] == "DGMG_ERR_ARG" and st["iterations"] == 0
+        assert not bool(u0.any())
+    u = torch.zeros_like(f)
+    assert ctx.solve(f, u)["converged"] and bool(torch.isfinite(u).all())
+
+
+@pytest.mark.parametrize("coarse", ["AMG", "P0"])
+def test_component_timers_and_inner_statistics(coarse):
+    """With opts.timing the solve reports device time per component; the
+    components are disjoint parts of the solve, so they are non-negative and
+    add up to the whole (the rest, the Krylov work, is the remainder).  The
+    inner iteration statistics obey 0 <= std and std^2 <= (max - mean) mean
+    (Bhatia-Davis, the counts lying in [0, max])."""
+    from paper_1805_11930_gb300 import dgmg
+    w = inputs.lognormal(8, 3)
+    ctx = gpu_context(w)
+    f = gpu_rhs(ctx, w, torch)
+    u = torch.zeros_like(f)
+    st = ctx.solve(f, u, dgmg.default_opts(timing=1, coarse=getattr(dgmg, "COARSE_" + coarse)))
+    assert st["converged"]
+    parts = [st[k] for k in ("ms_smooth", "ms_apply", "ms_transfer", "ms_coarse", "ms_krylov")]
+    assert all(x > 0 for x in parts)
+    assert sum(parts) == pytest.approx(st["ms_device"], rel=1e-6)
+    assert st["ms_device"] <= st["ms_total"] * 1.01
+    m, s, mx = st["inner_mean"], st["inner_std"], st["inner_max"]
+    assert 0 < m <= mx and 0 <= s and s * s <= (mx - m) * m * (1 + 1e-12)
+    # without timing the component times stay zero and the statistics agree
+    u.zero_()
+    st2 = ctx.solve(f, u, dgmg.default_opts(coarse=getattr(dgmg, "COARSE_" + coarse)))
+    assert st2["ms_device"] == 0 and st2["ms_coarse"] == 0
+    assert st2["inner_std"] == pytest.approx(s, rel=1e-12) and st2["inner_mean"] == pytest.approx(m, rel=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [0.6, 4.0])
+def test_penalty_parameter(alpha):
+    """dgmg_set_penalty: with alpha other than 1.25 the operator, diag(D_T),
+    the Q1 and P0 coarse matrices and the right-hand side (Dirichlet penalty
+    term) all match the oracle built with the same alpha."""
+    from oracle import dg as odg
+    w = make_case("p2_mixed")
+    P = odg.Problem(*w["nc"], *w["L"], w["p"], w["bc"], w["K"], b_vertex=w["b"], c_cell=w["c"], alpha=alpha)
+    A = P.assemble()
+    from paper_1805_11930_gb300 import dgmg
+    ctx = dgmg.Context(0)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_penalty(alpha)
+    ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
+    u = inputs.random_dg_vector(P.ndof, seed=61)
+    v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.apply(dev(u), v)
+    assert rel_err(v.cpu().numpy(), A @ u) < 1e-12
+    d = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
+    ctx.block_diagonal(d)
+    assert rel_err(d.cpu().numpy(), A.diagonal()) < 1e-12
+    Pm = transfer.prolongation(P)
+    G = (Pm.T @ A @ Pm).toarray()
+    st = ctx.coarse_matrix()
+    Vx, Vy, Vz = P.nv
+    Ah = np.zeros_like(G)
+    for vtx in range(P.nvert):
+        ix, iy, iz = vtx % Vx, (vtx // Vx) % Vy, vtx // (Vx * Vy)
+        for k in range(27):
+            jx, jy, jz = ix + k % 3 - 1, iy + (k // 3) % 3 - 1, iz + k // 9 - 1
+            if 0 <= jx < Vx and 0 <= jy < Vy and 0 <= jz < Vz:
+                Ah[vtx, jx + Vx * (jy + Vy * jz)] = st[vtx, k]
+    assert np.abs(Ah - G).max() < 1e-12 * np.abs(G).max()
+    G0 = transfer.p0_matrix(A, P).toarray()
+    assert np.abs(_stencil_dense(ctx.coarse_matrix_p0(), P.nc) - G0).max() < 1e-12 * np.abs(G0).max()
+    rhs = gpu_rhs(ctx, w, torch)
+    assert rel_err(rhs.cpu().numpy(), oracle_rhs(P, w)) < 1e-13
+    # the penalty is fixed once the coefficients are set; the context keeps it for the next mesh
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_penalty(1.25)
+    ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
+    ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
+    ctx.apply(dev(u), v)
+    assert rel_err(v.cpu().numpy(), A @ u) < 1e-12

@@ -44,3 +44,34 @@ def test_create_fails_cleanly_without_device():
     h = ctypes.c_void_p()
     st = lib.dgmg_create(ctypes.byref(h), 10_000, None)
     assert st == 1 and not h.value
+
+
+def _header_struct(name):
+    """(type, field) pairs of `typedef struct {...} name;` in include/dgmg.h."""
+    import re
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "dgmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_ ]*?)\s+([A-Za-z_][A-Za-z0-9_]*(?:\s*,\s*[A-Za-z_][A-Za-z0-9_]*)*)\s*;",
+                         body):
+        out += [(" ".join(m.group(1).split()), n.strip()) for n in m.group(2).split(",")]
+    return out
+
+
+@pytest.mark.parametrize("cname, pyname", [("dgmg_solve_opts", "SolveOpts"), ("dgmg_solve_stats", "SolveStats")])
+def test_binding_structs_match_header(cname, pyname):
+    """The ctypes mirrors of the option and statistics structs list the
+    header's fields in the same order with the same C types."""
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong}
+    fields = getattr(dgmg, pyname)._fields_
+    decl = _header_struct(cname)
+    assert [n for n, _ in fields] == [n for _, n in decl]
+    for (n, t), (ct, _) in zip(fields, decl):
+        assert t is ctype[ct], n
+
+
+def test_null_context_is_an_argument_error():
+    lib = dgmg.load()
+    assert lib.dgmg_set_penalty(None, 2.0) == 1
+    assert lib.dgmg_destroy(None) == 1

@@ -288,3 +288,33 @@ def test_variable_tensor_manufactured_convergence():
         u = spla.spsolve(A, F)
         errs.append(P.l2_error(u, u_fn))
     assert errs[0] / errs[1] > 6.0, errs
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_penalty_parameter_enters_only_the_jump_term(p):
+    """a_h depends on alpha only through gamma_F [[u]][[v]], which is linear in
+    alpha: A(alpha) = A_0 + alpha J with J symmetric positive semi-definite,
+    J u = 0 for every continuous u that vanishes on the Dirichlet faces (no
+    jumps), and u^T J u = p (p+2) sum_F <K>/h |F| [[u]]^2 for a unit jump."""
+    rng = np.random.default_rng(23)
+    nc = (3, 2, 2)
+    K = np.exp(rng.normal(size=(12, 3)))
+    bc = [0, 1, 1, 0, 1, 1]
+    mk = lambda a: dg.Problem(*nc, 1.0, 0.8, 0.6, p, bc, K, c_cell=np.full(12, 0.3), alpha=a).assemble().toarray()
+    A1, A2, A3 = mk(1.0), mk(2.0), mk(3.5)
+    J = A2 - A1
+    assert np.abs((A3 - A1) - 2.5 * J).max() < 1e-11 * np.abs(A1).max()
+    assert np.abs(J - J.T).max() < 1e-12 * np.abs(J).max()
+    assert np.linalg.eigvalsh(J).min() > -1e-10 * np.abs(J).max()
+    # a continuous piecewise-trilinear field, zero on the Dirichlet planes
+    # (bc[2k+s] is the plane x_k = s L_k: here x = 0 and y = L_y)
+    from oracle import transfer
+    P = dg.Problem(*nc, 1.0, 0.8, 0.6, p, bc, K, alpha=2.0)
+    Pm = transfer.prolongation(P).toarray()
+    nv = P.nv
+    uh = rng.normal(size=P.nvert)
+    v = np.arange(P.nvert)
+    uh[v % nv[0] == 0] = 0.0
+    uh[(v // nv[0]) % nv[1] == nv[1] - 1] = 0.0
+    u = Pm @ uh
+    assert np.abs(J @ u).max() < 1e-11 * np.abs(J).max() * np.abs(u).max()

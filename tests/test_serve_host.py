@@ -116,3 +116,112 @@ def test_exclusive_requests_run_alone_in_fifo_order():
     adm = [q.t_admit for q in sorted(trace, key=lambda q: q.rid)]
     assert adm == sorted(adm)                           # FIFO admission
     assert serve.summarize(trace)["completed"] == 24
+
+
+class ChunkRunner:
+    """A solve of `work` chunks that checks the request's flags between
+    chunks, as DeviceRunner does between library calls; the checkpoint holds
+    the chunks done."""
+
+    def __init__(self, work=20, chunk_s=0.01):
+        self.work, self.chunk_s = work, chunk_s
+        self.lock = threading.Lock()
+        self.calls = []          # rid per call, in call order
+        self.chunks = {}         # rid -> chunks executed in total
+
+    def __call__(self, req):
+        with self.lock:
+            self.calls.append(req.rid)
+        done = 0 if req.checkpoint is None else req.checkpoint.iterations
+        while done < self.work:
+            if req.cancel_requested:
+                raise serve.Cancelled()
+            if req.evict_requested:
+                raise serve.Evicted(serve.Checkpoint(None, float(self.work - done), done))
+            time.sleep(self.chunk_s)
+            done += 1
+            with self.lock:
+                self.chunks[req.rid] = self.chunks.get(req.rid, 0) + 1
+        return {"converged": 1, "rel_residual": 1e-9, "iterations": done}, None
+
+
+def _serve_in_thread(srv, trace):
+    t = threading.Thread(target=srv.run, args=(trace,))
+    t.start()
+    return t
+
+
+def test_cancel_waiting_request_never_runs():
+    trace = serve.make_trace(4, None, n_range=(8, 8), p_range=(2, 2))
+    r = FakeRunner(service=0.05)
+    srv = serve.SolveServer(r, slots=1)
+    t = _serve_in_thread(srv, trace)
+    time.sleep(0.02)
+    assert srv.cancel(3)
+    t.join()
+    srv.close()
+    assert trace[3].cancelled and 3 not in r.order and r.order == [0, 1, 2]
+    s = serve.summarize(trace)
+    assert s["cancelled"] == 1 and s["completed"] == 3
+    assert not srv.cancel(0)                       # finished requests cannot be cancelled
+
+
+def test_cancel_running_request_stops_at_a_checkpoint():
+    trace = serve.make_trace(2, None, n_range=(8, 8), p_range=(2, 2))
+    r = ChunkRunner(work=30)
+    srv = serve.SolveServer(r, slots=1)
+    t = _serve_in_thread(srv, trace)
+    time.sleep(0.08)
+    assert srv.cancel(0)
+    t.join()
+    srv.close()
+    assert trace[0].cancelled and trace[0].stats is None and r.chunks[0] < 30
+    assert not trace[1].cancelled and r.chunks[1] == 30
+    assert srv._used == 0 and srv._idle == 1
+
+
+def test_evicted_request_resumes_from_its_checkpoint_at_the_head():
+    """An evicted request loses no work (the resumed run starts from the
+    checkpoint) and is re-admitted before the requests queued behind it."""
+    trace = serve.make_trace(3, None, n_range=(8, 8), p_range=(2, 2))
+    r = ChunkRunner(work=40)
+    srv = serve.SolveServer(r, slots=1)
+    t = _serve_in_thread(srv, trace)
+    time.sleep(0.06)
+    assert srv.evict(0)
+    assert not srv.evict(2)                        # waiting, not running
+    t.join()
+    srv.close()
+    assert r.calls == [0, 0, 1, 2]
+    assert trace[0].evictions == 1 and trace[0].stats["iterations"] == 40 and r.chunks[0] == 40
+    assert 0 < trace[0].checkpoint.iterations < 40
+    s = serve.summarize(trace)
+    assert s["completed"] == 3 and s["evictions"] == 1 and s["cancelled"] == 0
+
+
+class OomOnceRunner(TrackingRunner):
+    """Fails request `rid` with DGMG_ERR_OOM when it shares the GPU."""
+
+    def __init__(self, rid, **kw):
+        super().__init__(**kw)
+        self.rid = rid
+        self.failed = 0
+
+    def __call__(self, req):
+        if req.rid == self.rid and not req.alone:
+            self.failed += 1
+            time.sleep(self.service)
+            raise RuntimeError(f"request {req.rid}: DGMG_ERR_OOM")
+        return super().__call__(req)
+
+
+def test_failed_allocation_is_retried_alone():
+    trace = serve.make_trace(8, None, n_range=(8, 9), p_range=(2, 3))
+    r = OomOnceRunner(3, service=0.03)
+    srv = serve.SolveServer(r, slots=3)
+    srv.run(trace)
+    srv.close()
+    assert r.failed == 1 and trace[3].retries == 1 and trace[3].error is None
+    assert r.seen[3] == 1                          # the retry ran with nothing beside it
+    s = serve.summarize(trace)
+    assert s["completed"] == 8 and s["errors"] == 0 and s["retries"] == 1
