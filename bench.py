@@ -38,7 +38,7 @@ WORKLOAD = dict(kind="lognormal", n=32, p=4)
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_SM = 4          # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz)
 SM_MAX_MHZ = 2070.0
-CPU_SAMPLE = dict(n=6, p=4)        # oracle sample: same workload family, 6^3 cells
+CPU_SAMPLE = dict(n=8, p=4)        # oracle sample: same workload family, 8^3 cells
 # DRAM bytes (read + write) of one k_smooth_pcg<double> launch on this mesh, from
 # the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt
 # (a sweep with defect, 1 warp per block; the block shape does not change the
@@ -310,10 +310,7 @@ def run_dgmg(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 9), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"variable-coefficient diffusion, log-normal K per cell (sigma 1, seed 1805), "
-                               f"SIPG Q{w['p']} on {WORKLOAD['n']}^3 hexes, {ndof} dofs, FP64 CG + hybrid V-cycle "
-                               f"(block-Jacobi, inner PCG eps 1e-2, Q1 + AMG), rtol 1e-8",
-                   "ndof": ndof, "p": w["p"], "mesh": list(w["nc"]), "l2": "flushed between steps (256 MiB write)",
+        "config": {**workload_config(), "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}",
                    "warps_per_block": {k: {"apply": a, "smoother": b} for k, (a, b) in shapes.items()}},
         "e2e": e2e,
@@ -341,11 +338,23 @@ def run_dgmg(args, rank, world, local_rank):
     return out
 
 
+def workload_config():
+    """The config of the benchmark line (both arms): the workload one step solves."""
+    n, p = WORKLOAD["n"], WORKLOAD["p"]
+    ndof = n ** 3 * (p + 1) ** 3
+    return {"workload": f"variable-coefficient diffusion, log-normal K per cell (sigma 1, seed 1805), "
+                        f"SIPG Q{p} on {n}^3 hexes, {ndof} dofs, FP64 CG + hybrid V-cycle "
+                        f"(block-Jacobi omega 0.8, inner PCG eps 1e-2, Q1 + AMG), rtol 1e-8",
+            "ndof": ndof, "p": p, "mesh": [n, n, n]}
+
+
 # ---------------------------------------------------------------- oracle (CPU)
-def oracle_solve_sample():
+def oracle_solve_sample(repeats=1):
     """The CPU oracle (MX design: assembled block-CSR A, PCG on dense blocks,
-    P^T A P + AMG, CG) on a bounded sample of the same workload family.
-    Returns (dofs per second of the solve phase, description)."""
+    P^T A P + AMG, CG) on a bounded sample of the same workload family, with
+    the benchmark's solver settings (block-Jacobi damping 0.8, the library's
+    default).  Set-up once, then `repeats` solves from u = 0.  Returns
+    ([(dofs per second of the solve phase, seconds)] per solve, description)."""
     import numpy as np
     from oracle import amg, dg, solvers, transfer
     from paper_1805_11930_gb300 import inputs
@@ -359,50 +368,58 @@ def oracle_solve_sample():
     Pm = transfer.prolongation(P)
     am = amg.AggregationAMG(transfer.q1_matrix(P), P.nv)
     S = solvers.BlockJacobi(A, P.N, inner="pcg", eps=1e-2)
-    V = solvers.HybridVCycle(A, Pm, S, am.vcycle)
+    V = solvers.HybridVCycle(A, Pm, S, am.vcycle, omega=0.8)
     t1 = time.perf_counter()
-    x, it, hist = solvers.cg(lambda v: A @ v, F, V, rtol=1e-8)
-    t2 = time.perf_counter()
+    out = []
+    for _ in range(repeats):
+        ta = time.perf_counter()
+        x, it, hist = solvers.cg(lambda v: A @ v, F, V, rtol=1e-8)
+        tb = time.perf_counter()
+        out.append((P.ndof / (tb - ta), tb - ta))
     desc = (f"oracle solve of lognormal {CPU_SAMPLE['n']}^3 Q{CPU_SAMPLE['p']} ({P.ndof} dofs), "
-            f"CG {it} its to {hist[-1]:.1e}, setup {t1 - t0:.1f} s excluded, solve {t2 - t1:.1f} s, 1 thread")
-    return P.ndof / (t2 - t1), t2 - t1, desc
+            f"CG {it} its to {hist[-1]:.1e}, setup {t1 - t0:.1f} s excluded, solve {out[-1][1]:.1f} s, 1 thread")
+    return out, desc
+
+
+def oracle_subprocess(repeats=1):
+    """Run the oracle sample in a fresh single-threaded process; returns
+    ([(dofs/s, seconds)] per solve, description) or (None, error text)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
+                        "--worker-repeats", str(repeats)], env=env, capture_output=True, text=True,
+                       timeout=600 + 120 * repeats)
+    if r.returncode != 0:
+        return None, "failed: " + r.stderr[-300:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["samples"], d["desc"]
 
 
 def cpu_baseline_subprocess():
-    """Run the oracle sample in a fresh single-threaded process."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker"], env=env,
-                       capture_output=True, text=True, timeout=600)
-    if r.returncode != 0:
-        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": round(d["dofs_per_s"] / 1e9, 9), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-            "sample": d["desc"], "seconds": round(d["seconds"], 2)}
+    """The cpu_baseline object of the GPU line: one oracle solve."""
+    samples, desc = oracle_subprocess(1)
+    if samples is None:
+        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc}
+    return {"value": round(samples[0][0] / 1e9, 9), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+            "sample": desc, "seconds": round(samples[0][1], 2)}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is one bounded oracle solve."""
-    vals = []
-    desc = ""
-    secs = 0.0
-    # one untimed sample warms the interpreter, the imports and the file cache;
-    # every sample runs in a fresh process, so further warm-up changes nothing
-    warm = min(args.warmup, 1)
-    for _ in range(warm):
-        cpu_baseline_subprocess()
-    for _ in range(max(1, args.steps)):
-        cb = cpu_baseline_subprocess()
-        if cb["value"] is None:
-            return {"impl": "reference", "unavailable": cb["sample"]}
-        vals.append(cb["value"])
-        desc = cb["sample"]
-        secs += cb["seconds"]
-    v = statistics.median(vals)
+    """The oracle as the reference arm: one process sets the sample up once,
+    then runs W untimed and K timed solves of it; each step is one solve."""
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    samples, desc = oracle_subprocess(warm + steps)
+    if samples is None:
+        return {"impl": "reference", "unavailable": desc}
+    timed = samples[warm:]
+    secs = sum(t for _, t in timed)
+    sample_dofs = CPU_SAMPLE["n"] ** 3 * (CPU_SAMPLE["p"] + 1) ** 3
+    v = round(sample_dofs * len(timed) / secs / 1e9, 9)       # dofs solved / solve time
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": 1,
-            "steps": len(vals), "warmup": warm, "ms_per_step": round(secs / len(vals) * 1e3, 1),
+            "steps": steps, "warmup": warm, "ms_per_step": round(secs / steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "bounded sample: " + desc},
+            "config": workload_config(),
             "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -415,11 +432,12 @@ def main():
     ap.add_argument("--impl", default="dgmg", choices=["dgmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
+    ap.add_argument("--worker-repeats", type=int, default=1)
     args = ap.parse_args()
 
     if args.cpu_baseline_worker:
-        dps, secs, desc = oracle_solve_sample()
-        print(json.dumps({"dofs_per_s": dps, "seconds": secs, "desc": desc}))
+        samples, desc = oracle_solve_sample(args.worker_repeats)
+        print(json.dumps({"samples": samples, "desc": desc}))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
