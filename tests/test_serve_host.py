@@ -225,3 +225,68 @@ def test_failed_allocation_is_retried_alone():
     assert r.seen[3] == 1                          # the retry ran with nothing beside it
     s = serve.summarize(trace)
     assert s["completed"] == 8 and s["errors"] == 0 and s["retries"] == 1
+
+
+class FakeCtx:
+    """Stands in for a library context: a stationary iteration that reduces
+    the residual by `rate` per outer iteration, reported the way dgmg_solve
+    reports it (rel_residual relative to the call's own initial residual,
+    status NOT_CONVERGED at maxit)."""
+
+    def __init__(self, rate=0.5):
+        self.rate = rate
+        self.calls = []
+
+    def solve(self, f, u, opts, check=False):
+        import math
+        import torch
+        r0 = float(torch.linalg.vector_norm(f - u))
+        need = math.ceil(math.log(opts.rtol) / math.log(self.rate))
+        its = min(need, opts.maxit)
+        u.add_((f - u) * (1 - self.rate ** its))      # residual f - u shrinks by rate^its
+        self.calls.append((opts.rtol, opts.maxit, its))
+        rel = float(torch.linalg.vector_norm(f - u)) / r0
+        return {"status": "DGMG_OK" if its == need else "DGMG_ERR_NOT_CONVERGED", "iterations": its,
+                "rel_residual": rel, "converged": int(its == need), "inner_mean": 0.0, "inner_max": 0}
+
+
+def test_chunked_solve_keeps_the_stopping_test_relative_to_f():
+    """DeviceRunner's chunked form: each call's tolerance is rescaled so that
+    the overall stop is ||r|| <= rtol ||f||, iterations add up, and a resumed
+    request continues from its checkpoint with the same total work as an
+    uninterrupted one."""
+    pytest = __import__("pytest")
+    torch = pytest.importorskip("torch")
+    from paper_1805_11930_gb300 import build, dgmg
+    if not build.up_to_date():
+        try:
+            build.build()
+        except RuntimeError as e:       # no nvcc: the options struct comes from the library
+            pytest.skip(str(e))
+    dgmg.load()
+    f = torch.linspace(1.0, 2.0, 50, dtype=torch.float64)
+    req = serve.make_trace(1, None)[0]
+    runner = serve.DeviceRunner(chunk=4, rtol=1e-8)
+    ctx = FakeCtx(0.5)
+    u, st = runner._chunked(ctx, f, req, {})
+    assert st["iterations"] == 27 and st["converged"] == 1      # 0.5^27 < 1e-8 < 0.5^26
+    assert st["rel_residual"] <= 1e-8 and len(ctx.calls) == 7   # 6 chunks of 4, then 3
+    assert all(m == 4 for _, m, _ in ctx.calls)
+    # stopped after the second chunk, then resumed from the checkpoint
+    hits = []
+
+    class Stop(serve.DeviceRunner):
+        def on_chunk(self, req, iterations, rel_residual):
+            hits.append((iterations, rel_residual))
+            if iterations == 8:
+                req.evict_requested = True
+
+    req2 = serve.make_trace(1, None)[0]
+    with pytest.raises(serve.Evicted) as ev:
+        Stop(chunk=4, rtol=1e-8)._chunked(FakeCtx(0.5), f, req2, {})
+    cp = ev.value.checkpoint
+    assert cp.iterations == 8 and abs(cp.res_abs / float(torch.linalg.vector_norm(f)) - 0.5 ** 8) < 1e-12
+    req2.checkpoint, req2.evict_requested = cp, False
+    u2, st2 = serve.DeviceRunner(chunk=4, rtol=1e-8)._chunked(FakeCtx(0.5), f, req2, {})
+    assert st2["iterations"] == 27 and st2["converged"] == 1
+    assert float(torch.linalg.vector_norm(u2 - u)) < 1e-12 * float(torch.linalg.vector_norm(u))
