@@ -107,6 +107,24 @@ def test_weighted_average_closed_form(p):
     assert abs(u @ A @ v - expected) < 1e-12 * abs(expected)      # symmetry term
 
 
+@pytest.mark.parametrize("p", [1, 3])
+def test_volume_and_reaction_closed_form(p):
+    """One cell, all Neumann, b = 0, so a_h(u, v) = (K grad u, grad v)_T +
+    (c u, v)_T: u = 1 gives c |T|; u = x - h_x/2 gives K_xx |T| + c |T| h_x^2/12."""
+    K = np.array([[2.0, 3.0, 0.5]])
+    h = np.array([0.5, 0.25, 2.0])
+    c = 0.7
+    P = dg.Problem(1, 1, 1, *h, p, [1] * 6, K, c_cell=np.array([c]))
+    A = P.assemble().toarray()
+    T = np.prod(h)
+    tol = 1e-14 * np.abs(A).sum()           # rounding of the cancelling stiffness entries
+    one = np.ones(P.N)
+    assert abs(one @ A @ one - c * T) < tol
+    u = P.interpolate(lambda x, y, z: x - h[0] / 2)
+    expected = K[0, 0] * T + c * T * h[0] ** 2 / 12
+    assert abs(u @ A @ u - expected) < tol
+
+
 @pytest.mark.parametrize("p", [1, 2])
 def test_upwind_closed_form(p):
     """Piecewise constants a, beta on two cells, b = (bx, 0, 0): the
