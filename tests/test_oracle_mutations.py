@@ -31,6 +31,9 @@ def test_pins_pass_unmutated():
     mg.test_q1_rediscretisation_equals_galerkin_product(True, True)
     mg.test_thomas_solve_brute_force()
     mg.test_vcycle_symmetric_with_exact_blocks()
+    mg.test_tridiagonal_preconditioner_exact_on_tridiagonal_block()
+    mg.test_multicolour_sor_properties()
+    mg.test_p0_galerkin_matrix_is_modified_fv(True)
     qd.test_gauss3_closed_form()
 
 
@@ -119,3 +122,26 @@ def test_gauss_nodes_left_on_minus_one_to_one(monkeypatch):
     orig = quadrature.gauss_legendre
     monkeypatch.setattr(quadrature, "gauss_legendre", lambda m: (2 * orig(m)[0] - 1, orig(m)[1]))
     _fails(qd.test_gauss3_closed_form)
+
+
+def test_thomas_preconditioner_dropped(monkeypatch):
+    monkeypatch.setattr(solvers, "thomas_solve", lambda sub, diag, sup, r: r / diag)
+    _fails(mg.test_tridiagonal_preconditioner_exact_on_tridiagonal_block)
+
+
+def test_colouring_by_x_parity_only(monkeypatch):
+    """Colours that let face neighbours in y or z share a colour."""
+    orig = solvers.MulticolourBlockSOR.__init__
+
+    def wrong(self, A, N, nc, *a, **kw):
+        orig(self, A, N, nc, *a, **kw)
+        c = np.arange(int(np.prod(nc)))
+        self.colour = c % nc[0] % 2
+    monkeypatch.setattr(solvers.MulticolourBlockSOR, "__init__", wrong)
+    _fails(mg.test_multicolour_sor_properties)
+
+
+def test_p0_coarse_values_spread_with_weight_one_half(monkeypatch):
+    orig = transfer.p0_prolongation
+    monkeypatch.setattr(transfer, "p0_prolongation", lambda prob: 0.5 * orig(prob))
+    _fails(mg.test_p0_galerkin_matrix_is_modified_fv, True)
