@@ -34,6 +34,13 @@ def paper_model(p, ncell, problem="diffusion", variant="MF", d=3, n_out=100, n_b
     raise ValueError(problem)
 
 
+def matrix_bytes(p, ncell, d=3):
+    """Bytes of the assembled DG matrix counted as in the paper's problem-size
+    table (Sec. 4): 7 blocks of (p+1)^(2d) doubles per cell (the cell and its
+    2d face neighbours; boundary cells counted alike)."""
+    return DOUBLE * 7 * ncell * (p + 1) ** (2 * d)
+
+
 def library_bytes(nc, p, krylov="fcg", restart=30):
     """Device bytes of one context plus the caller's f and u: per dof the
     FP64/FP32 diagonals and inverses (24 B), FP64 and FP32 V-cycle work

@@ -1,7 +1,8 @@
 """The paper's storage model (Sec. 4.4, eqs. memory_diffusion /
 memory_convection) against the values printed in its Tables 4-6
 (tests/golden/memory_tables.txt): Table 4 is in units of 1e9 bytes, Tables 5
-and 6 in GiB, each rounded as printed."""
+and 6 in GiB, each rounded as printed; and the problem sizes of Table 1
+(tests/golden/problem_sizes.txt)."""
 import os
 
 import pytest
@@ -35,3 +36,26 @@ def test_memory_tables(row):
     assert abs(val["PMF"] - pmf) <= 0.05 + 1e-9
     decimals = len(mf_text.split(".")[1])
     assert abs(val["MF"] - mf) <= 0.5 * 10 ** (-decimals) + 1e-9
+
+
+SIZES = os.path.join(os.path.dirname(__file__), "golden", "problem_sizes.txt")
+
+
+def size_rows():
+    out = []
+    for line in open(SIZES):
+        if line.startswith("#") or not line.strip():
+            continue
+        p, npc, nx, ny, nz, mdofs, gib, ratio = line.split()
+        out.append((int(p), int(npc), int(nx) * int(ny) * int(nz), float(mdofs), float(gib), int(ratio)))
+    return out
+
+
+@pytest.mark.parametrize("row", size_rows(), ids=lambda r: f"table1_p{r[0]}")
+def test_problem_size_table(row):
+    p, npc, ncell, mdofs, gib, ratio = row
+    ndof = ncell * (p + 1) ** 3
+    assert (p + 1) ** 3 == npc
+    assert round(ndof / 1e6, 1) == mdofs
+    assert abs(footprint.matrix_bytes(p, ncell) / 2.0 ** 30 - gib) <= 0.05 + 1e-9
+    assert footprint.matrix_bytes(p, ncell) // (8 * ndof) == ratio

@@ -336,3 +336,26 @@ def test_penalty_parameter_enters_only_the_jump_term(p):
     uh[(v // nv[0]) % nv[1] == nv[1] - 1] = 0.0
     u = Pm @ uh
     assert np.abs(J @ u).max() < 1e-11 * np.abs(J).max() * np.abs(u).max()
+
+
+def test_block_structure_matches_the_problem_size_count():
+    """The assembled matrix has a block for every cell and two for every
+    interior face, nothing else: ncell + 2 (interior faces) blocks of
+    (p+1)^6 entries, which tends to Table 1's 7 blocks per cell (Sec. 4)."""
+    nc = (4, 3, 2)
+    P = dg.Problem(*nc, 1, 1, 1, 1, [0, 1, 0, 1, 1, 0], np.ones(24))
+    A = P.assemble()
+    nx, ny, nz = nc
+    faces = (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+    assert A.indices.size == 24 + 2 * faces
+    cols = {c: set(A.indices[A.indptr[c]:A.indptr[c + 1]]) for c in range(24)}
+    for c in range(24):
+        cx, cy, cz = P.cell_coords(c)
+        nb = {c}
+        for k, (v, n) in enumerate(zip((cx, cy, cz), nc)):
+            for s in (-1, 1):
+                if 0 <= v + s < n:
+                    q = [cx, cy, cz]
+                    q[k] += s
+                    nb.add(P.cell_index(*q))
+        assert cols[c] == nb
