@@ -340,3 +340,26 @@ def test_energy_norm_estimate_identity():
     assert np.sqrt(eA[k] / (xs @ (A @ xs))) == pytest.approx(hist[-1], rel=0.5)
     assert np.abs(xe - xs_list[k + d]).max() <= 1e-12 * np.abs(xs).max()
     assert np.sqrt((xs - xe) @ (A @ (xs - xe)) / (xs @ (A @ xs))) <= 1e-6
+
+
+def test_outer_iterations_nearly_independent_of_inner_tolerance():
+    """Sec. 4.2 observes that the outer CG iteration count hardly depends on
+    the inner tolerance eps: with inner PCG to eps = 1e-2 .. 1e-8 the count
+    stays within two of the count with exact (LU) block solves."""
+    from paper_1805_11930_gb300 import inputs
+    w = inputs.lognormal(4, 2)
+    P = dg.Problem(*w["nc"], *w["L"], w["p"], w["bc"], w["K"])
+    A = P.assemble()
+    F = P.rhs(inputs.evaluate(w["f"], P.volume_points()))
+    Pm = transfer.prolongation(P)
+    am = amg.AggregationAMG(transfer.q1_matrix(P), P.nv)
+
+    def outer_its(**kw):
+        V = solvers.HybridVCycle(A, Pm, solvers.BlockJacobi(A, P.N, **kw), am.vcycle, omega=0.8)
+        x, it, hist = solvers.cg(lambda v: A @ v, F, V, rtol=1e-8)
+        assert np.linalg.norm(F - A @ x) <= 1e-8 * np.linalg.norm(F) * 1.0001
+        return it
+
+    exact = outer_its(inner="lu")
+    for eps in (1e-2, 1e-4, 1e-8):
+        assert abs(outer_its(inner="pcg", eps=eps) - exact) <= 2
