@@ -349,7 +349,7 @@ def workload_config():
 
 
 # ---------------------------------------------------------------- oracle (CPU)
-def oracle_solve_sample(repeats=1):
+def oracle_solve_sample(repeats=1, n=CPU_SAMPLE["n"]):
     """The CPU oracle (MX design: assembled block-CSR A, PCG on dense blocks,
     P^T A P + AMG, CG) on a bounded sample of the same workload family, with
     the benchmark's solver settings (block-Jacobi damping 0.8, the library's
@@ -358,7 +358,7 @@ def oracle_solve_sample(repeats=1):
     import numpy as np
     from oracle import amg, dg, solvers, transfer
     from paper_1805_11930_gb300 import inputs
-    w = inputs.lognormal(CPU_SAMPLE["n"], CPU_SAMPLE["p"])
+    w = inputs.lognormal(n, CPU_SAMPLE["p"])
     t0 = time.perf_counter()
     P = dg.Problem(*w["nc"], *w["L"], w["p"], w["bc"], w["K"])
     A = P.assemble()
@@ -376,18 +376,19 @@ def oracle_solve_sample(repeats=1):
         x, it, hist = solvers.cg(lambda v: A @ v, F, V, rtol=1e-8)
         tb = time.perf_counter()
         out.append((P.ndof / (tb - ta), tb - ta))
-    desc = (f"oracle solve of lognormal {CPU_SAMPLE['n']}^3 Q{CPU_SAMPLE['p']} ({P.ndof} dofs), "
+    desc = (f"oracle solve of lognormal {n}^3 Q{CPU_SAMPLE['p']} ({P.ndof} dofs), "
             f"CG {it} its to {hist[-1]:.1e}, setup {t1 - t0:.1f} s excluded, solve {out[-1][1]:.1f} s, 1 thread")
     return out, desc
 
 
-def oracle_subprocess(repeats=1):
-    """Run the oracle sample in a fresh single-threaded process; returns
-    ([(dofs/s, seconds)] per solve, description) or (None, error text)."""
+def oracle_subprocess(repeats=1, n=CPU_SAMPLE["n"]):
+    """Run the oracle sample (n^3 cells) in a fresh single-threaded process;
+    returns ([(dofs/s, seconds)] per solve, description) or (None, error text)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
-                        "--worker-repeats", str(repeats)], env=env, capture_output=True, text=True,
+                        "--worker-repeats", str(repeats), "--oracle-cells", str(n)], env=env,
+                       capture_output=True, text=True,
                        timeout=600 + 120 * repeats)
     if r.returncode != 0:
         return None, "failed: " + r.stderr[-300:]
@@ -395,9 +396,9 @@ def oracle_subprocess(repeats=1):
     return d["samples"], d["desc"]
 
 
-def cpu_baseline_subprocess():
+def cpu_baseline_subprocess(n=CPU_SAMPLE["n"]):
     """The cpu_baseline object of the GPU line: one oracle solve."""
-    samples, desc = oracle_subprocess(1)
+    samples, desc = oracle_subprocess(1, n)
     if samples is None:
         return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc}
     return {"value": round(samples[0][0] / 1e9, 9), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
@@ -409,12 +410,12 @@ def run_reference(args):
     then runs W untimed and K timed solves of it; each step is one solve."""
     steps = max(1, args.steps)
     warm = max(0, args.warmup)
-    samples, desc = oracle_subprocess(warm + steps)
+    samples, desc = oracle_subprocess(warm + steps, args.oracle_cells)
     if samples is None:
         return {"impl": "reference", "unavailable": desc}
     timed = samples[warm:]
     secs = sum(t for _, t in timed)
-    sample_dofs = CPU_SAMPLE["n"] ** 3 * (CPU_SAMPLE["p"] + 1) ** 3
+    sample_dofs = args.oracle_cells ** 3 * (CPU_SAMPLE["p"] + 1) ** 3
     v = round(sample_dofs * len(timed) / secs / 1e9, 9)       # dofs solved / solve time
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": 1,
             "steps": steps, "warmup": warm, "ms_per_step": round(secs / steps * 1e3, 1),
@@ -433,10 +434,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
     ap.add_argument("--worker-repeats", type=int, default=1)
+    ap.add_argument("--oracle-cells", type=int, default=CPU_SAMPLE["n"],
+                    help="cells per direction of the oracle sample (reference arm and cpu_baseline)")
     args = ap.parse_args()
 
     if args.cpu_baseline_worker:
-        samples, desc = oracle_solve_sample(args.worker_repeats)
+        samples, desc = oracle_solve_sample(args.worker_repeats, args.oracle_cells)
         print(json.dumps({"samples": samples, "desc": desc}))
         return
 
@@ -455,7 +458,7 @@ def main():
     out = run_dgmg(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_subprocess()
+            out["cpu_baseline"] = cpu_baseline_subprocess(args.oracle_cells)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
