@@ -152,9 +152,20 @@ typedef struct {
 void dgmg_default_opts(dgmg_solve_opts* opts);
 
 /* Create a context on CUDA `device`; `cuda_stream` is a cudaStream_t (NULL =
- * the legacy default stream).  *out receives the context. */
+ * the legacy default stream), used but not owned.  *out receives the context
+ * (owned by the caller until dgmg_destroy), or NULL on failure:
+ * DGMG_ERR_ARG for out == NULL or a device that does not exist (also when no
+ * GPU is visible), DGMG_ERR_CUDA when the device tables or the small
+ * reduction buffers cannot be set up. */
 dgmg_status dgmg_create(dgmg_ctx** out, int device, void* cuda_stream);
+
+/* Synchronise the context's stream, free every device and pinned buffer and
+ * captured graph of the context, and the context itself.  NULL:
+ * DGMG_ERR_ARG.  The caller's stream and vectors are not touched. */
 dgmg_status dgmg_destroy(dgmg_ctx* ctx);
+
+/* Message of the last failed call on ctx (owned by ctx, valid until its next
+ * call); "null context" for NULL. */
 const char* dgmg_last_error(const dgmg_ctx* ctx);
 
 /* Grid and degree (Sec. 2.1, uniform axis-parallel hexahedra): 1 <= p <= 8,
@@ -186,7 +197,8 @@ dgmg_status dgmg_set_coefficients(dgmg_ctx* ctx, const double* K, int kdim,
 
 /* Sizes of the current mesh: DG dofs, vertices, cells, volume quadrature
  * points (ncell (p+1)^3) and boundary-face quadrature points over all six
- * planes (2 (ny nz + nx nz + nx ny) (p+1)^2). */
+ * planes (2 (ny nz + nx nz + nx ny) (p+1)^2).  Host outputs, each may be
+ * NULL.  DGMG_ERR_STATE without a mesh. */
 dgmg_status dgmg_sizes(const dgmg_ctx* ctx, long long* ndof, long long* nvert, long long* ncell,
                        long long* nvol_qp, long long* nface_qp);
 
@@ -194,7 +206,10 @@ dgmg_status dgmg_sizes(const dgmg_ctx* ctx, long long* ndof, long long* nvert, l
  * which dgmg_assemble_rhs expects data.  Volume: cell-major, point
  * q1 + m q2 + m^2 q3 within a cell.  Faces: planes -x,+x,-y,+y,-z,+z; within a
  * plane normal to axis k with tangential axes a < b, cells ordered ca + n_a cb,
- * points qa + m qb within a cell face.  Either pointer may be NULL. */
+ * points qa + m qb within a cell face.  The points are the tensor Gauss rule
+ * with m = p + 1 points per direction mapped to each cell (Sec. 3.1).  Either
+ * pointer may be NULL; sizes from dgmg_sizes (3 doubles per point).
+ * DGMG_ERR_STATE without a mesh. */
 dgmg_status dgmg_quadrature_points(const dgmg_ctx* ctx, double* vol_xyz, double* face_xyz);
 
 /* Right-hand side f_i = l_h(psi_i) (Sec. 2.1, eq. rhs) from values at the
@@ -278,7 +293,8 @@ dgmg_status dgmg_prolong_add_p0(dgmg_ctx* ctx, const double* u_hat, void* u, dgm
  * entries per row).  Builds the P0 hierarchy if needed. */
 dgmg_status dgmg_coarse_matrix_p0(dgmg_ctx* ctx, double* stencil);
 
-/* u_hat = one aggregation-AMG V-cycle on the P0 A_hat from zero, as
+/* u_hat = one aggregation-AMG V-cycle on the P0 A_hat from zero (the coarse
+ * correction of Algorithm 1 on the P0 subspace, Sec. 2.2.2), as
  * dgmg_coarse_cycle does on Q1.  r_hat, u_hat: device FP64 cell vectors,
  * distinct. */
 dgmg_status dgmg_coarse_cycle_p0(dgmg_ctx* ctx, const double* r_hat, double* u_hat);

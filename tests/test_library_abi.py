@@ -75,3 +75,19 @@ def test_null_context_is_an_argument_error():
     lib = dgmg.load()
     assert lib.dgmg_set_penalty(None, 2.0) == 1
     assert lib.dgmg_destroy(None) == 1
+
+
+def test_every_declaration_is_documented():
+    """Each function the header declares sits under a comment block (a pair
+    of declarations may share one), so its argument layout, ownership and
+    errors are stated where the boundary is defined."""
+    import re
+    lines = open(os.path.join(os.path.dirname(__file__), "..", "include", "dgmg.h")).read().splitlines()
+    for i, line in enumerate(lines):
+        m = re.match(r"^(?:dgmg_status|const char\*|void)\s+(dgmg_[a-z0-9_]+)\(", line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
+            j -= 1                      # continuation lines of the neighbouring declaration
+        assert j >= 0 and lines[j].rstrip().endswith("*/"), m.group(1)
