@@ -1,6 +1,6 @@
 """Operator-apply throughput over the polynomial degree.
 
-python -m paper_1805_11930_gb300.apply_sweep [--degrees 2,3,4,5,6]
+python -m paper_1805_11930_gb300.apply_sweep [--degrees 2,3,4,5,6] [--advection]
 
 Meshes sized to 30-300 MB per FP64 vector: 64^3 cells for p <= 3, 40^3 for
 p = 4..6 (log-normal K, Dirichlet).  For each p and precision: median
@@ -11,6 +11,11 @@ x 2070 MHz; for df64, FP64 vectors in double-float arithmetic, as well) or of
 the measured FP32 FMA rate (75.6 TFLOP/s), and the HBM
 rate of the compulsory traffic (read u, write v) as a fraction of the
 measured copy bandwidth.  One JSON line per (p, precision).
+
+--advection: the advection-on variant (the rotating field b of the
+convection workload, kappa = 1e-3), whose volume term carries the value
+terms (algorithmic 36 n^4 + 120 n^3 per cell), in FP64 and FP32 (the
+double-float kernels cover b = 0 only).
 """
 import argparse
 import json
@@ -25,6 +30,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--degrees", default="2,3,4,5,6")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--advection", action="store_true")
     args = ap.parse_args()
     import torch
 
@@ -32,13 +38,15 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for p in [int(x) for x in args.degrees.split(",")]:
         n = 64 if p <= 3 else 40
-        w = inputs.lognormal(n, p)
+        w = inputs.convection(n, p) if args.advection else inputs.lognormal(n, p)
         ctx = dgmg.Context(0)
         ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
-        ctx.set_coefficients(w["K"])
+        ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
         s = ctx.sizes()
-        for dt, name, peak in ((torch.float64, "fp64", FP64_PEAK), (torch.float32, "fp32", FP32_PEAK),
-                               (torch.float64, "df64", FP64_PEAK)):
+        variants = [(torch.float64, "fp64", FP64_PEAK), (torch.float32, "fp32", FP32_PEAK)]
+        if not args.advection:
+            variants.append((torch.float64, "df64", FP64_PEAK))
+        for dt, name, peak in variants:
             x = torch.rand(s["ndof"], dtype=dt, device="cuda")
             y = torch.empty_like(x)
             df = name == "df64"
@@ -55,9 +63,10 @@ def main():
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
             t = statistics.median(ms) / 1e3
-            fl = flops.algorithmic_apply(p + 1) * s["ncell"] / t
+            fl = flops.algorithmic_apply(p + 1, value_terms=args.advection) * s["ncell"] / t
             by = flops.hbm_bytes_apply(p + 1, s["ncell"], 4 if name == "fp32" else 8) / t
-            print(json.dumps({"p": p, "mesh": n, "ndof": s["ndof"], "prec": name, "ms": round(t * 1e3, 4),
+            print(json.dumps({"p": p, "mesh": n, "ndof": s["ndof"], "prec": name, "advection": args.advection,
+                              "ms": round(t * 1e3, 4),
                               "gdofs": round(s["ndof"] / t / 1e9, 3), "tflops": round(fl / 1e12, 3),
                               "alu_frac": round(fl / peak, 3), "hbm_gbs": round(by / 1e9, 1),
                               "hbm_frac": round(by / 1e9 / HBM_GBS, 4)}), flush=True)
