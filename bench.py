@@ -353,8 +353,11 @@ def oracle_solve_sample(repeats=1, n=CPU_SAMPLE["n"]):
     """The CPU oracle (MX design: assembled block-CSR A, PCG on dense blocks,
     P^T A P + AMG, CG) on a bounded sample of the same workload family, with
     the benchmark's solver settings (block-Jacobi damping 0.8, the library's
-    default).  Set-up once, then `repeats` solves from u = 0.  Returns
-    ([(dofs per second of the solve phase, seconds)] per solve, description)."""
+    default).  Set-up once, then `repeats` solves from u = 0.  Also times the
+    oracle's block-CSR apply A u and one dense-LU block-Jacobi sweep (LU
+    factors computed before the timer).  Returns ([(dofs per second of the
+    solve phase, seconds)] per solve, description, {apply_gdofs,
+    lu_sweep_gdofs})."""
     import numpy as np
     from oracle import amg, dg, solvers, transfer
     from paper_1805_11930_gb300 import inputs
@@ -378,12 +381,24 @@ def oracle_solve_sample(repeats=1, n=CPU_SAMPLE["n"]):
         out.append((P.ndof / (tb - ta), tb - ta))
     desc = (f"oracle solve of lognormal {n}^3 Q{CPU_SAMPLE['p']} ({P.ndof} dofs), "
             f"CG {it} its to {hist[-1]:.1e}, setup {t1 - t0:.1f} s excluded, solve {out[-1][1]:.1f} s, 1 thread")
-    return out, desc
+    u = np.random.default_rng(0).uniform(-1, 1, P.ndof)
+    ta = time.perf_counter()
+    for _ in range(10):
+        A @ u
+    t_apply = (time.perf_counter() - ta) / 10
+    lu = solvers.BlockJacobi(A, P.N, inner="lu")
+    lu(F, u, 1, 0.8)                                  # factors the blocks
+    ta = time.perf_counter()
+    lu(F, u, 1, 0.8)
+    t_sweep = time.perf_counter() - ta
+    parts = {"apply_gdofs": round(P.ndof / t_apply / 1e9, 6), "lu_sweep_gdofs": round(P.ndof / t_sweep / 1e9, 6)}
+    return out, desc, parts
 
 
 def oracle_subprocess(repeats=1, n=CPU_SAMPLE["n"]):
     """Run the oracle sample (n^3 cells) in a fresh single-threaded process;
-    returns ([(dofs/s, seconds)] per solve, description) or (None, error text)."""
+    returns ([(dofs/s, seconds)] per solve, description, oracle apply and
+    LU-sweep rates) or (None, error text, {})."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
@@ -391,18 +406,18 @@ def oracle_subprocess(repeats=1, n=CPU_SAMPLE["n"]):
                        capture_output=True, text=True,
                        timeout=600 + 120 * repeats)
     if r.returncode != 0:
-        return None, "failed: " + r.stderr[-300:]
+        return None, "failed: " + r.stderr[-300:], {}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["samples"], d["desc"]
+    return d["samples"], d["desc"], d["parts"]
 
 
 def cpu_baseline_subprocess(n=CPU_SAMPLE["n"]):
     """The cpu_baseline object of the GPU line: one oracle solve."""
-    samples, desc = oracle_subprocess(1, n)
+    samples, desc, parts = oracle_subprocess(1, n)
     if samples is None:
         return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc}
     return {"value": round(samples[0][0] / 1e9, 9), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-            "sample": desc, "seconds": round(samples[0][1], 2)}
+            "sample": desc, "seconds": round(samples[0][1], 2), **parts}
 
 
 def run_reference(args):
@@ -410,7 +425,7 @@ def run_reference(args):
     then runs W untimed and K timed solves of it; each step is one solve."""
     steps = max(1, args.steps)
     warm = max(0, args.warmup)
-    samples, desc = oracle_subprocess(warm + steps, args.oracle_cells)
+    samples, desc, parts = oracle_subprocess(warm + steps, args.oracle_cells)
     if samples is None:
         return {"impl": "reference", "unavailable": desc}
     timed = samples[warm:]
@@ -421,7 +436,7 @@ def run_reference(args):
             "steps": steps, "warmup": warm, "ms_per_step": round(secs / steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc, **parts},
             "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -439,8 +454,8 @@ def main():
     args = ap.parse_args()
 
     if args.cpu_baseline_worker:
-        samples, desc = oracle_solve_sample(args.worker_repeats, args.oracle_cells)
-        print(json.dumps({"samples": samples, "desc": desc}))
+        samples, desc, parts = oracle_solve_sample(args.worker_repeats, args.oracle_cells)
+        print(json.dumps({"samples": samples, "desc": desc, "parts": parts}))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -27,6 +27,7 @@ def test_reference_arm_json_line():
     assert d["config"]["ndof"] == 32 ** 3 * 125 and d["config"]["mesh"] == [32, 32, 32]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and "3^3" in cb["sample"]
+    assert cb["apply_gdofs"] > 0 and cb["lu_sweep_gdofs"] > 0     # the oracle's SpMV and dense-LU sweep
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     # value = dofs solved / solve time
     assert abs(3 ** 3 * 125 / (d["ms_per_step"] / 1e3) / 1e9 - d["value"]) <= 0.01 * d["value"]
