@@ -197,3 +197,20 @@ def test_quadrature_rules_match_the_oracle(shim, n):
     shim.shim_gauss_lobatto01(n, _p(x), _p(w))
     lx, lw = quadrature.gauss_lobatto(n)
     assert np.abs(x - lx).max() < 1e-15 and np.abs(w - lw).max() < 1e-15
+
+
+@pytest.mark.parametrize("alpha", [0.6, 4.0])
+def test_coarse_matrices_follow_the_penalty_parameter(shim, alpha):
+    nc, L, p, bc, K, b, c = _case("p3_advection")
+    P = dg.Problem(*nc, *L, p, bc, K, b_vertex=b, c_cell=c, alpha=alpha)
+    A = P.assemble()
+    Pm = transfer.prolongation(P)
+    keep, args = _mesh_args(nc, L, p, bc, K, b, c, alpha=alpha)
+    st = np.zeros((P.nvert, 27))
+    shim.shim_q1_stencil(*args, _p(st))
+    G = (Pm.T @ A @ Pm).toarray()
+    assert np.abs(_dense(st, P.nv) - G).max() < 1e-12 * np.abs(G).max()
+    st0 = np.zeros((P.ncell, 27))
+    shim.shim_p0_stencil(*args, _p(st0))
+    G0 = transfer.p0_matrix(A, P).toarray()
+    assert np.abs(_dense(st0, P.nc) - G0).max() < 1e-12 * np.abs(G0).max()
