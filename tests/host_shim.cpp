@@ -71,6 +71,9 @@ void shim_quadrature_points(int nx, int ny, int nz, int p, const double* h, doub
   dgmg::quadrature_points_host(mesh(nx, ny, nz, p, h, bc, &one, 1, nullptr, nullptr, 1.25, nullptr), vol, face);
 }
 
+// The per-order 1D tables the kernels read (5 n^2 + 6 n doubles).
+void shim_build_tables(int n, double* T) { dgmg::build_tables_into(n, T); }
+
 void shim_gauss_legendre01(int m, double* x, double* w) { dgmg::gauss_legendre01(m, x, w); }
 void shim_gauss_lobatto01(int n, double* x, double* w) { dgmg::gauss_lobatto01(n, x, w); }
 

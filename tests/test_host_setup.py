@@ -3,8 +3,8 @@ against the oracle, through a test shim built with the host compiler alone:
 the Q1 coarse matrix by re-discretisation (App. A.2) against P^T A P, the P0
 coarse matrix (App. A.1) against P0^T A P0, one 2x2x2 Galerkin coarsening
 of the AMG against the oracle's aggregation, the right-hand side l_h (eq.
-rhs; also with K(x) in the Dirichlet terms, Sec. 4.2) and the Gauss and
-Gauss-Lobatto rules.  The same code runs on the GPU tier through the C ABI;
+rhs; also with K(x) in the Dirichlet terms, Sec. 4.2), the Gauss and
+Gauss-Lobatto rules and the 1D tables the kernels read.  The same code runs on the GPU tier through the C ABI;
 here it is checked without a GPU."""
 import ctypes
 import os
@@ -214,3 +214,36 @@ def test_coarse_matrices_follow_the_penalty_parameter(shim, alpha):
     shim.shim_p0_stencil(*args, _p(st0))
     G0 = transfer.p0_matrix(A, P).toarray()
     assert np.abs(_dense(st0, P.nc) - G0).max() < 1e-12 * np.abs(G0).max()
+
+
+@pytest.mark.parametrize("n", range(2, 10))
+def test_kernel_tables_match_the_oracle_basis(shim, n):
+    """The 1D tables the kernels read (GLL basis and its derivative at the
+    Gauss points, the Gauss collocation derivative, end-point derivatives,
+    mass and stiffness matrices, Q1 hats, Gauss points and weights) against
+    the oracle's basis functions, with the mass and stiffness matrices
+    integrated by the oracle with a finer Gauss rule."""
+    T = np.zeros(5 * n * n + 6 * n)
+    shim.shim_build_tables(n, _p(T))
+    gll, _ = quadrature.gauss_lobatto(n)
+    gq, gw = quadrature.gauss_legendre(n)
+    off = 0
+
+    def take(k):
+        nonlocal off
+        out = T[off:off + k]
+        off += k
+        return out
+    B, Dg, w, dl, M1, G, hat, g, S1 = (take(n * n), take(n * n), take(n), take(2 * n), take(n * n), take(n * n),
+                                       take(2 * n), take(n), take(n * n))
+    tol = 1e-12 * n ** 2
+    assert np.abs(B.reshape(n, n) - quadrature.lagrange_values(gll, gq)).max() < tol
+    assert np.abs(G.reshape(n, n) - quadrature.lagrange_derivatives(gll, gq)).max() < tol * n
+    assert np.abs(Dg.reshape(n, n) - quadrature.lagrange_derivatives(gq, gq)).max() < tol * n
+    assert np.abs(dl.reshape(2, n) - quadrature.lagrange_derivatives(gll, np.array([0.0, 1.0]))).max() < tol * n
+    assert np.abs(w - gw).max() < 1e-15 and np.abs(g - gq).max() < 1e-15
+    assert np.abs(hat.reshape(2, n) - np.stack([1 - gll, gll])).max() < 1e-15
+    fx, fw = quadrature.gauss_legendre(n + 3)
+    V, Vd = quadrature.lagrange_values(gll, fx), quadrature.lagrange_derivatives(gll, fx)
+    assert np.abs(M1.reshape(n, n) - V.T @ (fw[:, None] * V)).max() < tol
+    assert np.abs(S1.reshape(n, n) - Vd.T @ (fw[:, None] * Vd)).max() < tol * n * n
