@@ -71,6 +71,18 @@ void shim_quadrature_points(int nx, int ny, int nz, int p, const double* h, doub
   dgmg::quadrature_points_host(mesh(nx, ny, nz, p, h, bc, &one, 1, nullptr, nullptr, 1.25, nullptr), vol, face);
 }
 
+// In-place inverse of the n x n row-major A (the coarsest AMG solve);
+// returns 0 if A is singular.
+int shim_dense_inverse(int n, double* A) {
+  std::vector<double> a(A, A + (long long)n * n);
+  if (!dgmg::dense_inverse(n, a)) return 0;
+  std::memcpy(A, a.data(), a.size() * sizeof(double));
+  return 1;
+}
+
+// K(x) of the pointwise tensor at one point: (xx, yy, zz, xy, xz, yz).
+void shim_var_tensor(const double* var, const double* x, double* K) { dgmg::var_tensor(var, x, K); }
+
 // The per-order 1D tables the kernels read (5 n^2 + 6 n doubles).
 void shim_build_tables(int n, double* T) { dgmg::build_tables_into(n, T); }
 

@@ -247,3 +247,27 @@ def test_kernel_tables_match_the_oracle_basis(shim, n):
     V, Vd = quadrature.lagrange_values(gll, fx), quadrature.lagrange_derivatives(gll, fx)
     assert np.abs(M1.reshape(n, n) - V.T @ (fw[:, None] * V)).max() < tol
     assert np.abs(S1.reshape(n, n) - Vd.T @ (fw[:, None] * Vd)).max() < tol * n * n
+
+
+@pytest.mark.parametrize("n", [1, 7, 64])
+def test_coarsest_dense_inverse(shim, n):
+    rng = np.random.default_rng(n)
+    A = rng.normal(size=(n, n)) + n * np.eye(n)
+    Ai = np.ascontiguousarray(A.copy())
+    assert shim.shim_dense_inverse(n, _p(Ai)) == 1
+    assert np.abs(Ai @ A - np.eye(n)).max() < 1e-12
+    S = np.ascontiguousarray(np.outer(np.arange(1.0, n + 1), np.ones(n)))   # rank one
+    if n > 1:
+        assert shim.shim_dense_inverse(n, _p(S)) == 0
+
+
+def test_pointwise_tensor(shim):
+    """K(x) = sum_k (p0_k + p2_k x_k^2) n_k n_k^T (Sec. 4.2) at a few points."""
+    var = np.ascontiguousarray(np.concatenate([np.asarray(inputs.VARK_BASIS).reshape(-1), inputs.VARK_P0,
+                                               inputs.VARK_P2, [1e-8]]))
+    for x in ([0.1, 0.7, 0.3], [1.0, 0.0, 0.5], [0.25, 0.5, 0.75]):
+        K6 = np.zeros(6)
+        shim.shim_var_tensor(_p(var), _p(np.array(x, dtype=np.float64)), _p(K6))
+        K = inputs.vark_tensor(np.array(x))
+        ref = [K[0, 0], K[1, 1], K[2, 2], K[0, 1], K[0, 2], K[1, 2]]
+        assert np.abs(K6 - ref).max() < 1e-14 * np.abs(K).max()
