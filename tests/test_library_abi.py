@@ -91,3 +91,54 @@ def test_every_declaration_is_documented():
         while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
             j -= 1                      # continuation lines of the neighbouring declaration
         assert j >= 0 and lines[j].rstrip().endswith("*/"), m.group(1)
+
+
+def _header_prototypes():
+    """{name: (return type, [parameter types])} of the functions the header declares."""
+    import re
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "dgmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(dgmg_status|const char\s*\*|void)\s+(dgmg_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = []
+        for prm in m.group(3).split(","):
+            prm = " ".join(prm.split())
+            if prm in ("", "void"):
+                continue
+            prm = re.sub(r"\s*\[\d*\]$", "*", re.sub(r"\s+[A-Za-z_][A-Za-z0-9_]*(\s*\[\d*\])?$",
+                                                   lambda q: "*" if q.group(1) else "", prm))
+            params.append(prm.replace(" *", "*"))
+        out[m.group(2)] = (" ".join(m.group(1).split()), params)
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature in the binding has the header's arity and, per
+    argument, a ctypes type of the same kind (pointer, int/enum, double,
+    long long pointer), so no argument is passed with the wrong width."""
+    protos = _header_prototypes()
+    assert set(protos) == set(dgmg._SIG)
+    ints = {"int", "dgmg_prec", "dgmg_status"}
+    for name, (res, args) in dgmg._SIG.items():
+        ret, params = protos[name]
+        assert len(params) == len(args), name
+        if ret == "dgmg_status":
+            assert res is ctypes.c_int, name
+        elif ret == "void":
+            assert res is None, name
+        else:
+            assert res is ctypes.c_char_p, name
+        for c, a in zip(params, args):
+            base = c.replace("const ", "")
+            if base.endswith("*"):
+                assert a is ctypes.c_void_p or issubclass(a, ctypes._Pointer), (name, c)
+                if base == "long long*":
+                    assert a._type_ is ctypes.c_longlong, (name, c)
+                if base == "int*" and a is not ctypes.c_void_p:
+                    assert a._type_ is ctypes.c_int, (name, c)
+            elif base in ints:
+                assert a is ctypes.c_int, (name, c)
+            elif base == "double":
+                assert a is ctypes.c_double, (name, c)
+            else:
+                raise AssertionError((name, c))
