@@ -142,3 +142,17 @@ def test_binding_signatures_match_the_header():
                 assert a is ctypes.c_double, (name, c)
             else:
                 raise AssertionError((name, c))
+
+
+def test_binding_fails_loudly_without_the_library_or_a_gpu_tensor(monkeypatch, tmp_path):
+    """No CPU fallback: a missing library raises instead of computing
+    anything, and host tensors are refused where device pointers are due."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(dgmg, "_lib", None)
+    monkeypatch.setattr(dgmg._build, "LIB", str(tmp_path / "missing" / "libdgmg.so"))
+    with pytest.raises(dgmg.DgmgError):
+        dgmg.load(build_if_missing=False)
+    with pytest.raises(dgmg.DgmgError, match="CUDA tensor"):
+        dgmg._ptr(torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(dgmg.DgmgError, match="dtype"):
+        dgmg._prec(torch.zeros(4, dtype=torch.int32))
