@@ -210,25 +210,37 @@ std::vector<double> q1_stencil(const HostMesh& m) {
       }
     }
   };
-  // Without advection the element matrix is sum_d K_d R_d + c R_m with the
-  // reference matrices R_d = int grad_d phi_b grad_d phi_a, R_m = int phi_b phi_a
-  // over the cell (integrated once with the same rule, exact for Q1).
+  // The volume part of the element matrix from reference integrals over one
+  // cell, taken once with the same rule (exact for these Q1 integrands):
+  // R_d[a][b] = int d_d phi_b d_d phi_a, R_m[a][b] = int phi_b phi_a and, for
+  // the trilinear advection field b = sum_v b_v phi_v, T_d[v][a][b] =
+  // int phi_v phi_b d_d phi_a; then A_e = sum_d K_d R_d + c R_m -
+  // sum_d sum_v b_{v,d} T_d[v].
   double Rd[3][8][8], Rm[8][8];
   std::memset(Rd, 0, sizeof(Rd));
   std::memset(Rm, 0, sizeof(Rm));
-  if (!m.b) {
-    for (int q3 = 0; q3 < nq; ++q3)
-      for (int q2 = 0; q2 < nq; ++q2)
-        for (int q1 = 0; q1 < nq; ++q1) {
-          const double xi[3] = {g2[q1], g2[q2], g2[q3]};
-          const double w = w2[q1] * w2[q2] * w2[q3] * J;
-          for (int a = 0; a < 8; ++a)
-            for (int b = 0; b < 8; ++b) {
-              Rm[a][b] += w * q1phi(b, xi) * q1phi(a, xi);
-              for (int d = 0; d < 3; ++d) Rd[d][a][b] += w * q1grad(b, xi, d, m.h) * q1grad(a, xi, d, m.h);
-            }
+  std::vector<double> Tb(m.b ? 3 * 8 * 64 : 0, 0.0);
+  for (int q3 = 0; q3 < nq; ++q3)
+    for (int q2 = 0; q2 < nq; ++q2)
+      for (int q1 = 0; q1 < nq; ++q1) {
+        const double xi[3] = {g2[q1], g2[q2], g2[q3]};
+        const double w = w2[q1] * w2[q2] * w2[q3] * J;
+        double phi[8], gr[8][3];
+        for (int k = 0; k < 8; ++k) {
+          phi[k] = q1phi(k, xi);
+          for (int d = 0; d < 3; ++d) gr[k][d] = q1grad(k, xi, d, m.h);
         }
-  }
+        for (int a = 0; a < 8; ++a)
+          for (int b = 0; b < 8; ++b) {
+            Rm[a][b] += w * phi[b] * phi[a];
+            for (int d = 0; d < 3; ++d) Rd[d][a][b] += w * gr[b][d] * gr[a][d];
+          }
+        if (m.b)
+          for (int d = 0; d < 3; ++d)
+            for (int v = 0; v < 8; ++v)
+              for (int a = 0; a < 8; ++a)
+                for (int b = 0; b < 8; ++b) Tb[((d * 8 + v) * 8 + a) * 8 + b] += w * phi[v] * phi[b] * gr[a][d];
+      }
   for (int cz = 0; cz < m.nz; ++cz)
     for (int cy = 0; cy < m.ny; ++cy)
       for (int cx = 0; cx < m.nx; ++cx) {
@@ -236,31 +248,17 @@ std::vector<double> q1_stencil(const HostMesh& m) {
         const double K[3] = {kval(m, c, 0), kval(m, c, 1), kval(m, c, 2)};
         const double cc = m.c ? m.c[c] : 0.0;
         double Ae[8][8];
-        std::memset(Ae, 0, sizeof(Ae));
-        if (!m.b) {
-          for (int a = 0; a < 8; ++a)
-            for (int b = 0; b < 8; ++b)
-              Ae[a][b] = K[0] * Rd[0][a][b] + K[1] * Rd[1][a][b] + K[2] * Rd[2][a][b] + cc * Rm[a][b];
-        }
-        for (int q3 = 0; q3 < (m.b ? nq : 0); ++q3)
-          for (int q2 = 0; q2 < nq; ++q2)
-            for (int q1 = 0; q1 < nq; ++q1) {
-              const double xi[3] = {g2[q1], g2[q2], g2[q3]};
-              const double w = w2[q1] * w2[q2] * w2[q3] * J;
-              double bq[3];
-              b_at(m, cx, cy, cz, xi, bq);
-              double phi[8], gr[8][3];
-              for (int k = 0; k < 8; ++k) {
-                phi[k] = q1phi(k, xi);
-                for (int d = 0; d < 3; ++d) gr[k][d] = q1grad(k, xi, d, m.h);
-              }
-              for (int a = 0; a < 8; ++a)
-                for (int b = 0; b < 8; ++b) {
-                  double v = cc * phi[b] * phi[a];
-                  for (int d = 0; d < 3; ++d) v += K[d] * gr[b][d] * gr[a][d] - bq[d] * phi[b] * gr[a][d];
-                  Ae[a][b] += w * v;
-                }
+        for (int a = 0; a < 8; ++a)
+          for (int b = 0; b < 8; ++b)
+            Ae[a][b] = K[0] * Rd[0][a][b] + K[1] * Rd[1][a][b] + K[2] * Rd[2][a][b] + cc * Rm[a][b];
+        if (m.b)
+          for (int v = 0; v < 8; ++v) {
+            const double* bv = m.b + 3 * vid(m, cx + (v & 1), cy + ((v >> 1) & 1), cz + (v >> 2));
+            for (int d = 0; d < 3; ++d) {
+              const double* T = &Tb[(d * 8 + v) * 64];
+              for (int ab = 0; ab < 64; ++ab) Ae[ab >> 3][ab & 7] -= bv[d] * T[ab];
             }
+          }
         // Dirichlet faces of boundary cells (gamma from the DG degree p).
         const int cc3[3] = {cx, cy, cz};
         const int nn3[3] = {m.nx, m.ny, m.nz};
