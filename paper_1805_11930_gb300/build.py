@@ -40,7 +40,7 @@ def _jobs():
         jobs.append((obj, [nv] + common + ["-c", os.path.join(CSRC, name + ".cu"), "-o", obj]))
     gxx = shutil.which("g++") or "g++"
     obj = os.path.join(BUILD, "setup_host.o")
-    jobs.append((obj, [gxx, "-O2", "-fPIC", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-c",
+    jobs.append((obj, [gxx, "-O3", "-fPIC", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-c",
                        os.path.join(CSRC, "setup_host.cpp"), "-o", obj]))
     return nv, jobs
 

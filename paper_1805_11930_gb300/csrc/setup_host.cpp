@@ -433,10 +433,9 @@ bool dense_inverse(int n, std::vector<double>& A) {
       if (r == col) continue;
       const double f = A[(size_t)r * n + col];
       if (f == 0.0) continue;
-      for (int j = 0; j < n; ++j) {
-        A[(size_t)r * n + j] -= f * A[(size_t)col * n + j];
-        I[(size_t)r * n + j] -= f * I[(size_t)col * n + j];
-      }
+      // columns left of col are already eliminated in the pivot row of A
+      for (int j = col; j < n; ++j) A[(size_t)r * n + j] -= f * A[(size_t)col * n + j];
+      for (int j = 0; j < n; ++j) I[(size_t)r * n + j] -= f * I[(size_t)col * n + j];
     }
   }
   A.swap(I);

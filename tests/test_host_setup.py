@@ -29,7 +29,7 @@ def shim(tmp_path_factory):
     if cxx is None:
         pytest.skip("no host C++ compiler")
     so = str(tmp_path_factory.mktemp("shim") / "libhostshim.so")
-    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", os.path.join(HERE, "host_shim.cpp"),
+    subprocess.run([cxx, "-O3", "-std=c++17", "-shared", "-fPIC", os.path.join(HERE, "host_shim.cpp"),
                     os.path.join(CSRC, "setup_host.cpp"), "-I", CSRC, "-o", so], check=True)
     return ctypes.CDLL(so)
 
