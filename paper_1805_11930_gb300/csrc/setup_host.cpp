@@ -2,6 +2,7 @@
 // coarsening and the right-hand side l_h (Sec. 2.1, eq. rhs).
 #include "setup_host.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -475,29 +476,32 @@ void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp
   std::vector<double> t0(n3), t1(n3);
   for (long long c = 0; c < ncell; ++c) {
     double* out = rhs + c * n3;
-    for (int q = 0; q < n3; ++q) t0[q] = (f_qp ? f_qp[c * n3 + q] : 0.0) * W[q % n] * W[(q / n) % n] * W[q / n2] * J;
-    // B^T along x, y, z (quadrature point -> dof index)
-    for (int z = 0; z < n; ++z)
+    const double* fc = f_qp ? f_qp + c * n3 : nullptr;
+    for (int z = 0, q = 0; z < n; ++z)
       for (int y = 0; y < n; ++y)
-        for (int i = 0; i < n; ++i) {
-          double s = 0.0;
-          for (int q = 0; q < n; ++q) s += B[q * n + i] * t0[q + n * y + n2 * z];
-          t1[i + n * y + n2 * z] = s;
-        }
+        for (int x = 0; x < n; ++x, ++q) t0[q] = (fc ? fc[q] : 0.0) * W[x] * W[y] * W[z] * J;
+    // B^T along x, y, z (quadrature point -> dof index); each output sums its
+    // terms in quadrature-point order, with the output index innermost so
+    // that the loops vectorise
+    std::fill(t1.begin(), t1.end(), 0.0);
+    for (int r = 0; r < n2; ++r)                   // rows (y, z)
+      for (int q = 0; q < n; ++q) {
+        const double a = t0[q + n * r];
+        for (int i = 0; i < n; ++i) t1[i + n * r] += B[q * n + i] * a;
+      }
+    std::fill(t0.begin(), t0.end(), 0.0);
     for (int z = 0; z < n; ++z)
       for (int i = 0; i < n; ++i)
-        for (int x = 0; x < n; ++x) {
-          double s = 0.0;
-          for (int q = 0; q < n; ++q) s += B[q * n + i] * t1[x + n * q + n2 * z];
-          t0[x + n * i + n2 * z] = s;
+        for (int q = 0; q < n; ++q) {
+          const double b = B[q * n + i];
+          for (int x = 0; x < n; ++x) t0[x + n * i + n2 * z] += b * t1[x + n * q + n2 * z];
         }
+    for (int k = 0; k < n3; ++k) out[k] = 0.0;
     for (int i = 0; i < n; ++i)
-      for (int y = 0; y < n; ++y)
-        for (int x = 0; x < n; ++x) {
-          double s = 0.0;
-          for (int q = 0; q < n; ++q) s += B[q * n + i] * t0[x + n * y + n2 * q];
-          out[x + n * y + n2 * i] = s;
-        }
+      for (int q = 0; q < n; ++q) {
+        const double b = B[q * n + i];
+        for (int xy = 0; xy < n2; ++xy) out[xy + n2 * i] += b * t0[xy + n2 * q];
+      }
   }
   // boundary faces
   const double pen = m.alpha * m.p * (m.p + 2);
