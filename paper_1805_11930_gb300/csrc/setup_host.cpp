@@ -374,18 +374,24 @@ std::vector<double> coarsen_stencil(const std::vector<double>& st, int vx, int v
   cy = (vy + 1) / 2;
   cz = (vz + 1) / 2;
   std::vector<double> sc(27 * (size_t)cx * cy * cz, 0.0);
+  // Offset of stencil entry k = (dx+1) + 3 (dy+1) + 9 (dz+1) along each axis.
+  static const int DX[27] = {-1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1};
+  static const int DY[27] = {-1, -1, -1, 0, 0, 0, 1, 1, 1, -1, -1, -1, 0, 0, 0, 1, 1, 1, -1, -1, -1, 0, 0, 0, 1, 1, 1};
+  static const int DZ[27] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   for (int iz = 0; iz < vz; ++iz)
     for (int iy = 0; iy < vy; ++iy)
       for (int ix = 0; ix < vx; ++ix) {
         const long long i = ix + (long long)vx * (iy + (long long)vy * iz);
         const long long I = ix / 2 + (long long)cx * (iy / 2 + (long long)cy * (iz / 2));
+        const double* row = &st[27 * i];
+        double* out = &sc[27 * I];
         for (int k = 0; k < 27; ++k) {
-          const double a = st[27 * i + k];
+          const double a = row[k];
           if (a == 0.0) continue;
-          const int jx = ix + k % 3 - 1, jy = iy + (k / 3) % 3 - 1, jz = iz + k / 9 - 1;
+          const int jx = ix + DX[k], jy = iy + DY[k], jz = iz + DZ[k];
           if (jx < 0 || jy < 0 || jz < 0 || jx >= vx || jy >= vy || jz >= vz) continue;
-          const int ox = jx / 2 - ix / 2, oy = jy / 2 - iy / 2, oz = jz / 2 - iz / 2;
-          sc[27 * I + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] += a;
+          const int ox = (jx >> 1) - (ix >> 1), oy = (jy >> 1) - (iy >> 1), oz = (jz >> 1) - (iz >> 1);
+          out[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] += a;
         }
       }
   return sc;
