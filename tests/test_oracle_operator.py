@@ -359,3 +359,15 @@ def test_block_structure_matches_the_problem_size_count():
                     q[k] += s
                     nb.add(P.cell_index(*q))
         assert cols[c] == nb
+
+
+def test_l2_error_and_interpolation_closed_forms():
+    """The norm used by the convergence pins: ||0 - u||_L2 of
+    u = sin(pi x) sin(pi y) sin(pi z) on [0,1] x [0,2] x [0,1] is exactly
+    sqrt(1/8 * 2) = 1/2 (up to the rule's accuracy), and the nodal
+    interpolant of a polynomial in Q_p has zero error."""
+    P = dg.Problem(3, 4, 2, 1.0, 2.0, 1.0, 3, [0] * 6, np.ones(24))
+    u = lambda x, y, z: np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)   # noqa: E731
+    assert abs(P.l2_error(np.zeros(P.ndof), u, extra=4) - 0.5) < 1e-7
+    poly = lambda x, y, z: 1 + x ** 3 - 2 * x * y ** 2 * z ** 3 + y * z                 # noqa: E731
+    assert P.l2_error(P.interpolate(poly), poly) < 1e-13
