@@ -382,3 +382,18 @@ def test_fgmres_with_ssor_at_peclet_2000():
     assert it <= 25 and np.linalg.norm(F - A @ x) <= 1e-8 * np.linalg.norm(F) * 1.0001
     exact = spla.spsolve(A.tocsc(), F)
     assert np.abs(x - exact).max() < 1e-6 * np.abs(exact).max()
+
+
+def test_flexible_cg_equals_cg_for_a_fixed_preconditioner():
+    """With a fixed SPD preconditioner z_{k+1}.r_k = 0, so the Polak-Ribiere
+    beta of flexible CG equals the Fletcher-Reeves beta of CG: the two give
+    the same iterates up to rounding."""
+    P = small_problem(p=2, nc=(3, 3, 2), bc=(0,) * 6)
+    A = P.assemble().tocsr()
+    b = np.random.default_rng(12).normal(size=P.ndof)
+    dinv = 1.0 / A.diagonal()
+    x1, k1, h1 = solvers.cg(lambda v: A @ v, b, lambda v: dinv * v, rtol=1e-10)
+    x2, k2, h2 = solvers.cg(lambda v: A @ v, b, lambda v: dinv * v, rtol=1e-10, flexible=True)
+    assert abs(k1 - k2) <= 1
+    assert np.abs(x1 - x2).max() < 1e-8 * np.abs(x1).max()
+    assert np.allclose(h1[:20], h2[:20], rtol=1e-6)
