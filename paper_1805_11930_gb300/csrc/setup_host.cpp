@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 namespace dgmg {
@@ -479,35 +480,50 @@ void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp
   const double* dl = W + n;
   const double J = m.h[0] * m.h[1] * m.h[2];
   const long long ncell = (long long)m.nx * m.ny * m.nz;
-  std::vector<double> t0(n3), t1(n3);
-  for (long long c = 0; c < ncell; ++c) {
-    double* out = rhs + c * n3;
-    const double* fc = f_qp ? f_qp + c * n3 : nullptr;
-    for (int z = 0, q = 0; z < n; ++z)
-      for (int y = 0; y < n; ++y)
-        for (int x = 0; x < n; ++x, ++q) t0[q] = (fc ? fc[q] : 0.0) * W[x] * W[y] * W[z] * J;
-    // B^T along x, y, z (quadrature point -> dof index); each output sums its
-    // terms in quadrature-point order, with the output index innermost so
-    // that the loops vectorise
-    std::fill(t1.begin(), t1.end(), 0.0);
-    for (int r = 0; r < n2; ++r)                   // rows (y, z)
-      for (int q = 0; q < n; ++q) {
-        const double a = t0[q + n * r];
-        for (int i = 0; i < n; ++i) t1[i + n * r] += B[q * n + i] * a;
-      }
-    std::fill(t0.begin(), t0.end(), 0.0);
-    for (int z = 0; z < n; ++z)
+  // Volume term, cell by cell; the cells are independent, so large meshes
+  // are split over host threads (each cell's arithmetic is the same either way).
+  auto volume = [&](long long c0, long long c1) {
+    std::vector<double> t0(n3), t1(n3);
+    for (long long c = c0; c < c1; ++c) {
+      double* out = rhs + c * n3;
+      const double* fc = f_qp ? f_qp + c * n3 : nullptr;
+      for (int z = 0, q = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+          for (int x = 0; x < n; ++x, ++q) t0[q] = (fc ? fc[q] : 0.0) * W[x] * W[y] * W[z] * J;
+      // B^T along x, y, z (quadrature point -> dof index); each output sums its
+      // terms in quadrature-point order, with the output index innermost so
+      // that the loops vectorise
+      std::fill(t1.begin(), t1.end(), 0.0);
+      for (int r = 0; r < n2; ++r)                   // rows (y, z)
+        for (int q = 0; q < n; ++q) {
+          const double a = t0[q + n * r];
+          for (int i = 0; i < n; ++i) t1[i + n * r] += B[q * n + i] * a;
+        }
+      std::fill(t0.begin(), t0.end(), 0.0);
+      for (int z = 0; z < n; ++z)
+        for (int i = 0; i < n; ++i)
+          for (int q = 0; q < n; ++q) {
+            const double b = B[q * n + i];
+            for (int x = 0; x < n; ++x) t0[x + n * i + n2 * z] += b * t1[x + n * q + n2 * z];
+          }
+      for (int k = 0; k < n3; ++k) out[k] = 0.0;
       for (int i = 0; i < n; ++i)
         for (int q = 0; q < n; ++q) {
           const double b = B[q * n + i];
-          for (int x = 0; x < n; ++x) t0[x + n * i + n2 * z] += b * t1[x + n * q + n2 * z];
+          for (int xy = 0; xy < n2; ++xy) out[xy + n2 * i] += b * t0[xy + n2 * q];
         }
-    for (int k = 0; k < n3; ++k) out[k] = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int q = 0; q < n; ++q) {
-        const double b = B[q * n + i];
-        for (int xy = 0; xy < n2; ++xy) out[xy + n2 * i] += b * t0[xy + n2 * q];
-      }
+    }
+  };
+  const long long work = ncell * n3;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nthreads = (int)std::max<long long>(1, std::min<long long>({(long long)(hw ? hw : 1), 8LL, work / (1LL << 20)}));
+  if (nthreads == 1) {
+    volume(0, ncell);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+      pool.emplace_back(volume, ncell * t / nthreads, ncell * (t + 1) / nthreads);
+    for (auto& th : pool) th.join();
   }
   // boundary faces
   const double pen = m.alpha * m.p * (m.p + 2);
