@@ -271,3 +271,28 @@ def test_pointwise_tensor(shim):
         K = inputs.vark_tensor(np.array(x))
         ref = [K[0, 0], K[1, 1], K[2, 2], K[0, 1], K[0, 2], K[1, 2]]
         assert np.abs(K6 - ref).max() < 1e-14 * np.abs(K).max()
+
+
+def test_rhs_volume_term_on_a_mesh_split_over_threads(shim):
+    """A mesh large enough for the host right-hand side to split its cells
+    over threads (32 x 32 x 4 cells, Q7: 2^21 volume points): every sampled
+    cell, including the ones at the split, equals the definition
+    f_T(i) = sum_q w_q |J| f(x_q) psi_i(x_q) with the oracle's basis."""
+    nc, p = (32, 32, 4), 7
+    n = p + 1
+    ncell = int(np.prod(nc))
+    L = (1.0, 1.0, 0.125)
+    h = np.array(L) / np.array(nc)
+    fq = np.ascontiguousarray(np.random.default_rng(3).normal(size=ncell * n ** 3))
+    keep, args = _mesh_args(nc, L, p, [1] * 6, np.ones(ncell))
+    out = np.zeros(ncell * n ** 3)
+    shim.shim_rhs(*args, None, _p(fq), None, None, _p(out))
+    gll, _ = quadrature.gauss_lobatto(n)
+    gq, gw = quadrature.gauss_legendre(n)
+    Bv = quadrature.lagrange_values(gll, gq)                      # [q, i]
+    W3 = np.einsum("a,b,c->abc", gw, gw, gw) * np.prod(h)         # [qz, qy, qx]
+    for c in (0, 1, ncell // 4, ncell // 2 - 1, ncell // 2, ncell // 2 + 1, 3 * ncell // 4, ncell - 1):
+        F = fq[c * n ** 3:(c + 1) * n ** 3].reshape(n, n, n) * W3
+        ref = np.einsum("zyx,xi,yj,zk->kji", F, Bv, Bv, Bv)
+        got = out[c * n ** 3:(c + 1) * n ** 3].reshape(n, n, n)
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max(), c
