@@ -521,8 +521,14 @@ void assemble_rhs_host(const HostMesh& m, const double* f_qp, const double* g_qp
     volume(0, ncell);
   } else {
     std::vector<std::thread> pool;
-    for (int t = 0; t < nthreads; ++t)
-      pool.emplace_back(volume, ncell * t / nthreads, ncell * (t + 1) / nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+      const long long c0 = ncell * t / nthreads, c1 = ncell * (t + 1) / nthreads;
+      try {
+        pool.emplace_back(volume, c0, c1);
+      } catch (...) {   // no thread to be had: this range runs here
+        volume(c0, c1);
+      }
+    }
     for (auto& th : pool) th.join();
   }
   // boundary faces
