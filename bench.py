@@ -11,9 +11,10 @@ restriction, AMG cycle, prolongation, Krylov vector kernels.
              flushed between steps (a 256 MiB write outside the timed events)
   e2e        the same through the C ABI with host buffers: f copied in from
              pinned memory and u copied back, inside the timed region
-  roofline   the dominant kernel (the fused smoother, FP64), algorithmic FP64
-             operations per launch / its CUDA-event duration, against the
-             FP64 pipe peak (4 flop/clk/SM x 152 SMs x 2070 MHz)
+  roofline   the dominant kernel (the fused smoother, FP64): the FP64
+             operations it issues per launch / its CUDA-event duration in the
+             timed steps, against the FP64 pipe peak (4 flop/clk/SM x 152 SMs
+             x 2070 MHz); the survey's generic operation count beside it
   extra      apply GDOF/s (FP64 and FP32), the mixed-precision solve time
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgmg|reference]
@@ -196,20 +197,19 @@ def run_dgmg(args, rank, world, local_rank):
     sweeps = sum(x["sweeps"] for x in stats)
     zero = sum(x["zero_sweeps"] for x in stats)
     its = sum(x["inner_its_total"] for x in stats)
-    sm_flops = flops.algorithmic_smoother(n, ncell, sweeps, zero, its)
+    sm_gflops = flops.algorithmic_smoother(n, ncell, sweeps, zero, its)
     sm_kflops = flops.kernel_smoother(n, ncell, sweeps, zero, its)
-    ap_flops = flops.algorithmic_apply(n) * ncell * sum(x["applies"] for x in stats)
+    nap = sum(x["applies"] for x in stats)
+    ap_gflops = flops.algorithmic_apply(n) * ncell * nap
+    ap_kflops = flops.kernel_apply_full(n) * ncell * nap
     peak = fp64_peak_tflops()
     dominant = "smoother" if sm_ms >= ap_ms else "apply"
     if dominant == "smoother":
-        achieved = sm_flops / (sm_ms / 1e3) / 1e12
-        per_launch = sm_flops / max(sweeps, 1)
-        launch_ms = sm_ms / max(sweeps, 1)
+        k_flops, g_flops, k_ms, launches = sm_kflops, sm_gflops, sm_ms, max(sweeps, 1)
     else:
-        nap = sum(x["applies"] for x in stats)
-        achieved = ap_flops / (ap_ms / 1e3) / 1e12
-        per_launch = ap_flops / max(nap, 1)
-        launch_ms = ap_ms / max(nap, 1)
+        k_flops, g_flops, k_ms, launches = ap_kflops, ap_gflops, ap_ms, max(nap, 1)
+    achieved = k_flops / (k_ms / 1e3) / 1e12
+    achieved_generic = g_flops / (k_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_smooth_pcg<double>" if dominant == "smoother" else "k_apply<double>",
                 "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
@@ -217,15 +217,19 @@ def run_dgmg(args, rank, world, local_rank):
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one sweep with defect on this "
                                 "mesh (profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt); algorithmic bytes "
                                 "4 x 8 B x ndof = 131 MB, part of it served from L2",
-                "flops_per_launch": per_launch, "launch_ms": round(launch_ms, 4),
-                "frac_kernel_count": (round(sm_kflops / (sm_ms / 1e3) / 1e12 / peak, 4)
-                                      if dominant == "smoother" else None),
-                "kernel_count_note": "flops the kernel issues (Kronecker block apply 16 n^4 per inner iteration, "
-                                     "full apply 16 n^4 + 84 n^3 + 120 n^2 per defect, 13 n^3 vector work) over "
-                                     "the same time and peak",
-                "flops_note": "algorithmic: (32 n^4 + 120 n^3) per cell per apply, one apply per defect and per "
-                              "inner iteration",
-                "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x sm_max_mhz (derived, nominal 1.25 TFLOP/s)",
+                "flops_per_launch": k_flops / launches, "launch_ms": round(k_ms / launches, 4),
+                "launches": launches,
+                "flops_note": "FP64 flops the kernel issues, an FMA counted as 2 (flops.kernel_smoother / "
+                              "kernel_apply_full): per inner iteration the factored block apply and the PCG vector "
+                              "work, per defect the factored full operator; timed by CUDA events around every "
+                              "launch on the solve's stream inside the timed steps",
+                "achieved_generic_count": round(achieved_generic, 4),
+                "frac_generic_count": round(achieved_generic / peak, 4),
+                "generic_count_note": "the survey's generic count (32 n^4 + 120 n^3 per cell per apply, one apply "
+                                      "per defect and per inner iteration) over the same time; above 1 because the "
+                                      "kernels do the same operator with fewer operations",
+                "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x sm_max_mhz (derived from the nominal "
+                             "1.25 TFLOP/s; no measured FP64 peak in MEASURED_PEAKS.json)",
                 "time_share": {k: (round(sum(x[key] for x in stats) / total_ms, 3) if world == 1 else None)
                                for k, key in (("smoother", "ms_smooth"), ("apply", "ms_apply"),
                                               ("transfer", "ms_transfer"), ("coarse", "ms_coarse"),
@@ -287,19 +291,24 @@ def run_dgmg(args, rank, world, local_rank):
     pmf32_ms, pmf32st = time_solve(dgmg.default_opts(inner=dgmg.INNER_DIRECT, smoother_prec=dgmg.FP32,
                                                      krylov=dgmg.KRYLOV_FCG))
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: the same solve options as
+    # the timed steps, the same L2 flush before each step (outside its timer),
+    # f copied in from pinned memory and u copied back inside it
     f_host = f.cpu().pin_memory()
     u_host = torch.empty(ndof, dtype=torch.float64).pin_memory()
     f_dev = torch.empty_like(f)
     barrier()
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         f_dev.copy_(f_host, non_blocking=True)
         u.zero_()
-        ctx.solve(f_dev, u, dgmg.default_opts())
+        ctx.solve(f_dev, u, opts)
         u_host.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+        e2e_s += time.perf_counter() - t0
     barrier()
     e2e_s = max_over_ranks(e2e_s, world, dev)
     e2e = {"value": round(job_throughput(ndof, args.steps, world, e2e_s * 1e3), 9), "unit": "GDOF/s",
@@ -411,13 +420,43 @@ def oracle_subprocess(repeats=1, n=CPU_SAMPLE["n"]):
     return d["samples"], d["desc"], d["parts"]
 
 
+def host_cpu():
+    """CPU model and logical core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"cpu_model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
+CORES_NOTE = ("the oracle runs on one core: its block-CSR product (scipy.sparse) and its per-cell dense solves "
+              "(numpy) are single-threaded, and it is timed as it stands, with BLAS threads pinned to 1")
+
+
 def cpu_baseline_subprocess(n=CPU_SAMPLE["n"]):
     """The cpu_baseline object of the GPU line: one oracle solve."""
     samples, desc, parts = oracle_subprocess(1, n)
+    host = host_cpu()
     if samples is None:
-        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc}
+        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc, **host,
+                "cores_note": CORES_NOTE}
     return {"value": round(samples[0][0] / 1e9, 9), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-            "sample": desc, "seconds": round(samples[0][1], 2), **parts}
+            "sample": desc, "seconds": round(samples[0][1], 2), **parts, **host, "cores_note": CORES_NOTE}
 
 
 def run_reference(args):
@@ -436,7 +475,8 @@ def run_reference(args):
             "steps": steps, "warmup": warm, "ms_per_step": round(secs / steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc, **parts},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": desc, **parts,
+                             **host_cpu(), "cores_note": CORES_NOTE},
             "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -84,7 +84,9 @@ using namespace dgmg;
 struct AmgLevel {
   int vx, vy, vz;
   long long n;
-  double omega = 2.0 / 3.0;  // damped-Jacobi weight 4 / (3 G), G the Gershgorin bound of D^-1 A
+  // damped-Jacobi weight, set by build_hier to 4 / (3 G), G the Gershgorin
+  // bound of D^-1 A (the initial value is never used)
+  double omega = 2.0 / 3.0;
   double* st = nullptr;
   double* dinv = nullptr;
   double* b = nullptr;

@@ -127,7 +127,8 @@ def test_restrict_prolong_and_coarse_matrix(name):
 @pytest.mark.parametrize("nc", [(7, 6, 5), (9, 8, 8)])
 def test_coarse_amg_cycle(nc):
     """Device AMG V-cycle equals the oracle's AMG (same aggregation,
-    Galerkin levels, Jacobi 2/3, dense coarsest solve)."""
+    Galerkin levels, damped Jacobi with the Gershgorin weight 4/(3G),
+    dense coarsest solve)."""
     rng = np.random.default_rng(8)
     w = custom(nc, (1, 1, 1), 2, [0] * 6, np.exp(rng.normal(size=int(np.prod(nc)))))
     P = oracle_problem(w)
