@@ -271,7 +271,9 @@ dgmg_status dgmg_coarse_matrix(const dgmg_ctx* ctx, double* stencil);
 
 /* u_hat = one aggregation-AMG V-cycle on A_hat from zero (Algorithm 1, AMG step):
  * 2x2x2 vertex aggregates, piecewise-constant transfer, Galerkin levels, one
- * pre- and post-sweep of Jacobi (2/3), dense solve below 512 unknowns.
+ * pre- and post-sweep of damped Jacobi with the per-level weight 4/(3G), G the
+ * Gershgorin bound max_i sum_j |a_ij|/|a_ii| of D^-1 A (2/3 for the isotropic
+ * Q1 Laplacian), dense solve below 512 unknowns.
  * r_hat, u_hat: device FP64 vertex vectors, distinct. */
 dgmg_status dgmg_coarse_cycle(dgmg_ctx* ctx, const double* r_hat, double* u_hat);
 
@@ -395,9 +397,12 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
 #define DGMG_NOALLOC_MAX_CELLS 131072
 
 /* r_hat = R r, the same restriction as dgmg_restrict, for callers that cannot
- * allocate device memory (code running under CUDA-graph capture, hosts that
- * own all device memory through their own pool, loops that must not block on
- * an allocator).  The paper has no counterpart: this is a deployment variant.
+ * allocate device memory: a host application that owns all device memory
+ * through its own pool and forbids other allocators, or a real-time loop that
+ * must not wait on cudaMalloc, which can synchronise the device.  Such callers
+ * cannot use dgmg_restrict, because creating a context and setting its
+ * coefficients allocate.  The paper has no counterpart: this is a deployment
+ * variant of the restriction of Sec. 2.2.2.
  *
  * No context is needed and nothing is allocated: the per-cell corner sums live
  * in a fixed file-scope device array of 8 * DGMG_NOALLOC_MAX_CELLS doubles
@@ -407,9 +412,12 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
  *   r: device DG vector of `prec` (ncell (p+1)^3 values, layout above);
  *   r_hat: device FP64 vertex vector ((nx+1)(ny+1)(nz+1) values), overwritten;
  *   cuda_stream: cudaStream_t of the current device (NULL = default stream).
- * The first call on a device sets it up (with that device current it copies
- * the 1D tables into constant memory and looks up the scratch array's device
- * address), synchronously; make that first call before any stream capture.
+ * The first call on a device sets it up, synchronously, with that device
+ * current: it copies the 1D tables into constant memory and looks up the
+ * scratch array's device address, then keeps both for the life of the
+ * process.  Calls on a device after a cudaDeviceReset of that device are not
+ * supported (the kept set-up is not redone).  Every corner sum a call reads
+ * was written earlier in the same call, so the scratch needs no clearing.
  * All calls on a device share the one scratch array: calls whose work may
  * overlap on the GPU (different streams without ordering) race and give wrong
  * results.  Returns DGMG_ERR_CUDA if a CUDA call fails. */

@@ -1,14 +1,14 @@
 // dgmg_restrict_noalloc: the DG -> Q1 restriction for callers that cannot
 // allocate device memory.
 //
-// Some callers may not call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured, a host that manages all device memory through its
-// own pool and forbids other allocators, or a real-time loop that must not
-// block on the allocator.  dgmg_restrict needs a context, and creating a
-// context (and setting its coefficients) allocates.  This entry point needs
-// neither: the caller passes the input and output vectors and the grid size,
-// and the per-cell corner sums live in a file-scope device array of fixed
-// size that every GPU loading this library holds until the process exits.
+// Some callers may not call cudaMalloc at all: a host that manages all device
+// memory through its own pool and forbids other allocators, or a real-time
+// loop that must not wait on the allocator (cudaMalloc can synchronise the
+// device).  dgmg_restrict needs a context, and creating a context (and
+// setting its coefficients) allocates.  This entry point needs neither: the
+// caller passes the input and output vectors and the grid size, and the
+// per-cell corner sums live in a file-scope device array of fixed size that
+// every GPU loading this library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
