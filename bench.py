@@ -41,11 +41,9 @@ FP64_FLOP_PER_CLK_SM = 4          # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz)
 SM_MAX_MHZ = 2070.0
 CPU_SAMPLE = dict(n=8, p=4)        # oracle sample: same workload family, 8^3 cells
 # DRAM bytes (read + write) of one k_smooth_pcg<double> launch on this mesh, from
-# the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt
-# (a sweep with defect, 1 warp per block; the block shape does not change the
-# DRAM traffic of this L2-resident working set); None while that capture
-# predates the kernel.
-SMOOTHER_TRAFFIC_BYTES = 102.615296e6 + 14.325504e6
+# the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt;
+# None while no capture of the current kernel exists.
+SMOOTHER_TRAFFIC_BYTES = 102.638080e6 + 14.657024e6
 
 
 def fp64_peak_tflops():

@@ -5,10 +5,12 @@ python -m paper_1805_11930_gb300.apply_sweep [--degrees 2,3,4,5,6] [--advection]
 Meshes sized to 30-300 MB per FP64 vector: 64^3 cells for p <= 3, 40^3 for
 p = 4..6 (log-normal K, Dirichlet).  For each p and precision: median
 CUDA-event time of dgmg_apply over 20 launches (an L2-sized buffer is
-written between launches), GDOF/s, the algorithmic rate (32 n^4 + 120 n^3
-flop per cell) as a fraction of the FP64 pipe peak (4 flop/clk/SM x 152 SMs
-x 2070 MHz; for df64, FP64 vectors in double-float arithmetic, as well) or of
-the measured FP32 FMA rate (75.6 TFLOP/s), and the HBM
+written between launches), GDOF/s, the rate of the flops the kernel issues
+(flops.kernel_apply_full: the factored form in FP64, the Kronecker volume
+term and line-form faces in FP32) as a fraction of the FP64 pipe peak
+(4 flop/clk/SM x 152 SMs x 2070 MHz; for df64, FP64 vectors in double-float
+arithmetic, as well) or of the measured FP32 FMA rate (75.6 TFLOP/s), the
+same for the algorithmic count (32 n^4 + 120 n^3 flop per cell), and the HBM
 rate of the compulsory traffic (read u, write v) as a fraction of the
 measured copy bandwidth.  One JSON line per (p, precision).
 
@@ -64,11 +66,14 @@ def main():
                 ms.append(a.elapsed_time(b))
             t = statistics.median(ms) / 1e3
             fl = flops.algorithmic_apply(p + 1, value_terms=args.advection) * s["ncell"] / t
+            kfl = flops.kernel_apply_full(p + 1, advection=args.advection,
+                                          factored=name != "fp32") * s["ncell"] / t
             by = flops.hbm_bytes_apply(p + 1, s["ncell"], 4 if name == "fp32" else 8) / t
             print(json.dumps({"p": p, "mesh": n, "ndof": s["ndof"], "prec": name, "advection": args.advection,
                               "ms": round(t * 1e3, 4),
-                              "gdofs": round(s["ndof"] / t / 1e9, 3), "tflops": round(fl / 1e12, 3),
-                              "alu_frac": round(fl / peak, 3), "hbm_gbs": round(by / 1e9, 1),
+                              "gdofs": round(s["ndof"] / t / 1e9, 3), "tflops": round(kfl / 1e12, 3),
+                              "alu_frac": round(kfl / peak, 3), "alu_frac_generic_count": round(fl / peak, 3),
+                              "hbm_gbs": round(by / 1e9, 1),
                               "hbm_frac": round(by / 1e9 / HBM_GBS, 4)}), flush=True)
         ctx.close()
 

@@ -27,6 +27,7 @@
 //          (Sec. 3.2, eq. block_diag_apply).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -60,6 +61,10 @@ struct Tab {
   T hat[2][N];
   T gq[N];
   T S1[N][N];
+  // Derived on the host from M1, S1, dl for the factored operator (below):
+  T MIS[N][N];    // M^-1 S
+  T mie[2][N];    // M^-1 e_0, M^-1 e_{n-1} (columns 0 and n-1 of M^-1)
+  T midl[2][N];   // M^-1 dl_0, M^-1 dl_1
 };
 
 __constant__ Tab<double> c_tab_d;
@@ -367,24 +372,14 @@ __device__ __forceinline__ void block_matrices(const MeshParams& mp, T* Am, cons
   __syncwarp();
 }
 
-// Element-per-lane variant of the contractions for FP64 and double-float:
-// lane work items are the outputs (cell, line, i) instead of whole lines, so
-// that all 32 lanes stay busy when n^2 lines per cell do not fill the warp
-// (n = 5: 25 lines -> 78 % of the lanes, 125 outputs -> 98 %).  Each output
-// reads its line (n shared-memory loads) and a row of A from shared memory;
-// that costs more load instructions than the line form, which the FP64 pipe
-// can afford (it is the bound) but the FP32 kernels cannot (they are bound by
+// Element-per-lane contraction (FP64 and double-float kernels): lane work
+// items are the outputs (cell, line, i) instead of whole lines, so that all 32
+// lanes stay busy when n^2 lines per cell do not fill the warp (n = 5: 25
+// lines -> 78 % of the lanes, 125 outputs -> 98 %).  Each output reads its
+// line (n shared-memory loads) and a row of A from shared memory; that costs
+// more load instructions than the line form, which the FP64 pipe can afford
+// (it is the bound) but the FP32 kernels cannot (they are bound by
 // shared-memory instructions), so FP32 keeps the line form.
-constexpr int kLinePasses = (LINES + 31) / 32;
-constexpr int kElemPasses = (VEC + 31) / 32;
-// use the element form where it fills the lanes markedly better
-constexpr bool kElemForm = kElemPasses * LINES * 20 < kLinePasses * VEC * 19;
-
-// The b = 0 volume term in element form as well (FP64 and double-float): the
-// same Kronecker sequence with the volume-only 1D matrices.
-template <typename T, bool ADV>
-__host__ __device__ constexpr bool volume_elem() { return !ADV && kElemForm && !std::is_same<T, float>::value; }
-
 template <int D, bool ACC, typename T>
 __device__ __forceinline__ void contract_e(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ Am,
                                            int cstride, int lane, const unsigned char* act) {
@@ -414,28 +409,6 @@ __device__ __forceinline__ void contract_e(const T* __restrict__ in, T* __restri
   }
 }
 
-// block_kron with element work items; M1s: the 1D mass matrix in shared memory.
-template <typename T>
-__device__ __forceinline__ void block_kron_e(const T* X, T* Y, T* S0, T* S1, const T* Am, const T* M1s, int lane,
-                                             const unsigned char* act) {
-  contract_e<2, false>(X, S0, M1s, 0, lane, act);               // a = M_z u
-  __syncwarp();
-  contract_e<1, false>(S0, S1, M1s, 0, lane, act);              // b = M_y a
-  __syncwarp();
-  contract_e<0, false>(S1, Y, Am, 3 * N2, lane, act);           // Y = A_x b
-  __syncwarp();
-  contract_e<0, false>(S0, S1, M1s, 0, lane, act);              // c = M_x a
-  __syncwarp();
-  contract_e<1, true>(S1, Y, Am + N2, 3 * N2, lane, act);       // Y += A_y c
-  __syncwarp();
-  contract_e<0, false>(X, S0, M1s, 0, lane, act);               // e = M_x u
-  __syncwarp();
-  contract_e<1, false>(S0, S1, M1s, 0, lane, act);              // f = M_y e
-  __syncwarp();
-  contract_e<2, true>(S1, Y, Am + 2 * N2, 3 * N2, lane, act);   // Y += A_z f
-  __syncwarp();
-}
-
 // Q = D_T P for b = 0 by the Kronecker form above: 8 contractions, no face
 // passes (the face terms are inside A_d).
 template <typename T>
@@ -459,6 +432,200 @@ __device__ __forceinline__ void block_kron(const T* X, T* Y, T* S0, T* S1, const
   contract_cell<2, true>(S1, Y, Am, lane, act);        // Y += A_z f
   __syncwarp();
 }
+
+// ---------------------------------------------------------------------------
+// Factored form of the b = 0 operator (FP64 and double-float kernels).
+//
+// With K diagonal and constant per affine axis-aligned cell, the block is a
+// sum of Kronecker products D_T = sum_d A_d (x)_d M (x) M (reading of the
+// block matrices above), and M (the 1D mass matrix of the GLL basis under the
+// Gauss rule) is symmetric positive definite, so
+//     D_T = (M (x) M (x) M) o sum_d (M^-1 A_d) x_d ,
+// with x_d the 1D product along axis d.  One fused pass applies the three
+// per-cell matrices Ah_d = M^-1 A_d to every element (3n multiply-adds), then
+// three passes apply M along z, y, x (3n): 6 n^4 multiply-adds per cell
+// instead of 8 n^4 for the eight-contraction sequence.  The neighbour terms of
+// the full operator enter the same way: a face term e_e (x) (M (x) M) q (or
+// dl_s (x) (M (x) M) q) equals (M (x) M (x) M)((M^-1 e_e) (x) q), so the
+// neighbour's face values are added before the mass passes, weighted by the
+// tabulated vectors M^-1 e_e and M^-1 dl_s, and need no contraction of their
+// own.  Same operator up to rounding (M has condition number below 20 for
+// n <= 9).
+
+// Mass matrix and the vectors M^-1 e_e, M^-1 dl_s in shared memory (their
+// index varies across the lanes, which constant memory would serialise):
+// M1s[i N + j] = M[i][j]; MVs = [mie_0 | mie_1 | midl_0 | midl_1].
+template <typename T>
+__device__ __forceinline__ void factor_tables(T* M1s, T* MVs, int lane) {
+  const Tab<T>& t = tab<T>();
+  for (int k = lane; k < N2; k += 32) M1s[k] = t.M1[k / N][k % N];
+  for (int k = lane; k < 4 * N; k += 32) {
+    const int q = k / N, i = k % N;
+    MVs[k] = q < 2 ? t.mie[q][i] : t.midl[q - 2][i];
+  }
+}
+
+// Ah_d = M^-1 A_d of every staged cell, 3 n^2 per cell (row-major; Ah_d[i][j]
+// multiplies x_j into z_i):
+//   M^-1 A_d = |J| K_d / h_d^2 M^-1 S + [d = 2] c |J| I
+//            + sum over the non-Neumann faces s of d of
+//              |F| [ ks ((M^-1 e_e) dl_s^T + (M^-1 dl_s) e_e^T) + gamma (M^-1 e_e) e_e^T ],
+// ks = -kap sg / h_d, e = end node of side s, sg = +-1 its outward sign.
+template <typename T>
+__device__ __forceinline__ void hat_matrices(const MeshParams& mp, T* Ah, const CellInfo<T>* ci,
+                                             const unsigned char* act, int lane) {
+  const Tab<T>& t = tab<T>();
+  for (int k = lane; k < CPW * 3 * N2; k += 32) {
+    const int cw = k / (3 * N2), r = k - cw * 3 * N2, d = r / N2, i = (r % N2) / N, j = r % N;
+    if (!act[cw]) continue;
+    T a = ci[cw].kd[d] * t.MIS[i][j];
+    if (d == 2 && i == j) a = a + ci[cw].cJ;
+    const T ih = Prec<T>::ih(mp, d);
+    for (int s = 0; s < 2; ++s) {
+      const int f = 2 * d + s;
+      if (ci[cw].kind[f] == 2) continue;
+      const int e = s ? N - 1 : 0;
+      const T ks = (s ? -ci[cw].kap[f] : ci[cw].kap[f]) * ih;
+      T fv = ks * t.mie[s][i] * t.dl[s][j];
+      if (j == e) fv = fma(ks, t.midl[s][i], fma(ci[cw].gam[f], t.mie[s][i], fv));
+      a = fma(ci[cw].jh[d], fv, a);
+    }
+    Ah[k] = a;
+  }
+}
+
+// The neighbour side of the interior faces, for the full operator: at face
+// point L of face f = 2d + s of cell slot cw, from the neighbour's trace
+// u_o = u_nb(end 1-s) and normal derivative dn_o = sg / h_d sum_j dl_{1-s}[j] u_nb(j),
+//   FS[cw][f][0][L] = |F| (-gamma u_o - kap dn_o),   FS[cw][f][1][L] = sg |F| / h_d kap u_o,
+// (zero on boundary faces): the parts of qv = gamma [[u]] - kap (dn + dn_o),
+// qdv = -kap [[u]] that the block D_T leaves out.  12 n^2 values per cell.
+template <typename T, typename G>
+__device__ __forceinline__ void neighbour_faces(T* FS, const G* __restrict__ gu, const MeshParams& mp, int lane,
+                                                const unsigned char* act, const CellInfo<T>* ci) {
+  const Tab<T>& t = tab<T>();
+  for (int it = lane; it < CPW * 6 * N2; it += 32) {
+    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2;
+    const int d = f >> 1, S = f & 1;
+    T qv = T(0), qd = T(0);
+    if (act[cw] && ci[cw].kind[f] == 0) {
+      const int a = L % N, b = L / N;
+      const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+      const int base = d == 0 ? N * a + N2 * b : (d == 1 ? a + N2 * b : a + N * b);
+      const G* xo = gu + ci[cw].nb[f] * N3 + base;
+      const T tout = T(xo[(S ? 0 : N - 1) * st]);
+      T dno;
+      if constexpr (std::is_same<T, df>::value) {
+        df_acc acc;
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc.add_prod(t.dl[1 - S][j], T(xo[j * st]));
+        dno = acc.value();
+      } else {
+        dno = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], T(xo[j * st]), dno);
+      }
+      const T ih = Prec<T>::ih(mp, d), area = Prec<T>::area(mp, d);
+      const T sga = S ? area : -area;
+      dno = dno * (S ? ih : -ih);
+      qv = -area * fma(ci[cw].gam[f], tout, ci[cw].kap[f] * dno);
+      qd = sga * ih * (ci[cw].kap[f] * tout);
+    }
+    T* fs = FS + (cw * 6 + f) * 2 * N2;
+    fs[L] = qv;
+    fs[N2 + L] = qd;
+  }
+}
+
+// Z = sum_d Ah_d x_d X for the active cells, plus (FULL) the neighbour face
+// values weighted by M^-1 e_e and M^-1 dl_s along each face normal.
+template <bool FULL, typename T>
+__device__ __forceinline__ void hat_pass(const T* X, T* Z, const T* Ah, const T* MVs, const T* FS, int lane,
+                                         const unsigned char* act) {
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    if (!act[cw]) continue;
+    const int r = e - cw * N3;
+    const int i0 = r % N, i1 = (r / N) % N, i2 = r / N2;
+    const T* x = X + cw * N3;
+    const T* ax = Ah + cw * 3 * N2 + i0 * N;
+    const T* ay = Ah + cw * 3 * N2 + N2 + i1 * N;
+    const T* az = Ah + cw * 3 * N2 + 2 * N2 + i2 * N;
+    const int bx = r - i0, by = r - i1 * N, bz = r - i2 * N2;
+    const T* fs = FS + cw * 12 * N2;
+    const int L0 = i1 + N * i2, L1 = i0 + N * i2, L2 = i0 + N * i1;
+    T s;
+    if constexpr (std::is_same<T, df>::value) {
+      df_acc acc;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.add_prod(ax[j], x[bx + j]);
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.add_prod(ay[j], x[by + j * N]);
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.add_prod(az[j], x[bz + j * N2]);
+      if (FULL) {
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          acc.add_prod(MVs[sd * N + i0], fs[(0 + sd) * 2 * N2 + L0]);
+          acc.add_prod(MVs[2 * N + sd * N + i0], fs[(0 + sd) * 2 * N2 + N2 + L0]);
+          acc.add_prod(MVs[sd * N + i1], fs[(2 + sd) * 2 * N2 + L1]);
+          acc.add_prod(MVs[2 * N + sd * N + i1], fs[(2 + sd) * 2 * N2 + N2 + L1]);
+          acc.add_prod(MVs[sd * N + i2], fs[(4 + sd) * 2 * N2 + L2]);
+          acc.add_prod(MVs[2 * N + sd * N + i2], fs[(4 + sd) * 2 * N2 + N2 + L2]);
+        }
+      }
+      s = acc.value();
+    } else {
+      s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(ax[j], x[bx + j], s);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(ay[j], x[by + j * N], s);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(az[j], x[bz + j * N2], s);
+      if (FULL) {
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          s = fma(MVs[sd * N + i0], fs[(0 + sd) * 2 * N2 + L0], s);
+          s = fma(MVs[2 * N + sd * N + i0], fs[(0 + sd) * 2 * N2 + N2 + L0], s);
+          s = fma(MVs[sd * N + i1], fs[(2 + sd) * 2 * N2 + L1], s);
+          s = fma(MVs[2 * N + sd * N + i1], fs[(2 + sd) * 2 * N2 + N2 + L1], s);
+          s = fma(MVs[sd * N + i2], fs[(4 + sd) * 2 * N2 + L2], s);
+          s = fma(MVs[2 * N + sd * N + i2], fs[(4 + sd) * 2 * N2 + N2 + L2], s);
+        }
+      }
+    }
+    Z[e] = s;
+  }
+}
+
+// Y = A X (FULL, neighbour values from gu) or D_T X in the factored form;
+// S0, S1 scratch vectors, Ah, M1s, MVs, FS as above.  X and Y distinct from
+// S0 and S1.
+template <bool FULL, typename T, typename G>
+__device__ __forceinline__ void factored_apply(const T* X, T* Y, T* S0, T* S1, const T* Ah, const T* M1s,
+                                               const T* MVs, T* FS, const G* gu, const MeshParams& mp, int lane,
+                                               const unsigned char* act, const CellInfo<T>* ci) {
+  if (FULL) {
+    neighbour_faces(FS, gu, mp, lane, act, ci);
+    __syncwarp();
+  }
+  hat_pass<FULL>(X, S0, Ah, MVs, FS, lane, act);
+  __syncwarp();
+  contract_e<2, false>(S0, S1, M1s, 0, lane, act);
+  __syncwarp();
+  contract_e<1, false>(S1, S0, M1s, 0, lane, act);
+  __syncwarp();
+  contract_e<0, false>(S0, Y, M1s, 0, lane, act);
+  __syncwarp();
+}
+
+// Shared values per warp of the factored form: Ah (3 CPW n^2), M1s (n^2),
+// MVs (4 n), FS (12 CPW n^2).
+constexpr int kFactorExtra = 3 * CPW * N2 + N2 + 4 * N + 12 * CPW * N2;
+
+template <typename T, bool ADV>
+__host__ __device__ constexpr bool use_factored() { return !ADV && !std::is_same<T, float>::value; }
 
 // Y = A^v X for the warp's cells.  S0, S1 scratch.
 //  b = 0: K and c are constant per cell and the cell affine, so the volume
@@ -741,105 +908,6 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
   __syncwarp();
 }
 
-// The diffusion and penalty terms of all six faces with element work items
-// (one cell per warp, FP64, orders where the line layout leaves lanes idle):
-// the same quantities as faces_diffusion_dir, computed
-// for the three directions at once so that the items fill the warp —
-//   1. per (direction, face point, side): the face values qv = gamma [[u]]
-//      - kap (d_n u + d_n u_nb), qdv = -kap [[u]] (6 n^2 items);
-//   2. M along the first tangential axis of every field (12 n^2 items);
-//   3. M along the second tangential axis (12 n^2 items);
-//   4. per element: the face-layer values and the normal-derivative test
-//      functions of the three directions added to Y (n^3 items, no element
-//      touched by two lanes).
-// FS: 24 n^2 scratch values; M1s: the mass matrix in shared memory.
-template <typename T, typename G>
-__device__ void faces_diffusion_e(const T* X, T* Y, T* FS, const T* M1s, const G* __restrict__ gu,
-                                  const MeshParams& mp, int lane, const unsigned char* act,
-                                  const CellInfo<T>* ci) {
-  static_assert(CPW == 1 || sizeof(T) == 0, "element-form faces need one cell per warp");
-  if (!act[0]) return;
-  const Tab<T>& t = tab<T>();
-  T* Fq = FS;              // [3][4][N2]
-  T* Fr = FS + 12 * N2;    // [3][4][N2]
-  // 1. face values
-  for (int it = lane; it < 6 * N2; it += 32) {
-    const int d = it / (2 * N2), r = it - d * 2 * N2, S = r / N2, L = r - S * N2;
-    const int a = L % N, b = L / N;
-    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
-    const int base = d == 0 ? N * a + N2 * b : (d == 1 ? a + N2 * b : a + N * b);
-    const int f = 2 * d + S;
-    const int kind = ci[0].kind[f];
-    T qv = T(0), qdv = T(0);
-    if (kind != 2) {
-      const T ih = Prec<T>::ih(mp, d);
-      const T sgn = S ? T(1) : T(-1);
-      T dn = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], X[base + j * st], dn);
-      dn *= sgn * ih;
-      const T xin = X[base + (S ? N - 1 : 0) * st];
-      T tout = T(0), dno = T(0);
-      if (kind == 0) {
-        const G* xo = gu + ci[0].nb[f] * N3 + base;
-        tout = T(xo[(S ? 0 : N - 1) * st]);
-#pragma unroll
-        for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], T(xo[j * st]), dno);
-        dno *= sgn * ih;
-      }
-      const T kap = ci[0].kap[f];
-      const T jmp = xin - tout;
-      qv = ci[0].gam[f] * jmp - kap * (dn + dno);
-      qdv = -kap * jmp;
-    }
-    Fq[(d * 4 + 2 * S) * N2 + L] = qv;
-    Fq[(d * 4 + 2 * S + 1) * N2 + L] = qdv;
-  }
-  __syncwarp();
-  // 2. M along the first tangential axis: Fr[L = a + N b] = sum_j M[a][j] Fq[j + N b]
-  for (int it = lane; it < 12 * N2; it += 32) {
-    const int df = it / N2, L = it - df * N2, a = L % N, b = L / N;
-    const T* src = Fq + df * N2 + N * b;
-    const T* m = M1s + a * N;
-    T acc = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc = fma(m[j], src[j], acc);
-    Fr[it] = acc;
-  }
-  __syncwarp();
-  // 3. M along the second tangential axis: Fq[L] = sum_j M[b][j] Fr[a + N j]
-  for (int it = lane; it < 12 * N2; it += 32) {
-    const int df = it / N2, L = it - df * N2, a = L % N, b = L / N;
-    const T* src = Fr + df * N2 + a;
-    const T* m = M1s + b * N;
-    T acc = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc = fma(m[j], src[j * N], acc);
-    Fq[it] = acc;
-  }
-  __syncwarp();
-  // 4. scatter: element (i0, i1, i2); for direction d its face point and its
-  // index along d
-  for (int e = lane; e < N3; e += 32) {
-    const int i0 = e % N, i1 = (e / N) % N, i2 = e / N2;
-    T y = Y[e];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int j = d == 0 ? i0 : (d == 1 ? i1 : i2);
-      const int L = d == 0 ? i1 + N * i2 : (d == 1 ? i0 + N * i2 : i0 + N * i1);
-      const T area = Prec<T>::area(mp, d), ih = Prec<T>::ih(mp, d);
-      const T* q = Fq + d * 4 * N2 + L;
-      const T d0 = -area * ih * q[N2];       // sgn = -1 on face 0
-      const T d1 = area * ih * q[3 * N2];
-      y = fma(t.dl[0][j], d0, fma(t.dl[1][j], d1, y));
-      if (j == 0) y = fma(area, q[0], y);
-      if (j == N - 1) y = fma(area, q[2 * N2], y);
-    }
-    Y[e] = y;
-  }
-  __syncwarp();
-}
-
 // F0 must be followed by 4 * LINES values of scratch (F0, F1 and the
 // reduction area are contiguous in every kernel's shared-memory carve).
 template <bool FULL, bool ADV, typename T, typename G>
@@ -957,27 +1025,26 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
   T *F0, *F1, *red;
   CellInfo<T>* ci;
   unsigned char* act;
-  constexpr bool VE = volume_elem<T, ADV>();
-  // volume 1D matrices, the mass matrix and (full operator) the face scratch
-  constexpr bool FE = VE && FULL && std::is_same<T, double>::value;   // element-form faces
-  constexpr int XT = VE ? 3 * CPW * N2 + N2 + (FE ? 24 * N2 : 0) : 0;
-  T* Vm = nullptr;
-  carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Vm);
+  // FP64 / double-float with b = 0: the factored form (per-cell matrices,
+  // mass matrix, neighbour face values in the extra region)
+  constexpr bool FAC = use_factored<T, ADV>();
+  constexpr int XT = FAC ? kFactorExtra : 0;
+  T* Xt = nullptr;
+  carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Xt);
   T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
   stage_cells(mp, cell0, lane, ci, act);
   const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
   const G* ug = u + cell0 * N3;
   for (int e = lane; e < VEC; e += 32) X[e] = e < nval ? T(ug[e]) : T(0);
-  if constexpr (VE) {
-    T* M1s = Vm + 3 * CPW * N2;
-    block_matrices<false>(mp, Vm, ci, act, lane);
-    for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
+  if constexpr (FAC) {
+    T* Ah = Xt;
+    T* M1s = Ah + 3 * CPW * N2;
+    T* MVs = M1s + N2;
+    T* FS = MVs + 4 * N;
+    hat_matrices(mp, Ah, ci, act, lane);
+    factor_tables(M1s, MVs, lane);
     __syncwarp();
-    block_kron_e(X, Y, S0, S1, Vm, M1s, lane, act);
-    if constexpr (FE)
-      faces_diffusion_e(X, Y, M1s + N2, M1s, u, mp, lane, act, ci);
-    else
-      all_faces<FULL, ADV>(X, Y, F0, F1, u, mp, cell0, lane, act, ci);
+    factored_apply<FULL>(X, Y, S0, S1, Ah, M1s, MVs, FS, u, mp, lane, act, ci);
   } else {
     __syncwarp();
     volume<ADV>(X, Y, S0, S1, lane, ci, act, react);
@@ -1009,9 +1076,50 @@ __device__ __forceinline__ T cell_sum(T part, int lane, T* red) {
   }
 }
 
+// Two cell sums at once (the same summation order as cell_sum for each).
+template <typename T>
+__device__ __forceinline__ void cell_sum2(T& a, T& b, int lane, T* red) {
+  if (CPW == 1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += shfl_x(a, o);
+      b += shfl_x(b, o);
+    }
+  } else {
+    red[lane] = a;
+    red[LINES + lane] = b;
+    __syncwarp();
+    T sa = T(0), sb = T(0);
+    if (lane < LINES) {
+      const int c0 = (lane / N2) * N2;
+#pragma unroll
+      for (int k = 0; k < N2; ++k) {
+        sa += red[c0 + k];
+        sb += red[LINES + c0 + k];
+      }
+    }
+    __syncwarp();
+    a = sa;
+    b = sb;
+  }
+}
+
+// Extra shared values per warp of the inner-PCG smoother: the factored form's
+// region (FP64, double-float, b = 0), the per-cell 1D matrices of D_T (FP32,
+// b = 0), nothing with advection.
+template <typename T, bool ADV>
+__host__ __device__ constexpr int smooth_extra() {
+  return use_factored<T, ADV>() ? kFactorExtra : (ADV ? 0 : 3 * CPW * N2);
+}
+
 // Block-Jacobi sweep with inner PCG (Algorithm 2; inner solve Sec. 2.2.1).
-// Each lane owns the z-lines L = lane + 32k (elements base + N2 iz) for the
-// pointwise vector operations, so all of its elements belong to one cell.
+// Per cell: the defect d = f - A u_old (skipped from u = 0), PCG on D_T delta = d
+// with the preconditioner 1/diag(D_T) from delta_0 = 0, u_new = u_old + omega delta.
+// The block is applied in the factored form (FP64, double-float, b = 0), by
+// the eight Kronecker contractions (FP32, b = 0), or at the Gauss points
+// (advection).  With several cells per warp each lane owns one z-line of its
+// cell for the pointwise vector operations; with one cell per warp every lane
+// takes elements lane, lane + 32, ... (all 32 lanes busy).
 template <typename T, bool ADV, typename G = typename Store<T>::type>
 __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __restrict__ f,
                                                          const G* uold, G* unew, const G* __restrict__ diag,
@@ -1025,31 +1133,28 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  // b = 0: an extra region holds the per-cell 1D matrices of D_T, the mass
-  // matrix and (element form) the volume-only 1D matrices of the defect
-  constexpr bool VE = volume_elem<T, ADV>();
-  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2 + (VE ? 3 * CPW * N2 : 0);
+  constexpr bool FAC = use_factored<T, ADV>();
+  constexpr int XT = smooth_extra<T, ADV>();
   T* vec[6];
-  T* Am = nullptr;
-  carve(smem + warp * WarpMem<T>::bytes(6, XT), 6, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Am);
+  T* Xt = nullptr;
+  carve(smem + warp * WarpMem<T>::bytes(6, XT), 6, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Xt);
   T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3], *R = vec[4], *DL = vec[5];
   const bool react = mp.c != nullptr;
   const bool zero = uold == nullptr;   // first sweep from u = 0: no defect apply
   slot_cells(mp, color, s0, lane, cid);
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
-  T* M1s = Am + 3 * CPW * N2;   // the mass matrix next to the per-cell matrices
-  T* Vm = M1s + N2;
-  if constexpr (!ADV) {
-    block_matrices(mp, Am, ci, act, lane);
-    if constexpr (VE) block_matrices<false>(mp, Vm, ci, act, lane);
-    for (int k = lane; k < N2; k += 32) M1s[k] = tab<T>().M1[k / N][k % N];
+  T* Ah = Xt;                     // FAC: M^-1 A_d; FP32: A_d (3 n^2 per cell)
+  T* M1s = Ah + 3 * CPW * N2;     // FAC only: mass matrix, M^-1 e_e, M^-1 dl_s, face values
+  T* MVs = M1s + N2;
+  T* FS = MVs + 4 * N;
+  if constexpr (FAC) {
+    hat_matrices(mp, Ah, ci, act, lane);
+    factor_tables(M1s, MVs, lane);
     __syncwarp();
+  } else if constexpr (!ADV) {
+    block_matrices(mp, Ah, ci, act, lane);
   }
-  // The lane's cell slot and its elements for the per-cell vector work: with
-  // one cell per warp every lane takes elements lane, lane + 32, ... (all 32
-  // lanes busy); with several cells each lane owns one z-line of its cell
-  // (cell_sum groups lanes by cell).
   const int mycw = CPW == 1 ? 0 : (lane < LINES ? lane / N2 : -1);
   const bool mine = mycw >= 0 && act[mycw];
   const bool lead = CPW == 1 ? lane == 0 : (lane < LINES && lane % N2 == 0);
@@ -1071,15 +1176,8 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
     __syncwarp();
-    if constexpr (VE) {
-      block_kron_e(P, Q, S0, S1, Vm, M1s, lane, act);
-      // face scratch: S0, S1, R, DL and the face / reduction area are free
-      // here and contiguous (4 VEC + 5 LINES >= 24 n^2 for these orders)
-      static_assert(!VE || 4 * VEC + 5 * LINES >= 24 * N2, "face scratch");
-      if constexpr (std::is_same<T, double>::value)
-        faces_diffusion_e(P, Q, S0, M1s, uold, mp, lane, act, ci);
-      else   // double-float: the line form is faster (measured)
-        all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+    if constexpr (FAC) {
+      factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, FS, uold, mp, lane, act, ci);
     } else {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
@@ -1096,8 +1194,9 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       prr = fma(r, r, prr);
       prz = fma(r, z, prz);
     });
-  const T rr0 = cell_sum(prr, lane, red);
-  T rz = cell_sum(prz, lane, red);
+  cell_sum2(prr, prz, lane, red);
+  const T rr0 = prr;
+  T rz = prz;
   // The inner solve works on d / ||d|| (and scales the correction back):
   // FP32 products of a tiny defect would otherwise lose precision in the
   // subnormal range.  The stopping test ||r|| <= eps ||d|| becomes
@@ -1117,20 +1216,23 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
     if (mycw >= 0) act[mycw] = (live && it < maxit) ? 1 : 0;
     __syncwarp();
     const bool run = live && it < maxit;
+    // Q = D_T P
     if constexpr (ADV) {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
-    } else if constexpr (kElemForm && !std::is_same<T, float>::value) {
-      block_kron_e(P, Q, S0, S1, Am, M1s, lane, act);
+    } else if constexpr (FAC) {
+      factored_apply<false>(P, Q, S0, S1, Ah, M1s, MVs, FS, (const G*)nullptr, mp, lane, act, ci);
     } else {
-      block_kron(P, Q, S0, S1, Am, lane, act);
+      block_kron(P, Q, S0, S1, Ah, lane, act);
     }
     T ppq = T(0);
     if (run) my_elems([&](int e) { ppq = fma(P[e], Q[e], ppq); });
     const T pq = cell_sum(ppq, lane, red);
     bool upd = run && pq > T(0);
     if (run && !upd) live = false;   // breakdown: stop this cell
-    T prr2 = T(0);
+    // delta += alpha p, r -= alpha q, and with the new r both (r, r) and
+    // (r, z), z = r / diag (kept in S0 for the direction update)
+    T prr2 = T(0), prz2 = T(0);
     if (upd) {
       const T alpha = rz / pq;
       my_elems([&](int e) {
@@ -1138,26 +1240,21 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
         const T r = fma(-alpha, Q[e], R[e]);
         R[e] = r;
         prr2 = fma(r, r, prr2);
+        const T z = r * T(diag[gb + e]);
+        S0[e] = z;
+        prz2 = fma(r, z, prz2);
       });
       ++it;
     }
-    const T rr = cell_sum(prr2, lane, red);
-    if (upd && rr <= thr2) {
+    cell_sum2(prr2, prz2, lane, red);
+    if (upd && prr2 <= thr2) {
       live = false;
       upd = false;
     }
     if (upd && it >= maxit) upd = false;
-    T prz2 = T(0);
-    if (upd)
-      my_elems([&](int e) {
-        const T z = R[e] * T(diag[gb + e]);
-        S0[e] = z;
-        prz2 = fma(R[e], z, prz2);
-      });
-    const T rzn = cell_sum(prz2, lane, red);
     if (upd) {
-      const T beta = rzn / rz;
-      rz = rzn;
+      const T beta = prz2 / rz;
+      rz = prz2;
       my_elems([&](int e) { P[e] = fma(beta, P[e], S0[e]); });
     }
     __syncwarp();
@@ -1237,7 +1334,10 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  carve(smem + warp * WarpMem<T>::bytes(4), 4, vec, &F0, &F1, &red, &ci, &act, &cid);
+  constexpr bool FAC = use_factored<T, ADV>();
+  constexpr int XT = FAC ? kFactorExtra : 0;
+  T* Xt = nullptr;
+  carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Xt);
   T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3];
   const bool react = mp.c != nullptr;
   const bool zero = uold == nullptr;
@@ -1249,10 +1349,20 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
       const int cw = e / N3;
       P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
-    __syncwarp();
-    volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
-    all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
-    __syncwarp();
+    if constexpr (FAC) {   // the defect's operator in the factored form
+      T* Ah = Xt;
+      T* M1s = Ah + 3 * CPW * N2;
+      T* MVs = M1s + N2;
+      hat_matrices(mp, Ah, ci, act, lane);
+      factor_tables(M1s, MVs, lane);
+      __syncwarp();
+      factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, MVs + 4 * N, uold, mp, lane, act, ci);
+    } else {
+      __syncwarp();
+      volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
+      all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+      __syncwarp();
+    }
   }
   // the defect goes to P (no longer needed); FP64: also as double-float pairs in S0
   df* D2 = reinterpret_cast<df*>(S0);
@@ -2130,6 +2240,46 @@ cudaError_t upload_one(const double* h) {
   p += N;
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j) tb.S1[i][j] = T(p[i * N + j]);
+  // M^-1 by Gauss-Jordan elimination with partial pivoting in long double
+  // (M is symmetric positive definite with condition number below 20 for
+  // n <= 9), then M^-1 S, M^-1 e_0, M^-1 e_{n-1}, M^-1 dl_s
+  const double* M1 = h + 2 * N2 + 3 * N;
+  const double* S1 = p;
+  const double* dl = h + 2 * N2 + N;
+  long double a[N][2 * N];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < 2 * N; ++j) a[i][j] = j < N ? (long double)M1[i * N + j] : (j - N == i ? 1.0L : 0.0L);
+  for (int c = 0; c < N; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < N; ++r)
+      if (fabsl(a[r][c]) > fabsl(a[piv][c])) piv = r;
+    for (int j = 0; j < 2 * N; ++j) {
+      const long double tmp = a[c][j];
+      a[c][j] = a[piv][j];
+      a[piv][j] = tmp;
+    }
+    const long double ip = 1.0L / a[c][c];
+    for (int j = 0; j < 2 * N; ++j) a[c][j] *= ip;
+    for (int r = 0; r < N; ++r) {
+      if (r == c) continue;
+      const long double m = a[r][c];
+      for (int j = 0; j < 2 * N; ++j) a[r][j] -= m * a[c][j];
+    }
+  }
+  for (int i = 0; i < N; ++i) {
+    for (int j = 0; j < N; ++j) {
+      long double v = 0.0L;
+      for (int k = 0; k < N; ++k) v += a[i][N + k] * (long double)S1[k * N + j];
+      tb.MIS[i][j] = T((double)v);
+    }
+    tb.mie[0][i] = T((double)a[i][N]);
+    tb.mie[1][i] = T((double)a[i][2 * N - 1]);
+    for (int s2 = 0; s2 < 2; ++s2) {
+      long double v = 0.0L;
+      for (int k = 0; k < N; ++k) v += a[i][N + k] * (long double)dl[s2 * N + k];
+      tb.midl[s2][i] = T((double)v);
+    }
+  }
   if (std::is_same<T, double>::value) return cudaMemcpyToSymbol(c_tab_d, &tb, sizeof(tb));
   if (std::is_same<T, df>::value) return cudaMemcpyToSymbol(c_tab_df, &tb, sizeof(tb));
   return cudaMemcpyToSymbol(c_tab_f, &tb, sizeof(tb));
@@ -2174,9 +2324,7 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = volume_elem<T, ADV>()
-                        ? 3 * CPW * N2 + N2 + (FULL && std::is_same<T, double>::value ? 24 * N2 : 0)
-                        : 0;
+  constexpr int XT = use_factored<T, ADV>() ? kFactorExtra : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_apply<T, FULL, ADV>;
@@ -2210,7 +2358,7 @@ cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool f
 template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = ADV ? 0 : 3 * CPW * N2 + N2 + (volume_elem<T, ADV>() ? 3 * CPW * N2 : 0);
+  constexpr int XT = smooth_extra<T, ADV>();
   const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(6, XT);
   auto k = k_smooth_pcg<T, ADV>;
@@ -2227,8 +2375,9 @@ template <typename T, bool ADV>
 cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
   if (!a.binv) return cudaErrorInvalidValue;
-  const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4));
-  const size_t sm = wpb * WarpMem<T>::bytes(4);
+  constexpr int XT = use_factored<T, ADV>() ? kFactorExtra : 0;
+  const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
+  const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_smooth_inv<T, ADV>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;

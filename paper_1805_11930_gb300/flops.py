@@ -11,14 +11,17 @@ counted like a full apply.  One smoother sweep over a cell costs one apply
 for its defect (none when it starts from zero) plus one apply per inner
 iteration.
 
-Kernel count (what the kernels issue, b = 0, for reference): the volume term
-is the exact Kronecker form sum_d c_d (S (x) M (x) M)_d, 8 contractions of
-2 n^4 = 16 n^4; the faces of a full apply 84 n^3 + 120 n^2 (cell-centric);
-the inner block apply of the smoother is D_T = sum_d A_d (x) M (x) M with
-per-cell 1D matrices A_d that contain the own-side face terms, again
-16 n^4 with no face pass; inner-iteration vector work 13 n^3.  With
-advection the volume term runs at the Gauss points (24 n^4 + 9 n^3) and the
-block apply adds the own-side faces (72 n^3 + 100 n^2).
+Kernel count (what the kernels issue, b = 0): the FP64 and double-float
+kernels apply the block in the factored form D_T = (M (x) M (x) M) o
+sum_d (M^-1 A_d) x_d: one fused pass of 3 n multiply-adds per element and
+three mass passes of n each, 12 n^4 per cell; the full operator adds the
+neighbour face values (6 n^2 face points of n multiply-adds and 8 more
+operations each, 12 n^3 + 48 n^2) and their injection before the mass
+passes (12 multiply-adds per element, 24 n^3): 12 n^4 + 36 n^3 + 48 n^2.
+Inner-iteration vector work 13 n^3.  With advection the volume term runs at
+the Gauss points (24 n^4 + 9 n^3) and the faces add the upwind flux; the
+FP32 kernels keep the eight-contraction Kronecker sequence (16 n^4 per
+block apply).
 """
 
 
@@ -34,21 +37,27 @@ def algorithmic_smoother(n, ncell, sweeps, zero_sweeps, inner_its_total, value_t
     return F * (ncell * (sweeps - zero_sweeps) + inner_its_total)
 
 
-def kernel_apply_full(n, advection=False):
-    vol = 24 * n ** 4 + 9 * n ** 3 if advection else 16 * n ** 4
-    return vol + 84 * n ** 3 + 120 * n ** 2
+def kernel_apply_full(n, advection=False, factored=True):
+    """Flops one cell of a full operator apply issues: the factored form
+    (FP64, double-float), else the Kronecker volume term and line-form faces
+    (FP32: 16 n^4 + 84 n^3 + 120 n^2)."""
+    if advection:
+        return 24 * n ** 4 + 9 * n ** 3 + 84 * n ** 3 + 120 * n ** 2
+    if factored:
+        return 12 * n ** 4 + 36 * n ** 3 + 48 * n ** 2
+    return 16 * n ** 4 + 84 * n ** 3 + 120 * n ** 2
 
 
-def kernel_apply_block(n, advection=False):
+def kernel_apply_block(n, advection=False, factored=True):
     if advection:
         return 24 * n ** 4 + 9 * n ** 3 + 72 * n ** 3 + 100 * n ** 2
-    return 16 * n ** 4
+    return 12 * n ** 4 if factored else 16 * n ** 4
 
 
 def kernel_smoother(n, ncell, sweeps, zero_sweeps, inner_its_total):
-    """Flops the b = 0 inner-PCG smoother kernels issue over `sweeps` launches:
-    a full apply per defect, a Kronecker block apply plus the vector work per
-    inner iteration."""
+    """Flops the b = 0 inner-PCG smoother kernels issue (FP64, factored form)
+    over `sweeps` launches: a full apply per defect, a block apply plus the
+    vector work per inner iteration."""
     return (kernel_apply_full(n) * ncell * (sweeps - zero_sweeps)
             + (kernel_apply_block(n) + 13 * n ** 3) * inner_its_total)
 
