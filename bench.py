@@ -153,10 +153,13 @@ def run_dgmg(args, rank, world, local_rank):
     u = torch.zeros_like(f)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = dgmg.default_opts(timing=1)
-    # launch shapes (warps per block) of the operator and smoother kernels,
-    # timed on this mesh for each arithmetic before anything is measured
-    shapes = {name: ctx.autotune(prec) for name, prec in (("fp64", dgmg.FP64), ("fp32", dgmg.FP32),
-                                                          ("df64", dgmg.DF64))}
+    # launch shapes (warps per block) and work layouts (line / factored /
+    # plane) of the operator and smoother kernels, timed on this mesh for each
+    # arithmetic before anything is measured
+    shapes, layouts = {}, {}
+    for name, prec in (("fp64", dgmg.FP64), ("fp32", dgmg.FP32), ("df64", dgmg.DF64)):
+        shapes[name] = ctx.autotune(prec)
+        layouts[name] = [dgmg.LAYOUT_NAMES[x] for x in ctx.get_layout(prec)]
 
     def barrier():
         if world > 1:
@@ -319,7 +322,8 @@ def run_dgmg(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {**workload_config(), "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}",
-                   "warps_per_block": {k: {"apply": a, "smoother": b} for k, (a, b) in shapes.items()}},
+                   "warps_per_block": {k: {"apply": a, "smoother": b} for k, (a, b) in shapes.items()},
+                   "layouts": {k: {"apply": a, "smoother": b} for k, (a, b) in layouts.items()}},
         "e2e": e2e,
         "gpu_launches": int(sum(x["kernel_launches"] for x in stats)),
         "roofline": roofline,

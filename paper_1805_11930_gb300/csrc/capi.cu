@@ -163,6 +163,8 @@ struct dgmg_ctx {
   std::vector<void*> mesh_allocs;  // freed on a new mesh
   // warps per block of the operator / smoother kernels per precision (0 = 4)
   int wpb_apply[3] = {0, 0, 0}, wpb_smooth[3] = {0, 0, 0};
+  // work layouts per precision (dgmg_layout; AUTO = the default)
+  int lay_apply[3] = {0, 0, 0}, lay_smooth[3] = {0, 0, 0};
   // stored inverses of the diagonal blocks (DGMG_INNER_DIRECT), built on demand
   float2* binv_df = nullptr;    // for FP64 smoothers: double-float pairs
   float* binv32 = nullptr;      // for FP32 smoothers
@@ -274,6 +276,21 @@ void dfree(dgmg_ctx* ctx, void* q) {
     }
 }
 
+// The layout a kernel uses for precision prec: AUTO is the default of the
+// precision, order and kernel (FACTORED for FP64 and DF64; in FP32 LINE for
+// the operator, PLANE for the smoother with p <= 4, measured the faster pair
+// on GB300).
+int resolve_layout(const dgmg_ctx* ctx, int prec, int lay, bool smoother) {
+  if (lay != DGMG_LAYOUT_AUTO) return lay;
+  if (prec == DGMG_FP32) return smoother && ctx->p <= 4 ? DGMG_LAYOUT_PLANE : DGMG_LAYOUT_LINE;
+  return DGMG_LAYOUT_FACTORED;
+}
+
+bool layout_exists(const dgmg_ctx* ctx, int prec, int lay) {
+  if (lay == DGMG_LAYOUT_AUTO || lay == DGMG_LAYOUT_LINE || lay == DGMG_LAYOUT_FACTORED) return true;
+  return lay == DGMG_LAYOUT_PLANE && prec == DGMG_FP32 && ctx->p <= 4;
+}
+
 MeshParams params(const dgmg_ctx* ctx) {
   MeshParams m;
   m.nx = ctx->nx;
@@ -295,6 +312,8 @@ MeshParams params(const dgmg_ctx* ctx) {
   for (int i = 0; i < 3; ++i) {
     m.wpb_apply[i] = ctx->wpb_apply[i];
     m.wpb_smooth[i] = ctx->wpb_smooth[i];
+    m.lay_apply[i] = resolve_layout(ctx, i, ctx->lay_apply[i], false);
+    m.lay_smooth[i] = resolve_layout(ctx, i, ctx->lay_smooth[i], true);
   }
   const double J = ctx->h[0] * ctx->h[1] * ctx->h[2];
   for (int d = 0; d < 3; ++d) {
@@ -1198,7 +1217,7 @@ dgmg_status dgmg_set_mesh(dgmg_ctx* ctx, int nx, int ny, int nz, double lx, doub
   ctx->ndof = ncell * n3;
   ctx->nvert = (long long)(nx + 1) * (ny + 1) * (nz + 1);
   ctx->ops = cell_ops(p + 1);
-  for (int i = 0; i < 3; ++i) ctx->wpb_apply[i] = ctx->wpb_smooth[i] = 0;
+  for (int i = 0; i < 3; ++i) ctx->wpb_apply[i] = ctx->wpb_smooth[i] = ctx->lay_apply[i] = ctx->lay_smooth[i] = 0;
   ctx->has_mesh = true;
   ctx->has_coef = false;
   return DGMG_OK;
@@ -1583,6 +1602,28 @@ dgmg_status dgmg_set_launch_shape(dgmg_ctx* ctx, dgmg_prec prec, int wpb_apply, 
   return DGMG_OK;
 }
 
+dgmg_status dgmg_set_layout(dgmg_ctx* ctx, dgmg_prec prec, int layout_apply, int layout_smooth) {
+  if (!ctx) return DGMG_ERR_ARG;
+  if (!ctx->has_mesh) return fail(ctx, DGMG_ERR_STATE, "set_mesh first");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  if (!layout_exists(ctx, prec, layout_apply) || !layout_exists(ctx, prec, layout_smooth))
+    return fail(ctx, DGMG_ERR_ARG, "no such layout for this precision and order");
+  drop_graphs(ctx);   // captured graphs hold the old kernels
+  ctx->lay_apply[prec] = layout_apply;
+  ctx->lay_smooth[prec] = layout_smooth;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_get_layout(const dgmg_ctx* cctx, dgmg_prec prec, int* layout_apply, int* layout_smooth) {
+  if (!cctx) return DGMG_ERR_ARG;
+  dgmg_ctx* ctx = const_cast<dgmg_ctx*>(cctx);
+  if (!ctx->has_mesh) return fail(ctx, DGMG_ERR_STATE, "set_mesh first");
+  if (prec != DGMG_FP64 && prec != DGMG_FP32 && prec != DGMG_DF64) return fail(ctx, DGMG_ERR_ARG, "bad precision");
+  if (layout_apply) *layout_apply = resolve_layout(ctx, prec, ctx->lay_apply[prec], false);
+  if (layout_smooth) *layout_smooth = resolve_layout(ctx, prec, ctx->lay_smooth[prec], true);
+  return DGMG_OK;
+}
+
 dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_apply, int* wpb_smooth) {
   if (!ctx) return DGMG_ERR_ARG;
   CS(ready(ctx));
@@ -1599,8 +1640,12 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   dgmg_status st = DGMG_OK;
   const int cand[4] = {1, 2, 4, 8};
-  int best[2] = {0, 0};
+  std::vector<int> lays = {DGMG_LAYOUT_LINE, DGMG_LAYOUT_FACTORED};
+  if (layout_exists(ctx, prec, DGMG_LAYOUT_PLANE)) lays.push_back(DGMG_LAYOUT_PLANE);
+  if (ctx->db) lays = {DGMG_LAYOUT_LINE};   // advection: one form
+  int best[2] = {0, 0}, best_lay[2] = {0, 0};
   const int saved_a = ctx->wpb_apply[prec], saved_s = ctx->wpb_smooth[prec];
+  const int saved_la = ctx->lay_apply[prec], saved_ls = ctx->lay_smooth[prec];
   const bool saved_track = ctx->track_its, saved_timing = ctx->timing;
   ctx->track_its = false;
   ctx->timing = false;
@@ -1613,29 +1658,35 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
       CK(vec_fill(ctx->ndof, 1.0, (double*)f, ctx->stream));
     for (int kind = 0; kind < 2; ++kind) {
       float best_ms = 0.f;
-      for (int w : cand) {
-        if (kind == 0)
-          ctx->wpb_apply[prec] = w;
-        else
-          ctx->wpb_smooth[prec] = w;
-        const MeshParams mp = params(ctx);
-        float total = 0.f;
-        for (int r = 0; r <= reps; ++r) {
-          CK(cudaEventRecord(e0, ctx->stream));
+      for (int lay : lays) {
+        for (int w : cand) {
           if (kind == 0) {
-            CK(ctx->ops->apply(mp, f, u, prec, true, ctx->stream));
+            ctx->wpb_apply[prec] = w;
+            ctx->lay_apply[prec] = lay;
           } else {
-            CS(smooth_internal(ctx, f, u, t, 1, 1.0, 1e-2, 0, DGMG_INNER_PCG, 0, prec, true, nullptr));
+            ctx->wpb_smooth[prec] = w;
+            ctx->lay_smooth[prec] = lay;
           }
-          CK(cudaEventRecord(e1, ctx->stream));
-          CK(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          CK(cudaEventElapsedTime(&ms, e0, e1));
-          if (r > 0) total += ms;   // r = 0 is the warm-up
-        }
-        if (best[kind] == 0 || total < best_ms) {
-          best[kind] = w;
-          best_ms = total;
+          const MeshParams mp = params(ctx);
+          float total = 0.f;
+          for (int r = 0; r <= reps; ++r) {
+            CK(cudaEventRecord(e0, ctx->stream));
+            if (kind == 0) {
+              CK(ctx->ops->apply(mp, f, u, prec, true, ctx->stream));
+            } else {
+              CS(smooth_internal(ctx, f, u, t, 1, 1.0, 1e-2, 0, DGMG_INNER_PCG, 0, prec, true, nullptr));
+            }
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) total += ms;   // r = 0 is the warm-up
+          }
+          if (best[kind] == 0 || total < best_ms) {
+            best[kind] = w;
+            best_lay[kind] = lay;
+            best_ms = total;
+          }
         }
       }
     }
@@ -1651,11 +1702,15 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
   if (st != DGMG_OK) {
     ctx->wpb_apply[prec] = saved_a;
     ctx->wpb_smooth[prec] = saved_s;
+    ctx->lay_apply[prec] = saved_la;
+    ctx->lay_smooth[prec] = saved_ls;
     return st;
   }
   drop_graphs(ctx);
   ctx->wpb_apply[prec] = best[0];
   ctx->wpb_smooth[prec] = best[1];
+  ctx->lay_apply[prec] = best_lay[0];
+  ctx->lay_smooth[prec] = best_lay[1];
   if (wpb_apply) *wpb_apply = best[0];
   if (wpb_smooth) *wpb_smooth = best[1];
   return DGMG_OK;

@@ -472,25 +472,30 @@ __device__ __forceinline__ void factor_tables(T* M1s, T* MVs, int lane) {
 //              |F| [ ks ((M^-1 e_e) dl_s^T + (M^-1 dl_s) e_e^T) + gamma (M^-1 e_e) e_e^T ],
 // ks = -kap sg / h_d, e = end node of side s, sg = +-1 its outward sign.
 template <typename T>
+__device__ __forceinline__ T hat_entry(const MeshParams& mp, const CellInfo<T>& c, int d, int i, int j) {
+  const Tab<T>& t = tab<T>();
+  T a = c.kd[d] * t.MIS[i][j];
+  if (d == 2 && i == j) a = a + c.cJ;
+  const T ih = Prec<T>::ih(mp, d);
+  for (int s = 0; s < 2; ++s) {
+    const int f = 2 * d + s;
+    if (c.kind[f] == 2) continue;
+    const int e = s ? N - 1 : 0;
+    const T ks = (s ? -c.kap[f] : c.kap[f]) * ih;
+    T fv = ks * t.mie[s][i] * t.dl[s][j];
+    if (j == e) fv = fma(ks, t.midl[s][i], fma(c.gam[f], t.mie[s][i], fv));
+    a = fma(c.jh[d], fv, a);
+  }
+  return a;
+}
+
+template <typename T>
 __device__ __forceinline__ void hat_matrices(const MeshParams& mp, T* Ah, const CellInfo<T>* ci,
                                              const unsigned char* act, int lane) {
-  const Tab<T>& t = tab<T>();
   for (int k = lane; k < CPW * 3 * N2; k += 32) {
     const int cw = k / (3 * N2), r = k - cw * 3 * N2, d = r / N2, i = (r % N2) / N, j = r % N;
     if (!act[cw]) continue;
-    T a = ci[cw].kd[d] * t.MIS[i][j];
-    if (d == 2 && i == j) a = a + ci[cw].cJ;
-    const T ih = Prec<T>::ih(mp, d);
-    for (int s = 0; s < 2; ++s) {
-      const int f = 2 * d + s;
-      if (ci[cw].kind[f] == 2) continue;
-      const int e = s ? N - 1 : 0;
-      const T ks = (s ? -ci[cw].kap[f] : ci[cw].kap[f]) * ih;
-      T fv = ks * t.mie[s][i] * t.dl[s][j];
-      if (j == e) fv = fma(ks, t.midl[s][i], fma(ci[cw].gam[f], t.mie[s][i], fv));
-      a = fma(ci[cw].jh[d], fv, a);
-    }
-    Ah[k] = a;
+    Ah[k] = hat_entry(mp, ci[cw], d, i, j);
   }
 }
 
@@ -500,11 +505,11 @@ __device__ __forceinline__ void hat_matrices(const MeshParams& mp, T* Ah, const 
 //   FS[cw][f][0][L] = |F| (-gamma u_o - kap dn_o),   FS[cw][f][1][L] = sg |F| / h_d kap u_o,
 // (zero on boundary faces): the parts of qv = gamma [[u]] - kap (dn + dn_o),
 // qdv = -kap [[u]] that the block D_T leaves out.  12 n^2 values per cell.
-template <typename T, typename G>
+template <typename T, typename G, int C = CPW>
 __device__ __forceinline__ void neighbour_faces(T* FS, const G* __restrict__ gu, const MeshParams& mp, int lane,
                                                 const unsigned char* act, const CellInfo<T>* ci) {
   const Tab<T>& t = tab<T>();
-  for (int it = lane; it < CPW * 6 * N2; it += 32) {
+  for (int it = lane; it < C * 6 * N2; it += 32) {
     const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2;
     const int d = f >> 1, S = f & 1;
     T qv = T(0), qd = T(0);
@@ -624,8 +629,6 @@ __device__ __forceinline__ void factored_apply(const T* X, T* Y, T* S0, T* S1, c
 // MVs (4 n), FS (12 CPW n^2).
 constexpr int kFactorExtra = 3 * CPW * N2 + N2 + 4 * N + 12 * CPW * N2;
 
-template <typename T, bool ADV>
-__host__ __device__ constexpr bool use_factored() { return !ADV && !std::is_same<T, float>::value; }
 
 // Y = A^v X for the warp's cells.  S0, S1 scratch.
 //  b = 0: K and c are constant per cell and the cell affine, so the volume
@@ -953,10 +956,10 @@ __device__ __forceinline__ void slot_cells(const MeshParams& mp, int color, long
   __syncwarp();
 }
 
-template <typename T>
+template <typename T, int C = CPW>
 __device__ __forceinline__ void stage_cells(const MeshParams& mp, long long cell0, int lane, CellInfo<T>* ci,
                                             unsigned char* act, const long long* cid = nullptr) {
-  if (lane < CPW) {
+  if (lane < C) {
     const long long c = cid ? cid[lane] : cell0 + lane;
     const bool ok = c >= 0 && c < mp.ncell;
     act[lane] = ok ? 1 : 0;
@@ -1014,8 +1017,9 @@ __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T**
   if (cid) *cid = reinterpret_cast<long long*>(*act + 16);
 }
 
-template <typename T, bool FULL, bool ADV, typename G = typename Store<T>::type>
+template <typename T, bool FULL, bool ADV, bool FAC, typename G = typename Store<T>::type>
 __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restrict__ u, G* __restrict__ v) {
+  static_assert(!(FAC && ADV), "the factored form is for b = 0");
   const bool react = mp.c != nullptr;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1025,9 +1029,8 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
   T *F0, *F1, *red;
   CellInfo<T>* ci;
   unsigned char* act;
-  // FP64 / double-float with b = 0: the factored form (per-cell matrices,
-  // mass matrix, neighbour face values in the extra region)
-  constexpr bool FAC = use_factored<T, ADV>();
+  // FAC (b = 0): the factored form (per-cell matrices, mass matrix, neighbour
+  // face values in the extra region); else the line form
   constexpr int XT = FAC ? kFactorExtra : 0;
   T* Xt = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Xt);
@@ -1107,9 +1110,9 @@ __device__ __forceinline__ void cell_sum2(T& a, T& b, int lane, T* red) {
 // Extra shared values per warp of the inner-PCG smoother: the factored form's
 // region (FP64, double-float, b = 0), the per-cell 1D matrices of D_T (FP32,
 // b = 0), nothing with advection.
-template <typename T, bool ADV>
+template <bool ADV, bool FAC>
 __host__ __device__ constexpr int smooth_extra() {
-  return use_factored<T, ADV>() ? kFactorExtra : (ADV ? 0 : 3 * CPW * N2);
+  return FAC ? kFactorExtra : (ADV ? 0 : 3 * CPW * N2);
 }
 
 // Block-Jacobi sweep with inner PCG (Algorithm 2; inner solve Sec. 2.2.1).
@@ -1120,7 +1123,7 @@ __host__ __device__ constexpr int smooth_extra() {
 // (advection).  With several cells per warp each lane owns one z-line of its
 // cell for the pointwise vector operations; with one cell per warp every lane
 // takes elements lane, lane + 32, ... (all 32 lanes busy).
-template <typename T, bool ADV, typename G = typename Store<T>::type>
+template <typename T, bool ADV, bool FAC, typename G = typename Store<T>::type>
 __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __restrict__ f,
                                                          const G* uold, G* unew, const G* __restrict__ diag,
                                                          T omega, T eps, int maxit, int* __restrict__ its,
@@ -1133,8 +1136,8 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  constexpr bool FAC = use_factored<T, ADV>();
-  constexpr int XT = smooth_extra<T, ADV>();
+  static_assert(!(FAC && ADV), "the factored form is for b = 0");
+  constexpr int XT = smooth_extra<ADV, FAC>();
   T* vec[6];
   T* Xt = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(6, XT), 6, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Xt);
@@ -1321,7 +1324,8 @@ template <typename T> struct InvEntry { using type = T; };
 template <> struct InvEntry<double> { using type = float2; };
 template <> struct InvEntry<df> { using type = float2; };
 
-template <typename T, bool ADV, typename G = typename Store<T>::type, typename M = typename InvEntry<T>::type>
+template <typename T, bool ADV, bool FAC, typename G = typename Store<T>::type,
+          typename M = typename InvEntry<T>::type>
 __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __restrict__ f, const G* uold, G* unew,
                                                     const M* __restrict__ binv, int ld, T omega,
                                                     int* __restrict__ its, int color) {
@@ -1334,7 +1338,7 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  constexpr bool FAC = use_factored<T, ADV>();
+  static_assert(!(FAC && ADV), "the factored form is for b = 0");
   constexpr int XT = FAC ? kFactorExtra : 0;
   T* Xt = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Xt);
@@ -2210,6 +2214,8 @@ __global__ void __launch_bounds__(256) k_prolong_add(MeshParams mp, const double
   }
 }
 
+#include "plane_kernels.cuh"
+
 // ---------------------------------------------------------------- launchers
 // Synchronous copies: the staging struct lives on the host stack.
 template <typename T>
@@ -2321,18 +2327,58 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
   return cudaSuccess;
 }
 
-template <typename T, bool FULL, bool ADV>
-cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
+// Warps per block, at most wmax (the kernel's launch bound / 32).
+inline int pick_wpb_max(int tuned, size_t per_warp, int wmax) {
+  int w = pick_wpb(tuned, per_warp);
+  while (w > wmax) w >>= 1;
+  return w;
+}
+
+template <typename T, bool FULL, bool ADV, bool FAC>
+cudaError_t launch_apply_form(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = use_factored<T, ADV>() ? kFactorExtra : 0;
+  constexpr int XT = FAC ? kFactorExtra : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
-  auto k = k_apply<T, FULL, ADV>;
+  auto k = k_apply<T, FULL, ADV, FAC>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
   k<<<grid_for(mp.ncell, wpb), wpb * 32, sm, s>>>(mp, (const G*)u, (G*)v);
   count_launch();
   return cudaGetLastError();
+}
+
+#if DGMG_N <= 5
+template <bool FULL>
+cudaError_t launch_apply_plane(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
+  const size_t per = pl::warp_bytes(FULL);
+  const int wpb = pick_wpb_max(mp.wpb_apply[DGMG_FP32], per, 8);
+  const size_t sm = wpb * per;
+  auto k = k_apply_plane<FULL>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  const long long groups = (mp.ncell + pl::PC - 1) / pl::PC;
+  k<<<(unsigned)((groups + wpb - 1) / wpb), wpb * 32, sm, s>>>(mp, (const float*)u, (float*)v);
+  count_launch();
+  return cudaGetLastError();
+}
+#endif
+
+// Operator launch in the layout the mesh parameters select for this
+// precision (advection: the line form at the Gauss points).
+template <typename T, bool FULL, bool ADV>
+cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
+  if constexpr (ADV) {
+    return launch_apply_form<T, FULL, true, false>(mp, u, v, s);
+  } else {
+    const int lay = mp.lay_apply[prec_index<T>()];
+#if DGMG_N <= 5
+    if constexpr (std::is_same<T, float>::value)
+      if (lay == DGMG_LAYOUT_PLANE) return launch_apply_plane<FULL>(mp, u, v, s);
+#endif
+    if (lay == DGMG_LAYOUT_LINE) return launch_apply_form<T, FULL, false, false>(mp, u, v, s);
+    return launch_apply_form<T, FULL, false, true>(mp, u, v, s);
+  }
 }
 
 template <typename T, bool FULL>
@@ -2355,13 +2401,13 @@ cudaError_t apply(const MeshParams& mp, const void* u, void* v, int prec, bool f
   return full ? apply_t<double, true>(mp, u, v, s) : apply_t<double, false>(mp, u, v, s);
 }
 
-template <typename T, bool ADV>
-cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+template <typename T, bool ADV, bool FAC>
+cudaError_t launch_smooth_form(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = smooth_extra<T, ADV>();
+  constexpr int XT = smooth_extra<ADV, FAC>();
   const int wpb = pick_wpb(mp.wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(6, XT);
-  auto k = k_smooth_pcg<T, ADV>;
+  auto k = k_smooth_pcg<T, ADV, FAC>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
   const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
@@ -2371,14 +2417,44 @@ cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_
   return cudaGetLastError();
 }
 
+// Inner-PCG sweep in the selected layout; the plane form covers the Jacobi
+// sweep over all cells (a colour of block-SOR takes the line form).
 template <typename T, bool ADV>
-cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  if constexpr (ADV) {
+    return launch_smooth_form<T, true, false>(mp, a, s);
+  } else {
+    const int lay = mp.lay_smooth[prec_index<T>()];
+#if DGMG_N <= 5
+    if constexpr (std::is_same<T, float>::value) {
+      if (lay == DGMG_LAYOUT_PLANE) {
+        if (a.color >= 0) return launch_smooth_form<float, false, false>(mp, a, s);
+        const size_t per = pl::warp_bytes(true);
+        const int wpb = pick_wpb_max(mp.wpb_smooth[DGMG_FP32], per, 4);
+        const size_t sm = wpb * per;
+        cudaError_t e = set_smem(k_smooth_plane, sm);
+        if (e != cudaSuccess) return e;
+        const long long groups = (mp.ncell + pl::PC - 1) / pl::PC;
+        k_smooth_plane<<<(unsigned)((groups + wpb - 1) / wpb), wpb * 32, sm, s>>>(
+            mp, (const float*)a.f, (const float*)a.uold, (float*)a.unew, (const float*)a.diag, float(a.omega),
+            float(a.eps), a.maxit, a.its);
+        count_launch();
+        return cudaGetLastError();
+      }
+    }
+#endif
+    if (lay == DGMG_LAYOUT_LINE || lay == DGMG_LAYOUT_PLANE) return launch_smooth_form<T, false, false>(mp, a, s);
+    return launch_smooth_form<T, false, true>(mp, a, s);
+  }
+}
+
+template <typename T, bool ADV, bool FAC>
+cudaError_t launch_inv_form(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  if (!a.binv) return cudaErrorInvalidValue;
-  constexpr int XT = use_factored<T, ADV>() ? kFactorExtra : 0;
+  constexpr int XT = FAC ? kFactorExtra : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
-  auto k = k_smooth_inv<T, ADV>;
+  auto k = k_smooth_inv<T, ADV, FAC>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
   const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
@@ -2387,6 +2463,19 @@ cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s
                                           a.binv_ld, T(a.omega), a.its, a.color);
   count_launch();
   return cudaGetLastError();
+}
+
+// Stored-inverse sweep; its defect takes the factored form where the
+// smoother layout is the factored one.
+template <typename T, bool ADV>
+cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  if (!a.binv) return cudaErrorInvalidValue;
+  if constexpr (ADV) {
+    return launch_inv_form<T, true, false>(mp, a, s);
+  } else {
+    if (mp.lay_smooth[prec_index<T>()] == DGMG_LAYOUT_FACTORED) return launch_inv_form<T, false, true>(mp, a, s);
+    return launch_inv_form<T, false, false>(mp, a, s);
+  }
 }
 
 template <bool ADV>

@@ -42,6 +42,8 @@ struct MeshParams {
   // Warps per block of the operator and smoother (inner PCG) kernels per
   // precision (index DGMG_FP64 / FP32 / DF64; 0 = the default of 4).
   int wpb_apply[3], wpb_smooth[3];
+  // Work layouts (dgmg_layout, resolved: never DGMG_LAYOUT_AUTO) per precision.
+  int lay_apply[3], lay_smooth[3];
 };
 
 // Record layout: kd[3] = |J| K_d / h_d^2, cJ = c |J|, kap[6], gam[6] for the

@@ -19,6 +19,8 @@ DGMG_OK = 0
 STATUS = {0: "DGMG_OK", 1: "DGMG_ERR_ARG", 2: "DGMG_ERR_OOM", 3: "DGMG_ERR_CUDA", 4: "DGMG_ERR_STATE",
           5: "DGMG_ERR_NOT_CONVERGED", 6: "DGMG_ERR_BREAKDOWN", 7: "DGMG_ERR_TIMEOUT"}
 FP64, FP32, DF64 = 0, 1, 2
+LAYOUT_AUTO, LAYOUT_LINE, LAYOUT_FACTORED, LAYOUT_PLANE = 0, 1, 2, 3
+LAYOUT_NAMES = {LAYOUT_LINE: "line", LAYOUT_FACTORED: "factored", LAYOUT_PLANE: "plane"}
 KRYLOV_CG, KRYLOV_FCG, KRYLOV_FGMRES = 0, 1, 2
 INNER_PCG, INNER_GMRES, INNER_DIRECT, INNER_GMRES_TRIDIAG = 0, 1, 2, 3
 COARSE_AMG, COARSE_NONE, COARSE_P0 = 0, 1, 2
@@ -93,6 +95,8 @@ _SIG = {
     "dgmg_coarse_matrix_p0": (_I, [_P, _P]),
     "dgmg_coarse_cycle_p0": (_I, [_P, _P, _P]),
     "dgmg_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "dgmg_set_layout": (_I, [_P, _I, _I, _I]),
+    "dgmg_get_layout": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
 NOALLOC_MAX_CELLS = 131072
@@ -309,9 +313,21 @@ class Context:
         DF64 arithmetic (0 = default)."""
         self._check(self.lib.dgmg_set_launch_shape(self.h, prec, wpb_apply, wpb_smooth))
 
+    def set_layout(self, prec, layout_apply=LAYOUT_AUTO, layout_smooth=LAYOUT_AUTO):
+        """Work layouts (LAYOUT_LINE / FACTORED / PLANE, or AUTO) of the
+        operator and inner-PCG smoother kernels for FP64, FP32 or DF64."""
+        self._check(self.lib.dgmg_set_layout(self.h, prec, layout_apply, layout_smooth))
+
+    def get_layout(self, prec):
+        """The layouts in use for a precision: (layout_apply, layout_smooth)."""
+        a, s = _I(0), _I(0)
+        self._check(self.lib.dgmg_get_layout(self.h, prec, ctypes.byref(a), ctypes.byref(s)))
+        return a.value, s.value
+
     def autotune(self, prec=FP64, reps=3):
-        """Time the launch-shape candidates on the current mesh and keep the
-        fastest; returns (wpb_apply, wpb_smooth)."""
+        """Time the layout and launch-shape candidates on the current mesh and
+        keep the fastest; returns (wpb_apply, wpb_smooth) (get_layout gives the
+        layouts)."""
         a, s = _I(0), _I(0)
         self._check(self.lib.dgmg_autotune(self.h, prec, reps, ctypes.byref(a), ctypes.byref(s)))
         return a.value, s.value

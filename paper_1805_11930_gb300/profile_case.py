@@ -1,7 +1,7 @@
 """Small, fixed launch sequence of one kernel family, for ncu captures.
 
 python -m paper_1805_11930_gb300.profile_case --what apply|block|smooth --prec fp64|fp32 [--n 48] [--p 4]
-    [--inner pcg|direct] [--wpb-apply W] [--wpb-smooth W]
+    [--inner pcg|direct] [--wpb-apply W] [--wpb-smooth W] [--layout auto|line|factored|plane]
 
 Sets up the log-normal diffusion workload on an n^3 mesh (48^3 at p = 4 is
 13.8 M dofs, 110 MB per FP64 vector: larger than L2, a few hundred MB in
@@ -9,7 +9,8 @@ total), runs two warm-up launches and then `--reps` launches of the chosen
 operation through the C ABI.  Prints the median CUDA-event time per launch.
 --inner direct times the smoother with the stored block inverses (built
 before the warm-up); --wpb-* set the launch shapes (warps per block) so that
-a capture can use the shapes the benchmark's autotuning picked.
+a capture can use the shapes the benchmark's autotuning picked; --layout
+sets the work layout of both kernels.
 """
 import argparse
 import statistics
@@ -26,6 +27,7 @@ def main():
     ap.add_argument("--inner", default="pcg", choices=["pcg", "direct"])
     ap.add_argument("--wpb-apply", type=int, default=0)
     ap.add_argument("--wpb-smooth", type=int, default=0)
+    ap.add_argument("--layout", default="auto", choices=["auto", "line", "factored", "plane"])
     args = ap.parse_args()
 
     import torch
@@ -38,6 +40,9 @@ def main():
     nd = ctx.sizes()["ndof"]
     prec = dgmg.FP64 if args.prec == "fp64" else dgmg.FP32
     ctx.set_launch_shape(prec, args.wpb_apply, args.wpb_smooth)
+    lay = {"auto": dgmg.LAYOUT_AUTO, "line": dgmg.LAYOUT_LINE, "factored": dgmg.LAYOUT_FACTORED,
+           "plane": dgmg.LAYOUT_PLANE}[args.layout]
+    ctx.set_layout(prec, lay, lay)
     inner = dgmg.INNER_DIRECT if args.inner == "direct" else dgmg.INNER_PCG
     if inner == dgmg.INNER_DIRECT:
         ctx.block_inverse(prec)
@@ -67,7 +72,7 @@ def main():
         b.record(stream)
         b.synchronize()
         ms.append(a.elapsed_time(b))
-    print(f"{args.what} {args.prec} {args.inner} n={args.n} p={args.p} ndof={nd}: median {statistics.median(ms):.4f} ms "
+    print(f"{args.what} {args.prec} {args.inner} {args.layout} n={args.n} p={args.p} ndof={nd}: median {statistics.median(ms):.4f} ms "
           f"({nd / statistics.median(ms) / 1e6:.3f} GDOF/s)")
     sys.stdout.flush()
 

@@ -49,3 +49,26 @@ def rel_err(a, b):
 def custom(nc, L, p, bc, K, b=None, c=None, f=None, g=None, j=None):
     return dict(name="custom", nc=tuple(nc), L=tuple(L), p=p, bc=list(bc), K=K, b=b, c=c,
                 f=f if f is not None else (lambda x, y, z: np.ones_like(x)), g=g, j=j, exact=None)
+
+
+def elem_errors(v, ref, A, u, nc, ndof_cell):
+    """Largest element error of v against ref, scaled by ||A||_inf ||u||_inf,
+    over all elements and separately over the elements of the corner, edge and
+    face cells of the nc grid (cells with 3, 2 or 1 coordinates on the
+    boundary): {class: error}.  A norm-wise check could hide one wrong
+    boundary value; this one cannot."""
+    import scipy.sparse as sp
+    v = np.asarray(v, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = abs(sp.csr_matrix(A)).sum(axis=1).max() * np.abs(np.asarray(u, dtype=np.float64)).max()
+    err = np.abs(v - ref).reshape(-1, ndof_cell).max(axis=1) / max(scale, 1e-300)
+    nx, ny, nz = nc
+    c = np.arange(nx * ny * nz)
+    cx, cy, cz = c % nx, (c // nx) % ny, c // (nx * ny)
+    onb = (((cx == 0) | (cx == nx - 1)).astype(int) + ((cy == 0) | (cy == ny - 1)).astype(int)
+           + ((cz == 0) | (cz == nz - 1)).astype(int))
+    out = {"all": float(err.max())}
+    for k, name in ((3, "corner"), (2, "edge"), (1, "face")):
+        if (onb == k).any():
+            out[name] = float(err[onb == k].max())
+    return out

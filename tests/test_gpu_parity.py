@@ -12,7 +12,7 @@ import pytest
 from oracle import amg, dg, solvers, transfer
 from paper_1805_11930_gb300 import inputs
 
-from gpu_helpers import custom, gpu_context, gpu_rhs, oracle_problem, oracle_rhs, rel_err
+from gpu_helpers import custom, elem_errors, gpu_context, gpu_rhs, oracle_problem, oracle_rhs, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,10 +66,16 @@ def test_apply_fp64_and_fp32(name):
     v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
     ctx.apply(dev(u), v)
     assert rel_err(v.cpu().numpy(), ref) < 1e-12
+    # element by element on the corner, edge and face cells, against ||A|| ||u||
+    errs = elem_errors(v.cpu().numpy(), ref, A, u, w["nc"], P.N)
+    assert max(errs.values()) < 1e-13, errs
     u32 = dev(u, torch.float32)
     v32 = torch.empty(P.ndof, dtype=torch.float32, device="cuda")
     ctx.apply(u32, v32)
-    assert rel_err(v32.cpu().numpy(), A @ u32.cpu().double().numpy()) < 1e-5
+    ref32 = A @ u32.cpu().double().numpy()
+    assert rel_err(v32.cpu().numpy(), ref32) < 1e-5
+    errs = elem_errors(v32.cpu().numpy(), ref32, A, u32.cpu().double().numpy(), w["nc"], P.N)
+    assert max(errs.values()) < 2e-6, errs
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -88,6 +94,8 @@ def test_block_apply_and_diagonal(name):
     v = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
     ctx.block_apply(dev(u), v)
     assert rel_err(v.cpu().numpy(), ref) < 1e-12
+    errs = elem_errors(v.cpu().numpy(), ref, A, u, w["nc"], N)
+    assert max(errs.values()) < 1e-13, errs
     dg_ = torch.empty(P.ndof, dtype=torch.float64, device="cuda")
     ctx.block_diagonal(dg_)
     refd = np.einsum('cii->ci', D).reshape(-1)
@@ -521,53 +529,141 @@ def test_graph_captured_preconditioner_same_result():
     assert s0["kernel_launches"] == s1["kernel_launches"] and s0["sweeps"] == s1["sweeps"]
 
 
-@pytest.mark.parametrize("prec_name", ["FP64", "FP32", "DF64"])
-def test_launch_shape_does_not_change_results(prec_name):
-    """Every warp owns whole cells, so the warps per block of the operator and
-    smoother kernels change no bit of their outputs (ragged last block
-    included: 5^3 cells do not fill any of the shapes evenly)."""
+def _layouts(prec, p):
+    """The work layouts that exist for a precision and order."""
+    from paper_1805_11930_gb300 import dgmg
+    out = [dgmg.LAYOUT_LINE, dgmg.LAYOUT_FACTORED]
+    if prec == dgmg.FP32 and p <= 4:
+        out.append(dgmg.LAYOUT_PLANE)
+    return out
+
+
+@pytest.mark.parametrize("prec_name,p", [("FP64", 3), ("FP32", 3), ("FP32", 4), ("DF64", 3)])
+def test_launch_shape_does_not_change_results(prec_name, p):
+    """In every work layout each warp owns whole cells, so the warps per block
+    of the operator and smoother kernels change no bit of their outputs
+    (ragged last block included: 5^3 cells do not fill any of the shapes or
+    the plane layout's cells per warp evenly)."""
     from paper_1805_11930_gb300 import dgmg
     prec = getattr(dgmg, prec_name)
-    w = inputs.lognormal(5, 3)
+    w = inputs.lognormal(5, p)
     ctx = gpu_context(w)
     dt = torch.float32 if prec == dgmg.FP32 else torch.float64
     df64 = prec == dgmg.DF64
     s = ctx.sizes()
     x = torch.tensor(inputs.random_dg_vector(s["ndof"], seed=11), device="cuda").to(dt)
     f = torch.tensor(inputs.random_dg_vector(s["ndof"], seed=12), device="cuda").to(dt)
-    outs = []
-    for wpb in (0, 1, 2, 8):
-        ctx.set_launch_shape(prec, wpb, wpb)
-        v = torch.empty_like(x)
-        ctx.apply(x, v, df64=df64)
-        u = x.clone()
-        ctx.block_smooth(f, u, nsweep=2, omega=0.8, eps=1e-2, df64=df64)
-        outs.append((v.cpu().numpy(), u.cpu().numpy()))
-    for v, u in outs[1:]:
-        assert np.array_equal(v, outs[0][0]) and np.array_equal(u, outs[0][1])
+    for lay in _layouts(prec, p):
+        ctx.set_layout(prec, lay, lay)
+        assert ctx.get_layout(prec) == (lay, lay)
+        outs = []
+        for wpb in (0, 1, 2, 8):
+            ctx.set_launch_shape(prec, wpb, wpb)
+            v = torch.empty_like(x)
+            ctx.apply(x, v, df64=df64)
+            u = x.clone()
+            ctx.block_smooth(f, u, nsweep=2, omega=0.8, eps=1e-2, df64=df64)
+            outs.append((v.cpu().numpy(), u.cpu().numpy()))
+        for v, u in outs[1:]:
+            assert np.array_equal(v, outs[0][0]) and np.array_equal(u, outs[0][1]), lay
+
+
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p5_dir", "p8_dir"])
+def test_every_layout_matches_the_oracle(name):
+    """Each work layout of the b = 0 kernels (line, factored, and the FP32
+    plane layout for p <= 4) against the oracle: the operator and the block
+    D_T to 1e-12 (FP64) and 1e-5 (FP32), norm-wise and element by element on
+    the corner, edge and face cells; two FP64 block-Jacobi sweeps with
+    eps = 1e-13 equal dense-LU block-Jacobi to 1e-9; one FP32 sweep with
+    eps = 1e-2 meets every cell's stopping test (measured in FP64 against the
+    exact defect, 1e-4 of slack for the FP32 defect) and agrees to 1e-4 with
+    the oracle's block PCG where the iteration counts agree."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    N = P.N
+    Ab = A.tobsr(blocksize=(N, N))
+    D = np.zeros((P.ncell, N, N))
+    for c in range(P.ncell):
+        for k in range(Ab.indptr[c], Ab.indptr[c + 1]):
+            if Ab.indices[k] == c:
+                D[c] = Ab.data[k]
+    u = inputs.random_dg_vector(P.ndof, seed=3)
+    f = inputs.random_dg_vector(P.ndof, seed=9)
+    u0 = inputs.random_dg_vector(P.ndof, seed=10)
+    S = solvers.BlockJacobi(A, N, inner="lu")
+    ref_sm = S(f, u0, 2, 0.8)
+    ctx = gpu_context(w)
+    for prec, dt, tol, etol in ((dgmg.FP64, torch.float64, 1e-12, 1e-13), (dgmg.FP32, torch.float32, 1e-5, 2e-6)):
+        for lay in _layouts(prec, w["p"]):
+            ctx.set_layout(prec, lay, lay)
+            x = dev(u, dt)
+            xd = x.double().cpu().numpy()
+            for full in (True, False):
+                v = torch.empty_like(x)
+                (ctx.apply if full else ctx.block_apply)(x, v)
+                ref = A @ xd if full else np.einsum('cij,cj->ci', D, xd.reshape(P.ncell, N)).reshape(-1)
+                got = v.double().cpu().numpy()
+                assert rel_err(got, ref) < tol, (prec, lay, full)
+                errs = elem_errors(got, ref, A, xd, w["nc"], N)
+                assert max(errs.values()) < etol, (prec, lay, full, errs)
+            if prec == dgmg.FP64:
+                us = dev(u0)
+                ctx.block_smooth(dev(f), us, nsweep=2, omega=0.8, eps=1e-13, maxit=10 * N)
+                assert rel_err(us.cpu().numpy(), ref_sm) < 1e-9, lay
+            else:
+                its = torch.zeros(P.ncell, dtype=torch.int32, device="cuda")
+                us = dev(u0, dt)
+                fs = dev(f, dt)
+                ctx.block_smooth(fs, us, nsweep=1, omega=1.0, eps=1e-2, maxit=10 * N, inner_its=its)
+                f32 = fs.double().cpu().numpy()
+                u32 = dev(u0, dt).double().cpu().numpy()
+                d = f32 - A @ u32
+                got = us.double().cpu().numpy()
+                its = its.cpu().numpy()
+                same = 0
+                for c in range(P.ncell):
+                    sl = slice(c * N, (c + 1) * N)
+                    delta = got[sl] - u32[sl]
+                    assert np.linalg.norm(d[sl] - D[c] @ delta) <= (1.0001e-2 + 1e-4) * np.linalg.norm(d[sl]), lay
+                    x_or, it_or = solvers.block_pcg(D[c], d[sl], np.diag(D[c]), 1e-2, 10 * N)
+                    if it_or == its[c]:
+                        same += 1
+                        assert rel_err(delta, x_or) < 1e-4, (lay, c)
+                assert same >= 0.8 * P.ncell, lay
+        ctx.set_layout(prec, dgmg.LAYOUT_AUTO, dgmg.LAYOUT_AUTO)
 
 
 def test_autotune_choices_and_bitwise_solve():
-    """dgmg_autotune picks a shape for each kernel from {1, 2, 4, 8}, rejects
-    bad arguments, and a solve after tuning equals the untuned solve bit for
-    bit."""
+    """dgmg_autotune picks a layout and a shape for each kernel (warps per
+    block from {1, 2, 4, 8}), rejects bad arguments, and a solve with the
+    tuned layouts equals, bit for bit, the solve with the same layouts at the
+    default shapes; the tuned solve converges."""
     from paper_1805_11930_gb300 import dgmg
     w = inputs.lognormal(8, 4)
     ctx = gpu_context(w)
     f = gpu_rhs(ctx, w, torch)
     opts = dgmg.default_opts(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
-    u0 = torch.zeros_like(f)
-    s0 = ctx.solve(f, u0, opts)
     for prec in (dgmg.FP64, dgmg.FP32, dgmg.DF64):
         a, s = ctx.autotune(prec, reps=2)
         assert a in (1, 2, 4, 8) and s in (1, 2, 4, 8)
+        la, ls = ctx.get_layout(prec)
+        assert la in _layouts(prec, 4) and ls in _layouts(prec, 4)
     u1 = torch.zeros_like(f)
     s1 = ctx.solve(f, u1, opts)
+    assert s1["converged"]
+    for prec in (dgmg.FP64, dgmg.FP32, dgmg.DF64):
+        ctx.set_launch_shape(prec, 0, 0)
+    u0 = torch.zeros_like(f)
+    s0 = ctx.solve(f, u0, opts)
     assert s0["iterations"] == s1["iterations"] and np.array_equal(u0.cpu().numpy(), u1.cpu().numpy())
     with pytest.raises(dgmg.DgmgError):
         ctx.set_launch_shape(dgmg.FP64, 3, 0)
     with pytest.raises(dgmg.DgmgError):
         ctx.set_launch_shape(7, 4, 4)
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_layout(dgmg.FP64, dgmg.LAYOUT_PLANE, 0)
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_layout(dgmg.FP32, 9, 0)
 
 
 # ------------------------------------------------------------- stored inverses
