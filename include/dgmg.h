@@ -437,6 +437,90 @@ dgmg_status dgmg_get_layout(const dgmg_ctx* ctx, dgmg_prec prec, int* layout_app
  * where dgmg_apply rejects it, DGMG_ERR_STATE before dgmg_set_coefficients. */
 dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_apply, int* wpb_smooth);
 
+/* ------------------------------------------------------------------ batched solves
+ * A batch serves several requests of one polynomial order at once: the outer
+ * CG (or flexible CG) of every member runs in lockstep on the batch's stream,
+ * and each step of an outer iteration (operator, dot products, scalar and
+ * vector updates, the V-cycle's block-Jacobi sweeps, residual, restriction
+ * and prolongation) is one kernel launch over the cells or values of all
+ * running members, with each member's Krylov scalars (alpha, beta, residual
+ * norms, stop flag) kept in device memory.  An iteration therefore needs no
+ * host round trip; on a stream other than the legacy default stream it is
+ * captured into a CUDA graph on its second use with the same members and
+ * replayed.  The AMG cycles on the members' Q1 grids run
+ * member by member inside the same iteration.  Per member the arithmetic is
+ * that of dgmg_solve with the batch's options (the same kernels and the same
+ * reduction order of every dot product), so a request's iterates do not
+ * depend on the other members (Sec. 4.2's solver; the batching is a serving
+ * device with no counterpart in the paper). */
+typedef struct dgmg_batch dgmg_batch;
+
+/* Maximum number of members of a batch. */
+#define DGMG_BATCH_MAX 16
+
+/* Creates an empty batch on `device` whose work runs on `cuda_stream` (NULL:
+ * the default stream), with the solve options every member uses: krylov CG or
+ * FCG, smoother_prec, apply_prec (FP64 or DF64), omega, eps_inner,
+ * maxit_inner; inner = PCG, smoother = JACOBI, npre = npost = 1, coarse = AMG,
+ * stop = RESIDUAL (others: DGMG_ERR_ARG).  rtol and maxit are per member
+ * (dgmg_batch_add); graph and timing are ignored.  opts: host, or NULL for the
+ * defaults.  The batch owns a few small device buffers; DGMG_ERR_CUDA if
+ * they cannot be allocated. */
+dgmg_status dgmg_batch_create(dgmg_batch** out, int device, void* cuda_stream, const dgmg_solve_opts* opts);
+
+/* Synchronises the batch's stream, gives every member context its own stream
+ * back and frees the batch (the contexts stay alive). */
+dgmg_status dgmg_batch_destroy(dgmg_batch* batch);
+
+/* Message of the last failed batch call ("" after success; owned by the batch). */
+const char* dgmg_batch_last_error(const dgmg_batch* batch);
+
+/* Computes a request's initial Krylov state for a later dgmg_batch_add on
+ * the context's own stream: r = f - A u, ||r||, z = M r, p = z and (r, z) with
+ * the V-cycle and Krylov method of opts (host; NULL: defaults), one
+ * synchronisation.  The state is kept in the context (its Krylov vectors,
+ * allocated if needed) and used by dgmg_batch_add for the same f, u and the
+ * same options; any other call that changes the context's mesh or
+ * coefficients drops it.  Lets a set-up thread do this work on its own
+ * stream instead of the batch's.  Errors as dgmg_batch_add, reported through
+ * dgmg_last_error(ctx). */
+dgmg_status dgmg_batch_prime(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts);
+
+/* Adds a request: ctx with its mesh and coefficients set (b = 0, cell-wise K
+ * and c; the same order p and kernel layouts as the other members), its
+ * right-hand side f and initial guess / solution u (device FP64 DG vectors of
+ * the context, distinct; u is updated in place while the member runs), its
+ * relative tolerance rtol (on ||f - A u||_2 / ||f - A u_0||_2) and iteration
+ * cap maxit.  The context's stream is synchronised and replaced by the
+ * batch's stream until dgmg_batch_remove; meanwhile the caller must not use
+ * the context.  Takes the initial state of dgmg_batch_prime when it was
+ * computed for the same f, u and options, else computes r = f - A u,
+ * z = M r, p = z and (r, z) on the batch's stream (one synchronisation),
+ * allocating the context's Krylov vectors if needed.  On
+ * return *slot (host) names the member.  Errors: DGMG_ERR_ARG (bad or
+ * unsupported arguments, full batch, NaN or Inf in the initial residual:
+ * nothing added), DGMG_ERR_STATE (context not ready), DGMG_ERR_OOM. */
+dgmg_status dgmg_batch_add(dgmg_batch* batch, dgmg_ctx* ctx, const double* f, double* u, double rtol, int maxit,
+                           int* slot);
+
+/* Runs `iterations` outer iterations of every running member, then reads the
+ * members' stop flags (one synchronisation) and sets *running (host, or NULL)
+ * to the number of members still running.  A member stops when its residual
+ * meets its tolerance, at its iteration cap, or at a CG breakdown; stopped
+ * members take no part in later launches. */
+dgmg_status dgmg_batch_step(dgmg_batch* batch, int iterations, int* running);
+
+/* *done = 1 (host) once member `slot` has stopped, else 0.  For a stopped
+ * member the first call recomputes its true FP64 residual (as dgmg_solve does)
+ * and fills *stats (host, or NULL: iterations, rel_residual, converged; the
+ * timing and inner-iteration fields stay 0); the return value is then the
+ * member's status: DGMG_OK, DGMG_ERR_NOT_CONVERGED or DGMG_ERR_BREAKDOWN. */
+dgmg_status dgmg_batch_poll(dgmg_batch* batch, int slot, int* done, dgmg_solve_stats* stats);
+
+/* Removes member `slot` (running or not): synchronises the batch's stream and
+ * gives the context its own stream back. */
+dgmg_status dgmg_batch_remove(dgmg_batch* batch, int slot);
+
 /* Largest grid (nx*ny*nz cells) dgmg_restrict_noalloc accepts. */
 #define DGMG_NOALLOC_MAX_CELLS 131072
 

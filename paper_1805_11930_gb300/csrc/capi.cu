@@ -176,6 +176,13 @@ struct dgmg_ctx {
   // Thomas factors of the tridiagonal part of D_T (DGMG_INNER_GMRES_TRIDIAG)
   double* tri64 = nullptr;
   float* tri32 = nullptr;
+  // Initial Krylov state of a batched solve computed by dgmg_batch_prime:
+  // r, z, p in kry, ||r_0|| and (r, z), for (f, u) and the V-cycle options.
+  bool primed = false;
+  const double* prime_f = nullptr;
+  double* prime_u = nullptr;
+  double prime_r0 = 0.0, prime_rz = 0.0;
+  dgmg_solve_opts prime_key;
 };
 
 namespace {
@@ -241,6 +248,7 @@ void drop_graphs(dgmg_ctx* ctx) {
 }
 
 void free_mesh(dgmg_ctx* ctx) {
+  ctx->primed = false;
   drop_graphs(ctx);
   for (void* q : ctx->mesh_allocs) cudaFreeAsync(q, ctx->stream);
   ctx->mesh_allocs.clear();
@@ -1713,6 +1721,544 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
   ctx->lay_smooth[prec] = best_lay[1];
   if (wpb_apply) *wpb_apply = best[0];
   if (wpb_smooth) *wpb_smooth = best[1];
+  return DGMG_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batched solves
+// A batch runs the outer CG / flexible CG of up to kMaxBatch prepared requests
+// of one order in lockstep on one stream: every step of an iteration (the
+// operator, the dots, the scalar updates, the vector updates, the V-cycle's
+// smoothers, residual, transfers) is one launch over the cells or values of
+// all running members, reading each member's scalars from device memory, so
+// an iteration needs no host round trip and is replayed from a CUDA graph
+// while the membership stays the same.  Only the AMG cycles on the members'
+// coarse grids run member by member.  Per member the arithmetic is that of
+// dgmg_solve with the same options (the same kernels, the same reduction
+// order of every dot), so a request's result does not depend on the others.
+struct dgmg_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  dgmg_solve_opts opts;
+  struct Member {
+    bool used = false;
+    bool running = false;     // in the launches of the next step
+    bool finished = false;    // stopped (converged, breakdown or iteration cap)
+    bool final_done = false;  // final true residual computed
+    dgmg_ctx* ctx = nullptr;
+    cudaStream_t saved_stream = nullptr;
+    const double* f = nullptr;
+    double* u = nullptr;
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *ro = nullptr;
+    double r0 = 0.0, rtol = 1e-8;
+    dgmg_solve_stats st;
+    dgmg_status status = DGMG_OK;
+  };
+  Member m[kMaxBatch];
+  double* sc = nullptr;        // kMaxBatch * kScLen device scalars
+  double* sc_host = nullptr;   // pinned copy
+  double* partial = nullptr;   // kMaxBatch * kDotBlocks dot partials
+  std::vector<int> order;      // running slots, in launch order
+  bool order_valid = false;
+  cudaGraphExec_t graph = nullptr;
+  int graph_state = 0;         // 0: run eagerly once, 1: capture on the next iteration, 2: replay
+};
+
+namespace {
+
+dgmg_status fail_b(dgmg_batch* b, dgmg_status s, const std::string& msg) {
+  b->err = msg;
+  return s;
+}
+
+#define BK(expr)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail_b(b, DGMG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// A member's context call; its message becomes the batch's.
+#define BS(ctx, expr)                                 \
+  do {                                                \
+    dgmg_status s_ = (expr);                          \
+    if (s_ != DGMG_OK) return fail_b(b, s_, (ctx)->err); \
+  } while (0)
+
+void batch_invalidate(dgmg_batch* b) {
+  b->order_valid = false;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_state = 0;
+}
+
+void batch_order(dgmg_batch* b) {
+  if (b->order_valid) return;
+  b->order.clear();
+  for (int i = 0; i < kMaxBatch; ++i)
+    if (b->m[i].used && b->m[i].running) b->order.push_back(i);
+  b->order_valid = true;
+}
+
+// Segment table over the running members: vectors picked by `pick`.
+template <typename F>
+SegTable seg_table(dgmg_batch* b, long long len_scale, F pick) {
+  SegTable t;
+  t.k = (int)b->order.size();
+  for (int i = 0; i < t.k; ++i) {
+    dgmg_batch::Member& mb = b->m[b->order[i]];
+    t.n[i] = mb.ctx->ndof * len_scale;
+    t.sc[i] = b->sc + (size_t)b->order[i] * kScLen;
+    pick(mb, t, i);
+  }
+  return t;
+}
+
+BatchTable cell_table(dgmg_batch* b) {
+  BatchTable t;
+  t.k = (int)b->order.size();
+  for (int i = 0; i < t.k; ++i) t.mp[i] = params(b->m[b->order[i]].ctx);
+  return t;
+}
+
+// z = V(r) for every running member (Algorithm 1 with one pre- and one
+// post-sweep of block-Jacobi, inner PCG, Q1 + AMG): the steps of
+// vcycle_internal from a zero initial guess, each as one launch over the
+// members except the AMG cycles.
+dgmg_status batch_vcycle(dgmg_batch* b) {
+  const dgmg_solve_opts& o = b->opts;
+  const int prec = o.smoother_prec;
+  const bool fp32 = prec == DGMG_FP32;
+  const CellOps* ops = b->m[b->order[0]].ctx->ops;
+  const int K = (int)b->order.size();
+  auto F = [&](dgmg_batch::Member& mb) -> void* { return fp32 ? (void*)mb.ctx->w32[0] : (void*)mb.r; };
+  auto U = [&](dgmg_batch::Member& mb) -> void* { return fp32 ? (void*)mb.ctx->w32[1] : (void*)mb.z; };
+  auto T1 = [&](dgmg_batch::Member& mb) -> void* { return fp32 ? (void*)mb.ctx->w32[2] : (void*)mb.ctx->w64[0]; };
+  auto T2 = [&](dgmg_batch::Member& mb) -> void* { return fp32 ? (void*)mb.ctx->w32[3] : (void*)mb.ctx->w64[1]; };
+  const int n3 = b->m[b->order[0]].ctx->n * b->m[b->order[0]].ctx->n * b->m[b->order[0]].ctx->n;
+  const int maxit = o.maxit_inner > 0 ? o.maxit_inner : n3;
+  if (fp32) {
+    SegTable t = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+      s.a[i] = mb.r;
+      s.c[i] = F(mb);
+    });
+    BK(seg_op(SEG_D2F, t, b->stream));
+  }
+  auto sweep = [&](bool zero) -> dgmg_status {
+    BatchTable t = cell_table(b);
+    for (int i = 0; i < K; ++i) {
+      dgmg_batch::Member& mb = b->m[b->order[i]];
+      t.in[i] = F(mb);
+      t.uold[i] = zero ? nullptr : U(mb);
+      t.out[i] = T1(mb);
+      t.diag[i] = fp32 ? (const void*)mb.ctx->dinv32 : (const void*)mb.ctx->dinv64;
+    }
+    t.omega = o.omega;
+    t.eps = o.eps_inner;
+    t.maxit = maxit;
+    BK(ops->smooth_batch(t, prec, b->stream));
+    SegTable c = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+      s.a[i] = T1(mb);
+      s.c[i] = U(mb);
+    });
+    BK(seg_op(fp32 ? SEG_COPY32 : SEG_COPY64, c, b->stream));
+    return DGMG_OK;
+  };
+  CS(sweep(true));
+  {  // residual F - A U into T2
+    BatchTable t = cell_table(b);
+    for (int i = 0; i < K; ++i) {
+      dgmg_batch::Member& mb = b->m[b->order[i]];
+      t.in[i] = U(mb);
+      t.out[i] = T2(mb);
+    }
+    BK(ops->apply_batch(t, prec, true, b->stream));
+    SegTable s = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& st, int i) {
+      st.a[i] = F(mb);
+      st.b[i] = T2(mb);
+      st.c[i] = T2(mb);
+    });
+    BK(seg_op(fp32 ? SEG_SUB32 : SEG_SUB64, s, b->stream));
+  }
+  {  // restriction to Q1, AMG per member, prolongation
+    BatchTable t = cell_table(b);
+    for (int i = 0; i < K; ++i) {
+      dgmg_batch::Member& mb = b->m[b->order[i]];
+      t.in[i] = T2(mb);
+      t.out[i] = mb.ctx->corners;
+    }
+    BK(ops->restrict_batch(t, fp32, b->stream));
+    for (int i = 0; i < K; ++i) {
+      dgmg_ctx* ctx = b->m[b->order[i]].ctx;
+      BK(restrict_gather(ctx->nx, ctx->ny, ctx->nz, ctx->corners, ctx->q1h.rhat, b->stream));
+      BS(ctx, coarse_correction(ctx, ctx->q1h, o.coarse_cycles));
+    }
+    BatchTable pt = cell_table(b);
+    for (int i = 0; i < K; ++i) {
+      dgmg_batch::Member& mb = b->m[b->order[i]];
+      pt.in[i] = mb.ctx->q1h.uhat;
+      pt.out[i] = U(mb);
+    }
+    BK(ops->prolong_batch(pt, fp32, b->stream));
+  }
+  CS(sweep(false));
+  if (fp32) {
+    SegTable t = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+      s.a[i] = U(mb);
+      s.c[i] = mb.z;
+    });
+    BK(seg_op(SEG_F2D, t, b->stream));
+  }
+  return DGMG_OK;
+}
+
+// One outer iteration of every running member (the loop body of solve_cg).
+dgmg_status batch_iteration(dgmg_batch* b) {
+  const dgmg_solve_opts& o = b->opts;
+  const CellOps* ops = b->m[b->order[0]].ctx->ops;
+  const int K = (int)b->order.size();
+  const bool flex = o.krylov == DGMG_KRYLOV_FCG;
+  {  // q = A p
+    BatchTable t = cell_table(b);
+    for (int i = 0; i < K; ++i) {
+      t.in[i] = b->m[b->order[i]].p;
+      t.out[i] = b->m[b->order[i]].q;
+    }
+    BK(ops->apply_batch(t, o.apply_prec == DGMG_DF64 ? DGMG_DF64 : DGMG_FP64, true, b->stream));
+  }
+  SegTable pq = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+    s.a[i] = mb.p;
+    s.b[i] = mb.q;
+  });
+  BK(seg_dot(pq, b->partial, kScPq, b->stream));
+  BK(seg_scalar(SC_ALPHA, pq, b->stream));
+  SegTable up = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+    s.a[i] = mb.p;
+    s.b[i] = mb.q;
+    s.c[i] = mb.u;
+    s.d[i] = mb.r;
+    s.e[i] = mb.ro;
+  });
+  BK(seg_op(SEG_ALPHA, up, b->stream));
+  SegTable rr = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+    s.a[i] = mb.r;
+    s.b[i] = mb.r;
+  });
+  BK(seg_dot(rr, b->partial, kScRr, b->stream));
+  BK(seg_scalar(SC_CONV, rr, b->stream));
+  CS(batch_vcycle(b));
+  SegTable rz = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+    s.a[i] = mb.r;
+    s.b[i] = mb.z;
+  });
+  BK(seg_dot(rz, b->partial, kScRzn, b->stream));
+  if (flex) {
+    SegTable zr = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+      s.a[i] = mb.z;
+      s.b[i] = mb.ro;
+    });
+    BK(seg_dot(zr, b->partial, kScZro, b->stream));
+  }
+  BK(seg_scalar(SC_BETA, rz, b->stream));
+  SegTable pu = seg_table(b, 1, [&](dgmg_batch::Member& mb, SegTable& s, int i) {
+    s.a[i] = mb.z;
+    s.c[i] = mb.p;
+  });
+  BK(seg_op(SEG_P, pu, b->stream));
+  return DGMG_OK;
+}
+
+// Final true residual of a stopped member and its statistics (as dgmg_solve).
+dgmg_status batch_finish(dgmg_batch* b, dgmg_batch::Member& mb, const double* sc) {
+  dgmg_ctx* ctx = mb.ctx;
+  const long long n = ctx->ndof;
+  std::memset(&mb.st, 0, sizeof(mb.st));
+  if (mb.r0 == 0.0) {
+    mb.st.converged = 1;
+    mb.status = DGMG_OK;
+    mb.final_done = true;
+    return DGMG_OK;
+  }
+  const int state = (int)sc[kScDone];
+  mb.st.iterations = (int)sc[kScIts];
+  mb.st.iterations_run = mb.st.iterations;
+  BS(ctx, apply64(ctx, mb.u, mb.q));
+  BK(vec_sub(n, mb.f, mb.q, mb.r, b->stream));
+  double rr = 0.0;
+  BS(ctx, dot(ctx, mb.r, mb.r, rr));
+  mb.st.rel_residual = std::sqrt(rr) / mb.r0;
+  mb.st.converged = mb.st.rel_residual <= mb.rtol * (1.0 + 1e-6) ? 1 : 0;
+  if (state == 2) {
+    mb.status = DGMG_ERR_BREAKDOWN;
+  } else {
+    mb.status = mb.st.converged ? DGMG_OK : DGMG_ERR_NOT_CONVERGED;
+  }
+  mb.final_done = true;
+  return DGMG_OK;
+}
+
+// The options that shape a batched member's iterates (its initial state
+// included): the Krylov method and the V-cycle's.
+dgmg_solve_opts batch_key(const dgmg_solve_opts& o) {
+  dgmg_solve_opts k = precond_key(o);
+  k.krylov = o.krylov;
+  k.apply_prec = o.apply_prec;
+  return k;
+}
+
+// r = f - A u, ||r||, z = M r, p = z, (r, z) on the context's stream: the
+// steps of solve_cg before its loop, kept in the context for dgmg_batch_add.
+dgmg_status prime_internal(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts& o) {
+  const bool flex = o.krylov == DGMG_KRYLOV_FCG;
+  const long long n = ctx->ndof;
+  ctx->primed = false;
+  CS(ensure_krylov(ctx, flex ? 5 : 4));
+  double* r = ctx->kry;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  CS(apply64(ctx, u, q));
+  CK(vec_sub(n, f, q, r, ctx->stream));
+  double rr = 0.0;
+  CS(dot(ctx, r, r, rr));
+  const double r0 = std::sqrt(rr);
+  if (!std::isfinite(r0)) return fail(ctx, DGMG_ERR_ARG, "initial residual is not finite (NaN or Inf in f or u)");
+  double rz = 0.0;
+  if (r0 != 0.0) {
+    dgmg_solve_opts po = o;
+    po.graph = 0;
+    po.timing = 0;
+    CS(precond(ctx, r, z, po));
+    CK(vec_copy(n, z, p, ctx->stream));
+    CS(dot(ctx, r, z, rz));
+  }
+  ctx->prime_f = f;
+  ctx->prime_u = u;
+  ctx->prime_r0 = r0;
+  ctx->prime_rz = rz;
+  ctx->prime_key = batch_key(o);
+  ctx->primed = true;
+  return DGMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgmg_status dgmg_batch_create(dgmg_batch** out, int device, void* cuda_stream, const dgmg_solve_opts* opts) {
+  if (!out) return DGMG_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return DGMG_ERR_ARG;
+  }
+  dgmg_solve_opts o;
+  dgmg_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.krylov != DGMG_KRYLOV_CG && o.krylov != DGMG_KRYLOV_FCG) return DGMG_ERR_ARG;
+  if (o.smoother_prec < DGMG_FP64 || o.smoother_prec > DGMG_DF64) return DGMG_ERR_ARG;
+  if (o.apply_prec != DGMG_FP64 && o.apply_prec != DGMG_DF64) return DGMG_ERR_ARG;
+  if (o.inner != DGMG_INNER_PCG || o.smoother != DGMG_SMOOTHER_JACOBI || o.coarse != DGMG_COARSE_AMG ||
+      o.npre != 1 || o.npost != 1 || o.stop != DGMG_STOP_RESIDUAL || o.coarse_cycles < 1)
+    return DGMG_ERR_ARG;
+  dgmg_batch* b = new dgmg_batch();
+  b->device = device;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->opts = o;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->sc, sizeof(double) * kMaxBatch * kScLen);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->partial, sizeof(double) * kMaxBatch * kDotBlocks);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->sc_host, sizeof(double) * kMaxBatch * kScLen);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (b->sc) cudaFree(b->sc);
+    if (b->partial) cudaFree(b->partial);
+    delete b;
+    return DGMG_ERR_CUDA;
+  }
+  *out = b;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_batch_destroy(dgmg_batch* b) {
+  if (!b) return DGMG_ERR_ARG;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  for (int i = 0; i < kMaxBatch; ++i)
+    if (b->m[i].used) b->m[i].ctx->stream = b->m[i].saved_stream;
+  batch_invalidate(b);
+  cudaFree(b->sc);
+  cudaFree(b->partial);
+  cudaFreeHost(b->sc_host);
+  delete b;
+  return DGMG_OK;
+}
+
+const char* dgmg_batch_last_error(const dgmg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+dgmg_status dgmg_batch_prime(dgmg_ctx* ctx, const double* f, double* u, const dgmg_solve_opts* opts) {
+  CS(ready(ctx));
+  if (!f || !u || f == u) return fail(ctx, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
+  dgmg_solve_opts o;
+  dgmg_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.krylov != DGMG_KRYLOV_CG && o.krylov != DGMG_KRYLOV_FCG) return fail(ctx, DGMG_ERR_ARG, "CG or FCG only");
+  CS(check_df64(ctx, o.smoother_prec, o.inner));
+  CS(check_df64(ctx, o.apply_prec, DGMG_INNER_PCG));
+  cudaSetDevice(ctx->device);
+  return prime_internal(ctx, f, u, o);
+}
+
+dgmg_status dgmg_batch_add(dgmg_batch* b, dgmg_ctx* ctx, const double* f, double* u, double rtol, int maxit,
+                           int* slot) {
+  if (!b || !ctx || !slot) return DGMG_ERR_ARG;
+  *slot = -1;
+  if (ready(ctx) != DGMG_OK) return fail_b(b, DGMG_ERR_STATE, "the context needs a mesh and coefficients");
+  if (!f || !u || f == u) return fail_b(b, DGMG_ERR_ARG, "f, u must be distinct non-NULL device pointers");
+  if (!(rtol > 0.0) || maxit < 1) return fail_b(b, DGMG_ERR_ARG, "rtol > 0 and maxit >= 1 required");
+  if (ctx->device != b->device) return fail_b(b, DGMG_ERR_ARG, "the context is on another device");
+  if (ctx->db || ctx->var_on) return fail_b(b, DGMG_ERR_ARG, "batched solves cover b = 0 with cell-wise K, c");
+  int free_slot = -1;
+  for (int i = 0; i < kMaxBatch; ++i) {
+    if (b->m[i].used) {
+      if (b->m[i].ctx == ctx) return fail_b(b, DGMG_ERR_ARG, "the context is already in the batch");
+      if (b->m[i].ctx->n != ctx->n) return fail_b(b, DGMG_ERR_ARG, "the members of a batch share the order p");
+      const MeshParams a = params(b->m[i].ctx), c = params(ctx);
+      for (int k = 0; k < 3; ++k)
+        if (a.lay_apply[k] != c.lay_apply[k] || a.lay_smooth[k] != c.lay_smooth[k])
+          return fail_b(b, DGMG_ERR_ARG, "the members of a batch share the kernel layouts");
+    } else if (free_slot < 0) {
+      free_slot = i;
+    }
+  }
+  if (free_slot < 0) return fail_b(b, DGMG_ERR_ARG, "the batch is full");
+  const dgmg_solve_opts& o = b->opts;
+  if (check_df64(ctx, o.smoother_prec, o.inner) != DGMG_OK || check_df64(ctx, o.apply_prec, DGMG_INNER_PCG) != DGMG_OK)
+    return fail_b(b, DGMG_ERR_ARG, ctx->err);
+  cudaSetDevice(b->device);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail_b(b, DGMG_ERR_CUDA, "context stream");
+  dgmg_batch::Member& mb = b->m[free_slot];
+  mb = dgmg_batch::Member();
+  mb.used = true;
+  mb.ctx = ctx;
+  mb.saved_stream = ctx->stream;
+  ctx->stream = b->stream;   // the member's work runs on the batch's stream while it belongs to it
+  mb.f = f;
+  mb.u = u;
+  mb.rtol = rtol;
+  auto undo = [&](dgmg_status s) {
+    ctx->stream = mb.saved_stream;
+    mb.used = false;
+    return fail_b(b, s, ctx->err);
+  };
+  const bool flex = o.krylov == DGMG_KRYLOV_FCG;
+  const long long n = ctx->ndof;
+  const dgmg_solve_opts key = batch_key(o);
+  const bool primed = ctx->primed && ctx->prime_f == f && ctx->prime_u == u &&
+                      std::memcmp(&ctx->prime_key, &key, sizeof(key)) == 0;
+  ctx->primed = false;
+  if (!primed) {   // the initial state on the batch's stream
+    dgmg_status s = prime_internal(ctx, f, u, o);
+    if (s != DGMG_OK) return undo(s);
+  }
+  mb.r = ctx->kry;
+  mb.z = mb.r + n;
+  mb.p = mb.z + n;
+  mb.q = mb.p + n;
+  mb.ro = flex ? mb.q + n : nullptr;
+  mb.r0 = ctx->prime_r0;
+  double* sc = b->sc_host + (size_t)free_slot * kScLen;
+  for (int k = 0; k < kScLen; ++k) sc[k] = 0.0;
+  if (mb.r0 == 0.0) {
+    mb.finished = true;
+    mb.running = false;
+  } else {
+    sc[kScRz] = ctx->prime_rz;
+    sc[kScR0] = mb.r0;
+    sc[kScRtol] = rtol;
+    sc[kScMaxit] = (double)maxit;
+    sc[kScFlex] = flex ? 1.0 : 0.0;
+    mb.running = true;
+  }
+  BK(cudaMemcpyAsync(b->sc + (size_t)free_slot * kScLen, sc, sizeof(double) * kScLen, cudaMemcpyHostToDevice,
+                     b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  batch_invalidate(b);
+  *slot = free_slot;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_batch_step(dgmg_batch* b, int iterations, int* running) {
+  if (!b || iterations < 0) return DGMG_ERR_ARG;
+  cudaSetDevice(b->device);
+  batch_order(b);
+  if (!b->order.empty()) {
+    for (int it = 0; it < iterations; ++it) {
+      if (!b->stream) {   // the legacy default stream cannot be captured: eager launches
+        CS(batch_iteration(b));
+      } else if (b->graph_state == 2) {
+        BK(cudaGraphLaunch(b->graph, b->stream));
+      } else if (b->graph_state == 0) {   // first iteration of this membership: eager (sets kernel attributes)
+        CS(batch_iteration(b));
+        b->graph_state = 1;
+      } else {
+        BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        dgmg_status s = batch_iteration(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (s != DGMG_OK) {
+          if (g) cudaGraphDestroy(g);
+          return s;
+        }
+        if (e != cudaSuccess) return fail_b(b, DGMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail_b(b, DGMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        b->graph_state = 2;
+        BK(cudaGraphLaunch(b->graph, b->stream));
+      }
+    }
+  }
+  BK(cudaMemcpyAsync(b->sc_host, b->sc, sizeof(double) * kMaxBatch * kScLen, cudaMemcpyDeviceToHost, b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  int left = 0;
+  for (int i : b->order) {
+    if (b->sc_host[(size_t)i * kScLen + kScDone] != 0.0) {
+      b->m[i].running = false;
+      b->m[i].finished = true;
+      batch_invalidate(b);
+    } else {
+      ++left;
+    }
+  }
+  if (running) *running = left;
+  return DGMG_OK;
+}
+
+dgmg_status dgmg_batch_poll(dgmg_batch* b, int slot, int* done, dgmg_solve_stats* stats) {
+  if (!b || slot < 0 || slot >= kMaxBatch || !b->m[slot].used || !done) return DGMG_ERR_ARG;
+  dgmg_batch::Member& mb = b->m[slot];
+  *done = mb.finished ? 1 : 0;
+  if (!mb.finished) return DGMG_OK;
+  if (!mb.final_done) {
+    cudaSetDevice(b->device);
+    CS(batch_finish(b, mb, b->sc_host + (size_t)slot * kScLen));
+  }
+  if (stats) *stats = mb.st;
+  return mb.status;
+}
+
+dgmg_status dgmg_batch_remove(dgmg_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= kMaxBatch || !b->m[slot].used) return DGMG_ERR_ARG;
+  cudaSetDevice(b->device);
+  BK(cudaStreamSynchronize(b->stream));
+  dgmg_batch::Member& mb = b->m[slot];
+  mb.ctx->stream = mb.saved_stream;
+  mb = dgmg_batch::Member();
+  batch_invalidate(b);
   return DGMG_OK;
 }
 

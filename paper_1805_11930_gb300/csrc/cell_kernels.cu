@@ -1017,13 +1017,14 @@ __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T**
   if (cid) *cid = reinterpret_cast<long long*>(*act + 16);
 }
 
-template <typename T, bool FULL, bool ADV, bool FAC, typename G = typename Store<T>::type>
-__global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restrict__ u, G* __restrict__ v) {
+template <typename T, bool FULL, bool ADV, bool FAC, typename G>
+__device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __restrict__ u, G* __restrict__ v,
+                                           unsigned bid) {
   static_assert(!(FAC && ADV), "the factored form is for b = 0");
   const bool react = mp.c != nullptr;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long cell0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+  const long long cell0 = ((long long)bid * (blockDim.x >> 5) + warp) * CPW;
   if (cell0 >= mp.ncell) return;
   T* vec[4];
   T *F0, *F1, *red;
@@ -1055,6 +1056,25 @@ __global__ void __launch_bounds__(256) k_apply(MeshParams mp, const G* __restric
   }
   G* vg = v + cell0 * N3;
   for (int e = lane; e < nval; e += 32) vg[e] = static_cast<G>(Y[e]);
+}
+
+template <typename T, bool FULL, bool ADV, bool FAC, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(256) k_apply(const __grid_constant__ MeshParams mp, const G* __restrict__ u,
+                                               G* __restrict__ v) {
+  apply_body<T, FULL, ADV, FAC, G>(mp, u, v, blockIdx.x);
+}
+
+// Member of a batch that owns block bid (block0 ascending, block0[0] = 0).
+__device__ __forceinline__ int batch_member(const BatchTable& bt, unsigned bid) {
+  int r = 0;
+  while (r + 1 < bt.k && bid >= bt.block0[r + 1]) ++r;
+  return r;
+}
+
+template <typename T, bool FULL, bool ADV, bool FAC, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(256) k_apply_batch(const __grid_constant__ BatchTable bt) {
+  const int r = batch_member(bt, blockIdx.x);
+  apply_body<T, FULL, ADV, FAC, G>(bt.mp[r], (const G*)bt.in[r], (G*)bt.out[r], blockIdx.x - bt.block0[r]);
 }
 
 // Sum over the lanes that own lines of the same cell; every lane of that cell
@@ -1123,14 +1143,13 @@ __host__ __device__ constexpr int smooth_extra() {
 // (advection).  With several cells per warp each lane owns one z-line of its
 // cell for the pointwise vector operations; with one cell per warp every lane
 // takes elements lane, lane + 32, ... (all 32 lanes busy).
-template <typename T, bool ADV, bool FAC, typename G = typename Store<T>::type>
-__global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __restrict__ f,
-                                                         const G* uold, G* unew, const G* __restrict__ diag,
-                                                         T omega, T eps, int maxit, int* __restrict__ its,
-                                                         int color) {
+template <typename T, bool ADV, bool FAC, typename G>
+__device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* __restrict__ f, const G* uold, G* unew,
+                                                const G* __restrict__ diag, T omega, T eps, int maxit,
+                                                int* __restrict__ its, int color, unsigned bid) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long s0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+  const long long s0 = ((long long)bid * (blockDim.x >> 5) + warp) * CPW;
   if (s0 >= color_count(mp, color)) return;
   T *F0, *F1, *red;
   CellInfo<T>* ci;
@@ -1271,6 +1290,21 @@ __global__ void __launch_bounds__(256) k_smooth_pcg(MeshParams mp, const G* __re
       unew[g] = static_cast<G>(zero ? omega * dl : fma(omega, dl, T(uold[g])));
     });
   if (its && lead && mycw >= 0 && cid[mycw] >= 0) its[cid[mycw]] = it;
+}
+
+template <typename T, bool ADV, bool FAC, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(256) k_smooth_pcg(const __grid_constant__ MeshParams mp, const G* __restrict__ f,
+                                                    const G* uold, G* unew, const G* __restrict__ diag, T omega,
+                                                    T eps, int maxit, int* __restrict__ its, int color) {
+  smooth_pcg_body<T, ADV, FAC, G>(mp, f, uold, unew, diag, omega, eps, maxit, its, color, blockIdx.x);
+}
+
+template <typename T, bool ADV, bool FAC, typename G = typename Store<T>::type>
+__global__ void __launch_bounds__(256) k_smooth_pcg_batch(const __grid_constant__ BatchTable bt) {
+  const int r = batch_member(bt, blockIdx.x);
+  smooth_pcg_body<T, ADV, FAC, G>(bt.mp[r], (const G*)bt.in[r], (const G*)bt.uold[r], (G*)bt.out[r],
+                                  (const G*)bt.diag[r], T(bt.omega), T(bt.eps), bt.maxit, bt.its[r], -1,
+                                  blockIdx.x - bt.block0[r]);
 }
 
 // D_T of each cell column by column: column j is the block operator (volume
@@ -2140,14 +2174,48 @@ __global__ void k_diag(MeshParams mp, double* __restrict__ diag) {
   diag[gid] = acc;
 }
 
+// diag(D_T) for b = 0 from the Kronecker form of reading 20,
+// D_T = A_x (x) M (x) M + M (x) A_y (x) M + M (x) M (x) A_z:
+//   diag(D_T)(i0, i1, i2) = a_x(i0) m(i1) m(i2) + m(i0) a_y(i1) m(i2) + m(i0) m(i1) a_z(i2),
+// m = diag(M), a_d = diag(A_d) = |J| K_d / h_d^2 S_ii (+ c |J| M_ii for d = 2)
+// + on each non-Neumann face s of d, at its end node e: |F| (2 ks dl_s(e) + gamma),
+// ks = -kap sg / h_d (the diagonal of the per-cell matrices of block_matrices).
+// n^3 work per cell instead of the n^6 of the quadrature in k_diag.
+__global__ void k_diag_kron(MeshParams mp, double* __restrict__ diag) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= mp.ncell * N3) return;
+  const long long c = gid / N3;
+  const int i = (int)(gid - c * N3);
+  const int ii[3] = {i % N, (i / N) % N, i / N2};
+  const Tab<double>& t = c_tab_d;
+  const double* rec = mp.rec64 + c * kRecLen;
+  double a[3];
+  for (int d = 0; d < 3; ++d) {
+    const int k = ii[d];
+    double v = rec[kRecKd + d] * t.S1[k][k];
+    if (d == 2) v = fma(rec[kRecCJ], t.M1[k][k], v);
+    for (int s = 0; s < 2; ++s) {
+      if (k != (s ? N - 1 : 0)) continue;
+      long long nb;
+      if (face_kind(mp, c, d, s, nb) == 2) continue;
+      const double kap = rec[kRecKap + 2 * d + s], gam = rec[kRecGam + 2 * d + s];
+      const double ks = (s ? -kap : kap) * mp.ih[d];
+      v = fma(mp.jh[d], 2.0 * ks * t.dl[s][k] + gam, v);
+    }
+    a[d] = v;
+  }
+  const double m0 = t.M1[ii[0]][ii[0]], m1 = t.M1[ii[1]][ii[1]], m2 = t.M1[ii[2]][ii[2]];
+  diag[gid] = a[0] * m1 * m2 + m0 * a[1] * m2 + m0 * m1 * a[2];
+}
+
 // Corner sums r_hat_c(T) = sum_i prod_k phi_{c_k}(zeta_{i_k}) r_T(i) (the cell
 // part of R = P^T): one warp per cell, each lane accumulates the 8 corner
 // weights over its dofs in the kernel's precision, then a fixed-order warp
 // reduction.
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_cells(long long ncell, const T* __restrict__ r,
-                                                        double* __restrict__ corners) {
-  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void restrict_cells_body(long long ncell, const T* __restrict__ r,
+                                                    double* __restrict__ corners, unsigned bid) {
+  const long long c = ((long long)bid * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= ncell) return;
   const Tab<T>& t = tab<T>();
@@ -2182,12 +2250,24 @@ __global__ void __launch_bounds__(256) k_restrict_cells(long long ncell, const T
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_cells(long long ncell, const T* __restrict__ r,
+                                                        double* __restrict__ corners) {
+  restrict_cells_body<T>(ncell, r, corners, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_cells_batch(const __grid_constant__ BatchTable bt) {
+  const int m = batch_member(bt, blockIdx.x);
+  restrict_cells_body<T>(bt.mp[m].ncell, (const T*)bt.in[m], (double*)bt.out[m], blockIdx.x - bt.block0[m]);
+}
+
 // u_T(i) += sum_c u_hat(vertex(T, c)) prod_k phi_{c_k}(zeta_{i_k}): one warp
 // per cell; the 8 corner values are loaded once and broadcast.
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong_add(MeshParams mp, const double* __restrict__ uhat,
-                                                     T* __restrict__ u) {
-  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void prolong_add_body(const MeshParams& mp, const double* __restrict__ uhat,
+                                                 T* __restrict__ u, unsigned bid) {
+  const long long c = ((long long)bid * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= mp.ncell) return;
   int cx, cy, cz;
@@ -2212,6 +2292,18 @@ __global__ void __launch_bounds__(256) k_prolong_add(MeshParams mp, const double
     const T f0 = fma(y1, e10, y0 * e00), f1 = fma(y1, e11, y0 * e01);
     uc[i] += fma(t.hat[1][i3], f1, t.hat[0][i3] * f0);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(const __grid_constant__ MeshParams mp,
+                                                     const double* __restrict__ uhat, T* __restrict__ u) {
+  prolong_add_body<T>(mp, uhat, u, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add_batch(const __grid_constant__ BatchTable bt) {
+  const int m = batch_member(bt, blockIdx.x);
+  prolong_add_body<T>(bt.mp[m], (const double*)bt.in[m], (T*)bt.out[m], blockIdx.x - bt.block0[m]);
 }
 
 #include "plane_kernels.cuh"
@@ -2584,7 +2676,7 @@ cudaError_t diag(const MeshParams& mp, double* d, cudaStream_t s) {
   if (mp.bvert)
     k_diag<true><<<grid, 128, 0, s>>>(mp, d);
   else
-    k_diag<false><<<grid, 128, 0, s>>>(mp, d);
+    k_diag_kron<<<grid, 128, 0, s>>>(mp, d);
   count_launch();
   return cudaGetLastError();
 }
@@ -2611,6 +2703,146 @@ cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- batched launchers
+// One launch over the members of a batch (b = 0): member r gets
+// ceil(ncell_r / cells per block) blocks; layouts and launch shapes of member 0.
+inline void fill_blocks(BatchTable& bt, long long cells_per_block) {
+  bt.block0[0] = 0;
+  for (int r = 0; r < bt.k; ++r)
+    bt.block0[r + 1] = bt.block0[r] + (unsigned)((bt.mp[r].ncell + cells_per_block - 1) / cells_per_block);
+}
+
+template <typename T, bool FULL, bool FAC>
+cudaError_t launch_apply_batch_form(BatchTable& bt, cudaStream_t s) {
+  constexpr int XT = FAC ? kFactorExtra : 0;
+  const int wpb = pick_wpb(bt.mp[0].wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
+  const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
+  auto k = k_apply_batch<T, FULL, false, FAC>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  fill_blocks(bt, (long long)wpb * CPW);
+  if (bt.block0[bt.k] == 0) return cudaSuccess;
+  k<<<bt.block0[bt.k], wpb * 32, sm, s>>>(bt);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, bool FULL>
+cudaError_t apply_batch_t(BatchTable& bt, cudaStream_t s) {
+  const int lay = bt.mp[0].lay_apply[prec_index<T>()];
+#if DGMG_N <= 5
+  if constexpr (std::is_same<T, float>::value) {
+    if (lay == DGMG_LAYOUT_PLANE) {
+      const size_t per = pl::warp_bytes(FULL);
+      const int wpb = pick_wpb_max(bt.mp[0].wpb_apply[DGMG_FP32], per, 8);
+      const size_t sm = wpb * per;
+      auto k = k_apply_plane_batch<FULL>;
+      cudaError_t e = set_smem(k, sm);
+      if (e != cudaSuccess) return e;
+      fill_blocks(bt, (long long)wpb * pl::PC);
+      if (bt.block0[bt.k] == 0) return cudaSuccess;
+      k<<<bt.block0[bt.k], wpb * 32, sm, s>>>(bt);
+      count_launch();
+      return cudaGetLastError();
+    }
+  }
+#endif
+  if (lay == DGMG_LAYOUT_LINE || lay == DGMG_LAYOUT_PLANE) return launch_apply_batch_form<T, FULL, false>(bt, s);
+  return launch_apply_batch_form<T, FULL, true>(bt, s);
+}
+
+cudaError_t apply_batch(BatchTable& bt, int prec, bool full, cudaStream_t s) {
+  if (bt.k <= 0) return cudaSuccess;
+  for (int r = 0; r < bt.k; ++r)
+    if (bt.mp[r].bvert) return cudaErrorNotSupported;
+  if (prec == DGMG_FP32) return full ? apply_batch_t<float, true>(bt, s) : apply_batch_t<float, false>(bt, s);
+  if (prec == DGMG_DF64) {
+#if DGMG_N <= 7
+    return full ? apply_batch_t<df, true>(bt, s) : apply_batch_t<df, false>(bt, s);
+#else
+    return cudaErrorNotSupported;
+#endif
+  }
+  return full ? apply_batch_t<double, true>(bt, s) : apply_batch_t<double, false>(bt, s);
+}
+
+template <typename T, bool FAC>
+cudaError_t launch_smooth_batch_form(BatchTable& bt, cudaStream_t s) {
+  constexpr int XT = smooth_extra<false, FAC>();
+  const int wpb = pick_wpb(bt.mp[0].wpb_smooth[prec_index<T>()], WarpMem<T>::bytes(6, XT));
+  const size_t sm = wpb * WarpMem<T>::bytes(6, XT);
+  auto k = k_smooth_pcg_batch<T, false, FAC>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  fill_blocks(bt, (long long)wpb * CPW);
+  if (bt.block0[bt.k] == 0) return cudaSuccess;
+  k<<<bt.block0[bt.k], wpb * 32, sm, s>>>(bt);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t smooth_batch_t(BatchTable& bt, cudaStream_t s) {
+  const int lay = bt.mp[0].lay_smooth[prec_index<T>()];
+#if DGMG_N <= 5
+  if constexpr (std::is_same<T, float>::value) {
+    if (lay == DGMG_LAYOUT_PLANE) {
+      const size_t per = pl::warp_bytes(true);
+      const int wpb = pick_wpb_max(bt.mp[0].wpb_smooth[DGMG_FP32], per, 4);
+      const size_t sm = wpb * per;
+      cudaError_t e = set_smem(k_smooth_plane_batch, sm);
+      if (e != cudaSuccess) return e;
+      fill_blocks(bt, (long long)wpb * pl::PC);
+      if (bt.block0[bt.k] == 0) return cudaSuccess;
+      k_smooth_plane_batch<<<bt.block0[bt.k], wpb * 32, sm, s>>>(bt);
+      count_launch();
+      return cudaGetLastError();
+    }
+  }
+#endif
+  if (lay == DGMG_LAYOUT_LINE || lay == DGMG_LAYOUT_PLANE) return launch_smooth_batch_form<T, false>(bt, s);
+  return launch_smooth_batch_form<T, true>(bt, s);
+}
+
+cudaError_t smooth_batch(BatchTable& bt, int prec, cudaStream_t s) {
+  if (bt.k <= 0) return cudaSuccess;
+  for (int r = 0; r < bt.k; ++r)
+    if (bt.mp[r].bvert) return cudaErrorNotSupported;
+  if (prec == DGMG_FP32) return smooth_batch_t<float>(bt, s);
+  if (prec == DGMG_DF64) {
+#if DGMG_N <= 7
+    return smooth_batch_t<df>(bt, s);
+#else
+    return cudaErrorNotSupported;
+#endif
+  }
+  return smooth_batch_t<double>(bt, s);
+}
+
+cudaError_t restrict_batch(BatchTable& bt, bool fp32, cudaStream_t s) {
+  if (bt.k <= 0) return cudaSuccess;
+  fill_blocks(bt, 8);   // one warp per cell, 8 warps per block
+  if (bt.block0[bt.k] == 0) return cudaSuccess;
+  if (fp32)
+    k_restrict_cells_batch<float><<<bt.block0[bt.k], 256, 0, s>>>(bt);
+  else
+    k_restrict_cells_batch<double><<<bt.block0[bt.k], 256, 0, s>>>(bt);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t prolong_batch(BatchTable& bt, bool fp32, cudaStream_t s) {
+  if (bt.k <= 0) return cudaSuccess;
+  fill_blocks(bt, 8);
+  if (bt.block0[bt.k] == 0) return cudaSuccess;
+  if (fp32)
+    k_prolong_add_batch<float><<<bt.block0[bt.k], 256, 0, s>>>(bt);
+  else
+    k_prolong_add_batch<double><<<bt.block0[bt.k], 256, 0, s>>>(bt);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 #define DGMG_CAT2(a, b) a##b
@@ -2618,7 +2850,8 @@ cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool 
 
 const CellOps* DGMG_CAT(cell_ops_n, DGMG_N)() {
   static const CellOps ops = {N, &upload_tables, &apply, &smooth, &diag, &restrict_cells, &prolong_add,
-                              &block_matrix, &block_tridiag, &apply_var};
+                              &block_matrix, &block_tridiag, &apply_var, &apply_batch, &smooth_batch,
+                              &restrict_batch, &prolong_batch};
   return &ops;
 }
 

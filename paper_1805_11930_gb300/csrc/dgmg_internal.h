@@ -85,6 +85,24 @@ struct SmoothArgs {
   int color = -1;         // -1: all cells (Jacobi); 0..7: one parity class, in place allowed
 };
 
+// Requests of one order served by one launch: member r owns the blocks
+// [block0[r], block0[r+1]) of the grid (the launcher fills block0 from each
+// member's cell count and the launch shape), and its own mesh parameters and
+// vectors.  Passed by value as a __grid_constant__ kernel parameter.
+constexpr int kMaxBatch = DGMG_BATCH_MAX;
+struct BatchTable {
+  int k = 0;
+  unsigned block0[kMaxBatch + 1] = {};
+  MeshParams mp[kMaxBatch];
+  const void* in[kMaxBatch] = {};    // operator input; smoother f; restriction r; prolongation u_hat
+  void* out[kMaxBatch] = {};         // operator output; smoother u_new; corner sums; prolongation u
+  const void* uold[kMaxBatch] = {};  // smoother u_old (nullptr: zero start)
+  const void* diag[kMaxBatch] = {};  // smoother 1 / diag(D_T)
+  int* its[kMaxBatch] = {};          // smoother per-cell inner iteration counts, or nullptr
+  double omega = 1.0, eps = 1e-2;    // smoother parameters shared by the members
+  int maxit = 0;
+};
+
 // Per-order kernel entry points, one table per n (cell_kernels.cu built with
 // -DDGMG_N=n).
 struct CellOps {
@@ -107,6 +125,12 @@ struct CellOps {
   cudaError_t (*block_tridiag)(const MeshParams& mp, double* out, int* singular, cudaStream_t s);
   // v = A u with K(x), c(x) varying inside the cells (mp.var), FP64, b = 0
   cudaError_t (*apply_var)(const MeshParams& mp, const double* u, double* v, cudaStream_t s);
+  // The same for the members of a batch in one launch each (b = 0, the
+  // layouts and launch shapes of member 0); block0 is filled here.
+  cudaError_t (*apply_batch)(BatchTable& bt, int prec, bool full, cudaStream_t s);
+  cudaError_t (*smooth_batch)(BatchTable& bt, int prec, cudaStream_t s);   // inner-PCG Jacobi sweep
+  cudaError_t (*restrict_batch)(BatchTable& bt, bool fp32, cudaStream_t s);
+  cudaError_t (*prolong_batch)(BatchTable& bt, bool fp32, cudaStream_t s);
 };
 
 const CellOps* cell_ops(int n);
@@ -142,6 +166,51 @@ cudaError_t vec_dot(long long n, const double* x, const double* y, double* parti
 cudaError_t vec_multi_dot(long long n, int k, const double* const* xs, const double* y,
                           double* partial, double* out, cudaStream_t s);
 constexpr int kDotBlocks = 1024;
+
+// ---------------------------------------------------------------- batched Krylov
+// Segments of a batch for the vector kernels: member r's vectors a..e of
+// length n[r] and its device scalar block sc[r] (kScLen doubles); the blocks
+// of a launch are split among the members by block0 (filled by the launcher).
+struct SegTable {
+  int k = 0;
+  unsigned block0[kMaxBatch + 1] = {};
+  long long n[kMaxBatch] = {};
+  const void* a[kMaxBatch] = {};
+  const void* b[kMaxBatch] = {};
+  void* c[kMaxBatch] = {};
+  void* d[kMaxBatch] = {};
+  void* e[kMaxBatch] = {};
+  double* sc[kMaxBatch] = {};
+};
+
+// Scalar block of a member of a batched CG / flexible CG: (r, z), (p, q),
+// alpha, (r, r), new (r, z), (z, r_old), beta, ||r_0||, rtol, state (0
+// running, 1 converged, 2 breakdown, 3 iteration cap), iterations, maxit,
+// flexible (0 / 1).
+constexpr int kScRz = 0, kScPq = 1, kScAlpha = 2, kScRr = 3, kScRzn = 4, kScZro = 5, kScBeta = 6, kScR0 = 7,
+              kScRtol = 8, kScDone = 9, kScIts = 10, kScMaxit = 11, kScFlex = 12, kScLen = 16;
+
+enum SegOp {
+  SEG_D2F,      // c = (float) a
+  SEG_F2D,      // c = (double) a
+  SEG_COPY64,   // c = a (FP64)
+  SEG_COPY32,   // c = a (FP32)
+  SEG_SUB64,    // c = a - b (FP64)
+  SEG_SUB32,    // c = a - b (FP32)
+  SEG_ALPHA,    // CG update with alpha = sc[kScAlpha]: (flexible: e = d,) c += alpha a, d -= alpha b
+                // (a = p, b = q, c = u, d = r, e = r_old)
+  SEG_P         // c = a + beta c with beta = sc[kScBeta] (a = z, c = p)
+};
+enum ScalOp {
+  SC_ALPHA,     // alpha = (r, z) / (p, q), or 0 and state 2 when (p, q) <= 0, or 0 when stopped
+  SC_CONV,      // iterations += 1; state 1 when sqrt((r, r)) <= rtol ||r_0||, 3 at maxit
+  SC_BETA       // beta = ((r, z)_new - flexible (z, r_old)) / (r, z); (r, z) <- new; 0 when stopped
+};
+cudaError_t seg_op(int op, SegTable& t, cudaStream_t s);
+// sc[r][slot] = (a_r, b_r) with the summation order of vec_dot; partial:
+// k * kDotBlocks doubles.
+cudaError_t seg_dot(SegTable& t, double* partial, int slot, cudaStream_t s);
+cudaError_t seg_scalar(int op, SegTable& t, cudaStream_t s);
 
 // 27-point stencil operators of the AMG levels (row-major, 27 per row).
 cudaError_t stencil_jacobi(int vx, int vy, int vz, const double* st, const double* dinv,

@@ -263,11 +263,12 @@ __device__ __forceinline__ float cell_sum(float x, int cw) {
 
 // v = A u (FULL) or D_T u, FP32, b = 0, plane per lane.
 template <bool FULL>
-__global__ void __launch_bounds__(256) k_apply_plane(MeshParams mp, const float* __restrict__ u, float* __restrict__ v) {
+__device__ __forceinline__ void apply_plane_body(const MeshParams& mp, const float* __restrict__ u,
+                                                 float* __restrict__ v, unsigned bid) {
   using namespace pl;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long cell0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * PC;
+  const long long cell0 = ((long long)bid * (blockDim.x >> 5) + warp) * PC;
   if (cell0 >= mp.ncell) return;
   const Mem m = carve_plane(smem + warp * warp_bytes(FULL), FULL);
   stage_cells<float, PC>(mp, cell0, lane, m.ci, m.act);
@@ -289,17 +290,29 @@ __global__ void __launch_bounds__(256) k_apply_plane(MeshParams mp, const float*
   store_cells(v, cell0, nval, m.st, lane);
 }
 
+template <bool FULL>
+__global__ void __launch_bounds__(256) k_apply_plane(const __grid_constant__ MeshParams mp,
+                                                     const float* __restrict__ u, float* __restrict__ v) {
+  apply_plane_body<FULL>(mp, u, v, blockIdx.x);
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(256) k_apply_plane_batch(const __grid_constant__ BatchTable bt) {
+  const int r = batch_member(bt, blockIdx.x);
+  apply_plane_body<FULL>(bt.mp[r], (const float*)bt.in[r], (float*)bt.out[r], blockIdx.x - bt.block0[r]);
+}
+
 // Block-Jacobi sweep with inner PCG, FP32, b = 0, plane per lane (the same
 // algorithm as k_smooth_pcg: defect, PCG on D_T with 1/diag(D_T) from 0 on
 // d / ||d|| to ||r|| <= eps, u_new = u_old + omega delta).
-__global__ void __launch_bounds__(128) k_smooth_plane(MeshParams mp, const float* __restrict__ f,
-                                                      const float* uold, float* unew,
-                                                      const float* __restrict__ diag, float omega, float eps,
-                                                      int maxit, int* __restrict__ its) {
+__device__ __forceinline__ void smooth_plane_body(const MeshParams& mp, const float* __restrict__ f,
+                                                  const float* uold, float* unew, const float* __restrict__ diag,
+                                                  float omega, float eps, int maxit, int* __restrict__ its,
+                                                  unsigned bid) {
   using namespace pl;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long cell0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * PC;
+  const long long cell0 = ((long long)bid * (blockDim.x >> 5) + warp) * PC;
   if (cell0 >= mp.ncell) return;
   const Mem m = carve_plane(smem + warp * warp_bytes(true), true);
   stage_cells<float, PC>(mp, cell0, lane, m.ci, m.act);
@@ -412,5 +425,19 @@ __global__ void __launch_bounds__(128) k_smooth_plane(MeshParams mp, const float
   __syncwarp();
   store_cells(unew, cell0, nval, m.st, lane);
   if (its && on && k == 0 && m.act[cw]) its[cell0 + cw] = it;
+}
+
+__global__ void __launch_bounds__(128) k_smooth_plane(const __grid_constant__ MeshParams mp,
+                                                      const float* __restrict__ f, const float* uold, float* unew,
+                                                      const float* __restrict__ diag, float omega, float eps,
+                                                      int maxit, int* __restrict__ its) {
+  smooth_plane_body(mp, f, uold, unew, diag, omega, eps, maxit, its, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(128) k_smooth_plane_batch(const __grid_constant__ BatchTable bt) {
+  const int r = batch_member(bt, blockIdx.x);
+  smooth_plane_body(bt.mp[r], (const float*)bt.in[r], (const float*)bt.uold[r], (float*)bt.out[r],
+                    (const float*)bt.diag[r], float(bt.omega), float(bt.eps), bt.maxit, bt.its[r],
+                    blockIdx.x - bt.block0[r]);
 }
 #endif

@@ -199,8 +199,9 @@ std::vector<double> q1_stencil(const HostMesh& m) {
   // The DG rule (p+1 Gauss points per direction): with it A_hat equals P^T A P
   // exactly, also where the upwind term max(b.n, 0) has a kink inside a face.
   const int nq = m.p + 1;
-  std::vector<double> g2, w2;
+  std::vector<double> g2, w2, gf2, wf2;
   gauss_legendre01(nq, g2, w2);
+  gauss_legendre01(2, gf2, wf2);
   const double J = m.h[0] * m.h[1] * m.h[2];
   const double pen = m.alpha * m.p * (m.p + 2);
   auto scatter = [&](int cx, int cy, int cz, const double Ae[8][8]) {
@@ -261,7 +262,9 @@ std::vector<double> q1_stencil(const HostMesh& m) {
               for (int ab = 0; ab < 64; ++ab) Ae[ab >> 3][ab & 7] -= bv[d] * T[ab];
             }
           }
-        // Dirichlet faces of boundary cells (gamma from the DG degree p).
+        // Dirichlet faces of boundary cells (gamma from the DG degree p); the
+        // DG rule where the upwind term can have a kink inside the face, two
+        // points per direction (exact for these Q1 products) without advection.
         const int cc3[3] = {cx, cy, cz};
         const int nn3[3] = {m.nx, m.ny, m.nz};
         for (int d = 0; d < 3; ++d)
@@ -271,13 +274,16 @@ std::vector<double> q1_stencil(const HostMesh& m) {
             const double area = m.h[ta] * m.h[tb];
             const double sgn = s ? 1.0 : -1.0;
             const double gam = pen * K[d] / m.h[d];
-            for (int qb = 0; qb < nq; ++qb)
-              for (int qa = 0; qa < nq; ++qa) {
+            const int nf = m.b ? nq : 2;
+            const std::vector<double>& gf = m.b ? g2 : gf2;
+            const std::vector<double>& wf = m.b ? w2 : wf2;
+            for (int qb = 0; qb < nf; ++qb)
+              for (int qa = 0; qa < nf; ++qa) {
                 double xi[3];
                 xi[d] = s;
-                xi[ta] = g2[qa];
-                xi[tb] = g2[qb];
-                const double w = w2[qa] * w2[qb] * area;
+                xi[ta] = gf[qa];
+                xi[tb] = gf[qb];
+                const double w = wf[qa] * wf[qb] * area;
                 double bq[3];
                 b_at(m, cx, cy, cz, xi, bq);
                 const double bn = sgn * bq[d];

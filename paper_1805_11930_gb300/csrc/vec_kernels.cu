@@ -18,10 +18,21 @@ inline unsigned grid1(long long n, int per = kThreads) {
   return (unsigned)(g > 0 ? g : 1);
 }
 
+// a x + b y as fma(a, x, round(b y)) in every kernel that updates a Krylov
+// vector, so batched and single solves agree bit for bit: the product b y is
+// rounded on its own (__dmul_rn / __fmul_rn are never contracted), also where
+// a is the constant 1 and the compiler could otherwise fuse b y with x.
+__device__ __forceinline__ double axpby_op(double a, double x, double b, double y) {
+  return fma(a, x, __dmul_rn(b, y));
+}
+__device__ __forceinline__ float axpby_op(float a, float x, float b, float y) {
+  return fmaf(a, x, __fmul_rn(b, y));
+}
+
 template <typename T>
 __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+    y[i] = axpby_op(a, x[i], b, y[i]);
 }
 
 template <typename T>
@@ -200,6 +211,112 @@ __global__ void k_restrict_gather(int nx, int ny, int nz, const double* __restri
       }
     }
     rhat[v] = s;
+  }
+}
+
+// ------------------------------------------------------------- batched Krylov kernels
+__device__ __forceinline__ int seg_member(const SegTable& t, unsigned bid) {
+  int r = 0;
+  while (r + 1 < t.k && bid >= t.block0[r + 1]) ++r;
+  return r;
+}
+
+template <int OP>
+__global__ void k_seg(const __grid_constant__ SegTable t) {
+  const int r = seg_member(t, blockIdx.x);
+  const long long n = t.n[r];
+  const long long stride = (long long)(t.block0[r + 1] - t.block0[r]) * blockDim.x;
+  const long long i0 = (long long)(blockIdx.x - t.block0[r]) * blockDim.x + threadIdx.x;
+  if (OP == SEG_ALPHA) {
+    const double alpha = t.sc[r][kScAlpha];
+    const bool flex = t.sc[r][kScFlex] != 0.0;
+    const double* p = (const double*)t.a[r];
+    const double* q = (const double*)t.b[r];
+    double* u = (double*)t.c[r];
+    double* rv = (double*)t.d[r];
+    double* ro = (double*)t.e[r];
+    for (long long i = i0; i < n; i += stride) {
+      u[i] = axpby_op(alpha, p[i], 1.0, u[i]);
+      if (flex) ro[i] = rv[i];
+      rv[i] = axpby_op(-alpha, q[i], 1.0, rv[i]);
+    }
+  } else if (OP == SEG_P) {
+    const double beta = t.sc[r][kScBeta];
+    const double* z = (const double*)t.a[r];
+    double* p = (double*)t.c[r];
+    for (long long i = i0; i < n; i += stride) p[i] = axpby_op(1.0, z[i], beta, p[i]);
+  } else {
+    for (long long i = i0; i < n; i += stride) {
+      if (OP == SEG_D2F) ((float*)t.c[r])[i] = (float)((const double*)t.a[r])[i];
+      if (OP == SEG_F2D) ((double*)t.c[r])[i] = (double)((const float*)t.a[r])[i];
+      if (OP == SEG_COPY64) ((double*)t.c[r])[i] = ((const double*)t.a[r])[i];
+      if (OP == SEG_COPY32) ((float*)t.c[r])[i] = ((const float*)t.a[r])[i];
+      if (OP == SEG_SUB64) ((double*)t.c[r])[i] = ((const double*)t.a[r])[i] - ((const double*)t.b[r])[i];
+      if (OP == SEG_SUB32) ((float*)t.c[r])[i] = ((const float*)t.a[r])[i] - ((const float*)t.b[r])[i];
+    }
+  }
+}
+
+// Stage 1 of the members' dots: kDotBlocks blocks per member, block b of
+// member r sums its chunk exactly as k_dot_partial does with kDotBlocks blocks.
+__global__ void k_seg_dot_partial(const __grid_constant__ SegTable t, double* __restrict__ partial) {
+  __shared__ double sh[kThreads];
+  const int r = blockIdx.x / kDotBlocks;
+  const int b = blockIdx.x - r * kDotBlocks;
+  const long long n = t.n[r];
+  const long long chunk = (n + kDotBlocks - 1) / kDotBlocks;
+  const long long lo = b * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  const double* x = (const double*)t.a[r];
+  const double* y = (const double*)t.b[r];
+  double s = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(x[i], y[i], s);
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[(long long)r * kDotBlocks + b] = tot;
+}
+
+__global__ void k_seg_dot_final(const __grid_constant__ SegTable t, const double* __restrict__ partial, int slot) {
+  __shared__ double sh[kThreads];
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) s += partial[(long long)r * kDotBlocks + i];
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) t.sc[r][slot] = tot;
+}
+
+// The scalar steps of the members' CG iterations (one thread per member), the
+// same arithmetic as the host loop of the single solve.
+template <int OP>
+__global__ void k_seg_scalar(const __grid_constant__ SegTable t) {
+  const int r = threadIdx.x;
+  if (r >= t.k) return;
+  double* c = t.sc[r];
+  const bool stopped = c[kScDone] != 0.0;
+  if (OP == SC_ALPHA) {
+    if (stopped) {
+      c[kScAlpha] = 0.0;
+    } else if (!(c[kScPq] > 0.0)) {
+      c[kScAlpha] = 0.0;
+      c[kScDone] = 2.0;
+    } else {
+      c[kScAlpha] = c[kScRz] / c[kScPq];
+    }
+  } else if (OP == SC_CONV) {
+    if (!stopped) {
+      c[kScIts] += 1.0;
+      if (sqrt(c[kScRr]) <= c[kScRtol] * c[kScR0])
+        c[kScDone] = 1.0;
+      else if (c[kScIts] >= c[kScMaxit])
+        c[kScDone] = 3.0;
+    }
+  } else {
+    if (stopped) {
+      c[kScBeta] = 0.0;
+    } else {
+      const double num = c[kScFlex] != 0.0 ? c[kScRzn] - c[kScZro] : c[kScRzn];
+      c[kScBeta] = num / c[kScRz];
+      c[kScRz] = c[kScRzn];
+    }
   }
 }
 
@@ -509,6 +626,56 @@ cudaError_t vec_f2d(long long n, const float* x, double* y, cudaStream_t s) {
   count_launch();
   return cudaGetLastError();
 }
+// Elementwise launches over the members: about a thread per element, at most
+// 64 blocks per SM in all.
+cudaError_t seg_op(int op, SegTable& t, cudaStream_t s) {
+  if (t.k <= 0) return cudaSuccess;
+  const long long cap = 152LL * 64;
+  long long tb = 0;
+  for (int r = 0; r < t.k; ++r) tb += (t.n[r] + kThreads - 1) / kThreads;
+  t.block0[0] = 0;
+  for (int r = 0; r < t.k; ++r) {
+    long long b = (t.n[r] + kThreads - 1) / kThreads;
+    if (tb > cap) b = b * cap / tb;
+    if (b < 1) b = 1;
+    t.block0[r + 1] = t.block0[r] + (unsigned)b;
+  }
+  const unsigned g = t.block0[t.k];
+  switch (op) {
+    case SEG_D2F: k_seg<SEG_D2F><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_F2D: k_seg<SEG_F2D><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_COPY64: k_seg<SEG_COPY64><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_COPY32: k_seg<SEG_COPY32><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_SUB64: k_seg<SEG_SUB64><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_SUB32: k_seg<SEG_SUB32><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_ALPHA: k_seg<SEG_ALPHA><<<g, kThreads, 0, s>>>(t); break;
+    case SEG_P: k_seg<SEG_P><<<g, kThreads, 0, s>>>(t); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t seg_dot(SegTable& t, double* partial, int slot, cudaStream_t s) {
+  if (t.k <= 0) return cudaSuccess;
+  k_seg_dot_partial<<<t.k * kDotBlocks, kThreads, 0, s>>>(t, partial);
+  k_seg_dot_final<<<t.k, kThreads, 0, s>>>(t, partial, slot);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t seg_scalar(int op, SegTable& t, cudaStream_t s) {
+  if (t.k <= 0) return cudaSuccess;
+  switch (op) {
+    case SC_ALPHA: k_seg_scalar<SC_ALPHA><<<1, 32, 0, s>>>(t); break;
+    case SC_CONV: k_seg_scalar<SC_CONV><<<1, 32, 0, s>>>(t); break;
+    case SC_BETA: k_seg_scalar<SC_BETA><<<1, 32, 0, s>>>(t); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t vec_dot(long long n, const double* x, const double* y, double* partial, double* out, cudaStream_t s) {
   k_dot_partial<<<kDotBlocks, kThreads, 0, s>>>(n, 1, nullptr, x, y, partial);
   k_dot_final<<<1, kThreads, 0, s>>>(kDotBlocks, 1, partial, out);

@@ -97,7 +97,17 @@ _SIG = {
     "dgmg_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dgmg_set_layout": (_I, [_P, _I, _I, _I]),
     "dgmg_get_layout": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "dgmg_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(SolveOpts)]),
+    "dgmg_batch_destroy": (_I, [_P]),
+    "dgmg_batch_last_error": (ctypes.c_char_p, [_P]),
+    "dgmg_batch_add": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I)]),
+    "dgmg_batch_step": (_I, [_P, _I, ctypes.POINTER(_I)]),
+    "dgmg_batch_poll": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(SolveStats)]),
+    "dgmg_batch_remove": (_I, [_P, _I]),
+    "dgmg_batch_prime": (_I, [_P, _P, _P, ctypes.POINTER(SolveOpts)]),
 }
+
+BATCH_MAX = 16
 
 NOALLOC_MAX_CELLS = 131072
 
@@ -332,6 +342,12 @@ class Context:
         self._check(self.lib.dgmg_autotune(self.h, prec, reps, ctypes.byref(a), ctypes.byref(s)))
         return a.value, s.value
 
+    def batch_prime(self, f, u, opts=None):
+        """dgmg_batch_prime: the initial Krylov state of a batched solve of
+        (f, u) with `opts`, on this context's stream."""
+        o = opts if opts is not None else default_opts()
+        self._check(self.lib.dgmg_batch_prime(self.h, _ptr(f), _ptr(u), ctypes.byref(o)))
+
     def solve(self, f, u, opts=None, check=True):
         o = opts if opts is not None else default_opts()
         stats = SolveStats()
@@ -339,6 +355,73 @@ class Context:
         if check:
             self._check(st)
         return stats.as_dict() | {"status": STATUS.get(st, st)}
+
+
+class Batch:
+    """A dgmg_batch: the outer solves of several prepared contexts of one order
+    in lockstep, each step one launch over all members (see include/dgmg.h).
+    `opts`: the shared solve options (SolveOpts, default_opts() if None)."""
+
+    def __init__(self, device=0, stream=None, opts=None):
+        import torch
+        self.lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self.stream = stream
+        self.device = device
+        o = opts if opts is not None else default_opts()
+        h = _P()
+        st = self.lib.dgmg_batch_create(ctypes.byref(h), device, stream, ctypes.byref(o))
+        if st != DGMG_OK:
+            raise DgmgError(st, "dgmg_batch_create failed (unsupported options or no device)")
+        self.h = h
+
+    def _check(self, st):
+        if st != DGMG_OK:
+            msg = self.lib.dgmg_batch_last_error(self.h)
+            raise DgmgError(st, msg.decode() if msg else "")
+
+    def add(self, ctx, f, u, rtol=1e-8, maxit=500):
+        """Add a prepared context with its right-hand side f and iterate u
+        (device FP64 tensors); returns the member's slot."""
+        slot = _I(-1)
+        self._check(self.lib.dgmg_batch_add(self.h, ctx.h, _ptr(f), _ptr(u), rtol, maxit, ctypes.byref(slot)))
+        return slot.value
+
+    def step(self, iterations=1):
+        """Run `iterations` outer iterations of every running member; returns
+        how many still run."""
+        left = _I(0)
+        self._check(self.lib.dgmg_batch_step(self.h, iterations, ctypes.byref(left)))
+        return left.value
+
+    def poll(self, slot):
+        """None while the member runs, else its statistics (dict with
+        "status")."""
+        done = _I(0)
+        stats = SolveStats()
+        st = self.lib.dgmg_batch_poll(self.h, slot, ctypes.byref(done), ctypes.byref(stats))
+        if st not in (DGMG_OK, 5, 6):
+            self._check(st)
+        if not done.value:
+            return None
+        return stats.as_dict() | {"status": STATUS.get(st, st)}
+
+    def remove(self, slot):
+        self._check(self.lib.dgmg_batch_remove(self.h, slot))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgmg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def restrict_noalloc(nx, ny, nz, p, r, r_hat, stream=None):

@@ -339,6 +339,237 @@ class SolveServer:
             t.join()
 
 
+class BatchBackend:
+    """Device side of the batched server.
+
+    prepare(req) runs on a set-up worker thread: it takes a library context
+    from that worker's pool (or creates one on the worker's stream), sets the
+    request's mesh and coefficients, assembles its right-hand side, computes
+    the initial Krylov state (dgmg_batch_prime: residual, first V-cycle) and
+    returns the prepared item (context, f, u = 0).  new_batch(p) runs on the lane
+    thread of order p and returns a dgmg.Batch on a stream of its own.
+    finish(item, stats) copies the solution back if asked to, returns the
+    context to its pool and drops the request's vectors."""
+
+    def __init__(self, device=0, keep_solutions=False, rtol=1e-8, maxit=500, **opts):
+        self.device = device
+        self.keep = keep_solutions
+        self.rtol = rtol
+        self.maxit = maxit
+        self.opts = dict(opts)
+        self._local = threading.local()
+
+    def solve_opts(self):
+        from . import dgmg
+        kw = dict(smoother_prec=dgmg.FP32, krylov=dgmg.KRYLOV_FCG)
+        kw.update(self.opts)
+        return dgmg.default_opts(rtol=self.rtol, maxit=self.maxit, **kw)
+
+    def _worker(self):
+        st = getattr(self._local, "state", None)
+        if st is None:
+            import torch
+            torch.cuda.set_device(self.device)
+            st = self._local.state = (torch.cuda.Stream(self.device), [])
+        return st
+
+    def prepare(self, req):
+        import torch
+        from . import dgmg
+        stream, pool = self._worker()
+        ctx = pool.pop() if pool else dgmg.Context(self.device, stream=stream)
+        K, f_qp = request_inputs(req)
+        with torch.cuda.stream(stream):
+            ctx.set_mesh(req.n, req.n, req.n, 1.0, 1.0, 1.0, req.p, [0] * 6)
+            ctx.set_coefficients(K)
+            f = torch.empty(ctx.sizes()["ndof"], dtype=torch.float64, device=f"cuda:{self.device}")
+            ctx.assemble_rhs(f_qp, f)
+            u = torch.zeros_like(f)
+            ctx.batch_prime(f, u, self.solve_opts())   # the initial V-cycle on this worker's stream
+        stream.synchronize()
+        return {"ctx": ctx, "f": f, "u": u, "pool": pool}
+
+    def new_batch(self, p):
+        import torch
+        from . import dgmg
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(self.device)
+        return _DeviceBatch(dgmg.Batch(self.device, stream=stream, opts=self.solve_opts()), self)
+
+    def finish(self, item, stats):
+        sol = item["u"].cpu().numpy() if self.keep else None
+        item["pool"].append(item["ctx"])
+        item["f"] = item["u"] = None
+        return stats, sol
+
+
+class _DeviceBatch:
+    def __init__(self, batch, backend):
+        self.b, self.backend = batch, backend
+
+    def add(self, item):
+        return self.b.add(item["ctx"], item["f"], item["u"], rtol=self.backend.rtol, maxit=self.backend.maxit)
+
+    def step(self, k):
+        return self.b.step(k)
+
+    def poll(self, slot):
+        return self.b.poll(slot)
+
+    def remove(self, slot):
+        self.b.remove(slot)
+
+    def close(self):
+        self.b.close()
+
+
+class BatchedServer:
+    """Continuous batching with one batch per polynomial order.
+
+    Requests are admitted in arrival order while their HBM footprint fits the
+    budget; `setup_workers` host threads prepare admitted requests (mesh,
+    coefficients, right-hand side: host work that overlaps with the device);
+    a prepared request joins the batch of its order at the next step
+    boundary.  One lane thread per order drives its batch: `step` outer
+    iterations of all its members per call (one kernel launch per step of the
+    iteration for all of them, replayed from a CUDA graph), then retires the
+    members that stopped (statistics, solution, latency) and frees their
+    memory, which lets waiting requests in.  Lanes of different orders run on
+    their own streams, so their work overlaps on the device.  A request's
+    arithmetic is its own (see dgmg_batch_add): its result does not depend on
+    what runs beside it.
+
+    backend: an object with prepare(req), new_batch(p) and finish(item,
+    stats) (BatchBackend, or a fake for host tests)."""
+
+    def __init__(self, backend, setup_workers=4, hbm_budget=None, step=4, max_members=16):
+        self.backend = backend
+        self.budget = hbm_budget
+        self.step = step
+        self.max_members = max_members
+        self._lock = threading.Condition()
+        self._setup = queue.Queue()
+        self._ready = {}
+        self._lanes = {}
+        self._used = 0
+        self._open = 0            # admitted, not finished
+        self.max_used = 0
+        self.max_members_seen = 0
+        self._clock0 = None
+        self._stop = False
+        self._workers = [threading.Thread(target=self._setup_loop, daemon=True) for _ in range(setup_workers)]
+        for t in self._workers:
+            t.start()
+
+    def _now(self):
+        return time.perf_counter() - self._clock0
+
+    def _release(self, req):
+        with self._lock:
+            req.t_done = self._now()
+            self._used -= req.footprint
+            self._open -= 1
+            self._lock.notify_all()
+
+    def _setup_loop(self):
+        while True:
+            req = self._setup.get()
+            if req is None:
+                return
+            try:
+                item = self.backend.prepare(req)
+            except Exception as e:       # reported per request, the server keeps going
+                req.error = repr(e)
+                self._release(req)
+                continue
+            self._lane_queue(req.p).put((req, item))
+
+    def _lane_queue(self, p):
+        with self._lock:
+            if p not in self._ready:
+                self._ready[p] = queue.Queue()
+                t = threading.Thread(target=self._lane_loop, args=(p, self._ready[p]), daemon=True)
+                self._lanes[p] = t
+                t.start()
+            return self._ready[p]
+
+    def _lane_loop(self, p, q):
+        batch = self.backend.new_batch(p)
+        members = {}
+        closing = False
+        while True:
+            while len(members) < self.max_members and not closing:
+                try:
+                    got = q.get(timeout=0.02) if not members else q.get_nowait()
+                except queue.Empty:
+                    break
+                if got is None:
+                    closing = True
+                    break
+                req, item = got
+                try:
+                    slot = batch.add(item)
+                except Exception as e:
+                    req.error = repr(e)
+                    self._release(req)
+                    continue
+                req.t_start = self._now()
+                members[slot] = (req, item)
+            self.max_members_seen = max(self.max_members_seen, len(members))
+            if not members:
+                if closing:
+                    batch.close()
+                    return
+                continue
+            batch.step(self.step)
+            for slot, (req, item) in list(members.items()):
+                st = batch.poll(slot)
+                if st is None:
+                    continue
+                batch.remove(slot)
+                del members[slot]
+                req.stats, req.solution = self.backend.finish(item, st)
+                if st.get("status") not in ("DGMG_OK", None):
+                    req.error = st["status"]
+                self._release(req)
+
+    def run(self, trace):
+        """Serve the trace; returns when every request has completed or failed."""
+        self._clock0 = time.perf_counter()
+        pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
+        with self._lock:
+            while pending or self._open > 0:
+                if not pending:
+                    self._lock.wait(timeout=0.05)
+                    continue
+                head = pending[0]
+                now = self._now()
+                if head.arrival > now:
+                    self._lock.wait(timeout=head.arrival - now)
+                    continue
+                fits = self.budget is None or self._used + head.footprint <= self.budget or self._used == 0
+                if not fits:
+                    self._lock.wait(timeout=0.05)
+                    continue
+                pending.popleft()
+                head.t_admit = now
+                self._used += head.footprint
+                self._open += 1
+                self.max_used = max(self.max_used, self._used)
+                self._setup.put(head)
+        return trace
+
+    def close(self):
+        for _ in self._workers:
+            self._setup.put(None)
+        for t in self._workers:
+            t.join()
+        for p, q in list(self._ready.items()):
+            q.put(None)
+        for t in self._lanes.values():
+            t.join()
+
+
 def summarize(reqs):
     done = [r for r in reqs if r.t_done is not None and r.error is None and not r.cancelled]
     lat = sorted(r.latency for r in done)
@@ -367,6 +598,10 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=200.0)
     ap.add_argument("--exclusive-mdofs", type=float, default=0.0,
                     help="requests with at least this many million dofs run alone (0: off)")
+    ap.add_argument("--mode", default="batched", choices=["batched", "slots"],
+                    help="batched: per-order batches (BatchedServer); slots: one context and stream per slot")
+    ap.add_argument("--setup-workers", type=int, default=4)
+    ap.add_argument("--step", type=int, default=4, help="outer iterations per batch step")
     args = ap.parse_args()
     runner = DeviceRunner()
     budget = args.budget_gb * 1e9
@@ -388,16 +623,27 @@ def main():
                       "fp64_single_stream": summarize(fp64_trace)}), flush=True)
     for mult in [float(x) for x in args.rates.split(",")]:
         trace = make_trace(args.requests, mult * capacity, seed=SEED, **rng_kw)
-        excl = args.exclusive_mdofs * 1e6 if args.exclusive_mdofs > 0 else None
-        srv = SolveServer(runner, slots=args.slots, hbm_budget=budget, exclusive_dofs=excl)
-        srv.run(make_trace(args.slots, None, seed=SEED + 9, n_range=(8, 12)))    # warm the workers
-        srv.max_concurrent = srv.max_used = 0
-        srv.run(trace)
-        srv.close()
-        out = summarize(trace)
-        out.update({"rate_multiplier": mult, "rate_req_per_s": round(mult * capacity, 4), "slots": args.slots,
-                    "exclusive_mdofs": args.exclusive_mdofs,
-                    "max_concurrent": srv.max_concurrent, "max_hbm_gb": round(srv.max_used / 1e9, 3)})
+        if args.mode == "batched":
+            srv = BatchedServer(BatchBackend(), setup_workers=args.setup_workers, hbm_budget=budget, step=args.step)
+            srv.run(make_trace(10, None, seed=SEED + 9, n_range=(8, 12)))    # warm the workers and lanes
+            srv.max_used = srv.max_members_seen = 0
+            srv.run(trace)
+            srv.close()
+            out = summarize(trace)
+            out.update({"mode": "batched", "rate_multiplier": mult, "rate_req_per_s": round(mult * capacity, 4),
+                        "setup_workers": args.setup_workers, "step": args.step,
+                        "max_batch_members": srv.max_members_seen, "max_hbm_gb": round(srv.max_used / 1e9, 3)})
+        else:
+            excl = args.exclusive_mdofs * 1e6 if args.exclusive_mdofs > 0 else None
+            srv = SolveServer(runner, slots=args.slots, hbm_budget=budget, exclusive_dofs=excl)
+            srv.run(make_trace(args.slots, None, seed=SEED + 9, n_range=(8, 12)))    # warm the workers
+            srv.max_concurrent = srv.max_used = 0
+            srv.run(trace)
+            srv.close()
+            out = summarize(trace)
+            out.update({"mode": "slots", "rate_multiplier": mult, "rate_req_per_s": round(mult * capacity, 4),
+                        "slots": args.slots, "exclusive_mdofs": args.exclusive_mdofs,
+                        "max_concurrent": srv.max_concurrent, "max_hbm_gb": round(srv.max_used / 1e9, 3)})
         print(json.dumps(out), flush=True)
 
 

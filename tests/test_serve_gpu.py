@@ -58,3 +58,26 @@ def test_evicted_request_resumes_on_the_gpu():
         d = np.linalg.norm(x.solution - y.solution) / np.linalg.norm(y.solution)
         assert d < 1e-5, (x.rid, d)
     assert serve.summarize(a)["evictions"] == 3
+
+
+def test_batched_server_same_alone_and_in_the_mix():
+    """The batched server (one batch per order, several requests per launch):
+    each request's solution is bit for bit the one it gets alone in its batch,
+    and every request reaches the 1e-8 FP64 residual."""
+    from paper_1805_11930_gb300 import serve
+    kw = dict(n_range=(4, 9), p_range=(2, 4), seed=78)
+    mix = serve.make_trace(12, None, **kw)
+    srv = serve.BatchedServer(serve.BatchBackend(keep_solutions=True), setup_workers=3, step=3)
+    srv.run(mix)
+    srv.close()
+    assert srv.max_members_seen >= 2
+    alone = serve.make_trace(12, None, **kw)
+    one = serve.BatchedServer(serve.BatchBackend(keep_solutions=True), setup_workers=1, step=3, max_members=1)
+    for r in alone:
+        one.run([r])
+    one.close()
+    for a, b in zip(mix, alone):
+        assert a.error is None and b.error is None, (a.error, b.error)
+        assert a.stats["converged"] == 1 and a.stats["rel_residual"] <= 1e-8
+        assert a.stats["iterations"] == b.stats["iterations"]
+        assert np.array_equal(a.solution, b.solution), f"request {a.rid} differs"

@@ -290,3 +290,91 @@ def test_chunked_solve_keeps_the_stopping_test_relative_to_f():
     u2, st2 = serve.DeviceRunner(chunk=4, rtol=1e-8)._chunked(FakeCtx(0.5), f, req2, {})
     assert st2["iterations"] == 27 and st2["converged"] == 1
     assert float(torch.linalg.vector_norm(u2 - u)) < 1e-12 * float(torch.linalg.vector_norm(u))
+
+
+# ------------------------------------------------------------- batched server
+class FakeBatch:
+    """A batch whose members stop after as many steps as their order; records
+    the largest membership and the orders it saw."""
+
+    def __init__(self, p, log):
+        self.p, self.log = p, log
+        self.members = {}
+        self.next = 0
+
+    def add(self, item):
+        if item.get("fail_add"):
+            raise RuntimeError("DGMG_ERR_OOM")
+        slot = self.next
+        self.next += 1
+        self.members[slot] = [item, 0]
+        self.log["orders"].add(self.p)
+        self.log["peak"] = max(self.log["peak"], len(self.members))
+        return slot
+
+    def step(self, k):
+        time.sleep(0.002)
+        for m in self.members.values():
+            m[1] += k
+        return sum(1 for m in self.members.values() if m[1] < m[0]["steps"])
+
+    def poll(self, slot):
+        item, done = self.members[slot]
+        if done < item["steps"]:
+            return None
+        return {"converged": 1, "rel_residual": 1e-9, "iterations": done, "status": "DGMG_OK"}
+
+    def remove(self, slot):
+        del self.members[slot]
+
+    def close(self):
+        self.log["closed"] += 1
+
+
+class FakeBackend:
+    def __init__(self, fail=()):
+        self.fail = set(fail)
+        self.log = {"orders": set(), "peak": 0, "closed": 0, "prepared": []}
+        self.lock = threading.Lock()
+
+    def prepare(self, req):
+        if req.rid in self.fail:
+            raise RuntimeError("set-up failed")
+        with self.lock:
+            self.log["prepared"].append(req.rid)
+        time.sleep(0.001)
+        return {"steps": 4 * req.p}
+
+    def new_batch(self, p):
+        return FakeBatch(p, self.log)
+
+    def finish(self, item, stats):
+        return stats, None
+
+
+def test_batched_server_completes_every_request_per_order():
+    trace = serve.make_trace(40, None, n_range=(8, 10), p_range=(2, 6), seed=3)
+    be = FakeBackend()
+    srv = serve.BatchedServer(be, setup_workers=3, step=4, max_members=5)
+    srv.run(trace)
+    srv.close()
+    s = serve.summarize(trace)
+    assert s["completed"] == 40 and s["converged"] == 40 and s["errors"] == 0
+    assert be.log["orders"] == {r.p for r in trace}
+    assert be.log["peak"] <= 5 and srv.max_members_seen <= 5
+    assert be.log["closed"] == len(be.log["orders"])
+    for r in trace:
+        assert r.stats["iterations"] >= 4 * r.p and r.t_done >= r.t_start >= r.t_admit >= r.arrival
+
+
+def test_batched_server_budget_and_failures():
+    trace = serve.make_trace(10, None, n_range=(8, 8), p_range=(3, 3), seed=4)
+    fp = trace[0].footprint
+    be = FakeBackend(fail={2, 5})
+    srv = serve.BatchedServer(be, setup_workers=2, hbm_budget=2 * fp, step=2)
+    srv.run(trace)
+    srv.close()
+    assert srv.max_used <= 2 * fp and be.log["peak"] <= 2
+    s = serve.summarize(trace)
+    assert s["errors"] == 2 and s["completed"] == 8
+    assert all(trace[i].error for i in (2, 5))
