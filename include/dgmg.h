@@ -66,7 +66,7 @@ typedef enum { DGMG_KRYLOV_CG = 0, DGMG_KRYLOV_FCG = 1, DGMG_KRYLOV_FGMRES = 2 }
  * convection-dominated blocks (Sec. 3.2, 4.3; its factors, 3 n^3 values per
  * cell and precision, are built on first use); or DIRECT: multiplication by
  * the explicit inverse of D_T stored on the device (the partially matrix-free
- * variant, Sec. 4.1; see dgmg_block_inverse), p <= 4. */
+ * variant, Sec. 4.1; see dgmg_block_inverse). */
 typedef enum {
   DGMG_INNER_PCG = 0,
   DGMG_INNER_GMRES = 1,
@@ -349,7 +349,10 @@ dgmg_status dgmg_set_variable_coefficients(dgmg_ctx* ctx, const double* basis, c
  * Built on the device: column j of D_T is the block operator applied to the
  * unit vector e_j (n^3 block applications per cell), then each block is
  * inverted by Gauss-Jordan elimination with partial pivoting in FP64, one
- * thread block per cell with the block in shared memory.  For FP64 smoothers
+ * thread block per cell: for p <= 4 with the block in shared memory, for
+ * p >= 5 with the block in global memory and the pivot steps taken in panels
+ * of 16 columns (the same operations on every element, so the same inverse).
+ * For FP64 smoothers
  * the inverse is kept as double-float pairs (hi, lo: about 48 significant
  * bits) and the block solve runs in double-float arithmetic (GB300's FP64
  * pipe would bound a FP64 product); for FP32 smoothers it is rounded to FP32.
@@ -357,13 +360,14 @@ dgmg_status dgmg_set_variable_coefficients(dgmg_ctx* ctx, const double* basis, c
  * precision (built on first use when this call was not made).  Storage per
  * precision: ncell n^3 ld values of 8 (FP64) or 4 (FP32) bytes, ld = n^3
  * rounded up to a multiple of 8 (p = 2: 6.9 KB per cell for FP64, p = 4:
- * 128 KB).  dgmg_set_coefficients and dgmg_set_mesh drop it.
+ * 128 KB, p = 6: 0.94 MB, p = 8: 4.3 MB), plus a FP64 temporary of the same
+ * size during the set-up.  dgmg_set_coefficients and dgmg_set_mesh drop it.
  *   prec: FP64 or FP32 (DF64: DGMG_ERR_ARG);
  *   out: device buffer of ncell n^6 values of prec receiving a copy, or NULL;
  *        block T at out + T n^6, column-major: (D_T^-1)_{ij} at i + j n^3
  *        (FP64: hi + lo of the stored pairs).
- * p > 4: DGMG_ERR_ARG (the block no longer fits in shared memory); a singular
- * block: DGMG_ERR_ARG with nothing stored; allocation failure: DGMG_ERR_OOM.
+ * A singular block: DGMG_ERR_ARG with nothing stored; allocation failure:
+ * DGMG_ERR_OOM.
  * Synchronises the stream. */
 dgmg_status dgmg_block_inverse(dgmg_ctx* ctx, dgmg_prec prec, void* out);
 

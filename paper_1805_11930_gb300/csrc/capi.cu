@@ -399,7 +399,7 @@ dgmg_status ensure_binv(dgmg_ctx* ctx, int prec) {
   Range range("dgmg block inverse set-up");
   if (prec != DGMG_FP64 && prec != DGMG_FP32)
     return fail(ctx, DGMG_ERR_ARG, "stored block inverses are FP64 or FP32");
-  if (ctx->p > 4) return fail(ctx, DGMG_ERR_ARG, "stored block inverses are built for p <= 4");
+
   if (prec == DGMG_FP64 ? ctx->binv_df != nullptr : ctx->binv32 != nullptr) return DGMG_OK;
   if (ctx->stream) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -320,6 +320,161 @@ __global__ void k_seg_scalar(const __grid_constant__ SegTable t) {
   }
 }
 
+// The same Gauss-Jordan elimination for blocks too large for shared memory
+// (nb > kInvMaxN, p >= 5): the block stays in global memory (column-major,
+// column stride ld) and the pivot steps are taken in panels of kPanel
+// columns.  A panel's columns are eliminated in shared memory step by step
+// (pivot search, row swap, scaling, elimination of every other row); the
+// steps' pivot rows, reciprocal pivots and pivot columns are kept, and then
+// every column outside the panel receives the same swaps and eliminations in
+// the same order, one warp per column held in registers.  Each element sees
+// the same sequence of operations as in k_block_invert, so the inverse is the
+// same, while the block is read and written once per panel instead of once
+// per pivot step.  One thread block per cell; nb <= kInvMaxBig.
+constexpr int kPanel = 16;
+constexpr int kInvMaxBig = 736;                 // n^3 up to p = 8 (729), rounded to 32
+constexpr int kColRegs = kInvMaxBig / 32;
+
+__global__ void __launch_bounds__(256) k_block_invert_big(double* __restrict__ a, int nb, int ld, long long ncell,
+                                                           int* __restrict__ singular) {
+  extern __shared__ __align__(16) double sm_big[];
+  double* P = sm_big;                    // panel: nb x kPanel, column-major
+  double* L = P + (size_t)nb * kPanel;   // pivot columns before elimination: kPanel x nb
+  __shared__ double pinv_s[kPanel];
+  __shared__ int prow_s[kPanel];
+  __shared__ int perm[kInvMaxBig];
+  __shared__ double wv[8];
+  __shared__ int wi[8];
+  __shared__ int bad;
+  const long long c = blockIdx.x;
+  if (c >= ncell) return;
+  double* g = a + c * (long long)nb * ld;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  if (tid == 0) bad = 0;
+  for (int k0 = 0; k0 < nb; k0 += kPanel) {
+    const int kb = nb - k0 < kPanel ? nb - k0 : kPanel;
+    for (int t = tid; t < nb * kb; t += nt) P[t] = g[(t % nb) + (long long)(k0 + t / nb) * ld];
+    __syncthreads();
+    for (int kk = 0; kk < kb; ++kk) {
+      const int k = k0 + kk;
+      double best = -1.0;
+      int bi = nb;
+      for (int i = k + tid; i < nb; i += nt) {
+        const double v = fabs(P[i + kk * nb]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        wv[warp] = best;
+        wi[warp] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double b = wv[0];
+        int r = wi[0];
+        for (int w = 1; w < nw; ++w)
+          if (wv[w] > b || (wv[w] == b && wi[w] < r)) {
+            b = wv[w];
+            r = wi[w];
+          }
+        if (r >= nb) r = k;
+        prow_s[kk] = r;
+        perm[k] = r;
+      }
+      __syncthreads();
+      const int p = prow_s[kk];
+      if (p != k)
+        for (int j = tid; j < kb; j += nt) {
+          const double t = P[k + j * nb];
+          P[k + j * nb] = P[p + j * nb];
+          P[p + j * nb] = t;
+        }
+      __syncthreads();
+      const double piv = P[k + kk * nb];
+      if (piv == 0.0 || !isfinite(piv)) {
+        if (tid == 0) *singular = 1;
+        return;
+      }
+      const double pv = 1.0 / piv;
+      if (tid == 0) pinv_s[kk] = pv;
+      for (int i = tid; i < nb; i += nt) L[kk * nb + i] = P[i + kk * nb];
+      __syncthreads();
+      for (int j = tid; j < kb; j += nt) P[k + j * nb] = (j == kk ? 1.0 : P[k + j * nb]) * pv;
+      __syncthreads();
+      for (int t = tid; t < nb * kb; t += nt) {
+        const int i = t % nb, j = t / nb;
+        if (i == k) continue;
+        P[t] = fma(-L[kk * nb + i], P[k + j * nb], j == kk ? 0.0 : P[t]);
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < nb * kb; t += nt) g[(t % nb) + (long long)(k0 + t / nb) * ld] = P[t];
+    // the panel's steps on every other column, one warp per column
+    for (int j = warp; j < nb; j += nw) {
+      if (j >= k0 && j < k0 + kb) continue;
+      double* col = g + (long long)j * ld;
+      double x[kColRegs];
+#pragma unroll
+      for (int r = 0; r < kColRegs; ++r) {
+        const int i = lane + 32 * r;
+        x[r] = i < nb ? col[i] : 0.0;
+      }
+      for (int kk = 0; kk < kb; ++kk) {
+        const int k = k0 + kk, p = prow_s[kk];
+        // values at rows k and p (each held by one lane), swapped
+        double xk = 0.0, xp = 0.0;
+#pragma unroll
+        for (int r = 0; r < kColRegs; ++r) {
+          if (lane + 32 * r == k) xk = x[r];
+          if (lane + 32 * r == p) xp = x[r];
+        }
+        xk = __shfl_sync(0xffffffffu, xk, k & 31);
+        xp = __shfl_sync(0xffffffffu, xp, p & 31);
+        if (p != k) {
+#pragma unroll
+          for (int r = 0; r < kColRegs; ++r) {
+            if (lane + 32 * r == k) x[r] = xp;
+            if (lane + 32 * r == p) x[r] = xk;
+          }
+        }
+        const double rk = xp * pinv_s[kk];   // row k after the swap, scaled
+#pragma unroll
+        for (int r = 0; r < kColRegs; ++r) {
+          const int i = lane + 32 * r;
+          if (i < nb) x[r] = i == k ? rk : fma(-L[kk * nb + i], rk, x[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kColRegs; ++r) {
+        const int i = lane + 32 * r;
+        if (i < nb) col[i] = x[r];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = tid; i < nb; i += nt) {
+        const double t = g[i + (long long)k * ld];
+        g[i + (long long)k * ld] = g[i + (long long)p * ld];
+        g[i + (long long)p * ld] = t;
+      }
+    __syncthreads();
+  }
+}
+
 // Per-cell coefficient records (setup): kd[3], cJ, kap[6], gam[6].
 __global__ void k_cell_records(MeshParams mp, double* __restrict__ r64, float* __restrict__ r32) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -570,6 +725,17 @@ cudaError_t blocks_df_to_dense(long long ncell, int nb, int ld, const float2* pa
 
 cudaError_t block_invert(double* a, int nb, int ld, long long ncell, int* singular, cudaStream_t s) {
   if (ncell == 0) return cudaSuccess;
+  if (nb > kInvMaxN && nb <= kInvMaxBig) {
+    if (ncell > 0x7fffffffLL || ld < nb) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * nb * kPanel * sizeof(double);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_block_invert_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_block_invert_big<<<(unsigned)ncell, 256, smem, s>>>(a, nb, ld, ncell, singular);
+    count_launch();
+    return cudaGetLastError();
+  }
   if (nb < 1 || nb > kInvMaxN) return cudaErrorInvalidValue;
   const size_t smem = ((size_t)nb * nb + 2 * nb) * sizeof(double);
   if (smem > 48 * 1024) {

@@ -667,13 +667,14 @@ def test_autotune_choices_and_bitwise_solve():
 
 
 # ------------------------------------------------------------- stored inverses
-@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full"])
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full", "p5_dir", "p6_adv", "p8_dir"])
 def test_block_inverse_matches_oracle_blocks(name):
     """dgmg_block_inverse: every stored block times the oracle's assembled
     diagonal block D_T is the identity up to the rounding of the stored
     double-float pairs (64 units of 2^-48 times max |D_T^-1| |D_T|, about
     1e-13 here), and the FP32 copy is the same inverse rounded (1e-6
-    relative per block)."""
+    relative per block); p >= 5 takes the panel-blocked elimination in
+    global memory."""
     from paper_1805_11930_gb300 import dgmg
     w, P, A = oracle_matrix(name)
     ctx = gpu_context(w)
@@ -693,7 +694,7 @@ def test_block_inverse_matches_oracle_blocks(name):
         assert rel_err(inv32[c], inv[c]) < 1e-6
 
 
-@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full"])
+@pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p3_adv", "p4_full", "p5_dir", "p6_adv", "p8_dir"])
 def test_block_smooth_direct_matches_exact_block_jacobi(name):
     """inner = DIRECT (stored inverses): two block-Jacobi sweeps equal the
     oracle's dense-LU block-Jacobi to 1e-12 in FP64 and double-float (b = 0)
@@ -712,7 +713,7 @@ def test_block_smooth_direct_matches_exact_block_jacobi(name):
     u32 = dev(u0).float()
     ctx.block_smooth(dev(f).float(), u32, nsweep=2, omega=0.8, inner=dgmg.INNER_DIRECT)
     assert rel_err(u32.double().cpu().numpy(), ref) < 1e-5
-    if w["b"] is None:      # double-float defect and product (diffusion only)
+    if w["b"] is None and w["p"] <= 6:   # double-float defect and product (diffusion, p <= 6)
         udf = dev(u0)
         ctx.block_smooth(dev(f), udf, nsweep=2, omega=0.8, inner=dgmg.INNER_DIRECT, df64=True)
         assert rel_err(udf.cpu().numpy(), ref) < 1e-12
@@ -736,8 +737,9 @@ def test_block_ssor_direct_matches_oracle(name):
 def test_solve_direct_blocks_c1_and_rejections():
     """CG with a V-cycle whose smoother uses the stored inverses reaches 1e-8
     on the Poisson workload in no more iterations than inner PCG, also in
-    FP32 and double-float; DF64 rejects inner GMRES and p > 4 rejects the
-    stored inverses."""
+    FP32 and double-float; DF64 rejects inner GMRES; at p = 6 (blocks built
+    by the panel-blocked elimination) the stored-inverse solve reaches 1e-8
+    with no more iterations than inner PCG."""
     from paper_1805_11930_gb300 import dgmg
     w = inputs.poisson_sine(8, 2)
     ctx = gpu_context(w)
@@ -759,10 +761,13 @@ def test_solve_direct_blocks_c1_and_rejections():
     assert sdf["converged"] and sdf["rel_residual"] <= 1e-8
     with pytest.raises(dgmg.DgmgError):
         ctx.solve(f, torch.zeros_like(f), dgmg.default_opts(inner=dgmg.INNER_GMRES, smoother_prec=dgmg.DF64))
-    w5 = inputs.lognormal(2, 5)
-    ctx5 = gpu_context(w5)
-    with pytest.raises(dgmg.DgmgError):
-        ctx5.block_inverse(dgmg.FP64)
+    w6 = inputs.lognormal(4, 6)
+    ctx6 = gpu_context(w6)
+    f6 = gpu_rhs(ctx6, w6, torch)
+    s6p = ctx6.solve(f6, torch.zeros_like(f6), dgmg.default_opts())
+    u6 = torch.zeros_like(f6)
+    s6d = ctx6.solve(f6, u6, dgmg.default_opts(inner=dgmg.INNER_DIRECT))
+    assert s6d["converged"] and s6d["rel_residual"] <= 1e-8 and s6d["iterations"] <= s6p["iterations"]
 
 
 # ------------------------------------------------------------- tridiagonal inner preconditioner
