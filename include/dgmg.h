@@ -386,31 +386,34 @@ dgmg_status dgmg_block_inverse(dgmg_ctx* ctx, dgmg_prec prec, void* out);
  * The setting belongs to the current mesh: dgmg_set_mesh resets it. */
 dgmg_status dgmg_set_launch_shape(dgmg_ctx* ctx, dgmg_prec prec, int wpb_apply, int wpb_smooth);
 
-/* Work layouts of the b = 0 operator and inner-PCG smoother kernels: how a
- * warp's lanes share the work of its cells.  All compute the same operator
- * (the forms are exact rewritings of the block of eq. block_diag_apply and
- * the operator of Sec. 2.1, Sec. 3.1's sum factorisation), so results agree to
+/* Work layouts of the operator and inner-PCG smoother kernels: how a warp's
+ * lanes share the work of its cells.  All compute the same operator (exact
+ * rewritings of the operator of Sec. 2.1 and the block of eq.
+ * block_diag_apply, with Sec. 3.1's sum factorisation), so results agree to
  * rounding; within one layout the warps per block change no result bit.
- *   LINE      each lane a line of n values of its cell, eight Kronecker
- *             contractions per block apply (volume tensor form, Sec. 3.1) and
- *             line-form face passes; values in shared memory.
- *   FACTORED  each lane single elements, the block as (M (x) M (x) M) o
- *             sum_d (M^-1 A_d) x_d (one fused pass, three mass passes) with
- *             the neighbour face values added before the mass passes; values
- *             in shared memory.
- *   PLANE     FP32 and p <= 4 only: each lane one z-plane of a cell in
- *             registers, the factored form with the x and y contractions in
- *             registers and the z contractions through shared memory; used for
- *             the operator and the Jacobi sweep (a block-SOR colour takes LINE).
- * AUTO selects the default of the precision, order and kernel: FACTORED for
- * FP64 and DF64; in FP32 LINE for the operator and PLANE for the smoother with
- * p <= 4 (else LINE), the faster pair measured on GB300 at p = 3 and 4.  With advection (b != 0) the
- * kernels evaluate the volume term at the Gauss points in the line form
- * whatever the layout. */
+ *   LINE     each lane a line of n values of its cell; values in shared
+ *            memory.  b = 0: eight Kronecker contractions per block apply
+ *            (volume tensor form) and line-form face passes; b != 0: the
+ *            three stages at the Gauss points along lines, each face's upwind
+ *            flux in its own line passes.
+ *   ELEMENT  each lane single output elements; values in shared memory.
+ *            b = 0: the block as (M (x) M (x) M) o sum_d (M^-1 A_d) x_d (one
+ *            fused pass, three mass passes), the neighbour face values added
+ *            before the mass passes; b != 0: the three stages at the Gauss
+ *            points in element passes, all six faces (diffusion terms and
+ *            upwind flux) together in element passes.
+ *   PLANE    FP32, b = 0 and p <= 4 only: each lane one z-plane of a cell in
+ *            registers, the factored form with the x and y contractions in
+ *            registers and the z contractions through shared memory; used for
+ *            the operator and the Jacobi sweep (a block-SOR colour takes LINE).
+ * AUTO selects the default of the precision, order and kernel: b = 0: ELEMENT
+ * for FP64 and DF64; in FP32 LINE for the operator and PLANE for the smoother
+ * with p <= 4 (else LINE); b != 0: ELEMENT for FP64 at p = 5, else LINE (the
+ * faster forms measured on GB300). */
 typedef enum {
   DGMG_LAYOUT_AUTO = 0,
   DGMG_LAYOUT_LINE = 1,
-  DGMG_LAYOUT_FACTORED = 2,
+  DGMG_LAYOUT_ELEMENT = 2,
   DGMG_LAYOUT_PLANE = 3
 } dgmg_layout;
 
@@ -418,7 +421,7 @@ typedef enum {
  * dgmg_block_apply and the operators inside solves) and of the inner-PCG
  * smoother (layout_smooth; also the defect of the stored-inverse sweep) for
  * arithmetic `prec`.  DGMG_ERR_ARG for values outside dgmg_layout or PLANE
- * where it does not exist (FP64, DF64, p > 4); DGMG_ERR_STATE before
+ * where it does not exist (FP64, DF64, p > 4, b != 0); DGMG_ERR_STATE before
  * dgmg_set_mesh.  The setting belongs to the current mesh: dgmg_set_mesh
  * resets it to AUTO. */
 dgmg_status dgmg_set_layout(dgmg_ctx* ctx, dgmg_prec prec, int layout_apply, int layout_smooth);
@@ -429,9 +432,10 @@ dgmg_status dgmg_set_layout(dgmg_ctx* ctx, dgmg_prec prec, int layout_apply, int
 dgmg_status dgmg_get_layout(const dgmg_ctx* ctx, dgmg_prec prec, int* layout_apply, int* layout_smooth);
 
 /* Times every layout that exists for arithmetic `prec` and order p (LINE and
- * FACTORED, plus PLANE for FP32 with p <= 4) with every warps-per-block
- * candidate (1, 2, 4, 8), for the operator kernel and for one inner-PCG
- * block-Jacobi sweep (eps 1e-2, from u = 0 with f = 1), on the current mesh
+ * ELEMENT, plus PLANE for FP32 with p <= 4 and b = 0) with every warps-per-block
+ * candidate (1, 2, 4, 8), for the operator kernel and for one block-Jacobi
+ * sweep with the default inner solver (PCG; GMRES(12) with advection; eps
+ * 1e-2, from u = 0 with f = 1), on the current mesh
  * and coefficients, `reps` timed launches each after one warm-up (reps <= 0
  * means 3), with CUDA events on the context's stream, and keeps the fastest
  * pair of each through dgmg_set_layout and dgmg_set_launch_shape.

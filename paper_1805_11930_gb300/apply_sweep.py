@@ -1,13 +1,15 @@
 """Operator-apply throughput over the polynomial degree.
 
 python -m paper_1805_11930_gb300.apply_sweep [--degrees 2,3,4,5,6] [--advection]
+    [--layout auto|line|element|plane]
 
 Meshes sized to 30-300 MB per FP64 vector: 64^3 cells for p <= 3, 40^3 for
 p = 4..6 (log-normal K, Dirichlet).  For each p and precision: median
 CUDA-event time of dgmg_apply over 20 launches (an L2-sized buffer is
 written between launches), GDOF/s, the rate of the flops the kernel issues
-(flops.kernel_apply_full: the factored form in FP64, the Kronecker volume
-term and line-form faces in FP32) as a fraction of the FP64 pipe peak
+(flops.kernel_apply_full for the work layout the operator ran in: the
+element layout's factored or Gauss-point form, or the line form; the
+automatic choice unless --layout names one) as a fraction of the FP64 pipe peak
 (4 flop/clk/SM x 152 SMs x 2070 MHz; for df64, FP64 vectors in double-float
 arithmetic, as well) or of the measured FP32 FMA rate (75.6 TFLOP/s), the
 same for the algorithmic count (32 n^4 + 120 n^3 flop per cell), and the HBM
@@ -33,6 +35,7 @@ def main():
     ap.add_argument("--degrees", default="2,3,4,5,6")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--advection", action="store_true")
+    ap.add_argument("--layout", default="auto", choices=["auto", "line", "element", "plane"])
     args = ap.parse_args()
     import torch
 
@@ -45,10 +48,18 @@ def main():
         ctx.set_mesh(*w["nc"], *w["L"], w["p"], w["bc"])
         ctx.set_coefficients(w["K"], b_vertex=w["b"], c_cell=w["c"])
         s = ctx.sizes()
-        variants = [(torch.float64, "fp64", FP64_PEAK), (torch.float32, "fp32", FP32_PEAK)]
-        if not args.advection:
-            variants.append((torch.float64, "df64", FP64_PEAK))
-        for dt, name, peak in variants:
+        variants = [(torch.float64, "fp64", FP64_PEAK, dgmg.FP64), (torch.float32, "fp32", FP32_PEAK, dgmg.FP32),
+                    (torch.float64, "df64", FP64_PEAK, dgmg.DF64)]
+        for dt, name, peak, prec in variants:
+            if args.advection and prec == dgmg.DF64:
+                continue
+            if args.layout != "auto":
+                lay = getattr(dgmg, "LAYOUT_" + args.layout.upper())
+                try:
+                    ctx.set_layout(prec, lay, lay)
+                except dgmg.DgmgError:
+                    continue
+            layout = dgmg.LAYOUT_NAMES[ctx.get_layout(prec)[0]]
             x = torch.rand(s["ndof"], dtype=dt, device="cuda")
             y = torch.empty_like(x)
             df = name == "df64"
@@ -67,9 +78,10 @@ def main():
             t = statistics.median(ms) / 1e3
             fl = flops.algorithmic_apply(p + 1, value_terms=args.advection) * s["ncell"] / t
             kfl = flops.kernel_apply_full(p + 1, advection=args.advection,
-                                          factored=name != "fp32") * s["ncell"] / t
+                                          element=layout == "element") * s["ncell"] / t
             by = flops.hbm_bytes_apply(p + 1, s["ncell"], 4 if name == "fp32" else 8) / t
             print(json.dumps({"p": p, "mesh": n, "ndof": s["ndof"], "prec": name, "advection": args.advection,
+                              "layout": layout,
                               "ms": round(t * 1e3, 4),
                               "gdofs": round(s["ndof"] / t / 1e9, 3), "tflops": round(kfl / 1e12, 3),
                               "alu_frac": round(kfl / peak, 3), "alu_frac_generic_count": round(fl / peak, 3),

@@ -290,13 +290,14 @@ void dfree(dgmg_ctx* ctx, void* q) {
 // on GB300).
 int resolve_layout(const dgmg_ctx* ctx, int prec, int lay, bool smoother) {
   if (lay != DGMG_LAYOUT_AUTO) return lay;
+  if (ctx->db) return prec == DGMG_FP64 && ctx->p == 5 ? DGMG_LAYOUT_ELEMENT : DGMG_LAYOUT_LINE;
   if (prec == DGMG_FP32) return smoother && ctx->p <= 4 ? DGMG_LAYOUT_PLANE : DGMG_LAYOUT_LINE;
-  return DGMG_LAYOUT_FACTORED;
+  return DGMG_LAYOUT_ELEMENT;
 }
 
 bool layout_exists(const dgmg_ctx* ctx, int prec, int lay) {
-  if (lay == DGMG_LAYOUT_AUTO || lay == DGMG_LAYOUT_LINE || lay == DGMG_LAYOUT_FACTORED) return true;
-  return lay == DGMG_LAYOUT_PLANE && prec == DGMG_FP32 && ctx->p <= 4;
+  if (lay == DGMG_LAYOUT_AUTO || lay == DGMG_LAYOUT_LINE || lay == DGMG_LAYOUT_ELEMENT) return true;
+  return lay == DGMG_LAYOUT_PLANE && prec == DGMG_FP32 && ctx->p <= 4 && !ctx->db;
 }
 
 MeshParams params(const dgmg_ctx* ctx) {
@@ -1648,9 +1649,9 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   dgmg_status st = DGMG_OK;
   const int cand[4] = {1, 2, 4, 8};
-  std::vector<int> lays = {DGMG_LAYOUT_LINE, DGMG_LAYOUT_FACTORED};
+  std::vector<int> lays = {DGMG_LAYOUT_LINE, DGMG_LAYOUT_ELEMENT};
   if (layout_exists(ctx, prec, DGMG_LAYOUT_PLANE)) lays.push_back(DGMG_LAYOUT_PLANE);
-  if (ctx->db) lays = {DGMG_LAYOUT_LINE};   // advection: one form
+
   int best[2] = {0, 0}, best_lay[2] = {0, 0};
   const int saved_a = ctx->wpb_apply[prec], saved_s = ctx->wpb_smooth[prec];
   const int saved_la = ctx->lay_apply[prec], saved_ls = ctx->lay_smooth[prec];
@@ -1682,7 +1683,9 @@ dgmg_status dgmg_autotune(dgmg_ctx* ctx, dgmg_prec prec, int reps, int* wpb_appl
             if (kind == 0) {
               CK(ctx->ops->apply(mp, f, u, prec, true, ctx->stream));
             } else {
-              CS(smooth_internal(ctx, f, u, t, 1, 1.0, 1e-2, 0, DGMG_INNER_PCG, 0, prec, true, nullptr));
+              // the inner solver a solve takes by default: PCG, GMRES(12) with advection
+              CS(smooth_internal(ctx, f, u, t, 1, 1.0, 1e-2, 0, ctx->db ? DGMG_INNER_GMRES : DGMG_INNER_PCG,
+                                 12, prec, true, nullptr));
             }
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));

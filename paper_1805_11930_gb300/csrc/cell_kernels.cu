@@ -911,6 +911,286 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
   __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Element form of the operator with advection (b != 0): the lane work items
+// are single outputs, as in the factored form, so that all 32 lanes stay busy
+// at every order (the line form leaves 7 of 32 lanes idle at n = 5 and takes
+// five synchronised phases per face).
+//
+// Tables in shared memory (their row index varies across the lanes):
+// AT = [B | B^T | Dg | Dg^T | M], n^2 each, row-major.
+constexpr int kAdvTab = 5 * N2;
+
+template <typename T>
+__device__ __forceinline__ void adv_tables(T* AT, int lane) {
+  const Tab<T>& t = tab<T>();
+  for (int k = lane; k < N2; k += 32) {
+    const int i = k / N, j = k % N;
+    AT[k] = t.B[i][j];
+    AT[N2 + k] = t.B[j][i];
+    AT[2 * N2 + k] = t.Dg[i][j];
+    AT[3 * N2 + k] = t.Dg[j][i];
+    AT[4 * N2 + k] = t.M1[i][j];
+  }
+}
+
+// b_D at the Gauss point (gq[i0], gq[i1], gq[i2]) of cell slot cw: the
+// trilinear interpolation of the corner values, as nested linear blends.
+template <typename T>
+__device__ __forceinline__ T b_gauss(const CellInfo<T>& c, int D, int i0, int i1, int i2) {
+  const Tab<T>& t = tab<T>();
+  const T x = t.gq[i0], y = t.gq[i1], z = t.gq[i2];
+  const T* b = c.bc[D];
+  const T b00 = fma(x, b[1] - b[0], b[0]), b10 = fma(x, b[3] - b[2], b[2]);
+  const T b01 = fma(x, b[5] - b[4], b[4]), b11 = fma(x, b[7] - b[6], b[6]);
+  const T c0 = fma(y, b10 - b00, b00), c1 = fma(y, b11 - b01, b01);
+  return fma(z, c1 - c0, c0);
+}
+
+// Y = A^v X with advection at the Gauss points (Sec. 3.1's three stages):
+// U = (B (x) B (x) B) X; per direction D the pointwise flux
+// Q = w (|J| K_D / h_D^2 Dg_D U - |J| / h_D b_D U) and E (+)= Dg_D^T Q, with the
+// reaction c |J| w U added once; Y = (B^T (x) B^T (x) B^T) E.  Element passes;
+// S0, S1, E scratch vectors; AT the shared tables.
+template <typename T>
+__device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* E, const T* AT, int lane,
+                                             const CellInfo<T>* ci, const unsigned char* act) {
+  const Tab<T>& t = tab<T>();
+  const T* Bs = AT;
+  const T* Bts = AT + N2;
+  const T* Ds = AT + 2 * N2;
+  const T* Dts = AT + 3 * N2;
+  contract_e<0, false>(X, S1, Bs, 0, lane, act);
+  __syncwarp();
+  contract_e<1, false>(S1, S0, Bs, 0, lane, act);
+  __syncwarp();
+  contract_e<2, false>(S0, S1, Bs, 0, lane, act);   // S1 = u at the Gauss points
+  __syncwarp();
+#pragma unroll
+  for (int D = 0; D < 3; ++D) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int st = D == 0 ? 1 : (D == 1 ? N : N2);
+    for (int e = lane; e < VEC; e += 32) {
+      const int cw = e / N3;
+      if (!act[cw]) continue;
+      const int r = e - cw * N3;
+      const int i0 = r % N, i1 = (r / N) % N, i2 = r / N2;
+      const int id = D == 0 ? i0 : (D == 1 ? i1 : i2);
+      const T* line = S1 + (e - id * st);
+      const T* dr = Ds + id * N;
+      T g = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) g = fma(dr[j], line[j * st], g);
+      const T w3 = t.w[i0] * t.w[i1] * t.w[i2];
+      const T bq = b_gauss(ci[cw], D, i0, i1, i2);
+      S0[e] = w3 * fma(ci[cw].kd[D], g, -(ci[cw].jh[D] * bq) * S1[e]);
+    }
+    __syncwarp();
+    for (int e = lane; e < VEC; e += 32) {
+      const int cw = e / N3;
+      if (!act[cw]) continue;
+      const int r = e - cw * N3;
+      const int i0 = r % N, i1 = (r / N) % N, i2 = r / N2;
+      const int id = D == 0 ? i0 : (D == 1 ? i1 : i2);
+      const T* line = S0 + (e - id * st);
+      const T* dr = Dts + id * N;
+      T acc;
+      if (D == 0)
+        acc = ci[cw].cJ * (t.w[i0] * t.w[i1] * t.w[i2]) * S1[e];
+      else
+        acc = E[e];
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc = fma(dr[j], line[j * st], acc);
+      E[e] = acc;
+    }
+    __syncwarp();
+  }
+  contract_e<2, false>(E, S0, Bts, 0, lane, act);
+  __syncwarp();
+  contract_e<1, false>(S0, S1, Bts, 0, lane, act);
+  __syncwarp();
+  contract_e<0, false>(S1, Y, Bts, 0, lane, act);
+  __syncwarp();
+}
+
+// The face terms of all six faces with advection, element passes (FULL: with
+// the neighbours' values from gu; else the block D_T, neighbour values 0):
+//  1. per (face, node): qv = gamma [[u]] - kap (dn u + dn u_nb), qdv = -kap [[u]]
+//     (consistency, symmetry and penalty, as in faces_diffusion_dir) and the
+//     traces u_in, u_out;
+//  2. along the first tangential axis: M for qv, qdv; B (nodes to Gauss
+//     points) for the traces;
+//  3. along the second: M for qv, qdv; B for the traces and, at the face
+//     Gauss point, the upwind flux w |F| b.n (b.n >= 0 ? u_in : u_out);
+//  4, 5. B^T along the second, then the first tangential axis (the flux's
+//     test functions at the face nodes);
+//  6. per element: the face-layer values and the normal-derivative test
+//     functions of the six faces added to Y.
+// FS: 48 n^2 values per cell slot; AT the shared tables.
+constexpr int kAdvFace = 48 * N2;
+
+template <bool FULL, typename T, typename G>
+__device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __restrict__ gu, const MeshParams& mp,
+                            int lane, const unsigned char* act, const CellInfo<T>* ci) {
+  const Tab<T>& t = tab<T>();
+  const T* Bs = AT;
+  const T* Ms = AT + 4 * N2;
+  auto A0 = [&](int cw, int f, int fld) { return FS + ((cw * 2 + 0) * 24 + f * 4 + fld) * N2; };
+  auto A1 = [&](int cw, int f, int fld) { return FS + ((cw * 2 + 1) * 24 + f * 4 + fld) * N2; };
+  // 1. face-node values
+  for (int it = lane; it < CPW * 6 * N2; it += 32) {
+    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2;
+    const int d = f >> 1, S = f & 1;
+    T qv = T(0), qdv = T(0), tin = T(0), tout = T(0);
+    if (act[cw] && ci[cw].kind[f] != 2) {
+      const int a = L % N, b = L / N;
+      const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+      const int base = cw * N3 + (d == 0 ? N * a + N2 * b : (d == 1 ? a + N2 * b : a + N * b));
+      const T ih = Prec<T>::ih(mp, d);
+      const T sgn = S ? T(1) : T(-1);
+      T dn = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) dn = fma(t.dl[S][j], X[base + j * st], dn);
+      dn = dn * sgn * ih;
+      tin = X[base + (S ? N - 1 : 0) * st];
+      T dno = T(0);
+      if (FULL && ci[cw].kind[f] == 0) {
+        const G* xo = gu + ci[cw].nb[f] * N3 + (base - cw * N3);
+        tout = T(xo[(S ? 0 : N - 1) * st]);
+#pragma unroll
+        for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], T(xo[j * st]), dno);
+        dno = dno * sgn * ih;
+      }
+      const T kap = ci[cw].kap[f];
+      const T jmp = tin - tout;
+      qv = ci[cw].gam[f] * jmp - kap * (dn + dno);
+      qdv = -kap * jmp;
+    }
+    A0(cw, f, 0)[L] = qv;
+    A0(cw, f, 1)[L] = qdv;
+    A0(cw, f, 2)[L] = tin;
+    A0(cw, f, 3)[L] = tout;
+  }
+  __syncwarp();
+  // 2. first tangential axis: A1[L = a + N b] = sum_j Mat[a][j] A0[j + N b]
+  for (int it = lane; it < CPW * 24 * N2; it += 32) {
+    const int cw = it / (24 * N2), r = it - cw * 24 * N2, ff = r / N2, L = r - ff * N2;
+    const int f = ff >> 2, fld = ff & 3, a = L % N, b = L / N;
+    const T* src = A0(cw, f, fld) + N * b;
+    const T* m = (fld < 2 ? Ms : Bs) + a * N;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(m[j], src[j], acc);
+    A1(cw, f, fld)[L] = acc;
+  }
+  __syncwarp();
+  // 3. second tangential axis: qv, qdv by M into A0; the traces by B and the
+  //    upwind flux at the face Gauss point (qa, qb) into A0[..][2]
+  for (int it = lane; it < CPW * 18 * N2; it += 32) {
+    const int cw = it / (18 * N2), r = it - cw * 18 * N2;
+    if (r < 12 * N2) {
+      const int ff = r / N2, L = r - ff * N2, f = ff >> 1, fld = ff & 1, a = L % N, b = L / N;
+      const T* src = A1(cw, f, fld) + a;
+      const T* m = Ms + b * N;
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc = fma(m[j], src[j * N], acc);
+      A0(cw, f, fld)[L] = acc;
+    } else {
+      const int rr = r - 12 * N2, f = rr / N2, L = rr - f * N2, qa = L % N, qb = L / N;
+      const int d = f >> 1, S = f & 1;
+      const T* si = A1(cw, f, 2) + qa;
+      const T* so = A1(cw, f, 3) + qa;
+      const T* m = Bs + qb * N;
+      T ti = T(0), to = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        ti = fma(m[j], si[j * N], ti);
+        to = fma(m[j], so[j * N], to);
+      }
+      T phi = T(0);
+      if (act[cw] && ci[cw].kind[f] != 2) {
+        const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+        const T xa = t.gq[qa], xb = t.gq[qb];
+        T bn = T(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+          if (o[d] != S) continue;
+          const T wa = o[ta] ? xa : T(1) - xa;
+          const T wb = o[tb] ? xb : T(1) - xb;
+          bn = fma(ci[cw].bc[d][c], wa * wb, bn);
+        }
+        bn = S ? bn : -bn;
+        phi = t.w[qa] * t.w[qb] * Prec<T>::area(mp, d) * bn * (bn >= T(0) ? ti : to);
+      }
+      A0(cw, f, 2)[L] = phi;
+    }
+  }
+  __syncwarp();
+  // 4. B^T along the second axis: A1[.][3][a? qa + N b] = sum_qb B[qb][b] phi[qa + N qb]
+  for (int it = lane; it < CPW * 6 * N2; it += 32) {
+    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2, qa = L % N, b = L / N;
+    const T* src = A0(cw, f, 2) + qa;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(Bs[j * N + b], src[j * N], acc);
+    A1(cw, f, 3)[L] = acc;
+  }
+  __syncwarp();
+  // 5. B^T along the first axis: A0[.][3][a + N b] = sum_qa B[qa][a] A1[.][3][qa + N b]
+  for (int it = lane; it < CPW * 6 * N2; it += 32) {
+    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2, a = L % N, b = L / N;
+    const T* src = A1(cw, f, 3) + N * b;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(Bs[j * N + a], src[j], acc);
+    A0(cw, f, 3)[L] = acc;
+  }
+  __syncwarp();
+  // 6. scatter per element
+  for (int e = lane; e < VEC; e += 32) {
+    const int cw = e / N3;
+    if (!act[cw]) continue;
+    const int r = e - cw * N3;
+    const int i0 = r % N, i1 = (r / N) % N, i2 = r / N2;
+    T y = Y[e];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int j = d == 0 ? i0 : (d == 1 ? i1 : i2);
+      const int L = d == 0 ? i1 + N * i2 : (d == 1 ? i0 + N * i2 : i0 + N * i1);
+      const T area = Prec<T>::area(mp, d), ih = Prec<T>::ih(mp, d);
+#pragma unroll
+      for (int S = 0; S < 2; ++S) {
+        const int f = 2 * d + S;
+        const T dq = (S ? area * ih : -area * ih) * A0(cw, f, 1)[L];
+        y = fma(t.dl[S][j], dq, y);
+        if (j == (S ? N - 1 : 0)) y = fma(area, A0(cw, f, 0)[L], y + A0(cw, f, 3)[L]);
+      }
+    }
+    Y[e] = y;
+  }
+  __syncwarp();
+}
+
+// Shared values per warp of the element-form advection operator: the
+// Gauss-point accumulator E (one vector), the tables AT, the face scratch.
+constexpr int kAdvExtra = VEC + kAdvTab + CPW * kAdvFace;
+
+// Y = A X (FULL, neighbour values from gu) or D_T X with advection in element
+// form; Xt: the kAdvExtra region, its tables filled by adv_tables.
+template <bool FULL, typename T, typename G>
+__device__ __forceinline__ void adv_apply_e(const T* X, T* Y, T* S0, T* S1, T* Xt, const G* gu,
+                                            const MeshParams& mp, int lane, const unsigned char* act,
+                                            const CellInfo<T>* ci) {
+  T* E = Xt;
+  T* AT = Xt + VEC;
+  T* FS = AT + kAdvTab;
+  volume_adv_e(X, Y, S0, S1, E, AT, lane, ci, act);
+  faces_adv_e<FULL>(X, Y, FS, AT, gu, mp, lane, act, ci);
+}
+
 // F0 must be followed by 4 * LINES values of scratch (F0, F1 and the
 // reduction area are contiguous in every kernel's shared-memory carve).
 template <bool FULL, bool ADV, typename T, typename G>
@@ -1020,7 +1300,6 @@ __device__ __forceinline__ void carve(unsigned char* raw, int nvec, T** vec, T**
 template <typename T, bool FULL, bool ADV, bool FAC, typename G>
 __device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __restrict__ u, G* __restrict__ v,
                                            unsigned bid) {
-  static_assert(!(FAC && ADV), "the factored form is for b = 0");
   const bool react = mp.c != nullptr;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1030,9 +1309,11 @@ __device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __rest
   T *F0, *F1, *red;
   CellInfo<T>* ci;
   unsigned char* act;
-  // FAC (b = 0): the factored form (per-cell matrices, mass matrix, neighbour
-  // face values in the extra region); else the line form
-  constexpr int XT = FAC ? kFactorExtra : 0;
+  // FAC: element work items: for b = 0 the factored form (per-cell matrices,
+  // mass matrix, neighbour face values in the extra region), with advection
+  // the Gauss-point form (its accumulator, tables and face scratch there);
+  // else the line form
+  constexpr int XT = FAC ? (ADV ? kAdvExtra : kFactorExtra) : 0;
   T* Xt = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, nullptr, XT, &Xt);
   T *X = vec[0], *Y = vec[1], *S0 = vec[2], *S1 = vec[3];
@@ -1040,7 +1321,7 @@ __device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __rest
   const long long nval = (mp.ncell - cell0) * N3 < VEC ? (mp.ncell - cell0) * N3 : VEC;
   const G* ug = u + cell0 * N3;
   for (int e = lane; e < VEC; e += 32) X[e] = e < nval ? T(ug[e]) : T(0);
-  if constexpr (FAC) {
+  if constexpr (FAC && !ADV) {
     T* Ah = Xt;
     T* M1s = Ah + 3 * CPW * N2;
     T* MVs = M1s + N2;
@@ -1049,6 +1330,10 @@ __device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __rest
     factor_tables(M1s, MVs, lane);
     __syncwarp();
     factored_apply<FULL>(X, Y, S0, S1, Ah, M1s, MVs, FS, u, mp, lane, act, ci);
+  } else if constexpr (FAC && ADV) {
+    adv_tables(Xt + VEC, lane);
+    __syncwarp();
+    adv_apply_e<FULL>(X, Y, S0, S1, Xt, u, mp, lane, act, ci);
   } else {
     __syncwarp();
     volume<ADV>(X, Y, S0, S1, lane, ci, act, react);
@@ -1132,7 +1417,7 @@ __device__ __forceinline__ void cell_sum2(T& a, T& b, int lane, T* red) {
 // b = 0), nothing with advection.
 template <bool ADV, bool FAC>
 __host__ __device__ constexpr int smooth_extra() {
-  return FAC ? kFactorExtra : (ADV ? 0 : 3 * CPW * N2);
+  return FAC ? (ADV ? kAdvExtra : kFactorExtra) : (ADV ? 0 : 3 * CPW * N2);
 }
 
 // Block-Jacobi sweep with inner PCG (Algorithm 2; inner solve Sec. 2.2.1).
@@ -1155,7 +1440,6 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  static_assert(!(FAC && ADV), "the factored form is for b = 0");
   constexpr int XT = smooth_extra<ADV, FAC>();
   T* vec[6];
   T* Xt = nullptr;
@@ -1170,9 +1454,12 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
   T* M1s = Ah + 3 * CPW * N2;     // FAC only: mass matrix, M^-1 e_e, M^-1 dl_s, face values
   T* MVs = M1s + N2;
   T* FS = MVs + 4 * N;
-  if constexpr (FAC) {
+  if constexpr (FAC && !ADV) {
     hat_matrices(mp, Ah, ci, act, lane);
     factor_tables(M1s, MVs, lane);
+    __syncwarp();
+  } else if constexpr (FAC && ADV) {
+    adv_tables(Xt + VEC, lane);
     __syncwarp();
   } else if constexpr (!ADV) {
     block_matrices(mp, Ah, ci, act, lane);
@@ -1198,8 +1485,10 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
       P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
     __syncwarp();
-    if constexpr (FAC) {
+    if constexpr (FAC && !ADV) {
       factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, FS, uold, mp, lane, act, ci);
+    } else if constexpr (FAC && ADV) {
+      adv_apply_e<true>(P, Q, S0, S1, Xt, uold, mp, lane, act, ci);
     } else {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<true, ADV>(P, Q, F0, F1, uold, mp, cell0, lane, act, ci);
@@ -1239,7 +1528,9 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
     __syncwarp();
     const bool run = live && it < maxit;
     // Q = D_T P
-    if constexpr (ADV) {
+    if constexpr (ADV && FAC) {
+      adv_apply_e<false>(P, Q, S0, S1, Xt, (const G*)nullptr, mp, lane, act, ci);
+    } else if constexpr (ADV) {
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
     } else if constexpr (FAC) {
@@ -1372,8 +1663,7 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
   CellInfo<T>* ci;
   unsigned char* act;
   long long* cid;
-  static_assert(!(FAC && ADV), "the factored form is for b = 0");
-  constexpr int XT = FAC ? kFactorExtra : 0;
+  constexpr int XT = FAC ? (ADV ? kAdvExtra : kFactorExtra) : 0;
   T* Xt = nullptr;
   carve(smem + warp * WarpMem<T>::bytes(4, XT), 4, vec, &F0, &F1, &red, &ci, &act, &cid, XT, &Xt);
   T *P = vec[0], *Q = vec[1], *S0 = vec[2], *S1 = vec[3];
@@ -1387,7 +1677,7 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
       const int cw = e / N3;
       P[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
-    if constexpr (FAC) {   // the defect's operator in the factored form
+    if constexpr (FAC && !ADV) {   // the defect's operator in the factored form
       T* Ah = Xt;
       T* M1s = Ah + 3 * CPW * N2;
       T* MVs = M1s + N2;
@@ -1395,6 +1685,10 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
       factor_tables(M1s, MVs, lane);
       __syncwarp();
       factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, MVs + 4 * N, uold, mp, lane, act, ci);
+    } else if constexpr (FAC && ADV) {
+      adv_tables(Xt + VEC, lane);
+      __syncwarp();
+      adv_apply_e<true>(P, Q, S0, S1, Xt, uold, mp, lane, act, ci);
     } else {
       __syncwarp();
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
@@ -1799,7 +2093,7 @@ __host__ __device__ constexpr int gmres_scalars(int m) { return (m + 1) * m + 4 
 // |g_{j+1}| <= eps ||d|| or after maxit iterations; x += sum_i y_i V_i / diag;
 // restart from the recomputed residual d - D_T x.  The warp count per block is
 // blockDim.x / 32 (the basis needs (m+1) vectors per warp).
-template <typename T, bool ADV, typename G = typename Store<T>::type>
+template <typename T, bool ADV, bool ELEM, typename G = typename Store<T>::type>
 __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __restrict__ f, const G* uold,
                                                       G* unew, const G* __restrict__ diag, T omega, T eps,
                                                       int maxit, int m, int* __restrict__ its, int color,
@@ -1810,7 +2104,9 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
   const long long s0 = ((long long)blockIdx.x * wpb + warp) * CPW;
   if (s0 >= color_count(mp, color)) return;
   const int nvec = m + 7;
-  const size_t tbytes = align16((size_t)(nvec * VEC + 5 * LINES + CPW * gmres_scalars(m)) * sizeof(T));
+  // advection: the element-form operator's region after the scalars
+  constexpr int XA = (ADV && ELEM) ? kAdvExtra : 0;
+  const size_t tbytes = align16((size_t)(nvec * VEC + 5 * LINES + CPW * gmres_scalars(m) + XA) * sizeof(T));
   const size_t wbytes = tbytes + align16(CPW * sizeof(CellInfo<T>)) + 16 + align16(CPW * sizeof(long long));
   unsigned char* base = smem + warp * wbytes;
   T* p = reinterpret_cast<T*>(base);
@@ -1827,12 +2123,17 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
   T* F1 = F0 + LINES;
   T* red = F1 + LINES;
   T* sc = red + 3 * LINES;       // CPW * gmres_scalars(m)
+  T* Xa = sc + CPW * gmres_scalars(m);   // XA values (advection)
   CellInfo<T>* ci = reinterpret_cast<CellInfo<T>*>(base + tbytes);
   unsigned char* act = base + tbytes + align16(CPW * sizeof(CellInfo<T>));
   long long* cid = reinterpret_cast<long long*>(act + 16);
   slot_cells(mp, color, s0, lane, cid);
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
+  if constexpr (ADV && ELEM) {
+    adv_tables(Xa + VEC, lane);
+    __syncwarp();
+  }
   const int mycw = lane < LINES ? lane / N2 : -1;
   const bool mine = mycw >= 0 && act[mycw];
   const bool lead = lane < LINES && (lane % N2) == 0;    // writes the cell's scalars
@@ -1848,8 +2149,12 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
       Z[e] = act[cw] ? T(uold[cid[cw] * N3 + (e - cw * N3)]) : T(0);
     }
     __syncwarp();
-    volume<ADV>(Z, Q, S0, S1, lane, ci, act, react);
-    all_faces<true, ADV>(Z, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+    if constexpr (ADV && ELEM) {
+      adv_apply_e<true>(Z, Q, S0, S1, Xa, uold, mp, lane, act, ci);
+    } else {
+      volume<ADV>(Z, Q, S0, S1, lane, ci, act, react);
+      all_faces<true, ADV>(Z, Q, F0, F1, uold, mp, cell0, lane, act, ci);
+    }
   }
   T pdd = T(0);
   for (int L = lane; L < LINES; L += 32) {
@@ -1923,8 +2228,12 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
         }
       }
       __syncwarp();
-      volume<ADV>(Z, Q, S0, S1, lane, ci, act, react);
-      all_faces<false, ADV>(Z, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+      if constexpr (ADV && ELEM) {
+        adv_apply_e<false>(Z, Q, S0, S1, Xa, (const G*)nullptr, mp, lane, act, ci);
+      } else {
+        volume<ADV>(Z, Q, S0, S1, lane, ci, act, react);
+        all_faces<false, ADV>(Z, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+      }
       // modified Gram-Schmidt
       for (int i = 0; i <= j; ++i) {
         const T* Vi = V + i * VEC;
@@ -2045,8 +2354,12 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
     // r = d - D_T x; beta = ||r||
     if (lane < LINES) act[mycw] = ran ? 1 : 0;
     __syncwarp();
-    volume<ADV>(X, Q, S0, S1, lane, ci, act, react);
-    all_faces<false, ADV>(X, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+    if constexpr (ADV && ELEM) {
+      adv_apply_e<false>(X, Q, S0, S1, Xa, (const G*)nullptr, mp, lane, act, ci);
+    } else {
+      volume<ADV>(X, Q, S0, S1, lane, ci, act, react);
+      all_faces<false, ADV>(X, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
+    }
     T pr = T(0);
     if (ran) {
       for (int L = lane; L < LINES; L += 32) {
@@ -2429,7 +2742,7 @@ inline int pick_wpb_max(int tuned, size_t per_warp, int wmax) {
 template <typename T, bool FULL, bool ADV, bool FAC>
 cudaError_t launch_apply_form(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = FAC ? kFactorExtra : 0;
+  constexpr int XT = FAC ? (ADV ? kAdvExtra : kFactorExtra) : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_apply<T, FULL, ADV, FAC>;
@@ -2461,6 +2774,7 @@ cudaError_t launch_apply_plane(const MeshParams& mp, const void* u, void* v, cud
 template <typename T, bool FULL, bool ADV>
 cudaError_t launch_apply(const MeshParams& mp, const void* u, void* v, cudaStream_t s) {
   if constexpr (ADV) {
+    if (mp.lay_apply[prec_index<T>()] == DGMG_LAYOUT_ELEMENT) return launch_apply_form<T, FULL, true, true>(mp, u, v, s);
     return launch_apply_form<T, FULL, true, false>(mp, u, v, s);
   } else {
     const int lay = mp.lay_apply[prec_index<T>()];
@@ -2514,6 +2828,7 @@ cudaError_t launch_smooth_form(const MeshParams& mp, const SmoothArgs& a, cudaSt
 template <typename T, bool ADV>
 cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   if constexpr (ADV) {
+    if (mp.lay_smooth[prec_index<T>()] == DGMG_LAYOUT_ELEMENT) return launch_smooth_form<T, true, true>(mp, a, s);
     return launch_smooth_form<T, true, false>(mp, a, s);
   } else {
     const int lay = mp.lay_smooth[prec_index<T>()];
@@ -2543,7 +2858,7 @@ cudaError_t launch_smooth(const MeshParams& mp, const SmoothArgs& a, cudaStream_
 template <typename T, bool ADV, bool FAC>
 cudaError_t launch_inv_form(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
-  constexpr int XT = FAC ? kFactorExtra : 0;
+  constexpr int XT = FAC ? (ADV ? kAdvExtra : kFactorExtra) : 0;
   const int wpb = pick_wpb(mp.wpb_apply[prec_index<T>()], WarpMem<T>::bytes(4, XT));
   const size_t sm = wpb * WarpMem<T>::bytes(4, XT);
   auto k = k_smooth_inv<T, ADV, FAC>;
@@ -2563,9 +2878,10 @@ template <typename T, bool ADV>
 cudaError_t launch_inv(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   if (!a.binv) return cudaErrorInvalidValue;
   if constexpr (ADV) {
+    if (mp.lay_smooth[prec_index<T>()] == DGMG_LAYOUT_ELEMENT) return launch_inv_form<T, true, true>(mp, a, s);
     return launch_inv_form<T, true, false>(mp, a, s);
   } else {
-    if (mp.lay_smooth[prec_index<T>()] == DGMG_LAYOUT_FACTORED) return launch_inv_form<T, false, true>(mp, a, s);
+    if (mp.lay_smooth[prec_index<T>()] == DGMG_LAYOUT_ELEMENT) return launch_inv_form<T, false, true>(mp, a, s);
     return launch_inv_form<T, false, false>(mp, a, s);
   }
 }
@@ -2618,17 +2934,19 @@ cudaError_t block_matrix(const MeshParams& mp, double* out, int ld, cudaStream_t
   return mp.bvert ? launch_block_matrix<true>(mp, out, ld, s) : launch_block_matrix<false>(mp, out, ld, s);
 }
 
-template <typename T, bool ADV>
-cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+template <typename T, bool ADV, bool ELEM>
+cudaError_t launch_gmres_form(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
   using G = typename Store<T>::type;
   const int m = a.restart;
-  const size_t wbytes = align16((size_t)((m + 7) * VEC + 5 * LINES + CPW * gmres_scalars(m)) * sizeof(T)) +
-                        align16(CPW * sizeof(CellInfo<T>)) + 16 + align16(CPW * sizeof(long long));
+  constexpr int XA = (ADV && ELEM) ? kAdvExtra : 0;
+  const size_t wbytes =
+      align16((size_t)((m + 7) * VEC + 5 * LINES + CPW * gmres_scalars(m) + XA) * sizeof(T)) +
+      align16(CPW * sizeof(CellInfo<T>)) + 16 + align16(CPW * sizeof(long long));
   int wpb = (int)((200 * 1024) / wbytes);
   if (wpb > 4) wpb = 4;
   if (wpb < 1) return cudaErrorInvalidValue;      // restart too large for shared memory
   const size_t sm = wpb * wbytes;
-  auto k = k_smooth_gmres<T, ADV>;
+  auto k = k_smooth_gmres<T, ADV, ELEM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long long cells = a.color < 0 ? mp.ncell : host_color_count(mp, a.color);
@@ -2638,6 +2956,17 @@ cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t
                                T(a.eps), a.maxit, m, a.its, a.color, (const T*)a.tri);
   count_launch();
   return cudaGetLastError();
+}
+
+// GMRES sweep; with advection the element or line form by the smoother layout.
+template <typename T, bool ADV>
+cudaError_t launch_gmres(const MeshParams& mp, const SmoothArgs& a, cudaStream_t s) {
+  if constexpr (ADV) {
+    if (mp.lay_smooth[prec_index<T>()] == DGMG_LAYOUT_ELEMENT) return launch_gmres_form<T, true, true>(mp, a, s);
+    return launch_gmres_form<T, true, false>(mp, a, s);
+  } else {
+    return launch_gmres_form<T, false, false>(mp, a, s);
+  }
 }
 
 template <typename T>

@@ -19,8 +19,8 @@ DGMG_OK = 0
 STATUS = {0: "DGMG_OK", 1: "DGMG_ERR_ARG", 2: "DGMG_ERR_OOM", 3: "DGMG_ERR_CUDA", 4: "DGMG_ERR_STATE",
           5: "DGMG_ERR_NOT_CONVERGED", 6: "DGMG_ERR_BREAKDOWN", 7: "DGMG_ERR_TIMEOUT"}
 FP64, FP32, DF64 = 0, 1, 2
-LAYOUT_AUTO, LAYOUT_LINE, LAYOUT_FACTORED, LAYOUT_PLANE = 0, 1, 2, 3
-LAYOUT_NAMES = {LAYOUT_LINE: "line", LAYOUT_FACTORED: "factored", LAYOUT_PLANE: "plane"}
+LAYOUT_AUTO, LAYOUT_LINE, LAYOUT_ELEMENT, LAYOUT_PLANE = 0, 1, 2, 3
+LAYOUT_NAMES = {LAYOUT_LINE: "line", LAYOUT_ELEMENT: "element", LAYOUT_PLANE: "plane"}
 KRYLOV_CG, KRYLOV_FCG, KRYLOV_FGMRES = 0, 1, 2
 INNER_PCG, INNER_GMRES, INNER_DIRECT, INNER_GMRES_TRIDIAG = 0, 1, 2, 3
 COARSE_AMG, COARSE_NONE, COARSE_P0 = 0, 1, 2
@@ -324,7 +324,7 @@ class Context:
         self._check(self.lib.dgmg_set_launch_shape(self.h, prec, wpb_apply, wpb_smooth))
 
     def set_layout(self, prec, layout_apply=LAYOUT_AUTO, layout_smooth=LAYOUT_AUTO):
-        """Work layouts (LAYOUT_LINE / FACTORED / PLANE, or AUTO) of the
+        """Work layouts (LAYOUT_LINE / ELEMENT / PLANE, or AUTO) of the
         operator and inner-PCG smoother kernels for FP64, FP32 or DF64."""
         self._check(self.lib.dgmg_set_layout(self.h, prec, layout_apply, layout_smooth))
 

@@ -1,7 +1,7 @@
 """Small, fixed launch sequence of one kernel family, for ncu captures.
 
 python -m paper_1805_11930_gb300.profile_case --what apply|block|smooth --prec fp64|fp32 [--n 48] [--p 4]
-    [--inner pcg|direct] [--wpb-apply W] [--wpb-smooth W] [--layout auto|line|factored|plane]
+    [--inner pcg|direct] [--wpb-apply W] [--wpb-smooth W] [--layout auto|line|element|plane]
 
 Sets up the log-normal diffusion workload on an n^3 mesh (48^3 at p = 4 is
 13.8 M dofs, 110 MB per FP64 vector: larger than L2, a few hundred MB in
@@ -27,7 +27,7 @@ def main():
     ap.add_argument("--inner", default="pcg", choices=["pcg", "direct"])
     ap.add_argument("--wpb-apply", type=int, default=0)
     ap.add_argument("--wpb-smooth", type=int, default=0)
-    ap.add_argument("--layout", default="auto", choices=["auto", "line", "factored", "plane"])
+    ap.add_argument("--layout", default="auto", choices=["auto", "line", "element", "plane"])
     args = ap.parse_args()
 
     import torch
@@ -40,7 +40,7 @@ def main():
     nd = ctx.sizes()["ndof"]
     prec = dgmg.FP64 if args.prec == "fp64" else dgmg.FP32
     ctx.set_launch_shape(prec, args.wpb_apply, args.wpb_smooth)
-    lay = {"auto": dgmg.LAYOUT_AUTO, "line": dgmg.LAYOUT_LINE, "factored": dgmg.LAYOUT_FACTORED,
+    lay = {"auto": dgmg.LAYOUT_AUTO, "line": dgmg.LAYOUT_LINE, "element": dgmg.LAYOUT_ELEMENT,
            "plane": dgmg.LAYOUT_PLANE}[args.layout]
     ctx.set_layout(prec, lay, lay)
     inner = dgmg.INNER_DIRECT if args.inner == "direct" else dgmg.INNER_PCG

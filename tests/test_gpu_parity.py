@@ -529,31 +529,34 @@ def test_graph_captured_preconditioner_same_result():
     assert s0["kernel_launches"] == s1["kernel_launches"] and s0["sweeps"] == s1["sweeps"]
 
 
-def _layouts(prec, p):
+def _layouts(prec, p, advection=False):
     """The work layouts that exist for a precision and order."""
     from paper_1805_11930_gb300 import dgmg
-    out = [dgmg.LAYOUT_LINE, dgmg.LAYOUT_FACTORED]
-    if prec == dgmg.FP32 and p <= 4:
+    out = [dgmg.LAYOUT_LINE, dgmg.LAYOUT_ELEMENT]
+    if prec == dgmg.FP32 and p <= 4 and not advection:
         out.append(dgmg.LAYOUT_PLANE)
     return out
 
 
-@pytest.mark.parametrize("prec_name,p", [("FP64", 3), ("FP32", 3), ("FP32", 4), ("DF64", 3)])
-def test_launch_shape_does_not_change_results(prec_name, p):
+@pytest.mark.parametrize("prec_name,p,adv", [("FP64", 3, False), ("FP32", 3, False), ("FP32", 4, False),
+                                              ("DF64", 3, False), ("FP64", 3, True), ("FP32", 4, True)])
+def test_launch_shape_does_not_change_results(prec_name, p, adv):
     """In every work layout each warp owns whole cells, so the warps per block
     of the operator and smoother kernels change no bit of their outputs
     (ragged last block included: 5^3 cells do not fill any of the shapes or
-    the plane layout's cells per warp evenly)."""
+    the plane layout's cells per warp evenly); with advection for the line
+    and element forms and the inner GMRES smoother."""
     from paper_1805_11930_gb300 import dgmg
     prec = getattr(dgmg, prec_name)
-    w = inputs.lognormal(5, p)
+    w = inputs.convection(5, p, kappa=1e-2) if adv else inputs.lognormal(5, p)
+    inner = dgmg.INNER_GMRES if adv else dgmg.INNER_PCG
     ctx = gpu_context(w)
     dt = torch.float32 if prec == dgmg.FP32 else torch.float64
     df64 = prec == dgmg.DF64
     s = ctx.sizes()
     x = torch.tensor(inputs.random_dg_vector(s["ndof"], seed=11), device="cuda").to(dt)
     f = torch.tensor(inputs.random_dg_vector(s["ndof"], seed=12), device="cuda").to(dt)
-    for lay in _layouts(prec, p):
+    for lay in _layouts(prec, p, advection=adv):
         ctx.set_layout(prec, lay, lay)
         assert ctx.get_layout(prec) == (lay, lay)
         outs = []
@@ -562,7 +565,7 @@ def test_launch_shape_does_not_change_results(prec_name, p):
             v = torch.empty_like(x)
             ctx.apply(x, v, df64=df64)
             u = x.clone()
-            ctx.block_smooth(f, u, nsweep=2, omega=0.8, eps=1e-2, df64=df64)
+            ctx.block_smooth(f, u, nsweep=2, omega=0.8, eps=1e-2, df64=df64, inner=inner)
             outs.append((v.cpu().numpy(), u.cpu().numpy()))
         for v, u in outs[1:]:
             assert np.array_equal(v, outs[0][0]) and np.array_equal(u, outs[0][1]), lay
@@ -570,7 +573,7 @@ def test_launch_shape_does_not_change_results(prec_name, p):
 
 @pytest.mark.parametrize("name", ["p1_dir", "p2_mixed", "p5_dir", "p8_dir"])
 def test_every_layout_matches_the_oracle(name):
-    """Each work layout of the b = 0 kernels (line, factored, and the FP32
+    """Each work layout of the b = 0 kernels (line, element, and the FP32
     plane layout for p <= 4) against the oracle: the operator and the block
     D_T to 1e-12 (FP64) and 1e-5 (FP32), norm-wise and element by element on
     the corner, edge and face cells; two FP64 block-Jacobi sweeps with
@@ -631,6 +634,52 @@ def test_every_layout_matches_the_oracle(name):
                         assert rel_err(delta, x_or) < 1e-4, (lay, c)
                 assert same >= 0.8 * P.ncell, lay
         ctx.set_layout(prec, dgmg.LAYOUT_AUTO, dgmg.LAYOUT_AUTO)
+
+
+@pytest.mark.parametrize("name", ["p3_adv", "p4_full", "p6_adv"])
+def test_advection_layouts_match_the_oracle(name):
+    """With advection the line layout (one thread per pencil) and the element
+    layout (the Gauss-point form: interpolate, differentiate, weight, project
+    back) both give the oracle's operator and block D_T: FP64 to 1e-12, FP32
+    to 1e-5, element by element on the
+    corner, edge and face cells; in FP64 each form's block-Jacobi sweeps with
+    inner GMRES(12), eps = 1e-13, equal dense-LU block-Jacobi to 1e-9."""
+    from paper_1805_11930_gb300 import dgmg
+    w, P, A = oracle_matrix(name)
+    N = P.N
+    Ab = A.tobsr(blocksize=(N, N))
+    D = np.zeros((P.ncell, N, N))
+    for c in range(P.ncell):
+        for k in range(Ab.indptr[c], Ab.indptr[c + 1]):
+            if Ab.indices[k] == c:
+                D[c] = Ab.data[k]
+    u = inputs.random_dg_vector(P.ndof, seed=31)
+    f = inputs.random_dg_vector(P.ndof, seed=32)
+    u0 = inputs.random_dg_vector(P.ndof, seed=33)
+    ref_sm = solvers.BlockJacobi(A, N, inner="lu")(f, u0, 2, 0.8)
+    ctx = gpu_context(w)
+    cases = ((dgmg.FP64, torch.float64, 1e-12, 1e-13), (dgmg.FP32, torch.float32, 1e-5, 2e-6))
+    for prec, dt, tol, etol in cases:
+        for lay in (dgmg.LAYOUT_LINE, dgmg.LAYOUT_ELEMENT):
+            ctx.set_layout(prec, lay, lay)
+            x = dev(u, dt)
+            xd = x.double().cpu().numpy()
+            for full in (True, False):
+                v = torch.empty_like(x)
+                (ctx.apply if full else ctx.block_apply)(x, v)
+                ref = A @ xd if full else np.einsum('cij,cj->ci', D, xd.reshape(P.ncell, N)).reshape(-1)
+                got = v.double().cpu().numpy()
+                assert rel_err(got, ref) < tol, (prec, lay, full)
+                errs = elem_errors(got, ref, A, xd, w["nc"], N)
+                assert max(errs.values()) < etol, (prec, lay, full, errs)
+            if prec == dgmg.FP64:
+                us = dev(u0)
+                ctx.block_smooth(dev(f), us, nsweep=2, omega=0.8, eps=1e-13, maxit=20 * N,
+                                 inner=dgmg.INNER_GMRES, inner_restart=12)
+                assert rel_err(us.cpu().numpy(), ref_sm) < 1e-9, lay
+        ctx.set_layout(prec, dgmg.LAYOUT_AUTO, dgmg.LAYOUT_AUTO)
+    with pytest.raises(dgmg.DgmgError):
+        ctx.set_layout(dgmg.FP32, dgmg.LAYOUT_PLANE, dgmg.LAYOUT_PLANE)   # no plane form with advection
 
 
 def test_autotune_choices_and_bitwise_solve():
