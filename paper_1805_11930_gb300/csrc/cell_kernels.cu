@@ -917,9 +917,11 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
 // at every order (the line form leaves 7 of 32 lanes idle at n = 5 and takes
 // five synchronised phases per face).
 //
-// Tables in shared memory (their row index varies across the lanes):
-// AT = [B | B^T | Dg | Dg^T | M], n^2 each, row-major.
-constexpr int kAdvTab = 5 * N2;
+// Tables in shared memory (their index varies across the lanes, which
+// constant memory would serialise):
+// AT = [B | B^T | Dg | Dg^T | M | W2], n^2 each, row-major, W2[i + n j] =
+// w_i w_j; then [w | w gq | dl_0 | dl_1], n each.
+constexpr int kAdvTab = 6 * N2 + 4 * N;
 
 template <typename T>
 __device__ __forceinline__ void adv_tables(T* AT, int lane) {
@@ -931,31 +933,54 @@ __device__ __forceinline__ void adv_tables(T* AT, int lane) {
     AT[2 * N2 + k] = t.Dg[i][j];
     AT[3 * N2 + k] = t.Dg[j][i];
     AT[4 * N2 + k] = t.M1[i][j];
+    AT[5 * N2 + k] = t.w[j] * t.w[i];
+  }
+  for (int k = lane; k < N; k += 32) {
+    AT[6 * N2 + k] = t.w[k];
+    AT[6 * N2 + N + k] = t.w[k] * t.gq[k];
+    AT[6 * N2 + 2 * N + k] = t.dl[0][k];
+    AT[6 * N2 + 3 * N + k] = t.dl[1][k];
   }
 }
 
-// b_D at the Gauss point (gq[i0], gq[i1], gq[i2]) of cell slot cw: the
-// trilinear interpolation of the corner values, as nested linear blends.
+// Per cell slot and direction D the separable factors of the pointwise
+// volume coefficients at the Gauss points.  b_D is trilinear on the cell, so
+// b_D(x, y, z) = c0(x, y) + z c1(x, y) with c0 the bilinear blend of the
+// z = 0 corners and c1 that of the z = 1 corners minus c0:
+//   BT[(cw 3 + D) 3 n^2 + {0, 1, 2} n^2 + i0 + n i1]
+//     = |J|/h_D w_i0 w_i1 {c0, c1} (gq_i0, gq_i1),  |J| K_D / h_D^2 w_i0 w_i1,
+// so that at Gauss point (i0, i1, i2) w3 |J|/h_D b_D = w_i2 (c0' + gq_i2 c1')
+// and w3 |J| K_D / h_D^2 = w_i2 k'.
 template <typename T>
-__device__ __forceinline__ T b_gauss(const CellInfo<T>& c, int D, int i0, int i1, int i2) {
+__device__ __forceinline__ void adv_point_tables(T* BT, const T* AT, int lane, const CellInfo<T>* ci,
+                                                 const unsigned char* act) {
   const Tab<T>& t = tab<T>();
-  const T x = t.gq[i0], y = t.gq[i1], z = t.gq[i2];
-  const T* b = c.bc[D];
-  const T b00 = fma(x, b[1] - b[0], b[0]), b10 = fma(x, b[3] - b[2], b[2]);
-  const T b01 = fma(x, b[5] - b[4], b[4]), b11 = fma(x, b[7] - b[6], b[6]);
-  const T c0 = fma(y, b10 - b00, b00), c1 = fma(y, b11 - b01, b01);
-  return fma(z, c1 - c0, c0);
+  for (int it = lane; it < CPW * 3 * N2; it += 32) {
+    const int cw = it / (3 * N2), r = it - cw * 3 * N2, D = r / N2, L = r - D * N2;
+    if (!act[cw]) continue;
+    const int i0 = L % N, i1 = L / N;
+    const T x = t.gq[i0], y = t.gq[i1];
+    const T* b = ci[cw].bc[D];
+    const T b00 = fma(x, b[1] - b[0], b[0]), b10 = fma(x, b[3] - b[2], b[2]);
+    const T b01 = fma(x, b[5] - b[4], b[4]), b11 = fma(x, b[7] - b[6], b[6]);
+    const T c0 = fma(y, b10 - b00, b00), c1 = fma(y, b11 - b01, b01) - c0;
+    const T w2 = AT[5 * N2 + L];
+    T* bt = BT + (cw * 3 + D) * 3 * N2;
+    bt[L] = ci[cw].jh[D] * w2 * c0;
+    bt[N2 + L] = ci[cw].jh[D] * w2 * c1;
+    bt[2 * N2 + L] = ci[cw].kd[D] * w2;
+  }
 }
 
 // Y = A^v X with advection at the Gauss points (Sec. 3.1's three stages):
 // U = (B (x) B (x) B) X; per direction D the pointwise flux
 // Q = w (|J| K_D / h_D^2 Dg_D U - |J| / h_D b_D U) and E (+)= Dg_D^T Q, with the
 // reaction c |J| w U added once; Y = (B^T (x) B^T (x) B^T) E.  Element passes;
-// S0, S1, E scratch vectors; AT the shared tables.
+// S0, S1, E scratch vectors; AT the shared tables; BT scratch for the point
+// factors of adv_point_tables (9 n^2 values per cell slot).
 template <typename T>
-__device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* E, const T* AT, int lane,
+__device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* E, const T* AT, T* BT, int lane,
                                              const CellInfo<T>* ci, const unsigned char* act) {
-  const Tab<T>& t = tab<T>();
   const T* Bs = AT;
   const T* Bts = AT + N2;
   const T* Ds = AT + 2 * N2;
@@ -965,11 +990,12 @@ __device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* 
   contract_e<1, false>(S1, S0, Bs, 0, lane, act);
   __syncwarp();
   contract_e<2, false>(S0, S1, Bs, 0, lane, act);   // S1 = u at the Gauss points
+  adv_point_tables(BT, AT, lane, ci, act);
   __syncwarp();
+  const T* W2 = AT + 5 * N2;
+  const T* Wq = AT + 6 * N2;
 #pragma unroll
   for (int D = 0; D < 3; ++D) {
-    constexpr int dummy = 0;
-    (void)dummy;
     const int st = D == 0 ? 1 : (D == 1 ? N : N2);
     for (int e = lane; e < VEC; e += 32) {
       const int cw = e / N3;
@@ -982,9 +1008,10 @@ __device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* 
       T g = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) g = fma(dr[j], line[j * st], g);
-      const T w3 = t.w[i0] * t.w[i1] * t.w[i2];
-      const T bq = b_gauss(ci[cw], D, i0, i1, i2);
-      S0[e] = w3 * fma(ci[cw].kd[D], g, -(ci[cw].jh[D] * bq) * S1[e]);
+      const T* bt = BT + (cw * 3 + D) * 3 * N2 + i0 + N * i1;
+      const T wz = Wq[i2];
+      const T beta = fma(Wq[N + i2], bt[N2], wz * bt[0]);   // w3 |J|/h_D b_D
+      S0[e] = fma(wz * bt[2 * N2], g, -beta * S1[e]);
     }
     __syncwarp();
     for (int e = lane; e < VEC; e += 32) {
@@ -997,7 +1024,7 @@ __device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* 
       const T* dr = Dts + id * N;
       T acc;
       if (D == 0)
-        acc = ci[cw].cJ * (t.w[i0] * t.w[i1] * t.w[i2]) * S1[e];
+        acc = ci[cw].cJ * (W2[i0 + N * i1] * Wq[i2]) * S1[e];
       else
         acc = E[e];
 #pragma unroll
@@ -1036,6 +1063,7 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
   const Tab<T>& t = tab<T>();
   const T* Bs = AT;
   const T* Ms = AT + 4 * N2;
+  const T* DL = AT + 6 * N2 + 2 * N;   // dl_0, dl_1
   auto A0 = [&](int cw, int f, int fld) { return FS + ((cw * 2 + 0) * 24 + f * 4 + fld) * N2; };
   auto A1 = [&](int cw, int f, int fld) { return FS + ((cw * 2 + 1) * 24 + f * 4 + fld) * N2; };
   // 1. face-node values
@@ -1096,7 +1124,12 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
       T acc = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) acc = fma(m[j], src[j * N], acc);
-      A0(cw, f, fld)[L] = acc;
+      // the face measure, and for the normal-derivative test functions the
+      // outward 1/h, applied here once per face node
+      const int d = f >> 1;
+      const T area = Prec<T>::area(mp, d);
+      const T ah = (f & 1) ? area * Prec<T>::ih(mp, d) : -(area * Prec<T>::ih(mp, d));
+      A0(cw, f, fld)[L] = acc * (fld == 0 ? area : ah);
     } else {
       const int rr = r - 12 * N2, f = rr / N2, L = rr - f * N2, qa = L % N, qb = L / N;
       const int d = f >> 1, S = f & 1;
@@ -1123,7 +1156,7 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
           bn = fma(ci[cw].bc[d][c], wa * wb, bn);
         }
         bn = S ? bn : -bn;
-        phi = t.w[qa] * t.w[qb] * Prec<T>::area(mp, d) * bn * (bn >= T(0) ? ti : to);
+        phi = AT[5 * N2 + qa + N * qb] * Prec<T>::area(mp, d) * bn * (bn >= T(0) ? ti : to);
       }
       A0(cw, f, 2)[L] = phi;
     }
@@ -1160,13 +1193,11 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
     for (int d = 0; d < 3; ++d) {
       const int j = d == 0 ? i0 : (d == 1 ? i1 : i2);
       const int L = d == 0 ? i1 + N * i2 : (d == 1 ? i0 + N * i2 : i0 + N * i1);
-      const T area = Prec<T>::area(mp, d), ih = Prec<T>::ih(mp, d);
 #pragma unroll
       for (int S = 0; S < 2; ++S) {
         const int f = 2 * d + S;
-        const T dq = (S ? area * ih : -area * ih) * A0(cw, f, 1)[L];
-        y = fma(t.dl[S][j], dq, y);
-        if (j == (S ? N - 1 : 0)) y = fma(area, A0(cw, f, 0)[L], y + A0(cw, f, 3)[L]);
+        y = fma(DL[S * N + j], A0(cw, f, 1)[L], y);
+        if (j == (S ? N - 1 : 0)) y += A0(cw, f, 0)[L] + A0(cw, f, 3)[L];
       }
     }
     Y[e] = y;
@@ -1187,7 +1218,7 @@ __device__ __forceinline__ void adv_apply_e(const T* X, T* Y, T* S0, T* S1, T* X
   T* E = Xt;
   T* AT = Xt + VEC;
   T* FS = AT + kAdvTab;
-  volume_adv_e(X, Y, S0, S1, E, AT, lane, ci, act);
+  volume_adv_e(X, Y, S0, S1, E, AT, FS, lane, ci, act);
   faces_adv_e<FULL>(X, Y, FS, AT, gu, mp, lane, act, ci);
 }
 
@@ -2733,7 +2764,7 @@ cudaError_t set_smem(KernelT k, size_t bytes) {
 }
 
 // Warps per block, at most wmax (the kernel's launch bound / 32).
-inline int pick_wpb_max(int tuned, size_t per_warp, int wmax) {
+[[maybe_unused]] inline int pick_wpb_max(int tuned, size_t per_warp, int wmax) {
   int w = pick_wpb(tuned, per_warp);
   while (w > wmax) w >>= 1;
   return w;
