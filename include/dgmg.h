@@ -408,7 +408,7 @@ dgmg_status dgmg_set_launch_shape(dgmg_ctx* ctx, dgmg_prec prec, int wpb_apply, 
  *            the operator and the Jacobi sweep (a block-SOR colour takes LINE).
  * AUTO selects the default of the precision, order and kernel: b = 0: ELEMENT
  * for FP64 and DF64; in FP32 LINE for the operator and PLANE for the smoother
- * with p <= 4 (else LINE); b != 0: ELEMENT for FP64 at p = 4 and 5, else
+ * with p <= 4 (else LINE); b != 0: ELEMENT for FP64 at p = 4..6, else
  * LINE (the faster forms measured on GB300). */
 typedef enum {
   DGMG_LAYOUT_AUTO = 0,

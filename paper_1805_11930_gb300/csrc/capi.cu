@@ -288,10 +288,10 @@ void dfree(dgmg_ctx* ctx, void* q) {
 // precision, order and kernel, the faster form measured on GB300.  b = 0:
 // ELEMENT (the factored form) for FP64 and DF64; in FP32 LINE for the
 // operator, PLANE for the smoother with p <= 4.  b != 0: ELEMENT for FP64 at
-// p = 4 and 5, LINE otherwise.
+// p = 4..6, LINE otherwise (p = 7, 8 unmeasured: the line form).
 int resolve_layout(const dgmg_ctx* ctx, int prec, int lay, bool smoother) {
   if (lay != DGMG_LAYOUT_AUTO) return lay;
-  if (ctx->db) return prec == DGMG_FP64 && (ctx->p == 4 || ctx->p == 5) ? DGMG_LAYOUT_ELEMENT : DGMG_LAYOUT_LINE;
+  if (ctx->db) return prec == DGMG_FP64 && ctx->p >= 4 && ctx->p <= 6 ? DGMG_LAYOUT_ELEMENT : DGMG_LAYOUT_LINE;
   if (prec == DGMG_FP32) return smoother && ctx->p <= 4 ? DGMG_LAYOUT_PLANE : DGMG_LAYOUT_LINE;
   return DGMG_LAYOUT_ELEMENT;
 }

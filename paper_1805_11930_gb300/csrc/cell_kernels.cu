@@ -1041,8 +1041,9 @@ __device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* 
   __syncwarp();
 }
 
-// The face terms of all six faces with advection, element passes (FULL: with
-// the neighbours' values from gu; else the block D_T, neighbour values 0):
+// The face terms with advection, element passes, for the faces FB ..
+// FB + kAdvNF - 1 (FULL: with the neighbours' values from gu; else the block
+// D_T, neighbour values 0):
 //  1. per (face, node): qv = gamma [[u]] - kap (dn u + dn u_nb), qdv = -kap [[u]]
 //     (consistency, symmetry and penalty, as in faces_diffusion_dir) and the
 //     traces u_in, u_out;
@@ -1053,23 +1054,30 @@ __device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* 
 //  4, 5. B^T along the second, then the first tangential axis (the flux's
 //     test functions at the face nodes);
 //  6. per element: the face-layer values and the normal-derivative test
-//     functions of the six faces added to Y.
-// FS: 48 n^2 values per cell slot; AT the shared tables.
-constexpr int kAdvFace = 48 * N2;
+//     functions of the group's faces added to Y.
+// Faces per group: all six at once, or for n >= 7 the two of one direction
+// at a time, so that the face scratch fits where the volume term keeps its
+// Gauss-point accumulator and more warps fit on an SM (measured on GB300 in
+// FP64: 2.09 against 1.59 GDOF/s at n = 7, 2.19 against 2.35 at n = 6).
+// FS: kAdvFace values per cell slot (two areas of 4 fields per face); AT the
+// shared tables.
+constexpr int kAdvNF = N >= 7 ? 2 : 6;
+constexpr int kAdvFace = 8 * kAdvNF * N2;
 
-template <bool FULL, typename T, typename G>
+template <bool FULL, int FB, typename T, typename G>
 __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __restrict__ gu, const MeshParams& mp,
                             int lane, const unsigned char* act, const CellInfo<T>* ci) {
+  constexpr int NF = kAdvNF;
   const Tab<T>& t = tab<T>();
   const T* Bs = AT;
   const T* Ms = AT + 4 * N2;
   const T* DL = AT + 6 * N2 + 2 * N;   // dl_0, dl_1
-  auto A0 = [&](int cw, int f, int fld) { return FS + ((cw * 2 + 0) * 24 + f * 4 + fld) * N2; };
-  auto A1 = [&](int cw, int f, int fld) { return FS + ((cw * 2 + 1) * 24 + f * 4 + fld) * N2; };
+  auto A0 = [&](int cw, int fl, int fld) { return FS + ((cw * 2 + 0) * 4 * NF + fl * 4 + fld) * N2; };
+  auto A1 = [&](int cw, int fl, int fld) { return FS + ((cw * 2 + 1) * 4 * NF + fl * 4 + fld) * N2; };
   // 1. face-node values
-  for (int it = lane; it < CPW * 6 * N2; it += 32) {
-    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2;
-    const int d = f >> 1, S = f & 1;
+  for (int it = lane; it < CPW * NF * N2; it += 32) {
+    const int cw = it / (NF * N2), r = it - cw * NF * N2, fl = r / N2, L = r - fl * N2;
+    const int f = FB + fl, d = f >> 1, S = f & 1;
     T qv = T(0), qdv = T(0), tin = T(0), tout = T(0);
     if (act[cw] && ci[cw].kind[f] != 2) {
       const int a = L % N, b = L / N;
@@ -1095,31 +1103,32 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
       qv = ci[cw].gam[f] * jmp - kap * (dn + dno);
       qdv = -kap * jmp;
     }
-    A0(cw, f, 0)[L] = qv;
-    A0(cw, f, 1)[L] = qdv;
-    A0(cw, f, 2)[L] = tin;
-    A0(cw, f, 3)[L] = tout;
+    A0(cw, fl, 0)[L] = qv;
+    A0(cw, fl, 1)[L] = qdv;
+    A0(cw, fl, 2)[L] = tin;
+    A0(cw, fl, 3)[L] = tout;
   }
   __syncwarp();
   // 2. first tangential axis: A1[L = a + N b] = sum_j Mat[a][j] A0[j + N b]
-  for (int it = lane; it < CPW * 24 * N2; it += 32) {
-    const int cw = it / (24 * N2), r = it - cw * 24 * N2, ff = r / N2, L = r - ff * N2;
-    const int f = ff >> 2, fld = ff & 3, a = L % N, b = L / N;
-    const T* src = A0(cw, f, fld) + N * b;
+  for (int it = lane; it < CPW * 4 * NF * N2; it += 32) {
+    const int cw = it / (4 * NF * N2), r = it - cw * 4 * NF * N2, ff = r / N2, L = r - ff * N2;
+    const int fl = ff >> 2, fld = ff & 3, a = L % N, b = L / N;
+    const T* src = A0(cw, fl, fld) + N * b;
     const T* m = (fld < 2 ? Ms : Bs) + a * N;
     T acc = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) acc = fma(m[j], src[j], acc);
-    A1(cw, f, fld)[L] = acc;
+    A1(cw, fl, fld)[L] = acc;
   }
   __syncwarp();
   // 3. second tangential axis: qv, qdv by M into A0; the traces by B and the
   //    upwind flux at the face Gauss point (qa, qb) into A0[..][2]
-  for (int it = lane; it < CPW * 18 * N2; it += 32) {
-    const int cw = it / (18 * N2), r = it - cw * 18 * N2;
-    if (r < 12 * N2) {
-      const int ff = r / N2, L = r - ff * N2, f = ff >> 1, fld = ff & 1, a = L % N, b = L / N;
-      const T* src = A1(cw, f, fld) + a;
+  for (int it = lane; it < CPW * 3 * NF * N2; it += 32) {
+    const int cw = it / (3 * NF * N2), r = it - cw * 3 * NF * N2;
+    if (r < 2 * NF * N2) {
+      const int ff = r / N2, L = r - ff * N2, fl = ff >> 1, fld = ff & 1, a = L % N, b = L / N;
+      const int f = FB + fl;
+      const T* src = A1(cw, fl, fld) + a;
       const T* m = Ms + b * N;
       T acc = T(0);
 #pragma unroll
@@ -1129,12 +1138,12 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
       const int d = f >> 1;
       const T area = Prec<T>::area(mp, d);
       const T ah = (f & 1) ? area * Prec<T>::ih(mp, d) : -(area * Prec<T>::ih(mp, d));
-      A0(cw, f, fld)[L] = acc * (fld == 0 ? area : ah);
+      A0(cw, fl, fld)[L] = acc * (fld == 0 ? area : ah);
     } else {
-      const int rr = r - 12 * N2, f = rr / N2, L = rr - f * N2, qa = L % N, qb = L / N;
-      const int d = f >> 1, S = f & 1;
-      const T* si = A1(cw, f, 2) + qa;
-      const T* so = A1(cw, f, 3) + qa;
+      const int rr = r - 2 * NF * N2, fl = rr / N2, L = rr - fl * N2, qa = L % N, qb = L / N;
+      const int f = FB + fl, d = f >> 1, S = f & 1;
+      const T* si = A1(cw, fl, 2) + qa;
+      const T* so = A1(cw, fl, 3) + qa;
       const T* m = Bs + qb * N;
       T ti = T(0), to = T(0);
 #pragma unroll
@@ -1158,28 +1167,28 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
         bn = S ? bn : -bn;
         phi = AT[5 * N2 + qa + N * qb] * Prec<T>::area(mp, d) * bn * (bn >= T(0) ? ti : to);
       }
-      A0(cw, f, 2)[L] = phi;
+      A0(cw, fl, 2)[L] = phi;
     }
   }
   __syncwarp();
-  // 4. B^T along the second axis: A1[.][3][a? qa + N b] = sum_qb B[qb][b] phi[qa + N qb]
-  for (int it = lane; it < CPW * 6 * N2; it += 32) {
-    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2, qa = L % N, b = L / N;
-    const T* src = A0(cw, f, 2) + qa;
+  // 4. B^T along the second axis: A1[.][3][qa + N b] = sum_qb B[qb][b] phi[qa + N qb]
+  for (int it = lane; it < CPW * NF * N2; it += 32) {
+    const int cw = it / (NF * N2), r = it - cw * NF * N2, fl = r / N2, L = r - fl * N2, qa = L % N, b = L / N;
+    const T* src = A0(cw, fl, 2) + qa;
     T acc = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) acc = fma(Bs[j * N + b], src[j * N], acc);
-    A1(cw, f, 3)[L] = acc;
+    A1(cw, fl, 3)[L] = acc;
   }
   __syncwarp();
   // 5. B^T along the first axis: A0[.][3][a + N b] = sum_qa B[qa][a] A1[.][3][qa + N b]
-  for (int it = lane; it < CPW * 6 * N2; it += 32) {
-    const int cw = it / (6 * N2), r = it - cw * 6 * N2, f = r / N2, L = r - f * N2, a = L % N, b = L / N;
-    const T* src = A1(cw, f, 3) + N * b;
+  for (int it = lane; it < CPW * NF * N2; it += 32) {
+    const int cw = it / (NF * N2), r = it - cw * NF * N2, fl = r / N2, L = r - fl * N2, a = L % N, b = L / N;
+    const T* src = A1(cw, fl, 3) + N * b;
     T acc = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) acc = fma(Bs[j * N + a], src[j], acc);
-    A0(cw, f, 3)[L] = acc;
+    A0(cw, fl, 3)[L] = acc;
   }
   __syncwarp();
   // 6. scatter per element
@@ -1190,14 +1199,14 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
     const int i0 = r % N, i1 = (r / N) % N, i2 = r / N2;
     T y = Y[e];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int d = FB / 2; d < (FB + NF) / 2; ++d) {
       const int j = d == 0 ? i0 : (d == 1 ? i1 : i2);
       const int L = d == 0 ? i1 + N * i2 : (d == 1 ? i0 + N * i2 : i0 + N * i1);
 #pragma unroll
       for (int S = 0; S < 2; ++S) {
-        const int f = 2 * d + S;
-        y = fma(DL[S * N + j], A0(cw, f, 1)[L], y);
-        if (j == (S ? N - 1 : 0)) y += A0(cw, f, 0)[L] + A0(cw, f, 3)[L];
+        const int fl = 2 * d + S - FB;
+        y = fma(DL[S * N + j], A0(cw, fl, 1)[L], y);
+        if (j == (S ? N - 1 : 0)) y += A0(cw, fl, 0)[L] + A0(cw, fl, 3)[L];
       }
     }
     Y[e] = y;
@@ -1205,21 +1214,30 @@ __device__ void faces_adv_e(const T* X, T* Y, T* FS, const T* AT, const G* __res
   __syncwarp();
 }
 
-// Shared values per warp of the element-form advection operator: the
-// Gauss-point accumulator E (one vector), the tables AT, the face scratch.
-constexpr int kAdvExtra = VEC + kAdvTab + CPW * kAdvFace;
+// Shared values per warp of the element-form advection operator: the tables
+// AT, then one region that holds the Gauss-point accumulator E (one vector)
+// and the point factors BT (9 n^2 per cell slot) during the volume term and
+// the face scratch during the faces.
+constexpr int kAdvVol = VEC + 9 * CPW * N2;
+constexpr int kAdvRegion = kAdvVol > CPW * kAdvFace ? kAdvVol : CPW * kAdvFace;
+constexpr int kAdvExtra = kAdvTab + kAdvRegion;
 
 // Y = A X (FULL, neighbour values from gu) or D_T X with advection in element
-// form; Xt: the kAdvExtra region, its tables filled by adv_tables.
+// form; Xt: the kAdvExtra region, its tables filled by adv_tables(Xt).
 template <bool FULL, typename T, typename G>
 __device__ __forceinline__ void adv_apply_e(const T* X, T* Y, T* S0, T* S1, T* Xt, const G* gu,
                                             const MeshParams& mp, int lane, const unsigned char* act,
                                             const CellInfo<T>* ci) {
-  T* E = Xt;
-  T* AT = Xt + VEC;
-  T* FS = AT + kAdvTab;
-  volume_adv_e(X, Y, S0, S1, E, AT, FS, lane, ci, act);
-  faces_adv_e<FULL>(X, Y, FS, AT, gu, mp, lane, act, ci);
+  const T* AT = Xt;
+  T* E = Xt + kAdvTab;
+  volume_adv_e(X, Y, S0, S1, E, AT, E + VEC, lane, ci, act);
+  if constexpr (kAdvNF == 6) {
+    faces_adv_e<FULL, 0>(X, Y, E, AT, gu, mp, lane, act, ci);
+  } else {
+    faces_adv_e<FULL, 0>(X, Y, E, AT, gu, mp, lane, act, ci);
+    faces_adv_e<FULL, 2>(X, Y, E, AT, gu, mp, lane, act, ci);
+    faces_adv_e<FULL, 4>(X, Y, E, AT, gu, mp, lane, act, ci);
+  }
 }
 
 // F0 must be followed by 4 * LINES values of scratch (F0, F1 and the
@@ -1362,7 +1380,7 @@ __device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __rest
     __syncwarp();
     factored_apply<FULL>(X, Y, S0, S1, Ah, M1s, MVs, FS, u, mp, lane, act, ci);
   } else if constexpr (FAC && ADV) {
-    adv_tables(Xt + VEC, lane);
+    adv_tables(Xt, lane);
     __syncwarp();
     adv_apply_e<FULL>(X, Y, S0, S1, Xt, u, mp, lane, act, ci);
   } else {
@@ -1490,7 +1508,7 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
     factor_tables(M1s, MVs, lane);
     __syncwarp();
   } else if constexpr (FAC && ADV) {
-    adv_tables(Xt + VEC, lane);
+    adv_tables(Xt, lane);
     __syncwarp();
   } else if constexpr (!ADV) {
     block_matrices(mp, Ah, ci, act, lane);
@@ -1717,7 +1735,7 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
       __syncwarp();
       factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, MVs + 4 * N, uold, mp, lane, act, ci);
     } else if constexpr (FAC && ADV) {
-      adv_tables(Xt + VEC, lane);
+      adv_tables(Xt, lane);
       __syncwarp();
       adv_apply_e<true>(P, Q, S0, S1, Xt, uold, mp, lane, act, ci);
     } else {
@@ -2162,7 +2180,7 @@ __global__ void __launch_bounds__(128) k_smooth_gmres(MeshParams mp, const G* __
   stage_cells(mp, 0, lane, ci, act, cid);
   const long long cell0 = cid[0];
   if constexpr (ADV && ELEM) {
-    adv_tables(Xa + VEC, lane);
+    adv_tables(Xa, lane);
     __syncwarp();
   }
   const int mycw = lane < LINES ? lane / N2 : -1;
@@ -2552,46 +2570,75 @@ __global__ void k_diag_kron(MeshParams mp, double* __restrict__ diag) {
   diag[gid] = a[0] * m1 * m2 + m0 * a[1] * m2 + m0 * m1 * a[2];
 }
 
+// Lanes per cell of the transfer kernels (at least 8: one per corner) and
+// cells per warp: a lane per z-line (i, j) of the cell, n^2 lines.
+constexpr int kTG = N2 <= 8 ? 8 : (N2 <= 16 ? 16 : 32);
+constexpr int kTCells = 32 / kTG;
+
 // Corner sums r_hat_c(T) = sum_i prod_k phi_{c_k}(zeta_{i_k}) r_T(i) (the cell
-// part of R = P^T): one warp per cell, each lane accumulates the 8 corner
-// weights over its dofs in the kernel's precision, then a fixed-order warp
-// reduction.
+// part of R = P^T), in the separable order: each lane sums its z-line with
+// the two z hats (coalesced loads: the lanes' lines are adjacent), weights
+// the two sums with the four products of x and y hats of its line, and a
+// fixed-order reduction over the cell's lanes gives the 8 corners (kernel
+// precision; 4 flops per dof).  The reduction is transposed: at each of the
+// first three levels a lane keeps half of its values and adds its partner's
+// matching half, so that 8 values over kTG lanes take log2(kTG) + 4
+// shuffle-adds per lane instead of 8 log2(kTG) (the FP64 adds of the plain
+// tree cost more than the sums themselves).
 template <typename T>
 __device__ __forceinline__ void restrict_cells_body(long long ncell, const T* __restrict__ r,
                                                     double* __restrict__ corners, unsigned bid) {
-  const long long c = ((long long)bid * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (c >= ncell) return;
+  const long long c0 = (((long long)bid * blockDim.x + threadIdx.x) >> 5) * kTCells;
+  if (c0 >= ncell) return;   // the whole warp
+  const long long c = c0 + lane / kTG;
+  const int g = lane % kTG;
+  const bool on = c < ncell;
   const Tab<T>& t = tab<T>();
-  const T* rc = r + c * N3;
   T acc[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = T(0);
-  for (int i = lane; i < N3; i += 32) {
-    const int i1 = i % N, i2 = (i / N) % N, i3 = i / N2;
-    const T v = rc[i];
-    const T wz0 = t.hat[0][i3] * v, wz1 = t.hat[1][i3] * v;
-    const T w00 = t.hat[0][i2] * wz0, w10 = t.hat[1][i2] * wz0, w01 = t.hat[0][i2] * wz1, w11 = t.hat[1][i2] * wz1;
-    acc[0] = fma(t.hat[0][i1], w00, acc[0]);
-    acc[1] = fma(t.hat[1][i1], w00, acc[1]);
-    acc[2] = fma(t.hat[0][i1], w10, acc[2]);
-    acc[3] = fma(t.hat[1][i1], w10, acc[3]);
-    acc[4] = fma(t.hat[0][i1], w01, acc[4]);
-    acc[5] = fma(t.hat[1][i1], w01, acc[5]);
-    acc[6] = fma(t.hat[0][i1], w11, acc[6]);
-    acc[7] = fma(t.hat[1][i1], w11, acc[7]);
+  if (on) {
+    const T* rc = r + c * N3;
+    for (int L = g; L < N2; L += kTG) {
+      T s0 = T(0), s1 = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T v = rc[L + N2 * k];
+        s0 = fma(t.hat[0][k], v, s0);
+        s1 = fma(t.hat[1][k], v, s1);
+      }
+      const int i = L % N, j = L / N;
+      const T x0y0 = t.hat[0][i] * t.hat[0][j], x1y0 = t.hat[1][i] * t.hat[0][j];
+      const T x0y1 = t.hat[0][i] * t.hat[1][j], x1y1 = t.hat[1][i] * t.hat[1][j];
+      acc[0] = fma(x0y0, s0, acc[0]);
+      acc[1] = fma(x1y0, s0, acc[1]);
+      acc[2] = fma(x0y1, s0, acc[2]);
+      acc[3] = fma(x1y1, s0, acc[3]);
+      acc[4] = fma(x0y0, s1, acc[4]);
+      acc[5] = fma(x1y0, s1, acc[5]);
+      acc[6] = fma(x0y1, s1, acc[6]);
+      acc[7] = fma(x1y1, s1, acc[7]);
+    }
+  }
+  // xor offsets below kTG stay within the cell's lanes.  Levels with offsets
+  // kTG/2, kTG/4, kTG/8: the lower lane of a pair keeps values [0, h), the
+  // upper one [h, 2h), each adding the partner's copy of what it keeps; then
+  // the lane holds corner g / (kTG / 8), summed over the remaining offsets.
+#pragma unroll
+  for (int h = 4, o = kTG / 2; h >= 1; h >>= 1, o >>= 1) {
+    const bool upper = (g & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const T send = upper ? acc[k] : acc[k + h];
+      const T keep = upper ? acc[k + h] : acc[k];
+      acc[k] = keep + __shfl_xor_sync(FULLMASK, send, o);
+    }
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(FULLMASK, acc[k], o);
-  if (lane < 8) {
-    T v = acc[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k)
-      if (lane == k) v = acc[k];
-    corners[c * 8 + lane] = (double)v;
-  }
+  for (int o = kTG / 16; o > 0; o >>= 1) acc[0] += __shfl_xor_sync(FULLMASK, acc[0], o);
+  constexpr int kSpan = kTG / 8;   // lanes per corner
+  if (on && g % kSpan == 0) corners[c * 8 + g / kSpan] = (double)acc[0];
 }
 
 template <typename T>
@@ -2606,35 +2653,41 @@ __global__ void __launch_bounds__(256) k_restrict_cells_batch(const __grid_const
   restrict_cells_body<T>(bt.mp[m].ncell, (const T*)bt.in[m], (double*)bt.out[m], blockIdx.x - bt.block0[m]);
 }
 
-// u_T(i) += sum_c u_hat(vertex(T, c)) prod_k phi_{c_k}(zeta_{i_k}): one warp
-// per cell; the 8 corner values are loaded once and broadcast.
+// u_T(i) += sum_c u_hat(vertex(T, c)) prod_k phi_{c_k}(zeta_{i_k}), separable:
+// the cell's first 8 lanes load its corner values and broadcast them; each
+// lane blends them bilinearly in x and y for its z-line (i, j), once for the
+// z = 0 and once for the z = 1 corners, and adds the linear blend in z to the
+// n values of the line (coalesced across the lanes; two FMAs per dof).
 template <typename T>
 __device__ __forceinline__ void prolong_add_body(const MeshParams& mp, const double* __restrict__ uhat,
                                                  T* __restrict__ u, unsigned bid) {
-  const long long c = ((long long)bid * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (c >= mp.ncell) return;
-  int cx, cy, cz;
-  cell_xyz(mp, c, cx, cy, cz);
-  const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
+  const long long c0 = (((long long)bid * blockDim.x + threadIdx.x) >> 5) * kTCells;
+  if (c0 >= mp.ncell) return;   // the whole warp
+  const long long c = c0 + lane / kTG;
+  const int g = lane % kTG;
+  const bool on = c < mp.ncell;
   T cv = T(0);
-  if (lane < 8) {
-    const long long v = (cx + (lane & 1)) + vx * (cy + ((lane >> 1) & 1)) + vxy * (cz + (lane >> 2));
+  if (on && g < 8) {
+    int cx, cy, cz;
+    cell_xyz(mp, c, cx, cy, cz);
+    const long long vx = mp.nx + 1, vxy = (long long)(mp.nx + 1) * (mp.ny + 1);
+    const long long v = (cx + (g & 1)) + vx * (cy + ((g >> 1) & 1)) + vxy * (cz + (g >> 2));
     cv = (T)uhat[v];
   }
   T cor[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) cor[k] = __shfl_sync(FULLMASK, cv, k);
+  for (int k = 0; k < 8; ++k) cor[k] = __shfl_sync(FULLMASK, cv, lane - g + k);
+  if (!on) return;
   const Tab<T>& t = tab<T>();
   T* uc = u + c * N3;
-  for (int i = lane; i < N3; i += 32) {
-    const int i1 = i % N, i2 = (i / N) % N, i3 = i / N2;
-    const T x0 = t.hat[0][i1], x1 = t.hat[1][i1];
-    const T e00 = fma(x1, cor[1], x0 * cor[0]), e10 = fma(x1, cor[3], x0 * cor[2]);
-    const T e01 = fma(x1, cor[5], x0 * cor[4]), e11 = fma(x1, cor[7], x0 * cor[6]);
-    const T y0 = t.hat[0][i2], y1 = t.hat[1][i2];
-    const T f0 = fma(y1, e10, y0 * e00), f1 = fma(y1, e11, y0 * e01);
-    uc[i] += fma(t.hat[1][i3], f1, t.hat[0][i3] * f0);
+  for (int L = g; L < N2; L += kTG) {
+    const int i = L % N, j = L / N;
+    const T x0 = t.hat[0][i], x1 = t.hat[1][i], y0 = t.hat[0][j], y1 = t.hat[1][j];
+    const T g0 = fma(y1, fma(x1, cor[3], x0 * cor[2]), y0 * fma(x1, cor[1], x0 * cor[0]));
+    const T g1 = fma(y1, fma(x1, cor[7], x0 * cor[6]), y0 * fma(x1, cor[5], x0 * cor[4]));
+#pragma unroll
+    for (int k = 0; k < N; ++k) uc[L + N2 * k] = fma(t.hat[1][k], g1, fma(t.hat[0][k], g0, uc[L + N2 * k]));
   }
 }
 
@@ -3041,9 +3094,10 @@ cudaError_t diag(const MeshParams& mp, double* d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// kTCells cells per warp, 8 warps per block.
 cudaError_t restrict_cells(const MeshParams& mp, const void* r, double* corners, bool fp32, cudaStream_t s) {
   if (mp.ncell == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((mp.ncell * 32 + 255) / 256);
+  const unsigned grid = (unsigned)((mp.ncell + 8 * kTCells - 1) / (8 * kTCells));
   if (fp32)
     k_restrict_cells<float><<<grid, 256, 0, s>>>(mp.ncell, (const float*)r, corners);
   else
@@ -3054,7 +3108,7 @@ cudaError_t restrict_cells(const MeshParams& mp, const void* r, double* corners,
 
 cudaError_t prolong_add(const MeshParams& mp, const double* uhat, void* u, bool fp32, cudaStream_t s) {
   if (mp.ncell == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((mp.ncell * 32 + 255) / 256);
+  const unsigned grid = (unsigned)((mp.ncell + 8 * kTCells - 1) / (8 * kTCells));
   if (fp32)
     k_prolong_add<float><<<grid, 256, 0, s>>>(mp, uhat, (float*)u);
   else
@@ -3181,7 +3235,7 @@ cudaError_t smooth_batch(BatchTable& bt, int prec, cudaStream_t s) {
 
 cudaError_t restrict_batch(BatchTable& bt, bool fp32, cudaStream_t s) {
   if (bt.k <= 0) return cudaSuccess;
-  fill_blocks(bt, 8);   // one warp per cell, 8 warps per block
+  fill_blocks(bt, 8 * kTCells);   // kTCells cells per warp, 8 warps per block
   if (bt.block0[bt.k] == 0) return cudaSuccess;
   if (fp32)
     k_restrict_cells_batch<float><<<bt.block0[bt.k], 256, 0, s>>>(bt);
@@ -3193,7 +3247,7 @@ cudaError_t restrict_batch(BatchTable& bt, bool fp32, cudaStream_t s) {
 
 cudaError_t prolong_batch(BatchTable& bt, bool fp32, cudaStream_t s) {
   if (bt.k <= 0) return cudaSuccess;
-  fill_blocks(bt, 8);
+  fill_blocks(bt, 8 * kTCells);
   if (bt.block0[bt.k] == 0) return cudaSuccess;
   if (fp32)
     k_prolong_add_batch<float><<<bt.block0[bt.k], 256, 0, s>>>(bt);
