@@ -43,7 +43,7 @@ CPU_SAMPLE = dict(n=8, p=4)        # oracle sample: same workload family, 8^3 ce
 # DRAM bytes (read + write) of one k_smooth_pcg<double> launch on this mesh, from
 # the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt;
 # None while no capture of the current kernel exists.
-SMOOTHER_TRAFFIC_BYTES = 102.688256e6 + 14.646784e6
+SMOOTHER_TRAFFIC_BYTES = 102.545408e6 + 14.266368e6
 
 
 def fp64_peak_tflops():

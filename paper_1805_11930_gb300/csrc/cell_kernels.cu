@@ -114,6 +114,11 @@ template <> struct Store<df> { using type = double; };
 __device__ __forceinline__ float shfl_x(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ df shfl_x(df v, int o) { return shfl_xor(v, o); }
+__device__ __forceinline__ float shfl_i(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_i(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ df shfl_i(df v, int src) {
+  return df(__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src));
+}
 
 // Per-cell coefficients and face data staged in shared memory (computed
 // once per cell; faces f = 2d + s, s = 0 low side, 1 high side).
@@ -1434,14 +1439,19 @@ __device__ __forceinline__ T cell_sum(T part, int lane, T* red) {
 }
 
 // Two cell sums at once (the same summation order as cell_sum for each).
+// One cell per warp: after the first level the lower half-warp carries the
+// partial sums of a and the upper half those of b, so the remaining levels
+// reduce one value per lane; each sum is added in the same tree as in
+// cell_sum (the same bits, half the adds).
 template <typename T>
 __device__ __forceinline__ void cell_sum2(T& a, T& b, int lane, T* red) {
   if (CPW == 1) {
+    const bool hi = (lane & 16) != 0;
+    T v = (hi ? b : a) + shfl_x(hi ? a : b, 16);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += shfl_x(a, o);
-      b += shfl_x(b, o);
-    }
+    for (int o = 8; o > 0; o >>= 1) v += shfl_x(v, o);
+    a = shfl_i(v, 0);
+    b = shfl_i(v, 16);
   } else {
     red[lane] = a;
     red[LINES + lane] = b;
@@ -1459,6 +1469,17 @@ __device__ __forceinline__ void cell_sum2(T& a, T& b, int lane, T* red) {
     a = sa;
     b = sb;
   }
+}
+
+// a / b of a cell (the same on its lanes), computed on the cell's first lane
+// and broadcast, so that the division's instructions run once per cell
+// instead of on every lane; `on` as on the cell's lanes.
+template <typename T>
+__device__ __forceinline__ T cell_div(T a, T b, int lane, bool on) {
+  const int src = CPW == 1 ? 0 : (lane < LINES ? (lane / N2) * N2 : lane);
+  T q = T(0);
+  if (on && lane == src) q = a / b;
+  return shfl_i(q, src);
 }
 
 // Extra shared values per warp of the inner-PCG smoother: the factored form's
@@ -1595,8 +1616,8 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
     // delta += alpha p, r -= alpha q, and with the new r both (r, r) and
     // (r, z), z = r / diag (kept in S0 for the direction update)
     T prr2 = T(0), prz2 = T(0);
+    const T alpha = cell_div(rz, pq, lane, upd);
     if (upd) {
-      const T alpha = rz / pq;
       my_elems([&](int e) {
         DL[e] = fma(alpha, P[e], DL[e]);
         const T r = fma(-alpha, Q[e], R[e]);
@@ -1614,8 +1635,8 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
       upd = false;
     }
     if (upd && it >= maxit) upd = false;
+    const T beta = cell_div(prz2, rz, lane, upd);
     if (upd) {
-      const T beta = prz2 / rz;
       rz = prz2;
       my_elems([&](int e) { P[e] = fma(beta, P[e], S0[e]); });
     }
