@@ -470,37 +470,58 @@ __device__ __forceinline__ void factor_tables(T* M1s, T* MVs, int lane) {
   }
 }
 
+// Per cell slot and face f = 2d + s, the factors the face terms share (kept
+// in FC, 4 values per face, computed once per cell so that the per-entry and
+// per-node work is one product less each):
+//   FC[0] = -|F| gamma,  FC[1] = -|F| kap sg / h_d,  FC[2] = |J|/h_d ks,
+//   FC[3] = |J|/h_d gamma,  ks = -kap sg / h_d, sg = +-1 the outward sign.
+template <typename T, int C = CPW>
+__device__ __forceinline__ void face_consts(T* FC, const MeshParams& mp, const CellInfo<T>* ci,
+                                            const unsigned char* act, int lane) {
+  for (int it = lane; it < C * 6; it += 32) {
+    const int cw = it / 6, f = it - cw * 6, d = f >> 1, S = f & 1;
+    if (!act[cw]) continue;
+    const T ih = Prec<T>::ih(mp, d), area = Prec<T>::area(mp, d);
+    const T kap = ci[cw].kap[f], gam = ci[cw].gam[f], jh = ci[cw].jh[d];
+    const T skap = S ? -kap : kap;
+    T* q = FC + it * 4;
+    q[0] = -area * gam;
+    q[1] = skap * (area * ih);
+    q[2] = jh * (skap * ih);
+    q[3] = jh * gam;
+  }
+}
+
 // Ah_d = M^-1 A_d of every staged cell, 3 n^2 per cell (row-major; Ah_d[i][j]
 // multiplies x_j into z_i):
 //   M^-1 A_d = |J| K_d / h_d^2 M^-1 S + [d = 2] c |J| I
 //            + sum over the non-Neumann faces s of d of
 //              |F| [ ks ((M^-1 e_e) dl_s^T + (M^-1 dl_s) e_e^T) + gamma (M^-1 e_e) e_e^T ],
-// ks = -kap sg / h_d, e = end node of side s, sg = +-1 its outward sign.
+// ks = -kap sg / h_d, e = end node of side s, sg = +-1 its outward sign
+// (|F| = |J| / h_d on these cells); fc: the cell's face factors.
 template <typename T>
-__device__ __forceinline__ T hat_entry(const MeshParams& mp, const CellInfo<T>& c, int d, int i, int j) {
+__device__ __forceinline__ T hat_entry(const CellInfo<T>& c, const T* fc, int d, int i, int j) {
   const Tab<T>& t = tab<T>();
   T a = c.kd[d] * t.MIS[i][j];
   if (d == 2 && i == j) a = a + c.cJ;
-  const T ih = Prec<T>::ih(mp, d);
   for (int s = 0; s < 2; ++s) {
     const int f = 2 * d + s;
     if (c.kind[f] == 2) continue;
-    const int e = s ? N - 1 : 0;
-    const T ks = (s ? -c.kap[f] : c.kap[f]) * ih;
-    T fv = ks * t.mie[s][i] * t.dl[s][j];
-    if (j == e) fv = fma(ks, t.midl[s][i], fma(c.gam[f], t.mie[s][i], fv));
-    a = fma(c.jh[d], fv, a);
+    const T* q = fc + f * 4;
+    const T me = t.mie[s][i];
+    a = fma(q[2] * me, t.dl[s][j], a);
+    if (j == (s ? N - 1 : 0)) a = fma(q[2], t.midl[s][i], fma(q[3], me, a));
   }
   return a;
 }
 
 template <typename T>
-__device__ __forceinline__ void hat_matrices(const MeshParams& mp, T* Ah, const CellInfo<T>* ci,
-                                             const unsigned char* act, int lane) {
+__device__ __forceinline__ void hat_matrices(T* Ah, const T* FC, const CellInfo<T>* ci, const unsigned char* act,
+                                             int lane) {
   for (int k = lane; k < CPW * 3 * N2; k += 32) {
     const int cw = k / (3 * N2), r = k - cw * 3 * N2, d = r / N2, i = (r % N2) / N, j = r % N;
     if (!act[cw]) continue;
-    Ah[k] = hat_entry(mp, ci[cw], d, i, j);
+    Ah[k] = hat_entry(ci[cw], FC + cw * 24, d, i, j);
   }
 }
 
@@ -509,9 +530,10 @@ __device__ __forceinline__ void hat_matrices(const MeshParams& mp, T* Ah, const 
 // u_o = u_nb(end 1-s) and normal derivative dn_o = sg / h_d sum_j dl_{1-s}[j] u_nb(j),
 //   FS[cw][f][0][L] = |F| (-gamma u_o - kap dn_o),   FS[cw][f][1][L] = sg |F| / h_d kap u_o,
 // (zero on boundary faces): the parts of qv = gamma [[u]] - kap (dn + dn_o),
-// qdv = -kap [[u]] that the block D_T leaves out.  12 n^2 values per cell.
+// qdv = -kap [[u]] that the block D_T leaves out.  12 n^2 values per cell;
+// FC the face factors of face_consts.
 template <typename T, typename G, int C = CPW>
-__device__ __forceinline__ void neighbour_faces(T* FS, const G* __restrict__ gu, const MeshParams& mp, int lane,
+__device__ __forceinline__ void neighbour_faces(T* FS, const T* FC, const G* __restrict__ gu, int lane,
                                                 const unsigned char* act, const CellInfo<T>* ci) {
   const Tab<T>& t = tab<T>();
   for (int it = lane; it < C * 6 * N2; it += 32) {
@@ -535,11 +557,9 @@ __device__ __forceinline__ void neighbour_faces(T* FS, const G* __restrict__ gu,
 #pragma unroll
         for (int j = 0; j < N; ++j) dno = fma(t.dl[1 - S][j], T(xo[j * st]), dno);
       }
-      const T ih = Prec<T>::ih(mp, d), area = Prec<T>::area(mp, d);
-      const T sga = S ? area : -area;
-      dno = dno * (S ? ih : -ih);
-      qv = -area * fma(ci[cw].gam[f], tout, ci[cw].kap[f] * dno);
-      qd = sga * ih * (ci[cw].kap[f] * tout);
+      const T* q = FC + (cw * 6 + f) * 4;
+      qv = fma(q[0], tout, q[1] * dno);
+      qd = -q[1] * tout;
     }
     T* fs = FS + (cw * 6 + f) * 2 * N2;
     fs[L] = qv;
@@ -610,14 +630,14 @@ __device__ __forceinline__ void hat_pass(const T* X, T* Z, const T* Ah, const T*
 }
 
 // Y = A X (FULL, neighbour values from gu) or D_T X in the factored form;
-// S0, S1 scratch vectors, Ah, M1s, MVs, FS as above.  X and Y distinct from
-// S0 and S1.
+// S0, S1 scratch vectors, Ah, M1s, MVs, FS as above, the face factors FC
+// (face_consts) right after FS.  X and Y distinct from S0 and S1.
 template <bool FULL, typename T, typename G>
 __device__ __forceinline__ void factored_apply(const T* X, T* Y, T* S0, T* S1, const T* Ah, const T* M1s,
-                                               const T* MVs, T* FS, const G* gu, const MeshParams& mp, int lane,
+                                               const T* MVs, T* FS, const G* gu, int lane,
                                                const unsigned char* act, const CellInfo<T>* ci) {
   if (FULL) {
-    neighbour_faces(FS, gu, mp, lane, act, ci);
+    neighbour_faces(FS, FS + 12 * CPW * N2, gu, lane, act, ci);
     __syncwarp();
   }
   hat_pass<FULL>(X, S0, Ah, MVs, FS, lane, act);
@@ -631,8 +651,21 @@ __device__ __forceinline__ void factored_apply(const T* X, T* Y, T* S0, T* S1, c
 }
 
 // Shared values per warp of the factored form: Ah (3 CPW n^2), M1s (n^2),
-// MVs (4 n), FS (12 CPW n^2).
-constexpr int kFactorExtra = 3 * CPW * N2 + N2 + 4 * N + 12 * CPW * N2;
+// MVs (4 n), FS (12 CPW n^2), FC (24 CPW).
+constexpr int kFactorExtra = 3 * CPW * N2 + N2 + 4 * N + 12 * CPW * N2 + 24 * CPW;
+
+// The per-cell matrices and the tables of the factored form (Ah, M1s, MVs as
+// above; FC = FS + 12 CPW n^2 receives the face factors first).
+template <typename T>
+__device__ __forceinline__ void factor_setup(T* Ah, T* M1s, T* MVs, T* FS, const MeshParams& mp,
+                                             const CellInfo<T>* ci, const unsigned char* act, int lane) {
+  T* FC = FS + 12 * CPW * N2;
+  face_consts(FC, mp, ci, act, lane);
+  factor_tables(M1s, MVs, lane);
+  __syncwarp();
+  hat_matrices(Ah, FC, ci, act, lane);
+  __syncwarp();
+}
 
 
 // Y = A^v X for the warp's cells.  S0, S1 scratch.
@@ -1380,10 +1413,8 @@ __device__ __forceinline__ void apply_body(const MeshParams& mp, const G* __rest
     T* M1s = Ah + 3 * CPW * N2;
     T* MVs = M1s + N2;
     T* FS = MVs + 4 * N;
-    hat_matrices(mp, Ah, ci, act, lane);
-    factor_tables(M1s, MVs, lane);
-    __syncwarp();
-    factored_apply<FULL>(X, Y, S0, S1, Ah, M1s, MVs, FS, u, mp, lane, act, ci);
+    factor_setup(Ah, M1s, MVs, FS, mp, ci, act, lane);
+    factored_apply<FULL>(X, Y, S0, S1, Ah, M1s, MVs, FS, u, lane, act, ci);
   } else if constexpr (FAC && ADV) {
     adv_tables(Xt, lane);
     __syncwarp();
@@ -1525,9 +1556,7 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
   T* MVs = M1s + N2;
   T* FS = MVs + 4 * N;
   if constexpr (FAC && !ADV) {
-    hat_matrices(mp, Ah, ci, act, lane);
-    factor_tables(M1s, MVs, lane);
-    __syncwarp();
+    factor_setup(Ah, M1s, MVs, FS, mp, ci, act, lane);
   } else if constexpr (FAC && ADV) {
     adv_tables(Xt, lane);
     __syncwarp();
@@ -1556,7 +1585,7 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
     }
     __syncwarp();
     if constexpr (FAC && !ADV) {
-      factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, FS, uold, mp, lane, act, ci);
+      factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, FS, uold, lane, act, ci);
     } else if constexpr (FAC && ADV) {
       adv_apply_e<true>(P, Q, S0, S1, Xt, uold, mp, lane, act, ci);
     } else {
@@ -1604,7 +1633,7 @@ __device__ __forceinline__ void smooth_pcg_body(const MeshParams& mp, const G* _
       volume<ADV>(P, Q, S0, S1, lane, ci, act, react);
       all_faces<false, ADV>(P, Q, F0, F1, (const G*)nullptr, mp, cell0, lane, act, ci);
     } else if constexpr (FAC) {
-      factored_apply<false>(P, Q, S0, S1, Ah, M1s, MVs, FS, (const G*)nullptr, mp, lane, act, ci);
+      factored_apply<false>(P, Q, S0, S1, Ah, M1s, MVs, FS, (const G*)nullptr, lane, act, ci);
     } else {
       block_kron(P, Q, S0, S1, Ah, lane, act);
     }
@@ -1751,10 +1780,8 @@ __global__ void __launch_bounds__(256) k_smooth_inv(MeshParams mp, const G* __re
       T* Ah = Xt;
       T* M1s = Ah + 3 * CPW * N2;
       T* MVs = M1s + N2;
-      hat_matrices(mp, Ah, ci, act, lane);
-      factor_tables(M1s, MVs, lane);
-      __syncwarp();
-      factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, MVs + 4 * N, uold, mp, lane, act, ci);
+      factor_setup(Ah, M1s, MVs, MVs + 4 * N, mp, ci, act, lane);
+      factored_apply<true>(P, Q, S0, S1, Ah, M1s, MVs, MVs + 4 * N, uold, lane, act, ci);
     } else if constexpr (FAC && ADV) {
       adv_tables(Xt, lane);
       __syncwarp();

@@ -33,16 +33,19 @@ constexpr int AM0 = 3 * N * RP / 4;
 constexpr int AMC = (AM0 % 2) ? AM0 : AM0 + 1;
 constexpr int AMF = 4 * AMC;                   // floats per cell of the matrices
 constexpr int FSF = 12 * N2;                   // floats per cell of the neighbour face values
+constexpr int FCF = 24;                        // floats per cell of the face factors
 
-// Shared bytes per warp: staging area, per-cell matrices, (full operator)
-// neighbour face values, cell records, cell flags.
+// Shared bytes per warp: staging area, per-cell matrices, face factors,
+// (full operator) neighbour face values, cell records, cell flags.
 __host__ __device__ constexpr size_t warp_bytes(bool full) {
-  return (size_t)(PC * CF + PC * AMF + (full ? PC * FSF : 0)) * 4 + align16(PC * sizeof(CellInfo<float>)) + 16;
+  return (size_t)(PC * CF + PC * AMF + PC * FCF + (full ? PC * FSF : 0)) * 4 + align16(PC * sizeof(CellInfo<float>)) +
+         16;
 }
 
 struct Mem {
   float* st;
   float* ah;
+  float* fc;
   float* fs;
   CellInfo<float>* ci;
   unsigned char* act;
@@ -52,19 +55,22 @@ __device__ __forceinline__ Mem carve_plane(unsigned char* raw, bool full) {
   Mem m;
   m.st = reinterpret_cast<float*>(raw);
   m.ah = m.st + PC * CF;
-  m.fs = m.ah + PC * AMF;
-  unsigned char* tail = raw + (size_t)(PC * CF + PC * AMF + (full ? PC * FSF : 0)) * 4;
+  m.fc = m.ah + PC * AMF;
+  m.fs = m.fc + PC * FCF;
+  unsigned char* tail = raw + (size_t)(PC * CF + PC * AMF + PC * FCF + (full ? PC * FSF : 0)) * 4;
   m.ci = reinterpret_cast<CellInfo<float>*>(tail);
   m.act = tail + align16(PC * sizeof(CellInfo<float>));
   return m;
 }
 
-// Ah_d of the warp's cells, rows padded to RP.
+// The face factors and Ah_d of the warp's cells, rows padded to RP.
 __device__ __forceinline__ void matrices(const MeshParams& mp, const Mem& m, int lane) {
+  face_consts<float, PC>(m.fc, mp, m.ci, m.act, lane);
+  __syncwarp();
   for (int it = lane; it < PC * 3 * N2; it += 32) {
     const int cw = it / (3 * N2), r = it - cw * 3 * N2, d = r / N2, i = (r % N2) / N, j = r % N;
     if (!m.act[cw]) continue;
-    m.ah[cw * AMF + (d * N + i) * RP + j] = hat_entry(mp, m.ci[cw], d, i, j);
+    m.ah[cw * AMF + (d * N + i) * RP + j] = hat_entry(m.ci[cw], m.fc + cw * FCF, d, i, j);
   }
 }
 
@@ -278,7 +284,7 @@ __device__ __forceinline__ void apply_plane_body(const MeshParams& mp, const flo
   const long long nval = left < PC * N3 ? left : PC * N3;
   load_cells(u, cell0, nval, m.st, lane);
   matrices(mp, m, lane);
-  if (FULL) neighbour_faces<float, float, PC>(m.fs, u, mp, lane, m.act, m.ci);
+  if (FULL) neighbour_faces<float, float, PC>(m.fs, m.fc, u, lane, m.act, m.ci);
   __syncwarp();
   const LaneConst lc = lane_const(k);
   float P[N2], Q[N2], Z[N2];
@@ -337,7 +343,7 @@ __device__ __forceinline__ void smooth_plane_body(const MeshParams& mp, const fl
   // defect d = f - A u_old
   if (!zero) {
     load_cells(uold, cell0, nval, m.st, lane);
-    neighbour_faces<float, float, PC>(m.fs, uold, mp, lane, m.act, m.ci);
+    neighbour_faces<float, float, PC>(m.fs, m.fc, uold, lane, m.act, m.ci);
     __syncwarp();
     read_plane(m.st, cw, k, P);
     pl::apply<true>(P, Q, Z, m, cw, k, on, lc);
