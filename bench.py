@@ -14,7 +14,8 @@ restriction, AMG cycle, prolongation, Krylov vector kernels.
   roofline   the dominant kernel (the fused smoother, FP64): the FP64
              operations it issues per launch / its CUDA-event duration in the
              timed steps, against the FP64 pipe peak (4 flop/clk/SM x 152 SMs
-             x 2070 MHz); the survey's generic operation count beside it
+             x 2070 MHz); the generic operation count (32 n^4 + 120 n^3 per
+             cell and apply) beside it
   extra      apply GDOF/s (FP64 and FP32), the mixed-precision solve time
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgmg|reference]
@@ -43,7 +44,7 @@ CPU_SAMPLE = dict(n=8, p=4)        # oracle sample: same workload family, 8^3 ce
 # DRAM bytes (read + write) of one k_smooth_pcg<double> launch on this mesh, from
 # the ncu capture summarised in profiles/k_smooth_pcg_fp64_lognormal_32cubed_q4.txt;
 # None while no capture of the current kernel exists.
-SMOOTHER_TRAFFIC_BYTES = 102.545408e6 + 14.266368e6
+SMOOTHER_TRAFFIC_BYTES = 102.546176e6 + 14.194944e6
 
 
 def fp64_peak_tflops():
@@ -226,7 +227,7 @@ def run_dgmg(args, rank, world, local_rank):
                               "launch on the solve's stream inside the timed steps",
                 "achieved_generic_count": round(achieved_generic, 4),
                 "frac_generic_count": round(achieved_generic / peak, 4),
-                "generic_count_note": "the survey's generic count (32 n^4 + 120 n^3 per cell per apply, one apply "
+                "generic_count_note": "the generic count (32 n^4 + 120 n^3 per cell per apply, one apply "
                                       "per defect and per inner iteration) over the same time; above 1 because the "
                                       "kernels do the same operator with fewer operations",
                 "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x sm_max_mhz (derived from the nominal "

@@ -958,7 +958,7 @@ __device__ __forceinline__ void face_upwind(const T* X, T* Y, T* F0, T* F1, cons
 // Tables in shared memory (their index varies across the lanes, which
 // constant memory would serialise):
 // AT = [B | B^T | Dg | Dg^T | M | W2], n^2 each, row-major, W2[i + n j] =
-// w_i w_j; then [w | w gq | dl_0 | dl_1], n each.
+// w_i w_j; then [w | gq | dl_0 | dl_1], n each.
 constexpr int kAdvTab = 6 * N2 + 4 * N;
 
 template <typename T>
@@ -975,7 +975,7 @@ __device__ __forceinline__ void adv_tables(T* AT, int lane) {
   }
   for (int k = lane; k < N; k += 32) {
     AT[6 * N2 + k] = t.w[k];
-    AT[6 * N2 + N + k] = t.w[k] * t.gq[k];
+    AT[6 * N2 + N + k] = t.gq[k];
     AT[6 * N2 + 2 * N + k] = t.dl[0][k];
     AT[6 * N2 + 3 * N + k] = t.dl[1][k];
   }
@@ -988,7 +988,7 @@ __device__ __forceinline__ void adv_tables(T* AT, int lane) {
 //   BT[(cw 3 + D) 3 n^2 + {0, 1, 2} n^2 + i0 + n i1]
 //     = |J|/h_D w_i0 w_i1 {c0, c1} (gq_i0, gq_i1),  |J| K_D / h_D^2 w_i0 w_i1,
 // so that at Gauss point (i0, i1, i2) w3 |J|/h_D b_D = w_i2 (c0' + gq_i2 c1')
-// and w3 |J| K_D / h_D^2 = w_i2 k'.
+// and w3 |J| K_D / h_D^2 = w_i2 k': the flux is w_i2 (k' g - (c0' + gq_i2 c1') u).
 template <typename T>
 __device__ __forceinline__ void adv_point_tables(T* BT, const T* AT, int lane, const CellInfo<T>* ci,
                                                  const unsigned char* act) {
@@ -1047,9 +1047,8 @@ __device__ __forceinline__ void volume_adv_e(const T* X, T* Y, T* S0, T* S1, T* 
 #pragma unroll
       for (int j = 0; j < N; ++j) g = fma(dr[j], line[j * st], g);
       const T* bt = BT + (cw * 3 + D) * 3 * N2 + i0 + N * i1;
-      const T wz = Wq[i2];
-      const T beta = fma(Wq[N + i2], bt[N2], wz * bt[0]);   // w3 |J|/h_D b_D
-      S0[e] = fma(wz * bt[2 * N2], g, -beta * S1[e]);
+      const T bq = fma(Wq[N + i2], bt[N2], bt[0]);   // w3 |J|/h_D b_D / w_i2
+      S0[e] = Wq[i2] * fma(bt[2 * N2], g, -bq * S1[e]);
     }
     __syncwarp();
     for (int e = lane; e < VEC; e += 32) {
@@ -2584,7 +2583,8 @@ __global__ void k_diag(MeshParams mp, double* __restrict__ diag) {
   diag[gid] = acc;
 }
 
-// diag(D_T) for b = 0 from the Kronecker form of reading 20,
+// diag(D_T) for b = 0 from the Kronecker form of the block on affine
+// axis-aligned cells with K diagonal and constant per cell,
 // D_T = A_x (x) M (x) M + M (x) A_y (x) M + M (x) M (x) A_z:
 //   diag(D_T)(i0, i1, i2) = a_x(i0) m(i1) m(i2) + m(i0) a_y(i1) m(i2) + m(i0) m(i1) a_z(i2),
 // m = diag(M), a_d = diag(A_d) = |J| K_d / h_d^2 S_ii (+ c |J| M_ii for d = 2)

@@ -7,7 +7,8 @@
 // GB300 that bounds the FP32 kernels by shared-memory instructions, with the
 // FP32 pipe a quarter busy.  Here lane (cw, k) of a warp owns z-plane k of
 // cell slot cw in registers (PC = 32 / n cells per warp).  The block is
-// applied in the factored form of reading 22,
+// applied in the factored form (M symmetric positive definite, so
+// D_T = sum_d A_d (x)_d M (x) M = (M (x) M (x) M) o sum_d (M^-1 A_d) x_d),
 //     Q = M_x M_y M_z sum_d Ah_d x_d P,   Ah_d = M^-1 A_d,
 // with the contractions along x and y in registers (the per-cell matrix rows
 // come from shared memory in 16-byte loads, each row serving n lines) and
