@@ -551,7 +551,9 @@ dgmg_status dgmg_batch_remove(dgmg_batch* batch, int slot);
  * The first call on a device sets it up, synchronously, with that device
  * current: it copies the 1D tables into constant memory and looks up the
  * scratch array's device address, then keeps both for the life of the
- * process.  Calls on a device after a cudaDeviceReset of that device are not
+ * process.  Make that first call on each device before any stream capture
+ * begins there, since its set-up copies synchronously.  Calls on a device
+ * after a cudaDeviceReset of that device are not
  * supported (the kept set-up is not redone).  Every corner sum a call reads
  * was written earlier in the same call, so the scratch needs no clearing.
  * All calls on a device share the one scratch array: calls whose work may
