@@ -247,18 +247,17 @@ __device__ __forceinline__ void grad_pass(const T* __restrict__ U, T* __restrict
       lo *= ci[cw].jh[D] * wab;
       hi *= ci[cw].jh[D] * wab;
     }
+    const T dh = hi - lo;
     T q[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       T g = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) g = fma(t.Dg[i][j], u[j], g);
-      T v = kd * t.w[i] * g;
-      if (ADV) {
-        const T bq = lo + (hi - lo) * t.gq[i];
-        v = fma(-t.w[i] * bq, u[i], v);
-      }
-      q[i] = v;
+      // w_i (kd g - b u), the weight applied once
+      T v = kd * g;
+      if (ADV) v = fma(-fma(dh, t.gq[i], lo), u[i], v);
+      q[i] = t.w[i] * v;
     }
 #pragma unroll
     for (int r = 0; r < N; ++r) {
